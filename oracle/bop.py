@@ -1,0 +1,595 @@
+"""FP64 oracle of the analytic-BOP hot path, written from arXiv:1803.07491.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  The structural part
+(neighbours, Slater-Koster blocks, clusters, moments and their reverse sweep)
+is plain C in ``bop_oracle.c``; the per-orbital scalar stages below are
+numpy, written so that every function also accepts complex input: the
+weights w_n = dU/dmu_n are taken by complex-step differentiation of the
+scalar stage, which is exact to rounding and independent of any hand-written
+chain rule.
+
+Readings of the paper taken here (each listed in the design doc):
+  * n moments means mu_0 .. mu_{n-1}; n is odd, K = (n-1)/2 hops.
+  * the phase is eps = +cos(phi) (band bottom at phi = pi); Eq. chi and
+    Eq. Fermi-phase are only consistent with that sign.
+  * gamma_0 in the bond energy is (E_ialpha - a_inf)/b_inf.
+  * the DOS sums run over m = 0 .. n_exp with g_0 = 1.
+  * Jackson kernel with N = n_exp; g_m = g^J_{m+1}/g^J_1.
+  * Gershgorin over the computed levels n = 0 .. K'-1, b_0 = 0.
+  * b_inf is floored at B_INF_MIN so that an isolated atom (zero band width)
+    gives a narrow band instead of a division by zero.
+  * the recursion is truncated where b_{n+1}^2 <= TRUNC_REL * (mu_2 - mu_1^2).
+  * local charge neutrality acts per atom (one shift per atom).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+from math import comb
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bop_oracle.c")
+_SO = os.path.join(_HERE, "_build", "liborc.so")
+_LIB = None
+
+B_INF_MIN = 1e-3      # eV, floor of the band-width estimate
+TRUNC_REL = 1e-10     # relative threshold of the recursion truncation
+CS_H = 1e-30          # complex step
+
+
+def build(force: bool = False) -> str:
+    """Compile bop_oracle.c into oracle/_build/liborc.so (gcc, no FMA)."""
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = ctypes.CDLL(build())
+        L = _LIB
+        L.orc_neighbors.restype = ctypes.c_long
+        L.orc_cluster.restype = ctypes.c_int
+        L.orc_moments.restype = ctypes.c_int
+        L.orc_moments_adjoint.restype = ctypes.c_int
+    return _LIB
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class _CModel(ctypes.Structure):
+    _fields_ = [("norb", ctypes.c_int), ("r0", ctypes.c_double), ("lam", ctypes.c_double),
+                ("rc", ctypes.c_double), ("dc", ctypes.c_double), ("b0", ctypes.c_double * 3)]
+
+
+@dataclass
+class Model:
+    """Orthogonal two-centre TB model of one element (Eq. Hij, Eq. cutoff).
+
+    beta_x(r) = b0[x] * exp(-lam (r - r0)) * fcut(r); b0 = (ss sigma,) for s
+    or (dd sigma, dd pi, dd delta) for d, in eV at r0 (Angstrom)."""
+    norb: int
+    b0: tuple
+    r0: float
+    lam: float
+    rc: float
+    dc: float
+    onsite0: float = 0.0
+
+    def c(self) -> _CModel:
+        b = list(self.b0) + [0.0] * (3 - len(self.b0))
+        return _CModel(self.norb, self.r0, self.lam, self.rc, self.dc, (ctypes.c_double * 3)(*b))
+
+
+@dataclass
+class Settings:
+    """Run settings: moments, expansion length, spin, electron count, SCF."""
+    n_e: float                 # electrons per atom, summed over spin
+    n_mom: int = 9
+    n_exp: int = 200
+    n_spin: int = 1
+    scf: str = "none"          # none | lcn | stoner
+    eta: float = 0.5           # LCN mixing
+    scf_tol: float = 1e-9      # max |N_i - N_i^0| (and |dm| for Stoner: scf_tol*10)
+    scf_max_it: int = 200
+    stoner_I: float = 0.0
+    m_mix: float = 0.3
+    m0: float = 2.0
+    dos_floor: float = 0.1     # states/eV, LCN preconditioner floor
+
+
+@dataclass
+class Neighbors:
+    row_ptr: np.ndarray  # int64 [n+1]
+    col: np.ndarray      # int32 [E]
+    img: np.ndarray      # int8  [E, 3]
+
+    @property
+    def n_edges(self):
+        return int(self.row_ptr[-1])
+
+
+# ---------------------------------------------------------------- structure
+
+def neighbors(pos, cell, pbc, rcut) -> Neighbors:
+    """Short-range neighbour list by brute force ("Initialisation": linked
+    cells only make it O(N)); directed CSR sorted by (j, sx, sy, sz)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    cell = np.ascontiguousarray(cell, dtype=np.float64)
+    pbc = np.ascontiguousarray(pbc, dtype=np.int32)
+    n = len(pos)
+    cap = max(64, 32 * n)
+    while True:
+        row = np.zeros(n + 1, np.int64)
+        col = np.zeros(cap, np.int32)
+        img = np.zeros((cap, 3), np.int8)
+        ne = _lib().orc_neighbors(n, _p(pos), _p(cell), _p(pbc), ctypes.c_double(rcut),
+                                  ctypes.c_long(cap), _p(row), _p(col), _p(img))
+        if ne >= 0:
+            return Neighbors(row, col[:ne].copy(), img[:ne].copy())
+        cap = -ne
+
+
+def sk_block(model: Model, d) -> np.ndarray:
+    """Block <i b|H|j g> for bond vector d = r_j - r_i (Eq. Hij rotated by
+    Eq. Hij_rot, via the Slater-Koster direction-cosine table)."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    B = np.zeros(model.norb * model.norb)
+    _lib().orc_block(ctypes.byref(model.c()), _p(d), _p(B))
+    return B.reshape(model.norb, model.norb)
+
+
+def blocks(model: Model, pos, cell, nbr: Neighbors) -> np.ndarray:
+    """H_e for every directed edge: [E, norb, norb]."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    cell = np.ascontiguousarray(cell, dtype=np.float64)
+    H = np.zeros((nbr.n_edges, model.norb, model.norb))
+    _lib().orc_blocks(len(pos), _p(pos), _p(cell), _p(nbr.row_ptr), _p(nbr.col), _p(nbr.img),
+                      ctypes.byref(model.c()), _p(H))
+    return H
+
+
+def edge_vectors(pos, cell, nbr: Neighbors) -> np.ndarray:
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    cell = np.ascontiguousarray(cell, dtype=np.float64)
+    d = np.zeros((nbr.n_edges, 3))
+    _lib().orc_edge_vectors(len(pos), _p(pos), _p(cell), _p(nbr.row_ptr), _p(nbr.col),
+                            _p(nbr.img), _p(d))
+    return d
+
+
+def cluster(i: int, K: int, nbr: Neighbors, max_sites: int = 200000):
+    """Hop levels of (atom, image) sites around atom i (support of the
+    self-returning paths, Eq. momDOS).  Returns (site_atom, site_img,
+    level_end) in canonical order: level, atom, image."""
+    atom = np.zeros(max_sites, np.int32)
+    im = np.zeros((max_sites, 3), np.int8)
+    lev = np.zeros(K + 1, np.int32)
+    ns = _lib().orc_cluster(int(i), int(K), _p(nbr.row_ptr), _p(nbr.col), _p(nbr.img),
+                            int(max_sites), _p(atom), _p(im), _p(lev))
+    if ns < 0:
+        raise ValueError("image index overflow in cluster")
+    if ns > max_sites:
+        return cluster(i, K, nbr, ns)
+    return atom[:ns].copy(), im[:ns].copy(), lev
+
+
+def moments(nbr: Neighbors, H, onsite, n_mom: int, sel=None) -> np.ndarray:
+    """mu_n(i alpha) = <i alpha|H^n|i alpha>, n = 0..n_mom-1 (Eq. momDOS),
+    for one spin channel.  onsite: [n, norb].  Returns [nsel, norb, n_mom]."""
+    assert n_mom % 2 == 1 and n_mom >= 3
+    onsite = np.ascontiguousarray(onsite, dtype=np.float64)
+    n, norb = onsite.shape
+    sel = np.arange(n, dtype=np.int32) if sel is None else np.ascontiguousarray(sel, np.int32)
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    mu = np.zeros((len(sel), norb, n_mom))
+    st = _lib().orc_moments(len(sel), _p(sel), n_mom, norb, _p(nbr.row_ptr), _p(nbr.col),
+                            _p(nbr.img), _p(H), _p(onsite), _p(mu))
+    if st != 0:
+        raise ValueError("image index overflow in cluster")
+    return mu
+
+
+def moments_adjoint(nbr: Neighbors, H, onsite, w, sel=None):
+    """Reverse sweep of ``moments``: with w = dU/dmu [nsel, norb, n_mom]
+    returns (Hbar [E, norb, norb] = dU/dH_e, Ebar [n, norb] = dU/dE)."""
+    onsite = np.ascontiguousarray(onsite, dtype=np.float64)
+    n, norb = onsite.shape
+    sel = np.arange(n, dtype=np.int32) if sel is None else np.ascontiguousarray(sel, np.int32)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    n_mom = w.shape[-1]
+    Hbar = np.zeros((nbr.n_edges, norb, norb))
+    Ebar = np.zeros((n, norb))
+    st = _lib().orc_moments_adjoint(len(sel), _p(sel), n_mom, norb, _p(nbr.row_ptr),
+                                    _p(nbr.col), _p(nbr.img),
+                                    _p(np.ascontiguousarray(H, dtype=np.float64)),
+                                    _p(onsite), _p(w), _p(Hbar), _p(Ebar))
+    if st != 0:
+        raise ValueError("image index overflow in cluster")
+    return Hbar, Ebar
+
+
+def bond_gradient(model: Model, pos, cell, nbr: Neighbors, Hbar) -> np.ndarray:
+    """g_e = sum Hbar_e * dH_e/dd_e for every directed edge, [E, 3]."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    cell = np.ascontiguousarray(cell, dtype=np.float64)
+    g = np.zeros((nbr.n_edges, 3))
+    _lib().orc_bond_gradient(len(pos), _p(pos), _p(cell), _p(nbr.row_ptr), _p(nbr.col),
+                             _p(nbr.img), ctypes.byref(model.c()),
+                             _p(np.ascontiguousarray(Hbar, dtype=np.float64)), _p(g))
+    return g
+
+
+# ---------------------------------------------------------------- scalar stage
+
+def _re(x):
+    return np.real(x)
+
+
+def recursion_coefficients(mu):
+    """Recursion coefficients from moments (Eqs. momtoa, momtob and the
+    c_j^n recursion).  mu: [M, n_mom].  With K' = (n_mom-1)/2 returns
+    a [M, K'] (a_0..a_{K'-1}), b [M, K'+1] (b_0 = 0, b_1..b_{K'}) and
+    nlev [M] = number of a's computed (< K' where the chain was truncated,
+    in which case b[nlev] = 0)."""
+    mu = np.asarray(mu)
+    M, n_mom = mu.shape
+    Kp = (n_mom - 1) // 2
+    dt = mu.dtype
+    a = np.zeros((M, Kp), dt)
+    b = np.zeros((M, Kp + 1), dt)
+    nlev = np.full(M, Kp, np.int64)
+    alive = np.ones(M, bool)
+    width = np.maximum(_re(mu[:, 2] - mu[:, 1] ** 2), 0.0)
+    c_prev = np.zeros((M, Kp + 2), dt)
+    c = np.zeros((M, Kp + 2), dt)
+    c[:, 0] = 1.0
+    for n in range(Kp):
+        # a_n = sum_{j,l} c_j^n c_l^n mu_{j+l+1}
+        an = np.zeros(M, dt)
+        for j in range(n + 1):
+            for l in range(n + 1):
+                an = an + c[:, j] * c[:, l] * mu[:, j + l + 1]
+        a[:, n] = np.where(alive, an, 0.0)
+        # b_{n+1} c^{n+1} = c^n shifted - a_n c^n - b_n c^{n-1}
+        d = np.zeros_like(c)
+        d[:, 1:] = c[:, :-1]
+        d = d - an[:, None] * c - b[:, n][:, None] * c_prev
+        b2 = np.zeros(M, dt)
+        for j in range(n + 2):
+            for l in range(n + 2):
+                b2 = b2 + d[:, j] * d[:, l] * mu[:, j + l]
+        trunc = alive & (_re(b2) <= TRUNC_REL * width)
+        nlev = np.where(trunc, n + 1, nlev)
+        keep = alive & ~trunc
+        bn1 = np.sqrt(np.where(keep, b2, 1.0))
+        b[:, n + 1] = np.where(keep, bn1, 0.0)
+        c_new = d / bn1[:, None]
+        c_prev = np.where(keep[:, None], c, c_prev)
+        c = np.where(keep[:, None], c_new, c)
+        alive = keep
+    return a, b, nlev
+
+
+def gershgorin(a, b, nlev):
+    """Band edges from Gershgorin's circle theorem, Eq. gershogorin, over the
+    computed levels n < nlev: E_bot = min(a_n - b_n - b_{n+1}),
+    E_top = max(a_n + b_n + b_{n+1}).  Returns (a_inf, b_inf) with
+    A = (top+bot)/2, B = (top-bot)/4 (constant terminator, Eq. abinf)."""
+    M, Kp = a.shape
+    lo = np.zeros_like(a)
+    hi = np.zeros_like(a)
+    for n in range(Kp):
+        lo[:, n] = a[:, n] - b[:, n] - b[:, n + 1]
+        hi[:, n] = a[:, n] + b[:, n] + b[:, n + 1]
+    valid = np.arange(Kp)[None, :] < nlev[:, None]
+    ilo = np.argmin(np.where(valid, _re(lo), np.inf), axis=1)
+    ihi = np.argmax(np.where(valid, _re(hi), -np.inf), axis=1)
+    bot = lo[np.arange(M), ilo]
+    top = hi[np.arange(M), ihi]
+    a_inf = 0.5 * (top + bot)
+    b_inf = 0.25 * (top - bot)
+    b_inf = np.where(_re(b_inf) < B_INF_MIN, B_INF_MIN, b_inf)
+    return a_inf, b_inf
+
+
+def normalised_moments(mu, a_inf, b_inf):
+    """mu-hat_n = (2 b_inf)^-n sum_l C(n,l) (-a_inf)^l mu_{n-l}
+    (Eq. sigma_i and the normalisation beneath it)."""
+    M, n_mom = mu.shape
+    out = np.zeros_like(mu, dtype=np.result_type(mu, a_inf, b_inf))
+    for n in range(n_mom):
+        acc = 0.0
+        for l in range(n + 1):
+            acc = acc + comb(n, l) * (-a_inf) ** l * mu[:, n - l]
+        out[:, n] = acc / (2.0 * b_inf) ** n
+    return out
+
+
+def cheb_p(m_max: int) -> np.ndarray:
+    """Coefficients p_mn of the Chebyshev polynomials of the second kind,
+    P_m(eps) = sum_n p_mn eps^n (Eq. chebyshev), from
+    p_{(m+1)n} = 2 p_{m(n-1)} - p_{(m-1)n}, P_0 = 1, P_1 = 2 eps."""
+    p = np.zeros((m_max + 1, m_max + 1))
+    p[0, 0] = 1.0
+    if m_max >= 1:
+        p[1, 1] = 2.0
+    for m in range(1, m_max):
+        for n in range(m + 2):
+            p[m + 1, n] = (2.0 * p[m, n - 1] if n >= 1 else 0.0) - p[m - 1, n]
+    return p
+
+
+def sigma_from_moments(mu_hat):
+    """sigma_m = sum_n p_mn mu-hat_n for m < n_mom (Eq. sigma_i)."""
+    n_mom = mu_hat.shape[1]
+    p = cheb_p(n_mom - 1)
+    return mu_hat @ p.T
+
+
+def zeta_sigma(a, b, nlev, a_inf, b_inf, n_exp: int):
+    """sigma_m = zeta_0^(m), m = 0..n_exp, from the semi-infinite chain
+    recursion zeta^(m+1)_k = 2[a^_k z_k + b^_k z_{k-1} + b^_{k+1} z_{k+1}]
+    - zeta^(m-1)_k (Eq. aexp), with a^_k = (a_k - a_inf)/(2 b_inf),
+    b^_k = b_k/(2 b_inf) on the computed levels and the constant
+    terminator a_k = a_inf, b_k = b_inf (a^ = 0, b^ = 1/2) beyond them."""
+    M, Kp = a.shape
+    L = n_exp + 2
+    dt = np.result_type(a, b, a_inf, b_inf)
+    ah = np.zeros((M, L + 1), dt)
+    bh = np.full((M, L + 2), 0.5, dt)
+    bh[:, 0] = 0.0
+    for k in range(Kp):
+        on = k < nlev
+        ah[:, k] = np.where(on, (a[:, k] - a_inf) / (2.0 * b_inf), 0.0)
+    for k in range(1, Kp + 1):
+        on = k <= nlev
+        bh[:, k] = np.where(on, b[:, k] / (2.0 * b_inf), 0.5)
+    sig = np.zeros((M, n_exp + 1), dt)
+    z_prev = np.zeros((M, L + 1), dt)
+    z = np.zeros((M, L + 1), dt)
+    z[:, 0] = 1.0
+    sig[:, 0] = 1.0
+    for m in range(n_exp):
+        hz = ah * z
+        hz[:, 1:] = hz[:, 1:] + bh[:, 1:L + 1] * z[:, :-1]
+        hz[:, :-1] = hz[:, :-1] + bh[:, 1:L + 1] * z[:, 1:]
+        z_new = 2.0 * hz - z_prev
+        z_prev, z = z, z_new
+        sig[:, m + 1] = z[:, 0]
+    return sig
+
+
+def jackson(n_exp: int) -> np.ndarray:
+    """Damping factors g_m = g^J_{m+1} / g^J_1, m = 0..n_exp, from the
+    Jackson kernel Eq. Jackson with N = n_exp."""
+    N = n_exp
+    m = np.arange(N + 2, dtype=np.float64)
+    x = np.pi / (N + 1)
+    gJ = ((N - m + 1) * np.cos(m * x) + np.sin(m * x) / np.tan(x)) / (N + 1)
+    return gJ[1:N + 2] / gJ[1]
+
+
+def chi_hat(m_max: int, phi):
+    """Response functions chi-hat_m(phi), m = 0..m_max (Eq. chi and the
+    two special cases above it).  phi: [M].  Returns [M, m_max+1]."""
+    phi = np.asarray(phi)
+    out = np.zeros(phi.shape + (m_max + 1,), dtype=phi.dtype)
+    if m_max >= 1:
+        out[..., 1] = 1.0 - phi / np.pi + np.sin(2.0 * phi) / (2.0 * np.pi)
+    for m in range(2, m_max + 1):
+        out[..., m] = (np.sin((m + 1) * phi) / (m + 1) - np.sin((m - 1) * phi) / (m - 1)) / np.pi
+    return out
+
+
+def fermi_phase(E_F, a_inf, b_inf):
+    """phi_F from cos(phi_F) = (E_F - a_inf)/(2 b_inf) (Eq. Fermi-phase),
+    the cosine clamped to [-1, 1] (E_F below / above the band)."""
+    x = (E_F - a_inf) / (2.0 * b_inf)
+    xr = _re(x)
+    x = np.where(xr > 1.0, 1.0, np.where(xr < -1.0, -1.0, x))
+    return np.arccos(x)
+
+
+def orbital_N_U(gsig, a_inf, b_inf, E_on, E_F):
+    """Per-orbital, per-spin electron count and bond energy:
+    N = sum_m g_m sigma_m chi_{m+1}(phi_F);
+    U = b_inf sum_m g_m sigma_m [chi_{m+2} - gamma_0 chi_{m+1} + chi_m],
+    gamma_0 = (E_ialpha - a_inf)/b_inf (bond energy of Eq. TB-Ubond in the
+    closed form given with Eq. chi)."""
+    n_exp = gsig.shape[1] - 1
+    phi = fermi_phase(E_F, a_inf, b_inf)
+    chi = chi_hat(n_exp + 2, phi)
+    N = np.sum(gsig * chi[:, 1:n_exp + 2], axis=1)
+    g0 = (E_on - a_inf) / b_inf
+    U = b_inf * np.sum(gsig * (chi[:, 2:n_exp + 3] - g0[:, None] * chi[:, 1:n_exp + 2]
+                               + chi[:, 0:n_exp + 1]), axis=1)
+    return N, U
+
+
+def dos_at(gsig, a_inf, b_inf, E):
+    """Local DOS per orbital and spin at energy E (Eq. nialpha, divided by
+    2 b_inf for the change of variable eps -> E); zero outside the band."""
+    eps = (E - a_inf) / (2.0 * b_inf)
+    inside = np.abs(eps) < 1.0
+    e = np.where(inside, eps, 0.0)
+    n_exp = gsig.shape[1] - 1
+    Um1 = np.zeros_like(e)
+    Um = np.ones_like(e)
+    acc = gsig[:, 0] * Um
+    for m in range(1, n_exp + 1):
+        Up = 2.0 * e * Um - Um1
+        Um1, Um = Um, Up
+        acc = acc + gsig[:, m] * Um
+    val = (2.0 / np.pi) * np.sqrt(1.0 - e * e) * acc / (2.0 * b_inf)
+    return np.where(inside, val, 0.0)
+
+
+@dataclass
+class Expansion:
+    a: np.ndarray
+    b: np.ndarray
+    nlev: np.ndarray
+    a_inf: np.ndarray
+    b_inf: np.ndarray
+    sigma: np.ndarray
+    gsig: np.ndarray
+
+
+def scalar_stage(mu, n_exp: int) -> Expansion:
+    """Moments -> (a, b) -> Gershgorin (a_inf, b_inf) -> mu-hat -> sigma
+    (Eq. sigma_i below n_mom, the zeta chain above) -> g_m sigma_m."""
+    a, b, nlev = recursion_coefficients(mu)
+    a_inf, b_inf = gershgorin(a, b, nlev)
+    n_mom = mu.shape[1]
+    sig_mom = sigma_from_moments(normalised_moments(mu, a_inf, b_inf))
+    sig = zeta_sigma(a, b, nlev, a_inf, b_inf, n_exp)
+    sig[:, :n_mom] = sig_mom
+    g = jackson(n_exp)
+    return Expansion(a, b, nlev, a_inf, b_inf, sig, sig * g[None, :])
+
+
+def fermi_bisect(ex: Expansion, spin_factor: float, target: float,
+                 max_it: int = 100, tol: float = 1e-13):
+    """Fermi level by bisection on the total electron count
+    s * sum N_ialpha(E_F) = target ("DOS and Fermi energy").  The bracket is
+    [min(a_inf - 2 b_inf) - 1e-3, max(a_inf + 2 b_inf) + 1e-3]; stops after
+    max_it halvings or at a width below tol; returns the midpoint."""
+    lo = float(np.min(ex.a_inf - 2.0 * ex.b_inf)) - 1e-3
+    hi = float(np.max(ex.a_inf + 2.0 * ex.b_inf)) + 1e-3
+    zero_on = np.zeros_like(ex.a_inf)
+    it = 0
+    for it in range(max_it):
+        if hi - lo < tol:
+            break
+        mid = 0.5 * (lo + hi)
+        N, _ = orbital_N_U(ex.gsig, ex.a_inf, ex.b_inf, zero_on, mid)
+        f = spin_factor * float(np.sum(N)) - target
+        if f == 0.0:
+            return mid, it + 1
+        if f < 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi), it
+
+
+def weights(mu, E_on, E_F, n_exp: int, spin_factor: float):
+    """w_n = dU_total/dmu_n per orbital (Eq. weights), including the
+    response of E_F at fixed total electron number, by complex-step
+    differentiation of the scalar stage.  Returns (w [M, n_mom],
+    dU_dE [M] = direct derivative of s*U_ialpha w.r.t. its onsite level,
+    dN_dmu [M, n_mom], dN_dEF [M], dU_dEF [M])."""
+    M, n_mom = mu.shape
+    dU = np.zeros((M, n_mom))
+    dN = np.zeros((M, n_mom))
+    for n in range(n_mom):
+        mc = mu.astype(np.complex128)
+        mc[:, n] += 1j * CS_H
+        ex = scalar_stage(mc, n_exp)
+        N, U = orbital_N_U(ex.gsig, ex.a_inf, ex.b_inf, E_on.astype(np.complex128), E_F)
+        dU[:, n] = np.imag(U) / CS_H
+        dN[:, n] = np.imag(N) / CS_H
+    ex = scalar_stage(mu, n_exp)
+    N, U = orbital_N_U(ex.gsig, ex.a_inf, ex.b_inf, E_on.astype(np.complex128),
+                       E_F + 1j * CS_H)
+    dU_dEF = np.imag(U) / CS_H
+    dN_dEF = np.imag(N) / CS_H
+    N, U = orbital_N_U(ex.gsig, ex.a_inf, ex.b_inf, E_on + 1j * CS_H, E_F)
+    dU_dE = spin_factor * np.imag(U) / CS_H
+    lam = np.sum(dU_dEF) / np.sum(dN_dEF)
+    w = spin_factor * (dU - lam * dN)
+    return w, dU_dE, dN, dN_dEF, dU_dEF
+
+
+# ---------------------------------------------------------------- driver
+
+def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = True,
+             delta0=None, m_init=None):
+    """Energy (and forces, virial) of the analytic BOP for one structure.
+
+    Flow of Fig. BOP-calculation: neighbours -> H -> [moments -> recursion ->
+    terminator -> E_F -> N, U -> onsite update]* -> energy -> weights ->
+    reverse sweep -> forces.  Forces are the exact derivative of the energy
+    at fixed onsite levels with E_F following the electron count; with an
+    SCF the response of the onsite levels is not included (flag
+    ``forces_include_scf_response`` = False)."""
+    pos = np.asarray(pos, np.float64)
+    n = len(pos)
+    norb = model.norb
+    S = st.n_spin
+    s = 2.0 if S == 1 else 1.0
+    nbr = neighbors(pos, cell, pbc, model.rc)
+    H = blocks(model, pos, cell, nbr)
+    delta = np.zeros(n) if delta0 is None else np.array(delta0, np.float64)
+    m = None
+    if st.scf == "stoner":
+        m = np.full(n, st.m0) if m_init is None else np.array(m_init, np.float64)
+    N0 = st.n_e
+    target = st.n_e * n
+    it = 0
+    converged = st.scf == "none"
+    while True:
+        onsite = np.zeros((S, n, norb))
+        for v in range(S):
+            onsite[v] = model.onsite0 + delta[:, None]
+            if st.scf == "stoner":
+                sign = -1.0 if v == 0 else 1.0
+                onsite[v] += sign * 0.5 * st.stoner_I * m[:, None]
+        mu = np.stack([moments(nbr, H, onsite[v], st.n_mom) for v in range(S)])
+        mu_f = mu.reshape(-1, st.n_mom)
+        ex = scalar_stage(mu_f, st.n_exp)
+        E_F, n_bis = fermi_bisect(ex, s, target)
+        N, U = orbital_N_U(ex.gsig, ex.a_inf, ex.b_inf, onsite.reshape(-1), E_F)
+        Nsv = N.reshape(S, n, norb)
+        if st.scf == "none" or it >= st.scf_max_it:
+            break
+        Ni = s * Nsv.sum(axis=(0, 2))
+        res = Ni - N0
+        dos = s * dos_at(ex.gsig, ex.a_inf, ex.b_inf, E_F).reshape(S, n, norb).sum(axis=(0, 2))
+        done = np.max(np.abs(res)) < st.scf_tol
+        if st.scf == "stoner":
+            m_out = (Nsv[0] - Nsv[1]).sum(axis=1)
+            done = done and np.max(np.abs(m_out - m)) < 10 * st.scf_tol
+        if done:
+            converged = True
+            break
+        delta = delta + st.eta * res / np.maximum(dos, st.dos_floor)
+        delta = delta - delta.mean()
+        if st.scf == "stoner":
+            m = (1.0 - st.m_mix) * m + st.m_mix * m_out
+        it += 1
+    e_atom = s * U.reshape(S, n, norb).sum(axis=(0, 2))
+    if st.scf == "stoner":
+        e_atom = e_atom - 0.25 * st.stoner_I * m ** 2
+    out = dict(e_atom=e_atom, e_total=float(e_atom.sum()), e_fermi=E_F, mu=mu,
+               a=ex.a, b=ex.b, a_inf=ex.a_inf, b_inf=ex.b_inf, N=Nsv, delta=delta, m=m,
+               scf_iterations=it, scf_converged=converged, bisection_steps=n_bis,
+               neighbors=nbr, H=H, onsite=onsite, forces_include_scf_response=st.scf == "none")
+    if want_forces:
+        w, dU_dE, *_ = weights(mu_f, onsite.reshape(-1), E_F, st.n_exp, s)
+        w = w.reshape(S, n, norb, st.n_mom)
+        Hbar = np.zeros((nbr.n_edges, norb, norb))
+        for v in range(S):
+            hb, _ = moments_adjoint(nbr, H, onsite[v], w[v])
+            Hbar += hb
+        g = bond_gradient(model, pos, cell, nbr, Hbar)
+        F = np.zeros((n, 3))
+        src = np.repeat(np.arange(n), np.diff(nbr.row_ptr))
+        np.add.at(F, src, g)
+        np.add.at(F, nbr.col, -g)
+        dvec = edge_vectors(pos, cell, nbr)
+        vir = np.einsum("ea,eb->ab", g, dvec)
+        out.update(forces=F, virial=vir, weights=w, Hbar=Hbar)
+    return out

@@ -1,0 +1,177 @@
+"""Seeded synthetic inputs: bcc/fcc cells, jitter, vacancies, slabs, and the
+model parameter sets of the benchmark workloads.
+
+This module holds no arithmetic of the BOP method.  It is the one module
+that both the CUDA path and the CPU oracle take their inputs from.
+
+Random numbers come from ``numpy.random.default_rng(seed)``; the draws are
+made in a fixed order that is stated in each function.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+A_BCC = 2.87  # Angstrom, lattice constant of all bcc workloads
+
+
+def bcc_cell(n1: int, n2: int, n3: int, a: float = A_BCC):
+    """Perfect bcc crystal of n1 x n2 x n3 conventional cells (2 atoms each).
+    Atom order: cells in (i, j, k) row-major order, basis (0,0,0) then
+    (1/2,1/2,1/2).  Returns (pos [N,3], cell [3,3] rows = lattice vectors)."""
+    ii, jj, kk = np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij")
+    corners = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1).astype(np.float64)
+    basis = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.5]])
+    frac = (corners[:, None, :] + basis[None, :, :]).reshape(-1, 3)
+    pos = frac * a
+    cell = np.diag([n1 * a, n2 * a, n3 * a]).astype(np.float64)
+    return pos, cell
+
+
+def fcc_cell(n1: int, n2: int, n3: int, a: float):
+    """Perfect fcc crystal, 4 atoms per conventional cell, same ordering."""
+    ii, jj, kk = np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij")
+    corners = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1).astype(np.float64)
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]], np.float64)
+    pos = (corners[:, None, :] + basis[None, :, :]).reshape(-1, 3) * a
+    return pos, np.diag([n1 * a, n2 * a, n3 * a]).astype(np.float64)
+
+
+def wrap(pos, cell, pbc):
+    """Map positions into the cell along the periodic axes (fractional
+    coordinates in [0, 1))."""
+    frac = np.linalg.solve(np.asarray(cell).T, np.asarray(pos).T).T
+    for ax in range(3):
+        if pbc[ax]:
+            frac[:, ax] -= np.floor(frac[:, ax])
+            frac[:, ax] = np.where(frac[:, ax] >= 1.0, 0.0, frac[:, ax])
+    return frac @ np.asarray(cell)
+
+
+def jittered(pos, cell, pbc, sigma: float, rng):
+    """Add N(0, sigma^2) to every Cartesian component (one draw of shape
+    [N, 3], atom order then x, y, z) and wrap into the cell."""
+    d = rng.normal(0.0, sigma, size=pos.shape)
+    return wrap(pos + d, cell, pbc)
+
+
+@dataclass(frozen=True)
+class ModelParams:
+    """Exponential two-centre bond integrals with a cosine taper."""
+    norb: int          # 1 = s, 5 = d
+    b0: tuple          # eV at r0: (ss sigma,) or (dd sigma, dd pi, dd delta)
+    r0: float          # Angstrom
+    lam: float         # 1/Angstrom
+    rc: float          # cutoff radius, Angstrom
+    dc: float          # taper width, Angstrom
+    onsite0: float = 0.0
+
+
+# s-valent model: ss sigma = -1.0 eV exp(-1.5 (r - 2.48)), taper 3.2-3.6 A
+MODEL_S = ModelParams(norb=1, b0=(-1.0,), r0=2.48, lam=1.5, rc=3.6, dc=0.4)
+# canonical d model: sigma:pi:delta = -6:4:-1 scaled to dd sigma(2.48) = -0.9 eV,
+# exp decay 1.8/A, cutoff 3.6 A with a 0.4 A taper (1st + 2nd bcc shells)
+MODEL_D = ModelParams(norb=5, b0=(-0.9, 0.6, -0.15), r0=2.48, lam=1.8, rc=3.6, dc=0.4)
+
+
+@dataclass(frozen=True)
+class RunParams:
+    n_e: float            # electrons per atom, summed over spin
+    n_mom: int = 9
+    n_exp: int = 200
+    n_spin: int = 1
+    scf: str = "none"     # none | lcn | stoner
+    eta: float = 0.5
+    scf_tol: float = 1e-9
+    scf_max_it: int = 200
+    stoner_I: float = 0.0
+    m_mix: float = 0.3
+    m0: float = 2.0
+    dos_floor: float = 0.1
+
+
+@dataclass
+class Workload:
+    name: str
+    pos: np.ndarray
+    cell: np.ndarray
+    pbc: tuple
+    model: ModelParams
+    run: RunParams
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_atoms(self):
+        return len(self.pos)
+
+
+def bcc_jittered(n1, n2, n3, sigma, seed, pbc=(1, 1, 1)):
+    pos, cell = bcc_cell(n1, n2, n3)
+    rng = np.random.default_rng(seed)
+    return jittered(pos, cell, pbc, sigma, rng), cell
+
+
+def slab_with_vacancies(n1, n2, n3, n_vac, sigma, seed, vacuum=10.0):
+    """bcc slab with two free (001) surfaces: pbc (1, 1, 0); the cell's z
+    vector is n3*a + vacuum and the slab is centred in it.  Draw order from
+    default_rng(seed): first the vacancy indices (choice without
+    replacement), then the jitter of the remaining atoms."""
+    pos, cell = bcc_cell(n1, n2, n3)
+    rng = np.random.default_rng(seed)
+    vac = rng.choice(len(pos), size=n_vac, replace=False)
+    keep = np.ones(len(pos), bool)
+    keep[vac] = False
+    pos = pos[keep]
+    pos[:, 2] += 0.5 * vacuum
+    cell = cell.copy()
+    cell[2, 2] = n3 * A_BCC + vacuum
+    pbc = (1, 1, 0)
+    pos = jittered(pos, cell, pbc, sigma, rng)
+    return pos, cell, pbc
+
+
+def workload(name: str) -> Workload:
+    """Named workloads.
+
+    s128      128-atom bcc (4x4x4x2), jitter 0.05 A, seed 1; s model; 9 moments;
+              N_e = 0.7 per atom; no SCF.
+    d2000     2,000-atom bcc (10x10x10x2), jitter 0.05 A, seed 2; canonical d;
+              N_d = 6.8; local charge neutrality; 9 moments.
+    d2000nscf the same cell without SCF (fixed onsite levels).
+    slab16k   16x16x32x2 bcc slab with (001) surfaces, 64 vacancies, jitter
+              0.08 A, seed 3; canonical d; 13 moments; no SCF.
+    mag65k    65,536-atom bcc (32x32x32x2), jitter 0.05 A, seed 4; canonical d;
+              two spin channels, Stoner I = 0.8 eV from a ferromagnetic start;
+              9 moments.
+    mag2000   its 2,000-atom (10x10x10x2) counterpart, seed 4.
+    """
+    if name == "s128":
+        pos, cell = bcc_jittered(4, 4, 4, 0.05, 1)
+        return Workload(name, pos, cell, (1, 1, 1), MODEL_S, RunParams(n_e=0.7))
+    if name in ("d2000", "d2000nscf"):
+        pos, cell = bcc_jittered(10, 10, 10, 0.05, 2)
+        scf = "lcn" if name == "d2000" else "none"
+        return Workload(name, pos, cell, (1, 1, 1), MODEL_D, RunParams(n_e=6.8, scf=scf))
+    if name == "slab16k":
+        pos, cell, pbc = slab_with_vacancies(16, 16, 32, 64, 0.08, 3)
+        return Workload(name, pos, cell, pbc, MODEL_D, RunParams(n_e=6.8, n_mom=13))
+    if name in ("mag65k", "mag2000"):
+        n = 32 if name == "mag65k" else 10
+        pos, cell = bcc_jittered(n, n, n, 0.05, 4)
+        return Workload(name, pos, cell, (1, 1, 1), MODEL_D,
+                        RunParams(n_e=6.8, n_spin=2, scf="stoner", stoner_I=0.8))
+    raise KeyError(name)
+
+
+def small_bcc(n1, n2, n3, sigma, seed, model=MODEL_D, run=None, pbc=(1, 1, 1)):
+    """A small jittered bcc cell for tests."""
+    pos, cell = bcc_cell(n1, n2, n3)
+    rng = np.random.default_rng(seed)
+    pos = jittered(pos, cell, pbc, sigma, rng)
+    run = run or RunParams(n_e=6.8 if model.norb == 5 else 0.7)
+    return Workload(f"bcc{n1}x{n2}x{n3}", pos, cell, tuple(pbc), model, run)
+
+
+def with_run(w: Workload, **kw) -> Workload:
+    return Workload(w.name, w.pos, w.cell, w.pbc, w.model, replace(w.run, **kw), w.meta)
