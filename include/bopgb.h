@@ -1,0 +1,215 @@
+/*
+ * bopgb — GB300 (sm_103a) analytic bond-order potential, C ABI.
+ *
+ * The library computes, for one atomic structure, the hot path of the
+ * analytic BOP described in the BOPfox paper (arXiv:1803.07491):
+ *   short-range neighbour list ("Initialisation")
+ *   -> two-centre Slater-Koster Hamiltonian blocks (Eq. Hij, Eq. cutoff,
+ *      Eq. Hij_rot)
+ *   -> moments mu_n(i alpha) = <i alpha|H^n|i alpha> of every orbital
+ *      (Eq. momDOS) by the iterated interference paths (Eqs. xi_rec,
+ *      xi_merge) over each atom's cluster
+ *   -> recursion coefficients (Eqs. momtoa, momtob), Gershgorin band edges
+ *      (Eq. gershogorin), constant terminator (Eq. abinf), expansion
+ *      coefficients (Eq. sigma_i, Eq. aexp) with Jackson damping
+ *      (Eq. Jackson)
+ *   -> Fermi level by bisection ("DOS and Fermi energy"), local charge
+ *      neutrality (Eq. BOP_LCN) and collinear Stoner magnetism
+ *      (Eq. onsite_NCM, Eq. TB-UX) self-consistency
+ *   -> bond energy per atom (Eq. TB-Ubond in the closed form of Eq. chi)
+ *   -> exact gradient: weights (Eq. weights), reverse sweep of the moments
+ *      (Eqs. theta-tilde, Xi), forces (Eq. F_k) and virial (Eq. sigma_k).
+ *
+ * Conventions (all entry points):
+ *   - Every function returns an int status (enum bop_status); 0 = success.
+ *     On failure bop_last_error(ctx) describes the cause.  Outputs are
+ *     valid only on success, except BOP_ERR_NO_CONVERGENCE, where they hold
+ *     the last iterate.
+ *   - Array arguments are DEVICE pointers unless the parameter name ends
+ *     in _host.  The caller owns every array it passes; the library owns
+ *     only the workspaces inside the opaque context (allocated with
+ *     cudaMalloc on the current device, freed by bop_destroy).
+ *   - stream is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it; functions that must read sizes or convergence flags
+ *     synchronise that stream, as stated per function.
+ *   - Energies in eV, lengths in Angstrom, forces in eV/Angstrom.
+ *   - Orbitals: s (1) or d (5, order d_{3z^2-r^2}, d_zx, d_yz,
+ *     d_{x^2-y^2}, d_xy as in Eq. Hij).  "M" below = n_spin * n * norb.
+ *   - A context is not thread safe; use one context per host thread.
+ */
+#ifndef BOPGB_H
+#define BOPGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bop_ctx bop_ctx;
+typedef void* bop_stream; /* cudaStream_t */
+
+enum bop_status {
+  BOP_OK = 0,
+  BOP_ERR_ARG = 1,            /* invalid argument or model */
+  BOP_ERR_CUDA = 2,           /* a CUDA call failed */
+  BOP_ERR_OOM = 3,            /* device allocation failed */
+  BOP_ERR_NO_CONVERGENCE = 4, /* SCF hit scf_max_it; outputs = last iterate */
+  BOP_ERR_BRACKET = 5,        /* Fermi level could not be bracketed */
+  BOP_ERR_NUMERIC = 6,        /* NaN/Inf in the scalar stages */
+  BOP_ERR_STATE = 7,          /* call order violated (e.g. forces before energy) */
+  BOP_ERR_OVERFLOW = 8        /* neighbour degree / cluster / image index limit exceeded */
+};
+
+enum { BOP_SCF_NONE = 0, BOP_SCF_LCN = 1, BOP_SCF_STONER = 2 };
+enum { BOP_PREC_FP64 = 0, BOP_PREC_FP32 = 1 };
+
+/* Model and run settings.
+ * beta_x(r) = b0[x] * exp(-lam (r - r0)) * fcut(r), fcut the cosine taper
+ * of Eq. cutoff on [rc - dc, rc]; b0 = {ss sigma} (norb 1) or
+ * {dd sigma, dd pi, dd delta} (norb 5) in eV at r0.
+ * n_mom odd in [3, 17]; n_exp in [n_mom - 1, 253].
+ * n_e: electrons per atom summed over spin.  n_spin 1 (non-magnetic, spin
+ * factor 2) or 2 (collinear, Stoner).
+ * scf: LCN shifts one onsite level per atom, delta_i += eta (N_i - n_e) /
+ * max(n_i(E_F), dos_floor) then removes the mean, until max|N_i - n_e| <
+ * scf_tol; STONER additionally mixes m_i with m_mix from m0 until
+ * max|m_out - m| < 10 scf_tol, E_{i,up/down} = E0 + delta_i -/+ I m_i / 2.
+ * precision: FP64 everywhere, or FP32 products and accumulation in the
+ * moments and their reverse sweep with every scalar stage in FP64. */
+typedef struct {
+  int norb;
+  double b0[3];
+  double r0, lam, rc, dc;
+  double onsite0;
+  int n_mom;
+  int n_exp;
+  int n_spin;
+  double n_e;
+  int scf;
+  double eta, scf_tol;
+  int scf_max_it;
+  double stoner_I, m_mix, m0, dos_floor;
+  int precision;
+} bop_model;
+
+typedef struct {
+  int n_atoms;
+  int K;                  /* hops (n_mom - 1) / 2 */
+  long long n_edges;      /* directed neighbour pairs */
+  long long n_bonds;      /* undirected bonds = n_edges / 2 */
+  long long n_sites;      /* cluster sites summed over atoms */
+  long long n_adj;        /* cluster adjacency entries */
+  int max_cluster;        /* largest |C_K| */
+  int scf_iterations;
+  int scf_converged;
+  int bisection_rounds;
+  double scf_residual;    /* max |N_i - n_e| of the last iteration */
+  double e_fermi;
+  double e_total;
+  int forces_scf_response;/* 1 if forces include the SCF response (scf == NONE) */
+  int pad;
+} bop_stats;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int bop_version(void);
+
+/* Creates a context for one model on the current CUDA device.
+ * Errors: BOP_ERR_ARG for an invalid model, BOP_ERR_CUDA / BOP_ERR_OOM. */
+int bop_create(bop_ctx** ctx, const bop_model* model);
+
+/* Frees all device workspaces; ctx may be NULL. */
+int bop_destroy(bop_ctx* ctx);
+
+/* Text of the last error of ctx ("" if none); owned by ctx. */
+const char* bop_last_error(const bop_ctx* ctx);
+
+/* Neighbour list (linked cells, pairs with r < rc incl. periodic images),
+ * canonical bonds with their blocks and bond vectors, and the cluster of
+ * every atom ("Initialisation", Eq. Hij_rot, Eq. momDOS support).
+ *   n         atoms (>= 1)
+ *   pos       device [n][3] positions; must lie inside the cell
+ *             (fractional coordinates in [0, 1)) along every axis
+ *   cell_host host [3][3], rows = lattice vectors (right-handed or not)
+ *   pbc_host  host [3], 1 = periodic along that lattice vector
+ * Copies pos into the context.  Synchronises stream (reads back sizes).
+ * Errors: BOP_ERR_ARG (atom outside the cell, singular cell),
+ * BOP_ERR_OVERFLOW (> 64 neighbours of an atom, image index beyond
+ * +-127, cluster scratch exhausted after retries). */
+int bop_build_hamiltonian(bop_ctx* ctx, int n, const double* pos, const double* cell_host,
+                          const int* pbc_host, bop_stream stream);
+
+/* Sizes of the last build and statistics of the last energy/forces call
+ * (host struct). */
+int bop_get_stats(const bop_ctx* ctx, bop_stats* stats_host);
+
+/* Copies the neighbour list of the last build: row_ptr [n+1] (int64),
+ * col [E] (int32), img [E][3] (int8); rows sorted by (j, sx, sy, sz). */
+int bop_get_neighbors(bop_ctx* ctx, long long* row_ptr, int* col, signed char* img, bop_stream stream);
+
+/* Copies the cluster of one atom: site_atom [n_site], site_img
+ * [n_site][3], level_end [K+1] (all device); n_site = level_end[K].
+ * Order: hop level, then atom, then image.  Synchronises stream. */
+int bop_get_cluster(bop_ctx* ctx, int atom, int* site_atom, signed char* site_img, int* level_end,
+                    bop_stream stream);
+
+/* Copies the bonds: atoms [nb][2] (i < j or image-ordered), bond vectors
+ * d = r_j + S.cell - r_i [nb][3], unique block elements [nb][15] (d; the
+ * upper triangle row by row) or [nb][1] (s). Any pointer may be NULL. */
+int bop_get_bonds(bop_ctx* ctx, int* atoms, double* d, double* blocks, bop_stream stream);
+
+/* Moments (Eq. momDOS) of every orbital for the given onsite levels.
+ *   onsite  device [n_spin][n][norb] (FP64) or NULL for onsite0 everywhere
+ *   mu      device [n_spin][n][norb][n_mom] output (FP64 storage; FP32
+ *           arithmetic when precision = FP32)
+ * Requires a build. */
+int bop_moments(bop_ctx* ctx, const double* onsite, double* mu, bop_stream stream);
+
+/* Scalar stage of M orbitals from their moments: recursion coefficients
+ *   a [M][Kp], b [M][Kp+1] (b_0 = 0), nlev [M] (levels computed, < Kp
+ *   where the chain was truncated), a_inf, b_inf [M] (Gershgorin
+ *   terminator), gsig [n_exp+1][M] = g_m sigma_m (coefficient-major).
+ * Kp = (n_mom - 1) / 2.  Any output except gsig may be NULL. */
+int bop_recursion(bop_ctx* ctx, int M, const double* mu, double* a, double* b, int* nlev, double* a_inf,
+                  double* b_inf, double* gsig, bop_stream stream);
+
+/* Energy of the last built structure, including the SCF loop.
+ *   e_atom    device [n] bond (+ exchange) energy per atom, or NULL
+ *   delta_io  device [n] LCN onsite shifts: read as the starting guess
+ *             (warm start) and overwritten with the result; NULL = start
+ *             from 0 and keep internally
+ *   m_io      device [n] Stoner moments, same convention (NULL = m0)
+ *   stats_host optional host struct
+ * Synchronises stream once per SCF iteration (convergence flag) and at
+ * the end. */
+int bop_energy(bop_ctx* ctx, double* e_atom, double* delta_io, double* m_io, bop_stats* stats_host,
+               bop_stream stream);
+
+/* Forces (Eq. F_k) and virial W_ab = sum_bonds g_a d_b = dE/dF_ab for a
+ * deformation r -> F r (Eq. sigma_k summed over atoms), as the exact
+ * derivative of the energy of the last bop_energy call at fixed onsite
+ * levels with E_F following the electron count.
+ *   forces device [n][3], virial device [3][3] (row-major), either may be NULL.
+ * Errors: BOP_ERR_STATE without a preceding bop_energy. */
+int bop_forces(bop_ctx* ctx, double* forces, double* virial, bop_stats* stats_host, bop_stream stream);
+
+/* Per-orbital state of the last bop_energy / bop_forces call (device
+ * outputs, each may be NULL): mu [M][n_mom], N [M] and U [M] (per spin
+ * channel, before the spin factor), a_inf, b_inf [M], weights [M][n_mom]
+ * (dE/dmu, valid after bop_forces), onsite [M]. */
+int bop_get_orbital_state(bop_ctx* ctx, double* mu, double* N, double* U, double* a_inf, double* b_inf,
+                          double* weights, double* onsite, bop_stream stream);
+
+/* End-to-end energy + forces with HOST buffers: copies pos_host in,
+ * runs build, energy and forces, copies the results out and synchronises.
+ *   pos_host [n][3]; e_atom_host [n]; forces_host [n][3]; virial_host [9];
+ *   e_total_host [1]; outputs may be NULL. */
+int bop_evaluate_host(bop_ctx* ctx, int n, const double* pos_host, const double* cell_host,
+                      const int* pbc_host, double* e_atom_host, double* forces_host, double* virial_host,
+                      double* e_total_host, bop_stats* stats_host, bop_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BOPGB_H */

@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 from dataclasses import dataclass
 from math import comb
@@ -33,7 +34,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bop_oracle.c")
-_SO = os.path.join(_HERE, "_build", "liborc.so")
+_SO = os.path.join(_HERE, "_build", platform.machine(), "liborc.so")
 _LIB = None
 
 B_INF_MIN = 1e-3      # eV, floor of the band-width estimate

@@ -1,0 +1,317 @@
+"""Thin ctypes binding of libbopgb (include/bopgb.h).
+
+Argument marshalling only: every step of the BOP path runs in the CUDA
+kernels of libbopgb.so.  PyTorch provides device memory and the current
+stream.  There is no CPU fallback: a missing or unloadable library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+BOP_OK, BOP_ERR_ARG, BOP_ERR_CUDA, BOP_ERR_OOM, BOP_ERR_NO_CONVERGENCE = 0, 1, 2, 3, 4
+BOP_ERR_BRACKET, BOP_ERR_NUMERIC, BOP_ERR_STATE, BOP_ERR_OVERFLOW = 5, 6, 7, 8
+SCF = {"none": 0, "lcn": 1, "stoner": 2}
+PREC = {"fp64": 0, "fp32": 1}
+
+
+class BopError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libbopgb status {status}: {msg}")
+        self.status = status
+
+
+class bop_model(ctypes.Structure):
+    _fields_ = [("norb", ctypes.c_int), ("b0", ctypes.c_double * 3), ("r0", ctypes.c_double),
+                ("lam", ctypes.c_double), ("rc", ctypes.c_double), ("dc", ctypes.c_double),
+                ("onsite0", ctypes.c_double), ("n_mom", ctypes.c_int), ("n_exp", ctypes.c_int),
+                ("n_spin", ctypes.c_int), ("n_e", ctypes.c_double), ("scf", ctypes.c_int),
+                ("eta", ctypes.c_double), ("scf_tol", ctypes.c_double), ("scf_max_it", ctypes.c_int),
+                ("stoner_I", ctypes.c_double), ("m_mix", ctypes.c_double), ("m0", ctypes.c_double),
+                ("dos_floor", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class bop_stats(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int), ("K", ctypes.c_int), ("n_edges", ctypes.c_longlong),
+                ("n_bonds", ctypes.c_longlong), ("n_sites", ctypes.c_longlong), ("n_adj", ctypes.c_longlong),
+                ("max_cluster", ctypes.c_int), ("scf_iterations", ctypes.c_int), ("scf_converged", ctypes.c_int),
+                ("bisection_rounds", ctypes.c_int), ("scf_residual", ctypes.c_double),
+                ("e_fermi", ctypes.c_double), ("e_total", ctypes.c_double),
+                ("forces_scf_response", ctypes.c_int), ("pad", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+_LIB = None
+_VP = ctypes.c_void_p
+
+
+def lib(path: str | None = None):
+    """Load libbopgb.so (built in-tree by paper_1803_07491_gb300.build)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1803_07491_gb300.build.build(); "
+                           "the BOP path has no CPU fallback")
+    L = ctypes.CDLL(path)
+    sig = {
+        "bop_version": ([], ctypes.c_int),
+        "bop_create": ([ctypes.POINTER(_VP), ctypes.POINTER(bop_model)], ctypes.c_int),
+        "bop_destroy": ([_VP], ctypes.c_int),
+        "bop_last_error": ([_VP], ctypes.c_char_p),
+        "bop_build_hamiltonian": ([_VP, ctypes.c_int, _VP, _VP, _VP, _VP], ctypes.c_int),
+        "bop_get_stats": ([_VP, ctypes.POINTER(bop_stats)], ctypes.c_int),
+        "bop_get_neighbors": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+        "bop_get_cluster": ([_VP, ctypes.c_int, _VP, _VP, _VP, _VP], ctypes.c_int),
+        "bop_get_bonds": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+        "bop_moments": ([_VP, _VP, _VP, _VP], ctypes.c_int),
+        "bop_recursion": ([_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+        "bop_energy": ([_VP, _VP, _VP, _VP, ctypes.POINTER(bop_stats), _VP], ctypes.c_int),
+        "bop_forces": ([_VP, _VP, _VP, ctypes.POINTER(bop_stats), _VP], ctypes.c_int),
+        "bop_get_orbital_state": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+        "bop_evaluate_host": ([_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                               ctypes.POINTER(bop_stats), _VP], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _LIB = L
+    return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        assert t.is_contiguous(), "tensors passed to libbopgb must be contiguous"
+        return _VP(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data_as(_VP)
+    raise TypeError(type(t))
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _VP(s.cuda_stream)
+
+
+def make_model(params, run, precision: str = "fp64") -> bop_model:
+    """bop_model from inputs.ModelParams + inputs.RunParams."""
+    b0 = list(params.b0) + [0.0] * (3 - len(params.b0))
+    return bop_model(params.norb, (ctypes.c_double * 3)(*b0), params.r0, params.lam, params.rc, params.dc,
+                     params.onsite0, run.n_mom, run.n_exp, run.n_spin, run.n_e, SCF[run.scf], run.eta,
+                     run.scf_tol, run.scf_max_it, run.stoner_I, run.m_mix, run.m0, run.dos_floor,
+                     PREC[precision])
+
+
+def _check(ctx, st, allow=()):
+    if st != BOP_OK and st not in allow:
+        msg = lib().bop_last_error(ctx)
+        raise BopError(st, msg.decode() if msg else "")
+    return st
+
+
+# ------------------------------------------------------------ ABI mirrors
+
+def bop_create(model: bop_model):
+    h = _VP()
+    st = lib().bop_create(ctypes.byref(h), ctypes.byref(model))
+    if st != BOP_OK:
+        raise BopError(st, "bop_create rejected the model")
+    return h
+
+
+def bop_destroy(ctx):
+    lib().bop_destroy(ctx)
+
+
+def bop_build_hamiltonian(ctx, pos: torch.Tensor, cell, pbc, stream=None):
+    cell = np.ascontiguousarray(cell, dtype=np.float64).reshape(3, 3)
+    pbc = np.ascontiguousarray(pbc, dtype=np.int32).reshape(3)
+    assert pos.is_cuda and pos.dtype == torch.float64 and pos.shape[-1] == 3
+    _check(ctx, lib().bop_build_hamiltonian(ctx, pos.shape[0], _ptr(pos), _ptr(cell), _ptr(pbc), _stream(stream)))
+
+
+def bop_get_stats(ctx) -> dict:
+    s = bop_stats()
+    _check(ctx, lib().bop_get_stats(ctx, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def bop_get_neighbors(ctx, stream=None):
+    st = bop_get_stats(ctx)
+    n, E = st["n_atoms"], st["n_edges"]
+    dev = torch.device("cuda")
+    row = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(max(E, 1), dtype=torch.int32, device=dev)
+    img = torch.empty((max(E, 1), 3), dtype=torch.int8, device=dev)
+    _check(ctx, lib().bop_get_neighbors(ctx, _ptr(row), _ptr(col), _ptr(img), _stream(stream)))
+    return row, col[:E], img[:E]
+
+
+def bop_get_cluster(ctx, atom: int, K: int, max_sites: int, stream=None):
+    dev = torch.device("cuda")
+    sa = torch.empty(max_sites, dtype=torch.int32, device=dev)
+    si = torch.empty((max_sites, 3), dtype=torch.int8, device=dev)
+    lev = torch.empty(K + 1, dtype=torch.int32, device=dev)
+    _check(ctx, lib().bop_get_cluster(ctx, atom, _ptr(sa), _ptr(si), _ptr(lev), _stream(stream)))
+    ns = int(lev[-1].item())
+    return sa[:ns], si[:ns], lev
+
+
+def bop_get_bonds(ctx, norb: int, stream=None):
+    st = bop_get_stats(ctx)
+    nb = st["n_bonds"]
+    dev = torch.device("cuda")
+    hs = 1 if norb == 1 else 15
+    atoms = torch.empty((max(nb, 1), 2), dtype=torch.int32, device=dev)
+    d = torch.empty((max(nb, 1), 3), dtype=torch.float64, device=dev)
+    blk = torch.empty((max(nb, 1), hs), dtype=torch.float64, device=dev)
+    _check(ctx, lib().bop_get_bonds(ctx, _ptr(atoms), _ptr(d), _ptr(blk), _stream(stream)))
+    return atoms[:nb], d[:nb], blk[:nb]
+
+
+def bop_moments(ctx, n_spin: int, n: int, norb: int, n_mom: int, onsite=None, stream=None):
+    mu = torch.empty((n_spin, n, norb, n_mom), dtype=torch.float64, device="cuda")
+    _check(ctx, lib().bop_moments(ctx, _ptr(onsite), _ptr(mu), _stream(stream)))
+    return mu
+
+
+def bop_recursion(ctx, mu: torch.Tensor, n_exp: int, stream=None):
+    """Scalar stage of M orbitals: returns a, b, nlev, a_inf, b_inf, gsig [M][n_exp+1]."""
+    M, n_mom = mu.shape
+    Kp = (n_mom - 1) // 2
+    dev = mu.device
+    a = torch.empty((M, Kp), dtype=torch.float64, device=dev)
+    b = torch.empty((M, Kp + 1), dtype=torch.float64, device=dev)
+    nlev = torch.empty(M, dtype=torch.int32, device=dev)
+    ai = torch.empty(M, dtype=torch.float64, device=dev)
+    bi = torch.empty(M, dtype=torch.float64, device=dev)
+    gs = torch.empty((n_exp + 1, M), dtype=torch.float64, device=dev)
+    _check(ctx, lib().bop_recursion(ctx, M, _ptr(mu.contiguous()), _ptr(a), _ptr(b), _ptr(nlev), _ptr(ai),
+                                    _ptr(bi), _ptr(gs), _stream(stream)))
+    return a, b, nlev, ai, bi, gs.t().contiguous()
+
+
+def bop_energy(ctx, n: int, delta=None, m=None, stream=None, allow_noconv=False):
+    e = torch.empty(n, dtype=torch.float64, device="cuda")
+    s = bop_stats()
+    _check(ctx, lib().bop_energy(ctx, _ptr(e), _ptr(delta), _ptr(m), ctypes.byref(s), _stream(stream)),
+           allow=(BOP_ERR_NO_CONVERGENCE,) if allow_noconv else ())
+    return e, s.as_dict()
+
+
+def bop_forces(ctx, n: int, stream=None):
+    F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    W = torch.empty((3, 3), dtype=torch.float64, device="cuda")
+    s = bop_stats()
+    _check(ctx, lib().bop_forces(ctx, _ptr(F), _ptr(W), ctypes.byref(s), _stream(stream)))
+    return F, W
+
+
+def bop_get_orbital_state(ctx, M: int, n_mom: int, weights=False, stream=None):
+    dev = torch.device("cuda")
+    out = {k: torch.empty(M, dtype=torch.float64, device=dev) for k in ("N", "U", "a_inf", "b_inf", "onsite")}
+    out["mu"] = torch.empty((M, n_mom), dtype=torch.float64, device=dev)
+    out["weights"] = torch.empty((M, n_mom), dtype=torch.float64, device=dev) if weights else None
+    _check(ctx, lib().bop_get_orbital_state(ctx, _ptr(out["mu"]), _ptr(out["N"]), _ptr(out["U"]),
+                                            _ptr(out["a_inf"]), _ptr(out["b_inf"]), _ptr(out["weights"]),
+                                            _ptr(out["onsite"]), _stream(stream)))
+    return out
+
+
+def bop_evaluate_host(ctx, pos_host: torch.Tensor, cell, pbc, e_atom_host=None, forces_host=None,
+                      virial_host=None, stream=None):
+    """End-to-end E+F through host buffers (pinned tensors recommended)."""
+    cell = np.ascontiguousarray(cell, dtype=np.float64).reshape(3, 3)
+    pbc = np.ascontiguousarray(pbc, dtype=np.int32).reshape(3)
+    et = ctypes.c_double(0.0)
+    s = bop_stats()
+    _check(ctx, lib().bop_evaluate_host(ctx, pos_host.shape[0], _ptr(pos_host), _ptr(cell), _ptr(pbc),
+                                        _ptr(e_atom_host), _ptr(forces_host), _ptr(virial_host),
+                                        ctypes.cast(ctypes.pointer(et), _VP), ctypes.byref(s), _stream(stream)))
+    return et.value, s.as_dict()
+
+
+# ------------------------------------------------------------ convenience
+
+@dataclass
+class Result:
+    e_atom: torch.Tensor
+    e_total: float
+    e_fermi: float
+    forces: torch.Tensor | None
+    virial: torch.Tensor | None
+    stats: dict
+
+
+class Context:
+    """One model on the current CUDA device; owns a libbopgb context."""
+
+    def __init__(self, params, run, precision: str = "fp64"):
+        self.params, self.run, self.precision = params, run, precision
+        self.model = make_model(params, run, precision)
+        self.h = bop_create(self.model)
+        self.n = 0
+
+    def close(self):
+        if self.h:
+            bop_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build(self, pos, cell, pbc, stream=None):
+        pos = torch.as_tensor(pos, dtype=torch.float64, device="cuda").contiguous()
+        bop_build_hamiltonian(self.h, pos, cell, pbc, stream)
+        self.n = pos.shape[0]
+        return bop_get_stats(self.h)
+
+    def energy(self, delta=None, m=None, stream=None, allow_noconv=False):
+        return bop_energy(self.h, self.n, delta, m, stream, allow_noconv)
+
+    def forces(self, stream=None):
+        return bop_forces(self.h, self.n, stream)
+
+    def evaluate(self, pos, cell, pbc, forces=True) -> Result:
+        self.build(pos, cell, pbc)
+        e, st = self.energy()
+        F = W = None
+        if forces:
+            F, W = self.forces()
+        return Result(e, st["e_total"], st["e_fermi"], F, W, st)
+
+
+class BopEnergy(torch.autograd.Function):
+    """E_total(pos) with the exact gradient from the adjoint kernels.
+
+    forward: bop_build_hamiltonian + bop_energy; backward: bop_forces
+    (dE/dpos = -F) scaled by the incoming gradient."""
+
+    @staticmethod
+    def forward(actx, pos, ctx: Context, cell, pbc):
+        ctx.build(pos.detach(), cell, pbc)
+        e, st = ctx.energy()
+        F, _ = ctx.forces()
+        actx.save_for_backward(F)
+        return torch.as_tensor(st["e_total"], dtype=torch.float64, device=pos.device)
+
+    @staticmethod
+    def backward(actx, g):
+        (F,) = actx.saved_tensors
+        return -F * g, None, None, None

@@ -1,0 +1,814 @@
+// C ABI of libbopgb: the context (device workspaces), the build of the
+// neighbour list / bonds / clusters, and the orchestration of the energy
+// (SCF loop) and force passes.  Every arithmetic step of the path runs in
+// the kernels of nbr.cu, cluster.cu, moments.cu, scalar.cu and forces.cu;
+// this file only sizes buffers, launches and reads back flags.
+#include <cub/cub.cuh>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/bopgb.h"
+#include "kernels.h"
+
+int moments_columns(int norb, int cap, int fp64);
+int adjoint_columns(int norb);
+
+namespace {
+
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct bop_ctx {
+  bop_model m;
+  BondModel bm;
+  int norb, HS, HSu, K, Kp, n_mom, n_exp, S, fp64;
+  double sfac;
+  int device;
+  // structure
+  int n = 0;
+  long long E = 0, nb = 0, nsite = 0, nadj = 0;
+  Geometry g;
+  int maxlev[BOP_MAX_K + 1];
+  bool built = false, energized = false, weighted = false;
+  // buffers
+  DBuf pos, cell_of, cell_count, cell_start, cell_fill, cell_atoms, deg, row_ptr, col, img, flag, bond_scan,
+      bond_of_edge, bond_atoms, bond_img, bond_d, H64, H32, frac;
+  DBuf hkeys, hvals, skeys, sslot, scount;
+  DBuf level_end, atom_nsite, atom_nadj, max_level, site_off, adj_base, site_atom, site_img, adj_off, adj;
+  DBuf onsite, onsite32, delta, mval, delta_new, m_new, mu, a, b, nlev, a_inf, b_inf, gsig, D, gjack;
+  DBuf N, U, dos, fstate, partials, counter, result, e_total, lam, e_atom;
+  DBuf w, zscr, adjscr, Hbar, Ebar;
+  DBuf status;
+  DBuf cub_tmp;
+  int cl_hcap = 0, cl_maxs = 0, cl_slots = 0;
+  bop_stats st;
+  char err[512];
+};
+
+namespace {
+
+int fail(bop_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(c, BOP_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                       __FILE__, __LINE__);                                        \
+  } while (0)
+
+#define CKS(expr)            \
+  do {                       \
+    int s_ = (expr);         \
+    if (s_ != BOP_OK) return s_; \
+  } while (0)
+
+int ensure(bop_ctx* c, DBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return BOP_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, BOP_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  return BOP_OK;
+}
+
+template <class T>
+T* P(DBuf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+cudaStream_t S_(bop_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int check_status(bop_ctx* c, cudaStream_t s) {
+  unsigned h = 0;
+  CK(cudaMemcpyAsync(&h, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h == 0) return BOP_OK;
+  CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), s));
+  if (h & BOP_DEV_ERR_DEGREE) return fail(c, BOP_ERR_OVERFLOW, "an atom has more than %d neighbours", BOP_MAX_DEG);
+  if (h & BOP_DEV_ERR_IMAGE) return fail(c, BOP_ERR_OVERFLOW, "periodic image index outside [-127, 127]");
+  if (h & BOP_DEV_ERR_CLUSTER) return fail(c, BOP_ERR_OVERFLOW, "cluster scratch exhausted");
+  if (h & BOP_DEV_ERR_REVERSE) return fail(c, BOP_ERR_ARG, "neighbour list not symmetric");
+  if (h & BOP_DEV_ERR_NONFINITE) return fail(c, BOP_ERR_NUMERIC, "non-finite value in the scalar stages");
+  return fail(c, BOP_ERR_CUDA, "device status 0x%x", h);
+}
+
+template <class Tin, class Tout>
+int exclusive_scan(bop_ctx* c, const Tin* in, Tout* out, long long n, cudaStream_t s) {
+  size_t tmp = 0;
+  CK(cub::DeviceScan::ExclusiveSum(nullptr, tmp, in, out, (int)n, s));
+  CKS(ensure(c, c->cub_tmp, tmp));
+  CK(cub::DeviceScan::ExclusiveSum(c->cub_tmp.p, tmp, in, out, (int)n, s));
+  return BOP_OK;
+}
+
+int validate_model(bop_ctx* c, const bop_model* m) {
+  if (!m) return fail(c, BOP_ERR_ARG, "model is NULL");
+  if (m->norb != 1 && m->norb != 5) return fail(c, BOP_ERR_ARG, "norb must be 1 (s) or 5 (d)");
+  if (m->n_mom < 3 || m->n_mom > BOP_MAX_NMOM || m->n_mom % 2 == 0)
+    return fail(c, BOP_ERR_ARG, "n_mom must be odd in [3, %d]", BOP_MAX_NMOM);
+  if (m->n_exp < m->n_mom - 1 || m->n_exp > BOP_MAX_NEXP)
+    return fail(c, BOP_ERR_ARG, "n_exp must be in [n_mom-1, %d]", BOP_MAX_NEXP);
+  if (m->n_spin != 1 && m->n_spin != 2) return fail(c, BOP_ERR_ARG, "n_spin must be 1 or 2");
+  if (!(m->rc > 0) || !(m->dc > 0) || m->dc > m->rc) return fail(c, BOP_ERR_ARG, "need 0 < dc <= rc");
+  if (m->scf < 0 || m->scf > 2) return fail(c, BOP_ERR_ARG, "scf must be NONE, LCN or STONER");
+  if (m->scf == BOP_SCF_STONER && m->n_spin != 2) return fail(c, BOP_ERR_ARG, "STONER needs n_spin = 2");
+  if (m->n_spin == 2 && m->scf != BOP_SCF_STONER && m->scf != BOP_SCF_NONE)
+    return fail(c, BOP_ERR_ARG, "n_spin = 2 needs scf STONER or NONE");
+  if (m->n_e < 0 || m->n_e > 2.0 * m->norb) return fail(c, BOP_ERR_ARG, "n_e must be in [0, 2 norb]");
+  if (m->precision != BOP_PREC_FP64 && m->precision != BOP_PREC_FP32)
+    return fail(c, BOP_ERR_ARG, "precision must be FP64 or FP32");
+  if (m->scf != BOP_SCF_NONE && (m->scf_max_it < 0 || !(m->scf_tol > 0)))
+    return fail(c, BOP_ERR_ARG, "scf_tol > 0 and scf_max_it >= 0 required");
+  return BOP_OK;
+}
+
+int geometry(bop_ctx* c, const double* cell, const int* pbc, Geometry* g) {
+  memcpy(g->cell, cell, 9 * sizeof(double));
+  const double* a0 = cell;
+  const double* a1 = cell + 3;
+  const double* a2 = cell + 6;
+  double c12[3] = {a1[1] * a2[2] - a1[2] * a2[1], a1[2] * a2[0] - a1[0] * a2[2], a1[0] * a2[1] - a1[1] * a2[0]};
+  double c20[3] = {a2[1] * a0[2] - a2[2] * a0[1], a2[2] * a0[0] - a2[0] * a0[2], a2[0] * a0[1] - a2[1] * a0[0]};
+  double c01[3] = {a0[1] * a1[2] - a0[2] * a1[1], a0[2] * a1[0] - a0[0] * a1[2], a0[0] * a1[1] - a0[1] * a1[0]};
+  double vol = a0[0] * c12[0] + a0[1] * c12[1] + a0[2] * c12[2];
+  if (!(std::fabs(vol) > 1e-12)) return fail(c, BOP_ERR_ARG, "singular cell");
+  // inv[r][a] such that frac_a = sum_r pos_r inv[r][a]: columns = reciprocal vectors
+  for (int r = 0; r < 3; r++) {
+    g->inv[r * 3 + 0] = c12[r] / vol;
+    g->inv[r * 3 + 1] = c20[r] / vol;
+    g->inv[r * 3 + 2] = c01[r] / vol;
+  }
+  const double* rec[3] = {c12, c20, c01};
+  for (int a = 0; a < 3; a++) {
+    double nb = std::sqrt(rec[a][0] * rec[a][0] + rec[a][1] * rec[a][1] + rec[a][2] * rec[a][2]) / std::fabs(vol);
+    double width = 1.0 / nb;  // distance between the lattice planes spanned by the other two vectors
+    int nc = (int)std::floor(width / (c->m.rc * (1.0 + 1e-9) + 1e-9));
+    if (nc < 1) nc = 1;
+    if (nc > 1024) nc = 1024;
+    g->nc[a] = nc;
+    g->pbc[a] = pbc[a] ? 1 : 0;
+    g->nimg[a] = pbc[a] ? (int)std::ceil(c->m.rc * nb) + 1 : 0;
+  }
+  g->rc = c->m.rc;
+  return BOP_OK;
+}
+
+int build_clusters(bop_ctx* c, cudaStream_t s) {
+  const int n = c->n, K = c->K;
+  int grid = n < 1216 ? n : 1216;
+  int maxs = c->cl_maxs ? c->cl_maxs : (K <= 4 ? 1024 : (K <= 6 ? 2048 : 4096));
+  CKS(ensure(c, c->level_end, sizeof(int) * (size_t)n * (K + 1)));
+  CKS(ensure(c, c->atom_nsite, sizeof(int) * (n + 1)));
+  CKS(ensure(c, c->atom_nadj, sizeof(int) * (n + 1)));
+  CK(cudaMemsetAsync(c->atom_nsite.p, 0, sizeof(int) * (n + 1), s));
+  CK(cudaMemsetAsync(c->atom_nadj.p, 0, sizeof(int) * (n + 1), s));
+  CKS(ensure(c, c->max_level, sizeof(int) * (K + 1)));
+  CKS(ensure(c, c->site_off, sizeof(long long) * (n + 1)));
+  CKS(ensure(c, c->adj_base, sizeof(long long) * (n + 1)));
+  for (int attempt = 0; attempt < 4; attempt++) {
+    int hcap = 1;
+    while (hcap < 2 * maxs) hcap <<= 1;
+    int newcap = 1;
+    while (newcap < maxs && newcap < 8192) newcap <<= 1;
+    CKS(ensure(c, c->hkeys, sizeof(unsigned long long) * (size_t)grid * hcap));
+    CKS(ensure(c, c->hvals, sizeof(int) * (size_t)grid * hcap));
+    CKS(ensure(c, c->skeys, sizeof(unsigned long long) * (size_t)grid * maxs));
+    CKS(ensure(c, c->sslot, sizeof(int) * (size_t)grid * maxs));
+    CKS(ensure(c, c->scount, sizeof(int) * (size_t)grid * maxs));
+    CK(cudaMemsetAsync(c->hkeys.p, 0xff, sizeof(unsigned long long) * (size_t)grid * hcap, s));
+    CK(cudaMemsetAsync(c->max_level.p, 0, sizeof(int) * (K + 1), s));
+    ClusterScratch sc{P<unsigned long long>(c->hkeys), P<int>(c->hvals), P<unsigned long long>(c->skeys),
+                      P<int>(c->sslot), P<int>(c->scount), hcap, maxs, newcap};
+    ClusterOut out{};
+    out.level_end = P<int>(c->level_end);
+    out.atom_nsite = P<int>(c->atom_nsite);
+    out.atom_nadj = P<int>(c->atom_nadj);
+    out.max_level = P<int>(c->max_level);
+    if (launch_cluster(0, n, K, P<long long>(c->row_ptr), P<int>(c->col), P<signed char>(c->img),
+                       P<int>(c->bond_of_edge), sc, out, grid, P<unsigned>(c->status), s))
+      return fail(c, BOP_ERR_CUDA, "cluster pass 0 launch failed");
+    unsigned h = 0;
+    CK(cudaMemcpyAsync(&h, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h & BOP_DEV_ERR_CLUSTER) {
+      CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), s));
+      maxs *= 2;
+      continue;
+    }
+    CKS(check_status(c, s));
+    c->cl_maxs = maxs;
+    // offsets
+    CKS(exclusive_scan(c, P<int>(c->atom_nsite), P<long long>(c->site_off), n + 1, s));
+    CKS(exclusive_scan(c, P<int>(c->atom_nadj), P<long long>(c->adj_base), n + 1, s));
+    long long tot[2];
+    CK(cudaMemcpyAsync(&tot[0], P<long long>(c->site_off) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&tot[1], P<long long>(c->adj_base) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->maxlev, c->max_level.p, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    c->nsite = tot[0];
+    c->nadj = tot[1];
+    CKS(ensure(c, c->site_atom, sizeof(int) * c->nsite));
+    CKS(ensure(c, c->site_img, 3 * c->nsite));
+    CKS(ensure(c, c->adj_off, sizeof(long long) * (c->nsite + 1)));
+    CKS(ensure(c, c->adj, sizeof(int2) * c->nadj));
+    out.site_off = P<long long>(c->site_off);
+    out.adj_base = P<long long>(c->adj_base);
+    out.site_atom = P<int>(c->site_atom);
+    out.site_img = P<signed char>(c->site_img);
+    out.adj_off = P<long long>(c->adj_off);
+    out.adj = P<int2>(c->adj);
+    if (launch_cluster(1, n, K, P<long long>(c->row_ptr), P<int>(c->col), P<signed char>(c->img),
+                       P<int>(c->bond_of_edge), sc, out, grid, P<unsigned>(c->status), s))
+      return fail(c, BOP_ERR_CUDA, "cluster pass 1 launch failed");
+    CK(cudaMemcpyAsync(P<long long>(c->adj_off) + c->nsite, P<long long>(c->adj_base) + n, sizeof(long long),
+                       cudaMemcpyDeviceToDevice, s));
+    return check_status(c, s);
+  }
+  return fail(c, BOP_ERR_OVERFLOW, "cluster larger than %d sites", maxs);
+}
+
+ClusterView cview(bop_ctx* c) {
+  return ClusterView{P<long long>(c->site_off), P<int>(c->level_end), P<int>(c->site_atom),
+                     P<long long>(c->adj_off), P<int2>(c->adj), c->K};
+}
+
+int size_state(bop_ctx* c) {
+  const size_t M = (size_t)c->S * c->n * c->norb;
+  CKS(ensure(c, c->onsite, sizeof(double) * M));
+  CKS(ensure(c, c->onsite32, sizeof(float) * M));
+  CKS(ensure(c, c->delta, sizeof(double) * c->n));
+  CKS(ensure(c, c->mval, sizeof(double) * c->n));
+  CKS(ensure(c, c->delta_new, sizeof(double) * c->n));
+  CKS(ensure(c, c->m_new, sizeof(double) * c->n));
+  CKS(ensure(c, c->mu, sizeof(double) * M * c->n_mom));
+  CKS(ensure(c, c->a, sizeof(double) * M * c->Kp));
+  CKS(ensure(c, c->b, sizeof(double) * M * (c->Kp + 1)));
+  CKS(ensure(c, c->nlev, sizeof(int) * M));
+  CKS(ensure(c, c->a_inf, sizeof(double) * M));
+  CKS(ensure(c, c->b_inf, sizeof(double) * M));
+  CKS(ensure(c, c->gsig, sizeof(double) * M * (c->n_exp + 1)));
+  CKS(ensure(c, c->D, sizeof(double) * M * (c->n_exp + 3)));
+  CKS(ensure(c, c->N, sizeof(double) * M));
+  CKS(ensure(c, c->U, sizeof(double) * M));
+  CKS(ensure(c, c->dos, sizeof(double) * M));
+  CKS(ensure(c, c->e_atom, sizeof(double) * c->n));
+  return BOP_OK;
+}
+
+int run_moments(bop_ctx* c, const double* onsite_dev, double* mu, cudaStream_t s) {
+  MomentsArgs a;
+  a.cv = cview(c);
+  a.H = c->fp64 ? c->H64.p : c->H32.p;
+  a.HS = c->HS;
+  a.onsite = c->fp64 ? (const void*)onsite_dev : (const void*)c->onsite32.p;
+  a.n = c->n;
+  a.n_spin = c->S;
+  a.norb = c->norb;
+  a.n_mom = c->n_mom;
+  a.cap = c->maxlev[c->K - 1] > 0 ? c->maxlev[c->K - 1] : 1;
+  a.mu = mu;
+  int r = launch_moments(a, c->fp64, s);
+  if (r == -2) return fail(c, BOP_ERR_OVERFLOW, "cluster level too large for shared memory");
+  if (r) return fail(c, BOP_ERR_CUDA, "moments launch: %s", cudaGetErrorString(cudaGetLastError()));
+  return BOP_OK;
+}
+
+int run_scalar(bop_ctx* c, int M, const double* mu, cudaStream_t s) {
+  ScalarArgs a;
+  a.M = M;
+  a.n_mom = c->n_mom;
+  a.n_exp = c->n_exp;
+  a.mu = mu;
+  a.a = P<double>(c->a);
+  a.b = P<double>(c->b);
+  a.nlev = P<int>(c->nlev);
+  a.a_inf = P<double>(c->a_inf);
+  a.b_inf = P<double>(c->b_inf);
+  a.gsig = P<double>(c->gsig);
+  a.D = P<double>(c->D);
+  a.g = P<double>(c->gjack);
+  a.status = P<unsigned>(c->status);
+  if (launch_expand(a, s)) return fail(c, BOP_ERR_CUDA, "expand launch failed");
+  return BOP_OK;
+}
+
+int fermi_and_NU(bop_ctx* c, cudaStream_t s) {
+  const int M = c->S * c->n * c->norb;
+  const double target = c->m.n_e * c->n;
+  if (launch_fermi(M, P<double>(c->D), P<double>(c->gsig), P<double>(c->a_inf), P<double>(c->b_inf), c->n_exp,
+                   c->sfac, target, P<FermiState>(c->fstate), P<double>(c->partials), P<unsigned>(c->counter),
+                   100, 1e-13, s))
+    return fail(c, BOP_ERR_CUDA, "fermi launch failed");
+  if (launch_orbital_NU(M, c->n_exp, P<double>(c->gsig), P<double>(c->a_inf), P<double>(c->b_inf),
+                        P<double>(c->onsite), P<FermiState>(c->fstate), P<double>(c->N), P<double>(c->U),
+                        P<double>(c->dos), s))
+    return fail(c, BOP_ERR_CUDA, "orbital N/U launch failed");
+  return BOP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bop_version(void) { return 100; }
+
+int bop_create(bop_ctx** out, const bop_model* model) {
+  if (!out) return BOP_ERR_ARG;
+  *out = nullptr;
+  bop_ctx* c = new (std::nothrow) bop_ctx();
+  if (!c) return BOP_ERR_OOM;
+  c->err[0] = 0;
+  int r = validate_model(c, model);
+  if (r) {
+    fprintf(stderr, "bop_create: %s\n", c->err);
+    delete c;
+    return r;
+  }
+  c->m = *model;
+  c->norb = model->norb;
+  c->HS = model->norb == 1 ? 1 : BOP_HS_D;
+  c->HSu = model->norb == 1 ? 1 : 15;
+  c->n_mom = model->n_mom;
+  c->K = (model->n_mom - 1) / 2;
+  c->Kp = c->K;
+  c->n_exp = model->n_exp;
+  c->S = model->n_spin;
+  c->fp64 = model->precision == BOP_PREC_FP64;
+  c->sfac = model->n_spin == 1 ? 2.0 : 1.0;
+  c->bm.norb = model->norb;
+  for (int q = 0; q < 3; q++) c->bm.b0[q] = model->b0[q];
+  c->bm.r0 = model->r0;
+  c->bm.lam = model->lam;
+  c->bm.rc = model->rc;
+  c->bm.dc = model->dc;
+  cudaGetDevice(&c->device);
+  memset(&c->st, 0, sizeof(c->st));
+  if ((r = ensure(c, c->status, sizeof(unsigned))) || (r = ensure(c, c->gjack, sizeof(double) * (c->n_exp + 1))) ||
+      (r = ensure(c, c->fstate, sizeof(FermiState))) || (r = ensure(c, c->partials, sizeof(double) * 4096)) ||
+      (r = ensure(c, c->counter, sizeof(unsigned))) || (r = ensure(c, c->result, sizeof(double) * 4)) ||
+      (r = ensure(c, c->e_total, sizeof(double))) || (r = ensure(c, c->lam, sizeof(double) * 4))) {
+    bop_destroy(c);
+    return r;
+  }
+  cudaMemset(c->status.p, 0, sizeof(unsigned));
+  cudaMemset(c->counter.p, 0, sizeof(unsigned));
+  launch_jackson(P<double>(c->gjack), c->n_exp, 0);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    bop_destroy(c);
+    return BOP_ERR_CUDA;
+  }
+  *out = c;
+  return BOP_OK;
+}
+
+int bop_destroy(bop_ctx* c) {
+  if (!c) return BOP_OK;
+  DBuf* bufs[] = {&c->pos, &c->cell_of, &c->cell_count, &c->cell_start, &c->cell_fill, &c->cell_atoms, &c->deg,
+                  &c->row_ptr, &c->col, &c->img, &c->flag, &c->bond_scan, &c->bond_of_edge, &c->bond_atoms,
+                  &c->bond_img, &c->bond_d, &c->H64, &c->H32, &c->frac, &c->hkeys, &c->hvals, &c->skeys,
+                  &c->sslot, &c->scount, &c->level_end, &c->atom_nsite, &c->atom_nadj, &c->max_level,
+                  &c->site_off, &c->adj_base, &c->site_atom, &c->site_img, &c->adj_off, &c->adj, &c->onsite,
+                  &c->onsite32, &c->delta, &c->mval, &c->delta_new, &c->m_new, &c->mu, &c->a, &c->b, &c->nlev,
+                  &c->a_inf, &c->b_inf, &c->gsig, &c->D, &c->gjack, &c->N, &c->U, &c->dos, &c->fstate,
+                  &c->partials, &c->counter, &c->result, &c->e_total, &c->lam, &c->e_atom, &c->w, &c->zscr,
+                  &c->adjscr, &c->Hbar, &c->Ebar, &c->status, &c->cub_tmp};
+  for (DBuf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  delete c;
+  return BOP_OK;
+}
+
+const char* bop_last_error(const bop_ctx* c) { return c ? c->err : "null context"; }
+
+int bop_get_stats(const bop_ctx* c, bop_stats* st) {
+  if (!c || !st) return BOP_ERR_ARG;
+  *st = c->st;
+  return BOP_OK;
+}
+
+int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* cell, const int* pbc,
+                          bop_stream stream) {
+  if (!c) return BOP_ERR_ARG;
+  if (n < 1 || !pos || !cell || !pbc) return fail(c, BOP_ERR_ARG, "need n >= 1, pos, cell and pbc");
+  cudaStream_t s = S_(stream);
+  c->built = c->energized = c->weighted = false;
+  c->n = n;
+  CKS(geometry(c, cell, pbc, &c->g));
+  const Geometry& g = c->g;
+  CKS(ensure(c, c->pos, sizeof(double) * 3 * n));
+  CK(cudaMemcpyAsync(c->pos.p, pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+  const int ncell = g.nc[0] * g.nc[1] * g.nc[2];
+  CKS(ensure(c, c->cell_of, sizeof(int) * n));
+  CKS(ensure(c, c->cell_count, sizeof(int) * (ncell + 1)));
+  CKS(ensure(c, c->cell_start, sizeof(int) * (ncell + 1)));
+  CKS(ensure(c, c->cell_fill, sizeof(int) * ncell));
+  CKS(ensure(c, c->cell_atoms, sizeof(int) * n));
+  CKS(ensure(c, c->deg, sizeof(int) * (n + 1)));
+  CKS(ensure(c, c->row_ptr, sizeof(long long) * (n + 1)));
+  CKS(ensure(c, c->frac, sizeof(double) * 6 * 64));
+  const int TB = 256, gb = (n + TB - 1) / TB;
+  bopk::k_frac_range<<<64, 256, 0, s>>>(n, P<double>(c->pos), g, P<double>(c->frac));
+  CK(cudaMemsetAsync(c->cell_count.p, 0, sizeof(int) * (ncell + 1), s));
+  CK(cudaMemsetAsync(c->cell_fill.p, 0, sizeof(int) * ncell, s));
+  bopk::k_bin_atoms<<<gb, TB, 0, s>>>(n, P<double>(c->pos), g, P<int>(c->cell_of), P<int>(c->cell_count));
+  CKS(exclusive_scan(c, P<int>(c->cell_count), P<int>(c->cell_start), ncell + 1, s));
+  bopk::k_fill_cells<<<gb, TB, 0, s>>>(n, P<int>(c->cell_of), P<int>(c->cell_start), P<int>(c->cell_fill),
+                                       P<int>(c->cell_atoms));
+  CK(cudaMemsetAsync(c->deg.p, 0, sizeof(int) * (n + 1), s));
+  launch_neighbors(0, n, P<double>(c->pos), g, P<int>(c->cell_of), P<int>(c->cell_start), P<int>(c->cell_atoms),
+                   P<int>(c->deg), nullptr, nullptr, nullptr, P<unsigned>(c->status), s);
+  CK(cudaGetLastError());
+  CKS(exclusive_scan(c, P<int>(c->deg), P<long long>(c->row_ptr), n + 1, s));
+  double fr[6 * 64];
+  long long E = 0;
+  CK(cudaMemcpyAsync(fr, c->frac.p, sizeof(double) * 6 * 64, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&E, P<long long>(c->row_ptr) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CKS(check_status(c, s));
+  for (int a = 0; a < 3; a++) {
+    double mn = 1e300, mx = -1e300;
+    for (int q = 0; q < 64; q++) {
+      mn = fmin(mn, fr[6 * q + a]);
+      mx = fmax(mx, fr[6 * q + 3 + a]);
+    }
+    if (mn < -1e-9 || mx >= 1.0 + 1e-9)
+      return fail(c, BOP_ERR_ARG, "atoms outside the cell along axis %d (fractional range [%g, %g])", a, mn, mx);
+  }
+  if (E % 2) return fail(c, BOP_ERR_ARG, "odd number of directed neighbour pairs");
+  c->E = E;
+  c->nb = E / 2;
+  const long long nb = c->nb;
+  CKS(ensure(c, c->col, sizeof(int) * E));
+  CKS(ensure(c, c->img, 3 * E));
+  CKS(ensure(c, c->flag, sizeof(int) * (E + 1)));
+  CKS(ensure(c, c->bond_scan, sizeof(int) * (E + 1)));
+  CKS(ensure(c, c->bond_of_edge, sizeof(int) * E));
+  CKS(ensure(c, c->bond_atoms, sizeof(int) * 2 * nb));
+  CKS(ensure(c, c->bond_img, 3 * nb));
+  CKS(ensure(c, c->bond_d, sizeof(double) * 3 * nb));
+  CKS(ensure(c, c->H64, sizeof(double) * c->HS * nb));
+  CKS(ensure(c, c->H32, sizeof(float) * c->HS * nb));
+  launch_neighbors(1, n, P<double>(c->pos), g, P<int>(c->cell_of), P<int>(c->cell_start), P<int>(c->cell_atoms),
+                   nullptr, P<long long>(c->row_ptr), P<int>(c->col), P<signed char>(c->img),
+                   P<unsigned>(c->status), s);
+  bopk::k_edge_flags<<<gb, TB, 0, s>>>(n, P<long long>(c->row_ptr), P<int>(c->col), P<signed char>(c->img),
+                                       P<int>(c->flag));
+  if (E > 0) {
+    CKS(exclusive_scan(c, P<int>(c->flag), P<int>(c->bond_scan), E, s));
+    bopk::k_bonds<<<gb, TB, 0, s>>>(n, P<long long>(c->row_ptr), P<int>(c->col), P<signed char>(c->img),
+                                    P<int>(c->flag), P<int>(c->bond_scan), P<int>(c->bond_of_edge),
+                                    P<int>(c->bond_atoms), P<signed char>(c->bond_img), P<unsigned>(c->status));
+    bopk::k_bond_blocks<<<(int)((nb + TB - 1) / TB), TB, 0, s>>>(
+        (int)nb, P<double>(c->pos), g, c->bm, P<int>(c->bond_atoms), P<signed char>(c->bond_img),
+        P<double>(c->bond_d), P<double>(c->H64), P<float>(c->H32), c->HS);
+  }
+  CK(cudaGetLastError());
+  CKS(check_status(c, s));
+  CKS(build_clusters(c, s));
+  CKS(size_state(c));
+  c->built = true;
+  memset(&c->st, 0, sizeof(c->st));
+  c->st.n_atoms = n;
+  c->st.K = c->K;
+  c->st.n_edges = E;
+  c->st.n_bonds = nb;
+  c->st.n_sites = c->nsite;
+  c->st.n_adj = c->nadj;
+  c->st.max_cluster = c->maxlev[c->K];
+  return BOP_OK;
+}
+
+int bop_get_neighbors(bop_ctx* c, long long* row_ptr, int* col, signed char* img, bop_stream stream) {
+  if (!c || !c->built) return fail(c, BOP_ERR_STATE, "no structure built");
+  cudaStream_t s = S_(stream);
+  if (row_ptr) CK(cudaMemcpyAsync(row_ptr, c->row_ptr.p, sizeof(long long) * (c->n + 1), cudaMemcpyDeviceToDevice, s));
+  if (col && c->E) CK(cudaMemcpyAsync(col, c->col.p, sizeof(int) * c->E, cudaMemcpyDeviceToDevice, s));
+  if (img && c->E) CK(cudaMemcpyAsync(img, c->img.p, 3 * c->E, cudaMemcpyDeviceToDevice, s));
+  return BOP_OK;
+}
+
+int bop_get_cluster(bop_ctx* c, int atom, int* site_atom, signed char* site_img, int* level_end, bop_stream stream) {
+  if (!c || !c->built) return fail(c, BOP_ERR_STATE, "no structure built");
+  if (atom < 0 || atom >= c->n) return fail(c, BOP_ERR_ARG, "atom index out of range");
+  cudaStream_t s = S_(stream);
+  long long s0 = 0;
+  int lev[BOP_MAX_K + 1];
+  CK(cudaMemcpyAsync(&s0, P<long long>(c->site_off) + atom, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(lev, P<int>(c->level_end) + (size_t)atom * (c->K + 1), sizeof(int) * (c->K + 1),
+                     cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int ns = lev[c->K];
+  if (level_end) CK(cudaMemcpyAsync(level_end, lev, sizeof(int) * (c->K + 1), cudaMemcpyHostToDevice, s));
+  if (site_atom) CK(cudaMemcpyAsync(site_atom, P<int>(c->site_atom) + s0, sizeof(int) * ns, cudaMemcpyDeviceToDevice, s));
+  if (site_img) CK(cudaMemcpyAsync(site_img, P<signed char>(c->site_img) + 3 * s0, 3 * ns, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return BOP_OK;
+}
+
+int bop_get_bonds(bop_ctx* c, int* atoms, double* d, double* blocks, bop_stream stream) {
+  if (!c || !c->built) return fail(c, BOP_ERR_STATE, "no structure built");
+  cudaStream_t s = S_(stream);
+  if (c->nb == 0) return BOP_OK;
+  if (atoms) CK(cudaMemcpyAsync(atoms, c->bond_atoms.p, sizeof(int) * 2 * c->nb, cudaMemcpyDeviceToDevice, s));
+  if (d) CK(cudaMemcpyAsync(d, c->bond_d.p, sizeof(double) * 3 * c->nb, cudaMemcpyDeviceToDevice, s));
+  if (blocks)
+    CK(cudaMemcpy2DAsync(blocks, sizeof(double) * c->HSu, c->H64.p, sizeof(double) * c->HS, sizeof(double) * c->HSu,
+                         c->nb, cudaMemcpyDeviceToDevice, s));
+  return BOP_OK;
+}
+
+int bop_moments(bop_ctx* c, const double* onsite, double* mu, bop_stream stream) {
+  if (!c || !c->built) return fail(c, BOP_ERR_STATE, "no structure built");
+  if (!mu) return fail(c, BOP_ERR_ARG, "mu is NULL");
+  cudaStream_t s = S_(stream);
+  const size_t M = (size_t)c->S * c->n * c->norb;
+  if (onsite) {
+    CK(cudaMemcpyAsync(c->onsite.p, onsite, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+    launch_to_float(P<double>(c->onsite), P<float>(c->onsite32), M, s);
+  } else {
+    launch_build_onsite(c->n, c->norb, c->S, c->m.onsite0, 0.0, nullptr, nullptr, P<double>(c->onsite),
+                        P<float>(c->onsite32), s);
+  }
+  CKS(run_moments(c, P<double>(c->onsite), mu, s));
+  CK(cudaGetLastError());
+  return BOP_OK;
+}
+
+int bop_recursion(bop_ctx* c, int M, const double* mu, double* a, double* b, int* nlev, double* a_inf,
+                  double* b_inf, double* gsig, bop_stream stream) {
+  if (!c) return BOP_ERR_ARG;
+  if (M < 1 || !mu || !gsig) return fail(c, BOP_ERR_ARG, "need M >= 1, mu and gsig");
+  cudaStream_t s = S_(stream);
+  DBuf ta, tb, tn, tai, tbi, tD;
+  auto cleanup = [&]() {
+    for (DBuf* q : {&ta, &tb, &tn, &tai, &tbi, &tD})
+      if (q->p) cudaFree(q->p);
+  };
+  int r;
+  if ((r = ensure(c, ta, sizeof(double) * M * c->Kp)) || (r = ensure(c, tb, sizeof(double) * M * (c->Kp + 1))) ||
+      (r = ensure(c, tn, sizeof(int) * M)) || (r = ensure(c, tai, sizeof(double) * M)) ||
+      (r = ensure(c, tbi, sizeof(double) * M)) || (r = ensure(c, tD, sizeof(double) * M * (c->n_exp + 3)))) {
+    cleanup();
+    return r;
+  }
+  ScalarArgs A;
+  A.M = M;
+  A.n_mom = c->n_mom;
+  A.n_exp = c->n_exp;
+  A.mu = mu;
+  A.a = a ? a : P<double>(ta);
+  A.b = b ? b : P<double>(tb);
+  A.nlev = nlev ? nlev : P<int>(tn);
+  A.a_inf = a_inf ? a_inf : P<double>(tai);
+  A.b_inf = b_inf ? b_inf : P<double>(tbi);
+  A.gsig = gsig;
+  A.D = P<double>(tD);
+  A.g = P<double>(c->gjack);
+  A.status = P<unsigned>(c->status);
+  r = launch_expand(A, s) ? fail(c, BOP_ERR_CUDA, "expand launch failed") : BOP_OK;
+  if (r == BOP_OK) r = check_status(c, s);
+  cleanup();
+  return r;
+}
+
+int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_stats* st, bop_stream stream) {
+  if (!c || !c->built) return fail(c, BOP_ERR_STATE, "no structure built");
+  cudaStream_t s = S_(stream);
+  const int n = c->n, M = c->S * n * c->norb;
+  c->energized = c->weighted = false;
+  if (delta_io) CK(cudaMemcpyAsync(c->delta.p, delta_io, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  else CK(cudaMemsetAsync(c->delta.p, 0, sizeof(double) * n, s));
+  const bool stoner = c->m.scf == BOP_SCF_STONER;
+  if (stoner) {
+    if (m_io) CK(cudaMemcpyAsync(c->mval.p, m_io, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    else {
+      std::vector<double> h(n, c->m.m0);
+      CK(cudaMemcpyAsync(c->mval.p, h.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      CK(cudaStreamSynchronize(s));
+    }
+  }
+  int it = 0, converged = c->m.scf == BOP_SCF_NONE;
+  double res[4] = {0, 0, 0, 0};
+  for (;;) {
+    launch_build_onsite(n, c->norb, c->S, c->m.onsite0, c->m.stoner_I, P<double>(c->delta),
+                        stoner ? P<double>(c->mval) : nullptr, P<double>(c->onsite), P<float>(c->onsite32), s);
+    CKS(run_moments(c, P<double>(c->onsite), P<double>(c->mu), s));
+    CKS(run_scalar(c, M, P<double>(c->mu), s));
+    CKS(fermi_and_NU(c, s));
+    if (c->m.scf == BOP_SCF_NONE || it >= c->m.scf_max_it) break;
+    ScfArgs a;
+    a.n = n;
+    a.norb = c->norb;
+    a.n_spin = c->S;
+    a.mode = c->m.scf;
+    a.spin_factor = c->sfac;
+    a.n0 = c->m.n_e;
+    a.eta = c->m.eta;
+    a.tol = c->m.scf_tol;
+    a.dos_floor = c->m.dos_floor;
+    a.stoner_I = c->m.stoner_I;
+    a.m_mix = c->m.m_mix;
+    a.onsite0 = c->m.onsite0;
+    a.N = P<double>(c->N);
+    a.dos = P<double>(c->dos);
+    a.delta = P<double>(c->delta);
+    a.m = P<double>(c->mval);
+    a.delta_new = P<double>(c->delta_new);
+    a.m_new = P<double>(c->m_new);
+    a.onsite = P<double>(c->onsite);
+    a.onsite32 = P<float>(c->onsite32);
+    a.red = P<double>(c->partials);
+    a.counter = P<unsigned>(c->counter);
+    a.result = P<double>(c->result);
+    if (launch_scf_update(a, s)) return fail(c, BOP_ERR_CUDA, "scf update launch failed");
+    CK(cudaMemcpyAsync(res, c->result.p, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+    CKS(check_status(c, s));
+    if (res[2] != 0.0) {
+      converged = 1;
+      break;
+    }
+    it++;
+  }
+  if (launch_energy(n, c->norb, c->S, c->sfac, c->m.stoner_I, P<double>(c->U), stoner ? P<double>(c->mval) : nullptr,
+                    e_atom ? e_atom : P<double>(c->e_atom), P<double>(c->partials), P<unsigned>(c->counter),
+                    P<double>(c->e_total), s))
+    return fail(c, BOP_ERR_CUDA, "energy launch failed");
+  if (delta_io) CK(cudaMemcpyAsync(delta_io, c->delta.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  if (m_io && stoner) CK(cudaMemcpyAsync(m_io, c->mval.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  FermiState fs;
+  double et = 0.0;
+  CK(cudaMemcpyAsync(&fs, c->fstate.p, sizeof(FermiState), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&et, c->e_total.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CKS(check_status(c, s));
+  c->st.scf_iterations = it;
+  c->st.scf_converged = converged;
+  c->st.bisection_rounds = fs.iters;
+  c->st.scf_residual = res[0];
+  c->st.e_fermi = fs.ef;
+  c->st.e_total = et;
+  c->st.forces_scf_response = c->m.scf == BOP_SCF_NONE ? 1 : 0;
+  if (st) *st = c->st;
+  c->energized = true;
+  if (!converged) return fail(c, BOP_ERR_NO_CONVERGENCE, "SCF not converged after %d iterations (residual %g)",
+                              it, res[0]);
+  return BOP_OK;
+}
+
+int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_stream stream) {
+  if (!c || !c->built || !c->energized) return fail(c, BOP_ERR_STATE, "bop_forces needs a preceding bop_energy");
+  cudaStream_t s = S_(stream);
+  const int n = c->n, M = c->S * n * c->norb;
+  CKS(ensure(c, c->w, sizeof(double) * (size_t)M * c->n_mom));
+  CKS(ensure(c, c->zscr, sizeof(double) * (size_t)M * (c->n_exp + 1) * (c->Kp + 2)));
+  CKS(ensure(c, c->Hbar, sizeof(double) * (size_t)(c->nb > 0 ? c->nb : 1) * c->HSu));
+  CKS(ensure(c, c->Ebar, sizeof(double) * (size_t)M));
+  // E_F response and weights
+  if (launch_ef_response(M, c->n_exp, P<double>(c->gsig), P<double>(c->a_inf), P<double>(c->b_inf),
+                         P<double>(c->onsite), P<FermiState>(c->fstate), P<double>(c->partials),
+                         P<unsigned>(c->counter), P<double>(c->lam), s))
+    return fail(c, BOP_ERR_CUDA, "E_F response launch failed");
+  WeightArgs wa;
+  wa.M = M;
+  wa.n_mom = c->n_mom;
+  wa.n_exp = c->n_exp;
+  wa.norb = c->norb;
+  wa.mu = P<double>(c->mu);
+  wa.onsite = P<double>(c->onsite);
+  wa.st = P<FermiState>(c->fstate);
+  wa.g = P<double>(c->gjack);
+  wa.cU = c->sfac;
+  wa.lam = P<double>(c->lam);
+  wa.w = P<double>(c->w);
+  wa.dU_dE = nullptr;
+  wa.zscratch = P<double>(c->zscr);
+  wa.status = P<unsigned>(c->status);
+  if (launch_weights(wa, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
+  // reverse sweep of the moments
+  int nc = adjoint_columns(c->norb);
+  size_t per_site = (size_t)c->norb * nc;
+  long long levsum = 0;
+  for (int k = 0; k <= c->K; k++) levsum += c->maxlev[k];
+  size_t slot_elems = (2 * (size_t)levsum) * per_site + 64;
+  int nwork = n * c->S * (c->norb / nc);
+  int slots = nwork < 1216 ? nwork : 1216;
+  size_t esz = c->fp64 ? sizeof(double) : sizeof(float);
+  CKS(ensure(c, c->adjscr, esz * slot_elems * slots));
+  CK(cudaMemsetAsync(c->Hbar.p, 0, sizeof(double) * (size_t)(c->nb > 0 ? c->nb : 1) * c->HSu, s));
+  CK(cudaMemsetAsync(c->Ebar.p, 0, sizeof(double) * (size_t)M, s));
+  AdjointArgs aa;
+  aa.cv = cview(c);
+  aa.H = c->fp64 ? c->H64.p : c->H32.p;
+  aa.HS = c->HS;
+  aa.onsite = c->fp64 ? c->onsite.p : c->onsite32.p;
+  aa.n = n;
+  aa.n_spin = c->S;
+  aa.norb = c->norb;
+  aa.n_mom = c->n_mom;
+  aa.w = P<double>(c->w);
+  aa.scratch = c->adjscr.p;
+  aa.slot_elems = slot_elems;
+  aa.slots = slots;
+  aa.Hbar = P<double>(c->Hbar);
+  aa.HSu = c->HSu;
+  aa.Ebar = P<double>(c->Ebar);
+  if (launch_moments_adjoint(aa, c->fp64, s)) return fail(c, BOP_ERR_CUDA, "adjoint launch failed");
+  DBuf* fb = nullptr;
+  DBuf tf, tv;
+  double* F = forces;
+  double* W = virial;
+  if (!F) {
+    CKS(ensure(c, tf, sizeof(double) * 3 * n));
+    F = P<double>(tf);
+    fb = &tf;
+  }
+  if (!W) {
+    CKS(ensure(c, tv, sizeof(double) * 9));
+    W = P<double>(tv);
+  }
+  CK(cudaMemsetAsync(F, 0, sizeof(double) * 3 * n, s));
+  CK(cudaMemsetAsync(W, 0, sizeof(double) * 9, s));
+  if (c->nb > 0 &&
+      launch_forces((int)c->nb, c->bm, P<double>(c->bond_d), P<int>(c->bond_atoms), P<double>(c->Hbar), c->HSu, F, W, s))
+    return fail(c, BOP_ERR_CUDA, "forces launch failed");
+  int r = check_status(c, s);
+  if (fb && tf.p) cudaFree(tf.p);
+  if (tv.p) cudaFree(tv.p);
+  if (r) return r;
+  c->weighted = true;
+  if (st) *st = c->st;
+  return BOP_OK;
+}
+
+int bop_get_orbital_state(bop_ctx* c, double* mu, double* N, double* U, double* a_inf, double* b_inf,
+                          double* weights, double* onsite, bop_stream stream) {
+  if (!c || !c->energized) return fail(c, BOP_ERR_STATE, "no energy computed");
+  cudaStream_t s = S_(stream);
+  const size_t M = (size_t)c->S * c->n * c->norb;
+  if (mu) CK(cudaMemcpyAsync(mu, c->mu.p, sizeof(double) * M * c->n_mom, cudaMemcpyDeviceToDevice, s));
+  if (N) CK(cudaMemcpyAsync(N, c->N.p, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+  if (U) CK(cudaMemcpyAsync(U, c->U.p, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+  if (a_inf) CK(cudaMemcpyAsync(a_inf, c->a_inf.p, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+  if (b_inf) CK(cudaMemcpyAsync(b_inf, c->b_inf.p, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+  if (onsite) CK(cudaMemcpyAsync(onsite, c->onsite.p, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+  if (weights) {
+    if (!c->weighted) return fail(c, BOP_ERR_STATE, "weights need bop_forces");
+    CK(cudaMemcpyAsync(weights, c->w.p, sizeof(double) * M * c->n_mom, cudaMemcpyDeviceToDevice, s));
+  }
+  return BOP_OK;
+}
+
+int bop_evaluate_host(bop_ctx* c, int n, const double* pos_host, const double* cell_host, const int* pbc_host,
+                      double* e_atom_host, double* forces_host, double* virial_host, double* e_total_host,
+                      bop_stats* st, bop_stream stream) {
+  if (!c) return BOP_ERR_ARG;
+  if (n < 1 || !pos_host) return fail(c, BOP_ERR_ARG, "need n >= 1 and pos_host");
+  cudaStream_t s = S_(stream);
+  DBuf dpos, dF, dW;
+  int r = ensure(c, dpos, sizeof(double) * 3 * n);
+  if (!r) r = ensure(c, dF, sizeof(double) * 3 * n);
+  if (!r) r = ensure(c, dW, sizeof(double) * 9);
+  if (!r && cudaMemcpyAsync(dpos.p, pos_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    r = fail(c, BOP_ERR_CUDA, "H2D copy of positions failed");
+  if (!r) r = bop_build_hamiltonian(c, n, P<double>(dpos), cell_host, pbc_host, stream);
+  if (!r) r = bop_energy(c, nullptr, nullptr, nullptr, nullptr, stream);
+  if (!r) r = bop_forces(c, P<double>(dF), P<double>(dW), nullptr, stream);
+  if (!r && e_atom_host &&
+      cudaMemcpyAsync(e_atom_host, c->e_atom.p, sizeof(double) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    r = fail(c, BOP_ERR_CUDA, "D2H copy failed");
+  if (!r && forces_host &&
+      cudaMemcpyAsync(forces_host, dF.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    r = fail(c, BOP_ERR_CUDA, "D2H copy failed");
+  if (!r && virial_host &&
+      cudaMemcpyAsync(virial_host, dW.p, sizeof(double) * 9, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    r = fail(c, BOP_ERR_CUDA, "D2H copy failed");
+  if (!r && cudaStreamSynchronize(s) != cudaSuccess) r = fail(c, BOP_ERR_CUDA, "synchronise failed");
+  if (!r && e_total_host) *e_total_host = c->st.e_total;
+  if (!r && st) *st = c->st;
+  for (DBuf* q : {&dpos, &dF, &dW})
+    if (q->p) cudaFree(q->p);
+  return r;
+}
+
+}  // extern "C"

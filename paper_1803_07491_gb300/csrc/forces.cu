@@ -1,0 +1,68 @@
+// Forces and virial from the bond cotangents (Eq. F_k, Eq. sigma_k): for
+// every bond b with vector d_b = r_j + S.cell - r_i,
+//   g_b = sum_u Hbar_b,u  dH_b,u / dd_b      (u = unique block elements)
+//   F_i += g_b,  F_j -= g_b,  W += g_b (x) d_b.
+// dH/dd is exact: the two-centre block is evaluated in forward-mode dual
+// numbers.
+#include "kernels.h"
+
+namespace {
+
+constexpr int FT = 256;
+
+__global__ void __launch_bounds__(FT) k_forces(int nb, BondModel m, const double* __restrict__ bond_d,
+                                               const int* __restrict__ bond_atoms, const double* __restrict__ Hbar,
+                                               int HSu, double* __restrict__ F, double* __restrict__ W) {
+  __shared__ double sw[9][FT / 32];
+  double w9[9];
+  for (int q = 0; q < 9; q++) w9[q] = 0.0;
+  for (int b = blockIdx.x * FT + threadIdx.x; b < nb; b += gridDim.x * FT) {
+    D3 d[3];
+    double dv[3] = {bond_d[3 * b], bond_d[3 * b + 1], bond_d[3 * b + 2]};
+    d[0] = {dv[0], 1.0, 0.0, 0.0};
+    d[1] = {dv[1], 0.0, 1.0, 0.0};
+    d[2] = {dv[2], 0.0, 0.0, 1.0};
+    D3 u[15];
+    sk_unique<D3>(m, d, u);
+    const int nu = m.norb == 1 ? 1 : 15;
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    for (int q = 0; q < nu; q++) {
+      double hb = Hbar[(size_t)b * HSu + q];
+      g0 += hb * u[q].g0;
+      g1 += hb * u[q].g1;
+      g2 += hb * u[q].g2;
+    }
+    int i = bond_atoms[2 * b], j = bond_atoms[2 * b + 1];
+    atomicAdd(F + 3 * i, g0);
+    atomicAdd(F + 3 * i + 1, g1);
+    atomicAdd(F + 3 * i + 2, g2);
+    atomicAdd(F + 3 * j, -g0);
+    atomicAdd(F + 3 * j + 1, -g1);
+    atomicAdd(F + 3 * j + 2, -g2);
+    double g[3] = {g0, g1, g2};
+    for (int a = 0; a < 3; a++)
+      for (int c = 0; c < 3; c++) w9[3 * a + c] += g[a] * dv[c];
+  }
+  for (int q = 0; q < 9; q++) {
+    double v = w9[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sw[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double v = 0.0;
+    for (int q = 0; q < FT / 32; q++) v += sw[threadIdx.x][q];
+    atomicAdd(W + threadIdx.x, v);
+  }
+}
+
+}  // namespace
+
+int launch_forces(int nb, BondModel m, const double* bond_d, const int* bond_atoms, const double* Hbar, int HSu,
+                  double* forces, double* virial, cudaStream_t s) {
+  int g = (nb + FT - 1) / FT;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  k_forces<<<g, FT, 0, s>>>(nb, m, bond_d, bond_atoms, Hbar, HSu, forces, virial);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}

@@ -1,0 +1,164 @@
+// Internal interface between the C-ABI layer (api.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+// Cell, its inverse and the linked-cell grid of one structure.
+struct Geometry {
+  double cell[9];  // rows = lattice vectors
+  double inv[9];   // inverse matrix: frac = pos * inv
+  int nc[3];       // linked cells per axis (cell width >= rc)
+  int nimg[3];     // image search range for axes with fewer than 3 cells
+  int pbc[3];
+  double rc;
+};
+
+// Per-CTA scratch of the cluster builder (global memory).
+struct ClusterScratch {
+  unsigned long long* hkeys;  // [slots][hcap]
+  int* hvals;                 // [slots][hcap]
+  unsigned long long* skeys;  // [slots][maxs] site keys in cluster order
+  int* sslot;                 // [slots][maxs] hash slot of every site
+  int* scount;                // [slots][maxs] adjacency count / offset per site
+  int hcap, maxs, newcap;
+};
+
+// Outputs of the cluster builder.
+struct ClusterOut {
+  int* level_end;        // [n][K+1]
+  int* atom_nsite;       // [n]  (pass 1)
+  int* atom_nadj;        // [n]  (pass 1)
+  int* max_level;        // [K+1] largest |C_k| over atoms (pass 1)
+  const long long* site_off;  // [n+1] (pass 2 input)
+  const long long* adj_base;  // [n+1] (pass 2 input)
+  int* site_atom;        // [S]
+  signed char* site_img; // [S][3]
+  long long* adj_off;    // [S+1]
+  int2* adj;             // [A]
+};
+
+namespace bopk {
+// nbr.cu
+__global__ void k_bin_atoms(int n, const double* pos, Geometry g, int* cell_of, int* cell_count);
+__global__ void k_fill_cells(int n, const int* cell_of, const int* cell_start, int* cell_fill, int* cell_atoms);
+__global__ void k_edge_flags(int n, const long long* row_ptr, const int* col, const signed char* img, int* flag);
+__global__ void k_bonds(int n, const long long* row_ptr, const int* col, const signed char* img, const int* flag,
+                        const int* bond_scan, int* bond_of_edge, int* bond_atoms, signed char* bond_img,
+                        unsigned* status);
+__global__ void k_bond_blocks(int nb, const double* pos, Geometry g, BondModel m, const int* bond_atoms,
+                              const signed char* bond_img, double* bond_d, double* H64, float* H32, int HS);
+__global__ void k_frac_range(int n, const double* pos, Geometry g, double* out);
+}  // namespace bopk
+
+// Host launchers (defined in the .cu files that hold the templates).
+void launch_neighbors(int mode, int n, const double* pos, Geometry g, const int* cell_of, const int* cell_start,
+                      const int* cell_atoms, int* deg, const long long* row_ptr, int* col, signed char* img,
+                      unsigned* status, cudaStream_t s);
+int launch_cluster(int pass, int n, int K, const long long* row_ptr, const int* col, const signed char* img,
+                   const int* bond_of_edge, ClusterScratch sc, ClusterOut out, int grid, unsigned* status,
+                   cudaStream_t s);
+
+struct MomentsArgs {
+  ClusterView cv;
+  const void* H;       // float or double [nb][HS]
+  int HS;
+  const void* onsite;  // float or double [S][n][norb]
+  int n, n_spin, norb, n_mom;
+  int cap;             // largest stored level |C_{K-1}| over atoms
+  double* mu;          // [S][n][norb][n_mom]
+};
+int launch_moments(const MomentsArgs& a, int fp64, cudaStream_t s);
+
+struct AdjointArgs {
+  ClusterView cv;
+  const void* H;
+  int HS;
+  const void* onsite;
+  int n, n_spin, norb, n_mom;
+  const double* w;     // [S][n][norb][n_mom]
+  void* scratch;       // per-CTA Psi / Psi-bar storage
+  size_t slot_elems;   // elements of T per CTA
+  int slots;
+  double* Hbar;        // [nb][HSu]   (+=)
+  int HSu;
+  double* Ebar;        // [S][n][norb] (+=), may be null
+};
+int launch_moments_adjoint(const AdjointArgs& a, int fp64, cudaStream_t s);
+
+// scalar.cu
+struct ScalarArgs {
+  int M;               // orbitals (all spins)
+  int n_mom, n_exp;
+  const double* mu;    // [M][n_mom]
+  double* a;           // [M][Kp]
+  double* b;           // [M][Kp+1]
+  int* nlev;           // [M]
+  double* a_inf;       // [M]
+  double* b_inf;       // [M]
+  double* gsig;        // [n_exp+1][M]   (transposed)
+  double* D;           // [n_exp+3][M]   sine-series coefficients of N
+  const double* g;     // [n_exp+1] damping
+  unsigned* status;
+};
+int launch_expand(const ScalarArgs& a, cudaStream_t s);
+void launch_jackson(double* g, int n_exp, cudaStream_t s);
+
+struct FermiState {
+  double lo, hi, mid, ef;
+  int done, iters, pad0, pad1;
+};
+int launch_fermi(int M, const double* D, const double* gsig, const double* a_inf, const double* b_inf, int n_exp,
+                 double spin_factor, double target, FermiState* st, double* partials, unsigned* counter,
+                 int max_rounds, double tol, cudaStream_t s);
+
+int launch_orbital_NU(int M, int n_exp, const double* gsig, const double* a_inf, const double* b_inf,
+                      const double* onsite, const FermiState* st, double* N, double* U, double* dos,
+                      cudaStream_t s);
+
+struct ScfArgs {
+  int n, norb, n_spin, mode;  // mode 1 = LCN, 2 = Stoner
+  double spin_factor, n0, eta, tol, dos_floor, stoner_I, m_mix, onsite0;
+  const double* N;     // [S][n][norb]
+  const double* dos;   // [S][n][norb]
+  double* delta;       // [n]
+  double* m;           // [n]
+  double* delta_new;   // [n]
+  double* m_new;       // [n]
+  double* onsite;      // [S][n][norb] (rebuilt)
+  float* onsite32;
+  double* red;         // partials
+  unsigned* counter;
+  double* result;      // [4]: max|res|, max|dm|, converged, mean
+};
+int launch_scf_update(const ScfArgs& a, cudaStream_t s);
+void launch_to_float(const double* in, float* out, size_t n, cudaStream_t s);
+void launch_build_onsite(int n, int norb, int n_spin, double onsite0, double stoner_I, const double* delta,
+                         const double* m, double* onsite, float* onsite32, cudaStream_t s);
+
+int launch_energy(int n, int norb, int n_spin, double spin_factor, double stoner_I, const double* U,
+                  const double* m, double* e_atom, double* red, unsigned* counter, double* e_total,
+                  cudaStream_t s);
+
+struct WeightArgs {
+  int M, n_mom, n_exp, norb;
+  const double* mu;
+  const double* onsite;  // [M]
+  const FermiState* st;
+  const double* g;
+  double cU;             // L = cU*U + (cN + cN_orb[o]) * N
+  const double* lam;     // device scalar: cN = -cU * (*lam)  (E_F response)
+  double* w;             // [M][n_mom]
+  double* dU_dE;         // [M] direct derivative of L w.r.t. the onsite level, may be null
+  double* zscratch;      // [M][(n_exp+1)*(Kp+2)]
+  unsigned* status;
+};
+int launch_weights(const WeightArgs& a, cudaStream_t s);
+int launch_ef_response(int M, int n_exp, const double* gsig, const double* a_inf, const double* b_inf,
+                       const double* onsite, const FermiState* st, double* red, unsigned* counter, double* lam,
+                       cudaStream_t s);
+
+// forces.cu
+int launch_forces(int nb, BondModel m, const double* bond_d, const int* bond_atoms, const double* Hbar, int HSu,
+                  double* forces, double* virial, cudaStream_t s);

@@ -1,0 +1,402 @@
+// Moments mu_n(i alpha) = <i alpha|H^n|i alpha> (Eq. momDOS) by the
+// iterated interference paths Psi_k = H Psi_{k-1} (Eq. xi_rec) over every
+// atom's cluster, with the merge property (Eq. xi_merge):
+//   mu_2k = <Psi_k|Psi_k>,   mu_2k-1 = <Psi_k-1|Psi_k>,
+// and the reverse sweep of the same recursion, which gives dU/dH for every
+// bond and dU/dE for every onsite level from the weights w_n = dU/dmu_n
+// (the Theta-tilde / transfer-path sums of Eqs. theta-tilde, Xi).
+//
+// Forward: one CTA per (spin, atom[, alpha]).  Psi_{k-1} and Psi_k live in
+// shared memory (ping-pong); the last level Psi_K is never stored, only its
+// inner products.  Each thread owns one cluster site per pass and gathers
+// the 5x5 blocks of its bonds (15 unique elements, 16-element records) from
+// L2.  Products in T (float or double), moments written as double.
+//
+// Adjoint: one CTA per work item as well, Psi_0..Psi_K and the cotangents
+// Psi-bar_1..Psi-bar_K kept in the CTA's slot of global scratch; the bond
+// cotangents are summed over levels per cluster edge and added to the
+// bond's unique elements with FP64 atomics.
+#include "kernels.h"
+
+namespace {
+
+constexpr int MOM_THREADS = 256;
+
+template <typename T>
+struct Blk;
+template <>
+struct Blk<float> {
+  __device__ static void load(const float* __restrict__ h, float u[16]) {
+    const float4* p = reinterpret_cast<const float4*>(h);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      float4 v = __ldg(p + q);
+      u[4 * q] = v.x; u[4 * q + 1] = v.y; u[4 * q + 2] = v.z; u[4 * q + 3] = v.w;
+    }
+  }
+};
+template <>
+struct Blk<double> {
+  __device__ static void load(const double* __restrict__ h, double u[16]) {
+    const double2* p = reinterpret_cast<const double2*>(h);
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      double2 v = __ldg(p + q);
+      u[2 * q] = v.x; u[2 * q + 1] = v.y;
+    }
+  }
+};
+
+// unique element of (row, col) in the 15-element upper triangle
+__device__ __forceinline__ constexpr int U5(int b, int g) {
+  return b <= g ? b * 5 - (b * (b - 1)) / 2 + (g - b) : g * 5 - (g * (g - 1)) / 2 + (b - g);
+}
+
+// acc[r][c] += B[r][g] * x[g][c] for the symmetric block B given by u[].
+template <typename T, int NO, int NC>
+__device__ __forceinline__ void block_apply(const T* __restrict__ hrec, const T* __restrict__ x,
+                                            T acc[NO][NC]) {
+  if constexpr (NO == 1) {
+    T h = hrec[0];
+#pragma unroll
+    for (int c = 0; c < NC; c++) acc[0][c] += h * x[c];
+  } else {
+    T u[16];
+    Blk<T>::load(hrec, u);
+    T xs[NO][NC];
+#pragma unroll
+    for (int g = 0; g < NO; g++)
+#pragma unroll
+      for (int c = 0; c < NC; c++) xs[g][c] = x[g * NC + c];
+#pragma unroll
+    for (int r = 0; r < NO; r++)
+#pragma unroll
+      for (int g = 0; g < NO; g++) {
+        T h = u[U5(r, g)];
+#pragma unroll
+        for (int c = 0; c < NC; c++) acc[r][c] += h * xs[g][c];
+      }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// y[t] = E_t * x[t] (t < ncol) + sum_{adjacent s < ncol} B_ts x[s], t < nrow.
+// One thread per site; returns nothing, the caller consumes acc.
+template <typename T, int NO, int NC>
+__device__ __forceinline__ void gather_row(const ClusterView& cv, const T* __restrict__ H, int HS,
+                                           const T* __restrict__ E, const int* __restrict__ satom,
+                                           const long long* __restrict__ aoff, int t, int ncol,
+                                           const T* __restrict__ x, T acc[NO][NC]) {
+#pragma unroll
+  for (int r = 0; r < NO; r++)
+#pragma unroll
+    for (int c = 0; c < NC; c++) acc[r][c] = T(0);
+  if (t < ncol) {
+    const T* e = E + (size_t)satom[t] * NO;
+#pragma unroll
+    for (int r = 0; r < NO; r++) {
+      T er = e[r];
+#pragma unroll
+      for (int c = 0; c < NC; c++) acc[r][c] = er * x[(t * NO + r) * NC + c];
+    }
+  }
+  const long long q1 = aoff[t + 1];
+  for (long long q = aoff[t]; q < q1; q++) {
+    int2 en = cv.adj[q];
+    if (en.x >= ncol) break;
+    block_apply<T, NO, NC>(H + (size_t)en.y * HS, x + (size_t)en.x * NO * NC, acc);
+  }
+}
+
+// ------------------------------------------------------------------ forward
+template <typename T, int NO, int NC>
+__global__ void __launch_bounds__(MOM_THREADS)
+k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_mom,
+          int cap, double* __restrict__ mu) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* bufA = reinterpret_cast<T*>(smem_raw);
+  T* bufB = bufA + (size_t)cap * NO * NC;
+  __shared__ T red[2 * NC][MOM_THREADS / 32];
+  const int K = cv.K;
+  const int w = blockIdx.x;
+  const int grp = (NC == NO) ? 0 : (w % NO);
+  const int sa = (NC == NO) ? w : (w / NO);
+  const int spin = sa / n, atom = sa % n;
+  const long long s0 = cv.site_off[atom];
+  const int* lev = cv.level_end + (size_t)atom * (K + 1);
+  const int* satom = cv.site_atom + s0;
+  const long long* aoff = cv.adj_off + s0;
+  const T* E = onsite + (size_t)spin * n * NO;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+  for (int q = tid; q < NO * NC; q += blockDim.x) {
+    int r = q / NC, c = q % NC;
+    bufA[q] = (NC == NO) ? T(r == c ? 1 : 0) : T(r == grp ? 1 : 0);
+  }
+  __syncthreads();
+  T* prev = bufA;
+  T* cur = bufB;
+  double* out = mu + ((size_t)sa * NO + grp) * n_mom;  // column c adds c*n_mom when NC == NO
+  if (tid < NC) out[(size_t)tid * n_mom] = 1.0;
+  for (int k = 1; k <= K; k++) {
+    const int nrow = lev[k], ncol = lev[k - 1];
+    T d1[NC], d2[NC];
+#pragma unroll
+    for (int c = 0; c < NC; c++) d1[c] = d2[c] = T(0);
+    for (int t = tid; t < nrow; t += blockDim.x) {
+      T acc[NO][NC];
+      gather_row<T, NO, NC>(cv, H, HS, E, satom, aoff, t, ncol, prev, acc);
+      if (t < ncol) {
+#pragma unroll
+        for (int r = 0; r < NO; r++)
+#pragma unroll
+          for (int c = 0; c < NC; c++) d1[c] += prev[(t * NO + r) * NC + c] * acc[r][c];
+      }
+#pragma unroll
+      for (int r = 0; r < NO; r++)
+#pragma unroll
+        for (int c = 0; c < NC; c++) d2[c] += acc[r][c] * acc[r][c];
+      if (k < K) {
+#pragma unroll
+        for (int r = 0; r < NO; r++)
+#pragma unroll
+          for (int c = 0; c < NC; c++) cur[(t * NO + r) * NC + c] = acc[r][c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      T a = warp_sum(d1[c]), b = warp_sum(d2[c]);
+      if (lane == 0) {
+        red[c][wid] = a;
+        red[NC + c][wid] = b;
+      }
+    }
+    __syncthreads();
+    if (tid < 2 * NC) {
+      T acc = T(0);
+      for (int q = 0; q < (int)(blockDim.x >> 5); q++) acc += red[tid][q];
+      int c = tid % NC;
+      int m = tid < NC ? 2 * k - 1 : 2 * k;
+      out[(size_t)c * n_mom + m] = (double)acc;
+    }
+    __syncthreads();
+    T* sw = prev;
+    prev = cur;
+    cur = sw;
+  }
+}
+
+// ------------------------------------------------------------------ adjoint
+__device__ __forceinline__ int site_level(const int* lev, int K, int t) {
+  int k = 0;
+  while (k < K && t >= lev[k]) k++;
+  return k;
+}
+
+template <typename T, int NO, int NC>
+__global__ void __launch_bounds__(MOM_THREADS)
+k_moments_adj(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_mom,
+              int nwork, const double* __restrict__ wts, T* __restrict__ scratch, size_t slot_elems,
+              double* __restrict__ Hbar, int HSu, double* __restrict__ Ebar) {
+  __shared__ T ws[NC][BOP_MAX_NMOM];
+  __shared__ int s_lev[BOP_MAX_K + 1];
+  __shared__ long long s_off[BOP_MAX_K + 2];
+  const int K = cv.K;
+  const int tid = threadIdx.x;
+  T* psi = scratch + (size_t)blockIdx.x * slot_elems;
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int grp = (NC == NO) ? 0 : (w % NO);
+    const int sa = (NC == NO) ? w : (w / NO);
+    const int spin = sa / n, atom = sa % n;
+    const long long s0 = cv.site_off[atom];
+    const int* lev = cv.level_end + (size_t)atom * (K + 1);
+    const int* satom = cv.site_atom + s0;
+    const long long* aoff = cv.adj_off + s0;
+    const T* E = onsite + (size_t)spin * n * NO;
+    if (tid <= K) s_lev[tid] = lev[tid];
+    if (tid == 0) {  // Psi_k at s_off[k], Psi-bar_k at s_off[K+1] + (s_off[k] - s_off[1])
+      long long o = 0;
+      for (int k = 0; k <= K; k++) {
+        s_off[k] = o;
+        o += (long long)lev[k] * NO * NC;
+      }
+      s_off[K + 1] = o;
+    }
+    for (int q = tid; q < NC * n_mom; q += blockDim.x) {
+      int c = q / n_mom, m = q % n_mom;
+      ws[c][m] = (T)wts[((size_t)sa * NO + grp + c) * n_mom + m];
+    }
+    __syncthreads();
+    T* P = psi;
+    T* Pb = psi + s_off[K + 1] - s_off[1];  // Pb + s_off[k] is Psi-bar_k (k >= 1)
+    // forward: all levels
+    for (int q = tid; q < NO * NC; q += blockDim.x) {
+      int r = q / NC, c = q % NC;
+      P[q] = (NC == NO) ? T(r == c ? 1 : 0) : T(r == grp ? 1 : 0);
+    }
+    __syncthreads();
+    for (int k = 1; k <= K; k++) {
+      const T* x = P + s_off[k - 1];
+      T* y = P + s_off[k];
+      for (int t = tid; t < s_lev[k]; t += blockDim.x) {
+        T acc[NO][NC];
+        gather_row<T, NO, NC>(cv, H, HS, E, satom, aoff, t, s_lev[k - 1], x, acc);
+#pragma unroll
+        for (int r = 0; r < NO; r++)
+#pragma unroll
+          for (int c = 0; c < NC; c++) y[(t * NO + r) * NC + c] = acc[r][c];
+      }
+      __syncthreads();
+    }
+    // Psi-bar_K = 2 w_2K Psi_K + w_2K-1 Psi_K-1
+    {
+      const T* PK = P + s_off[K];
+      const T* PK1 = P + s_off[K - 1];
+      T* B = Pb + s_off[K];
+      for (int q = tid; q < s_lev[K] * NO * NC; q += blockDim.x) {
+        int t = q / (NO * NC), c = q % NC;
+        T v = T(2) * ws[c][2 * K] * PK[q];
+        if (t < s_lev[K - 1]) v += ws[c][2 * K - 1] * PK1[q];
+        B[q] = v;
+      }
+    }
+    __syncthreads();
+    // Psi-bar_{k-1} = H^T Psi-bar_k (rows < |C_k-1|, cols < |C_k|) + dot-product terms
+    for (int k = K; k >= 2; k--) {
+      const T* xb = Pb + s_off[k];
+      T* yb = Pb + s_off[k - 1];
+      const T* Pk = P + s_off[k];
+      const T* Pk1 = P + s_off[k - 1];
+      const T* Pk2 = P + s_off[k - 2];
+      for (int t = tid; t < s_lev[k - 1]; t += blockDim.x) {
+        T acc[NO][NC];
+        gather_row<T, NO, NC>(cv, H, HS, E, satom, aoff, t, s_lev[k], xb, acc);
+#pragma unroll
+        for (int r = 0; r < NO; r++)
+#pragma unroll
+          for (int c = 0; c < NC; c++) {
+            int q = (t * NO + r) * NC + c;
+            T v = acc[r][c] + T(2) * ws[c][2 * k - 2] * Pk1[q] + ws[c][2 * k - 1] * Pk[q];
+            if (t < s_lev[k - 2]) v += ws[c][2 * k - 3] * Pk2[q];
+            yb[q] = v;
+          }
+      }
+      __syncthreads();
+    }
+    // bond and onsite cotangents: dU/dH_ts = sum_k Psi-bar_k[t] Psi_k-1[s]^T
+    for (int t = tid; t < s_lev[K]; t += blockDim.x) {
+      const int lt = site_level(s_lev, K, t);
+      const long long q1 = aoff[t + 1];
+      for (long long q = aoff[t]; q < q1; q++) {
+        int2 en = cv.adj[q];
+        const int s = en.x;
+        if (s >= s_lev[K - 1]) break;
+        const int ls = site_level(s_lev, K, s);
+        const int kmin = lt > ls + 1 ? lt : ls + 1;
+        T G[NO][NO];
+#pragma unroll
+        for (int b = 0; b < NO; b++)
+#pragma unroll
+          for (int g = 0; g < NO; g++) G[b][g] = T(0);
+        for (int k = kmin; k <= K; k++) {
+          const T* pb = Pb + s_off[k] + (size_t)t * NO * NC;
+          const T* ps = P + s_off[k - 1] + (size_t)s * NO * NC;
+#pragma unroll
+          for (int b = 0; b < NO; b++)
+#pragma unroll
+            for (int g = 0; g < NO; g++) {
+              T a = T(0);
+#pragma unroll
+              for (int c = 0; c < NC; c++) a += pb[b * NC + c] * ps[g * NC + c];
+              G[b][g] += a;
+            }
+        }
+        double* hb = Hbar + (size_t)en.y * HSu;
+        if constexpr (NO == 1) {
+          atomicAdd(hb, (double)G[0][0]);
+        } else {
+#pragma unroll
+          for (int b = 0; b < NO; b++)
+#pragma unroll
+            for (int g = b; g < NO; g++) {
+              double v = (double)G[b][g] + (b != g ? (double)G[g][b] : 0.0);
+              atomicAdd(hb + U5(b, g), v);
+            }
+        }
+      }
+      if (Ebar != nullptr) {
+        double eb[NO];
+#pragma unroll
+        for (int b = 0; b < NO; b++) eb[b] = 0.0;
+        for (int k = lt + 1; k <= K; k++) {
+          const T* pb = Pb + s_off[k] + (size_t)t * NO * NC;
+          const T* pt = P + s_off[k - 1] + (size_t)t * NO * NC;
+#pragma unroll
+          for (int b = 0; b < NO; b++) {
+            T a = T(0);
+#pragma unroll
+            for (int c = 0; c < NC; c++) a += pb[b * NC + c] * pt[b * NC + c];
+            eb[b] += (double)a;
+          }
+        }
+        if (lt + 1 <= K) {
+          double* ep = Ebar + ((size_t)spin * n + satom[t]) * NO;
+#pragma unroll
+          for (int b = 0; b < NO; b++) atomicAdd(ep + b, eb[b]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int NO, int NC>
+int run_forward(const MomentsArgs& a, cudaStream_t s) {
+  size_t smem = (size_t)2 * a.cap * NO * NC * sizeof(T);
+  if (smem > 227 * 1024) return -2;
+  auto fn = k_moments<T, NO, NC>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int grid = a.n * a.n_spin * (NO / NC);
+  fn<<<grid, MOM_THREADS, smem, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n, a.n_mom, a.cap, a.mu);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename T, int NO, int NC>
+int run_adjoint(const AdjointArgs& a, cudaStream_t s) {
+  int nwork = a.n * a.n_spin * (NO / NC);
+  int grid = nwork < a.slots ? nwork : a.slots;
+  k_moments_adj<T, NO, NC><<<grid, MOM_THREADS, 0, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n,
+                                                       a.n_mom, nwork, a.w, (T*)a.scratch, a.slot_elems,
+                                                       a.Hbar, a.HSu, a.Ebar);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+// Column grouping: all 5 starting orbitals in one CTA when both Psi levels
+// fit in shared memory, one CTA per starting orbital otherwise.
+int moments_columns(int norb, int cap, int fp64) {
+  if (norb == 1) return 1;
+  size_t bytes = (size_t)2 * cap * 5 * 5 * (fp64 ? 8 : 4);
+  return bytes <= 100 * 1024 ? 5 : 1;
+}
+
+int launch_moments(const MomentsArgs& a, int fp64, cudaStream_t s) {
+  int nc = moments_columns(a.norb, a.cap, fp64);
+  if (a.norb == 1) return fp64 ? run_forward<double, 1, 1>(a, s) : run_forward<float, 1, 1>(a, s);
+  if (nc == 5) return fp64 ? run_forward<double, 5, 5>(a, s) : run_forward<float, 5, 5>(a, s);
+  return fp64 ? run_forward<double, 5, 1>(a, s) : run_forward<float, 5, 1>(a, s);
+}
+
+int adjoint_columns(int norb) { return norb == 1 ? 1 : 5; }
+
+int launch_moments_adjoint(const AdjointArgs& a, int fp64, cudaStream_t s) {
+  if (a.norb == 1) return fp64 ? run_adjoint<double, 1, 1>(a, s) : run_adjoint<float, 1, 1>(a, s);
+  return fp64 ? run_adjoint<double, 5, 5>(a, s) : run_adjoint<float, 5, 5>(a, s);
+}

@@ -1,0 +1,269 @@
+// Short-range neighbour list (linked cells, "Initialisation" of the paper's
+// program flow) and the canonical undirected bond list with its two-centre
+// blocks (Eq. Hij, Eq. cutoff, Eq. Hij_rot).
+//
+// Output order is fixed so that the integer arrays are reproducible bit for
+// bit: each CSR row of atom i lists (j, sx, sy, sz) in ascending
+// lexicographic order; a pair is kept iff r2 < rc*rc with the FP64
+// arithmetic of bond_vector()/norm2_rn().
+#include "kernels.h"
+
+namespace bopk {
+
+// Fractional coordinates f = pos * inv(cell) (rows of cell = lattice vectors)
+// and the linked-cell index of every atom.
+__global__ void k_bin_atoms(int n, const double* __restrict__ pos, Geometry g, int* __restrict__ cell_of,
+                            int* __restrict__ cell_count) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c3[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    double f = pos[3 * i] * g.inv[0 * 3 + a] + pos[3 * i + 1] * g.inv[1 * 3 + a] + pos[3 * i + 2] * g.inv[2 * 3 + a];
+    int c = (int)floor(f * g.nc[a]);
+    c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
+    c3[a] = c;
+  }
+  int c = (c3[0] * g.nc[1] + c3[1]) * g.nc[2] + c3[2];
+  cell_of[i] = c;
+  atomicAdd(&cell_count[c], 1);
+}
+
+__global__ void k_fill_cells(int n, const int* __restrict__ cell_of, const int* __restrict__ cell_start,
+                             int* __restrict__ cell_fill, int* __restrict__ cell_atoms) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = cell_of[i];
+  int slot = atomicAdd(&cell_fill[c], 1);
+  cell_atoms[cell_start[c] + slot] = i;
+}
+
+// Candidate ranges along one axis: with nc >= 3 the three adjacent cells
+// (wrapped, image = floor division); with fewer cells, every cell with
+// every image in [-nimg, nimg].
+struct AxisIter {
+  int count;
+  __device__ void get(const Geometry& g, int a, int c, int q, int* cell, int* img) const {
+    if (g.nc[a] >= 3) {
+      int cc = c + q - 1;
+      int im = 0;
+      if (cc < 0) { cc += g.nc[a]; im = -1; }
+      if (cc >= g.nc[a]) { cc -= g.nc[a]; im = 1; }
+      *cell = cc;
+      *img = im;
+    } else {
+      *cell = q % g.nc[a];
+      *img = q / g.nc[a] - g.nimg[a];
+    }
+  }
+};
+
+__device__ __forceinline__ int axis_count(const Geometry& g, int a) {
+  return g.nc[a] >= 3 ? 3 : g.nc[a] * (2 * g.nimg[a] + 1);
+}
+
+__device__ __forceinline__ bool axis_valid(const Geometry& g, int a, int c, int q) {
+  // non-periodic axes: no wrap, no images
+  if (g.pbc[a]) return true;
+  if (g.nc[a] >= 3) {
+    int cc = c + q - 1;
+    return cc >= 0 && cc < g.nc[a];
+  }
+  return q / g.nc[a] - g.nimg[a] == 0;
+}
+
+__device__ __forceinline__ uint64_t nbr_key(int j, int sx, int sy, int sz) {
+  return ((uint64_t)(uint32_t)j << 24) | ((uint64_t)(sx + 128) << 16) | ((uint64_t)(sy + 128) << 8) |
+         (uint64_t)(sz + 128);
+}
+
+// One thread per atom.  mode 0: count neighbours; mode 1: write the sorted row.
+template <int MODE>
+__global__ void k_neighbors(int n, const double* __restrict__ pos, Geometry g, const int* __restrict__ cell_of,
+                            const int* __restrict__ cell_start, const int* __restrict__ cell_atoms,
+                            int* __restrict__ deg, const long long* __restrict__ row_ptr, int* __restrict__ col,
+                            signed char* __restrict__ img, unsigned* __restrict__ status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double rc2 = g.rc * g.rc;
+  double pi[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+  int ci = cell_of[i];
+  int c3[3] = {ci / (g.nc[1] * g.nc[2]), (ci / g.nc[2]) % g.nc[1], ci % g.nc[2]};
+  uint64_t keys[BOP_MAX_DEG];
+  int cnt = 0;
+  int n0 = axis_count(g, 0), n1 = axis_count(g, 1), n2 = axis_count(g, 2);
+  for (int q0 = 0; q0 < n0; q0++) {
+    if (!axis_valid(g, 0, c3[0], q0)) continue;
+    for (int q1 = 0; q1 < n1; q1++) {
+      if (!axis_valid(g, 1, c3[1], q1)) continue;
+      for (int q2 = 0; q2 < n2; q2++) {
+        if (!axis_valid(g, 2, c3[2], q2)) continue;
+        int cx, cy, cz, sx, sy, sz;
+        AxisIter it;
+        it.get(g, 0, c3[0], q0, &cx, &sx);
+        it.get(g, 1, c3[1], q1, &cy, &sy);
+        it.get(g, 2, c3[2], q2, &cz, &sz);
+        int cc = (cx * g.nc[1] + cy) * g.nc[2] + cz;
+        for (int p = cell_start[cc]; p < cell_start[cc + 1]; p++) {
+          int j = cell_atoms[p];
+          if (j == i && sx == 0 && sy == 0 && sz == 0) continue;
+          double d[3];
+          bond_vector(pi, pos + 3 * j, g.cell, sx, sy, sz, d);
+          if (!(norm2_rn(d) < rc2)) continue;
+          if (cnt < BOP_MAX_DEG) keys[cnt] = nbr_key(j, sx, sy, sz);
+          cnt++;
+        }
+      }
+    }
+  }
+  if (MODE == 0) {
+    deg[i] = cnt;
+    if (cnt > BOP_MAX_DEG) raise_error(status, BOP_DEV_ERR_DEGREE);
+    return;
+  }
+  if (cnt > BOP_MAX_DEG) return;
+  for (int a = 1; a < cnt; a++) {  // insertion sort of the row
+    uint64_t k = keys[a];
+    int b = a - 1;
+    while (b >= 0 && keys[b] > k) {
+      keys[b + 1] = keys[b];
+      b--;
+    }
+    keys[b + 1] = k;
+  }
+  long long e0 = row_ptr[i];
+  for (int a = 0; a < cnt; a++) {
+    uint64_t k = keys[a];
+    col[e0 + a] = (int)(k >> 24);
+    img[3 * (e0 + a)] = (signed char)((int)((k >> 16) & 0xff) - 128);
+    img[3 * (e0 + a) + 1] = (signed char)((int)((k >> 8) & 0xff) - 128);
+    img[3 * (e0 + a) + 2] = (signed char)((int)(k & 0xff) - 128);
+  }
+}
+
+// Canonical orientation of a directed edge i->(j,S): i < j, or i == j and
+// S > 0 lexicographically.
+__device__ __forceinline__ bool canonical(int i, int j, const signed char* s) {
+  if (i != j) return i < j;
+  if (s[0] != 0) return s[0] > 0;
+  if (s[1] != 0) return s[1] > 0;
+  return s[2] > 0;
+}
+
+__global__ void k_edge_flags(int n, const long long* __restrict__ row_ptr, const int* __restrict__ col,
+                             const signed char* __restrict__ img, int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (long long e = row_ptr[i]; e < row_ptr[i + 1]; e++) flag[e] = canonical(i, col[e], img + 3 * e) ? 1 : 0;
+}
+
+// bond_of_edge for every directed edge (the reverse edge of a
+// non-canonical one is found by binary search in row j), and the bond's
+// end atoms and image.
+__global__ void k_bonds(int n, const long long* __restrict__ row_ptr, const int* __restrict__ col,
+                        const signed char* __restrict__ img, const int* __restrict__ flag,
+                        const int* __restrict__ bond_scan, int* __restrict__ bond_of_edge,
+                        int* __restrict__ bond_atoms, signed char* __restrict__ bond_img,
+                        unsigned* __restrict__ status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (long long e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
+    int j = col[e];
+    const signed char* s = img + 3 * e;
+    if (flag[e]) {
+      int b = bond_scan[e];
+      bond_of_edge[e] = b;
+      bond_atoms[2 * b] = i;
+      bond_atoms[2 * b + 1] = j;
+      bond_img[3 * b] = s[0];
+      bond_img[3 * b + 1] = s[1];
+      bond_img[3 * b + 2] = s[2];
+    } else {
+      uint64_t want = nbr_key(i, -s[0], -s[1], -s[2]);
+      long long lo = row_ptr[j], hi = row_ptr[j + 1] - 1, found = -1;
+      while (lo <= hi) {
+        long long mid = (lo + hi) >> 1;
+        const signed char* t = img + 3 * mid;
+        uint64_t k = nbr_key(col[mid], t[0], t[1], t[2]);
+        if (k == want) { found = mid; break; }
+        if (k < want) lo = mid + 1; else hi = mid - 1;
+      }
+      if (found < 0) {
+        raise_error(status, BOP_DEV_ERR_REVERSE);
+        bond_of_edge[e] = 0;
+      } else {
+        bond_of_edge[e] = bond_scan[found];
+      }
+    }
+  }
+}
+
+// Bond vectors and unique block elements of every canonical bond.
+__global__ void k_bond_blocks(int nb, const double* __restrict__ pos, Geometry g, BondModel m,
+                              const int* __restrict__ bond_atoms, const signed char* __restrict__ bond_img,
+                              double* __restrict__ bond_d, double* __restrict__ H64, float* __restrict__ H32,
+                              int HS) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  int i = bond_atoms[2 * b], j = bond_atoms[2 * b + 1];
+  const signed char* s = bond_img + 3 * b;
+  double d[3];
+  bond_vector(pos + 3 * i, pos + 3 * j, g.cell, s[0], s[1], s[2], d);
+  bond_d[3 * b] = d[0];
+  bond_d[3 * b + 1] = d[1];
+  bond_d[3 * b + 2] = d[2];
+  double u[15];
+  sk_unique<double>(m, d, u);
+  int nu = m.norb == 1 ? 1 : 15;
+  for (int q = 0; q < HS; q++) {
+    double v = q < nu ? u[q] : 0.0;
+    H64[(size_t)b * HS + q] = v;
+    H32[(size_t)b * HS + q] = (float)v;
+  }
+}
+
+// Largest / smallest fractional coordinate along each axis (validation that
+// all atoms lie inside the cell).
+__global__ void k_frac_range(int n, const double* __restrict__ pos, Geometry g, double* __restrict__ out) {
+  __shared__ double smin[3][256], smax[3][256];
+  double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int a = 0; a < 3; a++) {
+      double f = pos[3 * i] * g.inv[a] + pos[3 * i + 1] * g.inv[3 + a] + pos[3 * i + 2] * g.inv[6 + a];
+      mn[a] = fmin(mn[a], f);
+      mx[a] = fmax(mx[a], f);
+    }
+  }
+  for (int a = 0; a < 3; a++) {
+    smin[a][threadIdx.x] = mn[a];
+    smax[a][threadIdx.x] = mx[a];
+  }
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int a = 0; a < 3; a++) {
+        smin[a][threadIdx.x] = fmin(smin[a][threadIdx.x], smin[a][threadIdx.x + w]);
+        smax[a][threadIdx.x] = fmax(smax[a][threadIdx.x], smax[a][threadIdx.x + w]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int a = 0; a < 3; a++) {
+      out[6 * blockIdx.x + a] = smin[a][0];
+      out[6 * blockIdx.x + 3 + a] = smax[a][0];
+    }
+}
+
+}  // namespace bopk
+
+void launch_neighbors(int mode, int n, const double* pos, Geometry g, const int* cell_of, const int* cell_start,
+                      const int* cell_atoms, int* deg, const long long* row_ptr, int* col, signed char* img,
+                      unsigned* status, cudaStream_t s) {
+  const int TB = 256, gb = (n + TB - 1) / TB;
+  if (mode == 0)
+    bopk::k_neighbors<0><<<gb, TB, 0, s>>>(n, pos, g, cell_of, cell_start, cell_atoms, deg, row_ptr, col, img,
+                                           status);
+  else
+    bopk::k_neighbors<1><<<gb, TB, 0, s>>>(n, pos, g, cell_of, cell_start, cell_atoms, deg, row_ptr, col, img,
+                                           status);
+}
