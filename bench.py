@@ -1,0 +1,317 @@
+#!/usr/bin/env python3
+"""Benchmark of the analytic-BOP hot path: atoms/s for one energy + forces
+evaluation (neighbour list, blocks, clusters, the self-consistent moments /
+recursion / terminator / Fermi-level loop, bond energy, weights, reverse
+sweep, forces and virial) on the 2,000-atom d-valent bcc workload (10x10x10
+conventional cells, canonical d model, local charge neutrality, 9 moments).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload d2000] [--precision fp32|fp64]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun), every rank evaluates
+its own copy of the workload (independent problems, no collective on the
+data path) and the line reports the whole-job throughput ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atoms/s for E+F at n moments"
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 x max SM clock
+PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # SMs x FP64 FMA units x 2 x max SM clock
+L2_FLUSH_BYTES = 512 << 20
+FP32_SCF_TOL = 1e-5  # electrons: SCF tolerance with FP32 products (FP64 mode keeps 1e-9)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="d2000")
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ algorithmic work
+def chain_level_updates(n_exp: int) -> int:
+    """Level updates of the zeta chain restricted to the levels that reach
+    sigma_0 .. sigma_{n_exp} (the dependency cone)."""
+    return sum(min(m + 1, n_exp - m - 1) + 1 for m in range(n_exp))
+
+
+def algorithmic_flops(family: str, w, stats: dict, prof: dict, n_spin: int) -> float | None:
+    """FLOPs one launch region of a family must do (per region)."""
+    norb, n_mom, n_exp = w.model.norb, w.run.n_mom, w.run.n_exp
+    M = n_spin * w.n_atoms * norb
+    if family == "moments":
+        # block products Psi_k(t) += B_ts Psi_k-1(s) over the cluster pairs,
+        # norb x norb x norb multiply-adds each (all starting orbitals)
+        return 2.0 * stats["moment_products"] * n_spin * norb ** 3
+    if family == "expand":
+        return 8.0 * M * chain_level_updates(n_exp)
+    if family == "fermi":
+        rounds = max(1, stats["bisection_rounds"])
+        return rounds * M * (n_exp + 2) * 4.0
+    return None
+
+
+# ------------------------------------------------------------ our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1803_07491_gb300 import bop, build, inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    w = I.workload(args.workload)
+    if args.precision == "fp32" and w.run.scf != "none":
+        # FP32 moments put a floor of a few 1e-6 electrons under N_i
+        w = I.with_run(w, scf_tol=FP32_SCF_TOL)
+    ctx = bop.Context(w.model, w.run, args.precision)
+    pos = torch.tensor(w.pos, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.build(pos, w.cell, w.pbc)
+        ctx.energy()
+        return ctx.forces()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stats = bop.bop_get_stats(ctx.h)
+    bop.bop_set_profiling(ctx.h, True)
+    bop.bop_reset_profile(ctx.h)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in times)
+    prof = bop.bop_get_profile(ctx.h)
+    bop.bop_set_profiling(ctx.h, False)
+    stats = bop.bop_get_stats(ctx.h)
+    t_max = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    t_ms = float(t_max.item())
+    atoms = w.n_atoms * args.steps * world
+    value = atoms / (t_ms / 1e3)
+    launches = sum(v["launches"] for v in prof.values())
+
+    # end to end through the C ABI with host buffers (pinned)
+    pos_h = torch.tensor(w.pos, dtype=torch.float64).pin_memory()
+    e_h = torch.empty(w.n_atoms, dtype=torch.float64).pin_memory()
+    f_h = torch.empty((w.n_atoms, 3), dtype=torch.float64).pin_memory()
+    v_h = torch.empty((3, 3), dtype=torch.float64).pin_memory()
+    bop.bop_evaluate_host(ctx.h, pos_h, w.cell, w.pbc, e_h, f_h, v_h)
+    torch.cuda.synchronize()
+    te = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bop.bop_evaluate_host(ctx.h, pos_h, w.cell, w.pbc, e_h, f_h, v_h)
+        te.append(time.perf_counter() - t0)
+    t_e2e = torch.tensor([sum(te)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_value = atoms / float(t_e2e.item())
+
+    # roofline of the dominant kernel family (live CUDA-event times)
+    fam = max(prof, key=lambda k: prof[k]["ms"])
+    flops = algorithmic_flops(fam, w, {**stats, "moment_products": stats_products(ctx, bop)}, prof, w.run.n_spin)
+    per_region_ms = prof[fam]["ms"] / max(1, prof[fam]["regions"])
+    fp64_family = fam in ("expand", "fermi", "weights", "orbital_NU", "ef_response") or args.precision == "fp64"
+    peak = PEAK_FP64_TFLOPS if fp64_family else PEAK_FP32_TFLOPS
+    roof = None
+    if flops is not None:
+        achieved = flops / (per_region_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": fam, "achieved": round(achieved, 4), "peak": round(peak, 3),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": profile_traffic(fam),
+                "peak_source": "derived: SMs x lanes x 2 x max SM clock (FP64 for the scalar stages)",
+                "region_ms": round(per_region_ms, 4)}
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "atoms/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "fp32 products + fp64 scalar stages" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded jittered bcc, random-free model parameters)",
+        "config": {"workload": args.workload, "atoms": w.n_atoms, "orbitals": w.model.norb,
+                   "n_mom": w.run.n_mom, "n_exp": w.run.n_exp, "scf": w.run.scf,
+                   "scf_iterations": stats["scf_iterations"], "scf_tol": w.run.scf_tol,
+                   "bisection_rounds": stats["bisection_rounds"],
+                   "precision": args.precision, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "clocks": clocks, "gpu_launches": launches,
+        "e2e": {"value": round(e2e_value, 2), "unit": "atoms/s",
+                "h2d_bytes_per_step": w.n_atoms * 3 * 8,
+                "d2h_bytes_per_step": w.n_atoms * 8 + w.n_atoms * 3 * 8 + 9 * 8},
+        "roofline": roof,
+        "kernels": {k: {"ms_per_step": round(v["ms"] / args.steps, 4),
+                        "launches_per_step": v["launches"] / args.steps} for k, v in prof.items() if v["launches"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def stats_products(ctx, bop) -> int:
+    st = bop.bop_get_stats(ctx.h)
+    return st.get("moment_products", 0)
+
+
+def profile_traffic(family: str):
+    """DRAM bytes per launch region of the family from the committed ncu
+    summary (profiles/traffic.json), or None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        return json.load(open(p)).get(family)
+    except (ValueError, OSError):
+        return None
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample(n_cells: int):
+    """The oracle's energy + forces on an n x n x n x 2 cell of the same
+    model and settings (jitter 0.05 A, seed 2): a bounded sample of the
+    workload; the per-atom work of the method does not depend on the cell
+    size (clusters are built with periodic images)."""
+    from oracle import bop as ob
+    from paper_1803_07491_gb300 import inputs as I
+    ob.build()
+    pos, cell = I.bcc_jittered(n_cells, n_cells, n_cells, 0.05, 2)
+    r = I.workload("d2000").run
+    p = I.MODEL_D
+    t0 = time.perf_counter()
+    ob.evaluate(ob.Model(p.norb, tuple(p.b0), p.r0, p.lam, p.rc, p.dc, p.onsite0),
+                ob.Settings(n_e=r.n_e, n_mom=r.n_mom, n_exp=r.n_exp, scf=r.scf, eta=r.eta, scf_tol=r.scf_tol,
+                            scf_max_it=r.scf_max_it), pos, cell, (1, 1, 1))
+    return len(pos), time.perf_counter() - t0
+
+
+def cpu_baseline(workload: str):
+    n, t = oracle_sample(3)
+    return {"value": round(n / t, 3), "unit": "atoms/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle E+F (LCN SCF, 9 moments, canonical d) of a {n}-atom 3x3x3x2 jittered bcc "
+                      f"cell of the {workload} model, {t:.1f} s on one host core"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(2)
+    tot_n, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        n, t = oracle_sample(2)
+        tot_n += n
+        tot_t += t
+    value = tot_n / tot_t
+    sample = ("oracle E+F (LCN SCF, 9 moments, canonical d) of a 16-atom 2x2x2x2 jittered bcc cell of the "
+              f"{args.workload} model per step, one host core")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "atoms/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded jittered bcc)", "config": {"workload": args.workload, "sample": "2x2x2x2"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "atoms/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "atoms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -110,6 +110,8 @@ typedef struct {
   double e_total;
   int forces_scf_response;/* 1 if forces include the SCF response (scf == NONE) */
   int pad;
+  long long moment_products; /* block products Psi_k(t) += H_ts Psi_k-1(s) of one
+                                moments pass, summed over atoms (one spin) */
 } bop_stats;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -208,6 +210,25 @@ int bop_get_orbital_state(bop_ctx* ctx, double* mu, double* N, double* U, double
 int bop_evaluate_host(bop_ctx* ctx, int n, const double* pos_host, const double* cell_host,
                       const int* pbc_host, double* e_atom_host, double* forces_host, double* virial_host,
                       double* e_total_host, bop_stats* stats_host, bop_stream stream);
+
+/* Per-kernel-family timing, for measurement.  While profiling is on, every
+ * launch region of the context is bracketed by two CUDA events on the
+ * stream it is launched on; launch counts are kept whether or not
+ * profiling is on.  Families: "neighbours", "cluster", "onsite", "moments",
+ * "expand", "fermi", "orbital_NU", "scf", "energy", "ef_response",
+ * "weights", "adjoint", "forces".  bop_get_profile synchronises on the
+ * recorded events; name points to a static string. */
+typedef struct {
+  const char* name;
+  long long launches; /* kernels launched (all calls since the last reset) */
+  long long regions;  /* event-timed launch regions */
+  double ms;          /* summed device time of the timed regions */
+} bop_kernel_time;
+
+int bop_set_profiling(bop_ctx* ctx, int on);
+int bop_reset_profile(bop_ctx* ctx);
+/* Writes up to max entries, *n_out = number of families. */
+int bop_get_profile(bop_ctx* ctx, bop_kernel_time* out_host, int max, int* n_out);
 
 #ifdef __cplusplus
 }

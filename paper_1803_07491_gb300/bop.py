@@ -43,10 +43,16 @@ class bop_stats(ctypes.Structure):
                 ("max_cluster", ctypes.c_int), ("scf_iterations", ctypes.c_int), ("scf_converged", ctypes.c_int),
                 ("bisection_rounds", ctypes.c_int), ("scf_residual", ctypes.c_double),
                 ("e_fermi", ctypes.c_double), ("e_total", ctypes.c_double),
-                ("forces_scf_response", ctypes.c_int), ("pad", ctypes.c_int)]
+                ("forces_scf_response", ctypes.c_int), ("pad", ctypes.c_int),
+                ("moment_products", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class bop_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong), ("regions", ctypes.c_longlong),
+                ("ms", ctypes.c_double)]
 
 
 _LIB = None
@@ -80,6 +86,10 @@ def lib(path: str | None = None):
         "bop_get_orbital_state": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
         "bop_evaluate_host": ([_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                ctypes.POINTER(bop_stats), _VP], ctypes.c_int),
+        "bop_set_profiling": ([_VP, ctypes.c_int], ctypes.c_int),
+        "bop_reset_profile": ([_VP], ctypes.c_int),
+        "bop_get_profile": ([_VP, ctypes.POINTER(bop_kernel_time), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+                            ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -242,6 +252,23 @@ def bop_evaluate_host(ctx, pos_host: torch.Tensor, cell, pbc, e_atom_host=None, 
                                         _ptr(e_atom_host), _ptr(forces_host), _ptr(virial_host),
                                         ctypes.cast(ctypes.pointer(et), _VP), ctypes.byref(s), _stream(stream)))
     return et.value, s.as_dict()
+
+
+def bop_set_profiling(ctx, on: bool):
+    _check(ctx, lib().bop_set_profiling(ctx, 1 if on else 0))
+
+
+def bop_reset_profile(ctx):
+    _check(ctx, lib().bop_reset_profile(ctx))
+
+
+def bop_get_profile(ctx) -> dict:
+    """{family: {"launches", "regions", "ms"}} of the timed launch regions."""
+    arr = (bop_kernel_time * 32)()
+    n = ctypes.c_int(0)
+    _check(ctx, lib().bop_get_profile(ctx, arr, 32, ctypes.byref(n)))
+    return {arr[i].name.decode(): {"launches": arr[i].launches, "regions": arr[i].regions, "ms": arr[i].ms}
+            for i in range(n.value)}
 
 
 # ------------------------------------------------------------ convenience

@@ -18,6 +18,8 @@
 int moments_columns(int norb, int cap, int fp64);
 int adjoint_columns(int norb);
 
+constexpr int FERMI_ROUNDS = 100;
+
 namespace {
 
 struct DBuf {
@@ -26,6 +28,22 @@ struct DBuf {
 };
 
 }  // namespace
+
+enum ProfKind {
+  PK_NBR = 0, PK_CLUSTER, PK_ONSITE, PK_MOMENTS, PK_EXPAND, PK_FERMI, PK_NU, PK_SCF, PK_ENERGY, PK_EFRESP,
+  PK_WEIGHTS, PK_ADJOINT, PK_FORCES, PK_N
+};
+static const char* const PK_NAMES[PK_N] = {"neighbours", "cluster", "onsite", "moments", "expand", "fermi",
+                                          "orbital_NU", "scf", "energy", "ef_response", "weights", "adjoint",
+                                          "forces"};
+
+struct Prof {
+  bool on = false;
+  long long launches[PK_N] = {0};
+  std::vector<cudaEvent_t> pool;  // events in recording order: pairs (begin, end)
+  std::vector<int> kind;          // one entry per pair
+  size_t used = 0;                // events used in the pool
+};
 
 struct bop_ctx {
   bop_model m;
@@ -49,8 +67,10 @@ struct bop_ctx {
   DBuf w, zscr, adjscr, Hbar, Ebar;
   DBuf status;
   DBuf cub_tmp;
+  DBuf nprod;
   int cl_hcap = 0, cl_maxs = 0, cl_slots = 0;
   bop_stats st;
+  Prof prof;
   char err[512];
 };
 
@@ -78,6 +98,36 @@ int fail(bop_ctx* c, int code, const char* fmt, ...) {
     int s_ = (expr);         \
     if (s_ != BOP_OK) return s_; \
   } while (0)
+
+cudaEvent_t prof_event(bop_ctx* c) {
+  if (c->prof.used == c->prof.pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->prof.pool.push_back(e);
+  }
+  return c->prof.pool[c->prof.used++];
+}
+
+// Brackets one launch region of `nk` kernels of family k on stream s.
+struct Region {
+  bop_ctx* c;
+  int k;
+  cudaStream_t s;
+  Region(bop_ctx* c_, int k_, int nk, cudaStream_t s_) : c(c_), k(k_), s(s_) {
+    c->prof.launches[k] += nk;
+    if (c->prof.on) {
+      cudaEvent_t e = prof_event(c);
+      if (e) cudaEventRecord(e, s);
+      c->prof.kind.push_back(k);
+    }
+  }
+  ~Region() {
+    if (c->prof.on) {
+      cudaEvent_t e = prof_event(c);
+      if (e) cudaEventRecord(e, s);
+    }
+  }
+};
 
 int ensure(bop_ctx* c, DBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -207,9 +257,12 @@ int build_clusters(bop_ctx* c, cudaStream_t s) {
     out.atom_nsite = P<int>(c->atom_nsite);
     out.atom_nadj = P<int>(c->atom_nadj);
     out.max_level = P<int>(c->max_level);
+    {
+    Region R0(c, PK_CLUSTER, 1, s);
     if (launch_cluster(0, n, K, P<long long>(c->row_ptr), P<int>(c->col), P<signed char>(c->img),
                        P<int>(c->bond_of_edge), sc, out, grid, P<unsigned>(c->status), s))
       return fail(c, BOP_ERR_CUDA, "cluster pass 0 launch failed");
+    }
     unsigned h = 0;
     CK(cudaMemcpyAsync(&h, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -240,9 +293,15 @@ int build_clusters(bop_ctx* c, cudaStream_t s) {
     out.site_img = P<signed char>(c->site_img);
     out.adj_off = P<long long>(c->adj_off);
     out.adj = P<int2>(c->adj);
+    CKS(ensure(c, c->nprod, sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(c->nprod.p, 0, sizeof(unsigned long long), s));
+    out.n_products = P<unsigned long long>(c->nprod);
+    {
+    Region R1(c, PK_CLUSTER, 1, s);
     if (launch_cluster(1, n, K, P<long long>(c->row_ptr), P<int>(c->col), P<signed char>(c->img),
                        P<int>(c->bond_of_edge), sc, out, grid, P<unsigned>(c->status), s))
       return fail(c, BOP_ERR_CUDA, "cluster pass 1 launch failed");
+    }
     CK(cudaMemcpyAsync(P<long long>(c->adj_off) + c->nsite, P<long long>(c->adj_base) + n, sizeof(long long),
                        cudaMemcpyDeviceToDevice, s));
     return check_status(c, s);
@@ -290,6 +349,7 @@ int run_moments(bop_ctx* c, const double* onsite_dev, double* mu, cudaStream_t s
   a.n_mom = c->n_mom;
   a.cap = c->maxlev[c->K - 1] > 0 ? c->maxlev[c->K - 1] : 1;
   a.mu = mu;
+  Region R(c, PK_MOMENTS, 1, s);
   int r = launch_moments(a, c->fp64, s);
   if (r == -2) return fail(c, BOP_ERR_OVERFLOW, "cluster level too large for shared memory");
   if (r) return fail(c, BOP_ERR_CUDA, "moments launch: %s", cudaGetErrorString(cudaGetLastError()));
@@ -311,6 +371,7 @@ int run_scalar(bop_ctx* c, int M, const double* mu, cudaStream_t s) {
   a.D = P<double>(c->D);
   a.g = P<double>(c->gjack);
   a.status = P<unsigned>(c->status);
+  Region R(c, PK_EXPAND, 1, s);
   if (launch_expand(a, s)) return fail(c, BOP_ERR_CUDA, "expand launch failed");
   return BOP_OK;
 }
@@ -318,10 +379,14 @@ int run_scalar(bop_ctx* c, int M, const double* mu, cudaStream_t s) {
 int fermi_and_NU(bop_ctx* c, cudaStream_t s) {
   const int M = c->S * c->n * c->norb;
   const double target = c->m.n_e * c->n;
-  if (launch_fermi(M, P<double>(c->D), P<double>(c->gsig), P<double>(c->a_inf), P<double>(c->b_inf), c->n_exp,
+  {
+    Region R(c, PK_FERMI, 1 + FERMI_ROUNDS, s);
+    if (launch_fermi(M, P<double>(c->D), P<double>(c->gsig), P<double>(c->a_inf), P<double>(c->b_inf), c->n_exp,
                    c->sfac, target, P<FermiState>(c->fstate), P<double>(c->partials), P<unsigned>(c->counter),
-                   100, 1e-13, s))
-    return fail(c, BOP_ERR_CUDA, "fermi launch failed");
+                     FERMI_ROUNDS, 1e-13, s))
+      return fail(c, BOP_ERR_CUDA, "fermi launch failed");
+  }
+  Region R(c, PK_NU, 1, s);
   if (launch_orbital_NU(M, c->n_exp, P<double>(c->gsig), P<double>(c->a_inf), P<double>(c->b_inf),
                         P<double>(c->onsite), P<FermiState>(c->fstate), P<double>(c->N), P<double>(c->U),
                         P<double>(c->dos), s))
@@ -394,9 +459,10 @@ int bop_destroy(bop_ctx* c) {
                   &c->onsite32, &c->delta, &c->mval, &c->delta_new, &c->m_new, &c->mu, &c->a, &c->b, &c->nlev,
                   &c->a_inf, &c->b_inf, &c->gsig, &c->D, &c->gjack, &c->N, &c->U, &c->dos, &c->fstate,
                   &c->partials, &c->counter, &c->result, &c->e_total, &c->lam, &c->e_atom, &c->w, &c->zscr,
-                  &c->adjscr, &c->Hbar, &c->Ebar, &c->status, &c->cub_tmp};
+                  &c->adjscr, &c->Hbar, &c->Ebar, &c->status, &c->cub_tmp, &c->nprod};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
+  for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   delete c;
   return BOP_OK;
 }
@@ -430,6 +496,8 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
   CKS(ensure(c, c->row_ptr, sizeof(long long) * (n + 1)));
   CKS(ensure(c, c->frac, sizeof(double) * 6 * 64));
   const int TB = 256, gb = (n + TB - 1) / TB;
+  {
+  Region Rn(c, PK_NBR, 5, s);
   bopk::k_frac_range<<<64, 256, 0, s>>>(n, P<double>(c->pos), g, P<double>(c->frac));
   CK(cudaMemsetAsync(c->cell_count.p, 0, sizeof(int) * (ncell + 1), s));
   CK(cudaMemsetAsync(c->cell_fill.p, 0, sizeof(int) * ncell, s));
@@ -442,6 +510,7 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
                    P<int>(c->deg), nullptr, nullptr, nullptr, P<unsigned>(c->status), s);
   CK(cudaGetLastError());
   CKS(exclusive_scan(c, P<int>(c->deg), P<long long>(c->row_ptr), n + 1, s));
+  }
   double fr[6 * 64];
   long long E = 0;
   CK(cudaMemcpyAsync(fr, c->frac.p, sizeof(double) * 6 * 64, cudaMemcpyDeviceToHost, s));
@@ -470,6 +539,8 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
   CKS(ensure(c, c->bond_d, sizeof(double) * 3 * nb));
   CKS(ensure(c, c->H64, sizeof(double) * c->HS * nb));
   CKS(ensure(c, c->H32, sizeof(float) * c->HS * nb));
+  {
+  Region Rn2(c, PK_NBR, E > 0 ? 4 : 2, s);
   launch_neighbors(1, n, P<double>(c->pos), g, P<int>(c->cell_of), P<int>(c->cell_start), P<int>(c->cell_atoms),
                    nullptr, P<long long>(c->row_ptr), P<int>(c->col), P<signed char>(c->img),
                    P<unsigned>(c->status), s);
@@ -484,6 +555,7 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
         (int)nb, P<double>(c->pos), g, c->bm, P<int>(c->bond_atoms), P<signed char>(c->bond_img),
         P<double>(c->bond_d), P<double>(c->H64), P<float>(c->H32), c->HS);
   }
+  }
   CK(cudaGetLastError());
   CKS(check_status(c, s));
   CKS(build_clusters(c, s));
@@ -497,6 +569,11 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
   c->st.n_sites = c->nsite;
   c->st.n_adj = c->nadj;
   c->st.max_cluster = c->maxlev[c->K];
+  {
+    unsigned long long np = 0;
+    CK(cudaMemcpy(&np, c->nprod.p, sizeof(np), cudaMemcpyDeviceToHost));
+    c->st.moment_products = (long long)np;
+  }
   return BOP_OK;
 }
 
@@ -546,8 +623,10 @@ int bop_moments(bop_ctx* c, const double* onsite, double* mu, bop_stream stream)
   const size_t M = (size_t)c->S * c->n * c->norb;
   if (onsite) {
     CK(cudaMemcpyAsync(c->onsite.p, onsite, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+    Region R(c, PK_ONSITE, 1, s);
     launch_to_float(P<double>(c->onsite), P<float>(c->onsite32), M, s);
   } else {
+    Region R(c, PK_ONSITE, 1, s);
     launch_build_onsite(c->n, c->norb, c->S, c->m.onsite0, 0.0, nullptr, nullptr, P<double>(c->onsite),
                         P<float>(c->onsite32), s);
   }
@@ -612,8 +691,11 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   int it = 0, converged = c->m.scf == BOP_SCF_NONE;
   double res[4] = {0, 0, 0, 0};
   for (;;) {
-    launch_build_onsite(n, c->norb, c->S, c->m.onsite0, c->m.stoner_I, P<double>(c->delta),
-                        stoner ? P<double>(c->mval) : nullptr, P<double>(c->onsite), P<float>(c->onsite32), s);
+    {
+      Region R(c, PK_ONSITE, 1, s);
+      launch_build_onsite(n, c->norb, c->S, c->m.onsite0, c->m.stoner_I, P<double>(c->delta),
+                          stoner ? P<double>(c->mval) : nullptr, P<double>(c->onsite), P<float>(c->onsite32), s);
+    }
     CKS(run_moments(c, P<double>(c->onsite), P<double>(c->mu), s));
     CKS(run_scalar(c, M, P<double>(c->mu), s));
     CKS(fermi_and_NU(c, s));
@@ -642,7 +724,10 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
     a.red = P<double>(c->partials);
     a.counter = P<unsigned>(c->counter);
     a.result = P<double>(c->result);
-    if (launch_scf_update(a, s)) return fail(c, BOP_ERR_CUDA, "scf update launch failed");
+    {
+      Region R(c, PK_SCF, 2, s);
+      if (launch_scf_update(a, s)) return fail(c, BOP_ERR_CUDA, "scf update launch failed");
+    }
     CK(cudaMemcpyAsync(res, c->result.p, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
     CKS(check_status(c, s));
     if (res[2] != 0.0) {
@@ -651,10 +736,13 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
     }
     it++;
   }
+  {
+  Region Re(c, PK_ENERGY, 1, s);
   if (launch_energy(n, c->norb, c->S, c->sfac, c->m.stoner_I, P<double>(c->U), stoner ? P<double>(c->mval) : nullptr,
                     e_atom ? e_atom : P<double>(c->e_atom), P<double>(c->partials), P<unsigned>(c->counter),
                     P<double>(c->e_total), s))
     return fail(c, BOP_ERR_CUDA, "energy launch failed");
+  }
   if (delta_io) CK(cudaMemcpyAsync(delta_io, c->delta.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   if (m_io && stoner) CK(cudaMemcpyAsync(m_io, c->mval.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   FermiState fs;
@@ -685,10 +773,13 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   CKS(ensure(c, c->Hbar, sizeof(double) * (size_t)(c->nb > 0 ? c->nb : 1) * c->HSu));
   CKS(ensure(c, c->Ebar, sizeof(double) * (size_t)M));
   // E_F response and weights
+  {
+  Region R(c, PK_EFRESP, 1, s);
   if (launch_ef_response(M, c->n_exp, P<double>(c->gsig), P<double>(c->a_inf), P<double>(c->b_inf),
                          P<double>(c->onsite), P<FermiState>(c->fstate), P<double>(c->partials),
                          P<unsigned>(c->counter), P<double>(c->lam), s))
     return fail(c, BOP_ERR_CUDA, "E_F response launch failed");
+  }
   WeightArgs wa;
   wa.M = M;
   wa.n_mom = c->n_mom;
@@ -704,7 +795,10 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   wa.dU_dE = nullptr;
   wa.zscratch = P<double>(c->zscr);
   wa.status = P<unsigned>(c->status);
-  if (launch_weights(wa, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
+  {
+    Region R(c, PK_WEIGHTS, 1, s);
+    if (launch_weights(wa, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
+  }
   // reverse sweep of the moments
   int nc = adjoint_columns(c->norb);
   size_t per_site = (size_t)c->norb * nc;
@@ -733,7 +827,10 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   aa.Hbar = P<double>(c->Hbar);
   aa.HSu = c->HSu;
   aa.Ebar = P<double>(c->Ebar);
-  if (launch_moments_adjoint(aa, c->fp64, s)) return fail(c, BOP_ERR_CUDA, "adjoint launch failed");
+  {
+    Region R(c, PK_ADJOINT, 1, s);
+    if (launch_moments_adjoint(aa, c->fp64, s)) return fail(c, BOP_ERR_CUDA, "adjoint launch failed");
+  }
   DBuf* fb = nullptr;
   DBuf tf, tv;
   double* F = forces;
@@ -749,9 +846,12 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   }
   CK(cudaMemsetAsync(F, 0, sizeof(double) * 3 * n, s));
   CK(cudaMemsetAsync(W, 0, sizeof(double) * 9, s));
-  if (c->nb > 0 &&
-      launch_forces((int)c->nb, c->bm, P<double>(c->bond_d), P<int>(c->bond_atoms), P<double>(c->Hbar), c->HSu, F, W, s))
-    return fail(c, BOP_ERR_CUDA, "forces launch failed");
+  {
+    Region Rf(c, PK_FORCES, c->nb > 0 ? 1 : 0, s);
+    if (c->nb > 0 && launch_forces((int)c->nb, c->bm, P<double>(c->bond_d), P<int>(c->bond_atoms),
+                                   P<double>(c->Hbar), c->HSu, F, W, s))
+      return fail(c, BOP_ERR_CUDA, "forces launch failed");
+  }
   int r = check_status(c, s);
   if (fb && tf.p) cudaFree(tf.p);
   if (tv.p) cudaFree(tv.p);
@@ -809,6 +909,42 @@ int bop_evaluate_host(bop_ctx* c, int n, const double* pos_host, const double* c
   for (DBuf* q : {&dpos, &dF, &dW})
     if (q->p) cudaFree(q->p);
   return r;
+}
+
+int bop_set_profiling(bop_ctx* c, int on) {
+  if (!c) return BOP_ERR_ARG;
+  c->prof.on = on != 0;
+  return BOP_OK;
+}
+
+int bop_reset_profile(bop_ctx* c) {
+  if (!c) return BOP_ERR_ARG;
+  if (c->prof.used) CK(cudaEventSynchronize(c->prof.pool[c->prof.used - 1]));
+  for (int k = 0; k < PK_N; k++) c->prof.launches[k] = 0;
+  c->prof.kind.clear();
+  c->prof.used = 0;
+  return BOP_OK;
+}
+
+int bop_get_profile(bop_ctx* c, bop_kernel_time* out, int max, int* n_out) {
+  if (!c || !out) return BOP_ERR_ARG;
+  double ms[PK_N] = {0};
+  long long reg[PK_N] = {0};
+  if (c->prof.used) CK(cudaEventSynchronize(c->prof.pool[c->prof.used - 1]));
+  for (size_t q = 0; q < c->prof.kind.size() && 2 * q + 1 < c->prof.used; q++) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->prof.pool[2 * q], c->prof.pool[2 * q + 1]));
+    ms[c->prof.kind[q]] += t;
+    reg[c->prof.kind[q]]++;
+  }
+  for (int k = 0; k < PK_N && k < max; k++) {
+    out[k].name = PK_NAMES[k];
+    out[k].launches = c->prof.launches[k];
+    out[k].regions = reg[k];
+    out[k].ms = ms[k];
+  }
+  if (n_out) *n_out = PK_N;
+  return BOP_OK;
 }
 
 }  // extern "C"

@@ -227,6 +227,7 @@ k_cluster(int n, int K, const long long* __restrict__ row_ptr, const int* __rest
       } else {
         block_exclusive_scan(scnt, nsite, warp_tmp);
         long long s0 = out.site_off[atom], a0 = out.adj_base[atom];
+        unsigned long long prod = 0;
         for (int t = threadIdx.x; t < nsite; t += blockDim.x) {
           unsigned long long kt = sk[t];
           out.site_atom[s0 + t] = key_atom(kt);
@@ -259,7 +260,17 @@ k_cluster(int n, int K, const long long* __restrict__ row_ptr, const int* __rest
           }
           long long o = a0 + scnt[t];
           for (int x = 0; x < c; x++) out.adj[o + x] = ent[x];
+          // forward levels k = max(lt, ls+1) .. K use the pair (t, s)
+          int lt = 0;
+          while (lt < K && t >= s_lev[lt]) lt++;
+          for (int x = 0; x < c; x++) {
+            int ls = 0;
+            while (ls < K && ent[x].x >= s_lev[ls]) ls++;
+            int k0 = lt > ls + 1 ? lt : ls + 1;
+            if (k0 <= K) prod += (unsigned long long)(K - k0 + 1);
+          }
         }
+        if (prod) atomicAdd(out.n_products, prod);
       }
     } else if (PASS == 0 && threadIdx.x == 0) {
       out.atom_nsite[atom] = 0;

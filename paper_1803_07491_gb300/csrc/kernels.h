@@ -37,6 +37,7 @@ struct ClusterOut {
   signed char* site_img; // [S][3]
   long long* adj_off;    // [S+1]
   int2* adj;             // [A]
+  unsigned long long* n_products;  // block products of one moments pass (pass 2)
 };
 
 namespace bopk {
