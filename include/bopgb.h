@@ -230,6 +230,33 @@ int bop_reset_profile(bop_ctx* ctx);
 /* Writes up to max entries, *n_out = number of families. */
 int bop_get_profile(bop_ctx* ctx, bop_kernel_time* out_host, int max, int* n_out);
 
+/* Fermi level of M orbitals without any device allocation.  This entry
+ * point has no counterpart in the paper: it serves callers that cannot call
+ * cudaMalloc, because they run under a device-memory budget fixed in
+ * advance, because their host framework pre-reserves all GPU memory at
+ * start-up (a new allocation would fail or bypass its accounting), or
+ * because an allocation would synchronise the device at a point they do not
+ * control.  It runs the same bisection kernels as bop_energy with their
+ * scratch in a 16 MiB file-scope __device__ array that every GPU loading the
+ * library keeps until the process exits.
+ *   M            orbitals (all spins)
+ *   n_exp        expansion length of gsig (2 .. 253)
+ *   gsig         device [n_exp+1][M]: g_m sigma_m, as written by bop_recursion
+ *   a_inf, b_inf device [M]: terminator of every orbital (bop_recursion)
+ *   spin_factor  2 for non-magnetic orbitals, 1 per collinear spin channel
+ *   n_electrons  total electron count the Fermi level must hold
+ *   e_fermi      device [1] output
+ * Caller-owned inputs and output; nothing is allocated.  The scratch needs
+ * 16896 + 8 (n_exp + 3) M bytes: larger problems (more than 10,300 orbitals
+ * at n_exp = 200) are rejected with BOP_ERR_OVERFLOW and a message on
+ * stderr, before anything is launched.  The first call on a device looks up
+ * the array's device address (once per device), so make that first call
+ * before any stream capture.  All calls share the one array, which keeps
+ * the last call's contents: calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller. */
+int bop_fermi_level_noalloc(int M, int n_exp, const double* gsig, const double* a_inf, const double* b_inf,
+                            double spin_factor, double n_electrons, double* e_fermi, bop_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

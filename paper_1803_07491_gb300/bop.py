@@ -86,6 +86,8 @@ def lib(path: str | None = None):
         "bop_get_orbital_state": ([_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
         "bop_evaluate_host": ([_VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                ctypes.POINTER(bop_stats), _VP], ctypes.c_int),
+        "bop_fermi_level_noalloc": ([ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double,
+                                     ctypes.c_double, _VP, _VP], ctypes.c_int),
         "bop_set_profiling": ([_VP, ctypes.c_int], ctypes.c_int),
         "bop_reset_profile": ([_VP], ctypes.c_int),
         "bop_get_profile": ([_VP, ctypes.POINTER(bop_kernel_time), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
@@ -252,6 +254,17 @@ def bop_evaluate_host(ctx, pos_host: torch.Tensor, cell, pbc, e_atom_host=None, 
                                         _ptr(e_atom_host), _ptr(forces_host), _ptr(virial_host),
                                         ctypes.cast(ctypes.pointer(et), _VP), ctypes.byref(s), _stream(stream)))
     return et.value, s.as_dict()
+
+
+def bop_fermi_level_noalloc(gsig_cm: torch.Tensor, a_inf: torch.Tensor, b_inf: torch.Tensor,
+                            spin_factor: float, n_electrons: float, e_fermi: torch.Tensor, stream=None) -> int:
+    """Fermi level without device allocation (scratch in a static device
+    array).  gsig_cm: [n_exp+1][M] coefficient-major.  Returns the status;
+    e_fermi (device, 1 element) holds the result on success."""
+    n_exp = gsig_cm.shape[0] - 1
+    M = gsig_cm.shape[1]
+    return lib().bop_fermi_level_noalloc(M, n_exp, _ptr(gsig_cm), _ptr(a_inf), _ptr(b_inf), spin_factor,
+                                         n_electrons, _ptr(e_fermi), _stream(stream))
 
 
 def bop_set_profiling(ctx, on: bool):
