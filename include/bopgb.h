@@ -236,7 +236,8 @@ int bop_get_profile(bop_ctx* ctx, bop_kernel_time* out_host, int max, int* n_out
  * advance, because their host framework pre-reserves all GPU memory at
  * start-up (a new allocation would fail or bypass its accounting), or
  * because an allocation would synchronise the device at a point they do not
- * control.  It runs the same bisection kernels as bop_energy with their
+ * control.  It runs the library's bisection kernels (the same root as the
+ * Newton-accelerated search of bop_energy, within 1e-13 eV) with their
  * scratch in a 16 MiB file-scope __device__ array that every GPU loading the
  * library keeps until the process exits.
  *   M            orbitals (all spins)

@@ -18,7 +18,11 @@
 int moments_columns(int norb, int cap, int fp64);
 int adjoint_columns(int norb);
 
-constexpr int FERMI_ROUNDS = 100;
+constexpr int FERMI_ROUNDS_COLD = 32;  // Newton rounds launched for a cold start
+constexpr int FERMI_ROUNDS_WARM = 12;  // ... and from the previous SCF iteration's E_F
+constexpr int FERMI_ROUNDS_MORE = 64;  // extra rounds if a solve has not converged
+constexpr int FERMI_MAX_ROUNDS = 256;  // hard cap per solve
+constexpr double FERMI_TOL = 1e-13;    // eV
 
 namespace {
 
@@ -64,7 +68,7 @@ struct bop_ctx {
   DBuf level_end, atom_nsite, atom_nadj, max_level, site_off, adj_base, site_atom, site_img, adj_off, adj;
   DBuf onsite, onsite32, delta, mval, delta_new, m_new, mu, a, b, nlev, a_inf, b_inf, gsig, D, gjack;
   DBuf N, U, dos, fstate, partials, counter, result, e_total, lam, e_atom;
-  DBuf w, zscr, adjscr, Hbar, Ebar;
+  DBuf w, zscr, adjscr, Hbar, Ebar, ginv;
   DBuf status;
   DBuf cub_tmp;
   DBuf nprod;
@@ -368,7 +372,6 @@ int run_scalar(bop_ctx* c, int M, const double* mu, cudaStream_t s) {
   a.a_inf = P<double>(c->a_inf);
   a.b_inf = P<double>(c->b_inf);
   a.gsig = P<double>(c->gsig);
-  a.D = P<double>(c->D);
   a.g = P<double>(c->gjack);
   a.status = P<unsigned>(c->status);
   Region R(c, PK_EXPAND, 1, s);
@@ -376,21 +379,40 @@ int run_scalar(bop_ctx* c, int M, const double* mu, cudaStream_t s) {
   return BOP_OK;
 }
 
-int fermi_and_NU(bop_ctx* c, cudaStream_t s) {
+// Fermi level (Newton steps inside the bisection bracket) and N, DOS of every
+// orbital at E_F.  warm: start from the previous solve's E_F.
+int fermi_and_N(bop_ctx* c, int warm, cudaStream_t s) {
   const int M = c->S * c->n * c->norb;
   const double target = c->m.n_e * c->n;
+  const int rounds = warm ? FERMI_ROUNDS_WARM : FERMI_ROUNDS_COLD;
   {
-    Region R(c, PK_FERMI, 1 + FERMI_ROUNDS, s);
-    if (launch_fermi(M, P<double>(c->D), P<double>(c->gsig), P<double>(c->a_inf), P<double>(c->b_inf), c->n_exp,
-                   c->sfac, target, P<FermiState>(c->fstate), P<double>(c->partials), P<unsigned>(c->counter),
-                     FERMI_ROUNDS, 1e-13, s))
+    Region R(c, PK_FERMI, 1 + rounds, s);
+    if (launch_fermi_newton(M, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf), P<double>(c->b_inf),
+                            c->n_exp, c->sfac, target, P<FermiState>(c->fstate), P<double>(c->partials),
+                            P<unsigned>(c->counter), warm, rounds, FERMI_MAX_ROUNDS, FERMI_TOL, s))
       return fail(c, BOP_ERR_CUDA, "fermi launch failed");
   }
   Region R(c, PK_NU, 1, s);
-  if (launch_orbital_NU(M, c->n_exp, P<double>(c->gsig), P<double>(c->a_inf), P<double>(c->b_inf),
-                        P<double>(c->onsite), P<FermiState>(c->fstate), P<double>(c->N), P<double>(c->U),
-                        P<double>(c->dos), s))
-    return fail(c, BOP_ERR_CUDA, "orbital N/U launch failed");
+  if (launch_orbital_N(M, c->n_exp, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf),
+                       P<double>(c->b_inf), P<FermiState>(c->fstate), P<double>(c->N), P<double>(c->dos), s))
+    return fail(c, BOP_ERR_CUDA, "orbital N launch failed");
+  return BOP_OK;
+}
+
+// More Newton rounds for a solve that has not converged, then N and DOS again.
+int fermi_more(bop_ctx* c, cudaStream_t s) {
+  const int M = c->S * c->n * c->norb;
+  {
+    Region R(c, PK_FERMI, FERMI_ROUNDS_MORE, s);
+    if (launch_fermi_more(M, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf), P<double>(c->b_inf),
+                          c->n_exp, c->sfac, c->m.n_e * c->n, P<FermiState>(c->fstate), P<double>(c->partials),
+                          P<unsigned>(c->counter), FERMI_ROUNDS_MORE, FERMI_MAX_ROUNDS, FERMI_TOL, s))
+      return fail(c, BOP_ERR_CUDA, "fermi launch failed");
+  }
+  Region R(c, PK_NU, 1, s);
+  if (launch_orbital_N(M, c->n_exp, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf),
+                       P<double>(c->b_inf), P<FermiState>(c->fstate), P<double>(c->N), P<double>(c->dos), s))
+    return fail(c, BOP_ERR_CUDA, "orbital N launch failed");
   return BOP_OK;
 }
 
@@ -434,13 +456,15 @@ int bop_create(bop_ctx** out, const bop_model* model) {
   if ((r = ensure(c, c->status, sizeof(unsigned))) || (r = ensure(c, c->gjack, sizeof(double) * (c->n_exp + 1))) ||
       (r = ensure(c, c->fstate, sizeof(FermiState))) || (r = ensure(c, c->partials, sizeof(double) * 4096)) ||
       (r = ensure(c, c->counter, sizeof(unsigned))) || (r = ensure(c, c->result, sizeof(double) * 4)) ||
-      (r = ensure(c, c->e_total, sizeof(double))) || (r = ensure(c, c->lam, sizeof(double) * 4))) {
+      (r = ensure(c, c->e_total, sizeof(double))) || (r = ensure(c, c->lam, sizeof(double) * 4)) ||
+      (r = ensure(c, c->ginv, sizeof(double) * (c->n_exp + 8)))) {
     bop_destroy(c);
     return r;
   }
   cudaMemset(c->status.p, 0, sizeof(unsigned));
   cudaMemset(c->counter.p, 0, sizeof(unsigned));
   launch_jackson(P<double>(c->gjack), c->n_exp, 0);
+  launch_inverse_table(P<double>(c->ginv), c->n_exp + 8, 0);
   if (cudaDeviceSynchronize() != cudaSuccess) {
     bop_destroy(c);
     return BOP_ERR_CUDA;
@@ -459,7 +483,8 @@ int bop_destroy(bop_ctx* c) {
                   &c->onsite32, &c->delta, &c->mval, &c->delta_new, &c->m_new, &c->mu, &c->a, &c->b, &c->nlev,
                   &c->a_inf, &c->b_inf, &c->gsig, &c->D, &c->gjack, &c->N, &c->U, &c->dos, &c->fstate,
                   &c->partials, &c->counter, &c->result, &c->e_total, &c->lam, &c->e_atom, &c->w, &c->zscr,
-                  &c->adjscr, &c->Hbar, &c->Ebar, &c->status, &c->cub_tmp, &c->nprod};
+                  &c->adjscr, &c->Hbar, &c->Ebar, &c->status, &c->cub_tmp, &c->nprod,
+                  &c->ginv};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -640,15 +665,15 @@ int bop_recursion(bop_ctx* c, int M, const double* mu, double* a, double* b, int
   if (!c) return BOP_ERR_ARG;
   if (M < 1 || !mu || !gsig) return fail(c, BOP_ERR_ARG, "need M >= 1, mu and gsig");
   cudaStream_t s = S_(stream);
-  DBuf ta, tb, tn, tai, tbi, tD;
+  DBuf ta, tb, tn, tai, tbi;
   auto cleanup = [&]() {
-    for (DBuf* q : {&ta, &tb, &tn, &tai, &tbi, &tD})
+    for (DBuf* q : {&ta, &tb, &tn, &tai, &tbi})
       if (q->p) cudaFree(q->p);
   };
   int r;
   if ((r = ensure(c, ta, sizeof(double) * M * c->Kp)) || (r = ensure(c, tb, sizeof(double) * M * (c->Kp + 1))) ||
       (r = ensure(c, tn, sizeof(int) * M)) || (r = ensure(c, tai, sizeof(double) * M)) ||
-      (r = ensure(c, tbi, sizeof(double) * M)) || (r = ensure(c, tD, sizeof(double) * M * (c->n_exp + 3)))) {
+      (r = ensure(c, tbi, sizeof(double) * M))) {
     cleanup();
     return r;
   }
@@ -663,7 +688,6 @@ int bop_recursion(bop_ctx* c, int M, const double* mu, double* a, double* b, int
   A.a_inf = a_inf ? a_inf : P<double>(tai);
   A.b_inf = b_inf ? b_inf : P<double>(tbi);
   A.gsig = gsig;
-  A.D = P<double>(tD);
   A.g = P<double>(c->gjack);
   A.status = P<unsigned>(c->status);
   r = launch_expand(A, s) ? fail(c, BOP_ERR_CUDA, "expand launch failed") : BOP_OK;
@@ -690,6 +714,31 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   }
   int it = 0, converged = c->m.scf == BOP_SCF_NONE;
   double res[4] = {0, 0, 0, 0};
+  FermiState fs;
+  ScfArgs a;
+  a.n = n;
+  a.norb = c->norb;
+  a.n_spin = c->S;
+  a.mode = c->m.scf;
+  a.spin_factor = c->sfac;
+  a.n0 = c->m.n_e;
+  a.eta = c->m.eta;
+  a.tol = c->m.scf_tol;
+  a.dos_floor = c->m.dos_floor;
+  a.stoner_I = c->m.stoner_I;
+  a.m_mix = c->m.m_mix;
+  a.onsite0 = c->m.onsite0;
+  a.N = P<double>(c->N);
+  a.dos = P<double>(c->dos);
+  a.delta = P<double>(c->delta);
+  a.m = P<double>(c->mval);
+  a.delta_new = P<double>(c->delta_new);
+  a.m_new = P<double>(c->m_new);
+  a.onsite = P<double>(c->onsite);
+  a.onsite32 = P<float>(c->onsite32);
+  a.red = P<double>(c->partials);
+  a.counter = P<unsigned>(c->counter);
+  a.result = P<double>(c->result);
   for (;;) {
     {
       Region R(c, PK_ONSITE, 1, s);
@@ -698,43 +747,43 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
     }
     CKS(run_moments(c, P<double>(c->onsite), P<double>(c->mu), s));
     CKS(run_scalar(c, M, P<double>(c->mu), s));
-    CKS(fermi_and_NU(c, s));
-    if (c->m.scf == BOP_SCF_NONE || it >= c->m.scf_max_it) break;
-    ScfArgs a;
-    a.n = n;
-    a.norb = c->norb;
-    a.n_spin = c->S;
-    a.mode = c->m.scf;
-    a.spin_factor = c->sfac;
-    a.n0 = c->m.n_e;
-    a.eta = c->m.eta;
-    a.tol = c->m.scf_tol;
-    a.dos_floor = c->m.dos_floor;
-    a.stoner_I = c->m.stoner_I;
-    a.m_mix = c->m.m_mix;
-    a.onsite0 = c->m.onsite0;
-    a.N = P<double>(c->N);
-    a.dos = P<double>(c->dos);
-    a.delta = P<double>(c->delta);
-    a.m = P<double>(c->mval);
-    a.delta_new = P<double>(c->delta_new);
-    a.m_new = P<double>(c->m_new);
-    a.onsite = P<double>(c->onsite);
-    a.onsite32 = P<float>(c->onsite32);
-    a.red = P<double>(c->partials);
-    a.counter = P<unsigned>(c->counter);
-    a.result = P<double>(c->result);
-    {
-      Region R(c, PK_SCF, 2, s);
-      if (launch_scf_update(a, s)) return fail(c, BOP_ERR_CUDA, "scf update launch failed");
+    CKS(fermi_and_N(c, it > 0, s));
+    const bool last_it = c->m.scf == BOP_SCF_NONE || it >= c->m.scf_max_it;
+    if (!last_it) {
+      Region R(c, PK_SCF, 1, s);
+      if (launch_scf_residual(a, s)) return fail(c, BOP_ERR_CUDA, "scf residual launch failed");
     }
-    CK(cudaMemcpyAsync(res, c->result.p, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
-    CKS(check_status(c, s));
+    // one synchronisation per iteration: Fermi solve converged?  SCF converged?
+    for (int extra = 0;; extra++) {
+      CK(cudaMemcpyAsync(&fs, c->fstate.p, sizeof(FermiState), cudaMemcpyDeviceToHost, s));
+      if (!last_it) CK(cudaMemcpyAsync(res, c->result.p, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+      CKS(check_status(c, s));
+      if (fs.done) break;
+      if (fs.iters >= FERMI_MAX_ROUNDS || extra >= 4)
+        return fail(c, BOP_ERR_BRACKET, "Fermi level not converged after %d rounds", fs.iters);
+      CKS(fermi_more(c, s));
+      if (!last_it) {
+        Region R(c, PK_SCF, 1, s);
+        if (launch_scf_residual(a, s)) return fail(c, BOP_ERR_CUDA, "scf residual launch failed");
+      }
+    }
+    if (last_it) break;
     if (res[2] != 0.0) {
       converged = 1;
       break;
     }
+    {
+      Region R(c, PK_SCF, 1, s);
+      if (launch_scf_apply(a, s)) return fail(c, BOP_ERR_CUDA, "scf apply launch failed");
+    }
     it++;
+  }
+  {
+    Region R(c, PK_NU, 1, s);
+    if (launch_orbital_NU(M, c->n_exp, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf),
+                          P<double>(c->b_inf), P<double>(c->onsite), P<FermiState>(c->fstate), P<double>(c->N),
+                          P<double>(c->U), P<double>(c->dos), s))
+      return fail(c, BOP_ERR_CUDA, "orbital N/U launch failed");
   }
   {
   Region Re(c, PK_ENERGY, 1, s);
@@ -745,9 +794,7 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   }
   if (delta_io) CK(cudaMemcpyAsync(delta_io, c->delta.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   if (m_io && stoner) CK(cudaMemcpyAsync(m_io, c->mval.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  FermiState fs;
   double et = 0.0;
-  CK(cudaMemcpyAsync(&fs, c->fstate.p, sizeof(FermiState), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&et, c->e_total.p, sizeof(double), cudaMemcpyDeviceToHost, s));
   CKS(check_status(c, s));
   c->st.scf_iterations = it;
@@ -769,13 +816,14 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   cudaStream_t s = S_(stream);
   const int n = c->n, M = c->S * n * c->norb;
   CKS(ensure(c, c->w, sizeof(double) * (size_t)M * c->n_mom));
-  CKS(ensure(c, c->zscr, sizeof(double) * (size_t)M * (c->n_exp + 1) * (c->Kp + 2)));
+  CKS(ensure(c, c->zscr, sizeof(double) * (size_t)M * (c->n_exp + 1) * 2));
   CKS(ensure(c, c->Hbar, sizeof(double) * (size_t)(c->nb > 0 ? c->nb : 1) * c->HSu));
   CKS(ensure(c, c->Ebar, sizeof(double) * (size_t)M));
   // E_F response and weights
   {
   Region R(c, PK_EFRESP, 1, s);
-  if (launch_ef_response(M, c->n_exp, P<double>(c->gsig), P<double>(c->a_inf), P<double>(c->b_inf),
+  if (launch_ef_response(M, c->n_exp, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf),
+                         P<double>(c->b_inf),
                          P<double>(c->onsite), P<FermiState>(c->fstate), P<double>(c->partials),
                          P<unsigned>(c->counter), P<double>(c->lam), s))
     return fail(c, BOP_ERR_CUDA, "E_F response launch failed");
@@ -789,6 +837,7 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   wa.onsite = P<double>(c->onsite);
   wa.st = P<FermiState>(c->fstate);
   wa.g = P<double>(c->gjack);
+  wa.inv = P<double>(c->ginv);
   wa.cU = c->sfac;
   wa.lam = P<double>(c->lam);
   wa.w = P<double>(c->w);

@@ -98,8 +98,7 @@ struct ScalarArgs {
   int* nlev;           // [M]
   double* a_inf;       // [M]
   double* b_inf;       // [M]
-  double* gsig;        // [n_exp+1][M]   (transposed)
-  double* D;           // [n_exp+3][M]   sine-series coefficients of N
+  double* gsig;        // [n_exp+1][M]   (coefficient-major)
   const double* g;     // [n_exp+1] damping
   unsigned* status;
 };
@@ -114,9 +113,19 @@ int launch_fermi(int M, const double* D, const double* gsig, const double* a_inf
                  double spin_factor, double target, FermiState* st, double* partials, unsigned* counter,
                  int max_rounds, double tol, cudaStream_t s);
 
-int launch_orbital_NU(int M, int n_exp, const double* gsig, const double* a_inf, const double* b_inf,
-                      const double* onsite, const FermiState* st, double* N, double* U, double* dos,
-                      cudaStream_t s);
+int launch_orbital_NU(int M, int n_exp, const double* gsig, const double* inv, const double* a_inf,
+                      const double* b_inf, const double* onsite, const FermiState* st, double* N, double* U,
+                      double* dos, cudaStream_t s);
+int launch_orbital_N(int M, int n_exp, const double* gsig, const double* inv, const double* a_inf,
+                     const double* b_inf, const FermiState* st, double* N, double* dos, cudaStream_t s);
+// Newton steps inside the bisection bracket (chain.cu); warm: start from st->ef
+int launch_fermi_newton(int M, const double* gsig, const double* inv, const double* a_inf, const double* b_inf,
+                        int n_exp, double spin_factor, double target, FermiState* st, double* partials,
+                        unsigned* counter, int warm, int rounds, int max_rounds, double tol, cudaStream_t s);
+int launch_fermi_more(int M, const double* gsig, const double* inv, const double* a_inf, const double* b_inf,
+                      int n_exp, double spin_factor, double target, FermiState* st, double* partials,
+                      unsigned* counter, int rounds, int max_rounds, double tol, cudaStream_t s);
+void launch_inverse_table(double* inv, int n, cudaStream_t s);
 
 struct ScfArgs {
   int n, norb, n_spin, mode;  // mode 1 = LCN, 2 = Stoner
@@ -133,7 +142,8 @@ struct ScfArgs {
   unsigned* counter;
   double* result;      // [4]: max|res|, max|dm|, converged, mean
 };
-int launch_scf_update(const ScfArgs& a, cudaStream_t s);
+int launch_scf_residual(const ScfArgs& a, cudaStream_t s);
+int launch_scf_apply(const ScfArgs& a, cudaStream_t s);
 void launch_to_float(const double* in, float* out, size_t n, cudaStream_t s);
 void launch_build_onsite(int n, int norb, int n_spin, double onsite0, double stoner_I, const double* delta,
                          const double* m, double* onsite, float* onsite32, cudaStream_t s);
@@ -148,17 +158,18 @@ struct WeightArgs {
   const double* onsite;  // [M]
   const FermiState* st;
   const double* g;
-  double cU;             // L = cU*U + (cN + cN_orb[o]) * N
+  const double* inv;     // [n_exp+8] 1/k
+  double cU;             // L = cU*U + cN*N
   const double* lam;     // device scalar: cN = -cU * (*lam)  (E_F response)
   double* w;             // [M][n_mom]
   double* dU_dE;         // [M] direct derivative of L w.r.t. the onsite level, may be null
-  double* zscratch;      // [M][(n_exp+1)*(Kp+2)]
+  double* zscratch;      // [2][n_exp+1][M]: sigma_m and its cotangent
   unsigned* status;
 };
 int launch_weights(const WeightArgs& a, cudaStream_t s);
-int launch_ef_response(int M, int n_exp, const double* gsig, const double* a_inf, const double* b_inf,
-                       const double* onsite, const FermiState* st, double* red, unsigned* counter, double* lam,
-                       cudaStream_t s);
+int launch_ef_response(int M, int n_exp, const double* gsig, const double* inv, const double* a_inf,
+                       const double* b_inf, const double* onsite, const FermiState* st, double* red,
+                       unsigned* counter, double* lam, cudaStream_t s);
 
 // forces.cu
 int launch_forces(int nb, BondModel m, const double* bond_d, const int* bond_atoms, const double* Hbar, int HSu,

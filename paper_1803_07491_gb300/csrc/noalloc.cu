@@ -5,8 +5,9 @@
 // accounting), and paths where an allocation would synchronise the device
 // at the wrong moment.
 //
-// The search runs the same bisection kernels as bop_energy (k_bracket,
-// k_fermi_round in scalar.cu).  Their scratch (the sine-series coefficients
+// The search runs the library's bisection kernels (k_bracket, k_fermi_round
+// in scalar.cu; bop_energy finds the same root with Newton steps inside the
+// bisection bracket).  Their scratch (the sine-series coefficients
 // of N(phi), the per-block partial sums, the completion counter and the
 // bracket state) lives in one file-scope __device__ array instead of
 // context buffers.  Every GPU that loads the library holds that array until

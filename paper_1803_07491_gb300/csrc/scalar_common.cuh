@@ -1,0 +1,117 @@
+// Device helpers shared by the FP64 scalar-stage kernels (scalar.cu,
+// chain.cu): moments -> recursion coefficients (Eqs. momtoa, momtob and the
+// c_j^n recursion), Gershgorin band edges (Eq. gershogorin), the constant
+// terminator (Eq. abinf) and the normalised chain parameters (Eq. aexp).
+#pragma once
+#include "kernels.h"
+
+namespace scal {
+
+constexpr double PI = 3.14159265358979323846;
+constexpr double B_INF_MIN = 1e-3;   // eV, floor of the band-width estimate
+constexpr double TRUNC_REL = 1e-10;  // recursion truncation threshold
+constexpr int KPMAX = (BOP_MAX_NMOM - 1) / 2;
+
+// ------------------------------------------------------------ recursion
+struct Rec {
+  double a[KPMAX];
+  double b[KPMAX + 1];
+  int nlev;
+  bool trunc;
+};
+
+// a_n = sum c_j c_l mu_{j+l+1};  b_{n+1} c^{n+1} = c^n shifted - a_n c^n - b_n c^{n-1}
+__device__ inline void recursion(const double* mu, int Kp, Rec& r) {
+  double c[KPMAX + 2], cp[KPMAX + 2], d[KPMAX + 2];
+  for (int j = 0; j < KPMAX + 2; j++) c[j] = cp[j] = 0.0;
+  c[0] = 1.0;
+  r.b[0] = 0.0;
+  r.nlev = Kp;
+  r.trunc = false;
+  double width = fmax(mu[2] - mu[1] * mu[1], 0.0);
+  for (int n = 0; n < Kp; n++) {
+    double an = 0.0;
+    for (int j = 0; j <= n; j++)
+      for (int l = 0; l <= n; l++) an += c[j] * c[l] * mu[j + l + 1];
+    r.a[n] = an;
+    for (int j = 0; j <= n + 1; j++) d[j] = (j >= 1 ? c[j - 1] : 0.0) - an * c[j] - r.b[n] * cp[j];
+    double b2 = 0.0;
+    for (int j = 0; j <= n + 1; j++)
+      for (int l = 0; l <= n + 1; l++) b2 += d[j] * d[l] * mu[j + l];
+    if (b2 <= TRUNC_REL * width) {
+      r.b[n + 1] = 0.0;
+      r.nlev = n + 1;
+      r.trunc = true;
+      for (int q = n + 1; q < Kp; q++) {
+        r.a[q] = 0.0;
+        r.b[q + 1] = 0.0;
+      }
+      return;
+    }
+    double bn = sqrt(b2);
+    r.b[n + 1] = bn;
+    for (int j = 0; j <= n + 1; j++) {
+      cp[j] = c[j];
+      c[j] = d[j] / bn;
+    }
+  }
+}
+
+struct Term {
+  double a_inf, b_inf;
+  int ilo, ihi;
+  bool floored;
+};
+
+// Gershgorin over the computed levels n < nlev (b_0 = 0); first index wins ties.
+__device__ inline Term gershgorin(const Rec& r) {
+  Term t;
+  double bot = 0.0, top = 0.0;
+  t.ilo = t.ihi = 0;
+  for (int n = 0; n < r.nlev; n++) {
+    double lo = r.a[n] - r.b[n] - r.b[n + 1];
+    double hi = r.a[n] + r.b[n] + r.b[n + 1];
+    if (n == 0 || lo < bot) { bot = lo; t.ilo = n; }
+    if (n == 0 || hi > top) { top = hi; t.ihi = n; }
+  }
+  t.a_inf = 0.5 * (top + bot);
+  t.b_inf = 0.25 * (top - bot);
+  t.floored = t.b_inf < B_INF_MIN;
+  if (t.floored) t.b_inf = B_INF_MIN;
+  return t;
+}
+
+// Chain parameters: a^_k (k < nlev) and b^_k (1 <= k <= Kp, k <= nlev);
+// the constant terminator a^ = 0, b^ = 1/2 elsewhere.
+struct Chain {
+  double ah[KPMAX + 1];
+  double bh[KPMAX + 2];
+};
+__device__ inline void chain_params(const Rec& r, const Term& t, int Kp, Chain& ch) {
+  for (int k = 0; k <= KPMAX; k++) ch.ah[k] = 0.0;
+  for (int k = 0; k <= KPMAX + 1; k++) ch.bh[k] = 0.5;
+  ch.bh[0] = 0.0;
+  for (int k = 0; k < r.nlev; k++) ch.ah[k] = (r.a[k] - t.a_inf) / (2.0 * t.b_inf);
+  for (int k = 1; k <= Kp; k++)
+    if (k <= r.nlev) ch.bh[k] = r.b[k] / (2.0 * t.b_inf);
+}
+__device__ __forceinline__ double AH(const Chain& ch, int k) { return k <= KPMAX ? ch.ah[k] : 0.0; }
+__device__ __forceinline__ double BH(const Chain& ch, int k) { return k <= KPMAX + 1 ? ch.bh[k] : 0.5; }
+
+
+__device__ __forceinline__ double clamp1(double x) { return x > 1.0 ? 1.0 : (x < -1.0 ? -1.0 : x); }
+
+template <int NT>
+__device__ inline double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < NT / 32; q++) t += sh[q];
+  __syncthreads();
+  return t;  // valid on thread 0
+}
+
+constexpr int RT = 256;
+}  // namespace scal
