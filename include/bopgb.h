@@ -64,6 +64,7 @@ enum bop_status {
 
 enum { BOP_SCF_NONE = 0, BOP_SCF_LCN = 1, BOP_SCF_STONER = 2 };
 enum { BOP_PREC_FP64 = 0, BOP_PREC_FP32 = 1 };
+enum { BOP_MIX_LINEAR = 0, BOP_MIX_ANDERSON = 1 };
 
 /* Model and run settings.
  * beta_x(r) = b0[x] * exp(-lam (r - r0)) * fcut(r), fcut the cosine taper
@@ -77,7 +78,11 @@ enum { BOP_PREC_FP64 = 0, BOP_PREC_FP32 = 1 };
  * scf_tol; STONER additionally mixes m_i with m_mix from m0 until
  * max|m_out - m| < 10 scf_tol, E_{i,up/down} = E0 + delta_i -/+ I m_i / 2.
  * precision: FP64 everywhere, or FP32 products and accumulation in the
- * moments and their reverse sweep with every scalar stage in FP64. */
+ * moments and their reverse sweep with every scalar stage in FP64.
+ * mixer: BOP_MIX_LINEAR (x += F, F the preconditioned residual above) or
+ * BOP_MIX_ANDERSON (type-II Broyden over the last mix_history <= 8
+ * iterations, one of the paper's mixers); both converge to the same
+ * self-consistent state. */
 typedef struct {
   int norb;
   double b0[3];
@@ -92,6 +97,8 @@ typedef struct {
   int scf_max_it;
   double stoner_I, m_mix, m0, dos_floor;
   int precision;
+  int mixer;
+  int mix_history;
 } bop_model;
 
 typedef struct {

@@ -20,6 +20,9 @@ Readings of the paper taken here (each listed in the design doc):
     gives a narrow band instead of a division by zero.
   * the recursion is truncated where b_{n+1}^2 <= TRUNC_REL * (mu_2 - mu_1^2).
   * local charge neutrality acts per atom (one shift per atom).
+  * the SCF update is either linear mixing of the DOS-preconditioned
+    residual or Anderson (type-II Broyden) mixing of it; both reach the
+    same self-consistent state.
 """
 from __future__ import annotations
 
@@ -108,6 +111,8 @@ class Settings:
     m_mix: float = 0.3
     m0: float = 2.0
     dos_floor: float = 0.1     # states/eV, LCN preconditioner floor
+    mixer: str = "linear"      # linear | anderson (type-II Broyden, "SCF" of the paper)
+    mix_history: int = 6
 
 
 @dataclass
@@ -539,6 +544,7 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
         m = np.full(n, st.m0) if m_init is None else np.array(m_init, np.float64)
     N0 = st.n_e
     target = st.n_e * n
+    hist_x, hist_f = [], []
     it = 0
     converged = st.scf == "none"
     while True:
@@ -566,10 +572,30 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
         if done:
             converged = True
             break
-        delta = delta + st.eta * res / np.maximum(dos, st.dos_floor)
-        delta = delta - delta.mean()
+        # preconditioned residual F; linear mixing x += F, or Anderson mixing
+        F = st.eta * res / np.maximum(dos, st.dos_floor)
+        x = delta.copy()
         if st.scf == "stoner":
-            m = (1.0 - st.m_mix) * m + st.m_mix * m_out
+            F = np.concatenate([F, st.m_mix * (m_out - m)])
+            x = np.concatenate([x, m])
+        if st.mixer == "anderson":
+            hist_x.append(x)
+            hist_f.append(F)
+            del hist_x[:-(st.mix_history + 1)], hist_f[:-(st.mix_history + 1)]
+            h = len(hist_f) - 1
+            x_new = x + F
+            if h > 0:
+                dF = np.array([hist_f[j + 1] - hist_f[j] for j in range(h)])
+                dX = np.array([hist_x[j + 1] - hist_x[j] for j in range(h)])
+                A = dF @ dF.T
+                A[np.diag_indices(h)] += 1e-12 * np.max(np.diag(A)) + 1e-300
+                gamma = np.linalg.solve(A, dF @ F)
+                x_new = x_new - gamma @ (dX + dF)
+        else:
+            x_new = x + F
+        delta = x_new[:n] - x_new[:n].mean()
+        if st.scf == "stoner":
+            m = x_new[n:]
         it += 1
     e_atom = s * U.reshape(S, n, norb).sum(axis=(0, 2))
     if st.scf == "stoner":

@@ -19,6 +19,7 @@ BOP_OK, BOP_ERR_ARG, BOP_ERR_CUDA, BOP_ERR_OOM, BOP_ERR_NO_CONVERGENCE = 0, 1, 2
 BOP_ERR_BRACKET, BOP_ERR_NUMERIC, BOP_ERR_STATE, BOP_ERR_OVERFLOW = 5, 6, 7, 8
 SCF = {"none": 0, "lcn": 1, "stoner": 2}
 PREC = {"fp64": 0, "fp32": 1}
+MIXER = {"linear": 0, "anderson": 1}
 
 
 class BopError(RuntimeError):
@@ -34,7 +35,8 @@ class bop_model(ctypes.Structure):
                 ("n_spin", ctypes.c_int), ("n_e", ctypes.c_double), ("scf", ctypes.c_int),
                 ("eta", ctypes.c_double), ("scf_tol", ctypes.c_double), ("scf_max_it", ctypes.c_int),
                 ("stoner_I", ctypes.c_double), ("m_mix", ctypes.c_double), ("m0", ctypes.c_double),
-                ("dos_floor", ctypes.c_double), ("precision", ctypes.c_int)]
+                ("dos_floor", ctypes.c_double), ("precision", ctypes.c_int), ("mixer", ctypes.c_int),
+                ("mix_history", ctypes.c_int)]
 
 
 class bop_stats(ctypes.Structure):
@@ -124,7 +126,7 @@ def make_model(params, run, precision: str = "fp64") -> bop_model:
     return bop_model(params.norb, (ctypes.c_double * 3)(*b0), params.r0, params.lam, params.rc, params.dc,
                      params.onsite0, run.n_mom, run.n_exp, run.n_spin, run.n_e, SCF[run.scf], run.eta,
                      run.scf_tol, run.scf_max_it, run.stoner_I, run.m_mix, run.m0, run.dos_floor,
-                     PREC[precision])
+                     PREC[precision], MIXER[run.mixer], run.mix_history)
 
 
 def _check(ctx, st, allow=()):

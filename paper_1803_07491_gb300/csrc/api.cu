@@ -18,8 +18,8 @@
 int moments_columns(int norb, int cap, int fp64);
 int adjoint_columns(int norb);
 
-constexpr int FERMI_ROUNDS_COLD = 32;  // Newton rounds launched for a cold start
-constexpr int FERMI_ROUNDS_WARM = 12;  // ... and from the previous SCF iteration's E_F
+constexpr int FERMI_ROUNDS_COLD = 16;  // Newton rounds launched for a cold start
+constexpr int FERMI_ROUNDS_WARM = 5;  // ... and from the previous SCF iteration's E_F
 constexpr int FERMI_ROUNDS_MORE = 64;  // extra rounds if a solve has not converged
 constexpr int FERMI_MAX_ROUNDS = 256;  // hard cap per solve
 constexpr double FERMI_TOL = 1e-13;    // eV
@@ -69,6 +69,7 @@ struct bop_ctx {
   DBuf onsite, onsite32, delta, mval, delta_new, m_new, mu, a, b, nlev, a_inf, b_inf, gsig, D, gjack;
   DBuf N, U, dos, fstate, partials, counter, result, e_total, lam, e_atom;
   DBuf w, zscr, adjscr, Hbar, Ebar, ginv;
+  DBuf hx, hf, gamma, scfred;
   DBuf status;
   DBuf cub_tmp;
   DBuf nprod;
@@ -196,6 +197,10 @@ int validate_model(bop_ctx* c, const bop_model* m) {
     return fail(c, BOP_ERR_ARG, "precision must be FP64 or FP32");
   if (m->scf != BOP_SCF_NONE && (m->scf_max_it < 0 || !(m->scf_tol > 0)))
     return fail(c, BOP_ERR_ARG, "scf_tol > 0 and scf_max_it >= 0 required");
+  if (m->mixer != BOP_MIX_LINEAR && m->mixer != BOP_MIX_ANDERSON)
+    return fail(c, BOP_ERR_ARG, "mixer must be LINEAR or ANDERSON");
+  if (m->mixer == BOP_MIX_ANDERSON && (m->mix_history < 1 || m->mix_history > 8))
+    return fail(c, BOP_ERR_ARG, "mix_history must be in [1, 8]");
   return BOP_OK;
 }
 
@@ -338,6 +343,12 @@ int size_state(bop_ctx* c) {
   CKS(ensure(c, c->U, sizeof(double) * M));
   CKS(ensure(c, c->dos, sizeof(double) * M));
   CKS(ensure(c, c->e_atom, sizeof(double) * c->n));
+  const int H = c->m.mixer == BOP_MIX_ANDERSON ? c->m.mix_history : 1;
+  const size_t n2 = (size_t)c->n * (c->m.scf == BOP_SCF_STONER ? 2 : 1);
+  CKS(ensure(c, c->hx, sizeof(double) * (H + 1) * n2));
+  CKS(ensure(c, c->hf, sizeof(double) * (H + 1) * n2));
+  CKS(ensure(c, c->gamma, sizeof(double) * 16));
+  CKS(ensure(c, c->scfred, sizeof(double) * 64 * 1024));
   return BOP_OK;
 }
 
@@ -454,7 +465,7 @@ int bop_create(bop_ctx** out, const bop_model* model) {
   cudaGetDevice(&c->device);
   memset(&c->st, 0, sizeof(c->st));
   if ((r = ensure(c, c->status, sizeof(unsigned))) || (r = ensure(c, c->gjack, sizeof(double) * (c->n_exp + 1))) ||
-      (r = ensure(c, c->fstate, sizeof(FermiState))) || (r = ensure(c, c->partials, sizeof(double) * 4096)) ||
+      (r = ensure(c, c->fstate, sizeof(FermiState))) || (r = ensure(c, c->partials, sizeof(double) * 3 * 4096)) ||
       (r = ensure(c, c->counter, sizeof(unsigned))) || (r = ensure(c, c->result, sizeof(double) * 4)) ||
       (r = ensure(c, c->e_total, sizeof(double))) || (r = ensure(c, c->lam, sizeof(double) * 4)) ||
       (r = ensure(c, c->ginv, sizeof(double) * (c->n_exp + 8)))) {
@@ -484,7 +495,7 @@ int bop_destroy(bop_ctx* c) {
                   &c->a_inf, &c->b_inf, &c->gsig, &c->D, &c->gjack, &c->N, &c->U, &c->dos, &c->fstate,
                   &c->partials, &c->counter, &c->result, &c->e_total, &c->lam, &c->e_atom, &c->w, &c->zscr,
                   &c->adjscr, &c->Hbar, &c->Ebar, &c->status, &c->cub_tmp, &c->nprod,
-                  &c->ginv};
+                  &c->ginv, &c->hx, &c->hf, &c->gamma, &c->scfred};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -736,10 +747,16 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   a.m_new = P<double>(c->m_new);
   a.onsite = P<double>(c->onsite);
   a.onsite32 = P<float>(c->onsite32);
-  a.red = P<double>(c->partials);
+  a.red = P<double>(c->scfred);
   a.counter = P<unsigned>(c->counter);
   a.result = P<double>(c->result);
+  a.mixer = c->m.mixer;
+  a.hist = c->m.mixer == BOP_MIX_ANDERSON ? c->m.mix_history : 1;
+  a.hx = P<double>(c->hx);
+  a.hf = P<double>(c->hf);
+  a.gamma = P<double>(c->gamma);
   for (;;) {
+    a.it = it;
     {
       Region R(c, PK_ONSITE, 1, s);
       launch_build_onsite(n, c->norb, c->S, c->m.onsite0, c->m.stoner_I, P<double>(c->delta),

@@ -24,7 +24,8 @@ using namespace scal;
 
 namespace {
 
-constexpr int CT = 128;  // threads per block
+constexpr int CT = 32;  // threads per block: one orbital per thread, small blocks so that
+                         // a few thousand orbitals still spread over all SMs (FP64-bound)
 
 // polynomial coefficients D_0 (Q) and D_1 (P) of the generating function
 template <int KP>
@@ -121,7 +122,7 @@ __device__ __forceinline__ void count_and_dos(const double* __restrict__ gsig, c
   *dNde = (2.0 / PI) * s * c1;
 }
 
-constexpr int RT2 = 256;
+constexpr int RT2 = 32;  // threads per block of the per-orbital FP64 kernels (see CT)
 
 // Bracket [min(a_inf - 2 b_inf) - 1e-3, max(a_inf + 2 b_inf) + 1e-3]; the
 // first iterate is the previous Fermi level when warm and inside, else the
@@ -624,7 +625,7 @@ __global__ void __launch_bounds__(CT) k_weights(WeightArgs A) {
 
 int red_grid2(int M) {
   int g = (M + RT2 - 1) / RT2;
-  return g < 1 ? 1 : (g > 1024 ? 1024 : g);
+  return g < 1 ? 1 : (g > 4096 ? 4096 : g);  // the context's partials hold 2 x 4096 values
 }
 
 }  // namespace

@@ -138,9 +138,15 @@ struct ScfArgs {
   double* m_new;       // [n]
   double* onsite;      // [S][n][norb] (rebuilt)
   float* onsite32;
-  double* red;         // partials
+  double* red;         // partials [grid][64]
   unsigned* counter;
   double* result;      // [4]: max|res|, max|dm|, converged, mean
+  int mixer;           // 0 linear, 1 Anderson
+  int hist;            // Anderson history depth (<= 8)
+  int it;              // iteration index of this update (0-based)
+  double* hx;          // [(hist+1)][ncomp*n] iterates
+  double* hf;          // [(hist+1)][ncomp*n] preconditioned residuals
+  double* gamma;       // [hist] least-squares coefficients
 };
 int launch_scf_residual(const ScfArgs& a, cudaStream_t s);
 int launch_scf_apply(const ScfArgs& a, cudaStream_t s);

@@ -128,10 +128,32 @@ __global__ void __launch_bounds__(RT) k_fermi_round(int M, const double* __restr
 }
 
 // ------------------------------------------------------------ SCF
+// Self-consistency of the onsite levels (local charge neutrality, Eq.
+// BOP_LCN, per atom; collinear Stoner moments, Eq. onsite_NCM).  With the
+// preconditioned residual of atom i
+//   F_delta = eta (N_i - N0) / max(n_i(E_F), dos_floor),   F_m = m_mix (m_out - m),
+// linear mixing is x_{k+1} = x_k + F_k.  Anderson mixing (type-II Broyden)
+// over the last h iterations uses dF_j = F_{j+1} - F_j, dX_j = x_{j+1} - x_j:
+//   gamma = argmin | F_k - sum_j gamma_j dF_j |,
+//   x_{k+1} = x_k + F_k - sum_j gamma_j (dX_j + dF_j).
+// The onsite shifts keep zero mean (the gauge fixed by E_F).
+constexpr int NPAR = 64;  // partial sums per block: 3 + h(h+1)/2 + 2h + 1 <= 64 for h <= 8
+
+__device__ __forceinline__ int hslot(int it, int S1) { return ((it % S1) + S1) % S1; }
+
 __global__ void __launch_bounds__(RT) k_scf_residual(ScfArgs A) {
-  __shared__ double sh[RT / 32];
+  __shared__ double sh[NPAR][RT / 32];
   __shared__ bool last;
-  double mres = 0.0, mdm = 0.0, sd = 0.0;
+  const int H = A.hist, S1 = H + 1;
+  const int h = A.mixer == 1 ? (A.it < H ? A.it : H) : 0;
+  const int slot = hslot(A.it, S1);
+  const int nA = h * (h + 1) / 2;  // A_jl, j <= l
+  // acc: [0] max|res| [1] max|dm| [2] sum F_delta (or sum delta_new) [3..3+nA) A
+  //      [3+nA .. 3+nA+h) b_j   [3+nA+h .. 3+nA+2h) sum dF_j (delta part)
+  const int nv = 3 + nA + 2 * h;
+  double acc[NPAR];
+  for (int q = 0; q < NPAR; q++) acc[q] = 0.0;
+  const int ncomp = A.mode == 2 ? 2 : 1;
   for (int i = blockIdx.x * RT + threadIdx.x; i < A.n; i += gridDim.x * RT) {
     double Ni = 0.0, di = 0.0;
     for (int v = 0; v < A.n_spin; v++)
@@ -142,66 +164,159 @@ __global__ void __launch_bounds__(RT) k_scf_residual(ScfArgs A) {
       }
     Ni *= A.spin_factor;
     di *= A.spin_factor;
-    double res = Ni - A.n0;
-    double dn = A.delta[i] + A.eta * res / fmax(di, A.dos_floor);
-    A.delta_new[i] = dn;
-    sd += dn;
-    mres = fmax(mres, fabs(res));
+    const double res = Ni - A.n0;
+    const double Fd = A.eta * res / fmax(di, A.dos_floor);
+    acc[0] = fmax(acc[0], fabs(res));
+    double Fm = 0.0;
     if (A.mode == 2) {
       double mo = 0.0;
-      for (int a = 0; a < A.norb; a++)
-        mo += A.N[(size_t)i * A.norb + a] - A.N[((size_t)A.n + i) * A.norb + a];
-      mdm = fmax(mdm, fabs(mo - A.m[i]));
-      A.m_new[i] = (1.0 - A.m_mix) * A.m[i] + A.m_mix * mo;
+      for (int a = 0; a < A.norb; a++) mo += A.N[(size_t)i * A.norb + a] - A.N[((size_t)A.n + i) * A.norb + a];
+      acc[1] = fmax(acc[1], fabs(mo - A.m[i]));
+      Fm = A.m_mix * (mo - A.m[i]);
+    }
+    if (A.mixer == 0) {
+      const double dn = A.delta[i] + Fd;
+      A.delta_new[i] = dn;
+      acc[2] += dn;
+      if (A.mode == 2) A.m_new[i] = A.m[i] + Fm;
+      continue;
+    }
+    const size_t n2 = (size_t)A.n * ncomp;
+    for (int c = 0; c < ncomp; c++) {
+      const size_t idx = (size_t)c * A.n + i;
+      const double fk = c == 0 ? Fd : Fm;
+      A.hx[(size_t)slot * n2 + idx] = c == 0 ? A.delta[i] : A.m[i];
+      A.hf[(size_t)slot * n2 + idx] = fk;
+      double df[8];
+      for (int j = 0; j < h; j++) {
+        const int s0 = hslot(A.it - h + j, S1), s1 = hslot(A.it - h + j + 1, S1);
+        const double f1 = (j == h - 1) ? fk : A.hf[(size_t)s1 * n2 + idx];
+        df[j] = f1 - A.hf[(size_t)s0 * n2 + idx];
+      }
+      int q = 3;
+      for (int j = 0; j < h; j++)
+        for (int l = j; l < h; l++) acc[q++] += df[j] * df[l];
+      for (int j = 0; j < h; j++) acc[3 + nA + j] += df[j] * fk;
+      if (c == 0) {
+        acc[2] += fk;
+        for (int j = 0; j < h; j++) acc[3 + nA + h + j] += df[j];
+      }
     }
   }
-  // max reductions via the same shuffle tree
-  for (int o = 16; o > 0; o >>= 1) {
-    mres = fmax(mres, __shfl_xor_sync(0xffffffffu, mres, o));
-    mdm = fmax(mdm, __shfl_xor_sync(0xffffffffu, mdm, o));
+  // block reduction: max for [0], [1], sums for the rest
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = 0; q < nv; q++) {
+    double v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = q < 2 ? fmax(v, w) : v + w;
+    }
+    if (lane == 0) sh[q][wid] = v;
   }
-  __shared__ double shm[2][RT / 32];
-  if ((threadIdx.x & 31) == 0) {
-    shm[0][threadIdx.x >> 5] = mres;
-    shm[1][threadIdx.x >> 5] = mdm;
-  }
-  double bs = block_sum<RT>(sd, sh);
+  __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int q = 0; q < RT / 32; q++) {
-      a = fmax(a, shm[0][q]);
-      b = fmax(b, shm[1][q]);
+    for (int q = 0; q < nv; q++) {
+      double v = q < 2 ? 0.0 : 0.0;
+      for (int w = 0; w < RT / 32; w++) v = q < 2 ? fmax(v, sh[q][w]) : v + sh[q][w];
+      A.red[(size_t)NPAR * blockIdx.x + q] = v;
     }
-    A.red[3 * blockIdx.x] = a;
-    A.red[3 * blockIdx.x + 1] = b;
-    A.red[3 * blockIdx.x + 2] = bs;
     __threadfence();
     last = atomicAdd(A.counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    volatile double* p = A.red;
-    double a = 0.0, b = 0.0, s = 0.0;
-    for (unsigned q = 0; q < gridDim.x; q++) {
-      a = fmax(a, p[3 * q]);
-      b = fmax(b, p[3 * q + 1]);
-      s += p[3 * q + 2];
-    }
-    bool conv = a < A.tol && (A.mode != 2 || b < 10.0 * A.tol);
-    A.result[0] = a;
-    A.result[1] = b;
-    A.result[2] = conv ? 1.0 : 0.0;
-    A.result[3] = s / A.n;
-    *A.counter = 0;
+  if (!(last && threadIdx.x == 0)) return;
+  volatile double* p = A.red;
+  double tot[NPAR];
+  for (int q = 0; q < nv; q++) {
+    double v = 0.0;
+    for (unsigned b = 0; b < gridDim.x; b++) v = q < 2 ? fmax(v, p[(size_t)NPAR * b + q]) : v + p[(size_t)NPAR * b + q];
+    tot[q] = v;
   }
+  const bool conv = tot[0] < A.tol && (A.mode != 2 || tot[1] < 10.0 * A.tol);
+  A.result[0] = tot[0];
+  A.result[1] = tot[1];
+  A.result[2] = conv ? 1.0 : 0.0;
+  if (A.mixer == 0) {
+    A.result[3] = tot[2] / A.n;  // mean of delta_new
+  } else {
+    // normal equations of the least-squares problem, Gaussian elimination
+    double G[8][9];
+    double dmax = 0.0;
+    int q = 3;
+    for (int j = 0; j < h; j++)
+      for (int l = j; l < h; l++) {
+        G[j][l] = G[l][j] = tot[q++];
+        if (j == l) dmax = fmax(dmax, tot[q - 1]);
+      }
+    for (int j = 0; j < h; j++) {
+      G[j][h] = tot[3 + nA + j];
+      G[j][j] += 1e-12 * dmax + 1e-300;
+    }
+    bool ok = true;
+    for (int c = 0; c < h && ok; c++) {
+      int pr = c;
+      for (int r = c + 1; r < h; r++)
+        if (fabs(G[r][c]) > fabs(G[pr][c])) pr = r;
+      if (!(fabs(G[pr][c]) > 0.0)) {
+        ok = false;
+        break;
+      }
+      if (pr != c)
+        for (int k = 0; k <= h; k++) {
+          double t = G[c][k];
+          G[c][k] = G[pr][k];
+          G[pr][k] = t;
+        }
+      for (int r = c + 1; r < h; r++) {
+        const double f = G[r][c] / G[c][c];
+        for (int k = c; k <= h; k++) G[r][k] -= f * G[c][k];
+      }
+    }
+    double gam[8];
+    for (int j = h - 1; j >= 0; j--) {
+      double v = ok ? G[j][h] : 0.0;
+      if (ok) {
+        for (int k = j + 1; k < h; k++) v -= G[j][k] * gam[k];
+        v /= G[j][j];
+      }
+      gam[j] = isfinite(v) ? v : 0.0;
+    }
+    double mean = tot[2];
+    for (int j = 0; j < h; j++) {
+      A.gamma[j] = gam[j];
+      mean -= gam[j] * tot[3 + nA + h + j];
+    }
+    A.result[3] = mean / A.n;  // mean of the updated delta before the gauge shift
+  }
+  *A.counter = 0;
 }
 
 __global__ void __launch_bounds__(RT) k_scf_apply(ScfArgs A) {
   if (A.result[2] != 0.0) return;
   const double mean = A.result[3];
+  const int H = A.hist, S1 = H + 1;
+  const int h = A.mixer == 1 ? (A.it < H ? A.it : H) : 0;
+  const int ncomp = A.mode == 2 ? 2 : 1;
+  const size_t n2 = (size_t)A.n * ncomp;
   for (int i = blockIdx.x * RT + threadIdx.x; i < A.n; i += gridDim.x * RT) {
-    A.delta[i] = A.delta_new[i] - mean;
-    if (A.mode == 2) A.m[i] = A.m_new[i];
+    if (A.mixer == 0) {
+      A.delta[i] = A.delta_new[i] - mean;
+      if (A.mode == 2) A.m[i] = A.m_new[i];
+      continue;
+    }
+    for (int c = 0; c < ncomp; c++) {
+      const size_t idx = (size_t)c * A.n + i;
+      const int sk = hslot(A.it, S1);
+      double x = A.hx[(size_t)sk * n2 + idx] + A.hf[(size_t)sk * n2 + idx];
+      for (int j = 0; j < h; j++) {
+        const int s0 = hslot(A.it - h + j, S1), s1 = hslot(A.it - h + j + 1, S1);
+        const double dX = A.hx[(size_t)s1 * n2 + idx] - A.hx[(size_t)s0 * n2 + idx];
+        const double dF = A.hf[(size_t)s1 * n2 + idx] - A.hf[(size_t)s0 * n2 + idx];
+        x -= A.gamma[j] * (dX + dF);
+      }
+      if (c == 0) A.delta[i] = x - mean;
+      else A.m[i] = x;
+    }
   }
 }
 

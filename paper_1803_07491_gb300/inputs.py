@@ -89,6 +89,8 @@ class RunParams:
     m_mix: float = 0.3
     m0: float = 2.0
     dos_floor: float = 0.1
+    mixer: str = "anderson"   # linear | anderson (type-II Broyden)
+    mix_history: int = 6
 
 
 @dataclass
