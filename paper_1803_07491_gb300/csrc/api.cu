@@ -15,7 +15,7 @@
 #include "../../include/bopgb.h"
 #include "kernels.h"
 
-int moments_columns(int norb, int cap, int fp64);
+int moments_columns(int norb, int cap_sum, int fp64);
 int adjoint_columns(int norb);
 
 constexpr int FERMI_ROUNDS_COLD = 16;  // Newton rounds launched for a cold start
@@ -59,13 +59,13 @@ struct bop_ctx {
   int n = 0;
   long long E = 0, nb = 0, nsite = 0, nadj = 0;
   Geometry g;
-  int maxlev[BOP_MAX_K + 1];
+  int maxlev[BOP_MAX_K + 2];  // largest |C_k| per level, then the largest adjacency
   bool built = false, energized = false, weighted = false;
   // buffers
   DBuf pos, cell_of, cell_count, cell_start, cell_fill, cell_atoms, deg, row_ptr, col, img, flag, bond_scan,
       bond_of_edge, bond_atoms, bond_img, bond_d, H64, H32, frac;
   DBuf hkeys, hvals, skeys, sslot, scount;
-  DBuf level_end, atom_nsite, atom_nadj, max_level, site_off, adj_base, site_atom, site_img, adj_off, adj;
+  DBuf level_end, atom_nsite, atom_nadj, max_level, site_off, adj_base, site_atom, site_img, adj_off, adj, lvcnt;
   DBuf onsite, onsite32, delta, mval, delta_new, m_new, mu, a, b, nlev, a_inf, b_inf, gsig, D, gjack;
   DBuf N, U, dos, fstate, partials, counter, result, e_total, lam, e_atom;
   DBuf w, zscr, adjscr, Hbar, Ebar, ginv;
@@ -244,7 +244,7 @@ int build_clusters(bop_ctx* c, cudaStream_t s) {
   CKS(ensure(c, c->atom_nadj, sizeof(int) * (n + 1)));
   CK(cudaMemsetAsync(c->atom_nsite.p, 0, sizeof(int) * (n + 1), s));
   CK(cudaMemsetAsync(c->atom_nadj.p, 0, sizeof(int) * (n + 1), s));
-  CKS(ensure(c, c->max_level, sizeof(int) * (K + 1)));
+  CKS(ensure(c, c->max_level, sizeof(int) * (K + 2)));
   CKS(ensure(c, c->site_off, sizeof(long long) * (n + 1)));
   CKS(ensure(c, c->adj_base, sizeof(long long) * (n + 1)));
   for (int attempt = 0; attempt < 4; attempt++) {
@@ -258,7 +258,7 @@ int build_clusters(bop_ctx* c, cudaStream_t s) {
     CKS(ensure(c, c->sslot, sizeof(int) * (size_t)grid * maxs));
     CKS(ensure(c, c->scount, sizeof(int) * (size_t)grid * maxs));
     CK(cudaMemsetAsync(c->hkeys.p, 0xff, sizeof(unsigned long long) * (size_t)grid * hcap, s));
-    CK(cudaMemsetAsync(c->max_level.p, 0, sizeof(int) * (K + 1), s));
+    CK(cudaMemsetAsync(c->max_level.p, 0, sizeof(int) * (K + 2), s));
     ClusterScratch sc{P<unsigned long long>(c->hkeys), P<int>(c->hvals), P<unsigned long long>(c->skeys),
                       P<int>(c->sslot), P<int>(c->scount), hcap, maxs, newcap};
     ClusterOut out{};
@@ -288,7 +288,7 @@ int build_clusters(bop_ctx* c, cudaStream_t s) {
     long long tot[2];
     CK(cudaMemcpyAsync(&tot[0], P<long long>(c->site_off) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&tot[1], P<long long>(c->adj_base) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(c->maxlev, c->max_level.p, sizeof(int) * (K + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->maxlev, c->max_level.p, sizeof(int) * (K + 2), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     c->nsite = tot[0];
     c->nadj = tot[1];
@@ -296,12 +296,14 @@ int build_clusters(bop_ctx* c, cudaStream_t s) {
     CKS(ensure(c, c->site_img, 3 * c->nsite));
     CKS(ensure(c, c->adj_off, sizeof(long long) * (c->nsite + 1)));
     CKS(ensure(c, c->adj, sizeof(int2) * c->nadj));
+    CKS(ensure(c, c->lvcnt, sizeof(unsigned long long) * c->nsite));
     out.site_off = P<long long>(c->site_off);
     out.adj_base = P<long long>(c->adj_base);
     out.site_atom = P<int>(c->site_atom);
     out.site_img = P<signed char>(c->site_img);
     out.adj_off = P<long long>(c->adj_off);
     out.adj = P<int2>(c->adj);
+    out.lvcnt = P<unsigned long long>(c->lvcnt);
     CKS(ensure(c, c->nprod, sizeof(unsigned long long)));
     CK(cudaMemsetAsync(c->nprod.p, 0, sizeof(unsigned long long), s));
     out.n_products = P<unsigned long long>(c->nprod);
@@ -320,7 +322,7 @@ int build_clusters(bop_ctx* c, cudaStream_t s) {
 
 ClusterView cview(bop_ctx* c) {
   return ClusterView{P<long long>(c->site_off), P<int>(c->level_end), P<int>(c->site_atom),
-                     P<long long>(c->adj_off), P<int2>(c->adj), c->K};
+                     P<long long>(c->adj_off), P<int2>(c->adj), P<unsigned long long>(c->lvcnt), c->K};
 }
 
 int size_state(bop_ctx* c) {
@@ -362,7 +364,13 @@ int run_moments(bop_ctx* c, const double* onsite_dev, double* mu, cudaStream_t s
   a.n_spin = c->S;
   a.norb = c->norb;
   a.n_mom = c->n_mom;
-  a.cap = c->maxlev[c->K - 1] > 0 ? c->maxlev[c->K - 1] : 1;
+  a.max_sites = c->maxlev[c->K] > 0 ? c->maxlev[c->K] : 1;
+  a.max_adj = c->maxlev[c->K + 1] > 0 ? c->maxlev[c->K + 1] : 1;
+  a.cap_even = a.cap_odd = 1;
+  for (int k = 0; k < c->K; k++) {  // level K is never stored
+    int& cap = (k & 1) ? a.cap_odd : a.cap_even;
+    if (c->maxlev[k] > cap) cap = c->maxlev[k];
+  }
   a.mu = mu;
   Region R(c, PK_MOMENTS, 1, s);
   int r = launch_moments(a, c->fp64, s);
@@ -490,7 +498,7 @@ int bop_destroy(bop_ctx* c) {
                   &c->row_ptr, &c->col, &c->img, &c->flag, &c->bond_scan, &c->bond_of_edge, &c->bond_atoms,
                   &c->bond_img, &c->bond_d, &c->H64, &c->H32, &c->frac, &c->hkeys, &c->hvals, &c->skeys,
                   &c->sslot, &c->scount, &c->level_end, &c->atom_nsite, &c->atom_nadj, &c->max_level,
-                  &c->site_off, &c->adj_base, &c->site_atom, &c->site_img, &c->adj_off, &c->adj, &c->onsite,
+                  &c->site_off, &c->adj_base, &c->site_atom, &c->site_img, &c->adj_off, &c->adj, &c->lvcnt, &c->onsite,
                   &c->onsite32, &c->delta, &c->mval, &c->delta_new, &c->m_new, &c->mu, &c->a, &c->b, &c->nlev,
                   &c->a_inf, &c->b_inf, &c->gsig, &c->D, &c->gjack, &c->N, &c->U, &c->dos, &c->fstate,
                   &c->partials, &c->counter, &c->result, &c->e_total, &c->lam, &c->e_atom, &c->w, &c->zscr,

@@ -148,19 +148,17 @@ __global__ void __launch_bounds__(RT2) k_bracket_warm(int M, const double* __res
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = smn[0];
+    partials[2 * blockIdx.x] = -smn[0];  // negated: both halves reduce with max
     partials[2 * blockIdx.x + 1] = smx[0];
     __threadfence();
     last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    volatile double* p = partials;
-    double lo = 1e300, hi = -1e300;
-    for (unsigned q = 0; q < gridDim.x; q++) {
-      lo = fmin(lo, p[2 * q]);
-      hi = fmax(hi, p[2 * q + 1]);
-    }
+  if (!last) return;
+  __shared__ double fr[RT2 / 32 + 1];
+  double lo = -final_reduce<RT2>(partials, 2, 0, gridDim.x, true, fr);  // stored as -min below
+  double hi = final_reduce<RT2>(partials, 2, 1, gridDim.x, true, fr);
+  if (threadIdx.x == 0) {
     lo -= 1e-3;
     hi += 1e-3;
     const double prev = st->ef;
@@ -205,13 +203,11 @@ __global__ void __launch_bounds__(RT2) k_fermi_newton(int M, const double* __res
     last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    volatile double* p = partials;
-    double tN = 0.0, tD = 0.0;
-    for (unsigned q = 0; q < gridDim.x; q++) {
-      tN += p[2 * q];
-      tD += p[2 * q + 1];
-    }
+  if (!last) return;
+  __shared__ double fr[RT2 / 32 + 1];
+  const double tN = final_reduce<RT2>(partials, 2, 0, gridDim.x, false, fr);
+  const double tD = final_reduce<RT2>(partials, 2, 1, gridDim.x, false, fr);
+  if (threadIdx.x == 0) {
     const double f = sfac * tN - target, fp = sfac * tD;
     st->iters += 1;
     if (f == 0.0) {
@@ -325,13 +321,11 @@ __global__ void __launch_bounds__(RT2) k_ef_response2(int M, int ne, const doubl
     last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    volatile double* p = partials;
-    double tU = 0.0, tN = 0.0;
-    for (unsigned q = 0; q < gridDim.x; q++) {
-      tU += p[2 * q];
-      tN += p[2 * q + 1];
-    }
+  if (!last) return;
+  __shared__ double fr[RT2 / 32 + 1];
+  const double tU = final_reduce<RT2>(partials, 2, 0, gridDim.x, false, fr);
+  const double tN = final_reduce<RT2>(partials, 2, 1, gridDim.x, false, fr);
+  if (threadIdx.x == 0) {
     lam[0] = tN > 0.0 ? tU / tN : 0.0;
     lam[1] = tU;
     lam[2] = tN;

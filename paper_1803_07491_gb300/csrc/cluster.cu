@@ -219,6 +219,7 @@ k_cluster(int n, int K, const long long* __restrict__ row_ptr, const int* __rest
         if (threadIdx.x == 0) {
           out.atom_nsite[atom] = nsite;
           out.atom_nadj[atom] = tot;
+          atomicMax(&out.max_level[K + 1], tot);  // largest adjacency
         }
         for (int k = threadIdx.x; k <= K; k += blockDim.x) {
           out.level_end[(size_t)atom * (K + 1) + k] = s_lev[k];
@@ -260,6 +261,14 @@ k_cluster(int n, int K, const long long* __restrict__ row_ptr, const int* __rest
           }
           long long o = a0 + scnt[t];
           for (int x = 0; x < c; x++) out.adj[o + x] = ent[x];
+          // byte k: entries whose site lies in C_k (the gather of level k+1)
+          unsigned long long lc = 0;
+          for (int k = 0; k < K; k++) {
+            unsigned cnt = 0;
+            while ((int)cnt < c && ent[cnt].x < s_lev[k]) cnt++;
+            lc |= (unsigned long long)cnt << (8 * k);
+          }
+          out.lvcnt[s0 + t] = lc;
           // forward levels k = max(lt, ls+1) .. K use the pair (t, s)
           int lt = 0;
           while (lt < K && t >= s_lev[lt]) lt++;

@@ -31,6 +31,7 @@ struct ClusterView {
   const int* site_atom;       // [S] atom of every site
   const long long* adj_off;   // [S+1] adjacency of every site
   const int2* adj;            // {neighbour site (local index), bond}, ascending site
+  const unsigned long long* lvcnt;  // [S] byte k = entries with site < level_end[k]
   int K;
 };
 

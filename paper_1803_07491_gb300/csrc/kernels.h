@@ -30,7 +30,7 @@ struct ClusterOut {
   int* level_end;        // [n][K+1]
   int* atom_nsite;       // [n]  (pass 1)
   int* atom_nadj;        // [n]  (pass 1)
-  int* max_level;        // [K+1] largest |C_k| over atoms (pass 1)
+  int* max_level;        // [K+2] largest |C_k| over atoms, then the largest adjacency (pass 1)
   const long long* site_off;  // [n+1] (pass 2 input)
   const long long* adj_base;  // [n+1] (pass 2 input)
   int* site_atom;        // [S]
@@ -38,6 +38,7 @@ struct ClusterOut {
   long long* adj_off;    // [S+1]
   int2* adj;             // [A]
   unsigned long long* n_products;  // block products of one moments pass (pass 2)
+  unsigned long long* lvcnt;       // [S] per-level entry counts (pass 2)
 };
 
 namespace bopk {
@@ -67,7 +68,10 @@ struct MomentsArgs {
   int HS;
   const void* onsite;  // float or double [S][n][norb]
   int n, n_spin, norb, n_mom;
-  int cap;             // largest stored level |C_{K-1}| over atoms
+  int cap_even;        // largest stored even level |C_k| (k < K) over atoms
+  int cap_odd;         // largest stored odd level |C_k| (k < K) over atoms
+  int max_sites;       // largest cluster |C_K|
+  int max_adj;         // largest adjacency of one cluster
   double* mu;          // [S][n][norb][n_mom]
 };
 int launch_moments(const MomentsArgs& a, int fp64, cudaStream_t s);

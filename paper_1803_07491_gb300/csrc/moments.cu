@@ -115,80 +115,238 @@ __device__ __forceinline__ void gather_row(const ClusterView& cv, const T* __res
 }
 
 // ------------------------------------------------------------------ forward
-template <typename T, int NO, int NC>
-__global__ void __launch_bounds__(MOM_THREADS)
-k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_mom,
-          int cap, double* __restrict__ mu) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* bufA = reinterpret_cast<T*>(smem_raw);
-  T* bufB = bufA + (size_t)cap * NO * NC;
-  __shared__ T red[2 * NC][MOM_THREADS / 32];
-  const int K = cv.K;
-  const int w = blockIdx.x;
-  const int grp = (NC == NO) ? 0 : (w % NO);
-  const int sa = (NC == NO) ? w : (w / NO);
-  const int spin = sa / n, atom = sa % n;
-  const long long s0 = cv.site_off[atom];
-  const int* lev = cv.level_end + (size_t)atom * (K + 1);
-  const int* satom = cv.site_atom + s0;
-  const long long* aoff = cv.adj_off + s0;
-  const T* E = onsite + (size_t)spin * n * NO;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-
-  for (int q = tid; q < NO * NC; q += blockDim.x) {
-    int r = q / NC, c = q % NC;
-    bufA[q] = (NC == NO) ? T(r == c ? 1 : 0) : T(r == grp ? 1 : 0);
+// Shared-memory row of one site: NO x NC values padded to 16-byte multiples
+// so that a row is read with vector loads.
+template <typename T, int N>
+struct Row {
+  static constexpr int PS = (sizeof(T) == 4) ? ((N + 3) / 4) * 4 : ((N + 1) / 2) * 2;
+};
+template <typename T, int N, int PS>
+__device__ __forceinline__ void load_row(const T* __restrict__ p, T x[N]) {
+  if constexpr (N == 1) {
+    x[0] = p[0];
+  } else if constexpr (sizeof(T) == 4) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int v = 0; v < PS / 4; v++) {
+      float4 w = q[v];
+      if (4 * v + 0 < N) x[4 * v + 0] = w.x;
+      if (4 * v + 1 < N) x[4 * v + 1] = w.y;
+      if (4 * v + 2 < N) x[4 * v + 2] = w.z;
+      if (4 * v + 3 < N) x[4 * v + 3] = w.w;
+    }
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int v = 0; v < PS / 2; v++) {
+      double2 w = q[v];
+      if (2 * v + 0 < N) x[2 * v + 0] = w.x;
+      if (2 * v + 1 < N) x[2 * v + 1] = w.y;
+    }
   }
-  __syncthreads();
-  T* prev = bufA;
-  T* cur = bufB;
-  double* out = mu + ((size_t)sa * NO + grp) * n_mom;  // column c adds c*n_mom when NC == NO
-  if (tid < NC) out[(size_t)tid * n_mom] = 1.0;
-  for (int k = 1; k <= K; k++) {
-    const int nrow = lev[k], ncol = lev[k - 1];
-    T d1[NC], d2[NC];
+}
+
+template <typename T, int NO>
+__device__ __forceinline__ void load_bond(const T* __restrict__ h, T u[NO == 1 ? 1 : 16]) {
+  if constexpr (NO == 1) {
+    u[0] = __ldg(h);
+  } else {
+    Blk<T>::load(h, u);
+  }
+}
+
+// acc += B x for one symmetric block (unique elements u) and a site row x
+template <typename T, int NO, int NC>
+__device__ __forceinline__ void block_fma(const T* u, const T* x, T acc[NO][NC]) {
+  if constexpr (NO == 1) {
 #pragma unroll
-    for (int c = 0; c < NC; c++) d1[c] = d2[c] = T(0);
-    for (int t = tid; t < nrow; t += blockDim.x) {
-      T acc[NO][NC];
-      gather_row<T, NO, NC>(cv, H, HS, E, satom, aoff, t, ncol, prev, acc);
-      if (t < ncol) {
+    for (int c = 0; c < NC; c++) acc[0][c] += u[0] * x[c];
+  } else {
+#pragma unroll
+    for (int r = 0; r < NO; r++)
+#pragma unroll
+      for (int g = 0; g < NO; g++) {
+        const T h = u[U5(r, g)];
+#pragma unroll
+        for (int c = 0; c < NC; c++) acc[r][c] += h * x[g * NC + c];
+      }
+  }
+}
+
+// acc += sum over the first cnt adjacency entries of t of B_ts x[s]; the
+// next entry and its block are fetched while the current one is applied.
+template <typename T, int NO, int NC, int PS>
+__device__ __forceinline__ void gather_pf(const int2* __restrict__ adj, long long q0, int cnt,
+                                          const T* __restrict__ H, int HS, const T* __restrict__ x,
+                                          T acc[NO][NC]) {
+  if (cnt <= 0) return;
+  constexpr int HB = NO == 1 ? 1 : 16;
+  int2 en = __ldg(adj + q0);
+  T hb[HB];
+  load_bond<T, NO>(H + (size_t)en.y * HS, hb);
+  for (int e = 0; e < cnt; e++) {
+    const int s = en.x;
+    T hc[HB];
+#pragma unroll
+    for (int q = 0; q < HB; q++) hc[q] = hb[q];
+    if (e + 1 < cnt) {
+      en = __ldg(adj + q0 + e + 1);
+      load_bond<T, NO>(H + (size_t)en.y * HS, hb);
+    }
+    T xs[NO * NC];
+    load_row<T, NO * NC, PS>(x + (size_t)s * PS, xs);
+    block_fma<T, NO, NC>(hc, xs, acc);
+  }
+}
+
+// Forward kernel.  A persistent CTA takes a run of consecutive work items
+// (spin, atom[, alpha]); neighbouring atoms share most of their clusters'
+// blocks, which then come from L1.  For each item the atom's adjacency,
+// per-site offsets, level counts and site atoms are staged in shared memory
+// (one coalesced copy) when they fit, so that the edge loop only waits for
+// the bond blocks, which are fetched one edge ahead.  Each thread computes
+// all NC columns of one site (NO x NO x NC multiply-adds per edge); Psi
+// rows are padded to 16-byte multiples and kept in two exactly sized
+// buffers (even and odd levels).
+constexpr int FWD_THREADS = 192;
+
+struct FwdSmem {
+  int cap_even, cap_odd, max_sites, max_adj;
+  bool stage;
+};
+
+template <typename T, int NO, int NC>
+__global__ void __launch_bounds__(FWD_THREADS, sizeof(T) == 4 ? 2 : 1)
+k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_mom,
+          FwdSmem L, int n_items, int chunk, double* __restrict__ mu) {
+  constexpr int N = NO * NC;
+  constexpr int PS = (N == 1) ? 1 : Row<T, N>::PS;
+  constexpr int HB = NO == 1 ? 1 : 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* buf[2];
+  buf[0] = reinterpret_cast<T*>(smem_raw);
+  buf[1] = buf[0] + (size_t)L.cap_even * PS;
+  unsigned char* tail = reinterpret_cast<unsigned char*>(buf[1] + (size_t)L.cap_odd * PS);
+  int2* s_adj = reinterpret_cast<int2*>(tail);
+  unsigned long long* s_lvc = reinterpret_cast<unsigned long long*>(s_adj + (L.stage ? L.max_adj : 0));
+  int* s_aoff = reinterpret_cast<int*>(s_lvc + (L.stage ? L.max_sites : 0));
+  int* s_atom = s_aoff + (L.stage ? L.max_sites + 1 : 0);
+  __shared__ T red[2 * NC][FWD_THREADS / 32];
+  const int K = cv.K;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int w0 = blockIdx.x * chunk, w1 = min(n_items, w0 + chunk);
+  for (int w = w0; w < w1; w++) {
+    const int grp = (NC == NO) ? 0 : (w % NO);
+    const int sa = (NC == NO) ? w : (w / NO);
+    const int spin = sa / n, atom = sa % n;
+    const long long s0 = cv.site_off[atom];
+    const int* lev = cv.level_end + (size_t)atom * (K + 1);
+    const int nsite = lev[K];
+    const long long abase = cv.adj_off[s0];
+    const int2* adj = cv.adj + abase;
+    const unsigned long long* lvc = cv.lvcnt + s0;
+    const int* satom = cv.site_atom + s0;
+    const T* E = onsite + (size_t)spin * n * NO;
+    if (L.stage) {
+      const int nadj = (int)(cv.adj_off[s0 + nsite] - abase);
+      for (int q = tid; q < nadj; q += FWD_THREADS) s_adj[q] = __ldg(adj + q);
+      for (int q = tid; q <= nsite; q += FWD_THREADS) s_aoff[q] = (int)(cv.adj_off[s0 + q] - abase);
+      for (int q = tid; q < nsite; q += FWD_THREADS) {
+        s_lvc[q] = lvc[q];
+        s_atom[q] = satom[q];
+      }
+    }
+    for (int q = tid; q < N; q += FWD_THREADS) {
+      const int r = q / NC, c = q % NC;
+      buf[0][q] = (NC == NO) ? T(r == c ? 1 : 0) : T(r == grp ? 1 : 0);
+    }
+    __syncthreads();
+    double* out = mu + ((size_t)sa * NO + grp) * n_mom;
+    if (tid < NC) out[(size_t)tid * n_mom] = 1.0;
+    for (int k = 1; k <= K; k++) {
+      const int nrow = lev[k], ncol = lev[k - 1];
+      const T* prev = buf[(k - 1) & 1];
+      T* cur = buf[k & 1];
+      T d1[NC], d2[NC];
+#pragma unroll
+      for (int c = 0; c < NC; c++) d1[c] = d2[c] = T(0);
+      for (int t = tid; t < nrow; t += FWD_THREADS) {
+        T acc[NO][NC];
+        const bool in_prev = t < ncol;
+        T pt[N];
+        if (in_prev) {
+          load_row<T, N, PS>(prev + (size_t)t * PS, pt);
+          const T* e = E + (size_t)(L.stage ? s_atom[t] : satom[t]) * NO;
+#pragma unroll
+          for (int r = 0; r < NO; r++) {
+            const T er = e[r];
+#pragma unroll
+            for (int c = 0; c < NC; c++) acc[r][c] = er * pt[r * NC + c];
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < NO; r++)
+#pragma unroll
+            for (int c = 0; c < NC; c++) acc[r][c] = T(0);
+        }
+        const unsigned long long lc = L.stage ? s_lvc[t] : lvc[t];
+        const int cnt = (int)((lc >> (8 * (k - 1))) & 0xff);
+        if (cnt > 0) {
+          const int q0 = L.stage ? s_aoff[t] : (int)(cv.adj_off[s0 + t] - abase);
+          const int2* ent = L.stage ? s_adj + q0 : adj + q0;
+          int2 en = ent[0];
+          T hb[HB];
+          load_bond<T, NO>(H + (size_t)en.y * HS, hb);
+          for (int e = 0; e < cnt; e++) {
+            const int s = en.x;
+            T hc[HB];
+#pragma unroll
+            for (int q = 0; q < HB; q++) hc[q] = hb[q];
+            if (e + 1 < cnt) {
+              en = ent[e + 1];
+              load_bond<T, NO>(H + (size_t)en.y * HS, hb);
+            }
+            T xs[N];
+            load_row<T, N, PS>(prev + (size_t)s * PS, xs);
+            block_fma<T, NO, NC>(hc, xs, acc);
+          }
+        }
+        if (in_prev) {
+#pragma unroll
+          for (int r = 0; r < NO; r++)
+#pragma unroll
+            for (int c = 0; c < NC; c++) d1[c] += pt[r * NC + c] * acc[r][c];
+        }
 #pragma unroll
         for (int r = 0; r < NO; r++)
 #pragma unroll
-          for (int c = 0; c < NC; c++) d1[c] += prev[(t * NO + r) * NC + c] * acc[r][c];
+          for (int c = 0; c < NC; c++) d2[c] += acc[r][c] * acc[r][c];
+        if (k < K) {
+          T* dst = cur + (size_t)t * PS;
+#pragma unroll
+          for (int r = 0; r < NO; r++)
+#pragma unroll
+            for (int c = 0; c < NC; c++) dst[r * NC + c] = acc[r][c];
+        }
       }
 #pragma unroll
-      for (int r = 0; r < NO; r++)
-#pragma unroll
-        for (int c = 0; c < NC; c++) d2[c] += acc[r][c] * acc[r][c];
-      if (k < K) {
-#pragma unroll
-        for (int r = 0; r < NO; r++)
-#pragma unroll
-          for (int c = 0; c < NC; c++) cur[(t * NO + r) * NC + c] = acc[r][c];
+      for (int c = 0; c < NC; c++) {
+        T a = warp_sum(d1[c]), b = warp_sum(d2[c]);
+        if (lane == 0) {
+          red[c][wid] = a;
+          red[NC + c][wid] = b;
+        }
       }
-    }
-#pragma unroll
-    for (int c = 0; c < NC; c++) {
-      T a = warp_sum(d1[c]), b = warp_sum(d2[c]);
-      if (lane == 0) {
-        red[c][wid] = a;
-        red[NC + c][wid] = b;
+      __syncthreads();
+      if (tid < 2 * NC) {
+        T acc = T(0);
+        for (int q = 0; q < FWD_THREADS / 32; q++) acc += red[tid][q];
+        const int c = tid % NC;
+        const int m = tid < NC ? 2 * k - 1 : 2 * k;
+        out[(size_t)c * n_mom + m] = (double)acc;
       }
+      __syncthreads();
     }
-    __syncthreads();
-    if (tid < 2 * NC) {
-      T acc = T(0);
-      for (int q = 0; q < (int)(blockDim.x >> 5); q++) acc += red[tid][q];
-      int c = tid % NC;
-      int m = tid < NC ? 2 * k - 1 : 2 * k;
-      out[(size_t)c * n_mom + m] = (double)acc;
-    }
-    __syncthreads();
-    T* sw = prev;
-    prev = cur;
-    cur = sw;
   }
 }
 
@@ -358,12 +516,34 @@ k_moments_adj(ClusterView cv, const T* __restrict__ H, int HS, const T* __restri
 
 template <typename T, int NO, int NC>
 int run_forward(const MomentsArgs& a, cudaStream_t s) {
-  size_t smem = (size_t)2 * a.cap * NO * NC * sizeof(T);
+  constexpr int N = NO * NC;
+  constexpr int PS = (N == 1) ? 1 : Row<T, N>::PS;
+  FwdSmem L{a.cap_even, a.cap_odd, a.max_sites, a.max_adj, true};
+  size_t psi = (size_t)(a.cap_even + a.cap_odd) * PS * sizeof(T);
+  size_t stage = (size_t)a.max_adj * 8 + (size_t)a.max_sites * 8 + (size_t)(a.max_sites + 1) * 4 +
+                 (size_t)a.max_sites * 4 + 16;
+  size_t smem = psi + stage;
+  // stage the adjacency only while two CTAs (FP32) still fit on an SM
+  const size_t budget = sizeof(T) == 4 ? 110 * 1024 : 200 * 1024;
+  if (smem > budget) {
+    L.stage = false;
+    smem = psi;
+  }
   if (smem > 227 * 1024) return -2;
   auto fn = k_moments<T, NO, NC>;
   if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int grid = a.n * a.n_spin * (NO / NC);
-  fn<<<grid, MOM_THREADS, smem, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n, a.n_mom, a.cap, a.mu);
+  const int n_items = a.n * a.n_spin * (NO / NC);
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, FWD_THREADS, smem);
+  if (per_sm < 1) per_sm = 1;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int slots = sms * per_sm;
+  const int chunk = (n_items + slots - 1) / slots;
+  const int grid = (n_items + chunk - 1) / chunk;
+  fn<<<grid, FWD_THREADS, smem, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n, a.n_mom, L, n_items,
+                                      chunk, a.mu);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -381,14 +561,14 @@ int run_adjoint(const AdjointArgs& a, cudaStream_t s) {
 
 // Column grouping: all 5 starting orbitals in one CTA when both Psi levels
 // fit in shared memory, one CTA per starting orbital otherwise.
-int moments_columns(int norb, int cap, int fp64) {
+int moments_columns(int norb, int cap_sum, int fp64) {
   if (norb == 1) return 1;
-  size_t bytes = (size_t)2 * cap * 5 * 5 * (fp64 ? 8 : 4);
+  size_t bytes = (size_t)cap_sum * 25 * (fp64 ? 8 : 4);
   return bytes <= 100 * 1024 ? 5 : 1;
 }
 
 int launch_moments(const MomentsArgs& a, int fp64, cudaStream_t s) {
-  int nc = moments_columns(a.norb, a.cap, fp64);
+  int nc = moments_columns(a.norb, a.cap_even + a.cap_odd, fp64);
   if (a.norb == 1) return fp64 ? run_forward<double, 1, 1>(a, s) : run_forward<float, 1, 1>(a, s);
   if (nc == 5) return fp64 ? run_forward<double, 5, 5>(a, s) : run_forward<float, 5, 5>(a, s);
   return fp64 ? run_forward<double, 5, 1>(a, s) : run_forward<float, 5, 1>(a, s);

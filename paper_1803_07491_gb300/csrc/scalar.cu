@@ -224,14 +224,11 @@ __global__ void __launch_bounds__(RT) k_scf_residual(ScfArgs A) {
     last = atomicAdd(A.counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!(last && threadIdx.x == 0)) return;
-  volatile double* p = A.red;
+  if (!last) return;
+  __shared__ double fr[RT / 32 + 1];
   double tot[NPAR];
-  for (int q = 0; q < nv; q++) {
-    double v = 0.0;
-    for (unsigned b = 0; b < gridDim.x; b++) v = q < 2 ? fmax(v, p[(size_t)NPAR * b + q]) : v + p[(size_t)NPAR * b + q];
-    tot[q] = v;
-  }
+  for (int q = 0; q < nv; q++) tot[q] = final_reduce<RT>(A.red, NPAR, q, gridDim.x, q < 2, fr);
+  if (threadIdx.x != 0) return;
   const bool conv = tot[0] < A.tol && (A.mode != 2 || tot[1] < 10.0 * A.tol);
   A.result[0] = tot[0];
   A.result[1] = tot[1];
@@ -358,10 +355,10 @@ __global__ void __launch_bounds__(RT) k_energy(int n, int norb, int n_spin, doub
     last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    volatile double* p = red;
-    double s = 0.0;
-    for (unsigned q = 0; q < gridDim.x; q++) s += p[q];
+  if (!last) return;
+  __shared__ double fr[RT / 32 + 1];
+  const double s = final_reduce<RT>(red, 1, 0, gridDim.x, false, fr);
+  if (threadIdx.x == 0) {
     *e_total = s;
     *counter = 0;
   }

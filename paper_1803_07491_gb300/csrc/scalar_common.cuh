@@ -114,4 +114,33 @@ __device__ inline double block_sum(double v, double* sh) {
 }
 
 constexpr int RT = 256;
+// Reduction of per-block partials by the last block of a grid: every thread
+// of that block reads a strided share of the partials (L2 loads), then a
+// fixed shuffle tree and a fixed cross-warp order.  Deterministic for a
+// given grid size.  All threads of the block must call it; every thread
+// receives the result.  sh: >= NT/32 + 1 doubles of shared memory.
+template <int NT>
+__device__ inline double final_reduce(const double* part, size_t stride, int q, int nblk, bool take_max,
+                                      double* sh) {
+  double v = take_max ? -1.0e300 : 0.0;
+  for (int b = threadIdx.x; b < nblk; b += NT) {
+    const double x = __ldcg(part + (size_t)b * stride + q);
+    v = take_max ? fmax(v, x) : v + x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = take_max ? fmax(v, w) : v + w;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = sh[0];
+    for (int w = 1; w < NT / 32; w++) t = take_max ? fmax(t, sh[w]) : t + sh[w];
+    sh[NT / 32] = t;
+  }
+  __syncthreads();
+  return sh[NT / 32];
+}
+
 }  // namespace scal
