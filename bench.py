@@ -36,7 +36,7 @@ FP32_SCF_TOL = 1e-5  # electrons: SCF tolerance with FP32 products (FP64 mode ke
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="d2000")
@@ -109,6 +109,23 @@ def algorithmic_flops(family: str, w, stats: dict, prof: dict, n_spin: int) -> f
     return None
 
 
+def aggregate(t_local_ms: float, units_local: int, world: int):
+    """Whole-job throughput: every rank's units over the slowest rank's time
+    (MAX over ranks of the device time).  Returns (value, t_max_ms)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_local_ms], dtype=torch.float64)
+    u = torch.tensor([float(units_local)], dtype=torch.float64)
+    if world > 1 and dist.is_initialized():
+        dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else None
+        if dev is not None:
+            t, u = t.to(dev), u.to(dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    t_max = float(t.item())
+    return float(u.item()) / (t_max / 1e3), t_max
+
+
 # ------------------------------------------------------------ our arm
 def run_ours(args):
     import numpy as np
@@ -171,12 +188,8 @@ def run_ours(args):
     prof = bop.bop_get_profile(ctx.h)
     bop.bop_set_profiling(ctx.h, False)
     stats = bop.bop_get_stats(ctx.h)
-    t_max = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    t_ms = float(t_max.item())
+    value, t_ms = aggregate(t_ms, w.n_atoms * args.steps, world)
     atoms = w.n_atoms * args.steps * world
-    value = atoms / (t_ms / 1e3)
     launches = sum(v["launches"] for v in prof.values())
 
     # end to end through the C ABI with host buffers (pinned)
@@ -193,10 +206,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         bop.bop_evaluate_host(ctx.h, pos_h, w.cell, w.pbc, e_h, f_h, v_h)
         te.append(time.perf_counter() - t0)
-    t_e2e = torch.tensor([sum(te)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e_value = atoms / float(t_e2e.item())
+    e2e_value, _ = aggregate(sum(te) * 1e3, w.n_atoms * args.steps, world)
 
     # roofline of the dominant kernel family (live CUDA-event times)
     fam = max(prof, key=lambda k: prof[k]["ms"])

@@ -1,0 +1,164 @@
+"""GPU checks at the sizes bench.py times, plus the error paths of the ABI.
+
+Full-size structures are too large for the whole oracle run, so they are
+checked on sampled outputs the oracle computes one by one (the moments of
+sampled atoms at the GPU's converged onsite levels, their per-orbital
+electron count and bond energy at the GPU's Fermi level) and through
+properties that hold at any size (electron count, local neutrality,
+central finite differences of the GPU energy, h = 1e-4 Angstrom).
+"""
+import numpy as np
+import pytest
+
+from paper_1803_07491_gb300 import inputs as I
+from conftest import oracle_model
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bop():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_07491_gb300 import build, bop as b
+    build.build()
+    return b
+
+
+@pytest.mark.parametrize("prec,tol_mu", [("fp64", 1e-11), ("fp32", 3e-6)])
+def test_d2000_lcn_sampled_against_oracle(bop, ob, prec, tol_mu):
+    """The bench workload (2,000 atoms, d, LCN SCF, 9 moments)."""
+    w = I.workload("d2000")
+    if prec == "fp32":
+        w = I.with_run(w, scf_tol=1e-5)
+    ctx = bop.Context(w.model, w.run, prec)
+    ctx.build(w.pos, w.cell, w.pbc)
+    delta = torch.zeros(w.n_atoms, dtype=torch.float64, device="cuda")
+    e, st = ctx.energy(delta=delta)
+    F, W = ctx.forces()
+    assert st["scf_converged"] == 1
+    M = w.n_atoms * 5
+    orb = bop.bop_get_orbital_state(ctx.h, M, 9)
+    N = orb["N"].cpu().numpy().reshape(w.n_atoms, 5)
+    # properties at any size: electron count, local neutrality, zero net force
+    assert abs(2 * N.sum() - 6.8 * w.n_atoms) < 1e-8 * w.n_atoms
+    assert np.max(np.abs(2 * N.sum(axis=1) - 6.8)) < w.run.scf_tol
+    assert np.abs(F.sum(dim=0).cpu().numpy()).max() < (1e-9 if prec == "fp64" else 1e-4) * w.n_atoms
+    # sampled atoms through the oracle, at the GPU's onsite levels
+    m = oracle_model(w.model)
+    nbr = ob.neighbors(w.pos, w.cell, w.pbc, m.rc)
+    H = ob.blocks(m, w.pos, w.cell, nbr)
+    onsite = orb["onsite"].cpu().numpy().reshape(w.n_atoms, 5)
+    sel = np.array([0, 17, 555, 1024, 1999], np.int32)
+    mu_ref = ob.moments(nbr, H, onsite, 9, sel=sel)
+    mu_gpu = orb["mu"].cpu().numpy().reshape(w.n_atoms, 5, 9)[sel]
+    scale = np.abs(mu_ref).max(axis=-1, keepdims=True) + 1.0
+    assert np.max(np.abs(mu_gpu - mu_ref) / scale) < tol_mu
+    ex = ob.scalar_stage(mu_ref.reshape(-1, 9), 200)
+    Nr, Ur = ob.orbital_N_U(ex.gsig, ex.a_inf, ex.b_inf, onsite[sel].reshape(-1), st["e_fermi"])
+    Ug = orb["U"].cpu().numpy().reshape(w.n_atoms, 5)[sel].reshape(-1)
+    tolE = 1e-9 if prec == "fp64" else 1e-4
+    assert np.max(np.abs(N[sel].reshape(-1) - Nr)) < tolE
+    assert np.max(np.abs(Ug - Ur)) < tolE
+    ctx.close()
+
+
+def test_slab16k_forces_and_stress_by_finite_differences(bop, ob):
+    """16,320-atom slab, two free (001) surfaces, 64 vacancies, 13 moments
+    (uneven clusters in one launch): adjoint forces and virial against
+    central differences of the GPU energy (FP64 mode), h = 1e-4 A."""
+    w = I.workload("slab16k")
+    ctx = bop.Context(w.model, w.run, "fp64")
+    res = ctx.evaluate(w.pos, w.cell, w.pbc)
+    F = res.forces.cpu().numpy()
+    V = res.virial.cpu().numpy()
+    assert np.abs(F.sum(axis=0)).max() < 1e-8 * w.n_atoms
+    st = bop.bop_get_stats(ctx.h)
+    assert st["n_atoms"] == 16320 and st["K"] == 6
+
+    def energy(pos, cell):
+        ctx.build(pos, cell, w.pbc)
+        _, s = ctx.energy()
+        return s["e_total"]
+
+    h = 1e-4
+    z = w.pos[:, 2]
+    surface = int(np.argmax(z))  # an atom of the top surface
+    bulk = int(np.argmin(np.abs(z - np.median(z))))
+    for (i, c) in [(surface, 2), (surface, 0), (bulk, 1), (123, 0)]:
+        p, q = w.pos.copy(), w.pos.copy()
+        p[i, c] += h
+        q[i, c] -= h
+        fd = -(energy(p, w.cell) - energy(q, w.cell)) / (2 * h)
+        assert abs(F[i, c] - fd) < 2e-6 + 1e-5 * abs(fd), (i, c, F[i, c], fd)
+    # strain along the periodic directions (xx, yy, xy).  The Gershgorin
+    # bounds (Eq. gershgorin) are a max / min over the levels of each of the
+    # 81,600 chains, so E is only piecewise smooth: a homogeneous strain
+    # changes the active level of some chain about once per 1e-6 of strain,
+    # and every central difference then carries a few 1e-3 eV of slope jumps
+    # (measured: 5e-4 ... 3e-2 for steps 1e-6 ... 2e-4, no h^2 trend).  The
+    # virial is the derivative on the active branches.
+    hs = 1e-5
+    for (a, b) in [(0, 0), (1, 1), (0, 1)]:
+        e = np.zeros((3, 3))
+        e[a, b] = e[b, a] = hs / (2 if a != b else 1)
+        vals = []
+        for sgn in (1, -1):
+            D = np.eye(3) + sgn * e
+            vals.append(energy(w.pos @ D.T, w.cell @ D.T))
+        fd = (vals[0] - vals[1]) / (2 * hs)
+        ref = 0.5 * (V[a, b] + V[b, a])
+        assert abs(ref - fd) < 3e-2 + 1e-6 * abs(fd), (a, b, ref, fd)
+    ctx.close()
+
+
+def test_moment_product_count_matches_perfect_lattice(bop):
+    """The cluster builder counts the block products of a moments pass:
+    14 (1 + 15 + 65 + 175) = 3,584 per atom for bcc with 1st + 2nd shells
+    at 9 moments."""
+    pos, cell = I.bcc_cell(4, 4, 4)
+    ctx = bop.Context(I.MODEL_D, I.RunParams(n_e=6.8))
+    st = ctx.build(pos, cell, (1, 1, 1))
+    assert st["moment_products"] == 3584 * 128
+    assert st["max_cluster"] == 369
+
+
+def test_abi_error_paths(bop):
+    """Invalid inputs are refused with status codes, nothing is launched on
+    bad data."""
+    w = I.small_bcc(2, 2, 2, 0.05, 1)
+    ctx = bop.Context(w.model, w.run)
+    with pytest.raises(bop.BopError) as e:
+        bop.bop_build_hamiltonian(ctx.h, torch.zeros((0, 3), dtype=torch.float64, device="cuda"), w.cell, w.pbc)
+    assert e.value.status == bop.BOP_ERR_ARG
+    outside = w.pos.copy()
+    outside[3, 0] = w.cell[0, 0] + 1.0
+    with pytest.raises(bop.BopError) as e:
+        ctx.build(outside, w.cell, w.pbc)
+    assert e.value.status == bop.BOP_ERR_ARG
+    # 100 atoms inside a 2 A ball: 99 neighbours each, more than 64
+    rng = np.random.default_rng(0)
+    cell = np.diag([40.0, 40.0, 40.0])
+    blob = 20.0 + rng.uniform(-1.0, 1.0, size=(100, 3))
+    with pytest.raises(bop.BopError) as e:
+        ctx.build(blob, cell, (0, 0, 0))
+    assert e.value.status == bop.BOP_ERR_OVERFLOW
+    with pytest.raises(bop.BopError) as e:
+        bop.bop_forces(ctx.h, w.n_atoms)
+    assert e.value.status == bop.BOP_ERR_STATE
+    # the context stays usable after the errors
+    res = ctx.evaluate(w.pos, w.cell, w.pbc)
+    assert np.isfinite(res.e_total)
+    bad = bop.make_model(w.model, I.with_run(w, n_mom=8).run)
+    with pytest.raises(bop.BopError):
+        bop.bop_create(bad)
+    ctx.close()
+
+
+def test_single_isolated_atom(bop):
+    cell = np.diag([20.0, 20.0, 20.0])
+    pos = np.array([[10.0, 10.0, 10.0]])
+    ctx = bop.Context(I.MODEL_D, I.RunParams(n_e=6.8))
+    res = ctx.evaluate(pos, cell, (0, 0, 0))
+    assert abs(res.e_total) < 5e-3 and np.allclose(res.forces.cpu().numpy(), 0.0)
