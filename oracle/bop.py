@@ -113,6 +113,8 @@ class Settings:
     dos_floor: float = 0.1     # states/eV, LCN preconditioner floor
     mixer: str = "linear"      # linear | anderson (type-II Broyden, "SCF" of the paper)
     mix_history: int = 6
+    terminator: str = "constant"  # constant | mlp (learned continuation, oracle/mlp.py)
+    net: object = None            # mlp.Net for terminator = "mlp"
 
 
 @dataclass
@@ -491,7 +493,7 @@ def fermi_bisect(ex: Expansion, spin_factor: float, target: float,
     return 0.5 * (lo + hi), it
 
 
-def weights(mu, E_on, E_F, n_exp: int, spin_factor: float):
+def weights(mu, E_on, E_F, n_exp: int, spin_factor: float, stage=None):
     """w_n = dU_total/dmu_n per orbital (Eq. weights), including the
     response of E_F at fixed total electron number, by complex-step
     differentiation of the scalar stage.  Returns (w [M, n_mom],
@@ -503,11 +505,11 @@ def weights(mu, E_on, E_F, n_exp: int, spin_factor: float):
     for n in range(n_mom):
         mc = mu.astype(np.complex128)
         mc[:, n] += 1j * CS_H
-        ex = scalar_stage(mc, n_exp)
+        ex = stage(mc)
         N, U = orbital_N_U(ex.gsig, ex.a_inf, ex.b_inf, E_on.astype(np.complex128), E_F)
         dU[:, n] = np.imag(U) / CS_H
         dN[:, n] = np.imag(N) / CS_H
-    ex = scalar_stage(mu, n_exp)
+    ex = stage(mu)
     N, U = orbital_N_U(ex.gsig, ex.a_inf, ex.b_inf, E_on.astype(np.complex128),
                        E_F + 1j * CS_H)
     dU_dEF = np.imag(U) / CS_H
@@ -545,6 +547,12 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
     N0 = st.n_e
     target = st.n_e * n
     hist_x, hist_f = [], []
+    if st.terminator == "mlp":
+        from . import mlp as _mlp
+        assert st.n_mom == 9 and st.net is not None
+        stage = lambda m: _mlp.learned_stage(m, st.net, st.n_exp)  # noqa: E731
+    else:
+        stage = lambda m: scalar_stage(m, st.n_exp)  # noqa: E731
     it = 0
     converged = st.scf == "none"
     while True:
@@ -556,7 +564,7 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
                 onsite[v] += sign * 0.5 * st.stoner_I * m[:, None]
         mu = np.stack([moments(nbr, H, onsite[v], st.n_mom) for v in range(S)])
         mu_f = mu.reshape(-1, st.n_mom)
-        ex = scalar_stage(mu_f, st.n_exp)
+        ex = stage(mu_f)
         E_F, n_bis = fermi_bisect(ex, s, target)
         N, U = orbital_N_U(ex.gsig, ex.a_inf, ex.b_inf, onsite.reshape(-1), E_F)
         Nsv = N.reshape(S, n, norb)
@@ -603,9 +611,10 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
     out = dict(e_atom=e_atom, e_total=float(e_atom.sum()), e_fermi=E_F, mu=mu,
                a=ex.a, b=ex.b, a_inf=ex.a_inf, b_inf=ex.b_inf, N=Nsv, delta=delta, m=m,
                scf_iterations=it, scf_converged=converged, bisection_steps=n_bis,
-               neighbors=nbr, H=H, onsite=onsite, forces_include_scf_response=st.scf == "none")
+               neighbors=nbr, H=H, onsite=onsite, forces_include_scf_response=st.scf == "none",
+               learned=getattr(ex, "learned", None))
     if want_forces:
-        w, dU_dE, *_ = weights(mu_f, onsite.reshape(-1), E_F, st.n_exp, s)
+        w, dU_dE, *_ = weights(mu_f, onsite.reshape(-1), E_F, st.n_exp, s, stage)
         w = w.reshape(S, n, norb, st.n_mom)
         Hbar = np.zeros((nbr.n_edges, norb, norb))
         for v in range(S):
