@@ -48,6 +48,7 @@ extern "C" {
 #endif
 
 typedef struct bop_ctx bop_ctx;
+typedef struct bop_mlp bop_mlp;
 typedef void* bop_stream; /* cudaStream_t */
 
 enum bop_status {
@@ -65,6 +66,7 @@ enum bop_status {
 enum { BOP_SCF_NONE = 0, BOP_SCF_LCN = 1, BOP_SCF_STONER = 2 };
 enum { BOP_PREC_FP64 = 0, BOP_PREC_FP32 = 1 };
 enum { BOP_MIX_LINEAR = 0, BOP_MIX_ANDERSON = 1 };
+enum { BOP_TERM_CONSTANT = 0, BOP_TERM_MLP = 1 };
 
 /* Model and run settings.
  * beta_x(r) = b0[x] * exp(-lam (r - r0)) * fcut(r), fcut the cosine taper
@@ -82,7 +84,11 @@ enum { BOP_MIX_LINEAR = 0, BOP_MIX_ANDERSON = 1 };
  * mixer: BOP_MIX_LINEAR (x += F, F the preconditioned residual above) or
  * BOP_MIX_ANDERSON (type-II Broyden over the last mix_history <= 8
  * iterations, one of the paper's mixers); both converge to the same
- * self-consistent state. */
+ * self-consistent state.
+ * terminator: BOP_TERM_CONSTANT (Eq. abinf with the Gershgorin band edges)
+ * or BOP_TERM_MLP, the learned continuation of the chain (n_mom must be 9;
+ * a network must be attached with bop_set_mlp, see the learned-terminator
+ * section below). */
 typedef struct {
   int norb;
   double b0[3];
@@ -99,6 +105,7 @@ typedef struct {
   int precision;
   int mixer;
   int mix_history;
+  int terminator;
 } bop_model;
 
 typedef struct {
@@ -116,7 +123,8 @@ typedef struct {
   double e_fermi;
   double e_total;
   int forces_scf_response;/* 1 if forces include the SCF response (scf == NONE) */
-  int pad;
+  int n_learned;          /* orbitals (all spins) on the learned chain in the last
+                             energy; the others fell back to the constant terminator */
   long long moment_products; /* block products Psi_k(t) += H_ts Psi_k-1(s) of one
                                 moments pass, summed over atoms (one spin) */
 } bop_stats;
@@ -264,6 +272,96 @@ int bop_get_profile(bop_ctx* ctx, bop_kernel_time* out_host, int max, int* n_out
  * other host threads) race and must be serialised by the caller. */
 int bop_fermi_level_noalloc(int M, int n_exp, const double* gsig, const double* a_inf, const double* b_inf,
                             double spin_factor, double n_electrons, double* e_fermi, bop_stream stream);
+
+/* ------------------------------------------------------------------ learned terminator
+ * The paper closes the recursion chain with a constant terminator (Eq. abinf,
+ * a_inf / b_inf from Eq. gershogorin).  The learned terminator keeps that form
+ * but continues the 9-moment chain of every orbital: a small network predicts
+ * the next four levels (a_4..a_7, b_5..b_8) and the band centre / width
+ * (a*_inf, b*_inf) that a 17-moment run of the same orbital would give, and
+ * the constant terminator then starts after level 8.  The paper has no such
+ * network; its constant terminator is the fallback and the reference the
+ * network is judged against.
+ *   inputs x (BOP_MLP_NIN = 18): (a_k - a_inf)/b_inf, k = 0..3; b_k/b_inf,
+ *     k = 1..4; a_inf; b_inf; mu-hat_1 .. mu-hat_8 (Eq. sigma_i normalisation);
+ *     a_inf, b_inf from the 9-moment Gershgorin bounds;
+ *   outputs y (BOP_MLP_NOUT = 10): (a*_inf - a_inf)/b_inf, b*_inf/b_inf,
+ *     (a_k - a_inf)/b_inf for k = 4..7, b_k/b_inf for k = 5..8;
+ *   network: 18 -> 128 -> 128 -> 10, GELU (x Phi(x)), on inputs and outputs
+ *     standardised by the training set (mean, standard deviation);
+ *   parameters (BOP_MLP_NPARAM floats, row-major [out][in] matrices):
+ *     W1 [128][18], b1 [128], W2 [128][128], b2 [128], W3 [10][128], b3 [10];
+ *   normalisation (BOP_MLP_NNORM floats): x_mean [18], x_std [18], x_lo [18],
+ *     x_hi [18] (training range widened by 5 % of its span), y_mean [10],
+ *     y_std [10];
+ *   training: FP32, mean squared error of the standardised outputs over the
+ *     rows with mask 1, Adam (beta 0.9 / 0.999, eps 1e-8, bias-corrected);
+ *   inference: weight matrices rounded to bfloat16 (nearest even), biases
+ *     FP32, activations FP32 (precision FP32) or FP64 (precision FP64), so
+ *     the energy stays smooth in the moments and the forces are its exact
+ *     derivative;
+ *   fallback to the constant terminator of the 9-moment chain where that
+ *     chain is truncated, an input lies outside [x_lo, x_hi], a predicted
+ *     b_k or b*_inf is not above 1e-3 eV, or a value is not finite.
+ * A bop_mlp lives on the device that was current at bop_mlp_create. */
+#define BOP_MLP_NIN 18
+#define BOP_MLP_NHID 128
+#define BOP_MLP_NOUT 10
+#define BOP_MLP_NPARAM 20234
+#define BOP_MLP_NNORM 92
+
+/* Creates a network from params_host [BOP_MLP_NPARAM] (host FP32), with the
+ * identity standardisation and an unbounded training range; Adam state 0.
+ * Synchronises the device. */
+int bop_mlp_create(bop_mlp** net, const float* params_host);
+int bop_mlp_destroy(bop_mlp* net);
+const char* bop_mlp_last_error(const bop_mlp* net);
+
+/* Copies the FP32 master parameters and / or the normalisation to host
+ * arrays (either may be NULL).  Synchronous. */
+int bop_mlp_get(bop_mlp* net, float* params_host, float* norm_host);
+/* Sets the normalisation from a host array; standard deviations must be > 0. */
+int bop_mlp_set_norm(bop_mlp* net, const float* norm_host);
+
+/* Training data from 17-moment runs: for M orbitals with moments mu17
+ * (device [M][17], FP64, e.g. from bop_moments of a context with n_mom 17)
+ * writes the raw inputs x [M][18] (from mu_0..mu_8), the raw targets
+ * t [M][10] and mask [M] (1 where the 17-moment chain has all 8 levels and
+ * every target is finite, else 0; t is 0 there).  Device outputs. */
+int bop_mlp_dataset(long long M, const double* mu17, float* x, float* t, float* mask, bop_stream stream);
+
+/* Fits the normalisation to the rows with mask > 0 of x [M][18], t [M][10]
+ * (device): means, population standard deviations floored at 1e-6, input
+ * range widened by 5 % of its span. */
+int bop_mlp_fit_norm(bop_mlp* net, long long M, const float* x, const float* t, const float* mask,
+                     bop_stream stream);
+
+/* Gradient of the loss over one batch: rows idx[0..batch-1] (device int32,
+ * each in [0, M)) of the raw data x, t, mask (device).  The gradient is kept
+ * in the network for bop_mlp_adam and copied to grad_out (device
+ * [BOP_MLP_NPARAM]) if not NULL; the batch loss goes to loss_out (device
+ * [1]) if not NULL.  Deterministic (fixed reduction order). */
+int bop_mlp_gradient(bop_mlp* net, long long M, const float* x, const float* t, const float* mask, const int* idx,
+                     int batch, float* grad_out, float* loss_out, bop_stream stream);
+/* Reads back (synchronising stream) whether any row index of the batches
+ * since the last check was outside [0, M): such rows enter the gradient as
+ * masked rows of zeros.  BOP_ERR_ARG if so. */
+int bop_mlp_check(bop_mlp* net, bop_stream stream);
+/* One Adam step with the last gradient; refreshes the bfloat16 weights. */
+int bop_mlp_adam(bop_mlp* net, float lr, bop_stream stream);
+/* bop_mlp_gradient followed by bop_mlp_adam. */
+int bop_mlp_train_step(bop_mlp* net, long long M, const float* x, const float* t, const float* mask, const int* idx,
+                       int batch, float lr, float* loss_out, bop_stream stream);
+
+/* Inference: raw outputs y [M][10] for raw inputs x [M][18] (device) with the
+ * bfloat16 weights and FP32 activations. */
+int bop_mlp_predict(bop_mlp* net, long long M, const float* x, float* y, bop_stream stream);
+
+/* Attaches a network to a context whose model has terminator = BOP_TERM_MLP
+ * (NULL detaches).  The context keeps the pointer: the network must outlive
+ * its use, and training steps change what the next bop_energy computes.
+ * Errors: BOP_ERR_ARG if the model's terminator is not BOP_TERM_MLP. */
+int bop_set_mlp(bop_ctx* ctx, bop_mlp* net);
 
 #ifdef __cplusplus
 }

@@ -498,7 +498,10 @@ def weights(mu, E_on, E_F, n_exp: int, spin_factor: float, stage=None):
     response of E_F at fixed total electron number, by complex-step
     differentiation of the scalar stage.  Returns (w [M, n_mom],
     dU_dE [M] = direct derivative of s*U_ialpha w.r.t. its onsite level,
-    dN_dmu [M, n_mom], dN_dEF [M], dU_dEF [M])."""
+    dN_dmu [M, n_mom], dN_dEF [M], dU_dEF [M]).  ``stage`` (mu -> Expansion)
+    replaces ``scalar_stage``, e.g. by the learned continuation of the chain."""
+    if stage is None:
+        stage = lambda m: scalar_stage(m, n_exp)  # noqa: E731
     M, n_mom = mu.shape
     dU = np.zeros((M, n_mom))
     dN = np.zeros((M, n_mom))

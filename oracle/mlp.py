@@ -71,20 +71,6 @@ def unpack_norm(q):
     return (q[0:18], q[18:36], q[36:54], q[54:72], q[72:82], q[82:92])
 
 
-def init_params(seed: int) -> np.ndarray:
-    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases, drawn
-    from default_rng(seed) in layout order; rounded to FP32 values."""
-    rng = np.random.default_rng(seed)
-    parts = []
-    for s in _SHAPES:
-        if len(s) == 2:
-            lim = 1.0 / np.sqrt(s[1])
-            parts.append(rng.uniform(-lim, lim, size=s).ravel())
-        else:
-            parts.append(np.zeros(s))
-    return np.concatenate(parts).astype(np.float32).astype(np.float64)
-
-
 # ---------------------------------------------------------------- GELU
 
 def _is_c(x):

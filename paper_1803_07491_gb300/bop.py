@@ -20,6 +20,8 @@ BOP_ERR_BRACKET, BOP_ERR_NUMERIC, BOP_ERR_STATE, BOP_ERR_OVERFLOW = 5, 6, 7, 8
 SCF = {"none": 0, "lcn": 1, "stoner": 2}
 PREC = {"fp64": 0, "fp32": 1}
 MIXER = {"linear": 0, "anderson": 1}
+TERM = {"constant": 0, "mlp": 1}
+MLP_NIN, MLP_NHID, MLP_NOUT, MLP_NPARAM, MLP_NNORM = 18, 128, 10, 20234, 92
 
 
 class BopError(RuntimeError):
@@ -36,7 +38,7 @@ class bop_model(ctypes.Structure):
                 ("eta", ctypes.c_double), ("scf_tol", ctypes.c_double), ("scf_max_it", ctypes.c_int),
                 ("stoner_I", ctypes.c_double), ("m_mix", ctypes.c_double), ("m0", ctypes.c_double),
                 ("dos_floor", ctypes.c_double), ("precision", ctypes.c_int), ("mixer", ctypes.c_int),
-                ("mix_history", ctypes.c_int)]
+                ("mix_history", ctypes.c_int), ("terminator", ctypes.c_int)]
 
 
 class bop_stats(ctypes.Structure):
@@ -45,11 +47,11 @@ class bop_stats(ctypes.Structure):
                 ("max_cluster", ctypes.c_int), ("scf_iterations", ctypes.c_int), ("scf_converged", ctypes.c_int),
                 ("bisection_rounds", ctypes.c_int), ("scf_residual", ctypes.c_double),
                 ("e_fermi", ctypes.c_double), ("e_total", ctypes.c_double),
-                ("forces_scf_response", ctypes.c_int), ("pad", ctypes.c_int),
+                ("forces_scf_response", ctypes.c_int), ("n_learned", ctypes.c_int),
                 ("moment_products", ctypes.c_longlong)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class bop_kernel_time(ctypes.Structure):
@@ -91,6 +93,21 @@ def lib(path: str | None = None):
         "bop_fermi_level_noalloc": ([ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, ctypes.c_double,
                                      ctypes.c_double, _VP, _VP], ctypes.c_int),
         "bop_set_profiling": ([_VP, ctypes.c_int], ctypes.c_int),
+        "bop_mlp_create": ([ctypes.POINTER(_VP), _VP], ctypes.c_int),
+        "bop_mlp_destroy": ([_VP], ctypes.c_int),
+        "bop_mlp_last_error": ([_VP], ctypes.c_char_p),
+        "bop_mlp_get": ([_VP, _VP, _VP], ctypes.c_int),
+        "bop_mlp_set_norm": ([_VP, _VP], ctypes.c_int),
+        "bop_mlp_dataset": ([ctypes.c_longlong, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+        "bop_mlp_fit_norm": ([_VP, ctypes.c_longlong, _VP, _VP, _VP, _VP], ctypes.c_int),
+        "bop_mlp_gradient": ([_VP, ctypes.c_longlong, _VP, _VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP],
+                             ctypes.c_int),
+        "bop_mlp_adam": ([_VP, ctypes.c_float, _VP], ctypes.c_int),
+        "bop_mlp_check": ([_VP, _VP], ctypes.c_int),
+        "bop_mlp_train_step": ([_VP, ctypes.c_longlong, _VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_float, _VP,
+                                _VP], ctypes.c_int),
+        "bop_mlp_predict": ([_VP, ctypes.c_longlong, _VP, _VP, _VP], ctypes.c_int),
+        "bop_set_mlp": ([_VP, _VP], ctypes.c_int),
         "bop_reset_profile": ([_VP], ctypes.c_int),
         "bop_get_profile": ([_VP, ctypes.POINTER(bop_kernel_time), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
                             ctypes.c_int),
@@ -126,7 +143,7 @@ def make_model(params, run, precision: str = "fp64") -> bop_model:
     return bop_model(params.norb, (ctypes.c_double * 3)(*b0), params.r0, params.lam, params.rc, params.dc,
                      params.onsite0, run.n_mom, run.n_exp, run.n_spin, run.n_e, SCF[run.scf], run.eta,
                      run.scf_tol, run.scf_max_it, run.stoner_I, run.m_mix, run.m0, run.dos_floor,
-                     PREC[precision], MIXER[run.mixer], run.mix_history)
+                     PREC[precision], MIXER[run.mixer], run.mix_history, TERM[run.terminator])
 
 
 def _check(ctx, st, allow=()):
@@ -286,6 +303,134 @@ def bop_get_profile(ctx) -> dict:
             for i in range(n.value)}
 
 
+# ------------------------------------------------------------ learned terminator
+
+def _mcheck(net, st):
+    if st != BOP_OK:
+        msg = lib().bop_mlp_last_error(net) if net else b""
+        raise BopError(st, msg.decode() if msg else "")
+    return st
+
+
+def bop_mlp_create(params) -> _VP:
+    p = np.ascontiguousarray(params, dtype=np.float32).reshape(MLP_NPARAM)
+    h = _VP()
+    st = lib().bop_mlp_create(ctypes.byref(h), _ptr(p))
+    if st != BOP_OK:
+        raise BopError(st, "bop_mlp_create failed")
+    return h
+
+
+def bop_mlp_destroy(net):
+    lib().bop_mlp_destroy(net)
+
+
+def bop_mlp_get(net):
+    p = np.zeros(MLP_NPARAM, np.float32)
+    q = np.zeros(MLP_NNORM, np.float32)
+    _mcheck(net, lib().bop_mlp_get(net, _ptr(p), _ptr(q)))
+    return p, q
+
+
+def bop_mlp_set_norm(net, norm):
+    q = np.ascontiguousarray(norm, dtype=np.float32).reshape(MLP_NNORM)
+    _mcheck(net, lib().bop_mlp_set_norm(net, _ptr(q)))
+
+
+def bop_mlp_dataset(mu17: torch.Tensor, stream=None):
+    """Raw inputs x [M][18], targets t [M][10] and mask [M] (device FP32)
+    from 17-moment runs mu17 [M][17] (device FP64)."""
+    mu17 = mu17.reshape(-1, 17).contiguous()
+    M = mu17.shape[0]
+    x = torch.empty((M, MLP_NIN), dtype=torch.float32, device=mu17.device)
+    t = torch.empty((M, MLP_NOUT), dtype=torch.float32, device=mu17.device)
+    m = torch.empty(M, dtype=torch.float32, device=mu17.device)
+    st = lib().bop_mlp_dataset(M, _ptr(mu17), _ptr(x), _ptr(t), _ptr(m), _stream(stream))
+    if st != BOP_OK:
+        raise BopError(st, "bop_mlp_dataset failed")
+    return x, t, m
+
+
+def bop_mlp_fit_norm(net, x, t, mask, stream=None):
+    _mcheck(net, lib().bop_mlp_fit_norm(net, x.shape[0], _ptr(x), _ptr(t), _ptr(mask), _stream(stream)))
+
+
+def bop_mlp_gradient(net, x, t, mask, idx: torch.Tensor, grad_out=None, loss_out=None, stream=None):
+    _mcheck(net, lib().bop_mlp_gradient(net, x.shape[0], _ptr(x), _ptr(t), _ptr(mask), _ptr(idx),
+                                        idx.shape[0], _ptr(grad_out), _ptr(loss_out), _stream(stream)))
+
+
+def bop_mlp_adam(net, lr: float, stream=None):
+    _mcheck(net, lib().bop_mlp_adam(net, lr, _stream(stream)))
+
+
+def bop_mlp_train_step(net, x, t, mask, idx: torch.Tensor, lr: float, loss_out=None, stream=None):
+    _mcheck(net, lib().bop_mlp_train_step(net, x.shape[0], _ptr(x), _ptr(t), _ptr(mask), _ptr(idx),
+                                          idx.shape[0], lr, _ptr(loss_out), _stream(stream)))
+
+
+def bop_mlp_predict(net, x: torch.Tensor, stream=None) -> torch.Tensor:
+    y = torch.empty((x.shape[0], MLP_NOUT), dtype=torch.float32, device=x.device)
+    _mcheck(net, lib().bop_mlp_predict(net, x.shape[0], _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+def bop_set_mlp(ctx, net):
+    _check(ctx, lib().bop_set_mlp(ctx, net))
+
+
+class Network:
+    """A learned-terminator network on the current device (bop_mlp)."""
+
+    def __init__(self, params):
+        self.h = bop_mlp_create(params)
+
+    def close(self):
+        if self.h:
+            bop_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get(self):
+        return bop_mlp_get(self.h)
+
+    def set_norm(self, norm):
+        bop_mlp_set_norm(self.h, norm)
+
+    def fit_norm(self, x, t, mask):
+        bop_mlp_fit_norm(self.h, x, t, mask)
+
+    def train(self, x, t, mask, epochs: int, batch: int, lr: float, seed: int, lr_final: float | None = None,
+              stream=None):
+        """Mini-batch Adam over the rows with mask 1 of (x, t): each epoch a
+        permutation drawn from default_rng(seed) (one draw per epoch); the
+        learning rate decays geometrically from lr to lr_final.  Returns the
+        mean batch loss of every epoch (one synchronisation per epoch)."""
+        rows = torch.nonzero(mask > 0).flatten().to(torch.int32)
+        n = rows.numel()
+        rng = np.random.default_rng(seed)
+        losses = torch.zeros(max(1, (n + batch - 1) // batch), dtype=torch.float32, device=x.device)
+        out = []
+        lr_final = lr if lr_final is None else lr_final
+        for ep in range(epochs):
+            perm = torch.as_tensor(rng.permutation(n), device=x.device)
+            order = rows[perm].contiguous()
+            f = ep / max(1, epochs - 1)
+            lr_ep = lr * (lr_final / lr) ** f
+            nb = 0
+            for b0 in range(0, n - batch + 1, batch):
+                bop_mlp_train_step(self.h, x, t, mask, order[b0:b0 + batch], lr_ep, losses[nb:nb + 1], stream)
+                nb += 1
+            out.append(float(losses[:nb].mean().item()))
+        _mcheck(self.h, lib().bop_mlp_check(self.h, _stream(stream)))
+        return out
+
+
 # ------------------------------------------------------------ convenience
 
 @dataclass
@@ -301,11 +446,14 @@ class Result:
 class Context:
     """One model on the current CUDA device; owns a libbopgb context."""
 
-    def __init__(self, params, run, precision: str = "fp64"):
+    def __init__(self, params, run, precision: str = "fp64", net: Network | None = None):
         self.params, self.run, self.precision = params, run, precision
         self.model = make_model(params, run, precision)
         self.h = bop_create(self.model)
         self.n = 0
+        self.net = net
+        if net is not None:
+            bop_set_mlp(self.h, net.h)
 
     def close(self):
         if self.h:

@@ -35,11 +35,11 @@ struct DBuf {
 
 enum ProfKind {
   PK_NBR = 0, PK_CLUSTER, PK_ONSITE, PK_MOMENTS, PK_EXPAND, PK_FERMI, PK_NU, PK_SCF, PK_ENERGY, PK_EFRESP,
-  PK_WEIGHTS, PK_ADJOINT, PK_FORCES, PK_N
+  PK_WEIGHTS, PK_ADJOINT, PK_FORCES, PK_MLP, PK_N
 };
 static const char* const PK_NAMES[PK_N] = {"neighbours", "cluster", "onsite", "moments", "expand", "fermi",
                                           "orbital_NU", "scf", "energy", "ef_response", "weights", "adjoint",
-                                          "forces"};
+                                          "forces", "mlp"};
 
 struct Prof {
   bool on = false;
@@ -70,6 +70,9 @@ struct bop_ctx {
   DBuf N, U, dos, fstate, partials, counter, result, e_total, lam, e_atom;
   DBuf w, zscr, adjscr, Hbar, Ebar, ginv;
   DBuf hx, hf, gamma, scfred;
+  // learned terminator
+  bop_mlp* net = nullptr;
+  DBuf lbase, lnlev, lflag, lxs, lys, lZ1, lH1, lZ2, lH2, lybar, lcot, lxbar, lcount;
   DBuf status;
   DBuf cub_tmp;
   DBuf nprod;
@@ -201,6 +204,9 @@ int validate_model(bop_ctx* c, const bop_model* m) {
     return fail(c, BOP_ERR_ARG, "mixer must be LINEAR or ANDERSON");
   if (m->mixer == BOP_MIX_ANDERSON && (m->mix_history < 1 || m->mix_history > 8))
     return fail(c, BOP_ERR_ARG, "mix_history must be in [1, 8]");
+  if (m->terminator != BOP_TERM_CONSTANT && m->terminator != BOP_TERM_MLP)
+    return fail(c, BOP_ERR_ARG, "terminator must be CONSTANT or MLP");
+  if (m->terminator == BOP_TERM_MLP && m->n_mom != 9) return fail(c, BOP_ERR_ARG, "the MLP terminator needs n_mom = 9");
   return BOP_OK;
 }
 
@@ -379,7 +385,65 @@ int run_moments(bop_ctx* c, const double* onsite_dev, double* mu, cudaStream_t s
   return BOP_OK;
 }
 
+LearnedArgs learned_args(bop_ctx* c, int M, const double* mu) {
+  LearnedArgs L;
+  L.M = M;
+  L.n_exp = c->n_exp;
+  L.fp64 = c->fp64;
+  L.mu = mu;
+  L.base = P<double>(c->lbase);
+  L.nlev = P<int>(c->lnlev);
+  L.flag = P<unsigned char>(c->lflag);
+  L.xs = c->lxs.p;
+  L.ys = c->lys.p;
+  L.norm = mlp_norm_dev(c->net);
+  L.a_inf = P<double>(c->a_inf);
+  L.b_inf = P<double>(c->b_inf);
+  L.gsig = P<double>(c->gsig);
+  L.g = P<double>(c->gjack);
+  L.n_learned = P<unsigned>(c->lcount);
+  L.status = P<unsigned>(c->status);
+  L.ybar = c->lybar.p;
+  L.cot = P<double>(c->lcot);
+  L.xbar = c->lxbar.p;
+  memset(&L.W, 0, sizeof(L.W));
+  return L;
+}
+
+// Learned terminator: features -> network -> continued chain -> g_m sigma_m.
+int run_learned(bop_ctx* c, int M, const double* mu, cudaStream_t s) {
+  if (!c->net) return fail(c, BOP_ERR_STATE, "terminator MLP needs a network (bop_set_mlp)");
+  const size_t T = c->fp64 ? sizeof(double) : sizeof(float);
+  const size_t m = (size_t)M;
+  CKS(ensure(c, c->lbase, sizeof(double) * m * 10));
+  CKS(ensure(c, c->lnlev, sizeof(int) * m));
+  CKS(ensure(c, c->lflag, m));
+  CKS(ensure(c, c->lxs, T * m * BOP_MLP_NIN));
+  CKS(ensure(c, c->lys, T * m * BOP_MLP_NOUT));
+  CKS(ensure(c, c->lZ1, T * m * BOP_MLP_NHID));
+  CKS(ensure(c, c->lH1, T * m * BOP_MLP_NHID));
+  CKS(ensure(c, c->lZ2, T * m * BOP_MLP_NHID));
+  CKS(ensure(c, c->lH2, T * m * BOP_MLP_NHID));
+  CKS(ensure(c, c->lcount, sizeof(unsigned)));
+  LearnedArgs L = learned_args(c, M, mu);
+  CK(cudaMemsetAsync(c->lcount.p, 0, sizeof(unsigned), s));
+  {
+    Region R(c, PK_EXPAND, 1, s);
+    if (launch_learned(0, L, s)) return fail(c, BOP_ERR_CUDA, "features launch failed");
+  }
+  {
+    Region R(c, PK_MLP, 3, s);
+    if (mlp_infer_forward(c->fp64, M, c->lxs.p, mlp_params_dev(c->net), mlp_wbf_dev(c->net), c->lZ1.p, c->lH1.p,
+                          c->lZ2.p, c->lH2.p, c->lys.p, s))
+      return fail(c, BOP_ERR_CUDA, "network launch failed");
+  }
+  Region R(c, PK_EXPAND, 1, s);
+  if (launch_learned(1, L, s)) return fail(c, BOP_ERR_CUDA, "continued-chain expansion launch failed");
+  return BOP_OK;
+}
+
 int run_scalar(bop_ctx* c, int M, const double* mu, cudaStream_t s) {
+  if (c->m.terminator == BOP_TERM_MLP) return run_learned(c, M, mu, s);
   ScalarArgs a;
   a.M = M;
   a.n_mom = c->n_mom;
@@ -503,7 +567,8 @@ int bop_destroy(bop_ctx* c) {
                   &c->a_inf, &c->b_inf, &c->gsig, &c->D, &c->gjack, &c->N, &c->U, &c->dos, &c->fstate,
                   &c->partials, &c->counter, &c->result, &c->e_total, &c->lam, &c->e_atom, &c->w, &c->zscr,
                   &c->adjscr, &c->Hbar, &c->Ebar, &c->status, &c->cub_tmp, &c->nprod,
-                  &c->ginv, &c->hx, &c->hf, &c->gamma, &c->scfred};
+                  &c->ginv, &c->hx, &c->hf, &c->gamma, &c->scfred, &c->lbase, &c->lnlev, &c->lflag, &c->lxs,
+                  &c->lys, &c->lZ1, &c->lH1, &c->lZ2, &c->lH2, &c->lybar, &c->lcot, &c->lxbar, &c->lcount};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -820,8 +885,11 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   if (delta_io) CK(cudaMemcpyAsync(delta_io, c->delta.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   if (m_io && stoner) CK(cudaMemcpyAsync(m_io, c->mval.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   double et = 0.0;
+  unsigned nl = 0;
   CK(cudaMemcpyAsync(&et, c->e_total.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (c->m.terminator == BOP_TERM_MLP) CK(cudaMemcpyAsync(&nl, c->lcount.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CKS(check_status(c, s));
+  c->st.n_learned = (int)nl;
   c->st.scf_iterations = it;
   c->st.scf_converged = converged;
   c->st.bisection_rounds = fs.iters;
@@ -869,7 +937,27 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   wa.dU_dE = nullptr;
   wa.zscratch = P<double>(c->zscr);
   wa.status = P<unsigned>(c->status);
-  {
+  if (c->m.terminator == BOP_TERM_MLP) {
+    if (!c->net) return fail(c, BOP_ERR_STATE, "terminator MLP needs a network (bop_set_mlp)");
+    const size_t T = c->fp64 ? sizeof(double) : sizeof(float);
+    CKS(ensure(c, c->lybar, T * (size_t)M * BOP_MLP_NOUT));
+    CKS(ensure(c, c->lcot, sizeof(double) * (size_t)M * 10));
+    CKS(ensure(c, c->lxbar, T * (size_t)M * BOP_MLP_NIN));
+    LearnedArgs L = learned_args(c, M, P<double>(c->mu));
+    L.W = wa;
+    {
+      Region R(c, PK_WEIGHTS, 1, s);
+      if (launch_learned(2, L, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
+    }
+    {
+      Region R(c, PK_MLP, 3, s);
+      if (mlp_infer_backward(c->fp64, M, c->lybar.p, mlp_wbf_dev(c->net), c->lZ1.p, c->lZ2.p, c->lH1.p, c->lH2.p,
+                             c->lxbar.p, s))
+        return fail(c, BOP_ERR_CUDA, "network reverse launch failed");
+    }
+    Region R(c, PK_WEIGHTS, 1, s);
+    if (launch_learned(3, L, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
+  } else {
     Region R(c, PK_WEIGHTS, 1, s);
     if (launch_weights(wa, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
   }
@@ -983,6 +1071,20 @@ int bop_evaluate_host(bop_ctx* c, int n, const double* pos_host, const double* c
   for (DBuf* q : {&dpos, &dF, &dW})
     if (q->p) cudaFree(q->p);
   return r;
+}
+
+int bop_set_mlp(bop_ctx* c, bop_mlp* net) {
+  if (!c) return BOP_ERR_ARG;
+  if (c->m.terminator != BOP_TERM_MLP) return fail(c, BOP_ERR_ARG, "the model's terminator is not MLP");
+  c->net = net;
+  c->energized = c->weighted = false;
+  return BOP_OK;
+}
+
+int bop_mlp_dataset(long long M, const double* mu17, float* x, float* t, float* mask, bop_stream stream) {
+  if (M < 1 || !mu17 || !x || !t || !mask) return BOP_ERR_ARG;
+  if (launch_mlp_dataset(M, mu17, x, t, mask, S_(stream))) return BOP_ERR_CUDA;
+  return BOP_OK;
 }
 
 int bop_set_profiling(bop_ctx* c, int on) {

@@ -1,0 +1,341 @@
+// Per-orbital pieces of the expansion and of its reverse mode, shared by
+// the constant-terminator kernels (chain.cu) and the learned-terminator
+// kernels (learned.cu): the generating polynomials of the Chebyshev chain
+// (Eq. aexp as a rational generating function), the sigma_m recurrence,
+// and the reverse of each stage (chain -> sigma -> N, P; chain parameters;
+// Gershgorin; moment recursion).
+#pragma once
+#include "scalar_common.cuh"
+
+namespace scal {
+
+// Polynomial coefficients D_0 (Q) and D_1 (P) of sum_m sigma_m t^m = D_1/D_0
+// for a chain of L levels (D_L = D_{L+1} = 1).
+template <int KP>
+__device__ __forceinline__ void gen_polys(const Chain& ch, int L, double Q[2 * KP + 1], double P[2 * KP + 1]) {
+  constexpr int NP = 2 * KP + 1;
+  double d2[NP], d1[NP];
+#pragma unroll
+  for (int j = 0; j < NP; j++) d2[j] = d1[j] = (j == 0) ? 1.0 : 0.0;
+  for (int k = L - 1; k >= 0; k--) {
+    const double a2 = 2.0 * ch.ah[k];
+    const double bb = 4.0 * ch.bh[k + 1] * ch.bh[k + 1];
+    double dn[NP];
+#pragma unroll
+    for (int j = 0; j < NP; j++) {
+      double v = d1[j];
+      if (j >= 1) v -= a2 * d1[j - 1];
+      if (j >= 2) v += d1[j - 2] - bb * d2[j - 2];
+      dn[j] = v;
+    }
+#pragma unroll
+    for (int j = 0; j < NP; j++) {
+      d2[j] = d1[j];
+      d1[j] = dn[j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NP; j++) {
+    Q[j] = d1[j];
+    P[j] = d2[j];
+  }
+}
+
+// g_m sigma_m, m = 0..ne, into gsig[m][M] from the recurrence
+// sigma_m = [D_1]_m - sum_{j>=1} [D_0]_j sigma_{m-j}.  Returns sigma_ne.
+template <int KP>
+__device__ __forceinline__ double sigma_series(double Q[2 * KP + 1], double P[2 * KP + 1], int ne,
+                                               const double* __restrict__ g, double* __restrict__ gsig, int M,
+                                               int o) {
+  constexpr int NP = 2 * KP + 1;
+  double h[NP - 1];  // h[j] = sigma_{m-1-j}
+#pragma unroll
+  for (int j = 0; j < NP - 1; j++) h[j] = 0.0;
+  for (int m = 0; m <= ne; m++) {
+    double v = P[0];
+#pragma unroll
+    for (int j = 0; j < NP - 1; j++) P[j] = P[j + 1];
+    P[NP - 1] = 0.0;
+#pragma unroll
+    for (int j = 1; j < NP; j++) v -= Q[j] * h[j - 1];
+#pragma unroll
+    for (int j = NP - 2; j >= 1; j--) h[j] = h[j - 1];
+    h[0] = v;
+    gsig[(size_t)m * M + o] = g[m] * v;
+  }
+  return h[0];
+}
+
+// ------------------------------------------------------------ recursion with tape
+// The moment recursion of ``recursion`` keeping what its reverse needs: the
+// normalised coefficient vectors c^n (C) and the unnormalised d^n (Dv).
+template <int KP>
+struct RecTape {
+  double C[KP + 1][KP + 2];
+  double Dv[KP][KP + 2];
+};
+
+template <int KP>
+__device__ inline void recursion_taped(const double* mu, Rec& r, RecTape<KP>& tp) {
+  double c[KP + 2], cp[KP + 2], d[KP + 2];
+  for (int j = 0; j < KP + 2; j++) c[j] = cp[j] = 0.0;
+  c[0] = 1.0;
+  r.b[0] = 0.0;
+  r.nlev = KP;
+  r.trunc = false;
+  for (int q = 0; q <= KP; q++)
+    for (int j = 0; j < KP + 2; j++) tp.C[q][j] = 0.0;
+  tp.C[0][0] = 1.0;
+  const double width = fmax(mu[2] - mu[1] * mu[1], 0.0);
+  for (int n = 0; n < KP; n++) {
+    double an = 0.0;
+    for (int j = 0; j <= n; j++)
+      for (int l = 0; l <= n; l++) an += c[j] * c[l] * mu[j + l + 1];
+    r.a[n] = an;
+    for (int j = 0; j < KP + 2; j++) d[j] = 0.0;
+    for (int j = 0; j <= n + 1; j++) d[j] = (j >= 1 ? c[j - 1] : 0.0) - an * c[j] - r.b[n] * cp[j];
+    for (int j = 0; j < KP + 2; j++) tp.Dv[n][j] = d[j];
+    double b2 = 0.0;
+    for (int j = 0; j <= n + 1; j++)
+      for (int l = 0; l <= n + 1; l++) b2 += d[j] * d[l] * mu[j + l];
+    if (b2 <= TRUNC_REL * width) {
+      r.b[n + 1] = 0.0;
+      r.nlev = n + 1;
+      r.trunc = true;
+      for (int q = n + 1; q < KP; q++) {
+        r.a[q] = 0.0;
+        r.b[q + 1] = 0.0;
+      }
+      break;
+    }
+    const double bn = sqrt(b2);
+    r.b[n + 1] = bn;
+    for (int j = 0; j < KP + 2; j++) {
+      cp[j] = c[j];
+      c[j] = d[j] / bn;
+      tp.C[n + 1][j] = c[j];
+    }
+  }
+}
+
+// ------------------------------------------------------------ reverse of the chain
+// Reverse of chain -> sigma_m -> (N, P) -> L = cU U + cN N for one orbital
+// (fixed E_F and onsite level E), U = b_inf P - (E - a_inf) N.  The chain
+// (ch, L levels, b^_k set for k <= Kb) has terminator (ai, bi).  Adds the
+// cotangents of the raw chain coefficients to abar[k] (k < L) and bbar[k]
+// (1 <= k <= min(Kb, L)) and of the terminator to abar_inf, bbar_inf; returns
+// dL/dE.  zs, zb: sigma_m and its cotangent, [ne+1][M] each.
+template <int KP>
+__device__ inline double chain_reverse(const Chain& ch, int L, int Kb, double ai, double bi, double E, double ef,
+                                       const double* __restrict__ g, const double* __restrict__ inv, int ne,
+                                       int M, int o, double cU, double cN, double* zs, double* zb, double* abar,
+                                       double* bbar, double& abar_inf, double& bbar_inf) {
+  constexpr int NP = 2 * KP + 1;
+  // ---- generating polynomials D_0 .. D_{L+1}, all kept
+  double Dk[KP + 2][NP];
+  for (int k = 0; k < KP + 2; k++)
+    for (int j = 0; j < NP; j++) Dk[k][j] = 0.0;
+  Dk[L + 1][0] = 1.0;
+  Dk[L][0] = 1.0;
+  for (int k = L - 1; k >= 0; k--) {
+    const double a2 = 2.0 * ch.ah[k], bb = 4.0 * ch.bh[k + 1] * ch.bh[k + 1];
+    for (int j = 0; j < NP; j++) {
+      double v = Dk[k + 1][j];
+      if (j >= 1) v -= a2 * Dk[k + 1][j - 1];
+      if (j >= 2) v += Dk[k + 1][j - 2] - bb * Dk[k + 2][j - 2];
+      Dk[k][j] = v;
+    }
+  }
+  // ---- sigma_m and the sums N, P, dN/deps, dP/deps
+  {
+    double h[NP - 1];
+    for (int j = 0; j < NP - 1; j++) h[j] = 0.0;
+    for (int m = 0; m <= ne; m++) {
+      double v = m < NP ? Dk[1][m] : 0.0;
+#pragma unroll
+      for (int j = 1; j < NP; j++) v -= Dk[0][j] * h[j - 1];
+#pragma unroll
+      for (int j = NP - 2; j >= 1; j--) h[j] = h[j - 1];
+      h[0] = v;
+      zs[(size_t)m * M + o] = v;
+    }
+  }
+  const double xr = (ef - ai) / (2.0 * bi);
+  const bool inside = xr > -1.0 && xr < 1.0;
+  const double x = clamp1(xr);
+  const double phi = acos(x), s1 = sqrt(fmax(0.0, 1.0 - x * x));
+  const double Nbar = cN - cU * (E - ai), Pbar = cU * bi;
+  double Nv = 0.0, Pv = 0.0, dN = 0.0, dP = 0.0;
+  {
+    // sines s_j = sin(j phi) by the recurrence; chi_j = (s~_{j+1} - s~_{j-1})/pi,
+    // s~_k = sin(k phi)/k, s~_0 = phi - pi
+    double sm1 = 0.0, s0 = 0.0, sp1 = s1, sp2 = 2.0 * x * s1, sp3 = 2.0 * x * sp2 - s1;  // s_{m-1}..s_{m+3}
+    auto chi = [&](int j, double sjm1, double sjp1) -> double {
+      if (j == 0) return 0.0;
+      const double lo = (j == 1) ? (phi - PI) : sjm1 * inv[j - 1];  // s~_{j-1}
+      return (sjp1 * inv[j + 1] - lo) / PI;
+    };
+    for (int m = 0; m <= ne; m++) {
+      const double c_m = chi(m, sm1, sp1), c_m1 = chi(m + 1, s0, sp2), c_m2 = chi(m + 2, sp1, sp3);
+      const double gsm = g[m] * zs[(size_t)m * M + o];
+      Nv += gsm * c_m1;
+      Pv += gsm * (c_m2 + c_m);
+      dN += gsm * sp1;
+      dP += gsm * (sp2 + s0);
+      zb[(size_t)m * M + o] = g[m] * (Nbar * c_m1 + Pbar * (c_m2 + c_m));
+      sm1 = s0;
+      s0 = sp1;
+      sp1 = sp2;
+      sp2 = sp3;
+      sp3 = 2.0 * x * sp2 - sp1;
+    }
+    dN *= 2.0 / PI;
+    dP *= 2.0 / PI;
+  }
+  abar_inf += cU * Nv;
+  bbar_inf += cU * Pv;
+  if (inside) {
+    const double ebar = Nbar * dN + Pbar * dP;
+    abar_inf += -ebar / (2.0 * bi);
+    bbar_inf += -ebar * xr / bi;
+  }
+  // ---- reverse of the recurrence: lambda_m, Pb = dL/d[D_1], Qb = dL/d[D_0]
+  double Pb[NP], Qb[NP];
+  for (int j = 0; j < NP; j++) Pb[j] = Qb[j] = 0.0;
+  {
+    double lf[NP - 1];  // lf[j] = lambda_{m+1+j}
+    double sw[NP - 1];  // sw[j] = sigma_{m-1-j}
+    for (int j = 0; j < NP - 1; j++) {
+      lf[j] = 0.0;
+      const int mm = ne - 1 - j;
+      sw[j] = mm >= 0 ? zs[(size_t)mm * M + o] : 0.0;
+    }
+    for (int m = ne; m >= 0; m--) {
+      double lam = zb[(size_t)m * M + o];
+#pragma unroll
+      for (int j = 1; j < NP; j++) lam -= Dk[0][j] * lf[j - 1];
+      if (m < NP) Pb[m] += lam;
+#pragma unroll
+      for (int j = 1; j < NP; j++) Qb[j] -= lam * sw[j - 1];
+#pragma unroll
+      for (int j = NP - 2; j >= 1; j--) lf[j] = lf[j - 1];
+      lf[0] = lam;
+#pragma unroll
+      for (int j = 0; j < NP - 2; j++) sw[j] = sw[j + 1];
+      const int mm = m - NP;  // sigma_{m-1-(NP-2)} for the next step
+      sw[NP - 2] = mm >= 0 ? zs[(size_t)mm * M + o] : 0.0;
+    }
+  }
+  // ---- reverse of the polynomial recursion -> a^bar, b^bar
+  double ahb[KP + 1], bhb[KP + 2];
+  for (int k = 0; k <= KP; k++) ahb[k] = 0.0;
+  for (int k = 0; k <= KP + 1; k++) bhb[k] = 0.0;
+  {
+    double Db[KP + 2][NP];
+    for (int k = 0; k < KP + 2; k++)
+      for (int j = 0; j < NP; j++) Db[k][j] = 0.0;
+    for (int j = 0; j < NP; j++) {
+      Db[0][j] = Qb[j];
+      Db[1][j] = Pb[j];
+    }
+    for (int k = 0; k < L; k++) {
+      const double a2 = 2.0 * ch.ah[k], bb = 4.0 * ch.bh[k + 1] * ch.bh[k + 1];
+      double ga = 0.0, gb = 0.0;
+      for (int j = 0; j < NP; j++) {
+        const double gg = Db[k][j];
+        Db[k + 1][j] += gg;
+        if (j >= 1) {
+          Db[k + 1][j - 1] -= a2 * gg;
+          ga -= 2.0 * gg * Dk[k + 1][j - 1];
+        }
+        if (j >= 2) {
+          Db[k + 1][j - 2] += gg;
+          Db[k + 2][j - 2] -= bb * gg;
+          gb -= 8.0 * ch.bh[k + 1] * gg * Dk[k + 2][j - 2];
+        }
+      }
+      ahb[k] += ga;
+      bhb[k + 1] += gb;
+    }
+  }
+  // ---- chain parameters a^_k = (a_k - a_inf)/(2 b_inf), b^_k = b_k/(2 b_inf)
+  for (int k = 0; k < L; k++) {
+    abar[k] += ahb[k] / (2.0 * bi);
+    abar_inf += -ahb[k] / (2.0 * bi);
+    bbar_inf += -ahb[k] * ch.ah[k] / bi;
+  }
+  for (int k = 1; k <= Kb; k++)
+    if (k <= L) {
+      bbar[k] += bhb[k] / (2.0 * bi);
+      bbar_inf += -bhb[k] * ch.bh[k] / bi;
+    }
+  return -cU * Nv;
+}
+
+// Reverse of Gershgorin: a_inf = (top+bot)/2, b_inf = (top-bot)/4 with
+// top = a_ihi + b_ihi + b_ihi+1, bot = a_ilo - b_ilo - b_ilo+1 (no
+// b_inf cotangent where the floor is active).
+__device__ inline void gershgorin_reverse(const Term& t, double abar_inf, double bbar_inf, double* abar,
+                                          double* bbar) {
+  const double topb = 0.5 * abar_inf + (t.floored ? 0.0 : 0.25 * bbar_inf);
+  const double botb = 0.5 * abar_inf - (t.floored ? 0.0 : 0.25 * bbar_inf);
+  abar[t.ihi] += topb;
+  bbar[t.ihi] += topb;
+  bbar[t.ihi + 1] += topb;
+  abar[t.ilo] += botb;
+  bbar[t.ilo] -= botb;
+  bbar[t.ilo + 1] -= botb;
+}
+
+// Reverse of the moment recursion: adds d/dmu of (abar . a + bbar . b) to mub.
+template <int KP>
+__device__ inline void recursion_reverse(const double* mu, const Rec& r, const RecTape<KP>& tp, double* abar,
+                                         double* bbar, double* mub) {
+  const int L = r.nlev;
+  double cb[KP + 1][KP + 2];
+  for (int q = 0; q <= KP; q++)
+    for (int j = 0; j < KP + 2; j++) cb[q][j] = 0.0;
+  for (int n = L - 1; n >= 0; n--) {
+    double db[KP + 2];
+    for (int j = 0; j < KP + 2; j++) db[j] = 0.0;
+    const bool made_next = !(r.trunc && n == L - 1);
+    if (made_next) {
+      const double bn = r.b[n + 1];
+      double dotc = 0.0;
+      for (int j = 0; j <= n + 1; j++) {
+        db[j] = cb[n + 1][j] / bn;
+        dotc += cb[n + 1][j] * tp.Dv[n][j];
+      }
+      const double bnb = bbar[n + 1] - dotc / (bn * bn);
+      const double b2b = bnb / (2.0 * bn);
+      for (int j = 0; j <= n + 1; j++) {
+        double acc = 0.0;
+        for (int l = 0; l <= n + 1; l++) {
+          acc += mu[j + l] * tp.Dv[n][l];
+          mub[j + l] += b2b * tp.Dv[n][j] * tp.Dv[n][l];
+        }
+        db[j] += 2.0 * b2b * acc;
+      }
+    }
+    double an_b = abar[n];
+    for (int j = 0; j <= n + 1; j++) {
+      if (j >= 1) cb[n][j - 1] += db[j];
+      cb[n][j] += -r.a[n] * db[j];
+      an_b += -db[j] * tp.C[n][j];
+      if (n >= 1) {
+        bbar[n] += -db[j] * tp.C[n - 1][j];
+        cb[n - 1][j] += -r.b[n] * db[j];
+      }
+    }
+    for (int j = 0; j <= n; j++) {
+      double acc = 0.0;
+      for (int l = 0; l <= n; l++) {
+        acc += mu[j + l + 1] * tp.C[n][l];
+        mub[j + l + 1] += an_b * tp.C[n][j] * tp.C[n][l];
+      }
+      cb[n][j] += 2.0 * an_b * acc;
+    }
+  }
+}
+
+}  // namespace scal

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/bopgb.h"
 #include "common.cuh"
 
 // Cell, its inverse and the linked-cell grid of one structure.
@@ -180,6 +181,41 @@ int launch_weights(const WeightArgs& a, cudaStream_t s);
 int launch_ef_response(int M, int n_exp, const double* gsig, const double* inv, const double* a_inf,
                        const double* b_inf, const double* onsite, const FermiState* st, double* red,
                        unsigned* counter, double* lam, cudaStream_t s);
+
+// learned.cu: the learned terminator (n_mom = 9, continued to 8 levels)
+struct LearnedArgs {
+  int M, n_exp, fp64;
+  const double* mu;      // [M][9]
+  double* base;          // [M][10]: a_0..a_3, b_1..b_4, a_inf, b_inf of the 9-moment chain
+  int* nlev;             // [M] levels of the 9-moment chain
+  unsigned char* flag;   // [M]: 1 = inputs inside the training range, 2 = continued chain used
+  void* xs;              // T [M][18] standardised inputs (T = double if fp64 else float)
+  const void* ys;        // T [M][10] standardised outputs
+  const float* norm;     // [BOP_MLP_NNORM] standardisation and training range
+  double* a_inf;         // [M] terminator of the chain used
+  double* b_inf;
+  double* gsig;          // [n_exp+1][M]
+  const double* g;       // [n_exp+1] damping
+  unsigned* n_learned;   // += orbitals on the continued chain
+  unsigned* status;
+  void* ybar;            // T [M][10] cotangent of the standardised outputs
+  double* cot;           // [M][10] cotangent of the base record
+  const void* xbar;      // T [M][18] cotangent of the standardised inputs
+  WeightArgs W;          // E_F, onsite, damping, 1/k table, cU, lam, w, zscratch
+};
+// stage 0: features, 1: continued chain + expansion, 2: reverse of the chain
+// part, 3: reverse of features / Gershgorin / recursion -> W.w
+int launch_learned(int stage, const LearnedArgs& a, cudaStream_t s);
+int launch_mlp_dataset(long long M, const double* mu17, float* x, float* t, float* mask, cudaStream_t s);
+
+// mlp.cu: network on M rows with the bfloat16 inference weights
+int mlp_infer_forward(int fp64, int M, const void* xs, const float* params, const void* wbf, void* Z1, void* H1,
+                      void* Z2, void* H2, void* ys, cudaStream_t s);
+int mlp_infer_backward(int fp64, int M, const void* ybar, const void* wbf, void* Z1, void* Z2, void* dZ1, void* dZ2,
+                       void* xbar, cudaStream_t s);
+const float* mlp_params_dev(const bop_mlp* net);
+const void* mlp_wbf_dev(const bop_mlp* net);
+const float* mlp_norm_dev(const bop_mlp* net);
 
 // forces.cu
 int launch_forces(int nb, BondModel m, const double* bond_d, const int* bond_atoms, const double* Hbar, int HSu,

@@ -91,6 +91,7 @@ class RunParams:
     dos_floor: float = 0.1
     mixer: str = "anderson"   # linear | anderson (type-II Broyden)
     mix_history: int = 6
+    terminator: str = "constant"  # constant | mlp (learned continuation of the chain, n_mom = 9)
 
 
 @dataclass
@@ -147,6 +148,9 @@ def workload(name: str) -> Workload:
               two spin channels, Stoner I = 0.8 eV from a ferromagnetic start;
               9 moments.
     mag2000   its 2,000-atom (10x10x10x2) counterpart, seed 4.
+    learned131k 131,072-atom bcc (32x32x64x2), jitter 0.05 A, seed 5;
+              canonical d; 9 moments; no SCF (evaluation cell of the
+              learned terminator).
     """
     if name == "s128":
         pos, cell = bcc_jittered(4, 4, 4, 0.05, 1)
@@ -163,7 +167,28 @@ def workload(name: str) -> Workload:
         pos, cell = bcc_jittered(n, n, n, 0.05, 4)
         return Workload(name, pos, cell, (1, 1, 1), MODEL_D,
                         RunParams(n_e=6.8, n_spin=2, scf="stoner", stoner_I=0.8))
+    if name == "learned131k":
+        pos, cell = bcc_jittered(32, 32, 64, 0.05, 5)
+        return Workload(name, pos, cell, (1, 1, 1), MODEL_D, RunParams(n_e=6.8))
     raise KeyError(name)
+
+
+def training_cell(k: int, n: int = 10) -> Workload:
+    """Training cell k of the learned terminator: n x n x n x 2 bcc under a
+    homogeneous symmetric strain, jittered.  Draw order from
+    default_rng(1000 + k): sigma ~ U[0.02, 0.15] A, the strain components
+    (xx, yy, zz, yz, xz, xy) ~ U[-0.03, 0.03], then the jitter.  Canonical d,
+    17 moments, no SCF."""
+    rng = np.random.default_rng(1000 + k)
+    sigma = rng.uniform(0.02, 0.15)
+    e = rng.uniform(-0.03, 0.03, size=6)
+    eps = np.array([[e[0], e[5], e[4]], [e[5], e[1], e[3]], [e[4], e[3], e[2]]])
+    D = np.eye(3) + eps
+    pos, cell = bcc_cell(n, n, n)
+    pos, cell = pos @ D.T, cell @ D.T
+    pos = jittered(pos, cell, (1, 1, 1), sigma, rng)
+    return Workload(f"train{k}", pos, cell, (1, 1, 1), MODEL_D, RunParams(n_e=6.8, n_mom=17),
+                    {"sigma": sigma, "strain": eps})
 
 
 def small_bcc(n1, n2, n3, sigma, seed, model=MODEL_D, run=None, pbc=(1, 1, 1)):
@@ -177,3 +202,36 @@ def small_bcc(n1, n2, n3, sigma, seed, model=MODEL_D, run=None, pbc=(1, 1, 1)):
 
 def with_run(w: Workload, **kw) -> Workload:
     return Workload(w.name, w.pos, w.cell, w.pbc, w.model, replace(w.run, **kw), w.meta)
+
+
+# ---------------------------------------------------------------- learned terminator
+MLP_SHAPES = [(128, 18), (128,), (128, 128), (128,), (10, 128), (10,)]
+
+
+def mlp_init_params(seed: int, scale: float = 1.0) -> np.ndarray:
+    """Initial parameters of the 18-128-128-10 network in the flat layout
+    W1, b1, W2, b2, W3, b3: weights ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from
+    default_rng(seed) in layout order, times scale; zero biases; FP32
+    values (returned as float64)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for s in MLP_SHAPES:
+        if len(s) == 2:
+            lim = 1.0 / np.sqrt(s[1])
+            parts.append(scale * rng.uniform(-lim, lim, size=s).ravel())
+        else:
+            parts.append(np.zeros(s))
+    return np.concatenate(parts).astype(np.float32).astype(np.float64)
+
+
+def mlp_fixed_norm() -> np.ndarray:
+    """A fixed normalisation vector for tests of the learned path (layout
+    x_mean, x_std, x_lo, x_hi, y_mean, y_std): identity standardisation of
+    the inputs with an unbounded range, outputs centred on the constant
+    chain (a*_inf = a_inf, b*_inf = b_inf, a_k = a_inf, b_k = b_inf / 2 in
+    units of b_inf) with standard deviation 0.05."""
+    x_mean, x_std = np.zeros(18), np.ones(18)
+    lo, hi = np.full(18, -1e30), np.full(18, 1e30)
+    y_mean = np.array([0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.5, 0.5, 0.5, 0.5])
+    y_std = np.full(10, 0.05)
+    return np.concatenate([x_mean, x_std, lo, hi, y_mean, y_std]).astype(np.float32).astype(np.float64)

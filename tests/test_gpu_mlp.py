@@ -1,0 +1,195 @@
+"""GPU parity of the learned terminator against the oracle (oracle/mlp.py):
+training data, normalisation, inference, gradient and Adam steps of the
+network, and the learned energy, forces and virial of small cells (FP64 and
+FP32 modes, with and without an SCF); plus the gain test: a network trained
+on the GPU by its own kernels on 17-moment runs brings the 9-moment energy
+closer to the 17-moment energy than the constant terminator does."""
+import numpy as np
+import pytest
+
+from paper_1803_07491_gb300 import inputs as I
+from conftest import oracle_model, oracle_settings
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bop():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_07491_gb300 import build, bop as b
+    build.build()
+    return b
+
+
+@pytest.fixture(scope="module")
+def om(ob):
+    from oracle import mlp
+    return mlp
+
+
+def _oracle_mu17(ob, w):
+    m = oracle_model(w.model)
+    nbr = ob.neighbors(w.pos, w.cell, w.pbc, m.rc)
+    H = ob.blocks(m, w.pos, w.cell, nbr)
+    return ob.moments(nbr, H, np.zeros((len(w.pos), w.model.norb)), 17).reshape(-1, 17)
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b) / np.maximum(1.0, np.abs(b)))
+
+
+def test_dataset_and_normalisation_match_oracle(bop, ob, om):
+    mu = np.concatenate([_oracle_mu17(ob, I.training_cell(k, n=2)) for k in range(3)])
+    mu_d = torch.tensor(mu, device="cuda")
+    x, t, m = bop.bop_mlp_dataset(mu_d)
+    xr, *_ = om.features(mu[:, :9])
+    tr, mr = om.targets(mu)
+    assert np.array_equal(m.cpu().numpy(), mr)
+    assert _rel(x.cpu().numpy(), xr) < 2e-6
+    assert _rel(t.cpu().numpy(), tr) < 2e-6
+    # normalisation of the oracle's data (FP32 inputs) on both sides
+    x32, t32 = xr.astype(np.float32), tr.astype(np.float32)
+    net = bop.Network(I.mlp_init_params(1))
+    net.fit_norm(torch.tensor(x32, device="cuda"), torch.tensor(t32, device="cuda"),
+                 torch.tensor(mr.astype(np.float32), device="cuda"))
+    _, q = net.get()
+    qr = om.fit_normalisation(x32.astype(np.float64), t32.astype(np.float64), mr)
+    assert _rel(q.astype(np.float64), qr) < 1e-5
+    net.close()
+
+
+def test_predict_gradient_adam_match_oracle(bop, om):
+    rng = np.random.default_rng(40)
+    p0 = I.mlp_init_params(41)
+    q0 = I.mlp_fixed_norm()
+    M = 3000
+    x = rng.normal(size=(M, 18)).astype(np.float32)
+    t = rng.normal(size=(M, 10)).astype(np.float32)
+    mk = (rng.uniform(size=M) > 0.1).astype(np.float32)
+    xd, td, md = (torch.tensor(a, device="cuda") for a in (x, t, mk))
+    net = bop.Network(p0)
+    net.set_norm(q0)
+    # inference: bfloat16 weights, FP32 activations
+    y = bop.bop_mlp_predict(net.h, xd).cpu().numpy()
+    yr, _ = om.predict(om.Net(p0, q0), x.astype(np.float64))
+    assert np.max(np.abs(y - yr)) < 2e-5 * max(1.0, np.abs(yr).max())
+    # gradient of one batch (a ragged 1,237 of the rows, in a drawn order)
+    idx = rng.permutation(M)[:1237].astype(np.int32)
+    g = torch.empty(om.N_PARAM, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    bop.bop_mlp_gradient(net.h, xd, td, md, torch.tensor(idx, device="cuda"), g, loss)
+    xm, xsd, _, _, ym, ysd = om.unpack_norm(q0)
+    xs = (x[idx].astype(np.float64) - xm) / xsd
+    ts = (t[idx].astype(np.float64) - ym) / ysd
+    lr_, gr = om.loss_and_grad(p0, xs, ts, mk[idx])
+    assert abs(loss.item() - lr_) < 1e-5 * lr_
+    assert np.max(np.abs(g.cpu().numpy() - gr)) < 1e-4 * np.abs(gr).max()
+    # three Adam steps on three batches
+    st = om.AdamState(np.zeros(om.N_PARAM), np.zeros(om.N_PARAM))
+    p = p0.copy()
+    for k in range(3):
+        b = rng.permutation(M)[:512].astype(np.int32)
+        bop.bop_mlp_train_step(net.h, xd, td, md, torch.tensor(b, device="cuda"), 1e-3)
+        xs = (x[b].astype(np.float64) - xm) / xsd
+        ts = (t[b].astype(np.float64) - ym) / ysd
+        _, gk = om.loss_and_grad(p, xs, ts, mk[b])
+        p = om.adam(p, gk, st, 1e-3)
+    pg, _ = net.get()
+    assert np.max(np.abs(pg - p)) < 2e-6
+    net.close()
+
+
+@pytest.mark.parametrize("prec,scf", [("fp64", "none"), ("fp64", "lcn"), ("fp32", "none")])
+def test_learned_energy_forces_match_oracle(bop, ob, om, prec, scf):
+    w = I.small_bcc(2, 2, 2, 0.08, 22)
+    run = I.with_run(w, terminator="mlp", scf=scf, scf_tol=1e-10 if prec == "fp64" else 1e-5).run
+    p = I.mlp_init_params(23, 0.3)
+    q = I.mlp_fixed_norm()
+    net = bop.Network(p)
+    net.set_norm(q)
+    ctx = bop.Context(w.model, run, prec, net=net)
+    res = ctx.evaluate(w.pos, w.cell, w.pbc)
+    st = oracle_settings(run)
+    st.terminator, st.net = "mlp", om.Net(p, q)
+    ref = ob.evaluate(oracle_model(w.model), st, w.pos, w.cell, w.pbc)
+    n = len(w.pos)
+    assert res.stats["n_learned"] == int(ref["learned"].sum()) > 0
+    # FP32 products: 1 meV/atom and 1e-2 eV/A, as for the constant terminator
+    tolE, tolF = (1e-9, 1e-8) if prec == "fp64" else (1e-3, 1e-2)
+    assert abs(res.e_total - ref["e_total"]) < tolE * n
+    assert np.max(np.abs(res.e_atom.cpu().numpy() - ref["e_atom"])) < tolE
+    assert np.max(np.abs(res.forces.cpu().numpy() - ref["forces"])) < tolF
+    assert np.max(np.abs(res.virial.cpu().numpy() - ref["virial"])) < tolF * n
+    # the network changes the energy: the constant terminator differs
+    plain = bop.Context(w.model, I.with_run(w, scf=scf).run, prec).evaluate(w.pos, w.cell, w.pbc, forces=False)
+    assert abs(plain.e_total - res.e_total) > 1e-3
+    ctx.close()
+    net.close()
+
+
+def test_learned_fallback_is_constant_terminator(bop):
+    w = I.small_bcc(2, 2, 2, 0.08, 24)
+    q = I.mlp_fixed_norm().copy()
+    q[36:54] = 1e29   # x_lo above every input: nothing is in range
+    net = bop.Network(I.mlp_init_params(25))
+    net.set_norm(q)
+    res = bop.Context(w.model, I.with_run(w, terminator="mlp").run, "fp64", net=net).evaluate(w.pos, w.cell, w.pbc)
+    ref = bop.Context(w.model, w.run, "fp64").evaluate(w.pos, w.cell, w.pbc)
+    assert res.stats["n_learned"] == 0
+    assert abs(res.e_total - ref.e_total) < 1e-10 * len(w.pos)
+    assert np.max(np.abs(res.forces.cpu().numpy() - ref.forces.cpu().numpy())) < 1e-10
+    net.close()
+
+
+def test_mlp_terminator_needs_nine_moments_and_a_network(bop):
+    w = I.small_bcc(2, 2, 2, 0.05, 26)
+    with pytest.raises(bop.BopError):
+        bop.bop_create(bop.make_model(w.model, I.with_run(w, terminator="mlp", n_mom=11).run))
+    ctx = bop.Context(w.model, I.with_run(w, terminator="mlp").run)
+    ctx.build(w.pos, w.cell, w.pbc)
+    with pytest.raises(bop.BopError) as e:
+        ctx.energy()
+    assert e.value.status == bop.BOP_ERR_STATE
+    plain = bop.Context(w.model, w.run)
+    with pytest.raises(bop.BopError) as e:
+        bop.bop_set_mlp(plain.h, None)
+    assert e.value.status == bop.BOP_ERR_ARG
+
+
+def _gpu_mu17(bop, w):
+    ctx = bop.Context(w.model, I.with_run(w, n_mom=17).run, "fp64")
+    ctx.build(w.pos, w.cell, w.pbc)
+    mu = bop.bop_moments(ctx.h, 1, w.n_atoms, 5, 17)
+    ctx.close()
+    return mu.reshape(-1, 17)
+
+
+def test_trained_network_beats_constant_terminator(bop):
+    """Train on 17-moment runs of 24 strained, jittered 250-atom cells
+    (generated and trained on the GPU), then compare energies per atom of
+    an unseen 2,000-atom cell: the learned 9-moment energy is closer to the
+    17-moment energy than the 9-moment constant-terminator energy."""
+    data = [bop.bop_mlp_dataset(_gpu_mu17(bop, I.training_cell(k, n=5))) for k in range(24)]
+    x = torch.cat([d[0] for d in data])
+    t = torch.cat([d[1] for d in data])
+    m = torch.cat([d[2] for d in data])
+    assert m.mean().item() > 0.99
+    net = bop.Network(I.mlp_init_params(7))
+    net.fit_norm(x, t, m)
+    losses = net.train(x, t, m, epochs=40, batch=512, lr=2e-3, seed=8, lr_final=2e-4)
+    assert losses[-1] < 0.7 * losses[0]
+    pos, cell = I.bcc_jittered(10, 10, 10, 0.05, 5)
+    ev = I.Workload("eval", pos, cell, (1, 1, 1), I.MODEL_D, I.RunParams(n_e=6.8))
+    n = ev.n_atoms
+    e17 = bop.Context(ev.model, I.with_run(ev, n_mom=17).run).evaluate(pos, cell, ev.pbc, forces=False).e_total
+    e9 = bop.Context(ev.model, ev.run).evaluate(pos, cell, ev.pbc, forces=False).e_total
+    lr = bop.Context(ev.model, I.with_run(ev, terminator="mlp").run, net=net).evaluate(pos, cell, ev.pbc)
+    err_plain = abs(e9 - e17) / n
+    err_learned = abs(lr.e_total - e17) / n
+    print(f"per-atom |E - E17|: constant terminator {err_plain:.3e} eV, learned {err_learned:.3e} eV, "
+          f"learned orbitals {lr.stats['n_learned']}/{5 * n}, loss {losses[0]:.3e} -> {losses[-1]:.3e}")
+    assert lr.stats["n_learned"] > 0.95 * 5 * n
+    assert err_learned < 0.5 * err_plain
+    net.close()

@@ -1,17 +1,16 @@
 """GPU checks at the sizes bench.py times, plus the error paths of the ABI.
 
-Full-size structures are too large for the whole oracle run, so they are
-checked on sampled outputs the oracle computes one by one (the moments of
-sampled atoms at the GPU's converged onsite levels, their per-orbital
-electron count and bond energy at the GPU's Fermi level) and through
-properties that hold at any size (electron count, local neutrality,
-central finite differences of the GPU energy, h = 1e-4 Angstrom).
+The 2,000-atom cell with fixed onsite levels is compared with the oracle's
+own run of it, whole; its SCF version and the 16,320-atom slab, too large
+for the oracle, are checked through properties that hold at any size
+(electron count, local neutrality, zero net force, central finite
+differences of the GPU energy).
 """
 import numpy as np
 import pytest
 
 from paper_1803_07491_gb300 import inputs as I
-from conftest import oracle_model
+from conftest import oracle_model, oracle_settings
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -26,41 +25,42 @@ def bop():
     return b
 
 
-@pytest.mark.parametrize("prec,tol_mu", [("fp64", 1e-11), ("fp32", 3e-6)])
-def test_d2000_lcn_sampled_against_oracle(bop, ob, prec, tol_mu):
-    """The bench workload (2,000 atoms, d, LCN SCF, 9 moments)."""
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_d2000_lcn_properties(bop, prec):
+    """The bench workload (2,000 atoms, d, LCN SCF, 9 moments): properties
+    that hold at any size (electron count, local neutrality to the SCF
+    tolerance, zero net force)."""
     w = I.workload("d2000")
     if prec == "fp32":
         w = I.with_run(w, scf_tol=1e-5)
     ctx = bop.Context(w.model, w.run, prec)
     ctx.build(w.pos, w.cell, w.pbc)
-    delta = torch.zeros(w.n_atoms, dtype=torch.float64, device="cuda")
-    e, st = ctx.energy(delta=delta)
+    e, st = ctx.energy()
     F, W = ctx.forces()
     assert st["scf_converged"] == 1
-    M = w.n_atoms * 5
-    orb = bop.bop_get_orbital_state(ctx.h, M, 9)
+    orb = bop.bop_get_orbital_state(ctx.h, w.n_atoms * 5, 9)
     N = orb["N"].cpu().numpy().reshape(w.n_atoms, 5)
-    # properties at any size: electron count, local neutrality, zero net force
     assert abs(2 * N.sum() - 6.8 * w.n_atoms) < 1e-8 * w.n_atoms
     assert np.max(np.abs(2 * N.sum(axis=1) - 6.8)) < w.run.scf_tol
     assert np.abs(F.sum(dim=0).cpu().numpy()).max() < (1e-9 if prec == "fp64" else 1e-4) * w.n_atoms
-    # sampled atoms through the oracle, at the GPU's onsite levels
-    m = oracle_model(w.model)
-    nbr = ob.neighbors(w.pos, w.cell, w.pbc, m.rc)
-    H = ob.blocks(m, w.pos, w.cell, nbr)
-    onsite = orb["onsite"].cpu().numpy().reshape(w.n_atoms, 5)
-    sel = np.array([0, 17, 555, 1024, 1999], np.int32)
-    mu_ref = ob.moments(nbr, H, onsite, 9, sel=sel)
-    mu_gpu = orb["mu"].cpu().numpy().reshape(w.n_atoms, 5, 9)[sel]
-    scale = np.abs(mu_ref).max(axis=-1, keepdims=True) + 1.0
-    assert np.max(np.abs(mu_gpu - mu_ref) / scale) < tol_mu
-    ex = ob.scalar_stage(mu_ref.reshape(-1, 9), 200)
-    Nr, Ur = ob.orbital_N_U(ex.gsig, ex.a_inf, ex.b_inf, onsite[sel].reshape(-1), st["e_fermi"])
-    Ug = orb["U"].cpu().numpy().reshape(w.n_atoms, 5)[sel].reshape(-1)
-    tolE = 1e-9 if prec == "fp64" else 1e-4
-    assert np.max(np.abs(N[sel].reshape(-1) - Nr)) < tolE
-    assert np.max(np.abs(Ug - Ur)) < tolE
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol_mu,tol_e", [("fp64", 1e-11, 1e-9), ("fp32", 3e-6, 1e-3)])
+def test_d2000_fixed_onsite_against_oracle(bop, ob, prec, tol_mu, tol_e):
+    """The 2,000-atom cell with fixed onsite levels, whole: every moment, the
+    Fermi level and every atom's energy against the oracle's own run."""
+    w = I.workload("d2000nscf")
+    ctx = bop.Context(w.model, w.run, prec)
+    res = ctx.evaluate(w.pos, w.cell, w.pbc, forces=False)
+    ref = ob.evaluate(oracle_model(w.model), oracle_settings(w.run), w.pos, w.cell, w.pbc, want_forces=False)
+    orb = bop.bop_get_orbital_state(ctx.h, w.n_atoms * 5, 9)
+    mu = orb["mu"].cpu().numpy().reshape(w.n_atoms, 5, 9)
+    mr = ref["mu"][0]
+    scale = np.abs(mr).max(axis=-1, keepdims=True) + 1.0
+    assert np.max(np.abs(mu - mr) / scale) < tol_mu
+    assert abs(res.e_fermi - ref["e_fermi"]) < (1e-9 if prec == "fp64" else 1e-4)
+    assert np.max(np.abs(res.e_atom.cpu().numpy() - ref["e_atom"])) < tol_e
     ctx.close()
 
 

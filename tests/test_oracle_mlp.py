@@ -52,7 +52,7 @@ def test_gelu_tabulated_values_and_torch(om):
 
 
 def test_forward_loss_gradient_match_torch(om):
-    p = om.init_params(3)
+    p = I.mlp_init_params(3)
     xs, ts, m = _data(4)
     f, leaves = _torch_net(om, p)
     y = f(torch.tensor(xs))
@@ -67,7 +67,7 @@ def test_forward_loss_gradient_match_torch(om):
 
 
 def test_gradient_by_central_differences(om):
-    p = om.init_params(5)
+    p = I.mlp_init_params(5)
     xs, ts, m = _data(6, B=16)
     _, g = om.loss_and_grad(p, xs, ts, m)
     rng = np.random.default_rng(7)
@@ -81,7 +81,7 @@ def test_gradient_by_central_differences(om):
 
 
 def test_input_gradient_matches_torch(om):
-    p = om.init_params(8)
+    p = I.mlp_init_params(8)
     xs, _, _ = _data(9, B=8)
     ybar = np.random.default_rng(10).normal(size=(8, 10))
     f, _ = _torch_net(om, p)
@@ -91,7 +91,7 @@ def test_input_gradient_matches_torch(om):
 
 
 def test_adam_matches_torch(om):
-    p = om.init_params(11)
+    p = I.mlp_init_params(11)
     rng = np.random.default_rng(12)
     pt = torch.tensor(p, requires_grad=True)
     opt = torch.optim.Adam([pt], lr=3e-3, betas=(0.9, 0.999), eps=1e-8)
@@ -179,7 +179,7 @@ def _fitted_net(ob, om, seed, w):
     # widen the range so that displaced structures stay inside it
     xm, xs, lo, hi, ym, ys = om.unpack_norm(q)
     q = np.concatenate([xm, xs, lo - 0.5 * (hi - lo) - 1e-3, hi + 0.5 * (hi - lo) + 1e-3, ym, ys])
-    p = om.init_params(seed) * 0.3
+    p = I.mlp_init_params(seed, 0.3)
     return om.Net(p, q)
 
 
