@@ -6,7 +6,13 @@ sweep, forces and virial) on the 2,000-atom d-valent bcc workload (10x10x10
 conventional cells, canonical d model, local charge neutrality, 9 moments).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload d2000] [--precision fp32|fp64]
+                    [--workload d2000|learned131k|...] [--precision fp32|fp64]
+
+--workload learned131k trains the learned terminator on the GPU (17-moment
+runs of 200 strained, jittered 2,000-atom cells; not timed), reports the
+per-atom energy error of the learned 9-moment form and of the constant
+terminator at 9..15 moments against 17 moments, and times E+F of the
+learned form and of the cheapest constant-terminator form within 1 meV/atom.
 
 Prints one JSON line (rank 0).  With N > 1 (torchrun), every rank evaluates
 its own copy of the workload (independent problems, no collective on the
@@ -127,13 +133,9 @@ def aggregate(t_local_ms: float, units_local: int, world: int):
 
 
 # ------------------------------------------------------------ our arm
-def run_ours(args):
-    import numpy as np
+def setup_dist():
     import torch
     import torch.distributed as dist
-
-    from paper_1803_07491_gb300 import bop, build, inputs as I
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -142,15 +144,16 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     else:
         torch.cuda.set_device(0)
-    if rank == 0:
-        build.build()
-    if world > 1:
-        dist.barrier()
-    w = I.workload(args.workload)
-    if args.precision == "fp32" and w.run.scf != "none":
-        # FP32 moments put a floor of a few 1e-6 electrons under N_i
-        w = I.with_run(w, scf_tol=FP32_SCF_TOL)
-    ctx = bop.Context(w.model, w.run, args.precision)
+    return world, rank
+
+
+def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: str) -> dict:
+    """Times `steps` E+F evaluations of workload w through ctx (device
+    buffers, CUDA events, L2 flushed between steps), then the same through
+    the host-buffer entry point; returns the JSON fields of one line."""
+    import torch
+    import torch.distributed as dist
+
     pos = torch.tensor(w.pos, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -160,10 +163,9 @@ def run_ours(args):
         ctx.energy()
         return ctx.forces()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    stats = bop.bop_get_stats(ctx.h)
     bop.bop_set_profiling(ctx.h, True)
     bop.bop_reset_profile(ctx.h)
     sampler = ClockSampler(torch.cuda.current_device())
@@ -172,7 +174,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     times = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -188,8 +190,7 @@ def run_ours(args):
     prof = bop.bop_get_profile(ctx.h)
     bop.bop_set_profiling(ctx.h, False)
     stats = bop.bop_get_stats(ctx.h)
-    value, t_ms = aggregate(t_ms, w.n_atoms * args.steps, world)
-    atoms = w.n_atoms * args.steps * world
+    value, t_ms = aggregate(t_ms, w.n_atoms * steps, world)
     launches = sum(v["launches"] for v in prof.values())
 
     # end to end through the C ABI with host buffers (pinned)
@@ -200,19 +201,19 @@ def run_ours(args):
     bop.bop_evaluate_host(ctx.h, pos_h, w.cell, w.pbc, e_h, f_h, v_h)
     torch.cuda.synchronize()
     te = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         bop.bop_evaluate_host(ctx.h, pos_h, w.cell, w.pbc, e_h, f_h, v_h)
         te.append(time.perf_counter() - t0)
-    e2e_value, _ = aggregate(sum(te) * 1e3, w.n_atoms * args.steps, world)
+    e2e_value, _ = aggregate(sum(te) * 1e3, w.n_atoms * steps, world)
 
     # roofline of the dominant kernel family (live CUDA-event times)
     fam = max(prof, key=lambda k: prof[k]["ms"])
     flops = algorithmic_flops(fam, w, {**stats, "moment_products": stats_products(ctx, bop)}, prof, w.run.n_spin)
     per_region_ms = prof[fam]["ms"] / max(1, prof[fam]["regions"])
-    fp64_family = fam in ("expand", "fermi", "weights", "orbital_NU", "ef_response") or args.precision == "fp64"
+    fp64_family = fam in ("expand", "fermi", "weights", "orbital_NU", "ef_response") or precision == "fp64"
     peak = PEAK_FP64_TFLOPS if fp64_family else PEAK_FP32_TFLOPS
     roof = None
     if flops is not None:
@@ -221,34 +222,138 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": profile_traffic(fam),
                 "peak_source": "derived: SMs x lanes x 2 x max SM clock (FP64 for the scalar stages)",
                 "region_ms": round(per_region_ms, 4)}
-
-    line = {
-        "metric": METRIC, "value": round(value, 2), "unit": "atoms/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4), "higher_is_better": True,
+    return {
+        "metric": METRIC, "value": round(value, 2), "unit": "atoms/s", "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": round(t_ms / steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "fp32 products + fp64 scalar stages" if args.precision == "fp32" else "f64",
+        "dtype": "fp32 products + fp64 scalar stages" if precision == "fp32" else "f64",
         "data": "synthetic (seeded jittered bcc, random-free model parameters)",
         "config": {"workload": args.workload, "atoms": w.n_atoms, "orbitals": w.model.norb,
                    "n_mom": w.run.n_mom, "n_exp": w.run.n_exp, "scf": w.run.scf,
+                   "terminator": w.run.terminator,
                    "scf_iterations": stats["scf_iterations"], "scf_tol": w.run.scf_tol,
                    "bisection_rounds": stats["bisection_rounds"],
-                   "precision": args.precision, "l2": "flushed between steps (512 MB write)",
+                   "precision": precision, "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "gpu_launches": launches,
         "e2e": {"value": round(e2e_value, 2), "unit": "atoms/s",
                 "h2d_bytes_per_step": w.n_atoms * 3 * 8,
                 "d2h_bytes_per_step": w.n_atoms * 8 + w.n_atoms * 3 * 8 + 9 * 8},
         "roofline": roof,
-        "kernels": {k: {"ms_per_step": round(v["ms"] / args.steps, 4),
-                        "launches_per_step": v["launches"] / args.steps} for k, v in prof.items() if v["launches"]},
+        "kernels": {k: {"ms_per_step": round(v["ms"] / steps, 4),
+                        "launches_per_step": v["launches"] / steps} for k, v in prof.items() if v["launches"]},
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload)
+
+
+def run_ours(args):
+    import torch.distributed as dist
+
+    from paper_1803_07491_gb300 import bop, build, inputs as I
+
+    world, rank = setup_dist()
     if rank == 0:
-        print(json.dumps(line), flush=True)
-    ctx.close()
+        build.build()
+    if world > 1:
+        dist.barrier()
+    if args.workload == "learned131k":
+        run_learned(args, bop, I, world, rank)
+    else:
+        w = I.workload(args.workload)
+        if args.precision == "fp32" and w.run.scf != "none":
+            # FP32 moments put a floor of a few 1e-6 electrons under N_i
+            w = I.with_run(w, scf_tol=FP32_SCF_TOL)
+        ctx = bop.Context(w.model, w.run, args.precision)
+        line = measure(bop, ctx, w, args, world, args.steps, args.warmup, args.precision)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.workload)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ learned terminator
+LEARNED_CELLS = 200    # training cells (10x10x10x2, strained and jittered)
+LEARNED_EPOCHS = 30
+LEARNED_BATCH = 4096
+
+
+def train_learned(bop, I, n_cells: int, epochs: int, batch: int, seed: int = 7):
+    """Training data from 17-moment runs of n_cells training cells and the
+    network trained on it, all on the GPU (not timed)."""
+    import torch
+    t0 = time.perf_counter()
+    ctx = bop.Context(I.MODEL_D, I.RunParams(n_e=6.8, n_mom=17), "fp64")
+    xs, ts, ms = [], [], []
+    for k in range(n_cells):
+        w = I.training_cell(k)
+        ctx.build(w.pos, w.cell, w.pbc)
+        mu = bop.bop_moments(ctx.h, 1, w.n_atoms, 5, 17)
+        x, t, m = bop.bop_mlp_dataset(mu.reshape(-1, 17))
+        xs.append(x)
+        ts.append(t)
+        ms.append(m)
+    ctx.close()
+    x, t, m = torch.cat(xs), torch.cat(ts), torch.cat(ms)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    net = bop.Network(I.mlp_init_params(seed))
+    net.fit_norm(x, t, m)
+    losses = net.train(x, t, m, epochs=epochs, batch=batch, lr=2e-3, seed=seed + 1, lr_final=1e-4)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    info = {"cells": n_cells, "orbitals": int(x.shape[0]), "valid": int(m.sum().item()), "epochs": epochs,
+            "batch": batch, "loss_first_epoch": round(losses[0], 5), "loss_last_epoch": round(losses[-1], 5),
+            "data_s": round(t1 - t0, 2), "train_s": round(t2 - t1, 2)}
+    return net, info
+
+
+def run_learned(args, bop, I, world: int, rank: int):
+    """Learned terminator vs constant terminator on the 131,072-atom cell:
+    per-atom energy error of each against the 17-moment constant-terminator
+    energy (FP64), then E+F throughput of the learned 9-moment form and of
+    the cheapest constant-terminator form within 1 meV/atom."""
+    net, info = train_learned(bop, I, LEARNED_CELLS, LEARNED_EPOCHS, LEARNED_BATCH)
+    w = I.workload("learned131k")
+    n = w.n_atoms
+
+    def energy(run, prec="fp64", with_net=False):
+        ctx = bop.Context(w.model, run, prec, net=net if with_net else None)
+        r = ctx.evaluate(w.pos, w.cell, w.pbc, forces=False)
+        ctx.close()
+        return r
+
+    e_ref = energy(I.with_run(w, n_mom=17).run).e_total
+    err = {}
+    for nm in (9, 11, 13, 15):
+        err[f"constant_{nm}"] = abs(energy(I.with_run(w, n_mom=nm).run).e_total - e_ref) / n * 1e3
+    rl = energy(I.with_run(w, terminator="mlp").run, "fp64", True)
+    err["learned_9"] = abs(rl.e_total - e_ref) / n * 1e3
+    rl32 = energy(I.with_run(w, terminator="mlp").run, "fp32", True)
+    err["learned_9_fp32"] = abs(rl32.e_total - e_ref) / n * 1e3
+    n_star = next((nm for nm in (9, 11, 13, 15) if err[f"constant_{nm}"] <= 1.0), 17)
+    steps = min(args.steps, 10)
+    wl = I.with_run(w, terminator="mlp")
+    ctx = bop.Context(wl.model, wl.run, args.precision, net=net)
+    line = measure(bop, ctx, wl, args, world, steps, args.warmup, args.precision)
+    ctx.close()
+    wp = I.with_run(w, n_mom=n_star)
+    ctx = bop.Context(wp.model, wp.run, args.precision)
+    plain = measure(bop, ctx, wp, args, world, steps, min(args.warmup, 3), args.precision)
+    ctx.close()
+    line["learned_vs_plain"] = {
+        "reference": "17 moments, constant terminator, FP64",
+        "error_mev_per_atom": {k: round(v, 4) for k, v in err.items()},
+        "learned_orbitals": rl.stats["n_learned"], "orbitals": 5 * n,
+        "learned": {"n_mom": 9, "atoms_per_s": line["value"], "ms_per_step": line["ms_per_step"]},
+        "constant_within_1mev": {"n_mom": n_star, "atoms_per_s": plain["value"],
+                                 "ms_per_step": plain["ms_per_step"], "kernels": plain["kernels"]},
+        "training": info,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    net.close()
 
 
 def stats_products(ctx, bop) -> int:

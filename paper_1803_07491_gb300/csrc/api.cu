@@ -4,6 +4,7 @@
 // the kernels of nbr.cu, cluster.cu, moments.cu, scalar.cu and forces.cu;
 // this file only sizes buffers, launches and reads back flags.
 #include <cub/cub.cuh>
+#include <cuda/std/functional>
 
 #include <cmath>
 #include <cstdarg>
@@ -173,12 +174,14 @@ int check_status(bop_ctx* c, cudaStream_t s) {
   return fail(c, BOP_ERR_CUDA, "device status 0x%x", h);
 }
 
+// Exclusive prefix sum accumulated in the output type (an int count
+// summed into 64-bit offsets must not wrap at 2^31).
 template <class Tin, class Tout>
 int exclusive_scan(bop_ctx* c, const Tin* in, Tout* out, long long n, cudaStream_t s) {
   size_t tmp = 0;
-  CK(cub::DeviceScan::ExclusiveSum(nullptr, tmp, in, out, (int)n, s));
+  CK(cub::DeviceScan::ExclusiveScan(nullptr, tmp, in, out, cuda::std::plus<Tout>{}, Tout(0), (int)n, s));
   CKS(ensure(c, c->cub_tmp, tmp));
-  CK(cub::DeviceScan::ExclusiveSum(c->cub_tmp.p, tmp, in, out, (int)n, s));
+  CK(cub::DeviceScan::ExclusiveScan(c->cub_tmp.p, tmp, in, out, cuda::std::plus<Tout>{}, Tout(0), (int)n, s));
   return BOP_OK;
 }
 
