@@ -88,7 +88,12 @@ enum { BOP_TERM_CONSTANT = 0, BOP_TERM_MLP = 1 };
  * terminator: BOP_TERM_CONSTANT (Eq. abinf with the Gershgorin band edges)
  * or BOP_TERM_MLP, the learned continuation of the chain (n_mom must be 9;
  * a network must be attached with bop_set_mlp, see the learned-terminator
- * section below). */
+ * section below).
+ * scf_response: with an SCF, 1 = forces and virial are the total derivative
+ * of the self-consistent energy (the onsite shifts, and for STONER the
+ * moments, follow the atoms; an adjoint linear solve, see bop_forces);
+ * 0 = the derivative at fixed onsite levels (the Hellmann-Feynman form of
+ * Eq. F_k, which the paper notes is not exact for a non-variational SCF). */
 typedef struct {
   int norb;
   double b0[3];
@@ -106,6 +111,7 @@ typedef struct {
   int mixer;
   int mix_history;
   int terminator;
+  int scf_response;
 } bop_model;
 
 typedef struct {
@@ -127,6 +133,9 @@ typedef struct {
                              energy; the others fell back to the constant terminator */
   long long moment_products; /* block products Psi_k(t) += H_ts Psi_k-1(s) of one
                                 moments pass, summed over atoms (one spin) */
+  int response_iterations;   /* GMRES iterations of the SCF-response solve (last forces) */
+  int response_converged;    /* 1 if that solve reached its tolerance */
+  double response_residual;  /* its final relative residual */
 } bop_stats;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -205,8 +214,16 @@ int bop_energy(bop_ctx* ctx, double* e_atom, double* delta_io, double* m_io, bop
 
 /* Forces (Eq. F_k) and virial W_ab = sum_bonds g_a d_b = dE/dF_ab for a
  * deformation r -> F r (Eq. sigma_k summed over atoms), as the exact
- * derivative of the energy of the last bop_energy call at fixed onsite
- * levels with E_F following the electron count.
+ * derivative of the energy of the last bop_energy call with E_F following
+ * the electron count.  With an SCF and model.scf_response = 1 the
+ * derivative includes the response of the SCF unknowns u (delta_i, and
+ * m_i for STONER): with R(u) = 0 the SCF conditions at fixed E_F and
+ * J = dR/du, the multipliers y of J^T y = dE/du (GMRES, right-preconditioned
+ * by the inverse local DOS, each product J^T v one reverse sweep of the
+ * moments) give dE/dx = dE/dx|_u - y . dR/dx|_u; stats report its
+ * iterations and residual (relative tolerance 1e-10 in FP64 mode, 1e-5
+ * with FP32 products).  BOP_ERR_NO_CONVERGENCE if it stops at 120
+ * iterations above tolerance (outputs then use the last iterate).
  *   forces device [n][3], virial device [3][3] (row-major), either may be NULL.
  * Errors: BOP_ERR_STATE without a preceding bop_energy. */
 int bop_forces(bop_ctx* ctx, double* forces, double* virial, bop_stats* stats_host, bop_stream stream);

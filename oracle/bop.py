@@ -115,6 +115,7 @@ class Settings:
     mix_history: int = 6
     terminator: str = "constant"  # constant | mlp (learned continuation, oracle/mlp.py)
     net: object = None            # mlp.Net for terminator = "mlp"
+    scf_response: bool = True     # forces include the response of the SCF onsite levels
 
 
 @dataclass
@@ -521,7 +522,7 @@ def weights(mu, E_on, E_F, n_exp: int, spin_factor: float, stage=None):
     dU_dE = spin_factor * np.imag(U) / CS_H
     lam = np.sum(dU_dEF) / np.sum(dN_dEF)
     w = spin_factor * (dU - lam * dN)
-    return w, dU_dE, dN, dN_dEF, dU_dEF
+    return w, dU_dE, dN, dN_dEF, dU_dEF, dU
 
 
 # ---------------------------------------------------------------- driver
@@ -533,9 +534,10 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
     Flow of Fig. BOP-calculation: neighbours -> H -> [moments -> recursion ->
     terminator -> E_F -> N, U -> onsite update]* -> energy -> weights ->
     reverse sweep -> forces.  Forces are the exact derivative of the energy
-    at fixed onsite levels with E_F following the electron count; with an
-    SCF the response of the onsite levels is not included (flag
-    ``forces_include_scf_response`` = False)."""
+    with E_F following the electron count.  With an SCF the forces are the
+    total derivative of the self-consistent energy (``scf_response``, the
+    default; see ``scf_response_weights``), otherwise the derivative at fixed
+    onsite levels (the Hellmann-Feynman form of Eq. F_k)."""
     pos = np.asarray(pos, np.float64)
     n = len(pos)
     norb = model.norb
@@ -617,8 +619,14 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
                neighbors=nbr, H=H, onsite=onsite, forces_include_scf_response=st.scf == "none",
                learned=getattr(ex, "learned", None))
     if want_forces:
-        w, dU_dE, *_ = weights(mu_f, onsite.reshape(-1), E_F, st.n_exp, s, stage)
+        w, dU_dE, dN, _, _, dU = weights(mu_f, onsite.reshape(-1), E_F, st.n_exp, s, stage)
         w = w.reshape(S, n, norb, st.n_mom)
+        resp = st.scf != "none" and st.scf_response
+        if resp:
+            w, lam_scf = scf_response_weights(st, nbr, H, onsite, m, s * dU.reshape(w.shape),
+                                              dU_dE.reshape(S, n, norb), dN.reshape(w.shape))
+            out.update(scf_multipliers=lam_scf)
+        out["forces_include_scf_response"] = st.scf == "none" or resp
         Hbar = np.zeros((nbr.n_edges, norb, norb))
         for v in range(S):
             hb, _ = moments_adjoint(nbr, H, onsite[v], w[v])
@@ -632,3 +640,63 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
         vir = np.einsum("ea,eb->ab", g, dvec)
         out.update(forces=F, virial=vir, weights=w, Hbar=Hbar)
     return out
+
+
+def scf_response_weights(st: Settings, nbr: Neighbors, H, onsite, m, wU, dUE, wN):
+    """Weights dE/dmu of the self-consistent energy including the response
+    of the SCF unknowns u (the per-atom shifts delta, and for Stoner the
+    moments m), by the implicit function theorem written out densely.
+
+    SCF conditions at fixed E_F: R_i = s sum_{alpha,nu} N_i - n_e = 0 and,
+    for Stoner, Q_i = sum_alpha (N_i,up - N_i,down) - m_i = 0, with the onsite
+    levels E_i alpha nu = E0 + delta_i -/+ I m_i / 2.  A joint shift of all
+    levels and E_F leaves N and U unchanged, so with E_F held fixed the
+    partial derivatives below already satisfy the stationarity condition of
+    E_F and no gauge multiplier enters.  With J = d(R, Q)/du and
+    g = dE/du (both at fixed E_F and structure), J^T y = g gives the
+    multipliers y = (lambda, kappa), and
+        dE/dx = dE/dx|_u - lambda . dR/dx|_u - kappa . dQ/dx|_u,
+    i.e. the weights w = wU - c w^N with c_i,nu = s lambda_i + sigma_nu kappa_i
+    (sigma = +1 up, -1 down).  J is built row by row from the reverse sweep
+    of the moments (``moments_adjoint``) and solved with numpy.linalg.solve.
+    wU = s dU/dmu, wN = dN/dmu (fixed E_F), dUE = direct d(sU)/dE; all
+    [S, n, norb(, n_mom)]."""
+    S, n, norb, n_mom = wU.shape
+    s = 2.0 if S == 1 else 1.0
+    stoner = st.scf == "stoner"
+    I = st.stoner_I
+    sig = np.array([1.0, -1.0]) if S == 2 else np.array([1.0])
+    nu = 2 * n if stoner else n
+
+    def ebar_of(wts):
+        """d(sum wts . mu)/dE for every orbital: [S, n, norb]."""
+        return np.stack([moments_adjoint(nbr, H, onsite[v], wts[v])[1] for v in range(S)])
+
+    def project(eb):
+        """Derivative with respect to u of a function whose derivative with
+        respect to the onsite levels is eb [S, n, norb]."""
+        gd = eb.sum(axis=(0, 2))
+        if not stoner:
+            return gd
+        gm = -0.5 * I * eb[0].sum(axis=1) + 0.5 * I * eb[1].sum(axis=1)
+        return np.concatenate([gd, gm])
+
+    g = project(ebar_of(wU) + dUE)
+    if stoner:
+        g[n:] += -0.5 * I * m
+    J = np.zeros((nu, nu))
+    for i in range(nu):
+        c = np.zeros((S, n))
+        if i < n:
+            c[:, i] = s
+        else:
+            c[:, i - n] = sig
+        row = project(ebar_of(c[:, :, None, None] * wN))
+        if i >= n:
+            row[i] -= 1.0
+        J[i] = row
+    y = np.linalg.solve(J.T, g)
+    lam = y[:n]
+    kap = y[n:] if stoner else np.zeros(n)
+    cc = s * lam[None, :] + sig[:, None] * kap[None, :]
+    return wU - cc[:, :, None, None] * wN, y

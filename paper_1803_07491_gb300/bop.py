@@ -38,7 +38,7 @@ class bop_model(ctypes.Structure):
                 ("eta", ctypes.c_double), ("scf_tol", ctypes.c_double), ("scf_max_it", ctypes.c_int),
                 ("stoner_I", ctypes.c_double), ("m_mix", ctypes.c_double), ("m0", ctypes.c_double),
                 ("dos_floor", ctypes.c_double), ("precision", ctypes.c_int), ("mixer", ctypes.c_int),
-                ("mix_history", ctypes.c_int), ("terminator", ctypes.c_int)]
+                ("mix_history", ctypes.c_int), ("terminator", ctypes.c_int), ("scf_response", ctypes.c_int)]
 
 
 class bop_stats(ctypes.Structure):
@@ -48,7 +48,8 @@ class bop_stats(ctypes.Structure):
                 ("bisection_rounds", ctypes.c_int), ("scf_residual", ctypes.c_double),
                 ("e_fermi", ctypes.c_double), ("e_total", ctypes.c_double),
                 ("forces_scf_response", ctypes.c_int), ("n_learned", ctypes.c_int),
-                ("moment_products", ctypes.c_longlong)]
+                ("moment_products", ctypes.c_longlong), ("response_iterations", ctypes.c_int),
+                ("response_converged", ctypes.c_int), ("response_residual", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -143,7 +144,8 @@ def make_model(params, run, precision: str = "fp64") -> bop_model:
     return bop_model(params.norb, (ctypes.c_double * 3)(*b0), params.r0, params.lam, params.rc, params.dc,
                      params.onsite0, run.n_mom, run.n_exp, run.n_spin, run.n_e, SCF[run.scf], run.eta,
                      run.scf_tol, run.scf_max_it, run.stoner_I, run.m_mix, run.m0, run.dos_floor,
-                     PREC[precision], MIXER[run.mixer], run.mix_history, TERM[run.terminator])
+                     PREC[precision], MIXER[run.mixer], run.mix_history, TERM[run.terminator],
+                     1 if run.scf_response else 0)
 
 
 def _check(ctx, st, allow=()):
@@ -249,6 +251,15 @@ def bop_forces(ctx, n: int, stream=None):
     s = bop_stats()
     _check(ctx, lib().bop_forces(ctx, _ptr(F), _ptr(W), ctypes.byref(s), _stream(stream)))
     return F, W
+
+
+def bop_forces_stats(ctx, n: int, stream=None):
+    """bop_forces plus its statistics (SCF-response solve)."""
+    F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    W = torch.empty((3, 3), dtype=torch.float64, device="cuda")
+    s = bop_stats()
+    _check(ctx, lib().bop_forces(ctx, _ptr(F), _ptr(W), ctypes.byref(s), _stream(stream)))
+    return F, W, s.as_dict()
 
 
 def bop_get_orbital_state(ctx, M: int, n_mom: int, weights=False, stream=None):

@@ -74,6 +74,8 @@ struct bop_ctx {
   // learned terminator
   bop_mlp* net = nullptr;
   DBuf lbase, lnlev, lflag, lxs, lys, lZ1, lH1, lZ2, lH2, lybar, lcot, lxbar, lcount;
+  // SCF response of the forces
+  DBuf rwN, rwt, rdUE, rvec, rcoef;
   DBuf status;
   DBuf cub_tmp;
   DBuf nprod;
@@ -210,6 +212,7 @@ int validate_model(bop_ctx* c, const bop_model* m) {
   if (m->terminator != BOP_TERM_CONSTANT && m->terminator != BOP_TERM_MLP)
     return fail(c, BOP_ERR_ARG, "terminator must be CONSTANT or MLP");
   if (m->terminator == BOP_TERM_MLP && m->n_mom != 9) return fail(c, BOP_ERR_ARG, "the MLP terminator needs n_mom = 9");
+  if (m->scf_response != 0 && m->scf_response != 1) return fail(c, BOP_ERR_ARG, "scf_response must be 0 or 1");
   return BOP_OK;
 }
 
@@ -502,6 +505,238 @@ int fermi_more(bop_ctx* c, cudaStream_t s) {
   return BOP_OK;
 }
 
+
+// Weights of L = cU U + cN N for every orbital (cN = -cU * lam[0] with a
+// device lam, else cN0), through the constant- or learned-terminator path,
+// into w [M][n_mom]; dUE [M] = direct dL/dE (may be NULL).
+int compute_weights(bop_ctx* c, double cU, const double* lam, double cN0, double* w, double* dUE, cudaStream_t s) {
+  const int M = c->S * c->n * c->norb;
+  WeightArgs wa;
+  wa.M = M;
+  wa.n_mom = c->n_mom;
+  wa.n_exp = c->n_exp;
+  wa.norb = c->norb;
+  wa.mu = P<double>(c->mu);
+  wa.onsite = P<double>(c->onsite);
+  wa.st = P<FermiState>(c->fstate);
+  wa.g = P<double>(c->gjack);
+  wa.inv = P<double>(c->ginv);
+  wa.cU = cU;
+  wa.lam = lam;
+  wa.cN0 = cN0;
+  wa.w = w;
+  wa.dU_dE = dUE;
+  wa.zscratch = P<double>(c->zscr);
+  wa.status = P<unsigned>(c->status);
+  if (c->m.terminator == BOP_TERM_MLP) {
+    if (!c->net) return fail(c, BOP_ERR_STATE, "terminator MLP needs a network (bop_set_mlp)");
+    const size_t T = c->fp64 ? sizeof(double) : sizeof(float);
+    CKS(ensure(c, c->lybar, T * (size_t)M * BOP_MLP_NOUT));
+    CKS(ensure(c, c->lcot, sizeof(double) * (size_t)M * 10));
+    CKS(ensure(c, c->lxbar, T * (size_t)M * BOP_MLP_NIN));
+    LearnedArgs L = learned_args(c, M, P<double>(c->mu));
+    L.W = wa;
+    {
+      Region R(c, PK_WEIGHTS, 1, s);
+      if (launch_learned(2, L, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
+    }
+    {
+      Region R(c, PK_MLP, 3, s);
+      if (mlp_infer_backward(c->fp64, M, c->lybar.p, mlp_wbf_dev(c->net), c->lZ1.p, c->lZ2.p, c->lH1.p, c->lH2.p,
+                             c->lxbar.p, s))
+        return fail(c, BOP_ERR_CUDA, "network reverse launch failed");
+    }
+    Region R(c, PK_WEIGHTS, 1, s);
+    if (launch_learned(3, L, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
+    return BOP_OK;
+  }
+  Region R(c, PK_WEIGHTS, 1, s);
+  if (launch_weights(wa, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
+  return BOP_OK;
+}
+
+// One reverse sweep of the moments with weights w: Hbar += dL/dH (if not
+// NULL), Ebar += dL/dE (if not NULL).
+int adjoint_pass(bop_ctx* c, const double* w, double* Hbar, double* Ebar, cudaStream_t s) {
+  const int n = c->n;
+  int nc = adjoint_columns(c->norb);
+  size_t per_site = (size_t)c->norb * nc;
+  long long levsum = 0;
+  for (int k = 0; k <= c->K; k++) levsum += c->maxlev[k];
+  size_t slot_elems = (2 * (size_t)levsum) * per_site + 64;
+  int nwork = n * c->S * (c->norb / nc);
+  int slots = nwork < 1216 ? nwork : 1216;
+  size_t esz = c->fp64 ? sizeof(double) : sizeof(float);
+  CKS(ensure(c, c->adjscr, esz * slot_elems * slots));
+  AdjointArgs aa;
+  aa.cv = cview(c);
+  aa.H = c->fp64 ? c->H64.p : c->H32.p;
+  aa.HS = c->HS;
+  aa.onsite = c->fp64 ? c->onsite.p : c->onsite32.p;
+  aa.n = n;
+  aa.n_spin = c->S;
+  aa.norb = c->norb;
+  aa.n_mom = c->n_mom;
+  aa.w = w;
+  aa.scratch = c->adjscr.p;
+  aa.slot_elems = slot_elems;
+  aa.slots = slots;
+  aa.Hbar = Hbar;
+  aa.HSu = c->HSu;
+  aa.Ebar = Ebar;
+  Region R(c, PK_ADJOINT, 1, s);
+  if (launch_moments_adjoint(aa, c->fp64, s)) return fail(c, BOP_ERR_CUDA, "adjoint launch failed");
+  return BOP_OK;
+}
+
+constexpr int GM_KRYLOV = 40;   // GMRES basis size per cycle
+constexpr int GM_CYCLES = 3;    // cycles (restarts + 1)
+
+// Reads nv doubles from the device (synchronises s).
+int read_back(bop_ctx* c, const double* d, double* h, int nv, cudaStream_t s) {
+  CK(cudaMemcpyAsync(h, d, sizeof(double) * nv, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return BOP_OK;
+}
+
+// SCF response of the forces: weights w = wU - c wN with the multipliers y
+// of J^T y = dE/du (see bop_forces), then Hbar from one reverse sweep.
+int scf_response(bop_ctx* c, cudaStream_t s) {
+  const int n = c->n, S = c->S, norb = c->norb, nm = c->n_mom;
+  const int M = S * n * norb;
+  const bool stoner = c->m.scf == BOP_SCF_STONER;
+  const int nu = stoner ? 2 * n : n;
+  const double I = c->m.stoner_I;
+  const double rtol = c->fp64 ? 1e-10 : 1e-5;
+  CKS(ensure(c, c->rwN, sizeof(double) * (size_t)M * nm));
+  CKS(ensure(c, c->rwt, sizeof(double) * (size_t)M * nm));
+  CKS(ensure(c, c->rdUE, sizeof(double) * (size_t)M));
+  CKS(ensure(c, c->rvec, sizeof(double) * (size_t)nu * (GM_KRYLOV + 6)));
+  CKS(ensure(c, c->rcoef, sizeof(double) * (GM_KRYLOV + 2)));
+  double* V = P<double>(c->rvec);                 // Krylov basis [GM_KRYLOV + 1][nu]
+  double* rhs = V + (size_t)(GM_KRYLOV + 1) * nu;  // dE/du
+  double* Pd = rhs + nu;                           // diagonal preconditioner
+  double* tmp = Pd + nu;
+  double* y = tmp + nu;                            // solution
+  double* yc = y + nu;                             // one cycle's correction
+  double* coef = P<double>(c->rcoef);
+  double* wU = P<double>(c->w);
+  double* wN = P<double>(c->rwN);
+  double* Eb = P<double>(c->Ebar);
+  // weights of U (fixed E_F, no multiplier) and of N
+  CKS(compute_weights(c, c->sfac, nullptr, 0.0, wU, P<double>(c->rdUE), s));
+  CKS(compute_weights(c, 0.0, nullptr, 1.0, wN, nullptr, s));
+  // right-hand side g = dE/du
+  CK(cudaMemsetAsync(Eb, 0, sizeof(double) * M, s));
+  CKS(adjoint_pass(c, wU, nullptr, Eb, s));
+  if (launch_project(n, norb, S, I, Eb, P<double>(c->rdUE), stoner ? P<double>(c->mval) : nullptr, -0.5 * I,
+                     nullptr, rhs, s) ||
+      launch_precond_diag(n, norb, S, c->sfac, c->m.dos_floor, P<double>(c->dos), Pd, s))
+    return fail(c, BOP_ERR_CUDA, "response kernels failed");
+  // J^T v -> out
+  auto matvec = [&](const double* v, double* out) -> int {
+    if (launch_scale_weights(n, norb, S, nm, c->sfac, stoner ? 1 : 0, v, 1.0, wN, nullptr, P<double>(c->rwt), s))
+      return fail(c, BOP_ERR_CUDA, "response kernels failed");
+    CK(cudaMemsetAsync(Eb, 0, sizeof(double) * M, s));
+    CKS(adjoint_pass(c, P<double>(c->rwt), nullptr, Eb, s));
+    if (launch_project(n, norb, S, I, Eb, nullptr, nullptr, 0.0, stoner ? v + n : nullptr, out, s))
+      return fail(c, BOP_ERR_CUDA, "response kernels failed");
+    return BOP_OK;
+  };
+  auto dot = [&](const double* a, const double* b, double* h) -> int {
+    if (launch_dots(nu, 1, a, b, coef, s)) return fail(c, BOP_ERR_CUDA, "response kernels failed");
+    return read_back(c, coef, h, 1, s);
+  };
+  CK(cudaMemsetAsync(y, 0, sizeof(double) * nu, s));
+  double bnorm = 0.0;
+  CKS(dot(rhs, rhs, &bnorm));
+  bnorm = std::sqrt(bnorm);
+  int iters = 0;
+  double rel = 0.0;
+  bool conv = bnorm == 0.0;
+  const double one = 1.0, minus_one = -1.0;
+  for (int cyc = 0; cyc < GM_CYCLES && !conv; cyc++) {
+    // residual r = g - J^T y into V_0
+    CK(cudaMemcpyAsync(V, rhs, sizeof(double) * nu, cudaMemcpyDeviceToDevice, s));
+    if (cyc > 0) {
+      CKS(matvec(y, tmp));
+      CK(cudaMemcpyAsync(coef, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+      if (launch_axpy_multi(nu, 1, tmp, coef, V, s)) return fail(c, BOP_ERR_CUDA, "response kernels failed");
+    }
+    double beta = 0.0;
+    CKS(dot(V, V, &beta));
+    beta = std::sqrt(beta);
+    if (beta <= rtol * bnorm) {
+      conv = true;
+      rel = beta / bnorm;
+      break;
+    }
+    if (launch_scale_vec(nu, V, nullptr, 1.0 / beta, V, s)) return fail(c, BOP_ERR_CUDA, "response kernels failed");
+    double Hh[GM_KRYLOV + 1][GM_KRYLOV], cs[GM_KRYLOV], sn[GM_KRYLOV], gv[GM_KRYLOV + 1];
+    for (int q = 0; q <= GM_KRYLOV; q++) gv[q] = 0.0;
+    gv[0] = beta;
+    int k = 0;
+    for (int j = 0; j < GM_KRYLOV; j++) {
+      double* vj = V + (size_t)j * nu;
+      double* u = V + (size_t)(j + 1) * nu;
+      if (launch_scale_vec(nu, vj, Pd, 1.0, tmp, s)) return fail(c, BOP_ERR_CUDA, "response kernels failed");
+      CKS(matvec(tmp, u));
+      // classical Gram-Schmidt, twice
+      double h[GM_KRYLOV + 1], h2[GM_KRYLOV + 1];
+      for (int pass = 0; pass < 2; pass++) {
+        double* hp = pass ? h2 : h;
+        if (launch_dots(nu, j + 1, V, u, coef, s)) return fail(c, BOP_ERR_CUDA, "response kernels failed");
+        CKS(read_back(c, coef, hp, j + 1, s));
+        if (launch_axpy_multi(nu, j + 1, V, coef, u, s)) return fail(c, BOP_ERR_CUDA, "response kernels failed");
+      }
+      for (int q = 0; q <= j; q++) h[q] += h2[q];
+      double hn = 0.0;
+      CKS(dot(u, u, &hn));
+      hn = std::sqrt(hn);
+      if (hn > 0.0 && launch_scale_vec(nu, u, nullptr, 1.0 / hn, u, s))
+        return fail(c, BOP_ERR_CUDA, "response kernels failed");
+      // Givens rotations on the new Hessenberg column
+      for (int q = 0; q < j; q++) {
+        const double t0 = cs[q] * h[q] + sn[q] * h[q + 1];
+        h[q + 1] = -sn[q] * h[q] + cs[q] * h[q + 1];
+        h[q] = t0;
+      }
+      const double rr = std::hypot(h[j], hn);
+      cs[j] = rr > 0.0 ? h[j] / rr : 1.0;
+      sn[j] = rr > 0.0 ? hn / rr : 0.0;
+      h[j] = rr;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      for (int q = 0; q <= j; q++) Hh[q][j] = h[q];
+      k = j + 1;
+      iters++;
+      rel = std::fabs(gv[j + 1]) / bnorm;
+      if (rel <= rtol || hn == 0.0) break;
+    }
+    // z = H^-1 g (upper triangular), y += P sum z_q V_q
+    double z[GM_KRYLOV];
+    for (int q = k - 1; q >= 0; q--) {
+      double a = gv[q];
+      for (int r = q + 1; r < k; r++) a -= Hh[q][r] * z[r];
+      z[q] = a / Hh[q][q];
+    }
+    CK(cudaMemcpyAsync(coef, z, sizeof(double) * k, cudaMemcpyHostToDevice, s));
+    if (launch_lincomb(nu, k, V, coef, Pd, 1.0, yc, s)) return fail(c, BOP_ERR_CUDA, "response kernels failed");
+    CK(cudaMemcpyAsync(coef, &minus_one, sizeof(double), cudaMemcpyHostToDevice, s));
+    if (launch_axpy_multi(nu, 1, yc, coef, y, s)) return fail(c, BOP_ERR_CUDA, "response kernels failed");
+    CK(cudaStreamSynchronize(s));
+    conv = rel <= rtol;
+  }
+  c->st.response_iterations = iters;
+  c->st.response_converged = conv ? 1 : 0;
+  c->st.response_residual = rel;
+  // final weights w = wU - c wN, then Hbar
+  if (launch_scale_weights(n, norb, S, nm, c->sfac, stoner ? 1 : 0, y, -1.0, wN, wU, wU, s))
+    return fail(c, BOP_ERR_CUDA, "response kernels failed");
+  CKS(adjoint_pass(c, wU, P<double>(c->Hbar), nullptr, s));
+  return conv ? BOP_OK : BOP_ERR_NO_CONVERGENCE;
+}
+
 }  // namespace
 
 extern "C" {
@@ -571,7 +806,8 @@ int bop_destroy(bop_ctx* c) {
                   &c->partials, &c->counter, &c->result, &c->e_total, &c->lam, &c->e_atom, &c->w, &c->zscr,
                   &c->adjscr, &c->Hbar, &c->Ebar, &c->status, &c->cub_tmp, &c->nprod,
                   &c->ginv, &c->hx, &c->hf, &c->gamma, &c->scfred, &c->lbase, &c->lnlev, &c->lflag, &c->lxs,
-                  &c->lys, &c->lZ1, &c->lH1, &c->lZ2, &c->lH2, &c->lybar, &c->lcot, &c->lxbar, &c->lcount};
+                  &c->lys, &c->lZ1, &c->lH1, &c->lZ2, &c->lH2, &c->lybar, &c->lcot, &c->lxbar, &c->lcount,
+                  &c->rwN, &c->rwt, &c->rdUE, &c->rvec, &c->rcoef};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -899,7 +1135,7 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   c->st.scf_residual = res[0];
   c->st.e_fermi = fs.ef;
   c->st.e_total = et;
-  c->st.forces_scf_response = c->m.scf == BOP_SCF_NONE ? 1 : 0;
+  c->st.forces_scf_response = (c->m.scf == BOP_SCF_NONE || c->m.scf_response) ? 1 : 0;
   if (st) *st = c->st;
   c->energized = true;
   if (!converged) return fail(c, BOP_ERR_NO_CONVERGENCE, "SCF not converged after %d iterations (residual %g)",
@@ -915,86 +1151,26 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   CKS(ensure(c, c->zscr, sizeof(double) * (size_t)M * (c->n_exp + 1) * 2));
   CKS(ensure(c, c->Hbar, sizeof(double) * (size_t)(c->nb > 0 ? c->nb : 1) * c->HSu));
   CKS(ensure(c, c->Ebar, sizeof(double) * (size_t)M));
-  // E_F response and weights
-  {
-  Region R(c, PK_EFRESP, 1, s);
-  if (launch_ef_response(M, c->n_exp, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf),
-                         P<double>(c->b_inf),
-                         P<double>(c->onsite), P<FermiState>(c->fstate), P<double>(c->partials),
-                         P<unsigned>(c->counter), P<double>(c->lam), s))
-    return fail(c, BOP_ERR_CUDA, "E_F response launch failed");
-  }
-  WeightArgs wa;
-  wa.M = M;
-  wa.n_mom = c->n_mom;
-  wa.n_exp = c->n_exp;
-  wa.norb = c->norb;
-  wa.mu = P<double>(c->mu);
-  wa.onsite = P<double>(c->onsite);
-  wa.st = P<FermiState>(c->fstate);
-  wa.g = P<double>(c->gjack);
-  wa.inv = P<double>(c->ginv);
-  wa.cU = c->sfac;
-  wa.lam = P<double>(c->lam);
-  wa.w = P<double>(c->w);
-  wa.dU_dE = nullptr;
-  wa.zscratch = P<double>(c->zscr);
-  wa.status = P<unsigned>(c->status);
-  if (c->m.terminator == BOP_TERM_MLP) {
-    if (!c->net) return fail(c, BOP_ERR_STATE, "terminator MLP needs a network (bop_set_mlp)");
-    const size_t T = c->fp64 ? sizeof(double) : sizeof(float);
-    CKS(ensure(c, c->lybar, T * (size_t)M * BOP_MLP_NOUT));
-    CKS(ensure(c, c->lcot, sizeof(double) * (size_t)M * 10));
-    CKS(ensure(c, c->lxbar, T * (size_t)M * BOP_MLP_NIN));
-    LearnedArgs L = learned_args(c, M, P<double>(c->mu));
-    L.W = wa;
-    {
-      Region R(c, PK_WEIGHTS, 1, s);
-      if (launch_learned(2, L, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
-    }
-    {
-      Region R(c, PK_MLP, 3, s);
-      if (mlp_infer_backward(c->fp64, M, c->lybar.p, mlp_wbf_dev(c->net), c->lZ1.p, c->lZ2.p, c->lH1.p, c->lH2.p,
-                             c->lxbar.p, s))
-        return fail(c, BOP_ERR_CUDA, "network reverse launch failed");
-    }
-    Region R(c, PK_WEIGHTS, 1, s);
-    if (launch_learned(3, L, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
-  } else {
-    Region R(c, PK_WEIGHTS, 1, s);
-    if (launch_weights(wa, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
-  }
-  // reverse sweep of the moments
-  int nc = adjoint_columns(c->norb);
-  size_t per_site = (size_t)c->norb * nc;
-  long long levsum = 0;
-  for (int k = 0; k <= c->K; k++) levsum += c->maxlev[k];
-  size_t slot_elems = (2 * (size_t)levsum) * per_site + 64;
-  int nwork = n * c->S * (c->norb / nc);
-  int slots = nwork < 1216 ? nwork : 1216;
-  size_t esz = c->fp64 ? sizeof(double) : sizeof(float);
-  CKS(ensure(c, c->adjscr, esz * slot_elems * slots));
   CK(cudaMemsetAsync(c->Hbar.p, 0, sizeof(double) * (size_t)(c->nb > 0 ? c->nb : 1) * c->HSu, s));
-  CK(cudaMemsetAsync(c->Ebar.p, 0, sizeof(double) * (size_t)M, s));
-  AdjointArgs aa;
-  aa.cv = cview(c);
-  aa.H = c->fp64 ? c->H64.p : c->H32.p;
-  aa.HS = c->HS;
-  aa.onsite = c->fp64 ? c->onsite.p : c->onsite32.p;
-  aa.n = n;
-  aa.n_spin = c->S;
-  aa.norb = c->norb;
-  aa.n_mom = c->n_mom;
-  aa.w = P<double>(c->w);
-  aa.scratch = c->adjscr.p;
-  aa.slot_elems = slot_elems;
-  aa.slots = slots;
-  aa.Hbar = P<double>(c->Hbar);
-  aa.HSu = c->HSu;
-  aa.Ebar = P<double>(c->Ebar);
-  {
-    Region R(c, PK_ADJOINT, 1, s);
-    if (launch_moments_adjoint(aa, c->fp64, s)) return fail(c, BOP_ERR_CUDA, "adjoint launch failed");
+  int solve_status = BOP_OK;
+  c->st.response_iterations = 0;
+  c->st.response_converged = 1;
+  c->st.response_residual = 0.0;
+  if (c->m.scf != BOP_SCF_NONE && c->m.scf_response) {
+    solve_status = scf_response(c, s);
+    if (solve_status != BOP_OK && solve_status != BOP_ERR_NO_CONVERGENCE) return solve_status;
+  } else {
+    // E_F response (global multiplier), weights, reverse sweep
+    {
+      Region R(c, PK_EFRESP, 1, s);
+      if (launch_ef_response(M, c->n_exp, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf),
+                             P<double>(c->b_inf), P<double>(c->onsite), P<FermiState>(c->fstate),
+                             P<double>(c->partials), P<unsigned>(c->counter), P<double>(c->lam), s))
+        return fail(c, BOP_ERR_CUDA, "E_F response launch failed");
+    }
+    CKS(compute_weights(c, c->sfac, P<double>(c->lam), 0.0, P<double>(c->w), nullptr, s));
+    CK(cudaMemsetAsync(c->Ebar.p, 0, sizeof(double) * (size_t)M, s));
+    CKS(adjoint_pass(c, P<double>(c->w), P<double>(c->Hbar), P<double>(c->Ebar), s));
   }
   DBuf* fb = nullptr;
   DBuf tf, tv;
@@ -1022,7 +1198,11 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   if (tv.p) cudaFree(tv.p);
   if (r) return r;
   c->weighted = true;
+  c->st.forces_scf_response = (c->m.scf == BOP_SCF_NONE || c->m.scf_response) ? 1 : 0;
   if (st) *st = c->st;
+  if (solve_status != BOP_OK)
+    return fail(c, solve_status, "SCF-response solve stopped at relative residual %g after %d iterations",
+                c->st.response_residual, c->st.response_iterations);
   return BOP_OK;
 }
 

@@ -171,7 +171,8 @@ struct WeightArgs {
   const double* g;
   const double* inv;     // [n_exp+8] 1/k
   double cU;             // L = cU*U + cN*N
-  const double* lam;     // device scalar: cN = -cU * (*lam)  (E_F response)
+  const double* lam;     // device scalar: cN = -cU * (*lam)  (E_F response); NULL: cN = cN0
+  double cN0;
   double* w;             // [M][n_mom]
   double* dU_dE;         // [M] direct derivative of L w.r.t. the onsite level, may be null
   double* zscratch;      // [2][n_exp+1][M]: sigma_m and its cotangent
@@ -216,6 +217,27 @@ int mlp_infer_backward(int fp64, int M, const void* ybar, const void* wbf, void*
 const float* mlp_params_dev(const bop_mlp* net);
 const void* mlp_wbf_dev(const bop_mlp* net);
 const float* mlp_norm_dev(const bop_mlp* net);
+
+// scf_adjoint.cu: vector kernels of the SCF-response solve (nu = n or 2n unknowns)
+// w_out = (wU or 0) + sign * c_{atom,spin} * wN, c = s v[atom] + sigma_spin v[n + atom] (Stoner)
+int launch_scale_weights(int n, int norb, int S, int n_mom, double s, int stoner, const double* v, double sign,
+                         const double* wN, const double* wU, double* w_out, cudaStream_t st);
+// out_u = derivative w.r.t. u of a function whose onsite-level derivative is Eb (+ dUE):
+//   delta part sum_{alpha,nu}; Stoner moment part sum_alpha (-I/2 up + I/2 down),
+//   plus mcoef * m[i] (energy: -I/2 m) and minus v_m[i] if v_m (the -m_i of Q_i)
+int launch_project(int n, int norb, int S, double I, const double* Eb, const double* dUE, const double* m,
+                   double mcoef, const double* v_m, double* out, cudaStream_t st);
+// P = diagonal preconditioner: -1/max(s sum n_i, floor) for delta, -1 for m
+int launch_precond_diag(int n, int norb, int S, double s, double floor_, const double* dos, double* P,
+                        cudaStream_t st);
+int launch_dots(int nu, int nvec, const double* V, const double* w, double* out, cudaStream_t st);
+// w -= sum_k coef[k] V[k]  (coef device)
+int launch_axpy_multi(int nu, int nvec, const double* V, const double* coef, double* w, cudaStream_t st);
+// out = scale * (sum_k coef[k] V[k]) * (P if P else 1)
+int launch_lincomb(int nu, int nvec, const double* V, const double* coef, const double* P, double scale,
+                   double* out, cudaStream_t st);
+// out = a * x * (P if P else 1)
+int launch_scale_vec(int nu, const double* x, const double* P, double a, double* out, cudaStream_t st);
 
 // forces.cu
 int launch_forces(int nb, BondModel m, const double* bond_d, const int* bond_atoms, const double* Hbar, int HSu,

@@ -450,7 +450,7 @@ k_moments_adj(ClusterView cv, const T* __restrict__ H, int HS, const T* __restri
     // bond and onsite cotangents: dU/dH_ts = sum_k Psi-bar_k[t] Psi_k-1[s]^T
     for (int t = tid; t < s_lev[K]; t += blockDim.x) {
       const int lt = site_level(s_lev, K, t);
-      const long long q1 = aoff[t + 1];
+      const long long q1 = Hbar != nullptr ? aoff[t + 1] : aoff[t];  // no bond cotangents wanted
       for (long long q = aoff[t]; q < q1; q++) {
         int2 en = cv.adj[q];
         const int s = en.x;

@@ -1,0 +1,154 @@
+// Vector kernels of the SCF-response solve (bop_forces with an SCF): the
+// multipliers y of J^T y = dE/du, with u the SCF unknowns (one onsite shift
+// per atom, and for Stoner one moment per atom) and J the derivative of the
+// SCF conditions at fixed E_F.  Products J^T v come from a reverse sweep of
+// the moments (moments.cu) with weights c_{i,nu} dN/dmu; these kernels form
+// those weights, project onsite-level cotangents onto u, and carry out the
+// Gram-Schmidt and combination steps of GMRES.  Every reduction has a fixed
+// order.
+#include "kernels.h"
+
+namespace {
+
+constexpr int VT = 256;
+
+// c_{i,nu} = s v[i] (+ sigma_nu v[n + i] for Stoner, sigma = +1 up, -1 down)
+__global__ void k_scale_weights(int n, int norb, int S, int n_mom, double s, int stoner,
+                                const double* __restrict__ v, double sign, const double* __restrict__ wN,
+                                const double* __restrict__ wU, double* __restrict__ w) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long tot = (long long)S * n * norb * n_mom;
+  if (q >= tot) return;
+  const long long o = q / n_mom;                // orbital (spin-major)
+  const int atom = (int)((o / norb) % n);
+  const int spin = (int)(o / ((long long)norb * n));
+  double c = s * v[atom];
+  if (stoner) c += (spin == 0 ? 1.0 : -1.0) * v[n + atom];
+  w[q] = (wU ? wU[q] : 0.0) + sign * c * wN[q];
+}
+
+__global__ void k_project(int n, int norb, int S, double I, const double* __restrict__ Eb,
+                          const double* __restrict__ dUE, const double* __restrict__ m, double mcoef,
+                          const double* __restrict__ v_m, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double gd = 0.0, gm = 0.0;
+  for (int sp = 0; sp < S; sp++) {
+    double a = 0.0;
+    for (int al = 0; al < norb; al++) {
+      const size_t o = ((size_t)sp * n + i) * norb + al;
+      a += Eb[o] + (dUE ? dUE[o] : 0.0);
+    }
+    gd += a;
+    gm += (sp == 0 ? -0.5 : 0.5) * I * a;
+  }
+  out[i] = gd;
+  if (S == 2) {
+    if (m) gm += mcoef * m[i];
+    if (v_m) gm -= v_m[i];
+    out[n + i] = gm;
+  }
+}
+
+__global__ void k_precond_diag(int n, int norb, int S, double s, double floor_, const double* __restrict__ dos,
+                               double* __restrict__ P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double d = 0.0;
+  for (int sp = 0; sp < S; sp++)
+    for (int al = 0; al < norb; al++) d += dos[((size_t)sp * n + i) * norb + al];
+  d *= s;
+  P[i] = -1.0 / (d > floor_ ? d : floor_);
+  if (S == 2) P[n + i] = -1.0;
+}
+
+// out[k] = V[k] . w, one block per vector: strided partial sums, a fixed
+// shuffle tree and a fixed cross-warp order.
+__global__ void __launch_bounds__(VT) k_dots(int nu, const double* __restrict__ V, const double* __restrict__ w,
+                                             double* __restrict__ out) {
+  __shared__ double sh[VT / 32];
+  const int k = blockIdx.x;
+  const double* vk = V + (size_t)k * nu;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < nu; i += VT) a += vk[i] * w[i];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < VT / 32; q++) t += sh[q];
+    out[k] = t;
+  }
+}
+
+__global__ void k_axpy_multi(int nu, int nvec, const double* __restrict__ V, const double* __restrict__ coef,
+                             double* __restrict__ w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nu) return;
+  double a = w[i];
+  for (int k = 0; k < nvec; k++) a -= coef[k] * V[(size_t)k * nu + i];
+  w[i] = a;
+}
+
+__global__ void k_lincomb(int nu, int nvec, const double* __restrict__ V, const double* __restrict__ coef,
+                          const double* __restrict__ P, double scale, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nu) return;
+  double a = 0.0;
+  for (int k = 0; k < nvec; k++) a += coef[k] * V[(size_t)k * nu + i];
+  out[i] = scale * a * (P ? P[i] : 1.0);
+}
+
+__global__ void k_scale_vec(int nu, const double* __restrict__ x, const double* __restrict__ P, double a,
+                            double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nu) return;
+  out[i] = a * x[i] * (P ? P[i] : 1.0);
+}
+
+unsigned grid(long long n) { return (unsigned)((n + VT - 1) / VT); }
+int ok() { return cudaGetLastError() == cudaSuccess ? 0 : -1; }
+
+}  // namespace
+
+int launch_scale_weights(int n, int norb, int S, int n_mom, double s, int stoner, const double* v, double sign,
+                         const double* wN, const double* wU, double* w_out, cudaStream_t st) {
+  const long long tot = (long long)S * n * norb * n_mom;
+  k_scale_weights<<<grid(tot), VT, 0, st>>>(n, norb, S, n_mom, s, stoner, v, sign, wN, wU, w_out);
+  return ok();
+}
+
+int launch_project(int n, int norb, int S, double I, const double* Eb, const double* dUE, const double* m,
+                   double mcoef, const double* v_m, double* out, cudaStream_t st) {
+  k_project<<<grid(n), VT, 0, st>>>(n, norb, S, I, Eb, dUE, m, mcoef, v_m, out);
+  return ok();
+}
+
+int launch_precond_diag(int n, int norb, int S, double s, double floor_, const double* dos, double* P,
+                        cudaStream_t st) {
+  k_precond_diag<<<grid(n), VT, 0, st>>>(n, norb, S, s, floor_, dos, P);
+  return ok();
+}
+
+int launch_dots(int nu, int nvec, const double* V, const double* w, double* out, cudaStream_t st) {
+  if (nvec <= 0) return 0;
+  k_dots<<<nvec, VT, 0, st>>>(nu, V, w, out);
+  return ok();
+}
+
+int launch_axpy_multi(int nu, int nvec, const double* V, const double* coef, double* w, cudaStream_t st) {
+  if (nvec <= 0) return 0;
+  k_axpy_multi<<<grid(nu), VT, 0, st>>>(nu, nvec, V, coef, w);
+  return ok();
+}
+
+int launch_lincomb(int nu, int nvec, const double* V, const double* coef, const double* P, double scale,
+                   double* out, cudaStream_t st) {
+  k_lincomb<<<grid(nu), VT, 0, st>>>(nu, nvec, V, coef, P, scale, out);
+  return ok();
+}
+
+int launch_scale_vec(int nu, const double* x, const double* P, double a, double* out, cudaStream_t st) {
+  k_scale_vec<<<grid(nu), VT, 0, st>>>(nu, x, P, a, out);
+  return ok();
+}

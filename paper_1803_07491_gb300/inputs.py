@@ -92,6 +92,7 @@ class RunParams:
     mixer: str = "anderson"   # linear | anderson (type-II Broyden)
     mix_history: int = 6
     terminator: str = "constant"  # constant | mlp (learned continuation of the chain, n_mom = 9)
+    scf_response: bool = True     # with an SCF, forces include the response of the onsite levels
 
 
 @dataclass

@@ -1,0 +1,94 @@
+"""GPU forces with the SCF response (the exact gradient of the
+self-consistent energy): parity with the oracle's dense implicit-function
+solve on small cells (LCN and Stoner, FP64 and FP32 products), the
+Hellmann-Feynman form when the response is switched off, and central
+differences of the GPU's own energy on the 2,000-atom LCN workload."""
+import numpy as np
+import pytest
+
+from paper_1803_07491_gb300 import inputs as I
+from conftest import oracle_model, oracle_settings
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bop():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_07491_gb300 import build, bop as b
+    build.build()
+    return b
+
+
+def _case(scf):
+    base = I.small_bcc(2, 2, 2, 0.08, 47)
+    kw = dict(scf="lcn") if scf == "lcn" else dict(scf="stoner", n_spin=2, stoner_I=0.8)
+    return I.with_run(base, scf_tol=1e-12, scf_max_it=400, **kw)
+
+
+@pytest.mark.parametrize("scf", ["lcn", "stoner"])
+@pytest.mark.parametrize("response", [True, False])
+def test_scf_forces_match_oracle_fp64(bop, ob, scf, response):
+    w = _case(scf)
+    w = I.with_run(w, scf_response=response)
+    ctx = bop.Context(w.model, w.run, "fp64")
+    ctx.build(w.pos, w.cell, w.pbc)
+    e, st = ctx.energy()
+    F, W, fs = bop.bop_forces_stats(ctx.h, w.n_atoms)
+    ref = ob.evaluate(oracle_model(w.model), oracle_settings(w.run), w.pos, w.cell, w.pbc)
+    assert st["scf_converged"] == 1 and ref["scf_converged"]
+    assert fs["forces_scf_response"] == (1 if response else 0)
+    assert ref["forces_include_scf_response"] == response
+    if response:
+        assert fs["response_converged"] == 1 and fs["response_residual"] < 1e-10
+        assert 0 < fs["response_iterations"] < 60
+    assert np.max(np.abs(e.cpu().numpy() - ref["e_atom"])) < 1e-8
+    assert np.max(np.abs(F.cpu().numpy() - ref["forces"])) < 1e-7
+    assert np.max(np.abs(W.cpu().numpy() - ref["virial"])) < 1e-6
+    ctx.close()
+
+
+def test_scf_forces_fp32_products(bop, ob):
+    w = I.with_run(_case("lcn"), scf_tol=1e-5)
+    ctx = bop.Context(w.model, w.run, "fp32")
+    ctx.build(w.pos, w.cell, w.pbc)
+    e, st = ctx.energy()
+    F, W, fs = bop.bop_forces_stats(ctx.h, w.n_atoms)
+    ref = ob.evaluate(oracle_model(w.model), oracle_settings(I.with_run(w, scf_tol=1e-12).run), w.pos, w.cell,
+                      w.pbc)
+    assert fs["response_converged"] == 1
+    assert np.max(np.abs(e.cpu().numpy() - ref["e_atom"])) < 1e-3
+    assert np.max(np.abs(F.cpu().numpy() - ref["forces"])) < 1e-2
+    ctx.close()
+
+
+def test_d2000_lcn_forces_by_finite_differences(bop):
+    """The bench workload in FP64: forces of the self-consistent energy
+    against central differences of the GPU energy, h = 1e-4 A (SCF to 1e-11
+    electrons, warm-started from the converged shifts)."""
+    w = I.with_run(I.workload("d2000"), scf_tol=1e-11)
+    ctx = bop.Context(w.model, w.run, "fp64")
+    ctx.build(w.pos, w.cell, w.pbc)
+    delta = torch.zeros(w.n_atoms, dtype=torch.float64, device="cuda")
+    _, st = ctx.energy(delta=delta)
+    F, W, fs = bop.bop_forces_stats(ctx.h, w.n_atoms)
+    assert fs["response_converged"] == 1
+    F = F.cpu().numpy()
+    d0 = delta.clone()
+
+    def energy(pos):
+        ctx.build(pos, w.cell, w.pbc)
+        d = d0.clone()
+        _, s = ctx.energy(delta=d)
+        return s["e_total"]
+
+    h = 1e-4
+    for (i, c) in [(0, 0), (1234, 2)]:
+        p, q = w.pos.copy(), w.pos.copy()
+        p[i, c] += h
+        q[i, c] -= h
+        fd = -(energy(p) - energy(q)) / (2 * h)
+        assert abs(F[i, c] - fd) < 2e-5 + 1e-4 * abs(fd), (i, c, F[i, c], fd)
+    ctx.close()

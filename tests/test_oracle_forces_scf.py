@@ -88,6 +88,36 @@ def test_rotation_and_permutation_invariance(ob, which):
     assert np.allclose(o3["forces"], out["forces"][perm], atol=1e-9)
 
 
+@pytest.mark.parametrize("scf", ["lcn", "stoner"])
+def test_scf_forces_central_differences(ob, scf):
+    """With an SCF the forces are the total derivative of the self-consistent
+    energy (onsite shifts, and for Stoner the moments, follow the atoms):
+    against central differences of the converged energy, h = 1e-4 A.  The
+    Hellmann-Feynman form (fixed onsite levels) misses that response."""
+    base = I.small_bcc(2, 2, 2, 0.08, 47)
+    kw = dict(scf="lcn") if scf == "lcn" else dict(scf="stoner", n_spin=2, stoner_I=0.8)
+    w = I.with_run(base, scf_tol=1e-13, scf_max_it=400, **kw)
+    out = run(ob, w)
+    assert out["scf_converged"] and out["forces_include_scf_response"]
+    warm = dict(delta0=out["delta"], m_init=out["m"])
+    hf = run(ob, I.with_run(w, scf_response=False), **warm)
+    assert not hf["forces_include_scf_response"]
+    F, Fhf = out["forces"], hf["forces"]
+    assert np.allclose(F.sum(axis=0), 0, atol=1e-10)
+    h = 1e-4
+    gap = 0.0
+    for (i, c) in [(0, 0), (5, 2), (11, 1)]:
+        p, q = w.pos.copy(), w.pos.copy()
+        p[i, c] += h
+        q[i, c] -= h
+        Ep = run(ob, I.Workload("p", p, w.cell, w.pbc, w.model, w.run), want_forces=False, **warm)["e_total"]
+        Eq = run(ob, I.Workload("q", q, w.cell, w.pbc, w.model, w.run), want_forces=False, **warm)["e_total"]
+        fd = -(Ep - Eq) / (2 * h)
+        assert abs(F[i, c] - fd) < 1e-6 + 1e-5 * abs(fd), (i, c, F[i, c], fd)
+        gap = max(gap, abs(Fhf[i, c] - fd))
+    assert gap > 1e-4
+
+
 def test_lcn_scf_reaches_local_neutrality(ob):
     w = I.with_run(I.small_bcc(3, 3, 3, 0.08, 45), scf="lcn")
     out = run(ob, w, want_forces=False)
