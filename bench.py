@@ -99,7 +99,7 @@ def chain_level_updates(n_exp: int) -> int:
     return sum(min(m + 1, n_exp - m - 1) + 1 for m in range(n_exp))
 
 
-def algorithmic_flops(family: str, w, stats: dict, prof: dict, n_spin: int) -> float | None:
+def algorithmic_flops(family: str, w, stats: dict, prof: dict, n_spin: int, steps: int = 1) -> float | None:
     """FLOPs one launch region of a family must do (per region)."""
     norb, n_mom, n_exp = w.model.norb, w.run.n_mom, w.run.n_exp
     M = n_spin * w.n_atoms * norb
@@ -107,6 +107,16 @@ def algorithmic_flops(family: str, w, stats: dict, prof: dict, n_spin: int) -> f
         # block products Psi_k(t) += B_ts Psi_k-1(s) over the cluster pairs,
         # norb x norb x norb multiply-adds each (all starting orbitals)
         return 2.0 * stats["moment_products"] * n_spin * norb ** 3
+    if family == "adjoint":
+        # a reverse sweep recomputes Psi (one moments pass), runs H^T over
+        # Psi-bar (one more) and, when bond cotangents are wanted, forms
+        # sum_k Psi-bar_k(t) Psi_k-1(s)^T over the same pairs (one more);
+        # one pass per step forms bond cotangents, the others (SCF-response
+        # products) only onsite ones
+        one = 2.0 * stats["moment_products"] * n_spin * norb ** 3
+        regions = max(1, prof["adjoint"]["regions"])
+        with_h = min(steps, regions)
+        return one * (3.0 * with_h + 2.0 * (regions - with_h)) / regions
     if family == "expand":
         return 8.0 * M * chain_level_updates(n_exp)
     if family == "fermi":
@@ -211,7 +221,8 @@ def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: s
 
     # roofline of the dominant kernel family (live CUDA-event times)
     fam = max(prof, key=lambda k: prof[k]["ms"])
-    flops = algorithmic_flops(fam, w, {**stats, "moment_products": stats_products(ctx, bop)}, prof, w.run.n_spin)
+    flops = algorithmic_flops(fam, w, {**stats, "moment_products": stats_products(ctx, bop)}, prof, w.run.n_spin,
+                              steps)
     per_region_ms = prof[fam]["ms"] / max(1, prof[fam]["regions"])
     fp64_family = fam in ("expand", "fermi", "weights", "orbital_NU", "ef_response") or precision == "fp64"
     peak = PEAK_FP64_TFLOPS if fp64_family else PEAK_FP32_TFLOPS
@@ -233,6 +244,9 @@ def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: s
                    "terminator": w.run.terminator,
                    "scf_iterations": stats["scf_iterations"], "scf_tol": w.run.scf_tol,
                    "bisection_rounds": stats["bisection_rounds"],
+                   "forces": ("exact: SCF response included" if stats["forces_scf_response"]
+                              else "fixed onsite levels (Hellmann-Feynman form)"),
+                   "response_iterations": stats["response_iterations"],
                    "precision": precision, "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "gpu_launches": launches,

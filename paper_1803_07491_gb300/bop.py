@@ -109,6 +109,7 @@ def lib(path: str | None = None):
                                 _VP], ctypes.c_int),
         "bop_mlp_predict": ([_VP, ctypes.c_longlong, _VP, _VP, _VP], ctypes.c_int),
         "bop_set_mlp": ([_VP, _VP], ctypes.c_int),
+        "bop_set_store_budget": ([_VP, ctypes.c_longlong], ctypes.c_int),
         "bop_reset_profile": ([_VP], ctypes.c_int),
         "bop_get_profile": ([_VP, ctypes.POINTER(bop_kernel_time), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
                             ctypes.c_int),
@@ -384,6 +385,10 @@ def bop_mlp_predict(net, x: torch.Tensor, stream=None) -> torch.Tensor:
     y = torch.empty((x.shape[0], MLP_NOUT), dtype=torch.float32, device=x.device)
     _mcheck(net, lib().bop_mlp_predict(net, x.shape[0], _ptr(x), _ptr(y), _stream(stream)))
     return y
+
+
+def bop_set_store_budget(ctx, nbytes: int):
+    _check(ctx, lib().bop_set_store_budget(ctx, int(nbytes)))
 
 
 def bop_set_mlp(ctx, net):

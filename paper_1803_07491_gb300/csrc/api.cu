@@ -76,6 +76,11 @@ struct bop_ctx {
   DBuf lbase, lnlev, lflag, lxs, lys, lZ1, lH1, lZ2, lH2, lybar, lcot, lxbar, lcount;
   // SCF response of the forces
   DBuf rwN, rwt, rdUE, rvec, rcoef;
+  // stored Psi of every work item for the reverse sweeps (when it fits)
+  DBuf psi_off, psis, psib, lsum;
+  long long psi_tot = 0;
+  bool psi_valid = false;
+  size_t store_budget = (size_t)-1;
   DBuf status;
   DBuf cub_tmp;
   DBuf nprod;
@@ -366,7 +371,18 @@ int size_state(bop_ctx* c) {
   return BOP_OK;
 }
 
-int run_moments(bop_ctx* c, const double* onsite_dev, double* mu, cudaStream_t s) {
+// Columns per work item of the forward pass (all 5 starting orbitals when
+// both stored levels fit in shared memory).
+int forward_nc(bop_ctx* c) {
+  int ce = 1, co = 1;
+  for (int k = 0; k < c->K; k++) {
+    int& cap = (k & 1) ? co : ce;
+    if (c->maxlev[k] > cap) cap = c->maxlev[k];
+  }
+  return moments_columns(c->norb, ce + co, c->fp64);
+}
+
+int run_moments(bop_ctx* c, const double* onsite_dev, double* mu, cudaStream_t s, void* pstore = nullptr) {
   MomentsArgs a;
   a.cv = cview(c);
   a.H = c->fp64 ? c->H64.p : c->H32.p;
@@ -384,6 +400,9 @@ int run_moments(bop_ctx* c, const double* onsite_dev, double* mu, cudaStream_t s
     if (c->maxlev[k] > cap) cap = c->maxlev[k];
   }
   a.mu = mu;
+  a.pstore = pstore;
+  a.psi_off = P<long long>(c->psi_off);
+  a.psi_tot = c->psi_tot;
   Region R(c, PK_MOMENTS, 1, s);
   int r = launch_moments(a, c->fp64, s);
   if (r == -2) return fail(c, BOP_ERR_OVERFLOW, "cluster level too large for shared memory");
@@ -555,20 +574,37 @@ int compute_weights(bop_ctx* c, double cU, const double* lam, double cN0, double
   return BOP_OK;
 }
 
+// Row padding of a stored Psi row (norb x nc values), as in the kernels.
+int psi_row(int N, int fp64) {
+  if (N == 1) return 1;
+  return fp64 ? (N + 1) / 2 * 2 : (N + 3) / 4 * 4;
+}
+
+// Stores Psi of every work item (one more forward pass at the current
+// onsite levels) when the store and its cotangent copy fit in a third of
+// the device memory that is free; otherwise the reverse sweeps recompute Psi.
+int prepare_psi_store(bop_ctx* c, cudaStream_t s) {
+  c->psi_valid = false;
+  const int nc = forward_nc(c);
+  const size_t esz = c->fp64 ? sizeof(double) : sizeof(float);
+  const size_t bytes = (size_t)c->S * (c->norb / nc) * (size_t)c->psi_tot * psi_row(c->norb * nc, c->fp64) * esz;
+  size_t freeb = 0, totalb = 0;
+  CK(cudaMemGetInfo(&freeb, &totalb));
+  const size_t held = c->psis.bytes + c->psib.bytes;
+  if (2 * bytes > (freeb + held) / 3 || 2 * bytes > c->store_budget) return BOP_OK;
+  CKS(ensure(c, c->psis, bytes));
+  CKS(ensure(c, c->psib, bytes));
+  CKS(run_moments(c, P<double>(c->onsite), P<double>(c->mu), s, c->psis.p));
+  c->psi_valid = true;
+  return BOP_OK;
+}
+
 // One reverse sweep of the moments with weights w: Hbar += dL/dH (if not
-// NULL), Ebar += dL/dE (if not NULL).
+// NULL), Ebar += dL/dE (if not NULL).  Over the stored Psi when present.
 int adjoint_pass(bop_ctx* c, const double* w, double* Hbar, double* Ebar, cudaStream_t s) {
   const int n = c->n;
-  int nc = adjoint_columns(c->norb);
-  size_t per_site = (size_t)c->norb * nc;
-  long long levsum = 0;
-  for (int k = 0; k <= c->K; k++) levsum += c->maxlev[k];
-  size_t slot_elems = (2 * (size_t)levsum) * per_site + 64;
-  int nwork = n * c->S * (c->norb / nc);
-  int slots = nwork < 1216 ? nwork : 1216;
-  size_t esz = c->fp64 ? sizeof(double) : sizeof(float);
-  CKS(ensure(c, c->adjscr, esz * slot_elems * slots));
   AdjointArgs aa;
+  memset(&aa, 0, sizeof(aa));
   aa.cv = cview(c);
   aa.H = c->fp64 ? c->H64.p : c->H32.p;
   aa.HS = c->HS;
@@ -578,14 +614,43 @@ int adjoint_pass(bop_ctx* c, const double* w, double* Hbar, double* Ebar, cudaSt
   aa.norb = c->norb;
   aa.n_mom = c->n_mom;
   aa.w = w;
-  aa.scratch = c->adjscr.p;
-  aa.slot_elems = slot_elems;
-  aa.slots = slots;
   aa.Hbar = Hbar;
   aa.HSu = c->HSu;
   aa.Ebar = Ebar;
+  if (c->psi_valid) {
+    aa.pstore = c->psis.p;
+    aa.pbstore = c->psib.p;
+    aa.psi_off = P<long long>(c->psi_off);
+    aa.psi_tot = c->psi_tot;
+    aa.nc = forward_nc(c);
+    int ce = 1, co = 1;
+    for (int k = 1; k <= c->K; k++) {
+      int& cap = (k & 1) ? co : ce;
+      if (c->maxlev[k] > cap) cap = c->maxlev[k];
+    }
+    aa.cap_even = ce;
+    aa.cap_odd = co;
+    aa.max_sites = c->maxlev[c->K] > 0 ? c->maxlev[c->K] : 1;
+    aa.max_adj = c->maxlev[c->K + 1] > 0 ? c->maxlev[c->K + 1] : 1;
+    aa.cap_eb = c->maxlev[c->K - 1] > 0 ? c->maxlev[c->K - 1] : 1;
+  } else {
+    int nc = adjoint_columns(c->norb);
+    size_t per_site = (size_t)c->norb * nc;
+    long long levsum = 0;
+    for (int k = 0; k <= c->K; k++) levsum += c->maxlev[k];
+    size_t slot_elems = (2 * (size_t)levsum) * per_site + 64;
+    int nwork = n * c->S * (c->norb / nc);
+    int slots = nwork < 1216 ? nwork : 1216;
+    size_t esz = c->fp64 ? sizeof(double) : sizeof(float);
+    CKS(ensure(c, c->adjscr, esz * slot_elems * slots));
+    aa.scratch = c->adjscr.p;
+    aa.slot_elems = slot_elems;
+    aa.slots = slots;
+  }
   Region R(c, PK_ADJOINT, 1, s);
-  if (launch_moments_adjoint(aa, c->fp64, s)) return fail(c, BOP_ERR_CUDA, "adjoint launch failed");
+  const int r = launch_moments_adjoint(aa, c->fp64, s);
+  if (r == -2) return fail(c, BOP_ERR_OVERFLOW, "cluster level too large for shared memory");
+  if (r) return fail(c, BOP_ERR_CUDA, "adjoint launch failed");
   return BOP_OK;
 }
 
@@ -807,7 +872,8 @@ int bop_destroy(bop_ctx* c) {
                   &c->adjscr, &c->Hbar, &c->Ebar, &c->status, &c->cub_tmp, &c->nprod,
                   &c->ginv, &c->hx, &c->hf, &c->gamma, &c->scfred, &c->lbase, &c->lnlev, &c->lflag, &c->lxs,
                   &c->lys, &c->lZ1, &c->lH1, &c->lZ2, &c->lH2, &c->lybar, &c->lcot, &c->lxbar, &c->lcount,
-                  &c->rwN, &c->rwt, &c->rdUE, &c->rvec, &c->rcoef};
+                  &c->rwN, &c->rwt, &c->rdUE, &c->rvec, &c->rcoef,
+                  &c->psi_off, &c->psis, &c->psib, &c->lsum};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -908,6 +974,15 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
   CKS(check_status(c, s));
   CKS(build_clusters(c, s));
   CKS(size_state(c));
+  // per-atom row offsets of a stored Psi sweep
+  CKS(ensure(c, c->lsum, sizeof(long long) * (n + 1)));
+  CKS(ensure(c, c->psi_off, sizeof(long long) * (n + 1)));
+  CK(cudaMemsetAsync(c->lsum.p, 0, sizeof(long long) * (n + 1), s));
+  launch_level_sums(n, c->K, P<int>(c->level_end), P<long long>(c->lsum), s);
+  CKS(exclusive_scan(c, P<long long>(c->lsum), P<long long>(c->psi_off), n + 1, s));
+  CK(cudaMemcpyAsync(&c->psi_tot, P<long long>(c->psi_off) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  c->psi_valid = false;
   c->built = true;
   memset(&c->st, 0, sizeof(c->st));
   c->st.n_atoms = n;
@@ -1024,6 +1099,7 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   cudaStream_t s = S_(stream);
   const int n = c->n, M = c->S * n * c->norb;
   c->energized = c->weighted = false;
+  c->psi_valid = false;
   if (delta_io) CK(cudaMemcpyAsync(c->delta.p, delta_io, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   else CK(cudaMemsetAsync(c->delta.p, 0, sizeof(double) * n, s));
   const bool stoner = c->m.scf == BOP_SCF_STONER;
@@ -1152,6 +1228,7 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   CKS(ensure(c, c->Hbar, sizeof(double) * (size_t)(c->nb > 0 ? c->nb : 1) * c->HSu));
   CKS(ensure(c, c->Ebar, sizeof(double) * (size_t)M));
   CK(cudaMemsetAsync(c->Hbar.p, 0, sizeof(double) * (size_t)(c->nb > 0 ? c->nb : 1) * c->HSu, s));
+  CKS(prepare_psi_store(c, s));
   int solve_status = BOP_OK;
   c->st.response_iterations = 0;
   c->st.response_converged = 1;
@@ -1254,6 +1331,20 @@ int bop_evaluate_host(bop_ctx* c, int n, const double* pos_host, const double* c
   for (DBuf* q : {&dpos, &dF, &dW})
     if (q->p) cudaFree(q->p);
   return r;
+}
+
+int bop_set_store_budget(bop_ctx* c, long long bytes) {
+  if (!c) return BOP_ERR_ARG;
+  c->store_budget = bytes < 0 ? (size_t)-1 : (size_t)bytes;
+  if (c->store_budget == 0) {
+    for (DBuf* b : {&c->psis, &c->psib})
+      if (b->p) {
+        cudaFree(b->p);
+        b->p = nullptr;
+        b->bytes = 0;
+      }
+  }
+  return BOP_OK;
 }
 
 int bop_set_mlp(bop_ctx* c, bop_mlp* net) {

@@ -313,3 +313,16 @@ int launch_cluster(int pass, int n, int K, const long long* row_ptr, const int* 
     k_cluster<1><<<grid, CL_THREADS, smem, s>>>(n, K, row_ptr, col, img, bond_of_edge, sc, out, status);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
+
+// Rows of one stored Psi sweep per atom: sum_{k=0..K} |C_k|.
+__global__ void k_level_sums(int n, int K, const int* __restrict__ level_end, long long* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long a = 0;
+  for (int k = 0; k <= K; k++) a += level_end[(size_t)i * (K + 1) + k];
+  out[i] = a;
+}
+
+void launch_level_sums(int n, int K, const int* level_end, long long* out, cudaStream_t s) {
+  k_level_sums<<<(n + 255) / 256, 256, 0, s>>>(n, K, level_end, out);
+}

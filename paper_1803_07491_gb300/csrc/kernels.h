@@ -63,6 +63,8 @@ int launch_cluster(int pass, int n, int K, const long long* row_ptr, const int* 
                    const int* bond_of_edge, ClusterScratch sc, ClusterOut out, int grid, unsigned* status,
                    cudaStream_t s);
 
+void launch_level_sums(int n, int K, const int* level_end, long long* out, cudaStream_t s);
+
 struct MomentsArgs {
   ClusterView cv;
   const void* H;       // float or double [nb][HS]
@@ -74,6 +76,12 @@ struct MomentsArgs {
   int max_sites;       // largest cluster |C_K|
   int max_adj;         // largest adjacency of one cluster
   double* mu;          // [S][n][norb][n_mom]
+  // optional store of every Psi_k (NULL = none): rows of the item
+  // (spin, atom[, alpha]) at ((spin (norb/nc) + alpha) psi_tot + psi_off[atom]) rows,
+  // level k at row offset sum_{j<k} |C_j|; row = norb x nc values padded
+  void* pstore;
+  const long long* psi_off;  // [n+1] prefix sums of sum_k |C_k| over atoms
+  long long psi_tot;
 };
 int launch_moments(const MomentsArgs& a, int fp64, cudaStream_t s);
 
@@ -90,6 +98,14 @@ struct AdjointArgs {
   double* Hbar;        // [nb][HSu]   (+=)
   int HSu;
   double* Ebar;        // [S][n][norb] (+=), may be null
+  // reverse sweep over stored Psi (pstore != NULL; layout of MomentsArgs.pstore)
+  const void* pstore;
+  void* pbstore;       // Psi-bar store, same layout (needed when Hbar != NULL)
+  const long long* psi_off;
+  long long psi_tot;
+  int nc;              // columns per work item used by the forward pass that stored Psi
+  int cap_even, cap_odd;  // largest even / odd level |C_k|, k = 1..K
+  int max_sites, max_adj, cap_eb;  // cap_eb: largest |C_K-1|
 };
 int launch_moments_adjoint(const AdjointArgs& a, int fp64, cudaStream_t s);
 

@@ -79,6 +79,12 @@ __device__ __forceinline__ void block_apply(const T* __restrict__ hrec, const T*
   }
 }
 
+// next 16-byte boundary (the staged adjacency holds int2 / u64 records); the
+// launchers reserve 16 bytes of slack for it
+__device__ __forceinline__ unsigned char* align16(unsigned char* p) {
+  return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -142,6 +148,33 @@ __device__ __forceinline__ void load_row(const T* __restrict__ p, T x[N]) {
       double2 w = q[v];
       if (2 * v + 0 < N) x[2 * v + 0] = w.x;
       if (2 * v + 1 < N) x[2 * v + 1] = w.y;
+    }
+  }
+}
+
+template <typename T, int N, int PS>
+__device__ __forceinline__ void store_row(T* __restrict__ p, const T x[N]) {
+  if constexpr (N == 1) {
+    p[0] = x[0];
+  } else if constexpr (sizeof(T) == 4) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int v = 0; v < PS / 4; v++) {
+      float4 w;
+      w.x = 4 * v + 0 < N ? x[4 * v + 0] : 0.f;
+      w.y = 4 * v + 1 < N ? x[4 * v + 1] : 0.f;
+      w.z = 4 * v + 2 < N ? x[4 * v + 2] : 0.f;
+      w.w = 4 * v + 3 < N ? x[4 * v + 3] : 0.f;
+      q[v] = w;
+    }
+  } else {
+    double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+    for (int v = 0; v < PS / 2; v++) {
+      double2 w;
+      w.x = 2 * v + 0 < N ? x[2 * v + 0] : 0.0;
+      w.y = 2 * v + 1 < N ? x[2 * v + 1] : 0.0;
+      q[v] = w;
     }
   }
 }
@@ -218,7 +251,8 @@ struct FwdSmem {
 template <typename T, int NO, int NC>
 __global__ void __launch_bounds__(FWD_THREADS, sizeof(T) == 4 ? 2 : 1)
 k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_mom,
-          FwdSmem L, int n_items, int chunk, double* __restrict__ mu) {
+          FwdSmem L, int n_items, int chunk, double* __restrict__ mu, T* __restrict__ pstore,
+          const long long* __restrict__ psi_off, long long psi_tot) {
   constexpr int N = NO * NC;
   constexpr int PS = (N == 1) ? 1 : Row<T, N>::PS;
   constexpr int HB = NO == 1 ? 1 : 16;
@@ -226,7 +260,7 @@ k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
   T* buf[2];
   buf[0] = reinterpret_cast<T*>(smem_raw);
   buf[1] = buf[0] + (size_t)L.cap_even * PS;
-  unsigned char* tail = reinterpret_cast<unsigned char*>(buf[1] + (size_t)L.cap_odd * PS);
+  unsigned char* tail = align16(reinterpret_cast<unsigned char*>(buf[1] + (size_t)L.cap_odd * PS));
   int2* s_adj = reinterpret_cast<int2*>(tail);
   unsigned long long* s_lvc = reinterpret_cast<unsigned long long*>(s_adj + (L.stage ? L.max_adj : 0));
   int* s_aoff = reinterpret_cast<int*>(s_lvc + (L.stage ? L.max_sites : 0));
@@ -260,10 +294,21 @@ k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
       const int r = q / NC, c = q % NC;
       buf[0][q] = (NC == NO) ? T(r == c ? 1 : 0) : T(r == grp ? 1 : 0);
     }
+    // stored Psi: item rows start at ib, level k at row lo_k = sum_{j<k} |C_j|
+    T* pitem = nullptr;
+    if (pstore != nullptr) {
+      pitem = pstore + ((size_t)(spin * (NO / NC) + grp) * psi_tot + psi_off[atom]) * PS;
+      for (int q = tid; q < PS; q += FWD_THREADS) {
+        const int r = q / NC, c = q % NC;
+        pitem[q] = q < N ? ((NC == NO) ? T(r == c ? 1 : 0) : T(r == grp ? 1 : 0)) : T(0);
+      }
+    }
+    long long lo_k = 0;
     __syncthreads();
     double* out = mu + ((size_t)sa * NO + grp) * n_mom;
     if (tid < NC) out[(size_t)tid * n_mom] = 1.0;
     for (int k = 1; k <= K; k++) {
+      lo_k += lev[k - 1];
       const int nrow = lev[k], ncol = lev[k - 1];
       const T* prev = buf[(k - 1) & 1];
       T* cur = buf[k & 1];
@@ -328,6 +373,14 @@ k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
 #pragma unroll
             for (int c = 0; c < NC; c++) dst[r * NC + c] = acc[r][c];
         }
+        if (pitem != nullptr) {
+          T row[N];
+#pragma unroll
+          for (int r = 0; r < NO; r++)
+#pragma unroll
+            for (int c = 0; c < NC; c++) row[r * NC + c] = acc[r][c];
+          store_row<T, N, PS>(pitem + (size_t)(lo_k + t) * PS, row);
+        }
       }
 #pragma unroll
       for (int c = 0; c < NC; c++) {
@@ -350,7 +403,246 @@ k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
   }
 }
 
-// ------------------------------------------------------------------ adjoint
+
+// ------------------------------------------------------------------ reverse sweep over stored Psi
+// With every Psi_k of every work item stored in global memory (rows of the
+// forward kernel, level k at rows lo_k .. lo_k + |C_k|), the reverse sweep
+//   Psi-bar_K     = 2 w_2K Psi_K + w_2K-1 Psi_K-1
+//   Psi-bar_k-1   = H Psi-bar_k (rows < |C_k-1|, columns < |C_k|)
+//                   + 2 w_2k-2 Psi_k-1 + w_2k-1 Psi_k + w_2k-3 Psi_k-2
+// runs like the forward kernel: Psi-bar_k and Psi-bar_k-1 in two shared
+// buffers (even / odd levels), the adjacency staged, one site row per
+// thread.  The onsite cotangents dL/dE_t = sum_k Psi-bar_k[t] . Psi_k-1[t]
+// are accumulated per site in shared memory and added once per item.
+// With HBAR the Psi-bar levels are also stored, and the bond cotangents
+// sum_k Psi-bar_k(t) Psi_k-1(s)^T are formed per cluster edge from the two
+// stores and added to the bond's unique elements with FP64 atomics.
+struct RevSmem {
+  int cap_even, cap_odd, max_sites, max_adj, cap_eb;
+  bool stage;
+};
+
+template <typename T, int NO>
+__host__ __device__ constexpr size_t eb_elems(int cap_eb) {
+  return ((size_t)cap_eb * NO * sizeof(T) + 15) / 16 * 16 / sizeof(T);
+}
+
+template <typename T, int NO, int NC, bool HBAR>
+__global__ void __launch_bounds__(FWD_THREADS, sizeof(T) == 4 ? 2 : 1)
+k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_mom,
+          RevSmem L, int n_items, int chunk, const T* __restrict__ pstore, T* __restrict__ pbstore,
+          const long long* __restrict__ psi_off, long long psi_tot, const double* __restrict__ wts,
+          double* __restrict__ Hbar, int HSu, double* __restrict__ Ebar) {
+  constexpr int N = NO * NC;
+  constexpr int PS = (N == 1) ? 1 : Row<T, N>::PS;
+  constexpr int HB = NO == 1 ? 1 : 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* buf[2];
+  buf[0] = reinterpret_cast<T*>(smem_raw);
+  buf[1] = buf[0] + (size_t)L.cap_even * PS;
+  T* eb = buf[1] + (size_t)L.cap_odd * PS;  // [cap_eb][NO], padded to 16 bytes
+  unsigned char* tail = align16(reinterpret_cast<unsigned char*>(eb + eb_elems<T, NO>(L.cap_eb)));
+  int2* s_adj = reinterpret_cast<int2*>(tail);
+  unsigned long long* s_lvc = reinterpret_cast<unsigned long long*>(s_adj + (L.stage ? L.max_adj : 0));
+  int* s_aoff = reinterpret_cast<int*>(s_lvc + (L.stage ? L.max_sites : 0));
+  int* s_atom = s_aoff + (L.stage ? L.max_sites + 1 : 0);
+  __shared__ T ws[NC][BOP_MAX_NMOM];
+  __shared__ int s_lev[BOP_MAX_K + 1];
+  __shared__ long long s_lo[BOP_MAX_K + 1];
+  const int K = cv.K;
+  const int tid = threadIdx.x;
+  const int w0 = blockIdx.x * chunk, w1 = min(n_items, w0 + chunk);
+  for (int w = w0; w < w1; w++) {
+    const int grp = (NC == NO) ? 0 : (w % NO);
+    const int sa = (NC == NO) ? w : (w / NO);
+    const int spin = sa / n, atom = sa % n;
+    const long long s0 = cv.site_off[atom];
+    const int* lev = cv.level_end + (size_t)atom * (K + 1);
+    const int nsite = lev[K];
+    const long long abase = cv.adj_off[s0];
+    const int2* adj = cv.adj + abase;
+    const unsigned long long* lvc = cv.lvcnt + s0;
+    const int* satom = cv.site_atom + s0;
+    const T* E = onsite + (size_t)spin * n * NO;
+    const size_t ib = ((size_t)(spin * (NO / NC) + grp) * psi_tot + psi_off[atom]) * PS;
+    const T* P = pstore + ib;
+    T* PB = HBAR ? pbstore + ib : nullptr;
+    if (L.stage) {
+      const int nadj = (int)(cv.adj_off[s0 + nsite] - abase);
+      for (int q = tid; q < nadj; q += FWD_THREADS) s_adj[q] = __ldg(adj + q);
+      for (int q = tid; q <= nsite; q += FWD_THREADS) s_aoff[q] = (int)(cv.adj_off[s0 + q] - abase);
+      for (int q = tid; q < nsite; q += FWD_THREADS) {
+        s_lvc[q] = lvc[q];
+        s_atom[q] = satom[q];
+      }
+    }
+    if (tid <= K) s_lev[tid] = lev[tid];
+    if (tid == 0) {
+      long long o = 0;
+      for (int k = 0; k <= K; k++) {
+        s_lo[k] = o;
+        o += lev[k];
+      }
+    }
+    for (int q = tid; q < NC * n_mom; q += FWD_THREADS) {
+      const int c = q / n_mom, m = q % n_mom;
+      ws[c][m] = (T)wts[((size_t)sa * NO + grp + c) * n_mom + m];
+    }
+    __syncthreads();
+    const int neb = s_lev[K - 1];
+    for (int q = tid; q < neb * NO; q += FWD_THREADS) eb[q] = T(0);
+    // Psi-bar_K
+    {
+      T* xb = buf[K & 1];
+      for (int t = tid; t < s_lev[K]; t += FWD_THREADS) {
+        T pk[N], row[N];
+        load_row<T, N, PS>(P + (size_t)(s_lo[K] + t) * PS, pk);
+#pragma unroll
+        for (int q = 0; q < N; q++) row[q] = T(2) * ws[q % NC][2 * K] * pk[q];
+        if (t < s_lev[K - 1]) {
+          T pk1[N];
+          load_row<T, N, PS>(P + (size_t)(s_lo[K - 1] + t) * PS, pk1);
+#pragma unroll
+          for (int q = 0; q < N; q++) row[q] += ws[q % NC][2 * K - 1] * pk1[q];
+        }
+        store_row<T, N, PS>(xb + (size_t)t * PS, row);
+        if (HBAR) store_row<T, N, PS>(PB + (size_t)(s_lo[K] + t) * PS, row);
+      }
+    }
+    __syncthreads();
+    for (int k = K; k >= 1; k--) {
+      const T* xb = buf[k & 1];
+      T* yb = buf[(k - 1) & 1];
+      const int nrow = s_lev[k - 1];
+      for (int t = tid; t < nrow; t += FWD_THREADS) {
+        T xt[N], p1[N];
+        load_row<T, N, PS>(xb + (size_t)t * PS, xt);
+        load_row<T, N, PS>(P + (size_t)(s_lo[k - 1] + t) * PS, p1);
+        // onsite cotangent of level k
+#pragma unroll
+        for (int r = 0; r < NO; r++) {
+          T a = T(0);
+#pragma unroll
+          for (int c = 0; c < NC; c++) a += xt[r * NC + c] * p1[r * NC + c];
+          eb[t * NO + r] += a;
+        }
+        if (k >= 2) {
+          T acc[NO][NC];
+          const T* e = E + (size_t)(L.stage ? s_atom[t] : satom[t]) * NO;
+#pragma unroll
+          for (int r = 0; r < NO; r++) {
+            const T er = e[r];
+#pragma unroll
+            for (int c = 0; c < NC; c++) acc[r][c] = er * xt[r * NC + c];
+          }
+          int cnt;
+          if (k < K) {
+            const unsigned long long lc = L.stage ? s_lvc[t] : lvc[t];
+            cnt = (int)((lc >> (8 * k)) & 0xff);
+          } else {
+            cnt = L.stage ? s_aoff[t + 1] - s_aoff[t] : (int)(cv.adj_off[s0 + t + 1] - cv.adj_off[s0 + t]);
+          }
+          if (cnt > 0) {
+            const int q0 = L.stage ? s_aoff[t] : (int)(cv.adj_off[s0 + t] - abase);
+            const int2* ent = L.stage ? s_adj + q0 : adj + q0;
+            int2 en = ent[0];
+            T hb[HB];
+            load_bond<T, NO>(H + (size_t)en.y * HS, hb);
+            for (int q = 0; q < cnt; q++) {
+              const int sidx = en.x;
+              T hc[HB];
+#pragma unroll
+              for (int z = 0; z < HB; z++) hc[z] = hb[z];
+              if (q + 1 < cnt) {
+                en = ent[q + 1];
+                load_bond<T, NO>(H + (size_t)en.y * HS, hb);
+              }
+              T xs[N];
+              load_row<T, N, PS>(xb + (size_t)sidx * PS, xs);
+              block_fma<T, NO, NC>(hc, xs, acc);
+            }
+          }
+          T pk[N];
+          load_row<T, N, PS>(P + (size_t)(s_lo[k] + t) * PS, pk);
+          T row[N];
+#pragma unroll
+          for (int r = 0; r < NO; r++)
+#pragma unroll
+            for (int c = 0; c < NC; c++) {
+              const int q = r * NC + c;
+              row[q] = acc[r][c] + T(2) * ws[c][2 * k - 2] * p1[q] + ws[c][2 * k - 1] * pk[q];
+            }
+          if (k >= 2 && t < s_lev[k - 2]) {
+            T p2[N];
+            load_row<T, N, PS>(P + (size_t)(s_lo[k - 2] + t) * PS, p2);
+#pragma unroll
+            for (int q = 0; q < N; q++) row[q] += ws[q % NC][2 * k - 3] * p2[q];
+          }
+          store_row<T, N, PS>(yb + (size_t)t * PS, row);
+          if (HBAR) store_row<T, N, PS>(PB + (size_t)(s_lo[k - 1] + t) * PS, row);
+        }
+      }
+      __syncthreads();
+    }
+    if (Ebar != nullptr) {
+      for (int q = tid; q < neb * NO; q += FWD_THREADS) {
+        const int t = q / NO, r = q % NO;
+        atomicAdd(Ebar + ((size_t)spin * n + (L.stage ? s_atom[t] : satom[t])) * NO + r, (double)eb[q]);
+      }
+    }
+    if (HBAR) {
+      // bond cotangents from the two stores (the item's rows were written by this CTA)
+      for (int t = tid; t < s_lev[K]; t += FWD_THREADS) {
+        int lt = 0;
+        while (lt < K && t >= s_lev[lt]) lt++;
+        const int q0 = L.stage ? s_aoff[t] : (int)(cv.adj_off[s0 + t] - abase);
+        const int q1 = L.stage ? s_aoff[t + 1] : (int)(cv.adj_off[s0 + t + 1] - abase);
+        for (int q = q0; q < q1; q++) {
+          const int2 en = L.stage ? s_adj[q] : adj[q];
+          const int sidx = en.x;
+          if (sidx >= s_lev[K - 1]) break;
+          int ls = 0;
+          while (ls < K && sidx >= s_lev[ls]) ls++;
+          const int kmin = lt > ls + 1 ? lt : ls + 1;
+          T G[NO][NO];
+#pragma unroll
+          for (int b = 0; b < NO; b++)
+#pragma unroll
+            for (int g = 0; g < NO; g++) G[b][g] = T(0);
+          for (int k = kmin; k <= K; k++) {
+            T pb[N], ps[N];
+            load_row<T, N, PS>(PB + (size_t)(s_lo[k] + t) * PS, pb);
+            load_row<T, N, PS>(P + (size_t)(s_lo[k - 1] + sidx) * PS, ps);
+#pragma unroll
+            for (int b = 0; b < NO; b++)
+#pragma unroll
+              for (int g = 0; g < NO; g++) {
+                T a = T(0);
+#pragma unroll
+                for (int c = 0; c < NC; c++) a += pb[b * NC + c] * ps[g * NC + c];
+                G[b][g] += a;
+              }
+          }
+          double* hbp = Hbar + (size_t)en.y * HSu;
+          if constexpr (NO == 1) {
+            atomicAdd(hbp, (double)G[0][0]);
+          } else {
+#pragma unroll
+            for (int b = 0; b < NO; b++)
+#pragma unroll
+              for (int g = b; g < NO; g++) {
+                const double v = (double)G[b][g] + (b != g ? (double)G[g][b] : 0.0);
+                atomicAdd(hbp + U5(b, g), v);
+              }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ adjoint (recompute)
 __device__ __forceinline__ int site_level(const int* lev, int K, int t) {
   int k = 0;
   while (k < K && t >= lev[k]) k++;
@@ -543,7 +835,7 @@ int run_forward(const MomentsArgs& a, cudaStream_t s) {
   const int chunk = (n_items + slots - 1) / slots;
   const int grid = (n_items + chunk - 1) / chunk;
   fn<<<grid, FWD_THREADS, smem, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n, a.n_mom, L, n_items,
-                                      chunk, a.mu);
+                                      chunk, a.mu, (T*)a.pstore, a.psi_off, a.psi_tot);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -555,6 +847,50 @@ int run_adjoint(const AdjointArgs& a, cudaStream_t s) {
                                                        a.n_mom, nwork, a.w, (T*)a.scratch, a.slot_elems,
                                                        a.Hbar, a.HSu, a.Ebar);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename T, int NO, int NC, bool HBAR>
+int run_reverse(const AdjointArgs& a, cudaStream_t s) {
+  constexpr int N = NO * NC;
+  constexpr int PS = (N == 1) ? 1 : Row<T, N>::PS;
+  RevSmem L{a.cap_even, a.cap_odd, a.max_sites, a.max_adj, a.cap_eb, true};
+  const size_t psi = (size_t)(a.cap_even + a.cap_odd) * PS * sizeof(T) + eb_elems<T, NO>(a.cap_eb) * sizeof(T);
+  const size_t stage = (size_t)a.max_adj * 8 + (size_t)a.max_sites * 8 + (size_t)(a.max_sites + 1) * 4 +
+                       (size_t)a.max_sites * 4 + 16;
+  auto fn = k_adj_rev<T, NO, NC, HBAR>;
+  size_t smem = psi + stage;
+  int per_sm = 0, per_sm_unstaged = 0;
+  if (smem <= 227 * 1024) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, FWD_THREADS, smem);
+  }
+  if (psi > 227 * 1024) return -2;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psi);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_unstaged, fn, FWD_THREADS, psi);
+  if (per_sm < per_sm_unstaged) {  // staging the adjacency would cost a resident CTA
+    L.stage = false;
+    smem = psi;
+    per_sm = per_sm_unstaged;
+  } else {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  if (per_sm < 1) per_sm = 1;
+  const int n_items = a.n * a.n_spin * (NO / NC);
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int slots = sms * per_sm;
+  const int chunk = (n_items + slots - 1) / slots;
+  const int grid = (n_items + chunk - 1) / chunk;
+  fn<<<grid, FWD_THREADS, smem, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n, a.n_mom, L, n_items, chunk,
+                                      (const T*)a.pstore, (T*)a.pbstore, a.psi_off, a.psi_tot, a.w, a.Hbar, a.HSu,
+                                      a.Ebar);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename T, int NO, int NC>
+int run_reverse_mode(const AdjointArgs& a, cudaStream_t s) {
+  return a.Hbar ? run_reverse<T, NO, NC, true>(a, s) : run_reverse<T, NO, NC, false>(a, s);
 }
 
 }  // namespace
@@ -577,6 +913,11 @@ int launch_moments(const MomentsArgs& a, int fp64, cudaStream_t s) {
 int adjoint_columns(int norb) { return norb == 1 ? 1 : 5; }
 
 int launch_moments_adjoint(const AdjointArgs& a, int fp64, cudaStream_t s) {
+  if (a.pstore != nullptr) {  // reverse sweep over stored Psi
+    if (a.norb == 1) return fp64 ? run_reverse_mode<double, 1, 1>(a, s) : run_reverse_mode<float, 1, 1>(a, s);
+    if (a.nc == 5) return fp64 ? run_reverse_mode<double, 5, 5>(a, s) : run_reverse_mode<float, 5, 5>(a, s);
+    return fp64 ? run_reverse_mode<double, 5, 1>(a, s) : run_reverse_mode<float, 5, 1>(a, s);
+  }
   if (a.norb == 1) return fp64 ? run_adjoint<double, 1, 1>(a, s) : run_adjoint<float, 1, 1>(a, s);
   return fp64 ? run_adjoint<double, 5, 5>(a, s) : run_adjoint<float, 5, 5>(a, s);
 }

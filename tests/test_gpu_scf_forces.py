@@ -92,3 +92,29 @@ def test_d2000_lcn_forces_by_finite_differences(bop):
         fd = -(energy(p) - energy(q)) / (2 * h)
         assert abs(F[i, c] - fd) < 2e-5 + 1e-4 * abs(fd), (i, c, F[i, c], fd)
     ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-4)])
+@pytest.mark.parametrize("which", ["d_lcn", "s", "d13"])
+def test_stored_and_recomputed_reverse_sweeps_agree(bop, prec, tol, which):
+    """bop_forces with Psi stored (default) and with Psi recomputed in every
+    reverse sweep (store budget 0): the same forces, virial and weights."""
+    if which == "d_lcn":
+        w = I.with_run(I.small_bcc(3, 3, 3, 0.08, 48), scf="lcn", scf_tol=1e-10 if prec == "fp64" else 1e-5)
+    elif which == "s":
+        w = I.small_bcc(3, 3, 3, 0.08, 49, model=I.MODEL_S, run=I.RunParams(n_e=0.7))
+    else:
+        w = I.with_run(I.small_bcc(2, 2, 2, 0.08, 50), n_mom=13)
+    out = []
+    for budget in (-1, 0):
+        ctx = bop.Context(w.model, w.run, prec)
+        bop.bop_set_store_budget(ctx.h, budget)
+        res = ctx.evaluate(w.pos, w.cell, w.pbc)
+        orb = bop.bop_get_orbital_state(ctx.h, w.n_atoms * w.model.norb * w.run.n_spin, w.run.n_mom, weights=True)
+        out.append((res.forces.cpu().numpy(), res.virial.cpu().numpy(), orb["weights"].cpu().numpy()))
+        ctx.close()
+    (F1, V1, W1), (F2, V2, W2) = out
+    scale = max(1.0, np.abs(F2).max())
+    assert np.max(np.abs(F1 - F2)) < tol * scale
+    assert np.max(np.abs(V1 - V2)) < tol * max(1.0, np.abs(V2).max())
+    assert np.max(np.abs(W1 - W2)) < tol * max(1.0, np.abs(W2).max())
