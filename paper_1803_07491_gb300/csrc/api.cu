@@ -492,6 +492,16 @@ int run_scalar(bop_ctx* c, int M, const double* mu, cudaStream_t s) {
 int fermi_and_N(bop_ctx* c, int warm, cudaStream_t s) {
   const int M = c->S * c->n * c->norb;
   const double target = c->m.n_e * c->n;
+  {
+    // one cooperative launch: bracket, Newton rounds to convergence, N and DOS
+    Region R(c, PK_FERMI, 1, s);
+    const int r = launch_fermi_coop(M, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf),
+                                    P<double>(c->b_inf), c->n_exp, c->sfac, target, P<FermiState>(c->fstate),
+                                    P<double>(c->partials), warm, FERMI_MAX_ROUNDS, FERMI_TOL, P<double>(c->N),
+                                    P<double>(c->dos), s);
+    if (r == 0) return BOP_OK;
+    if (r != -2) return fail(c, BOP_ERR_CUDA, "fermi launch failed");
+  }
   const int rounds = warm ? FERMI_ROUNDS_WARM : FERMI_ROUNDS_COLD;
   {
     Region R(c, PK_FERMI, 1 + rounds, s);

@@ -18,6 +18,8 @@
 // 2L multiply-adds per coefficient instead of a sweep over the chain.  The
 // numbers are the same as the chain's (the tests compare with the oracle,
 // which runs the chain as printed).
+#include <cooperative_groups.h>
+
 #include "chain_common.cuh"
 
 using namespace scal;
@@ -286,6 +288,127 @@ __global__ void __launch_bounds__(RT2) k_ef_response2(int M, int ne, const doubl
   }
 }
 
+
+// The whole Fermi-level solve in one cooperative launch: the bracket, the
+// safeguarded Newton rounds of k_fermi_newton (same update rules) until
+// convergence or max_rounds, then N and the DOS of every orbital at E_F.
+// Per round every block writes its partial sums, the grid synchronises once,
+// and every block reduces all partials in the same fixed order, so all
+// blocks take the same decision without a second synchronisation.  The
+// partial buffers alternate between rounds (a block can only overwrite a
+// buffer after every block has passed the next grid barrier).
+constexpr int FC = 64;  // threads per block of the cooperative solve
+
+__device__ __forceinline__ double coop_block_reduce(double v, double* sh, bool take_max) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = take_max ? fmax(v, w) : v + w;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = sh[0];
+  for (int w = 1; w < FC / 32; w++) t = take_max ? fmax(t, sh[w]) : t + sh[w];
+  return t;  // every thread
+}
+
+// Rounds evaluate N and the DOS of every orbital at the current iterate and
+// store them; the stored values are those of the last iterate E, within
+// tol of E_F (the SCF residual uses them; the energy is evaluated at E_F).
+__global__ void __launch_bounds__(FC) k_fermi_coop(int M, const double* __restrict__ gsig,
+                                                   const double* __restrict__ inv, const double* __restrict__ a_inf,
+                                                   const double* __restrict__ b_inf, int ne, double sfac,
+                                                   double target, FermiState* st, double* part, int warm,
+                                                   int max_rounds, double tol, double* __restrict__ Nout,
+                                                   double* __restrict__ dos) {
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  __shared__ double sh[FC / 32 + 1];
+  __shared__ double fr[FC / 32 + 1];
+  const int nb = gridDim.x, b = blockIdx.x;
+  const int stride = nb * FC;
+  // bracket [min(a - 2b) - 1e-3, max(a + 2b) + 1e-3]
+  double mn = 1e300, mx = -1e300;
+  for (int o = b * FC + threadIdx.x; o < M; o += stride) {
+    mn = fmin(mn, a_inf[o] - 2.0 * b_inf[o]);
+    mx = fmax(mx, a_inf[o] + 2.0 * b_inf[o]);
+  }
+  mn = coop_block_reduce(-mn, sh, true);
+  mx = coop_block_reduce(mx, sh, true);
+  if (threadIdx.x == 0) {
+    part[2 * b] = mn;
+    part[2 * b + 1] = mx;
+  }
+  grid.sync();
+  double lo = -final_reduce<FC>(part, 2, 0, nb, true, fr) - 1e-3;
+  double hi = final_reduce<FC>(part, 2, 1, nb, true, fr) + 1e-3;
+  const double prev = st->ef;
+  double E = (warm && prev > lo && prev < hi) ? prev : 0.5 * (lo + hi);
+  double ef = E;
+  int iters = 0;
+  bool done = hi - lo < tol;
+  if (done) ef = 0.5 * (lo + hi);
+  bool evaluated = false;
+  for (int r = 0; !done && r < max_rounds; r++) {
+    double aN = 0.0, aD = 0.0;
+    for (int o = b * FC + threadIdx.x; o < M; o += stride) {
+      const double bi = b_inf[o];
+      const double xr = (E - a_inf[o]) / (2.0 * bi);
+      double Nv, dN;
+      count_and_dos(gsig, inv, M, o, ne, clamp1(xr), &Nv, &dN);
+      const double d = (xr > -1.0 && xr < 1.0) ? dN / (2.0 * bi) : 0.0;
+      aN += Nv;
+      aD += d;
+      Nout[o] = Nv;
+      dos[o] = d;
+    }
+    evaluated = true;
+    aN = coop_block_reduce(aN, sh, false);
+    aD = coop_block_reduce(aD, sh, false);
+    double* pr = part + (size_t)((r + 1) & 1) * 2 * nb;
+    if (threadIdx.x == 0) {
+      pr[2 * b] = aN;
+      pr[2 * b + 1] = aD;
+    }
+    grid.sync();
+    const double tN = final_reduce<FC>(pr, 2, 0, nb, false, fr);
+    const double tD = final_reduce<FC>(pr, 2, 1, nb, false, fr);
+    const double f = sfac * tN - target, fp = sfac * tD;
+    iters++;
+    if (f == 0.0) {
+      ef = E;
+      done = true;
+    } else {
+      if (f < 0.0) lo = E; else hi = E;
+      double xn = fp > 0.0 ? E - f / fp : lo - 1.0;
+      if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+      if (fabs(xn - E) < tol || hi - lo < tol || iters >= max_rounds) {
+        ef = xn;
+        done = true;
+      } else {
+        E = xn;
+      }
+    }
+  }
+  if (b == 0 && threadIdx.x == 0) {
+    st->lo = lo;
+    st->hi = hi;
+    st->mid = E;
+    st->ef = ef;
+    st->iters = iters;
+    st->done = done ? 1 : 0;
+  }
+  if (!evaluated) {  // bracket narrower than tol: N and DOS at its midpoint
+    for (int o = b * FC + threadIdx.x; o < M; o += stride) {
+      const double bi = b_inf[o];
+      const double xr = (ef - a_inf[o]) / (2.0 * bi);
+      double Nv, dN;
+      count_and_dos(gsig, inv, M, o, ne, clamp1(xr), &Nv, &dN);
+      Nout[o] = Nv;
+      dos[o] = (xr > -1.0 && xr < 1.0) ? dN / (2.0 * bi) : 0.0;
+    }
+  }
+}
+
 __global__ void k_inverse_table(double* inv, int n) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) inv[k] = k == 0 ? 0.0 : 1.0 / (double)k;
@@ -395,6 +518,33 @@ int launch_fermi_more(int M, const double* gsig, const double* inv, const double
     k_fermi_newton<<<g, RT2, 0, s>>>(M, gsig, inv, a_inf, b_inf, n_exp, spin_factor, target, st, partials, counter,
                                      max_rounds, tol);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int fermi_coop_grid() {
+  static int g = 0;
+  if (g == 0) {
+    int dev = 0, sms = 0, per = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fermi_coop, FC, 0);
+    g = coop && per > 0 ? sms * (per < 4 ? per : 4) : -1;
+  }
+  return g;
+}
+
+int launch_fermi_coop(int M, const double* gsig, const double* inv, const double* a_inf, const double* b_inf,
+                      int n_exp, double spin_factor, double target, FermiState* st, double* partials, int warm,
+                      int max_rounds, double tol, double* N, double* dos, cudaStream_t s) {
+  const int gmax = fermi_coop_grid();
+  if (gmax <= 0) return -2;
+  int g = (M + FC - 1) / FC;
+  if (g > gmax) g = gmax;
+  if (g < 1) g = 1;
+  void* args[] = {&M, &gsig, &inv, &a_inf, &b_inf, &n_exp, &spin_factor, &target, &st, &partials, &warm,
+                  &max_rounds, &tol, &N, &dos};
+  if (cudaLaunchCooperativeKernel((const void*)k_fermi_coop, g, FC, args, 0, s) != cudaSuccess) return -1;
+  return 0;
 }
 
 int launch_orbital_N(int M, int n_exp, const double* gsig, const double* inv, const double* a_inf,

@@ -147,6 +147,12 @@ int launch_fermi_more(int M, const double* gsig, const double* inv, const double
                       int n_exp, double spin_factor, double target, FermiState* st, double* partials,
                       unsigned* counter, int rounds, int max_rounds, double tol, cudaStream_t s);
 void launch_inverse_table(double* inv, int n, cudaStream_t s);
+// The whole Fermi solve (bracket, Newton rounds, N and DOS at E_F) in one
+// cooperative launch; partials: >= 4 x (grid) doubles.  -2: cooperative
+// launch unavailable.
+int launch_fermi_coop(int M, const double* gsig, const double* inv, const double* a_inf, const double* b_inf,
+                      int n_exp, double spin_factor, double target, FermiState* st, double* partials, int warm,
+                      int max_rounds, double tol, double* N, double* dos, cudaStream_t s);
 
 struct ScfArgs {
   int n, norb, n_spin, mode;  // mode 1 = LCN, 2 = Stoner
