@@ -631,8 +631,8 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
             for (int b = 0; b < NO; b++)
 #pragma unroll
               for (int g = b; g < NO; g++) {
-                const double v = (double)G[b][g] + (b != g ? (double)G[g][b] : 0.0);
-                atomicAdd(hbp + U5(b, g), v);
+                const T v = G[b][g] + (b != g ? G[g][b] : T(0));  // sum in T, one conversion
+                atomicAdd(hbp + U5(b, g), (double)v);
               }
           }
         }

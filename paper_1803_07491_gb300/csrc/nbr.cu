@@ -77,21 +77,29 @@ __device__ __forceinline__ uint64_t nbr_key(int j, int sx, int sy, int sz) {
          (uint64_t)(sz + 128);
 }
 
-// One thread per atom.  mode 0: count neighbours; mode 1: write the sorted row.
+// One warp per atom.  The lanes test the atoms of each candidate cell
+// (32 at a time); hits go to a per-warp list in shared memory in ballot
+// order.  mode 0: count neighbours; mode 1: every entry's rank among the
+// keys (j, sx, sy, sz) gives its slot in the sorted row.
+constexpr int NBR_WARPS = 4;
+
 template <int MODE>
-__global__ void k_neighbors(int n, const double* __restrict__ pos, Geometry g, const int* __restrict__ cell_of,
-                            const int* __restrict__ cell_start, const int* __restrict__ cell_atoms,
-                            int* __restrict__ deg, const long long* __restrict__ row_ptr, int* __restrict__ col,
-                            signed char* __restrict__ img, unsigned* __restrict__ status) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__global__ void __launch_bounds__(32 * NBR_WARPS)
+k_neighbors(int n, const double* __restrict__ pos, Geometry g, const int* __restrict__ cell_of,
+            const int* __restrict__ cell_start, const int* __restrict__ cell_atoms, int* __restrict__ deg,
+            const long long* __restrict__ row_ptr, int* __restrict__ col, signed char* __restrict__ img,
+            unsigned* __restrict__ status) {
+  __shared__ uint64_t skeys[NBR_WARPS][BOP_MAX_DEG];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int i = blockIdx.x * NBR_WARPS + wib;
+  if (i >= n) return;  // whole warp
   const double rc2 = g.rc * g.rc;
-  double pi[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-  int ci = cell_of[i];
-  int c3[3] = {ci / (g.nc[1] * g.nc[2]), (ci / g.nc[2]) % g.nc[1], ci % g.nc[2]};
-  uint64_t keys[BOP_MAX_DEG];
+  const double pi[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+  const int ci = cell_of[i];
+  const int c3[3] = {ci / (g.nc[1] * g.nc[2]), (ci / g.nc[2]) % g.nc[1], ci % g.nc[2]};
+  const unsigned lt_mask = (1u << lane) - 1u;
   int cnt = 0;
-  int n0 = axis_count(g, 0), n1 = axis_count(g, 1), n2 = axis_count(g, 2);
+  const int n0 = axis_count(g, 0), n1 = axis_count(g, 1), n2 = axis_count(g, 2);
   for (int q0 = 0; q0 < n0; q0++) {
     if (!axis_valid(g, 0, c3[0], q0)) continue;
     for (int q1 = 0; q1 < n1; q1++) {
@@ -103,41 +111,50 @@ __global__ void k_neighbors(int n, const double* __restrict__ pos, Geometry g, c
         it.get(g, 0, c3[0], q0, &cx, &sx);
         it.get(g, 1, c3[1], q1, &cy, &sy);
         it.get(g, 2, c3[2], q2, &cz, &sz);
-        int cc = (cx * g.nc[1] + cy) * g.nc[2] + cz;
-        for (int p = cell_start[cc]; p < cell_start[cc + 1]; p++) {
-          int j = cell_atoms[p];
-          if (j == i && sx == 0 && sy == 0 && sz == 0) continue;
-          double d[3];
-          bond_vector(pi, pos + 3 * j, g.cell, sx, sy, sz, d);
-          if (!(norm2_rn(d) < rc2)) continue;
-          if (cnt < BOP_MAX_DEG) keys[cnt] = nbr_key(j, sx, sy, sz);
-          cnt++;
+        const int cc = (cx * g.nc[1] + cy) * g.nc[2] + cz;
+        const int p0 = cell_start[cc], p1 = cell_start[cc + 1];
+        for (int base = p0; base < p1; base += 32) {
+          const int p = base + lane;
+          bool hit = false;
+          uint64_t key = 0;
+          if (p < p1) {
+            const int j = cell_atoms[p];
+            if (!(j == i && sx == 0 && sy == 0 && sz == 0)) {
+              double d[3];
+              bond_vector(pi, pos + 3 * j, g.cell, sx, sy, sz, d);
+              hit = norm2_rn(d) < rc2;
+              key = nbr_key(j, sx, sy, sz);
+            }
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, hit);
+          if (hit) {
+            const int slot = cnt + __popc(bal & lt_mask);
+            if (slot < BOP_MAX_DEG) skeys[wib][slot] = key;
+          }
+          cnt += __popc(bal);
         }
       }
     }
   }
   if (MODE == 0) {
-    deg[i] = cnt;
-    if (cnt > BOP_MAX_DEG) raise_error(status, BOP_DEV_ERR_DEGREE);
+    if (lane == 0) {
+      deg[i] = cnt;
+      if (cnt > BOP_MAX_DEG) raise_error(status, BOP_DEV_ERR_DEGREE);
+    }
     return;
   }
   if (cnt > BOP_MAX_DEG) return;
-  for (int a = 1; a < cnt; a++) {  // insertion sort of the row
-    uint64_t k = keys[a];
-    int b = a - 1;
-    while (b >= 0 && keys[b] > k) {
-      keys[b + 1] = keys[b];
-      b--;
-    }
-    keys[b + 1] = k;
-  }
-  long long e0 = row_ptr[i];
-  for (int a = 0; a < cnt; a++) {
-    uint64_t k = keys[a];
-    col[e0 + a] = (int)(k >> 24);
-    img[3 * (e0 + a)] = (signed char)((int)((k >> 16) & 0xff) - 128);
-    img[3 * (e0 + a) + 1] = (signed char)((int)((k >> 8) & 0xff) - 128);
-    img[3 * (e0 + a) + 2] = (signed char)((int)(k & 0xff) - 128);
+  __syncwarp();
+  const long long e0 = row_ptr[i];
+  for (int a = lane; a < cnt; a += 32) {
+    const uint64_t k = skeys[wib][a];
+    int rank = 0;
+    for (int b = 0; b < cnt; b++) rank += skeys[wib][b] < k ? 1 : 0;
+    const long long e = e0 + rank;
+    col[e] = (int)(k >> 24);
+    img[3 * e] = (signed char)((int)((k >> 16) & 0xff) - 128);
+    img[3 * e + 1] = (signed char)((int)((k >> 8) & 0xff) - 128);
+    img[3 * e + 2] = (signed char)((int)(k & 0xff) - 128);
   }
 }
 
@@ -259,7 +276,7 @@ __global__ void k_frac_range(int n, const double* __restrict__ pos, Geometry g, 
 void launch_neighbors(int mode, int n, const double* pos, Geometry g, const int* cell_of, const int* cell_start,
                       const int* cell_atoms, int* deg, const long long* row_ptr, int* col, signed char* img,
                       unsigned* status, cudaStream_t s) {
-  const int TB = 256, gb = (n + TB - 1) / TB;
+  const int TB = 32 * bopk::NBR_WARPS, gb = (n + bopk::NBR_WARPS - 1) / bopk::NBR_WARPS;
   if (mode == 0)
     bopk::k_neighbors<0><<<gb, TB, 0, s>>>(n, pos, g, cell_of, cell_start, cell_atoms, deg, row_ptr, col, img,
                                            status);

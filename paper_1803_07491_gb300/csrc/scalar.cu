@@ -225,10 +225,21 @@ __global__ void __launch_bounds__(RT) k_scf_residual(ScfArgs A) {
   }
   __syncthreads();
   if (!last) return;
-  __shared__ double fr[RT / 32 + 1];
-  double tot[NPAR];
-  for (int q = 0; q < nv; q++) tot[q] = final_reduce<RT>(A.red, NPAR, q, gridDim.x, q < 2, fr);
+  // one thread per reduced quantity, blocks in ascending order (fixed order)
+  __shared__ double tot_s[NPAR];
+  if (threadIdx.x < nv) {
+    const int q = threadIdx.x;
+    double v = 0.0;
+    for (int b = 0; b < (int)gridDim.x; b++) {
+      const double x = __ldcg(A.red + (size_t)NPAR * b + q);
+      v = q < 2 ? fmax(v, x) : v + x;
+    }
+    tot_s[q] = v;
+  }
+  __syncthreads();
   if (threadIdx.x != 0) return;
+  double tot[NPAR];
+  for (int q = 0; q < nv; q++) tot[q] = tot_s[q];
   const bool conv = tot[0] < A.tol && (A.mode != 2 || tot[1] < 10.0 * A.tol);
   A.result[0] = tot[0];
   A.result[1] = tot[1];
