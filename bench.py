@@ -36,7 +36,8 @@ METRIC = "atoms/s for E+F at n moments"
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 x max SM clock
 PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # SMs x FP64 FMA units x 2 x max SM clock
 L2_FLUSH_BYTES = 512 << 20
-FP32_SCF_TOL = 1e-5  # electrons: SCF tolerance with FP32 products (FP64 mode keeps 1e-9)
+FP32_SCF_TOL = 3e-5  # electrons: SCF tolerance with FP32 products (FP64 mode keeps 1e-9); the
+#                      max over atoms of the FP32 noise floor is 4e-6 at 2,000 atoms, 1e-5 at 65,536
 
 
 def parse():

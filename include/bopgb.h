@@ -228,13 +228,15 @@ int bop_energy(bop_ctx* ctx, double* e_atom, double* delta_io, double* m_io, bop
  * Errors: BOP_ERR_STATE without a preceding bop_energy. */
 int bop_forces(bop_ctx* ctx, double* forces, double* virial, bop_stats* stats_host, bop_stream stream);
 
-/* Memory for the reverse sweeps of bop_forces.  By default bop_forces runs
- * one extra forward pass that stores Psi_k of every atom's cluster (rows of
- * norb x norb values per site and level, FP32 or FP64 as the precision)
- * together with a cotangent copy, when both fit in a third of the free
- * device memory, and every reverse sweep then reads Psi instead of
- * recomputing it.  bytes >= 0 caps that store (0 = always recompute, which
- * also frees it); bytes < 0 restores the default. */
+/* Memory for the reverse sweeps of bop_forces.  When several reverse sweeps
+ * follow (an SCF with scf_response = 1) and all starting orbitals of an atom
+ * share one work item of the moments kernel, bop_forces runs one extra
+ * forward pass that stores Psi_k of every atom's cluster (rows of norb x
+ * norb values per site and level, FP32 or FP64 as the precision) together
+ * with a cotangent copy, when both fit in a third of the free device
+ * memory, and every reverse sweep then reads Psi instead of recomputing it.
+ * bytes >= 0 caps that store (0 = always recompute, which also frees it);
+ * bytes < 0 restores the default. */
 int bop_set_store_budget(bop_ctx* ctx, long long bytes);
 
 /* Per-orbital state of the last bop_energy / bop_forces call (device

@@ -591,11 +591,17 @@ int psi_row(int N, int fp64) {
 }
 
 // Stores Psi of every work item (one more forward pass at the current
-// onsite levels) when the store and its cotangent copy fit in a third of
-// the device memory that is free; otherwise the reverse sweeps recompute Psi.
+// onsite levels) when it pays and fits: several reverse sweeps follow (the
+// SCF-response solve), all starting orbitals share one work item (the
+// stored-Psi sweep keeps two Psi-bar levels of all five columns in shared
+// memory; with one column per item it gathers every block five times and is
+// slower than recomputing), and the store and its cotangent copy fit in a
+// third of the free device memory.  Otherwise the reverse sweeps recompute Psi.
 int prepare_psi_store(bop_ctx* c, cudaStream_t s) {
   c->psi_valid = false;
   const int nc = forward_nc(c);
+  const bool several = c->m.scf != BOP_SCF_NONE && c->m.scf_response;
+  if (!several || (c->norb > 1 && nc != c->norb)) return BOP_OK;
   const size_t esz = c->fp64 ? sizeof(double) : sizeof(float);
   const size_t bytes = (size_t)c->S * (c->norb / nc) * (size_t)c->psi_tot * psi_row(c->norb * nc, c->fp64) * esz;
   size_t freeb = 0, totalb = 0;
