@@ -232,6 +232,37 @@ __device__ __forceinline__ void gather_pf(const int2* __restrict__ adj, long lon
   }
 }
 
+// acc += sum over cnt adjacency entries of B_ts x[s], with the blocks of
+// the next two entries in flight while the current one is applied.
+template <typename T, int NO, int NC, int PS>
+__device__ __forceinline__ void gather_pf2(const int2* __restrict__ ent, int cnt, const T* __restrict__ H, int HS,
+                                           const T* __restrict__ x, T acc[NO][NC]) {
+  constexpr int HB = NO == 1 ? 1 : 16;
+  constexpr int N = NO * NC;
+  if (cnt <= 0) return;
+  int2 e0 = ent[0];
+  int2 e1 = cnt > 1 ? ent[1] : e0;
+  T h0[HB], h1[HB];
+  load_bond<T, NO>(H + (size_t)e0.y * HS, h0);
+  if (cnt > 1) load_bond<T, NO>(H + (size_t)e1.y * HS, h1);
+  for (int e = 0; e < cnt; e++) {
+    const int s = e0.x;
+    T hc[HB];
+#pragma unroll
+    for (int q = 0; q < HB; q++) hc[q] = h0[q];
+    e0 = e1;
+#pragma unroll
+    for (int q = 0; q < HB; q++) h0[q] = h1[q];
+    if (e + 2 < cnt) {
+      e1 = ent[e + 2];
+      load_bond<T, NO>(H + (size_t)e1.y * HS, h1);
+    }
+    T xs[N];
+    load_row<T, N, PS>(x + (size_t)s * PS, xs);
+    block_fma<T, NO, NC>(hc, xs, acc);
+  }
+}
+
 // Forward kernel.  A persistent CTA takes a run of consecutive work items
 // (spin, atom[, alpha]); neighbouring atoms share most of their clusters'
 // blocks, which then come from L1.  For each item the atom's adjacency,
@@ -318,8 +349,8 @@ k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
       for (int t = tid; t < nrow; t += FWD_THREADS) {
         T acc[NO][NC];
         const bool in_prev = t < ncol;
-        T pt[N];
         if (in_prev) {
+          T pt[N];
           load_row<T, N, PS>(prev + (size_t)t * PS, pt);
           const T* e = E + (size_t)(L.stage ? s_atom[t] : satom[t]) * NO;
 #pragma unroll
@@ -338,25 +369,11 @@ k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
         const int cnt = (int)((lc >> (8 * (k - 1))) & 0xff);
         if (cnt > 0) {
           const int q0 = L.stage ? s_aoff[t] : (int)(cv.adj_off[s0 + t] - abase);
-          const int2* ent = L.stage ? s_adj + q0 : adj + q0;
-          int2 en = ent[0];
-          T hb[HB];
-          load_bond<T, NO>(H + (size_t)en.y * HS, hb);
-          for (int e = 0; e < cnt; e++) {
-            const int s = en.x;
-            T hc[HB];
-#pragma unroll
-            for (int q = 0; q < HB; q++) hc[q] = hb[q];
-            if (e + 1 < cnt) {
-              en = ent[e + 1];
-              load_bond<T, NO>(H + (size_t)en.y * HS, hb);
-            }
-            T xs[N];
-            load_row<T, N, PS>(prev + (size_t)s * PS, xs);
-            block_fma<T, NO, NC>(hc, xs, acc);
-          }
+          gather_pf2<T, NO, NC, PS>(L.stage ? s_adj + q0 : adj + q0, cnt, H, HS, prev, acc);
         }
-        if (in_prev) {
+        if (in_prev) {  // row t of Psi_k-1 again (shared memory), rather than kept live over the gather
+          T pt[N];
+          load_row<T, N, PS>(prev + (size_t)t * PS, pt);
 #pragma unroll
           for (int r = 0; r < NO; r++)
 #pragma unroll
