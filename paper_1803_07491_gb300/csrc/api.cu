@@ -688,7 +688,7 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
   const bool stoner = c->m.scf == BOP_SCF_STONER;
   const int nu = stoner ? 2 * n : n;
   const double I = c->m.stoner_I;
-  const double rtol = c->fp64 ? 1e-10 : 1e-5;
+  const double rtol = c->fp64 ? 1e-10 : 1e-4;  // FP32 products: at the SCF tolerance's level
   CKS(ensure(c, c->rwN, sizeof(double) * (size_t)M * nm));
   CKS(ensure(c, c->rwt, sizeof(double) * (size_t)M * nm));
   CKS(ensure(c, c->rdUE, sizeof(double) * (size_t)M));
