@@ -110,6 +110,15 @@ class Workload:
         return len(self.pos)
 
 
+A_FCC = 3.51  # Angstrom: nearest-neighbour distance 2.482 A, the canonical model's r0
+
+
+def fcc_jittered(n1, n2, n3, sigma, seed, a=A_FCC, pbc=(1, 1, 1)):
+    pos, cell = fcc_cell(n1, n2, n3, a)
+    rng = np.random.default_rng(seed)
+    return jittered(pos, cell, pbc, sigma, rng), cell
+
+
 def bcc_jittered(n1, n2, n3, sigma, seed, pbc=(1, 1, 1)):
     pos, cell = bcc_cell(n1, n2, n3)
     rng = np.random.default_rng(seed)
@@ -149,6 +158,9 @@ def workload(name: str) -> Workload:
               two spin channels, Stoner I = 0.8 eV from a ferromagnetic start;
               9 moments.
     mag2000   its 2,000-atom (10x10x10x2) counterpart, seed 4.
+    fcc2048   2,048-atom fcc (8x8x8x4, a = 3.51 A: 12 + 6 neighbours within
+              3.6 A), jitter 0.05 A, seed 6; canonical d; N_d = 6.8; local
+              charge neutrality; 9 moments.
     learned131k 131,072-atom bcc (32x32x64x2), jitter 0.05 A, seed 5;
               canonical d; 9 moments; no SCF (evaluation cell of the
               learned terminator).
@@ -168,6 +180,9 @@ def workload(name: str) -> Workload:
         pos, cell = bcc_jittered(n, n, n, 0.05, 4)
         return Workload(name, pos, cell, (1, 1, 1), MODEL_D,
                         RunParams(n_e=6.8, n_spin=2, scf="stoner", stoner_I=0.8))
+    if name == "fcc2048":
+        pos, cell = fcc_jittered(8, 8, 8, 0.05, 6)
+        return Workload(name, pos, cell, (1, 1, 1), MODEL_D, RunParams(n_e=6.8, scf="lcn"))
     if name == "learned131k":
         pos, cell = bcc_jittered(32, 32, 64, 0.05, 5)
         return Workload(name, pos, cell, (1, 1, 1), MODEL_D, RunParams(n_e=6.8))

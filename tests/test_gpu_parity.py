@@ -31,6 +31,8 @@ def tiny_cells():
            I.workload("s128")]
     pos, cell, pbc = I.slab_with_vacancies(3, 3, 4, 3, 0.08, 103)
     out.append(I.Workload("slab", pos, cell, pbc, I.MODEL_D, I.RunParams(n_e=6.8)))
+    pos, cell = I.fcc_jittered(2, 2, 2, 0.06, 104)
+    out.append(I.Workload("fcc", pos, cell, (1, 1, 1), I.MODEL_D, I.RunParams(n_e=6.8)))
     return out
 
 
@@ -38,7 +40,7 @@ def oracle_nbr(ob, w):
     return ob.neighbors(w.pos, w.cell, w.pbc, w.model.rc)
 
 
-@pytest.mark.parametrize("k", range(4))
+@pytest.mark.parametrize("k", range(5))
 def test_neighbor_list_bit_exact(bop, ob, k):
     w = tiny_cells()[k]
     ctx = bop.Context(w.model, w.run)
@@ -50,7 +52,7 @@ def test_neighbor_list_bit_exact(bop, ob, k):
     assert np.array_equal(img.cpu().numpy(), ref.img)
 
 
-@pytest.mark.parametrize("k", range(4))
+@pytest.mark.parametrize("k", range(5))
 def test_clusters_bit_exact(bop, ob, k):
     w = tiny_cells()[k]
     ctx = bop.Context(w.model, w.run)
@@ -89,7 +91,7 @@ def moment_case(ob, w, seed=0):
     return nbr, H, on
 
 
-@pytest.mark.parametrize("k", range(4))
+@pytest.mark.parametrize("k", range(5))
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_moments(bop, ob, k, prec):
     w = tiny_cells()[k]
@@ -128,7 +130,7 @@ def run_both(bop, ob, w, prec="fp64", forces=True):
     return ctx, res, ref
 
 
-@pytest.mark.parametrize("k", range(4))
+@pytest.mark.parametrize("k", range(5))
 def test_energy_and_forces_fp64(bop, ob, k):
     w = tiny_cells()[k]
     ctx, res, ref = run_both(bop, ob, w)

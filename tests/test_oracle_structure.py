@@ -61,10 +61,13 @@ def test_neighbors_slab_and_symmetry(ob):
     assert fwd == numpy_pairs(pos, cell, pbc, 3.6)
 
 
-def lattice_bfs_sizes(K):
-    """Hop-level sizes on the infinite bcc lattice with 1st+2nd shell bonds,
-    in integer coordinates (units of a/2)."""
-    vecs = [v for v in itertools.product((-1, 1), repeat=3)]
+def lattice_bfs_sizes(K, lattice="bcc"):
+    """Hop-level sizes on the infinite bcc / fcc lattice with 1st+2nd shell
+    bonds, in integer coordinates (units of a/2)."""
+    if lattice == "bcc":
+        vecs = [v for v in itertools.product((-1, 1), repeat=3)]
+    else:  # fcc: 12 first neighbours (a/2)(+-1, +-1, 0) and permutations
+        vecs = [v for v in itertools.product((-1, 0, 1), repeat=3) if sum(abs(c) for c in v) == 2]
     vecs += [(2, 0, 0), (-2, 0, 0), (0, 2, 0), (0, -2, 0), (0, 0, 2), (0, 0, -2)]
     seen = {(0, 0, 0)}
     front = [(0, 0, 0)]
@@ -90,6 +93,17 @@ def test_cluster_levels_perfect_bcc(ob, K):
     assert list(lev) == lattice_bfs_sizes(K)
     if K == 6:
         assert list(lev) == [1, 15, 65, 175, 369, 671, 1105]
+
+
+@pytest.mark.parametrize("K", [4, 5])
+def test_cluster_levels_perfect_fcc(ob, K):
+    """fcc with 1st (12) + 2nd (6) shells within 3.6 A: the same hop-level
+    sizes as a breadth-first search on the integer lattice."""
+    pos, cell = I.fcc_cell(4, 4, 4, I.A_FCC)
+    nbr = ob.neighbors(pos, cell, (1, 1, 1), 3.6)
+    assert np.all(np.diff(nbr.row_ptr) == 18)
+    _, _, lev = ob.cluster(9, K, nbr)
+    assert list(lev) == lattice_bfs_sizes(K, "fcc")
 
 
 def test_cluster_is_bfs_in_canonical_order(ob):
