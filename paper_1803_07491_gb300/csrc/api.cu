@@ -705,8 +705,31 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
   double* wN = P<double>(c->rwN);
   double* Eb = P<double>(c->Ebar);
   // weights of U (fixed E_F, no multiplier) and of N
-  CKS(compute_weights(c, c->sfac, nullptr, 0.0, wU, P<double>(c->rdUE), s));
-  CKS(compute_weights(c, 0.0, nullptr, 1.0, wN, nullptr, s));
+  if (c->m.terminator == BOP_TERM_MLP) {
+    CKS(compute_weights(c, c->sfac, nullptr, 0.0, wU, P<double>(c->rdUE), s));
+    CKS(compute_weights(c, 0.0, nullptr, 1.0, wN, nullptr, s));
+  } else {  // both from one forward pass of the chain
+    CKS(ensure(c, c->zscr, sizeof(double) * (size_t)M * (c->n_exp + 1) * 3));
+    WeightArgs wa;
+    wa.M = M;
+    wa.n_mom = c->n_mom;
+    wa.n_exp = c->n_exp;
+    wa.norb = c->norb;
+    wa.mu = P<double>(c->mu);
+    wa.onsite = P<double>(c->onsite);
+    wa.st = P<FermiState>(c->fstate);
+    wa.g = P<double>(c->gjack);
+    wa.inv = P<double>(c->ginv);
+    wa.cU = 0.0;
+    wa.lam = nullptr;
+    wa.cN0 = 0.0;
+    wa.w = wU;
+    wa.dU_dE = P<double>(c->rdUE);
+    wa.zscratch = P<double>(c->zscr);
+    wa.status = P<unsigned>(c->status);
+    Region R(c, PK_WEIGHTS, 1, s);
+    if (launch_weights_pair(wa, c->sfac, 0.0, 0.0, 1.0, wN, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
+  }
   // right-hand side g = dE/du
   CK(cudaMemsetAsync(Eb, 0, sizeof(double) * M, s));
   CKS(adjoint_pass(c, wU, nullptr, Eb, s));

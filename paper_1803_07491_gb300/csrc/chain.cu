@@ -456,6 +456,51 @@ __global__ void __launch_bounds__(CT) k_weights(WeightArgs A) {
   if (bad) raise_error(A.status, BOP_DEV_ERR_NONFINITE);
 }
 
+// Two weight sets at once, w1 for (cU1, cN1) and w2 for (cU2, cN2), both
+// at fixed E_F (no E_F multiplier): the SCF-response solve needs dU/dmu and
+// dN/dmu.  The forward part of the chain runs once.  zscratch holds sigma_m
+// and the two cotangents ([3][n_exp+1][M]).
+template <int KP>
+__global__ void __launch_bounds__(CT) k_weights_pair(WeightArgs A, double cU1, double cN1, double cU2, double cN2,
+                                                     double* __restrict__ w2) {
+  const int o = blockIdx.x * CT + threadIdx.x;
+  if (o >= A.M) return;
+  const int M = A.M, nm = 2 * KP + 1;
+  double mu[BOP_MAX_NMOM];
+  for (int n = 0; n < nm; n++) mu[n] = A.mu[(size_t)o * nm + n];
+  Rec r;
+  RecTape<KP> tp;
+  recursion_taped<KP>(mu, r, tp);
+  const Term t = gershgorin(r);
+  Chain ch;
+  chain_params(r, t, KP, ch);
+  double abar[2][KPMAX + 1], bbar[2][KPMAX + 2];
+  for (int q = 0; q < 2; q++) {
+    for (int k = 0; k <= KPMAX; k++) abar[q][k] = 0.0;
+    for (int k = 0; k <= KPMAX + 1; k++) bbar[q][k] = 0.0;
+  }
+  double abar_inf[2] = {0.0, 0.0}, bbar_inf[2] = {0.0, 0.0}, dE[2];
+  const double cU[2] = {cU1, cU2}, cN[2] = {cN1, cN2};
+  const size_t zl = (size_t)(A.n_exp + 1) * M;
+  double* zb[2] = {A.zscratch + zl, A.zscratch + 2 * zl};
+  chain_reverse_ns<KP, 2>(ch, r.nlev, KP, t.a_inf, t.b_inf, A.onsite[o], A.st->ef, A.g, A.inv, A.n_exp, M, o, cU,
+                          cN, A.zscratch, zb, abar, bbar, abar_inf, bbar_inf, dE);
+  if (A.dU_dE) A.dU_dE[o] = dE[0];
+  bool bad = false;
+  for (int q = 0; q < 2; q++) {
+    gershgorin_reverse(t, abar_inf[q], bbar_inf[q], abar[q], bbar[q]);
+    double mub[BOP_MAX_NMOM];
+    for (int n = 0; n < nm; n++) mub[n] = 0.0;
+    recursion_reverse<KP>(mu, r, tp, abar[q], bbar[q], mub);
+    double* w = q == 0 ? A.w : w2;
+    for (int n = 0; n < nm; n++) {
+      w[(size_t)o * nm + n] = mub[n];
+      bad |= !isfinite(mub[n]);
+    }
+  }
+  if (bad) raise_error(A.status, BOP_DEV_ERR_NONFINITE);
+}
+
 int red_grid2(int M) {
   int g = (M + RT2 - 1) / RT2;
   return g < 1 ? 1 : (g > 4096 ? 4096 : g);  // the context's partials hold 2 x 4096 values
@@ -494,6 +539,23 @@ int launch_weights(const WeightArgs& a, cudaStream_t s) {
     case 6: k_weights<6><<<g, CT, 0, s>>>(a); break;
     case 7: k_weights<7><<<g, CT, 0, s>>>(a); break;
     case 8: k_weights<8><<<g, CT, 0, s>>>(a); break;
+    default: return -1;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_weights_pair(const WeightArgs& a, double cU1, double cN1, double cU2, double cN2, double* w2,
+                        cudaStream_t s) {
+  const int g = (a.M + CT - 1) / CT, Kp = (a.n_mom - 1) / 2;
+  switch (Kp) {
+    case 1: k_weights_pair<1><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 2: k_weights_pair<2><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 3: k_weights_pair<3><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 4: k_weights_pair<4><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 5: k_weights_pair<5><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 6: k_weights_pair<6><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 7: k_weights_pair<7><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 8: k_weights_pair<8><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
     default: return -1;
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

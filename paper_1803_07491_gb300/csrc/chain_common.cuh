@@ -120,16 +120,20 @@ __device__ inline void recursion_taped(const double* mu, Rec& r, RecTape<KP>& tp
 
 // ------------------------------------------------------------ reverse of the chain
 // Reverse of chain -> sigma_m -> (N, P) -> L = cU U + cN N for one orbital
-// (fixed E_F and onsite level E), U = b_inf P - (E - a_inf) N.  The chain
-// (ch, L levels, b^_k set for k <= Kb) has terminator (ai, bi).  Adds the
-// cotangents of the raw chain coefficients to abar[k] (k < L) and bbar[k]
-// (1 <= k <= min(Kb, L)) and of the terminator to abar_inf, bbar_inf; returns
-// dL/dE.  zs, zb: sigma_m and its cotangent, [ne+1][M] each.
-template <int KP>
-__device__ inline double chain_reverse(const Chain& ch, int L, int Kb, double ai, double bi, double E, double ef,
-                                       const double* __restrict__ g, const double* __restrict__ inv, int ne,
-                                       int M, int o, double cU, double cN, double* zs, double* zb, double* abar,
-                                       double* bbar, double& abar_inf, double& bbar_inf) {
+// (fixed E_F and onsite level E), U = b_inf P - (E - a_inf) N, for NS seeds
+// (cU[q], cN[q]) at once: the forward part (generating polynomials, sigma_m,
+// the sums N, P) is shared and everything after it is linear in the seed.
+// The chain (ch, L levels, b^_k set for k <= Kb) has terminator (ai, bi).
+// Adds the cotangents of the raw chain coefficients to abar[q][k] (k < L)
+// and bbar[q][k] (1 <= k <= min(Kb, L)) and of the terminator to
+// abar_inf[q], bbar_inf[q]; dE[q] = dL/dE.  zs: sigma_m [ne+1][M]; zb[q]:
+// its cotangent for seed q, [ne+1][M] each.
+template <int KP, int NS>
+__device__ inline void chain_reverse_ns(const Chain& ch, int L, int Kb, double ai, double bi, double E, double ef,
+                                        const double* __restrict__ g, const double* __restrict__ inv, int ne, int M,
+                                        int o, const double* cU, const double* cN, double* zs, double* const* zb,
+                                        double (*abar)[KPMAX + 1], double (*bbar)[KPMAX + 2], double* abar_inf,
+                                        double* bbar_inf, double* dE) {
   constexpr int NP = 2 * KP + 1;
   // ---- generating polynomials D_0 .. D_{L+1}, all kept
   double Dk[KP + 2][NP];
@@ -164,7 +168,12 @@ __device__ inline double chain_reverse(const Chain& ch, int L, int Kb, double ai
   const bool inside = xr > -1.0 && xr < 1.0;
   const double x = clamp1(xr);
   const double phi = acos(x), s1 = sqrt(fmax(0.0, 1.0 - x * x));
-  const double Nbar = cN - cU * (E - ai), Pbar = cU * bi;
+  double Nbar[NS], Pbar[NS];
+#pragma unroll
+  for (int q = 0; q < NS; q++) {
+    Nbar[q] = cN[q] - cU[q] * (E - ai);
+    Pbar[q] = cU[q] * bi;
+  }
   double Nv = 0.0, Pv = 0.0, dN = 0.0, dP = 0.0;
   {
     // sines s_j = sin(j phi) by the recurrence; chi_j = (s~_{j+1} - s~_{j-1})/pi,
@@ -182,7 +191,8 @@ __device__ inline double chain_reverse(const Chain& ch, int L, int Kb, double ai
       Pv += gsm * (c_m2 + c_m);
       dN += gsm * sp1;
       dP += gsm * (sp2 + s0);
-      zb[(size_t)m * M + o] = g[m] * (Nbar * c_m1 + Pbar * (c_m2 + c_m));
+#pragma unroll
+      for (int q = 0; q < NS; q++) zb[q][(size_t)m * M + o] = g[m] * (Nbar[q] * c_m1 + Pbar[q] * (c_m2 + c_m));
       sm1 = s0;
       s0 = sp1;
       sp1 = sp2;
@@ -192,84 +202,113 @@ __device__ inline double chain_reverse(const Chain& ch, int L, int Kb, double ai
     dN *= 2.0 / PI;
     dP *= 2.0 / PI;
   }
-  abar_inf += cU * Nv;
-  bbar_inf += cU * Pv;
-  if (inside) {
-    const double ebar = Nbar * dN + Pbar * dP;
-    abar_inf += -ebar / (2.0 * bi);
-    bbar_inf += -ebar * xr / bi;
+#pragma unroll
+  for (int q = 0; q < NS; q++) {
+    abar_inf[q] += cU[q] * Nv;
+    bbar_inf[q] += cU[q] * Pv;
+    if (inside) {
+      const double ebar = Nbar[q] * dN + Pbar[q] * dP;
+      abar_inf[q] += -ebar / (2.0 * bi);
+      bbar_inf[q] += -ebar * xr / bi;
+    }
+    dE[q] = -cU[q] * Nv;
   }
   // ---- reverse of the recurrence: lambda_m, Pb = dL/d[D_1], Qb = dL/d[D_0]
-  double Pb[NP], Qb[NP];
-  for (int j = 0; j < NP; j++) Pb[j] = Qb[j] = 0.0;
+  double Pb[NS][NP], Qb[NS][NP];
+  for (int q = 0; q < NS; q++)
+    for (int j = 0; j < NP; j++) Pb[q][j] = Qb[q][j] = 0.0;
   {
-    double lf[NP - 1];  // lf[j] = lambda_{m+1+j}
-    double sw[NP - 1];  // sw[j] = sigma_{m-1-j}
+    double lf[NS][NP - 1];  // lf[q][j] = lambda_{m+1+j}
+    double sw[NP - 1];      // sw[j] = sigma_{m-1-j}
     for (int j = 0; j < NP - 1; j++) {
-      lf[j] = 0.0;
+#pragma unroll
+      for (int q = 0; q < NS; q++) lf[q][j] = 0.0;
       const int mm = ne - 1 - j;
       sw[j] = mm >= 0 ? zs[(size_t)mm * M + o] : 0.0;
     }
     for (int m = ne; m >= 0; m--) {
-      double lam = zb[(size_t)m * M + o];
 #pragma unroll
-      for (int j = 1; j < NP; j++) lam -= Dk[0][j] * lf[j - 1];
-      if (m < NP) Pb[m] += lam;
+      for (int q = 0; q < NS; q++) {
+        double lam = zb[q][(size_t)m * M + o];
 #pragma unroll
-      for (int j = 1; j < NP; j++) Qb[j] -= lam * sw[j - 1];
+        for (int j = 1; j < NP; j++) lam -= Dk[0][j] * lf[q][j - 1];
+        if (m < NP) Pb[q][m] += lam;
 #pragma unroll
-      for (int j = NP - 2; j >= 1; j--) lf[j] = lf[j - 1];
-      lf[0] = lam;
+        for (int j = 1; j < NP; j++) Qb[q][j] -= lam * sw[j - 1];
+#pragma unroll
+        for (int j = NP - 2; j >= 1; j--) lf[q][j] = lf[q][j - 1];
+        lf[q][0] = lam;
+      }
 #pragma unroll
       for (int j = 0; j < NP - 2; j++) sw[j] = sw[j + 1];
       const int mm = m - NP;  // sigma_{m-1-(NP-2)} for the next step
       sw[NP - 2] = mm >= 0 ? zs[(size_t)mm * M + o] : 0.0;
     }
   }
-  // ---- reverse of the polynomial recursion -> a^bar, b^bar
-  double ahb[KP + 1], bhb[KP + 2];
-  for (int k = 0; k <= KP; k++) ahb[k] = 0.0;
-  for (int k = 0; k <= KP + 1; k++) bhb[k] = 0.0;
-  {
-    double Db[KP + 2][NP];
-    for (int k = 0; k < KP + 2; k++)
-      for (int j = 0; j < NP; j++) Db[k][j] = 0.0;
-    for (int j = 0; j < NP; j++) {
-      Db[0][j] = Qb[j];
-      Db[1][j] = Pb[j];
-    }
-    for (int k = 0; k < L; k++) {
-      const double a2 = 2.0 * ch.ah[k], bb = 4.0 * ch.bh[k + 1] * ch.bh[k + 1];
-      double ga = 0.0, gb = 0.0;
+  // ---- reverse of the polynomial recursion -> a^bar, b^bar; chain parameters
+  for (int q = 0; q < NS; q++) {
+    double ahb[KP + 1], bhb[KP + 2];
+    for (int k = 0; k <= KP; k++) ahb[k] = 0.0;
+    for (int k = 0; k <= KP + 1; k++) bhb[k] = 0.0;
+    {
+      double Db[KP + 2][NP];
+      for (int k = 0; k < KP + 2; k++)
+        for (int j = 0; j < NP; j++) Db[k][j] = 0.0;
       for (int j = 0; j < NP; j++) {
-        const double gg = Db[k][j];
-        Db[k + 1][j] += gg;
-        if (j >= 1) {
-          Db[k + 1][j - 1] -= a2 * gg;
-          ga -= 2.0 * gg * Dk[k + 1][j - 1];
-        }
-        if (j >= 2) {
-          Db[k + 1][j - 2] += gg;
-          Db[k + 2][j - 2] -= bb * gg;
-          gb -= 8.0 * ch.bh[k + 1] * gg * Dk[k + 2][j - 2];
-        }
+        Db[0][j] = Qb[q][j];
+        Db[1][j] = Pb[q][j];
       }
-      ahb[k] += ga;
-      bhb[k + 1] += gb;
+      for (int k = 0; k < L; k++) {
+        const double a2 = 2.0 * ch.ah[k], bb = 4.0 * ch.bh[k + 1] * ch.bh[k + 1];
+        double ga = 0.0, gb = 0.0;
+        for (int j = 0; j < NP; j++) {
+          const double gg = Db[k][j];
+          Db[k + 1][j] += gg;
+          if (j >= 1) {
+            Db[k + 1][j - 1] -= a2 * gg;
+            ga -= 2.0 * gg * Dk[k + 1][j - 1];
+          }
+          if (j >= 2) {
+            Db[k + 1][j - 2] += gg;
+            Db[k + 2][j - 2] -= bb * gg;
+            gb -= 8.0 * ch.bh[k + 1] * gg * Dk[k + 2][j - 2];
+          }
+        }
+        ahb[k] += ga;
+        bhb[k + 1] += gb;
+      }
     }
-  }
-  // ---- chain parameters a^_k = (a_k - a_inf)/(2 b_inf), b^_k = b_k/(2 b_inf)
-  for (int k = 0; k < L; k++) {
-    abar[k] += ahb[k] / (2.0 * bi);
-    abar_inf += -ahb[k] / (2.0 * bi);
-    bbar_inf += -ahb[k] * ch.ah[k] / bi;
-  }
-  for (int k = 1; k <= Kb; k++)
-    if (k <= L) {
-      bbar[k] += bhb[k] / (2.0 * bi);
-      bbar_inf += -bhb[k] * ch.bh[k] / bi;
+    // chain parameters a^_k = (a_k - a_inf)/(2 b_inf), b^_k = b_k/(2 b_inf)
+    for (int k = 0; k < L; k++) {
+      abar[q][k] += ahb[k] / (2.0 * bi);
+      abar_inf[q] += -ahb[k] / (2.0 * bi);
+      bbar_inf[q] += -ahb[k] * ch.ah[k] / bi;
     }
-  return -cU * Nv;
+    for (int k = 1; k <= Kb; k++)
+      if (k <= L) {
+        bbar[q][k] += bhb[k] / (2.0 * bi);
+        bbar_inf[q] += -bhb[k] * ch.bh[k] / bi;
+      }
+  }
+}
+
+// One seed (cU, cN); returns dL/dE.
+template <int KP>
+__device__ inline double chain_reverse(const Chain& ch, int L, int Kb, double ai, double bi, double E, double ef,
+                                       const double* __restrict__ g, const double* __restrict__ inv, int ne,
+                                       int M, int o, double cU, double cN, double* zs, double* zb, double* abar,
+                                       double* bbar, double& abar_inf, double& bbar_inf) {
+  double* zbs[1] = {zb};
+  double ab[1][KPMAX + 1], bb_[1][KPMAX + 2];
+  for (int k = 0; k <= KPMAX; k++) ab[0][k] = abar[k];
+  for (int k = 0; k <= KPMAX + 1; k++) bb_[0][k] = bbar[k];
+  double ai_[1] = {abar_inf}, bi_[1] = {bbar_inf}, dE[1];
+  chain_reverse_ns<KP, 1>(ch, L, Kb, ai, bi, E, ef, g, inv, ne, M, o, &cU, &cN, zs, zbs, ab, bb_, ai_, bi_, dE);
+  for (int k = 0; k <= KPMAX; k++) abar[k] = ab[0][k];
+  for (int k = 0; k <= KPMAX + 1; k++) bbar[k] = bb_[0][k];
+  abar_inf = ai_[0];
+  bbar_inf = bi_[0];
+  return dE[0];
 }
 
 // Reverse of Gershgorin: a_inf = (top+bot)/2, b_inf = (top-bot)/4 with
