@@ -85,6 +85,18 @@ __device__ __forceinline__ unsigned char* align16(unsigned char* p) {
   return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
 }
 
+// Hint to bring the 128-byte lines of a stored row into L2 before it is read.
+template <typename T, int PS>
+__device__ __forceinline__ void prefetch_row_l2(const T* p) {
+  constexpr int BYTES = PS * (int)sizeof(T);
+#pragma unroll
+  for (int o = 0; o < BYTES; o += 128)
+    asm volatile("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\tprefetch.global.L2 [ga];\n\t}" ::"l"(
+        reinterpret_cast<const char*>(p) + o));
+  asm volatile("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\tprefetch.global.L2 [ga];\n\t}" ::"l"(
+      reinterpret_cast<const char*>(p) + BYTES - 1));
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -532,19 +544,17 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
       T* yb = buf[(k - 1) & 1];
       const int nrow = s_lev[k - 1];
       for (int t = tid; t < nrow; t += FWD_THREADS) {
-        T xt[N], p1[N];
-        load_row<T, N, PS>(xb + (size_t)t * PS, xt);
-        load_row<T, N, PS>(P + (size_t)(s_lo[k - 1] + t) * PS, p1);
-        // onsite cotangent of level k
-#pragma unroll
-        for (int r = 0; r < NO; r++) {
-          T a = T(0);
-#pragma unroll
-          for (int c = 0; c < NC; c++) a += xt[r * NC + c] * p1[r * NC + c];
-          eb[t * NO + r] += a;
-        }
+        // the stored rows this site needs, towards L2 while the gather runs
+        const T* r1 = P + (size_t)(s_lo[k - 1] + t) * PS;
+        prefetch_row_l2<T, PS>(r1);
         if (k >= 2) {
-          T acc[NO][NC];
+          prefetch_row_l2<T, PS>(P + (size_t)(s_lo[k] + t) * PS);
+          if (t < s_lev[k - 2]) prefetch_row_l2<T, PS>(P + (size_t)(s_lo[k - 2] + t) * PS);
+        }
+        T acc[NO][NC];
+        if (k >= 2) {
+          T xt[N];
+          load_row<T, N, PS>(xb + (size_t)t * PS, xt);
           const T* e = E + (size_t)(L.stage ? s_atom[t] : satom[t]) * NO;
 #pragma unroll
           for (int r = 0; r < NO; r++) {
@@ -561,24 +571,24 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
           }
           if (cnt > 0) {
             const int q0 = L.stage ? s_aoff[t] : (int)(cv.adj_off[s0 + t] - abase);
-            const int2* ent = L.stage ? s_adj + q0 : adj + q0;
-            int2 en = ent[0];
-            T hb[HB];
-            load_bond<T, NO>(H + (size_t)en.y * HS, hb);
-            for (int q = 0; q < cnt; q++) {
-              const int sidx = en.x;
-              T hc[HB];
-#pragma unroll
-              for (int z = 0; z < HB; z++) hc[z] = hb[z];
-              if (q + 1 < cnt) {
-                en = ent[q + 1];
-                load_bond<T, NO>(H + (size_t)en.y * HS, hb);
-              }
-              T xs[N];
-              load_row<T, N, PS>(xb + (size_t)sidx * PS, xs);
-              block_fma<T, NO, NC>(hc, xs, acc);
-            }
+            gather_pf2<T, NO, NC, PS>(L.stage ? s_adj + q0 : adj + q0, cnt, H, HS, xb, acc);
           }
+        }
+        // onsite cotangent of level k: Psi-bar_k[t] . Psi_k-1[t] (rows read after the gather)
+        T p1[N];
+        {
+          T xt[N];
+          load_row<T, N, PS>(xb + (size_t)t * PS, xt);
+          load_row<T, N, PS>(r1, p1);
+#pragma unroll
+          for (int r = 0; r < NO; r++) {
+            T a = T(0);
+#pragma unroll
+            for (int c = 0; c < NC; c++) a += xt[r * NC + c] * p1[r * NC + c];
+            eb[t * NO + r] += a;
+          }
+        }
+        if (k >= 2) {
           T pk[N];
           load_row<T, N, PS>(P + (size_t)(s_lo[k] + t) * PS, pk);
           T row[N];
@@ -589,7 +599,7 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
               const int q = r * NC + c;
               row[q] = acc[r][c] + T(2) * ws[c][2 * k - 2] * p1[q] + ws[c][2 * k - 1] * pk[q];
             }
-          if (k >= 2 && t < s_lev[k - 2]) {
+          if (t < s_lev[k - 2]) {
             T p2[N];
             load_row<T, N, PS>(P + (size_t)(s_lo[k - 2] + t) * PS, p2);
 #pragma unroll
