@@ -116,6 +116,7 @@ class Settings:
     terminator: str = "constant"  # constant | mlp (learned continuation, oracle/mlp.py)
     net: object = None            # mlp.Net for terminator = "mlp"
     scf_response: bool = True     # forces include the response of the SCF onsite levels
+    bandwidth: object = None      # Bandwidth (None: Gershgorin)
 
 
 @dataclass
@@ -313,6 +314,90 @@ def gershgorin(a, b, nlev):
     return a_inf, b_inf
 
 
+BANDWIDTH_MODES = ("gershgorin", "lowest", "highest", "average", "average_centre", "minmax", "global",
+                   "weighted")
+
+
+@dataclass
+class Bandwidth:
+    """Choice of the band centre / width estimate ("Band-width estimates"
+    (i)-(v), (vii), (viii)) or of the weighted-average terminator (Eq.
+    weighted, parameter beta).  ga, gb: the global values of (viii)."""
+    mode: str = "gershgorin"
+    beta: float = 1.0
+    ga: float = 0.0
+    gb: float = 1.0
+
+
+def _pick(x, idx):
+    return x[np.arange(x.shape[0]), idx]
+
+
+def band_estimate(a, b, nlev, bw: Bandwidth):
+    """(a_inf, b_inf) = (A, B) for every orbital from its computed levels
+    a_0 .. a_{L-1}, b_1 .. b_L (L = nlev), by the chosen estimate.
+    Readings: (i) "lowest" takes a_0 and b_1 (the lowest computed of each;
+    the printed a^(1) would skip the first computed a); (ii) "highest" takes
+    a_{L-1} and b_L; (iii) "average" averages a_0..a_{L-1} and takes the root
+    mean square of b_1..b_L; (iv) "average_centre" the same centre with b_L;
+    (v) "minmax" (max a + min a)/2 and (max a - min a + 4 max b)/4; (viii)
+    "global" (ga, gb) for every orbital; "weighted" the weighted averages of
+    Eq. weighted with w_m = 1/(beta (m_max - m) + 1), m_max the highest
+    computed index of each sequence (L-1 for a, L for b).  B is floored at
+    B_INF_MIN as for Gershgorin (complex-step safe: max / min by real part)."""
+    if bw.mode == "gershgorin":
+        return gershgorin(a, b, nlev)
+    M, Kp = a.shape
+    L = np.asarray(nlev)
+    dt = np.result_type(a, b)
+    ka = np.arange(Kp)[None, :]
+    kb = np.arange(Kp + 1)[None, :]
+    va = ka < L[:, None]                  # computed a_n
+    vb = (kb >= 1) & (kb <= L[:, None])   # computed b_n
+    zero = np.zeros((), dt)
+    if bw.mode == "lowest":
+        A, B = a[:, 0], b[:, 1]
+    elif bw.mode == "highest":
+        A, B = _pick(a, L - 1), _pick(b, L)
+    elif bw.mode in ("average", "average_centre"):
+        A = np.sum(np.where(va, a, zero), axis=1) / L
+        if bw.mode == "average":
+            B = np.sqrt(np.sum(np.where(vb, b * b, zero), axis=1) / L)
+        else:
+            B = _pick(b, L)
+    elif bw.mode == "minmax":
+        ar = np.real(a)
+        imax = np.argmax(np.where(va, ar, -np.inf), axis=1)
+        imin = np.argmin(np.where(va, ar, np.inf), axis=1)
+        ib = np.argmax(np.where(vb, np.real(b), -np.inf), axis=1)
+        amax, amin, bmax = _pick(a, imax), _pick(a, imin), _pick(b, ib)
+        A = 0.5 * (amax + amin)
+        B = 0.25 * (amax - amin + 4.0 * bmax)
+    elif bw.mode == "global":
+        A = np.full(M, bw.ga, dt)
+        B = np.full(M, bw.gb, dt)
+    elif bw.mode == "weighted":
+        with np.errstate(divide="ignore"):  # levels beyond L are masked out
+            wa = np.where(va, 1.0 / (bw.beta * ((L[:, None] - 1) - ka) + 1.0), 0.0)
+            wb = np.where(vb, 1.0 / (bw.beta * (L[:, None] - kb) + 1.0), 0.0)
+        A = np.sum(wa * a, axis=1) / np.sum(wa, axis=1)
+        B = np.sum(wb * b, axis=1) / np.sum(wb, axis=1)
+    else:
+        raise ValueError(bw.mode)
+    B = np.where(np.real(B) < B_INF_MIN, B_INF_MIN, B)
+    return A, B
+
+
+def outside_band(sigma):
+    """Per orbital: True if some |sigma_m| > m + 1.  sigma_m integrates
+    U_m(x) against a density of unit weight (section "Chebyshev
+    polynomials", Eq. sigma_i), and |U_m| <= m + 1 on [-1, 1], so the
+    density then has weight outside the estimated band and the series grows
+    with m instead of decaying."""
+    m = np.arange(sigma.shape[1])
+    return np.any(np.abs(np.real(sigma)) > (m + 1) * (1.0 + 1e-9), axis=1)
+
+
 def normalised_moments(mu, a_inf, b_inf):
     """mu-hat_n = (2 b_inf)^-n sum_l C(n,l) (-a_inf)^l mu_{n-l}
     (Eq. sigma_i and the normalisation beneath it)."""
@@ -456,11 +541,12 @@ class Expansion:
     gsig: np.ndarray
 
 
-def scalar_stage(mu, n_exp: int) -> Expansion:
-    """Moments -> (a, b) -> Gershgorin (a_inf, b_inf) -> mu-hat -> sigma
-    (Eq. sigma_i below n_mom, the zeta chain above) -> g_m sigma_m."""
+def scalar_stage(mu, n_exp: int, bw: Bandwidth | None = None) -> Expansion:
+    """Moments -> (a, b) -> (a_inf, b_inf) (Gershgorin unless bw says
+    otherwise) -> mu-hat -> sigma (Eq. sigma_i below n_mom, the zeta chain
+    above) -> g_m sigma_m."""
     a, b, nlev = recursion_coefficients(mu)
-    a_inf, b_inf = gershgorin(a, b, nlev)
+    a_inf, b_inf = gershgorin(a, b, nlev) if bw is None else band_estimate(a, b, nlev, bw)
     n_mom = mu.shape[1]
     sig_mom = sigma_from_moments(normalised_moments(mu, a_inf, b_inf))
     sig = zeta_sigma(a, b, nlev, a_inf, b_inf, n_exp)
@@ -557,7 +643,7 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
         assert st.n_mom == 9 and st.net is not None
         stage = lambda m: _mlp.learned_stage(m, st.net, st.n_exp)  # noqa: E731
     else:
-        stage = lambda m: scalar_stage(m, st.n_exp)  # noqa: E731
+        stage = lambda m: scalar_stage(m, st.n_exp, st.bandwidth)  # noqa: E731
     it = 0
     converged = st.scf == "none"
     while True:
@@ -617,7 +703,8 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
                a=ex.a, b=ex.b, a_inf=ex.a_inf, b_inf=ex.b_inf, N=Nsv, delta=delta, m=m,
                scf_iterations=it, scf_converged=converged, bisection_steps=n_bis,
                neighbors=nbr, H=H, onsite=onsite, forces_include_scf_response=st.scf == "none",
-               learned=getattr(ex, "learned", None))
+               learned=getattr(ex, "learned", None),
+               unbounded=outside_band(ex.sigma))
     if want_forces:
         w, dU_dE, dN, _, _, dU = weights(mu_f, onsite.reshape(-1), E_F, st.n_exp, s, stage)
         w = w.reshape(S, n, norb, st.n_mom)

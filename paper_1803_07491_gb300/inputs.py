@@ -93,6 +93,11 @@ class RunParams:
     mix_history: int = 6
     terminator: str = "constant"  # constant | mlp (learned continuation of the chain, n_mom = 9)
     scf_response: bool = True     # with an SCF, forces include the response of the onsite levels
+    bandwidth: str = "gershgorin"  # gershgorin | lowest | highest | average | average_centre | minmax | global
+    #                                | weighted: the band centre / width estimate of the constant terminator
+    bw_beta: float = 1.0          # weighted: w_m = 1/(beta (m_max - m) + 1)
+    bw_a: float = 0.0             # global: A (eV)
+    bw_b: float = 1.0             # global: B (eV)
 
 
 @dataclass

@@ -31,4 +31,6 @@ def oracle_settings(r):
     return bop.Settings(n_e=r.n_e, n_mom=r.n_mom, n_exp=r.n_exp, n_spin=r.n_spin, scf=r.scf,
                         eta=r.eta, scf_tol=r.scf_tol, scf_max_it=r.scf_max_it,
                         stoner_I=r.stoner_I, m_mix=r.m_mix, m0=r.m0, dos_floor=r.dos_floor,
-                        mixer=r.mixer, mix_history=r.mix_history, scf_response=r.scf_response)
+                        mixer=r.mixer, mix_history=r.mix_history, scf_response=r.scf_response,
+                        bandwidth=None if r.bandwidth == "gershgorin" else
+                        bop.Bandwidth(r.bandwidth, r.bw_beta, r.bw_a, r.bw_b))
