@@ -67,6 +67,19 @@ enum { BOP_SCF_NONE = 0, BOP_SCF_LCN = 1, BOP_SCF_STONER = 2 };
 enum { BOP_PREC_FP64 = 0, BOP_PREC_FP32 = 1 };
 enum { BOP_MIX_LINEAR = 0, BOP_MIX_ANDERSON = 1 };
 enum { BOP_TERM_CONSTANT = 0, BOP_TERM_MLP = 1 };
+/* Band centre / width estimate (A, B) of the constant terminator (section
+ * "Band-width estimates"; L = levels computed for the orbital, a_0..a_{L-1},
+ * b_1..b_L): */
+enum {
+  BOP_BW_GERSHGORIN = 0,  /* (vii) Eq. gershogorin band edges (default) */
+  BOP_BW_LOWEST = 1,      /* (i) A = a_0, B = b_1 */
+  BOP_BW_HIGHEST = 2,     /* (ii) A = a_{L-1}, B = b_L */
+  BOP_BW_AVERAGE = 3,     /* (iii) A = mean of a_0..a_{L-1}, B = rms of b_1..b_L */
+  BOP_BW_AVG_CENTRE = 4,  /* (iv) A as (iii), B = b_L */
+  BOP_BW_MINMAX = 5,      /* (v) A = (max a + min a)/2, B = (max a - min a + 4 max b)/4 */
+  BOP_BW_GLOBAL = 6,      /* (viii) A = bw_a, B = bw_b for every orbital */
+  BOP_BW_WEIGHTED = 7     /* Eq. weighted: w_m = 1/(bw_beta (m_max - m) + 1), m_max = L-1 for a, L for b */
+};
 
 /* Model and run settings.
  * beta_x(r) = b0[x] * exp(-lam (r - r0)) * fcut(r), fcut the cosine taper
@@ -93,7 +106,11 @@ enum { BOP_TERM_CONSTANT = 0, BOP_TERM_MLP = 1 };
  * of the self-consistent energy (the onsite shifts, and for STONER the
  * moments, follow the atoms; an adjoint linear solve, see bop_forces);
  * 0 = the derivative at fixed onsite levels (the Hellmann-Feynman form of
- * Eq. F_k, which the paper notes is not exact for a non-variational SCF). */
+ * Eq. F_k, which the paper notes is not exact for a non-variational SCF).
+ * bandwidth: one of BOP_BW_*; B is floored at 1e-3 eV in every mode (no
+ * derivative flows through a floored B).  bw_beta >= 0 (WEIGHTED), bw_a and
+ * bw_b > 0 (GLOBAL, eV); ignored otherwise.  The MLP terminator takes
+ * BOP_BW_GERSHGORIN only. */
 typedef struct {
   int norb;
   double b0[3];
@@ -112,6 +129,9 @@ typedef struct {
   int mix_history;
   int terminator;
   int scf_response;
+  int bandwidth;
+  double bw_beta;
+  double bw_a, bw_b;
 } bop_model;
 
 typedef struct {
@@ -136,6 +156,11 @@ typedef struct {
   int response_iterations;   /* GMRES iterations of the SCF-response solve (last forces) */
   int response_converged;    /* 1 if that solve reached its tolerance */
   double response_residual;  /* its final relative residual */
+  int n_unbounded;           /* orbitals (all spins) of the last energy, constant
+                                terminator, whose expansion has some |sigma_m| > m + 1:
+                                the chain has weight outside [A - 2B, A + 2B] and the
+                                Chebyshev series grows with n_exp (0 for the Gershgorin
+                                and min / max estimates in practice) */
 } bop_stats;
 
 /* Library version (major * 10000 + minor * 100 + patch). */

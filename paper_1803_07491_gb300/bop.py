@@ -21,6 +21,8 @@ SCF = {"none": 0, "lcn": 1, "stoner": 2}
 PREC = {"fp64": 0, "fp32": 1}
 MIXER = {"linear": 0, "anderson": 1}
 TERM = {"constant": 0, "mlp": 1}
+BANDWIDTH = {"gershgorin": 0, "lowest": 1, "highest": 2, "average": 3, "average_centre": 4, "minmax": 5,
+             "global": 6, "weighted": 7}
 MLP_NIN, MLP_NHID, MLP_NOUT, MLP_NPARAM, MLP_NNORM = 18, 128, 10, 20234, 92
 
 
@@ -38,7 +40,9 @@ class bop_model(ctypes.Structure):
                 ("eta", ctypes.c_double), ("scf_tol", ctypes.c_double), ("scf_max_it", ctypes.c_int),
                 ("stoner_I", ctypes.c_double), ("m_mix", ctypes.c_double), ("m0", ctypes.c_double),
                 ("dos_floor", ctypes.c_double), ("precision", ctypes.c_int), ("mixer", ctypes.c_int),
-                ("mix_history", ctypes.c_int), ("terminator", ctypes.c_int), ("scf_response", ctypes.c_int)]
+                ("mix_history", ctypes.c_int), ("terminator", ctypes.c_int), ("scf_response", ctypes.c_int),
+                ("bandwidth", ctypes.c_int), ("bw_beta", ctypes.c_double), ("bw_a", ctypes.c_double),
+                ("bw_b", ctypes.c_double)]
 
 
 class bop_stats(ctypes.Structure):
@@ -49,7 +53,8 @@ class bop_stats(ctypes.Structure):
                 ("e_fermi", ctypes.c_double), ("e_total", ctypes.c_double),
                 ("forces_scf_response", ctypes.c_int), ("n_learned", ctypes.c_int),
                 ("moment_products", ctypes.c_longlong), ("response_iterations", ctypes.c_int),
-                ("response_converged", ctypes.c_int), ("response_residual", ctypes.c_double)]
+                ("response_converged", ctypes.c_int), ("response_residual", ctypes.c_double),
+                ("n_unbounded", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -146,7 +151,7 @@ def make_model(params, run, precision: str = "fp64") -> bop_model:
                      params.onsite0, run.n_mom, run.n_exp, run.n_spin, run.n_e, SCF[run.scf], run.eta,
                      run.scf_tol, run.scf_max_it, run.stoner_I, run.m_mix, run.m0, run.dos_floor,
                      PREC[precision], MIXER[run.mixer], run.mix_history, TERM[run.terminator],
-                     1 if run.scf_response else 0)
+                     1 if run.scf_response else 0, BANDWIDTH[run.bandwidth], run.bw_beta, run.bw_a, run.bw_b)
 
 
 def _check(ctx, st, allow=()):

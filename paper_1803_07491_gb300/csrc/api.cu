@@ -218,7 +218,24 @@ int validate_model(bop_ctx* c, const bop_model* m) {
     return fail(c, BOP_ERR_ARG, "terminator must be CONSTANT or MLP");
   if (m->terminator == BOP_TERM_MLP && m->n_mom != 9) return fail(c, BOP_ERR_ARG, "the MLP terminator needs n_mom = 9");
   if (m->scf_response != 0 && m->scf_response != 1) return fail(c, BOP_ERR_ARG, "scf_response must be 0 or 1");
+  if (m->bandwidth < BOP_BW_GERSHGORIN || m->bandwidth > BOP_BW_WEIGHTED)
+    return fail(c, BOP_ERR_ARG, "bandwidth must be one of BOP_BW_*");
+  if (m->bandwidth == BOP_BW_WEIGHTED && !(m->bw_beta >= 0 && m->bw_beta < 1e300))
+    return fail(c, BOP_ERR_ARG, "bw_beta must be finite and >= 0");
+  if (m->bandwidth == BOP_BW_GLOBAL && !(m->bw_b > 0 && m->bw_b < 1e300 && fabs(m->bw_a) < 1e300))
+    return fail(c, BOP_ERR_ARG, "bw_a must be finite and bw_b finite and > 0");
+  if (m->terminator == BOP_TERM_MLP && m->bandwidth != BOP_BW_GERSHGORIN)
+    return fail(c, BOP_ERR_ARG, "the MLP terminator takes the Gershgorin band width only");
   return BOP_OK;
+}
+
+BandSel band_sel(const bop_model& m) {
+  BandSel b;
+  b.mode = m.bandwidth;
+  b.beta = m.bw_beta;
+  b.ga = m.bw_a;
+  b.gb = m.bw_b;
+  return b;
 }
 
 int geometry(bop_ctx* c, const double* cell, const int* pbc, Geometry* g) {
@@ -449,9 +466,9 @@ int run_learned(bop_ctx* c, int M, const double* mu, cudaStream_t s) {
   CKS(ensure(c, c->lH1, T * m * BOP_MLP_NHID));
   CKS(ensure(c, c->lZ2, T * m * BOP_MLP_NHID));
   CKS(ensure(c, c->lH2, T * m * BOP_MLP_NHID));
-  CKS(ensure(c, c->lcount, sizeof(unsigned)));
+  CKS(ensure(c, c->lcount, 2 * sizeof(unsigned)));
   LearnedArgs L = learned_args(c, M, mu);
-  CK(cudaMemsetAsync(c->lcount.p, 0, sizeof(unsigned), s));
+  CK(cudaMemsetAsync(c->lcount.p, 0, 2 * sizeof(unsigned), s));
   {
     Region R(c, PK_EXPAND, 1, s);
     if (launch_learned(0, L, s)) return fail(c, BOP_ERR_CUDA, "features launch failed");
@@ -482,6 +499,11 @@ int run_scalar(bop_ctx* c, int M, const double* mu, cudaStream_t s) {
   a.gsig = P<double>(c->gsig);
   a.g = P<double>(c->gjack);
   a.status = P<unsigned>(c->status);
+  a.bw = band_sel(c->m);
+  // lcount: [0] learned orbitals, [1] orbitals outside the estimated band
+  CKS(ensure(c, c->lcount, 2 * sizeof(unsigned)));
+  CK(cudaMemsetAsync(c->lcount.p, 0, 2 * sizeof(unsigned), s));
+  a.n_unbounded = P<unsigned>(c->lcount) + 1;
   Region R(c, PK_EXPAND, 1, s);
   if (launch_expand(a, s)) return fail(c, BOP_ERR_CUDA, "expand launch failed");
   return BOP_OK;
@@ -557,6 +579,7 @@ int compute_weights(bop_ctx* c, double cU, const double* lam, double cN0, double
   wa.dU_dE = dUE;
   wa.zscratch = P<double>(c->zscr);
   wa.status = P<unsigned>(c->status);
+  wa.bw = band_sel(c->m);
   if (c->m.terminator == BOP_TERM_MLP) {
     if (!c->net) return fail(c, BOP_ERR_STATE, "terminator MLP needs a network (bop_set_mlp)");
     const size_t T = c->fp64 ? sizeof(double) : sizeof(float);
@@ -727,6 +750,7 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
     wa.dU_dE = P<double>(c->rdUE);
     wa.zscratch = P<double>(c->zscr);
     wa.status = P<unsigned>(c->status);
+  wa.bw = band_sel(c->m);
     Region R(c, PK_WEIGHTS, 1, s);
     if (launch_weights_pair(wa, c->sfac, 0.0, 0.0, 1.0, wN, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
   }
@@ -1127,6 +1151,8 @@ int bop_recursion(bop_ctx* c, int M, const double* mu, double* a, double* b, int
   A.gsig = gsig;
   A.g = P<double>(c->gjack);
   A.status = P<unsigned>(c->status);
+  A.bw = band_sel(c->m);
+  A.n_unbounded = nullptr;
   r = launch_expand(A, s) ? fail(c, BOP_ERR_CUDA, "expand launch failed") : BOP_OK;
   if (r == BOP_OK) r = check_status(c, s);
   cleanup();
@@ -1239,11 +1265,12 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   if (delta_io) CK(cudaMemcpyAsync(delta_io, c->delta.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   if (m_io && stoner) CK(cudaMemcpyAsync(m_io, c->mval.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   double et = 0.0;
-  unsigned nl = 0;
+  unsigned nl[2] = {0, 0};
   CK(cudaMemcpyAsync(&et, c->e_total.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-  if (c->m.terminator == BOP_TERM_MLP) CK(cudaMemcpyAsync(&nl, c->lcount.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(nl, c->lcount.p, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CKS(check_status(c, s));
-  c->st.n_learned = (int)nl;
+  c->st.n_learned = (int)nl[0];
+  c->st.n_unbounded = (int)nl[1];
   c->st.scf_iterations = it;
   c->st.scf_converged = converged;
   c->st.bisection_rounds = fs.iters;

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(CT) k_expand(ScalarArgs A) {
   for (int n = 0; n < nm; n++) mu[n] = A.mu[(size_t)o * nm + n];
   Rec r;
   recursion(mu, KP, r);
-  Term t = gershgorin(r);
+  Term t = bandwidth(r, A.bw);
   Chain ch;
   chain_params(r, t, KP, ch);
   for (int k = 0; k < KP; k++) A.a[(size_t)o * KP + k] = r.a[k];
@@ -51,7 +51,9 @@ __global__ void __launch_bounds__(CT) k_expand(ScalarArgs A) {
   A.b_inf[o] = t.b_inf;
   double Q[NP], P[NP];
   gen_polys<KP>(ch, r.nlev, Q, P);
-  const double last = sigma_series<KP>(Q, P, ne, A.g, A.gsig, M, o);
+  bool outside = false;
+  const double last = sigma_series<KP>(Q, P, ne, A.g, A.gsig, M, o, A.n_unbounded ? &outside : nullptr);
+  if (outside) atomicAdd(A.n_unbounded, 1u);
   if (!isfinite(t.a_inf) || !isfinite(t.b_inf) || !isfinite(last)) raise_error(A.status, BOP_DEV_ERR_NONFINITE);
 }
 
@@ -433,7 +435,7 @@ __global__ void __launch_bounds__(CT) k_weights(WeightArgs A) {
   Rec r;
   RecTape<KP> tp;
   recursion_taped<KP>(mu, r, tp);
-  const Term t = gershgorin(r);
+  const Term t = bandwidth(r, A.bw);
   Chain ch;
   chain_params(r, t, KP, ch);
   double abar[KPMAX + 1], bbar[KPMAX + 2];
@@ -444,7 +446,7 @@ __global__ void __launch_bounds__(CT) k_weights(WeightArgs A) {
                                       M, o, cU, cN, A.zscratch, A.zscratch + (size_t)(A.n_exp + 1) * M, abar, bbar,
                                       abar_inf, bbar_inf);
   if (A.dU_dE) A.dU_dE[o] = dE;
-  gershgorin_reverse(t, abar_inf, bbar_inf, abar, bbar);
+  bandwidth_reverse(r, t, A.bw, abar_inf, bbar_inf, abar, bbar);
   double mub[BOP_MAX_NMOM];
   for (int n = 0; n < nm; n++) mub[n] = 0.0;
   recursion_reverse<KP>(mu, r, tp, abar, bbar, mub);
@@ -471,7 +473,7 @@ __global__ void __launch_bounds__(CT) k_weights_pair(WeightArgs A, double cU1, d
   Rec r;
   RecTape<KP> tp;
   recursion_taped<KP>(mu, r, tp);
-  const Term t = gershgorin(r);
+  const Term t = bandwidth(r, A.bw);
   Chain ch;
   chain_params(r, t, KP, ch);
   double abar[2][KPMAX + 1], bbar[2][KPMAX + 2];
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(CT) k_weights_pair(WeightArgs A, double cU1, d
   if (A.dU_dE) A.dU_dE[o] = dE[0];
   bool bad = false;
   for (int q = 0; q < 2; q++) {
-    gershgorin_reverse(t, abar_inf[q], bbar_inf[q], abar[q], bbar[q]);
+    bandwidth_reverse(r, t, A.bw, abar_inf[q], bbar_inf[q], abar[q], bbar[q]);
     double mub[BOP_MAX_NMOM];
     for (int n = 0; n < nm; n++) mub[n] = 0.0;
     recursion_reverse<KP>(mu, r, tp, abar[q], bbar[q], mub);

@@ -44,9 +44,14 @@ __device__ __forceinline__ void gen_polys(const Chain& ch, int L, double Q[2 * K
 // g_m sigma_m, m = 0..ne, into gsig[m][M] from the recurrence
 // sigma_m = [D_1]_m - sum_{j>=1} [D_0]_j sigma_{m-j}.  Returns sigma_ne.
 template <int KP>
+// With a non-null `outside`, *outside becomes true if some |sigma_m| > m + 1:
+// sigma_m is the integral of U_m(x) times a density of unit weight, and
+// |U_m| <= m + 1 on [-1, 1], so the density then has weight outside the
+// estimated band (a bound state of the terminated chain) and the series
+// grows with m.
 __device__ __forceinline__ double sigma_series(double Q[2 * KP + 1], double P[2 * KP + 1], int ne,
                                                const double* __restrict__ g, double* __restrict__ gsig, int M,
-                                               int o) {
+                                               int o, bool* outside = nullptr) {
   constexpr int NP = 2 * KP + 1;
   double h[NP - 1];  // h[j] = sigma_{m-1-j}
 #pragma unroll
@@ -62,6 +67,7 @@ __device__ __forceinline__ double sigma_series(double Q[2 * KP + 1], double P[2 
     for (int j = NP - 2; j >= 1; j--) h[j] = h[j - 1];
     h[0] = v;
     gsig[(size_t)m * M + o] = g[m] * v;
+    if (outside && fabs(v) > (m + 1) * (1.0 + 1e-9)) *outside = true;
   }
   return h[0];
 }
@@ -324,6 +330,46 @@ __device__ inline void gershgorin_reverse(const Term& t, double abar_inf, double
   abar[t.ilo] += botb;
   bbar[t.ilo] -= botb;
   bbar[t.ilo + 1] -= botb;
+}
+
+// Reverse of bandwidth(): adds the cotangents of a_inf, b_inf onto those of
+// the computed a_n, b_n (nothing through a floored B or the global mode).
+__device__ inline void bandwidth_reverse(const Rec& r, const Term& t, const BandSel& p, double abar_inf,
+                                         double bbar_inf, double* abar, double* bbar) {
+  const int L = r.nlev;
+  const double Bb = t.floored ? 0.0 : bbar_inf;
+  switch (p.mode) {
+    case BOP_BW_GERSHGORIN:
+      gershgorin_reverse(t, abar_inf, bbar_inf, abar, bbar);
+      return;
+    case BOP_BW_LOWEST:
+      abar[0] += abar_inf;
+      bbar[1] += Bb;
+      return;
+    case BOP_BW_HIGHEST:
+      abar[L - 1] += abar_inf;
+      bbar[L] += Bb;
+      return;
+    case BOP_BW_AVERAGE:
+    case BOP_BW_AVG_CENTRE:
+      for (int n = 0; n < L; n++) abar[n] += abar_inf / L;
+      if (p.mode == BOP_BW_AVG_CENTRE) {
+        bbar[L] += Bb;
+      } else if (Bb != 0.0) {  // B = sqrt(sum b^2 / L) >= the floor here
+        for (int n = 1; n <= L; n++) bbar[n] += Bb * r.b[n] / (L * t.bsum);
+      }
+      return;
+    case BOP_BW_MINMAX:
+      abar[t.ihi] += 0.5 * abar_inf + 0.25 * Bb;
+      abar[t.ilo] += 0.5 * abar_inf - 0.25 * Bb;
+      bbar[t.ib] += Bb;
+      return;
+    case BOP_BW_GLOBAL:
+      return;
+    default:  // BOP_BW_WEIGHTED
+      for (int m = 0; m < L; m++) abar[m] += abar_inf / ((p.beta * (L - 1 - m) + 1.0) * t.bsum);
+      for (int m = 1; m <= L; m++) bbar[m] += Bb / ((p.beta * (L - m) + 1.0) * t.wsum_b);
+  }
 }
 
 // Reverse of the moment recursion: adds d/dmu of (abar . a + bbar . b) to mub.

@@ -109,6 +109,13 @@ struct AdjointArgs {
 };
 int launch_moments_adjoint(const AdjointArgs& a, int fp64, cudaStream_t s);
 
+// Band centre / width estimate of the constant terminator (BOP_BW_* of
+// bopgb.h): mode, beta of the weighted average, (A, B) of the global mode.
+struct BandSel {
+  int mode;
+  double beta, ga, gb;
+};
+
 // scalar.cu
 struct ScalarArgs {
   int M;               // orbitals (all spins)
@@ -122,6 +129,8 @@ struct ScalarArgs {
   double* gsig;        // [n_exp+1][M]   (coefficient-major)
   const double* g;     // [n_exp+1] damping
   unsigned* status;
+  BandSel bw;
+  unsigned* n_unbounded;  // may be null: orbitals with some |sigma_m| > m + 1
 };
 int launch_expand(const ScalarArgs& a, cudaStream_t s);
 void launch_jackson(double* g, int n_exp, cudaStream_t s);
@@ -199,6 +208,7 @@ struct WeightArgs {
   double* dU_dE;         // [M] direct derivative of L w.r.t. the onsite level, may be null
   double* zscratch;      // [2][n_exp+1][M]: sigma_m and its cotangent
   unsigned* status;
+  BandSel bw;
 };
 int launch_weights(const WeightArgs& a, cudaStream_t s);
 // Weights of L1 = cU1 U + cN1 N into a.w and of L2 = cU2 U + cN2 N into w2 at

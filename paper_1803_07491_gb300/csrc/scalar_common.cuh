@@ -59,7 +59,10 @@ __device__ inline void recursion(const double* mu, int Kp, Rec& r) {
 
 struct Term {
   double a_inf, b_inf;
-  int ilo, ihi;
+  int ilo, ihi;  // Gershgorin: bottom / top level; MINMAX: argmin / argmax of a
+  int ib;        // MINMAX: argmax of b
+  double bsum;   // AVERAGE: rms b before the floor; WEIGHTED: sum of the a weights
+  double wsum_b; // WEIGHTED: sum of the b weights
   bool floored;
 };
 
@@ -67,7 +70,8 @@ struct Term {
 __device__ inline Term gershgorin(const Rec& r) {
   Term t;
   double bot = 0.0, top = 0.0;
-  t.ilo = t.ihi = 0;
+  t.ilo = t.ihi = t.ib = 0;
+  t.bsum = t.wsum_b = 0.0;
   for (int n = 0; n < r.nlev; n++) {
     double lo = r.a[n] - r.b[n] - r.b[n + 1];
     double hi = r.a[n] + r.b[n] + r.b[n + 1];
@@ -77,6 +81,78 @@ __device__ inline Term gershgorin(const Rec& r) {
   t.a_inf = 0.5 * (top + bot);
   t.b_inf = 0.25 * (top - bot);
   t.floored = t.b_inf < B_INF_MIN;
+  if (t.floored) t.b_inf = B_INF_MIN;
+  return t;
+}
+
+// The other estimates of the band centre A and width B (section "Band-width
+// estimates", items (i)-(v), (viii), and the weighted averages of Eq.
+// weighted) over the computed levels a_0..a_{L-1}, b_1..b_L, L = nlev.
+// Ties in max / min go to the first index.  B is floored like Gershgorin's.
+__device__ inline Term bandwidth(const Rec& r, const BandSel& p) {
+  if (p.mode == BOP_BW_GERSHGORIN) return gershgorin(r);
+  Term t;
+  const int L = r.nlev;
+  t.ilo = t.ihi = t.ib = 0;
+  t.bsum = t.wsum_b = 0.0;
+  double A = 0.0, B = 0.0;
+  switch (p.mode) {
+    case BOP_BW_LOWEST:
+      A = r.a[0];
+      B = r.b[1];
+      break;
+    case BOP_BW_HIGHEST:
+      A = r.a[L - 1];
+      B = r.b[L];
+      break;
+    case BOP_BW_AVERAGE:
+    case BOP_BW_AVG_CENTRE: {
+      double sa = 0.0, sb = 0.0;
+      for (int n = 0; n < L; n++) sa += r.a[n];
+      for (int n = 1; n <= L; n++) sb += r.b[n] * r.b[n];
+      A = sa / L;
+      B = p.mode == BOP_BW_AVERAGE ? sqrt(sb / L) : r.b[L];
+      t.bsum = B;
+      break;
+    }
+    case BOP_BW_MINMAX: {
+      double amax = r.a[0], amin = r.a[0], bmax = r.b[1];
+      for (int n = 1; n < L; n++) {
+        if (r.a[n] > amax) { amax = r.a[n]; t.ihi = n; }
+        if (r.a[n] < amin) { amin = r.a[n]; t.ilo = n; }
+      }
+      t.ib = 1;
+      for (int n = 2; n <= L; n++)
+        if (r.b[n] > bmax) { bmax = r.b[n]; t.ib = n; }
+      A = 0.5 * (amax + amin);
+      B = 0.25 * (amax - amin + 4.0 * bmax);
+      break;
+    }
+    case BOP_BW_GLOBAL:
+      A = p.ga;
+      B = p.gb;
+      break;
+    default: {  // BOP_BW_WEIGHTED
+      double wa = 0.0, wb = 0.0, sa = 0.0, sb = 0.0;
+      for (int m = 0; m < L; m++) {
+        const double w = 1.0 / (p.beta * (L - 1 - m) + 1.0);
+        wa += w;
+        sa += w * r.a[m];
+      }
+      for (int m = 1; m <= L; m++) {
+        const double w = 1.0 / (p.beta * (L - m) + 1.0);
+        wb += w;
+        sb += w * r.b[m];
+      }
+      A = sa / wa;
+      B = sb / wb;
+      t.bsum = wa;
+      t.wsum_b = wb;
+    }
+  }
+  t.a_inf = A;
+  t.b_inf = B;
+  t.floored = B < B_INF_MIN;
   if (t.floored) t.b_inf = B_INF_MIN;
   return t;
 }
