@@ -23,6 +23,10 @@ Readings of the paper taken here (each listed in the design doc):
   * the SCF update is either linear mixing of the DOS-preconditioned
     residual or Anderson (type-II Broyden) mixing of it; both reach the
     same self-consistent state.
+  * the variational SCF (Eq. BOP_SCF) shifts one onsite level per atom and
+    drives sum_alpha (Theta~_ii - N_i) = dU_B/d delta_i to zero, with
+    U_B = U_bond + sum_i J_ii q_i^2 / 2 (one species: U_prom and the
+    electronegativity term sum to E^0 sum_i q_i = 0 at fixed electron count).
 """
 from __future__ import annotations
 
@@ -103,7 +107,7 @@ class Settings:
     n_mom: int = 9
     n_exp: int = 200
     n_spin: int = 1
-    scf: str = "none"          # none | lcn | stoner
+    scf: str = "none"          # none | lcn | stoner | variational
     eta: float = 0.5           # LCN mixing
     scf_tol: float = 1e-9      # max |N_i - N_i^0| (and |dm| for Stoner: scf_tol*10)
     scf_max_it: int = 200
@@ -117,6 +121,7 @@ class Settings:
     net: object = None            # mlp.Net for terminator = "mlp"
     scf_response: bool = True     # forces include the response of the SCF onsite levels
     bandwidth: object = None      # Bandwidth (None: Gershgorin)
+    J_ii: float = 0.0             # variational SCF: onsite charging J_ii of Eq. TB-Uion (eV / e^2)
 
 
 @dataclass
@@ -611,6 +616,34 @@ def weights(mu, E_on, E_F, n_exp: int, spin_factor: float, stage=None):
     return w, dU_dE, dN, dN_dEF, dU_dEF, dU
 
 
+def variational_gradient(st: Settings, nbr: Neighbors, H, onsite, mu_f, E_F, stage, s: float):
+    """Gradient of the binding energy U_B = U_bond + sum_i J_ii q_i^2 / 2
+    (Eqs. U_B, TB-Ubond, TB-Uion; q_i = s sum_alpha N_i alpha - n_e) with
+    respect to the per-atom onsite shifts delta_i at fixed electron count:
+    Delta_i = sum_alpha dU_B/dE_i alpha = sum_alpha (Theta~_i alpha i alpha -
+    N_i alpha) of Eq. BOP_SCF, Theta~_ii the derivative of U_B through the
+    moments (reverse sweep of the moments with the weights below) and -N the
+    explicit derivative of U_bond's (E - E_i alpha) term (n_spin = 1).
+
+    The weights are those of U_B with E_F following the electron count:
+    w = s dU/dmu + s (J_ii q_i - Lambda) dN/dmu,
+    Lambda = (dU_B/dE_F) / (dN_total/dE_F).  Returns (Delta [n], w
+    [1, n, norb, n_mom], q [n])."""
+    S, n, norb = onsite.shape
+    n_mom = mu_f.shape[1]
+    _, dU_dE, dN, dN_dEF, dU_dEF, dU = weights(mu_f, onsite.reshape(-1), E_F, st.n_exp, s, stage)
+    ex = stage(mu_f)
+    N, _ = orbital_N_U(ex.gsig, ex.a_inf, ex.b_inf, onsite.reshape(-1), E_F)
+    q = s * N.reshape(n, norb).sum(axis=1) - st.n_e
+    qo = np.repeat(q, norb)                            # q of each orbital's atom
+    dUB_dEF = s * np.sum(dU_dEF) + st.J_ii * s * np.sum(qo * dN_dEF)
+    Lam = dUB_dEF / (s * np.sum(dN_dEF))
+    w = s * dU + (s * (st.J_ii * qo - Lam))[:, None] * dN
+    _, Ebar = moments_adjoint(nbr, H, onsite[0], w.reshape(n, norb, n_mom))
+    Delta = (Ebar + dU_dE.reshape(n, norb)).sum(axis=1)
+    return Delta, w.reshape(1, n, norb, n_mom), q
+
+
 # ---------------------------------------------------------------- driver
 
 def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = True,
@@ -664,6 +697,10 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
         Ni = s * Nsv.sum(axis=(0, 2))
         res = Ni - N0
         dos = s * dos_at(ex.gsig, ex.a_inf, ex.b_inf, E_F).reshape(S, n, norb).sum(axis=(0, 2))
+        if st.scf == "variational":
+            # residual Delta_i = dU_B/d delta_i; Newton-like step with the
+            # local estimate d Delta_i / d delta_i ~ D (1 + J_ii D), D = s n_i(E_F)
+            res, _, _ = variational_gradient(st, nbr, H, onsite, mu_f, E_F, stage, s)
         done = np.max(np.abs(res)) < st.scf_tol
         if st.scf == "stoner":
             m_out = (Nsv[0] - Nsv[1]).sum(axis=1)
@@ -672,7 +709,11 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
             converged = True
             break
         # preconditioned residual F; linear mixing x += F, or Anderson mixing
-        F = st.eta * res / np.maximum(dos, st.dos_floor)
+        if st.scf == "variational":
+            Dt = np.maximum(dos, st.dos_floor)
+            F = -st.eta * res / (Dt * (1.0 + st.J_ii * Dt))
+        else:
+            F = st.eta * res / np.maximum(dos, st.dos_floor)
         x = delta.copy()
         if st.scf == "stoner":
             F = np.concatenate([F, st.m_mix * (m_out - m)])
@@ -699,6 +740,9 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
     e_atom = s * U.reshape(S, n, norb).sum(axis=(0, 2))
     if st.scf == "stoner":
         e_atom = e_atom - 0.25 * st.stoner_I * m ** 2
+    if st.scf == "variational":
+        q = s * Nsv.sum(axis=(0, 2)) - N0
+        e_atom = e_atom + 0.5 * st.J_ii * q ** 2
     out = dict(e_atom=e_atom, e_total=float(e_atom.sum()), e_fermi=E_F, mu=mu,
                a=ex.a, b=ex.b, a_inf=ex.a_inf, b_inf=ex.b_inf, N=Nsv, delta=delta, m=m,
                scf_iterations=it, scf_converged=converged, bisection_steps=n_bis,
@@ -708,12 +752,15 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
     if want_forces:
         w, dU_dE, dN, _, _, dU = weights(mu_f, onsite.reshape(-1), E_F, st.n_exp, s, stage)
         w = w.reshape(S, n, norb, st.n_mom)
-        resp = st.scf != "none" and st.scf_response
+        resp = st.scf in ("lcn", "stoner") and st.scf_response
+        if st.scf == "variational":
+            # U_B is stationary in delta: its derivative at fixed delta is exact
+            _, w, _ = variational_gradient(st, nbr, H, onsite, mu_f, E_F, stage, s)
         if resp:
             w, lam_scf = scf_response_weights(st, nbr, H, onsite, m, s * dU.reshape(w.shape),
                                               dU_dE.reshape(S, n, norb), dN.reshape(w.shape))
             out.update(scf_multipliers=lam_scf)
-        out["forces_include_scf_response"] = st.scf == "none" or resp
+        out["forces_include_scf_response"] = st.scf in ("none", "variational") or resp
         Hbar = np.zeros((nbr.n_edges, norb, norb))
         for v in range(S):
             hb, _ = moments_adjoint(nbr, H, onsite[v], w[v])

@@ -81,7 +81,7 @@ class RunParams:
     n_mom: int = 9
     n_exp: int = 200
     n_spin: int = 1
-    scf: str = "none"     # none | lcn | stoner
+    scf: str = "none"     # none | lcn | stoner | variational
     eta: float = 0.5
     scf_tol: float = 1e-9
     scf_max_it: int = 200
@@ -98,6 +98,7 @@ class RunParams:
     bw_beta: float = 1.0          # weighted: w_m = 1/(beta (m_max - m) + 1)
     bw_a: float = 0.0             # global: A (eV)
     bw_b: float = 1.0             # global: B (eV)
+    J_ii: float = 0.0             # variational SCF: onsite charging energy J_ii q_i^2 / 2 (eV / e^2)
 
 
 @dataclass
