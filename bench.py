@@ -38,6 +38,8 @@ PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12     # SMs x FP64 FMA units x 2 x
 L2_FLUSH_BYTES = 512 << 20
 FP32_SCF_TOL = 3e-5  # electrons: SCF tolerance with FP32 products (FP64 mode keeps 1e-9); the
 #                      max over atoms of the FP32 noise floor is 4e-6 at 2,000 atoms, 1e-5 at 65,536
+FP32_VAR_TOL = 1e-3  # electrons: the same for the variational residual sum (Theta~_ii - N_i), whose
+#                      FP32 floor is 2e-4 at 2,000 atoms (a difference of two sums of many terms)
 
 
 def parse():
@@ -94,12 +96,6 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ algorithmic work
-def chain_level_updates(n_exp: int) -> int:
-    """Level updates of the zeta chain restricted to the levels that reach
-    sigma_0 .. sigma_{n_exp} (the dependency cone)."""
-    return sum(min(m + 1, n_exp - m - 1) + 1 for m in range(n_exp))
-
-
 def algorithmic_flops(family: str, w, stats: dict, prof: dict, n_spin: int, steps: int = 1) -> float | None:
     """FLOPs one launch region of a family must do (per region)."""
     norb, n_mom, n_exp = w.model.norb, w.run.n_mom, w.run.n_exp
@@ -109,17 +105,26 @@ def algorithmic_flops(family: str, w, stats: dict, prof: dict, n_spin: int, step
         # norb x norb x norb multiply-adds each (all starting orbitals)
         return 2.0 * stats["moment_products"] * n_spin * norb ** 3
     if family == "adjoint":
-        # a reverse sweep recomputes Psi (one moments pass), runs H^T over
-        # Psi-bar (one more) and, when bond cotangents are wanted, forms
-        # sum_k Psi-bar_k(t) Psi_k-1(s)^T over the same pairs (one more);
-        # one pass per step forms bond cotangents, the others (SCF-response
-        # products) only onsite ones
+        # a reverse sweep runs H^T over Psi-bar (one moments pass) and, when
+        # bond cotangents are wanted, forms sum_k Psi-bar_k(t) Psi_k-1(s)^T
+        # over the same pairs (one more); Psi itself is stored by the forward
+        # pass (recomputing it, where it does not fit, is not counted).  One
+        # sweep per step forms bond cotangents, the others (SCF-response
+        # products, variational residuals) only onsite ones
         one = 2.0 * stats["moment_products"] * n_spin * norb ** 3
         regions = max(1, prof["adjoint"]["regions"])
         with_h = min(steps, regions)
-        return one * (3.0 * with_h + 2.0 * (regions - with_h)) / regions
+        return one * (2.0 * with_h + 1.0 * (regions - with_h)) / regions
+    K = (n_mom - 1) // 2
     if family == "expand":
-        return 8.0 * M * chain_level_updates(n_exp)
+        # sigma_m from the 2K-term recurrence of the generating function,
+        # times g_m: (4K + 1) flops per coefficient
+        return M * (n_exp + 1) * (4.0 * K + 1.0)
+    if family == "weights":
+        # the forward recurrence and, per seed (two for the SCF-response
+        # pair dU/dmu, dN/dmu, else one), its adjoint with the N / U sums
+        seeds = 2 if (w.run.scf in ("lcn", "stoner") and w.run.scf_response) else 1
+        return M * (n_exp + 1) * (4.0 * K + 1.0 + seeds * (4.0 * K + 2.0))
     if family == "fermi":
         rounds = max(1, stats["bisection_rounds"])
         return rounds * M * (n_exp + 2) * 4.0
@@ -245,8 +250,10 @@ def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: s
                    "terminator": w.run.terminator,
                    "scf_iterations": stats["scf_iterations"], "scf_tol": w.run.scf_tol,
                    "bisection_rounds": stats["bisection_rounds"],
-                   "forces": ("exact: SCF response included" if stats["forces_scf_response"]
+                   "forces": ("exact: U_B stationary in the shifts" if w.run.scf == "variational"
+                              else "exact: SCF response included" if stats["forces_scf_response"]
                               else "fixed onsite levels (Hellmann-Feynman form)"),
+                   **({"J_ii": w.run.J_ii} if w.run.scf == "variational" else {}),
                    "response_iterations": stats["response_iterations"],
                    "precision": precision, "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
@@ -276,7 +283,7 @@ def run_ours(args):
         w = I.workload(args.workload)
         if args.precision == "fp32" and w.run.scf != "none":
             # FP32 moments put a floor of a few 1e-6 electrons under N_i
-            w = I.with_run(w, scf_tol=FP32_SCF_TOL)
+            w = I.with_run(w, scf_tol=FP32_VAR_TOL if w.run.scf == "variational" else FP32_SCF_TOL)
         ctx = bop.Context(w.model, w.run, args.precision)
         line = measure(bop, ctx, w, args, world, args.steps, args.warmup, args.precision)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -389,7 +396,13 @@ def profile_traffic(family: str):
 
 
 # ------------------------------------------------------------ CPU oracle
-def oracle_sample(n_cells: int):
+def sample_settings(workload: str):
+    """Run settings of a 2,000-atom bcc workload (d2000 for the others)."""
+    from paper_1803_07491_gb300 import inputs as I
+    return I.workload(workload if workload in ("d2000", "d2000nscf", "d2000var") else "d2000").run
+
+
+def oracle_sample(n_cells: int, workload: str = "d2000"):
     """The oracle's energy + forces on an n x n x n x 2 cell of the same
     model and settings (jitter 0.05 A, seed 2): a bounded sample of the
     workload; the per-atom work of the method does not depend on the cell
@@ -398,20 +411,27 @@ def oracle_sample(n_cells: int):
     from paper_1803_07491_gb300 import inputs as I
     ob.build()
     pos, cell = I.bcc_jittered(n_cells, n_cells, n_cells, 0.05, 2)
-    r = I.workload("d2000").run
+    r = sample_settings(workload)
     p = I.MODEL_D
     t0 = time.perf_counter()
     ob.evaluate(ob.Model(p.norb, tuple(p.b0), p.r0, p.lam, p.rc, p.dc, p.onsite0),
                 ob.Settings(n_e=r.n_e, n_mom=r.n_mom, n_exp=r.n_exp, scf=r.scf, eta=r.eta, scf_tol=r.scf_tol,
-                            scf_max_it=r.scf_max_it), pos, cell, (1, 1, 1))
+                            scf_max_it=r.scf_max_it, mixer=r.mixer, mix_history=r.mix_history, J_ii=r.J_ii),
+                pos, cell, (1, 1, 1))
     return len(pos), time.perf_counter() - t0
 
 
+def sample_label(workload: str) -> str:
+    scf = sample_settings(workload).scf
+    return {"lcn": "LCN SCF", "none": "no SCF", "variational": "variational SCF"}[scf]
+
+
 def cpu_baseline(workload: str):
-    n, t = oracle_sample(3)
+    k = 2 if sample_settings(workload).scf == "variational" else 3
+    n, t = oracle_sample(k, workload)
     return {"value": round(n / t, 3), "unit": "atoms/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle E+F (LCN SCF, 9 moments, canonical d) of a {n}-atom 3x3x3x2 jittered bcc "
-                      f"cell of the {workload} model, {t:.1f} s on one host core"}
+            "sample": f"oracle E+F ({sample_label(workload)}, 9 moments, canonical d) of a {n}-atom "
+                      f"{k}x{k}x{k}x2 jittered bcc cell of the {workload} model, {t:.1f} s on one host core"}
 
 
 def run_reference(args):
@@ -419,15 +439,15 @@ def run_reference(args):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(2)
+        oracle_sample(2, args.workload)
     tot_n, tot_t = 0, 0.0
     for _ in range(args.steps):
-        n, t = oracle_sample(2)
+        n, t = oracle_sample(2, args.workload)
         tot_n += n
         tot_t += t
     value = tot_n / tot_t
-    sample = ("oracle E+F (LCN SCF, 9 moments, canonical d) of a 16-atom 2x2x2x2 jittered bcc cell of the "
-              f"{args.workload} model per step, one host core")
+    sample = (f"oracle E+F ({sample_label(args.workload)}, 9 moments, canonical d) of a 16-atom 2x2x2x2 "
+              f"jittered bcc cell of the {args.workload} model per step, one host core")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "atoms/s", "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 1),

@@ -63,7 +63,7 @@ enum bop_status {
   BOP_ERR_OVERFLOW = 8        /* neighbour degree / cluster / image index limit exceeded */
 };
 
-enum { BOP_SCF_NONE = 0, BOP_SCF_LCN = 1, BOP_SCF_STONER = 2 };
+enum { BOP_SCF_NONE = 0, BOP_SCF_LCN = 1, BOP_SCF_STONER = 2, BOP_SCF_VARIATIONAL = 3 };
 enum { BOP_PREC_FP64 = 0, BOP_PREC_FP32 = 1 };
 enum { BOP_MIX_LINEAR = 0, BOP_MIX_ANDERSON = 1 };
 enum { BOP_TERM_CONSTANT = 0, BOP_TERM_MLP = 1 };
@@ -92,6 +92,16 @@ enum {
  * max(n_i(E_F), dos_floor) then removes the mean, until max|N_i - n_e| <
  * scf_tol; STONER additionally mixes m_i with m_mix from m0 until
  * max|m_out - m| < 10 scf_tol, E_{i,up/down} = E0 + delta_i -/+ I m_i / 2.
+ * VARIATIONAL (n_spin 1, Eq. BOP_SCF) minimises the binding energy
+ * U_B = U_bond + sum_i j_ii q_i^2 / 2 (q_i = N_i - n_e, Eq. TB-Uion) over
+ * one onsite shift per atom: Delta_i = sum_alpha (Theta~_ii - N_i) =
+ * dU_B/d delta_i at fixed electron count comes from a reverse sweep of the
+ * moments every iteration, delta_i -= eta Delta_i / (D (1 + j_ii D)) with
+ * D = max(n_i(E_F), dos_floor) (mixed like LCN), until max|Delta_i| <
+ * scf_tol.  The energy per atom includes j_ii q_i^2 / 2, and the forces
+ * need no response solve (U_B is stationary in the shifts).  With j_ii = 0
+ * the minimum can sit on a kink of the Gershgorin estimate, where Delta
+ * jumps across zero; the loop then stops at scf_max_it.
  * precision: FP64 everywhere, or FP32 products and accumulation in the
  * moments and their reverse sweep with every scalar stage in FP64.
  * mixer: BOP_MIX_LINEAR (x += F, F the preconditioned residual above) or
@@ -132,6 +142,7 @@ typedef struct {
   int bandwidth;
   double bw_beta;
   double bw_a, bw_b;
+  double j_ii;  /* VARIATIONAL: onsite charging J_ii >= 0 (eV / e^2) */
 } bop_model;
 
 typedef struct {

@@ -17,7 +17,7 @@ from . import build as _build
 
 BOP_OK, BOP_ERR_ARG, BOP_ERR_CUDA, BOP_ERR_OOM, BOP_ERR_NO_CONVERGENCE = 0, 1, 2, 3, 4
 BOP_ERR_BRACKET, BOP_ERR_NUMERIC, BOP_ERR_STATE, BOP_ERR_OVERFLOW = 5, 6, 7, 8
-SCF = {"none": 0, "lcn": 1, "stoner": 2}
+SCF = {"none": 0, "lcn": 1, "stoner": 2, "variational": 3}
 PREC = {"fp64": 0, "fp32": 1}
 MIXER = {"linear": 0, "anderson": 1}
 TERM = {"constant": 0, "mlp": 1}
@@ -42,7 +42,7 @@ class bop_model(ctypes.Structure):
                 ("dos_floor", ctypes.c_double), ("precision", ctypes.c_int), ("mixer", ctypes.c_int),
                 ("mix_history", ctypes.c_int), ("terminator", ctypes.c_int), ("scf_response", ctypes.c_int),
                 ("bandwidth", ctypes.c_int), ("bw_beta", ctypes.c_double), ("bw_a", ctypes.c_double),
-                ("bw_b", ctypes.c_double)]
+                ("bw_b", ctypes.c_double), ("j_ii", ctypes.c_double)]
 
 
 class bop_stats(ctypes.Structure):
@@ -151,7 +151,8 @@ def make_model(params, run, precision: str = "fp64") -> bop_model:
                      params.onsite0, run.n_mom, run.n_exp, run.n_spin, run.n_e, SCF[run.scf], run.eta,
                      run.scf_tol, run.scf_max_it, run.stoner_I, run.m_mix, run.m0, run.dos_floor,
                      PREC[precision], MIXER[run.mixer], run.mix_history, TERM[run.terminator],
-                     1 if run.scf_response else 0, BANDWIDTH[run.bandwidth], run.bw_beta, run.bw_a, run.bw_b)
+                     1 if run.scf_response else 0, BANDWIDTH[run.bandwidth], run.bw_beta, run.bw_a, run.bw_b,
+                     run.J_ii)
 
 
 def _check(ctx, st, allow=()):

@@ -76,6 +76,9 @@ struct bop_ctx {
   DBuf lbase, lnlev, lflag, lxs, lys, lZ1, lH1, lZ2, lH2, lybar, lcot, lxbar, lcount;
   // SCF response of the forces
   DBuf rwN, rwt, rdUE, rvec, rcoef;
+  // variational SCF: dU_B/d delta, q; weights in w valid for the final state
+  DBuf vgrad, vq;
+  bool var_w_valid = false;
   // stored Psi of every work item for the reverse sweeps (when it fits)
   DBuf psi_off, psis, psib, lsum;
   long long psi_tot = 0;
@@ -201,7 +204,10 @@ int validate_model(bop_ctx* c, const bop_model* m) {
     return fail(c, BOP_ERR_ARG, "n_exp must be in [n_mom-1, %d]", BOP_MAX_NEXP);
   if (m->n_spin != 1 && m->n_spin != 2) return fail(c, BOP_ERR_ARG, "n_spin must be 1 or 2");
   if (!(m->rc > 0) || !(m->dc > 0) || m->dc > m->rc) return fail(c, BOP_ERR_ARG, "need 0 < dc <= rc");
-  if (m->scf < 0 || m->scf > 2) return fail(c, BOP_ERR_ARG, "scf must be NONE, LCN or STONER");
+  if (m->scf < 0 || m->scf > 3) return fail(c, BOP_ERR_ARG, "scf must be NONE, LCN, STONER or VARIATIONAL");
+  if (m->scf == BOP_SCF_VARIATIONAL && m->n_spin != 1) return fail(c, BOP_ERR_ARG, "VARIATIONAL needs n_spin = 1");
+  if (m->scf == BOP_SCF_VARIATIONAL && !(m->j_ii >= 0 && m->j_ii < 1e300))
+    return fail(c, BOP_ERR_ARG, "j_ii must be finite and >= 0");
   if (m->scf == BOP_SCF_STONER && m->n_spin != 2) return fail(c, BOP_ERR_ARG, "STONER needs n_spin = 2");
   if (m->n_spin == 2 && m->scf != BOP_SCF_STONER && m->scf != BOP_SCF_NONE)
     return fail(c, BOP_ERR_ARG, "n_spin = 2 needs scf STONER or NONE");
@@ -560,7 +566,8 @@ int fermi_more(bop_ctx* c, cudaStream_t s) {
 // Weights of L = cU U + cN N for every orbital (cN = -cU * lam[0] with a
 // device lam, else cN0), through the constant- or learned-terminator path,
 // into w [M][n_mom]; dUE [M] = direct dL/dE (may be NULL).
-int compute_weights(bop_ctx* c, double cU, const double* lam, double cN0, double* w, double* dUE, cudaStream_t s) {
+int compute_weights(bop_ctx* c, double cU, const double* lam, double cN0, double* w, double* dUE, cudaStream_t s,
+                    const double* var_q = nullptr, const double* var_lam = nullptr, double var_J = 0.0) {
   const int M = c->S * c->n * c->norb;
   WeightArgs wa;
   wa.M = M;
@@ -580,6 +587,9 @@ int compute_weights(bop_ctx* c, double cU, const double* lam, double cN0, double
   wa.zscratch = P<double>(c->zscr);
   wa.status = P<unsigned>(c->status);
   wa.bw = band_sel(c->m);
+  wa.var_q = var_q;
+  wa.var_lam = var_lam;
+  wa.var_J = var_J;
   if (c->m.terminator == BOP_TERM_MLP) {
     if (!c->net) return fail(c, BOP_ERR_STATE, "terminator MLP needs a network (bop_set_mlp)");
     const size_t T = c->fp64 ? sizeof(double) : sizeof(float);
@@ -619,12 +629,12 @@ int psi_row(int N, int fp64) {
 // stored-Psi sweep keeps two Psi-bar levels of all five columns in shared
 // memory; with one column per item it gathers every block five times and is
 // slower than recomputing), and the store and its cotangent copy fit in a
-// third of the free device memory.  Otherwise the reverse sweeps recompute Psi.
-int prepare_psi_store(bop_ctx* c, cudaStream_t s) {
-  c->psi_valid = false;
+// third of the free device memory (psi_store_alloc).  Otherwise the reverse
+// sweeps recompute Psi.
+int psi_store_alloc(bop_ctx* c, bool* fits) {
+  *fits = false;
   const int nc = forward_nc(c);
-  const bool several = c->m.scf != BOP_SCF_NONE && c->m.scf_response;
-  if (!several || (c->norb > 1 && nc != c->norb)) return BOP_OK;
+  if (c->norb > 1 && nc != c->norb) return BOP_OK;
   const size_t esz = c->fp64 ? sizeof(double) : sizeof(float);
   const size_t bytes = (size_t)c->S * (c->norb / nc) * (size_t)c->psi_tot * psi_row(c->norb * nc, c->fp64) * esz;
   size_t freeb = 0, totalb = 0;
@@ -633,6 +643,19 @@ int prepare_psi_store(bop_ctx* c, cudaStream_t s) {
   if (2 * bytes > (freeb + held) / 3 || 2 * bytes > c->store_budget) return BOP_OK;
   CKS(ensure(c, c->psis, bytes));
   CKS(ensure(c, c->psib, bytes));
+  *fits = true;
+  return BOP_OK;
+}
+
+int prepare_psi_store(bop_ctx* c, cudaStream_t s) {
+  // the variational SCF loop stores Psi in its forward passes; the last one
+  // is at the final onsite levels
+  if (c->m.scf == BOP_SCF_VARIATIONAL) return BOP_OK;
+  c->psi_valid = false;
+  const bool several = (c->m.scf == BOP_SCF_LCN || c->m.scf == BOP_SCF_STONER) && c->m.scf_response;
+  bool fits = false;
+  if (several) CKS(psi_store_alloc(c, &fits));
+  if (!fits) return BOP_OK;
   CKS(run_moments(c, P<double>(c->onsite), P<double>(c->mu), s, c->psis.p));
   c->psi_valid = true;
   return BOP_OK;
@@ -750,7 +773,9 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
     wa.dU_dE = P<double>(c->rdUE);
     wa.zscratch = P<double>(c->zscr);
     wa.status = P<unsigned>(c->status);
-  wa.bw = band_sel(c->m);
+    wa.bw = band_sel(c->m);
+    wa.var_q = wa.var_lam = nullptr;
+    wa.var_J = 0.0;
     Region R(c, PK_WEIGHTS, 1, s);
     if (launch_weights_pair(wa, c->sfac, 0.0, 0.0, 1.0, wN, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
   }
@@ -865,6 +890,43 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
   return conv ? BOP_OK : BOP_ERR_NO_CONVERGENCE;
 }
 
+// Variational SCF: the weights of U_B = U_bond + J sum q^2 / 2 with E_F
+// following the electron count, L = s U + s (J q_i - Lambda) N per orbital,
+// into c->w (one pass of the chain); rdUE = the explicit d(s U)/dE.
+int var_weights(bop_ctx* c, cudaStream_t s) {
+  const int n = c->n, norb = c->norb, nm = c->n_mom, M = n * norb;
+  CKS(ensure(c, c->w, sizeof(double) * (size_t)M * nm));
+  CKS(ensure(c, c->rdUE, sizeof(double) * (size_t)M));
+  CKS(ensure(c, c->vq, sizeof(double) * (size_t)n));
+  CKS(ensure(c, c->zscr, sizeof(double) * (size_t)M * (c->n_exp + 1) * 2));
+  {
+    Region R(c, PK_SCF, 1, s);
+    if (launch_var_lambda(n, norb, c->sfac, c->m.j_ii, c->m.n_e, P<double>(c->N), P<double>(c->dos),
+                          P<double>(c->onsite), P<FermiState>(c->fstate), P<double>(c->vq), P<double>(c->lam),
+                          P<double>(c->scfred), P<unsigned>(c->counter), s))
+      return fail(c, BOP_ERR_CUDA, "variational multiplier launch failed");
+  }
+  return compute_weights(c, c->sfac, nullptr, 0.0, P<double>(c->w), P<double>(c->rdUE), s, P<double>(c->vq),
+                         P<double>(c->lam), c->m.j_ii);
+}
+
+// Delta_i = dU_B/d delta_i = sum_alpha (Theta~_ii + explicit dU_B/dE) into
+// c->vgrad: the weights above, one reverse sweep for the onsite cotangents,
+// and their per-atom sums.
+int var_gradient(bop_ctx* c, cudaStream_t s) {
+  const int n = c->n, M = n * c->norb;
+  CKS(var_weights(c, s));
+  CKS(ensure(c, c->Ebar, sizeof(double) * (size_t)M));
+  CKS(ensure(c, c->vgrad, sizeof(double) * (size_t)n));
+  CK(cudaMemsetAsync(c->Ebar.p, 0, sizeof(double) * (size_t)M, s));
+  CKS(adjoint_pass(c, P<double>(c->w), nullptr, P<double>(c->Ebar), s));
+  Region R(c, PK_SCF, 1, s);
+  if (launch_project(n, c->norb, 1, 0.0, P<double>(c->Ebar), P<double>(c->rdUE), nullptr, 0.0, nullptr,
+                     P<double>(c->vgrad), s))
+    return fail(c, BOP_ERR_CUDA, "variational gradient launch failed");
+  return BOP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -935,7 +997,7 @@ int bop_destroy(bop_ctx* c) {
                   &c->adjscr, &c->Hbar, &c->Ebar, &c->status, &c->cub_tmp, &c->nprod,
                   &c->ginv, &c->hx, &c->hf, &c->gamma, &c->scfred, &c->lbase, &c->lnlev, &c->lflag, &c->lxs,
                   &c->lys, &c->lZ1, &c->lH1, &c->lZ2, &c->lH2, &c->lybar, &c->lcot, &c->lxbar, &c->lcount,
-                  &c->rwN, &c->rwt, &c->rdUE, &c->rvec, &c->rcoef,
+                  &c->rwN, &c->rwt, &c->rdUE, &c->rvec, &c->rcoef, &c->vgrad, &c->vq,
                   &c->psi_off, &c->psis, &c->psib, &c->lsum};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
@@ -1165,6 +1227,8 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   const int n = c->n, M = c->S * n * c->norb;
   c->energized = c->weighted = false;
   c->psi_valid = false;
+  c->var_w_valid = false;
+  const bool variational = c->m.scf == BOP_SCF_VARIATIONAL;
   if (delta_io) CK(cudaMemcpyAsync(c->delta.p, delta_io, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   else CK(cudaMemsetAsync(c->delta.p, 0, sizeof(double) * n, s));
   const bool stoner = c->m.scf == BOP_SCF_STONER;
@@ -1208,6 +1272,22 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   a.hx = P<double>(c->hx);
   a.hf = P<double>(c->hf);
   a.gamma = P<double>(c->gamma);
+  a.grad = nullptr;
+  a.J = c->m.j_ii;
+  // SCF residual of this iteration (for VARIATIONAL after the gradient sweep)
+  // the variational SCF sweeps back once per iteration: store Psi in each
+  // forward pass when it fits
+  bool var_store = false;
+  if (variational) CKS(psi_store_alloc(c, &var_store));
+  auto residual = [&]() -> int {
+    if (variational) {
+      CKS(var_gradient(c, s));
+      a.grad = P<double>(c->vgrad);
+    }
+    Region R(c, PK_SCF, 1, s);
+    if (launch_scf_residual(a, s)) return fail(c, BOP_ERR_CUDA, "scf residual launch failed");
+    return BOP_OK;
+  };
   for (;;) {
     a.it = it;
     {
@@ -1215,14 +1295,12 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
       launch_build_onsite(n, c->norb, c->S, c->m.onsite0, c->m.stoner_I, P<double>(c->delta),
                           stoner ? P<double>(c->mval) : nullptr, P<double>(c->onsite), P<float>(c->onsite32), s);
     }
-    CKS(run_moments(c, P<double>(c->onsite), P<double>(c->mu), s));
+    CKS(run_moments(c, P<double>(c->onsite), P<double>(c->mu), s, var_store ? c->psis.p : nullptr));
+    c->psi_valid = var_store;
     CKS(run_scalar(c, M, P<double>(c->mu), s));
     CKS(fermi_and_N(c, it > 0, s));
     const bool last_it = c->m.scf == BOP_SCF_NONE || it >= c->m.scf_max_it;
-    if (!last_it) {
-      Region R(c, PK_SCF, 1, s);
-      if (launch_scf_residual(a, s)) return fail(c, BOP_ERR_CUDA, "scf residual launch failed");
-    }
+    if (!last_it) CKS(residual());
     // one synchronisation per iteration: Fermi solve converged?  SCF converged?
     for (int extra = 0;; extra++) {
       CK(cudaMemcpyAsync(&fs, c->fstate.p, sizeof(FermiState), cudaMemcpyDeviceToHost, s));
@@ -1232,14 +1310,12 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
       if (fs.iters >= FERMI_MAX_ROUNDS || extra >= 4)
         return fail(c, BOP_ERR_BRACKET, "Fermi level not converged after %d rounds", fs.iters);
       CKS(fermi_more(c, s));
-      if (!last_it) {
-        Region R(c, PK_SCF, 1, s);
-        if (launch_scf_residual(a, s)) return fail(c, BOP_ERR_CUDA, "scf residual launch failed");
-      }
+      if (!last_it) CKS(residual());
     }
     if (last_it) break;
     if (res[2] != 0.0) {
       converged = 1;
+      c->var_w_valid = variational;  // c->w holds the weights of this final state
       break;
     }
     {
@@ -1258,6 +1334,7 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   {
   Region Re(c, PK_ENERGY, 1, s);
   if (launch_energy(n, c->norb, c->S, c->sfac, c->m.stoner_I, P<double>(c->U), stoner ? P<double>(c->mval) : nullptr,
+                    c->m.j_ii, variational ? P<double>(c->N) : nullptr, c->m.n_e,
                     e_atom ? e_atom : P<double>(c->e_atom), P<double>(c->partials), P<unsigned>(c->counter),
                     P<double>(c->e_total), s))
     return fail(c, BOP_ERR_CUDA, "energy launch failed");
@@ -1277,7 +1354,8 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   c->st.scf_residual = res[0];
   c->st.e_fermi = fs.ef;
   c->st.e_total = et;
-  c->st.forces_scf_response = (c->m.scf == BOP_SCF_NONE || c->m.scf_response) ? 1 : 0;
+  c->st.forces_scf_response =
+      (c->m.scf == BOP_SCF_NONE || c->m.scf == BOP_SCF_VARIATIONAL || c->m.scf_response) ? 1 : 0;
   if (st) *st = c->st;
   c->energized = true;
   if (!converged) return fail(c, BOP_ERR_NO_CONVERGENCE, "SCF not converged after %d iterations (residual %g)",
@@ -1299,7 +1377,12 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   c->st.response_iterations = 0;
   c->st.response_converged = 1;
   c->st.response_residual = 0.0;
-  if (c->m.scf != BOP_SCF_NONE && c->m.scf_response) {
+  if (c->m.scf == BOP_SCF_VARIATIONAL) {
+    // U_B is stationary in the shifts: its weights at fixed shifts give the
+    // exact derivative (no response solve)
+    if (!c->var_w_valid) CKS(var_weights(c, s));
+    CKS(adjoint_pass(c, P<double>(c->w), P<double>(c->Hbar), nullptr, s));
+  } else if (c->m.scf != BOP_SCF_NONE && c->m.scf_response) {
     solve_status = scf_response(c, s);
     if (solve_status != BOP_OK && solve_status != BOP_ERR_NO_CONVERGENCE) return solve_status;
   } else {
@@ -1341,7 +1424,8 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   if (tv.p) cudaFree(tv.p);
   if (r) return r;
   c->weighted = true;
-  c->st.forces_scf_response = (c->m.scf == BOP_SCF_NONE || c->m.scf_response) ? 1 : 0;
+  c->st.forces_scf_response =
+      (c->m.scf == BOP_SCF_NONE || c->m.scf == BOP_SCF_VARIATIONAL || c->m.scf_response) ? 1 : 0;
   if (st) *st = c->st;
   if (solve_status != BOP_OK)
     return fail(c, solve_status, "SCF-response solve stopped at relative residual %g after %d iterations",

@@ -429,7 +429,9 @@ __global__ void __launch_bounds__(CT) k_weights(WeightArgs A) {
   const int o = blockIdx.x * CT + threadIdx.x;
   if (o >= A.M) return;
   const int M = A.M, nm = 2 * KP + 1;
-  const double cU = A.cU, cN = A.lam ? -A.cU * A.lam[0] : A.cN0;
+  const double cU = A.cU;
+  const double cN = A.var_q ? cU * (A.var_J * A.var_q[o / A.norb] - A.var_lam[0])
+                            : (A.lam ? -A.cU * A.lam[0] : A.cN0);
   double mu[BOP_MAX_NMOM];
   for (int n = 0; n < nm; n++) mu[n] = A.mu[(size_t)o * nm + n];
   Rec r;

@@ -183,6 +183,8 @@ struct ScfArgs {
   double* hx;          // [(hist+1)][ncomp*n] iterates
   double* hf;          // [(hist+1)][ncomp*n] preconditioned residuals
   double* gamma;       // [hist] least-squares coefficients
+  const double* grad;  // mode 3 (variational): dU_B/d delta_i [n]
+  double J;            // mode 3: onsite charging J_ii
 };
 int launch_scf_residual(const ScfArgs& a, cudaStream_t s);
 int launch_scf_apply(const ScfArgs& a, cudaStream_t s);
@@ -190,9 +192,10 @@ void launch_to_float(const double* in, float* out, size_t n, cudaStream_t s);
 void launch_build_onsite(int n, int norb, int n_spin, double onsite0, double stoner_I, const double* delta,
                          const double* m, double* onsite, float* onsite32, cudaStream_t s);
 
+// e_i = s sum U (- I m_i^2 / 4 with m) (+ J q_i^2 / 2, q_i = s sum N - n0, with N)
 int launch_energy(int n, int norb, int n_spin, double spin_factor, double stoner_I, const double* U,
-                  const double* m, double* e_atom, double* red, unsigned* counter, double* e_total,
-                  cudaStream_t s);
+                  const double* m, double J, const double* N, double n0, double* e_atom, double* red,
+                  unsigned* counter, double* e_total, cudaStream_t s);
 
 struct WeightArgs {
   int M, n_mom, n_exp, norb;
@@ -209,6 +212,11 @@ struct WeightArgs {
   double* zscratch;      // [2][n_exp+1][M]: sigma_m and its cotangent
   unsigned* status;
   BandSel bw;
+  // n_spin 1 only: per-atom cN = cU (var_J var_q[i] - var_lam[0]) when var_q
+  // is set (the variational SCF's binding energy U_B); else lam / cN0 above
+  const double* var_q;
+  const double* var_lam;
+  double var_J;
 };
 int launch_weights(const WeightArgs& a, cudaStream_t s);
 // Weights of L1 = cU1 U + cN1 N into a.w and of L2 = cU2 U + cN2 N into w2 at
@@ -256,6 +264,12 @@ const float* mlp_norm_dev(const bop_mlp* net);
 
 // scf_adjoint.cu: vector kernels of the SCF-response solve (nu = n or 2n unknowns)
 // w_out = (wU or 0) + sign * c_{atom,spin} * wN, c = s v[atom] + sigma_spin v[n + atom] (Stoner)
+// Variational SCF: q_i = s sum_alpha N - n0 into q, and the E_F multiplier
+// of U_B = U_bond + J sum q^2 / 2 into lam[0]:
+// Lambda = sum_i D_i (E_F - E_i + J q_i) / sum_i D_i, D_i = s sum_alpha dos.
+int launch_var_lambda(int n, int norb, double s, double J, double n0, const double* N, const double* dos,
+                      const double* onsite, const FermiState* st, double* q, double* lam, double* red,
+                      unsigned* counter, cudaStream_t stream);
 int launch_scale_weights(int n, int norb, int S, int n_mom, double s, int stoner, const double* v, double sign,
                          const double* wN, const double* wU, double* w_out, cudaStream_t st);
 // out_u = derivative w.r.t. u of a function whose onsite-level derivative is Eb (+ dUE):

@@ -163,7 +163,9 @@ __global__ void __launch_bounds__(CT) k_weights_learned_a(LearnedArgs A) {
   if (o >= A.M) return;
   const WeightArgs& W = A.W;
   const int M = A.M;
-  const double cU = W.cU, cN = W.lam ? -W.cU * W.lam[0] : W.cN0;
+  const double cU = W.cU;
+  const double cN = W.var_q ? cU * (W.var_J * W.var_q[o / W.norb] - W.var_lam[0])
+                            : (W.lam ? -W.cU * W.lam[0] : W.cN0);
   double yh[NO];
   destandardise<T>(A, o, yh);
   const double* base = A.base + (size_t)o * NB;

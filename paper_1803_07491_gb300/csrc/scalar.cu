@@ -164,8 +164,15 @@ __global__ void __launch_bounds__(RT) k_scf_residual(ScfArgs A) {
       }
     Ni *= A.spin_factor;
     di *= A.spin_factor;
-    const double res = Ni - A.n0;
-    const double Fd = A.eta * res / fmax(di, A.dos_floor);
+    double res, Fd;
+    if (A.mode == 3) {  // variational: Newton-like step on dU_B/d delta_i
+      res = A.grad[i];
+      const double Dt = fmax(di, A.dos_floor);
+      Fd = -A.eta * res / (Dt * (1.0 + A.J * Dt));
+    } else {
+      res = Ni - A.n0;
+      Fd = A.eta * res / fmax(di, A.dos_floor);
+    }
     acc[0] = fmax(acc[0], fabs(res));
     double Fm = 0.0;
     if (A.mode == 2) {
@@ -345,6 +352,7 @@ __global__ void __launch_bounds__(RT) k_build_onsite(int n, int norb, int n_spin
 
 __global__ void __launch_bounds__(RT) k_energy(int n, int norb, int n_spin, double sfac, double I,
                                                const double* __restrict__ U, const double* __restrict__ m,
+                                               double J, const double* __restrict__ N, double n0,
                                                double* __restrict__ e_atom, double* red, unsigned* counter,
                                                double* e_total) {
   __shared__ double sh[RT / 32];
@@ -356,6 +364,13 @@ __global__ void __launch_bounds__(RT) k_energy(int n, int norb, int n_spin, doub
       for (int a = 0; a < norb; a++) e += U[((size_t)v * n + i) * norb + a];
     e *= sfac;
     if (m && n_spin == 2) e -= 0.25 * I * m[i] * m[i];
+    if (N) {
+      double q = 0.0;
+      for (int v = 0; v < n_spin; v++)
+        for (int a = 0; a < norb; a++) q += N[((size_t)v * n + i) * norb + a];
+      q = sfac * q - n0;
+      e += 0.5 * J * q * q;
+    }
     e_atom[i] = e;
     acc += e;
   }
@@ -429,9 +444,9 @@ void launch_build_onsite(int n, int norb, int n_spin, double onsite0, double sto
 }
 
 int launch_energy(int n, int norb, int n_spin, double spin_factor, double stoner_I, const double* U,
-                  const double* m, double* e_atom, double* red, unsigned* counter, double* e_total,
-                  cudaStream_t s) {
-  k_energy<<<red_grid(n), RT, 0, s>>>(n, norb, n_spin, spin_factor, stoner_I, U, m, e_atom, red, counter,
-                                      e_total);
+                  const double* m, double J, const double* N, double n0, double* e_atom, double* red,
+                  unsigned* counter, double* e_total, cudaStream_t s) {
+  k_energy<<<red_grid(n), RT, 0, s>>>(n, norb, n_spin, spin_factor, stoner_I, U, m, J, N, n0, e_atom, red,
+                                      counter, e_total);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -106,6 +106,61 @@ __global__ void k_scale_vec(int nu, const double* __restrict__ x, const double* 
   out[i] = a * x[i] * (P ? P[i] : 1.0);
 }
 
+// Variational SCF: q_i and the E_F multiplier of U_B (see kernels.h).  Block
+// partial sums in red[2 b], red[2 b + 1]; the last block adds them in block
+// order (deterministic for a given grid).
+__global__ void __launch_bounds__(VT) k_var_lambda(int n, int norb, double s, double J, double n0,
+                                                   const double* __restrict__ N, const double* __restrict__ dos,
+                                                   const double* __restrict__ onsite,
+                                                   const FermiState* __restrict__ st, double* __restrict__ q,
+                                                   double* __restrict__ lam, double* red, unsigned* counter) {
+  __shared__ double sh[2][VT / 32];
+  __shared__ bool last;
+  const double ef = st->ef;
+  double a = 0.0, b = 0.0;
+  for (int i = blockIdx.x * VT + threadIdx.x; i < n; i += gridDim.x * VT) {
+    double Ni = 0.0, Di = 0.0;
+    for (int al = 0; al < norb; al++) {
+      Ni += N[(size_t)i * norb + al];
+      Di += dos[(size_t)i * norb + al];
+    }
+    const double qi = s * Ni - n0;
+    Di *= s;
+    q[i] = qi;
+    a += Di * (ef - onsite[(size_t)i * norb] + J * qi);
+    b += Di;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = a;
+    sh[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int w = 0; w < VT / 32; w++) {
+      ta += sh[0][w];
+      tb += sh[1][w];
+    }
+    red[2 * blockIdx.x] = ta;
+    red[2 * blockIdx.x + 1] = tb;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  double ta = 0.0, tb = 0.0;
+  for (int k = 0; k < (int)gridDim.x; k++) {
+    ta += __ldcg(red + 2 * k);
+    tb += __ldcg(red + 2 * k + 1);
+  }
+  lam[0] = tb > 0.0 ? ta / tb : 0.0;
+  *counter = 0;
+}
+
 unsigned grid(long long n) { return (unsigned)((n + VT - 1) / VT); }
 int ok() { return cudaGetLastError() == cudaSuccess ? 0 : -1; }
 
@@ -150,5 +205,15 @@ int launch_lincomb(int nu, int nvec, const double* V, const double* coef, const 
 
 int launch_scale_vec(int nu, const double* x, const double* P, double a, double* out, cudaStream_t st) {
   k_scale_vec<<<grid(nu), VT, 0, st>>>(nu, x, P, a, out);
+  return ok();
+}
+
+int launch_var_lambda(int n, int norb, double s, double J, double n0, const double* N, const double* dos,
+                      const double* onsite, const FermiState* st, double* q, double* lam, double* red,
+                      unsigned* counter, cudaStream_t stream) {
+  unsigned g = grid(n);
+  if (g < 1) g = 1;
+  if (g > 1024) g = 1024;
+  k_var_lambda<<<g, VT, 0, stream>>>(n, norb, s, J, n0, N, dos, onsite, st, q, lam, red, counter);
   return ok();
 }

@@ -166,6 +166,10 @@ def workload(name: str) -> Workload:
               N_d = 6.8; local charge neutrality (Anderson, ANDERSON_STEP);
               9 moments.
     d2000nscf the same cell without SCF (fixed onsite levels).
+    d2000var  the same cell with the variational SCF (Eq. BOP_SCF), J_ii =
+              20 eV / e^2 (Anderson, ANDERSON_STEP); with J_ii = 2 the minimum
+              of this cell sits on a kink of the Gershgorin estimate and the
+              residual stalls at 9e-5.
     slab16k   16x16x32x2 bcc slab with (001) surfaces, 64 vacancies, jitter
               0.08 A, seed 3; canonical d; 13 moments; no SCF.
     mag65k    65,536-atom bcc (32x32x32x2), jitter 0.05 A, seed 4; canonical d;
@@ -182,10 +186,11 @@ def workload(name: str) -> Workload:
     if name == "s128":
         pos, cell = bcc_jittered(4, 4, 4, 0.05, 1)
         return Workload(name, pos, cell, (1, 1, 1), MODEL_S, RunParams(n_e=0.7))
-    if name in ("d2000", "d2000nscf"):
+    if name in ("d2000", "d2000nscf", "d2000var"):
         pos, cell = bcc_jittered(10, 10, 10, 0.05, 2)
-        scf = "lcn" if name == "d2000" else "none"
-        return Workload(name, pos, cell, (1, 1, 1), MODEL_D, RunParams(n_e=6.8, scf=scf, **ANDERSON_STEP))
+        scf = {"d2000": "lcn", "d2000nscf": "none", "d2000var": "variational"}[name]
+        J = 20.0 if name == "d2000var" else 0.0
+        return Workload(name, pos, cell, (1, 1, 1), MODEL_D, RunParams(n_e=6.8, scf=scf, J_ii=J, **ANDERSON_STEP))
     if name == "slab16k":
         pos, cell, pbc = slab_with_vacancies(16, 16, 32, 64, 0.08, 3)
         return Workload(name, pos, cell, pbc, MODEL_D, RunParams(n_e=6.8, n_mom=13))
