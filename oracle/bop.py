@@ -94,6 +94,8 @@ class Model:
     rc: float
     dc: float
     onsite0: float = 0.0
+    rep_A: float = 0.0    # repulsive energy U_rep (Eq. U_B) as a pair form, see pair_repulsion
+    rep_p: float = 0.0
 
     def c(self) -> _CModel:
         b = list(self.b0) + [0.0] * (3 - len(self.b0))
@@ -247,6 +249,20 @@ def bond_gradient(model: Model, pos, cell, nbr: Neighbors, Hbar) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- scalar stage
+
+def pair_repulsion(model: Model, r):
+    """U_rep of one bond: rep_A exp(-rep_p (r - r0)) fcut(r), with the
+    cosine taper of Eq. cutoff (the paper leaves U_rep to empirical
+    functions).  Returns (phi, dphi/dr)."""
+    r = np.asarray(r, dtype=np.float64)
+    e = model.rep_A * np.exp(-model.rep_p * (r - model.r0))
+    de = -model.rep_p * e
+    lo = model.rc - model.dc
+    x = np.clip((r - lo) / model.dc, 0.0, 1.0)
+    f = np.where(r < lo, 1.0, np.where(r > model.rc, 0.0, 0.5 * (np.cos(np.pi * x) + 1.0)))
+    df = np.where((r < lo) | (r > model.rc), 0.0, -0.5 * np.pi / model.dc * np.sin(np.pi * x))
+    return e * f, de * f + e * df
+
 
 def _re(x):
     return np.real(x)
@@ -743,6 +759,12 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
     if st.scf == "variational":
         q = s * Nsv.sum(axis=(0, 2)) - N0
         e_atom = e_atom + 0.5 * st.J_ii * q ** 2
+    if model.rep_A != 0.0:
+        # half of every bond to each of its atoms: half of each directed edge
+        dvec = edge_vectors(pos, cell, nbr)
+        phi, _ = pair_repulsion(model, np.linalg.norm(dvec, axis=1))
+        src = np.repeat(np.arange(n), np.diff(nbr.row_ptr))
+        e_atom = e_atom + np.bincount(src, weights=0.5 * phi, minlength=n)
     out = dict(e_atom=e_atom, e_total=float(e_atom.sum()), e_fermi=E_F, mu=mu,
                a=ex.a, b=ex.b, a_inf=ex.a_inf, b_inf=ex.b_inf, N=Nsv, delta=delta, m=m,
                scf_iterations=it, scf_converged=converged, bisection_steps=n_bis,
@@ -766,6 +788,11 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
             hb, _ = moments_adjoint(nbr, H, onsite[v], w[v])
             Hbar += hb
         g = bond_gradient(model, pos, cell, nbr, Hbar)
+        if model.rep_A != 0.0:
+            dvec = edge_vectors(pos, cell, nbr)
+            r = np.linalg.norm(dvec, axis=1)
+            _, dphi = pair_repulsion(model, r)
+            g = g + (0.5 * dphi / r)[:, None] * dvec   # d(phi/2)/dd per directed edge
         F = np.zeros((n, 3))
         src = np.repeat(np.arange(n), np.diff(nbr.row_ptr))
         np.add.at(F, src, g)

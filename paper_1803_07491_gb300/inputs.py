@@ -66,6 +66,8 @@ class ModelParams:
     rc: float          # cutoff radius, Angstrom
     dc: float          # taper width, Angstrom
     onsite0: float = 0.0
+    rep_A: float = 0.0   # pair repulsion rep_A exp(-rep_p (r - r0)) fcut(r), eV; 0 = none
+    rep_p: float = 0.0   # 1/Angstrom
 
 
 # s-valent model: ss sigma = -1.0 eV exp(-1.5 (r - 2.48)), taper 3.2-3.6 A
@@ -73,6 +75,11 @@ MODEL_S = ModelParams(norb=1, b0=(-1.0,), r0=2.48, lam=1.5, rc=3.6, dc=0.4)
 # canonical d model: sigma:pi:delta = -6:4:-1 scaled to dd sigma(2.48) = -0.9 eV,
 # exp decay 1.8/A, cutoff 3.6 A with a 0.4 A taper (1st + 2nd bcc shells)
 MODEL_D = ModelParams(norb=5, b0=(-0.9, 0.6, -0.15), r0=2.48, lam=1.8, rc=3.6, dc=0.4)
+# the same with a pair repulsion decaying twice as fast as the bond integrals,
+# its amplitude chosen so that perfect bcc of the cells below has zero
+# pressure without SCF (a stable lattice for MD; checked by the oracle tests)
+MODEL_D_REP = ModelParams(norb=5, b0=(-0.9, 0.6, -0.15), r0=2.48, lam=1.8, rc=3.6, dc=0.4,
+                          rep_A=0.6218844075436114, rep_p=3.6)
 
 
 @dataclass(frozen=True)
@@ -157,6 +164,19 @@ def slab_with_vacancies(n1, n2, n3, n_vac, sigma, seed, vacuum=10.0):
 ANDERSON_STEP = dict(eta=1.0, mix_history=8)
 
 
+MASS_FE = 55.845       # amu
+K_B = 8.617333262e-5   # eV / K
+EV_PER_AMU = 1.602176634e-19 / 1.66053906660e-27 * 1e-10   # (A / fs)^2 per (eV / amu)
+
+
+def maxwell_velocities(n: int, T: float, mass: float, seed: int) -> np.ndarray:
+    """Velocities (A/fs) drawn from the Maxwell-Boltzmann distribution at T,
+    with the mean (net momentum) removed."""
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=(n, 3)) * np.sqrt(K_B * T / mass * EV_PER_AMU)
+    return v - v.mean(axis=0)
+
+
 def workload(name: str) -> Workload:
     """Named workloads.
 
@@ -179,6 +199,10 @@ def workload(name: str) -> Workload:
     fcc2048   2,048-atom fcc (8x8x8x4, a = 3.51 A: 12 + 6 neighbours within
               3.6 A), jitter 0.05 A, seed 6; canonical d; N_d = 6.8; local
               charge neutrality; 9 moments.
+    md2000    the d2000 cell and settings (LCN) with the pair repulsion of
+              MODEL_D_REP, as the start of an NVE run: Maxwell-Boltzmann
+              velocities at 300 K (seed 7, no net momentum), iron's mass,
+              time step 1 fs (meta: vel, mass, dt).
     learned131k 131,072-atom bcc (32x32x64x2), jitter 0.05 A, seed 5;
               canonical d; 9 moments; no SCF (evaluation cell of the
               learned terminator).
@@ -202,6 +226,10 @@ def workload(name: str) -> Workload:
     if name == "fcc2048":
         pos, cell = fcc_jittered(8, 8, 8, 0.05, 6)
         return Workload(name, pos, cell, (1, 1, 1), MODEL_D, RunParams(n_e=6.8, scf="lcn", **ANDERSON_STEP))
+    if name == "md2000":
+        w = workload("d2000")
+        vel = maxwell_velocities(w.n_atoms, 300.0, MASS_FE, 7)
+        return Workload(name, w.pos, w.cell, w.pbc, MODEL_D_REP, w.run, dict(vel=vel, mass=MASS_FE, dt=1.0))
     if name == "learned131k":
         pos, cell = bcc_jittered(32, 32, 64, 0.05, 5)
         return Workload(name, pos, cell, (1, 1, 1), MODEL_D, RunParams(n_e=6.8))
