@@ -163,10 +163,12 @@ def setup_dist():
     return world, rank
 
 
-def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: str) -> dict:
+def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: str, md=None) -> dict:
     """Times `steps` E+F evaluations of workload w through ctx (device
     buffers, CUDA events, L2 flushed between steps), then the same through
-    the host-buffer entry point; returns the JSON fields of one line."""
+    the host-buffer entry point; returns the JSON fields of one line.  With
+    md = (step, e2e_step, h2d, d2h) a step is an MD step instead and the end
+    to end leg runs e2e_step (an MD step with its host copies)."""
     import torch
     import torch.distributed as dist
 
@@ -178,6 +180,9 @@ def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: s
         ctx.build(pos, w.cell, w.pbc)
         ctx.energy()
         return ctx.forces()
+
+    if md is not None:
+        step = md[0]
 
     for _ in range(warmup):
         step()
@@ -214,14 +219,22 @@ def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: s
     e_h = torch.empty(w.n_atoms, dtype=torch.float64).pin_memory()
     f_h = torch.empty((w.n_atoms, 3), dtype=torch.float64).pin_memory()
     v_h = torch.empty((3, 3), dtype=torch.float64).pin_memory()
-    bop.bop_evaluate_host(ctx.h, pos_h, w.cell, w.pbc, e_h, f_h, v_h)
+
+    def e2e_step():
+        bop.bop_evaluate_host(ctx.h, pos_h, w.cell, w.pbc, e_h, f_h, v_h)
+
+    h2d, d2h = w.n_atoms * 3 * 8, w.n_atoms * 8 + w.n_atoms * 3 * 8 + 9 * 8
+    if md is not None:
+        e2e_step, h2d, d2h = md[1], md[2], md[3]
+    e2e_step()
     torch.cuda.synchronize()
     te = []
     for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        bop.bop_evaluate_host(ctx.h, pos_h, w.cell, w.pbc, e_h, f_h, v_h)
+        e2e_step()
+        torch.cuda.synchronize()
         te.append(time.perf_counter() - t0)
     e2e_value, _ = aggregate(sum(te) * 1e3, w.n_atoms * steps, world)
 
@@ -258,9 +271,8 @@ def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: s
                    "precision": precision, "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks, "gpu_launches": launches,
-        "e2e": {"value": round(e2e_value, 2), "unit": "atoms/s",
-                "h2d_bytes_per_step": w.n_atoms * 3 * 8,
-                "d2h_bytes_per_step": w.n_atoms * 8 + w.n_atoms * 3 * 8 + 9 * 8},
+        "e2e": {"value": round(e2e_value, 2), "unit": "atoms/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
         "roofline": roof,
         "kernels": {k: {"ms_per_step": round(v["ms"] / steps, 4),
                         "launches_per_step": v["launches"] / steps} for k, v in prof.items() if v["launches"]},
@@ -279,6 +291,8 @@ def run_ours(args):
         dist.barrier()
     if args.workload == "learned131k":
         run_learned(args, bop, I, world, rank)
+    elif args.workload == "md2000":
+        run_md(args, bop, I, world, rank)
     else:
         w = I.workload(args.workload)
         if args.precision == "fp32" and w.run.scf != "none":
@@ -293,6 +307,60 @@ def run_ours(args):
         ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ MD with warm starts
+def run_md(args, bop, I, world: int, rank: int):
+    """NVE molecular dynamics of the 2,000-atom LCN cell (velocity Verlet,
+    1 fs): one step = kick + drift, Hamiltonian, SCF warm-started from the
+    previous step's shifts, exact forces, kick.  Reports atom-steps per
+    second, SCF iterations per step (against the cold start) and the drift
+    of the total energy over the timed steps."""
+    import torch
+    w = I.workload("md2000")
+    if args.precision == "fp32":
+        w = I.with_run(w, scf_tol=FP32_SCF_TOL)
+    dt, mass, n = w.meta["dt"], w.meta["mass"], w.n_atoms
+    ctx = bop.Context(w.model, w.run, args.precision)
+    pos = torch.tensor(w.pos, dtype=torch.float64, device="cuda")
+    vel = torch.tensor(w.meta["vel"], dtype=torch.float64, device="cuda")
+    F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    delta = torch.zeros(n, dtype=torch.float64, device="cuda")
+    ctx.build(pos, w.cell, w.pbc)
+    _, st0 = ctx.energy(delta=delta)
+    F.copy_(ctx.forces()[0])
+    cold = st0["scf_iterations"]
+    iters, energies = [], []
+
+    def kinetic():
+        return 0.5 * mass * float((vel * vel).sum()) / I.EV_PER_AMU
+
+    def step():
+        _, st = ctx.md_step(pos, vel, F, w.cell, w.pbc, dt, mass, delta)
+        iters.append(st["scf_iterations"])
+        energies.append(st["e_total"])
+
+    pos_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+
+    def e2e_step():   # one MD step and a trajectory frame (positions) to the host
+        step()
+        pos_h.copy_(pos, non_blocking=True)
+
+    e_start = st0["e_total"] + kinetic()
+    line = measure(bop, ctx, w, args, world, args.steps, args.warmup, args.precision,
+                   md=(step, e2e_step, 0, n * 3 * 8))
+    e_end = energies[-1] + kinetic()
+    timed = iters[args.warmup:args.warmup + args.steps]
+    line["config"].update({"md": "NVE velocity Verlet, 1 fs, 300 K start, iron mass",
+                           "scf_warm_start": "shifts of the previous step",
+                           "scf_iterations": round(sum(timed) / max(1, len(timed)), 2),
+                           "scf_iterations_cold": cold, "md_steps": len(iters),
+                           "energy_drift_meV_per_atom_over_md_steps": round((e_end - e_start) / n * 1e3, 4)})
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline("d2000")
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 # ------------------------------------------------------------ learned terminator

@@ -117,6 +117,10 @@ enum {
  * moments, follow the atoms; an adjoint linear solve, see bop_forces);
  * 0 = the derivative at fixed onsite levels (the Hellmann-Feynman form of
  * Eq. F_k, which the paper notes is not exact for a non-variational SCF).
+ * rep_A (eV), rep_p (1/A) >= 0: the repulsive energy U_rep of Eq. U_B,
+ * which the paper leaves to empirical functions, as the pair form
+ * sum over bonds of rep_A exp(-rep_p (r - r0)) fcut(r) (the taper of the
+ * bond integrals); each atom's energy holds half of each of its bonds.
  * bandwidth: one of BOP_BW_*; B is floored at 1e-3 eV in every mode (no
  * derivative flows through a floored B).  bw_beta >= 0 (WEIGHTED), bw_a and
  * bw_b > 0 (GLOBAL, eV); ignored otherwise.  The MLP terminator takes
@@ -143,6 +147,7 @@ typedef struct {
   double bw_beta;
   double bw_a, bw_b;
   double j_ii;  /* VARIATIONAL: onsite charging J_ii >= 0 (eV / e^2) */
+  double rep_A, rep_p;  /* pair repulsion (described above): rep_A = 0 for none */
 } bop_model;
 
 typedef struct {
@@ -289,6 +294,24 @@ int bop_get_orbital_state(bop_ctx* ctx, double* mu, double* N, double* U, double
 int bop_evaluate_host(bop_ctx* ctx, int n, const double* pos_host, const double* cell_host,
                       const int* pbc_host, double* e_atom_host, double* forces_host, double* virial_host,
                       double* e_total_host, bop_stats* stats_host, bop_stream stream);
+
+/* One half of a velocity-Verlet step of molecular dynamics on BOP forces
+ * (the MD loop that the warm start of the onsite levels, speed-up (ii) under
+ * "Performance", is meant for: pass the previous step's shifts to
+ * bop_energy as delta_io).  With a = F / mass:
+ *   phase 0: v += a dt / 2, then x += v dt   (before the force evaluation)
+ *   phase 1: v += a dt / 2                   (after it)
+ * Units: positions A, velocities A/fs, forces eV/A, dt fs, mass amu (one
+ * mass for all atoms).  pos, vel, forces: device [n][3], in place; pos may
+ * be NULL for phase 1.  cell_host [3][3] (rows: lattice vectors) and
+ * pbc_host [3], or both NULL: after the drift, an atom that left the cell
+ * along a periodic axis is moved back by whole lattice vectors (atoms
+ * inside are untouched), as bop_build_hamiltonian requires.
+ * Stream-ordered; no synchronisation.
+ * Errors: BOP_ERR_ARG for n < 0, dt <= 0, mass <= 0, a bad phase, a
+ * missing pointer or a singular cell; BOP_ERR_CUDA if the launch fails. */
+int bop_md_verlet(int n, double* pos, double* vel, const double* forces, const double* cell_host,
+                  const int* pbc_host, double dt, double mass, int phase, bop_stream stream);
 
 /* Per-kernel-family timing, for measurement.  While profiling is on, every
  * launch region of the context is bracketed by two CUDA events on the

@@ -42,7 +42,8 @@ class bop_model(ctypes.Structure):
                 ("dos_floor", ctypes.c_double), ("precision", ctypes.c_int), ("mixer", ctypes.c_int),
                 ("mix_history", ctypes.c_int), ("terminator", ctypes.c_int), ("scf_response", ctypes.c_int),
                 ("bandwidth", ctypes.c_int), ("bw_beta", ctypes.c_double), ("bw_a", ctypes.c_double),
-                ("bw_b", ctypes.c_double), ("j_ii", ctypes.c_double)]
+                ("bw_b", ctypes.c_double), ("j_ii", ctypes.c_double), ("rep_A", ctypes.c_double),
+                ("rep_p", ctypes.c_double)]
 
 
 class bop_stats(ctypes.Structure):
@@ -115,6 +116,8 @@ def lib(path: str | None = None):
         "bop_mlp_predict": ([_VP, ctypes.c_longlong, _VP, _VP, _VP], ctypes.c_int),
         "bop_set_mlp": ([_VP, _VP], ctypes.c_int),
         "bop_set_store_budget": ([_VP, ctypes.c_longlong], ctypes.c_int),
+        "bop_md_verlet": ([ctypes.c_int, _VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                           _VP], ctypes.c_int),
         "bop_reset_profile": ([_VP], ctypes.c_int),
         "bop_get_profile": ([_VP, ctypes.POINTER(bop_kernel_time), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
                             ctypes.c_int),
@@ -152,7 +155,7 @@ def make_model(params, run, precision: str = "fp64") -> bop_model:
                      run.scf_tol, run.scf_max_it, run.stoner_I, run.m_mix, run.m0, run.dos_floor,
                      PREC[precision], MIXER[run.mixer], run.mix_history, TERM[run.terminator],
                      1 if run.scf_response else 0, BANDWIDTH[run.bandwidth], run.bw_beta, run.bw_a, run.bw_b,
-                     run.J_ii)
+                     run.J_ii, params.rep_A, params.rep_p)
 
 
 def _check(ctx, st, allow=()):
@@ -291,6 +294,18 @@ def bop_evaluate_host(ctx, pos_host: torch.Tensor, cell, pbc, e_atom_host=None, 
                                         _ptr(e_atom_host), _ptr(forces_host), _ptr(virial_host),
                                         ctypes.cast(ctypes.pointer(et), _VP), ctypes.byref(s), _stream(stream)))
     return et.value, s.as_dict()
+
+
+def bop_md_verlet(pos, vel: torch.Tensor, forces: torch.Tensor, dt: float, mass: float, phase: int,
+                  cell=None, pbc=None, stream=None):
+    """Half of a velocity-Verlet step in place (phase 0: kick + drift, 1:
+    kick); with cell and pbc, atoms that left the cell are moved back."""
+    c = None if cell is None else np.ascontiguousarray(cell, dtype=np.float64).reshape(3, 3)
+    p = None if pbc is None else np.ascontiguousarray(pbc, dtype=np.int32).reshape(3)
+    st = lib().bop_md_verlet(vel.shape[0], _ptr(pos), _ptr(vel), _ptr(forces), _ptr(c), _ptr(p), dt, mass, phase,
+                             _stream(stream))
+    if st != BOP_OK:
+        raise BopError(st, "bop_md_verlet rejected its arguments")
 
 
 def bop_fermi_level_noalloc(gsig_cm: torch.Tensor, a_inf: torch.Tensor, b_inf: torch.Tensor,
@@ -499,6 +514,20 @@ class Context:
 
     def forces(self, stream=None):
         return bop_forces(self.h, self.n, stream)
+
+    def md_step(self, pos, vel, forces, cell, pbc, dt: float, mass: float, delta=None, stream=None):
+        """One velocity-Verlet MD step on the device: kick + drift, new
+        Hamiltonian, energy (warm-started from `delta`, the previous step's
+        shifts, updated in place), forces into `forces`, kick.  pos, vel,
+        forces: device [n][3] float64.  Returns (e_atom, stats)."""
+        bop_md_verlet(pos, vel, forces, dt, mass, 0, cell, pbc, stream)
+        bop_build_hamiltonian(self.h, pos, cell, pbc, stream)
+        self.n = pos.shape[0]
+        e, st = bop_energy(self.h, self.n, delta, None, stream)
+        s = bop_stats()
+        _check(self.h, lib().bop_forces(self.h, _ptr(forces), None, ctypes.byref(s), _stream(stream)))
+        bop_md_verlet(None, vel, forces, dt, mass, 1, stream=stream)
+        return e, st
 
     def evaluate(self, pos, cell, pbc, forces=True) -> Result:
         self.build(pos, cell, pbc)

@@ -79,6 +79,7 @@ struct bop_ctx {
   // variational SCF: dU_B/d delta, q; weights in w valid for the final state
   DBuf vgrad, vq;
   bool var_w_valid = false;
+  DBuf erep;  // pair repulsion per atom
   // stored Psi of every work item for the reverse sweeps (when it fits)
   DBuf psi_off, psis, psib, lsum;
   long long psi_tot = 0;
@@ -230,6 +231,8 @@ int validate_model(bop_ctx* c, const bop_model* m) {
     return fail(c, BOP_ERR_ARG, "bw_beta must be finite and >= 0");
   if (m->bandwidth == BOP_BW_GLOBAL && !(m->bw_b > 0 && m->bw_b < 1e300 && fabs(m->bw_a) < 1e300))
     return fail(c, BOP_ERR_ARG, "bw_a must be finite and bw_b finite and > 0");
+  if (!(m->rep_A >= 0 && m->rep_A < 1e300 && m->rep_p >= 0 && m->rep_p < 1e300))
+    return fail(c, BOP_ERR_ARG, "rep_A and rep_p must be finite and >= 0");
   if (m->terminator == BOP_TERM_MLP && m->bandwidth != BOP_BW_GERSHGORIN)
     return fail(c, BOP_ERR_ARG, "the MLP terminator takes the Gershgorin band width only");
   return BOP_OK;
@@ -962,6 +965,8 @@ int bop_create(bop_ctx** out, const bop_model* model) {
   c->bm.lam = model->lam;
   c->bm.rc = model->rc;
   c->bm.dc = model->dc;
+  c->bm.rep_A = model->rep_A;
+  c->bm.rep_p = model->rep_p;
   cudaGetDevice(&c->device);
   memset(&c->st, 0, sizeof(c->st));
   if ((r = ensure(c, c->status, sizeof(unsigned))) || (r = ensure(c, c->gjack, sizeof(double) * (c->n_exp + 1))) ||
@@ -997,7 +1002,7 @@ int bop_destroy(bop_ctx* c) {
                   &c->adjscr, &c->Hbar, &c->Ebar, &c->status, &c->cub_tmp, &c->nprod,
                   &c->ginv, &c->hx, &c->hf, &c->gamma, &c->scfred, &c->lbase, &c->lnlev, &c->lflag, &c->lxs,
                   &c->lys, &c->lZ1, &c->lH1, &c->lZ2, &c->lH2, &c->lybar, &c->lcot, &c->lxbar, &c->lcount,
-                  &c->rwN, &c->rwt, &c->rdUE, &c->rvec, &c->rcoef, &c->vgrad, &c->vq,
+                  &c->rwN, &c->rwt, &c->rdUE, &c->rvec, &c->rcoef, &c->vgrad, &c->vq, &c->erep,
                   &c->psi_off, &c->psis, &c->psib, &c->lsum};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
@@ -1331,10 +1336,18 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
                           P<double>(c->U), P<double>(c->dos), s))
       return fail(c, BOP_ERR_CUDA, "orbital N/U launch failed");
   }
+  const bool rep = c->m.rep_A != 0.0;
+  if (rep) {
+    CKS(ensure(c, c->erep, sizeof(double) * (size_t)(n > 0 ? n : 1)));
+    Region Rr(c, PK_ENERGY, 1, s);
+    if (launch_rep_energy(n, c->bm, P<long long>(c->row_ptr), P<int>(c->bond_of_edge), P<double>(c->bond_d),
+                          P<double>(c->erep), s))
+      return fail(c, BOP_ERR_CUDA, "repulsion launch failed");
+  }
   {
   Region Re(c, PK_ENERGY, 1, s);
   if (launch_energy(n, c->norb, c->S, c->sfac, c->m.stoner_I, P<double>(c->U), stoner ? P<double>(c->mval) : nullptr,
-                    c->m.j_ii, variational ? P<double>(c->N) : nullptr, c->m.n_e,
+                    c->m.j_ii, variational ? P<double>(c->N) : nullptr, c->m.n_e, rep ? P<double>(c->erep) : nullptr,
                     e_atom ? e_atom : P<double>(c->e_atom), P<double>(c->partials), P<unsigned>(c->counter),
                     P<double>(c->e_total), s))
     return fail(c, BOP_ERR_CUDA, "energy launch failed");

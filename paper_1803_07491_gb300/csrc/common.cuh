@@ -22,6 +22,7 @@ struct BondModel {
   int norb;
   double b0[3];
   double r0, lam, rc, dc;
+  double rep_A, rep_p;  // pair repulsion A e^{-p(r-r0)} fcut(r); A = 0: none
 };
 
 // Cluster of (atom, image) sites around every atom, hop levels in order.
@@ -82,6 +83,19 @@ __device__ __forceinline__ S bond_integral(const BondModel& m, int x, S r) {
   const double PI = 3.14159265358979323846;
   double rv = dval(r);
   S e = m.b0[x] * dexp(-m.lam * (r - m.r0));
+  if (rv < m.rc - m.dc) return e;
+  if (rv > m.rc) return 0.0 * e;
+  S f = 0.5 * (dcos((PI / m.dc) * (r - (m.rc - m.dc))) + 1.0);
+  return e * f;
+}
+
+// Pair repulsion of one bond, A e^{-p (r - r0)} fcut(r), with the taper of
+// the bond integrals.
+template <class S>
+__device__ __forceinline__ S pair_repulsion(const BondModel& m, S r) {
+  const double PI = 3.14159265358979323846;
+  double rv = dval(r);
+  S e = m.rep_A * dexp(-m.rep_p * (r - m.r0));
   if (rv < m.rc - m.dc) return e;
   if (rv > m.rc) return 0.0 * e;
   S f = 0.5 * (dcos((PI / m.dc) * (r - (m.rc - m.dc))) + 1.0);

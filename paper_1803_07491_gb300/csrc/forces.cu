@@ -1,6 +1,7 @@
 // Forces and virial from the bond cotangents (Eq. F_k, Eq. sigma_k): for
 // every bond b with vector d_b = r_j + S.cell - r_i,
 //   g_b = sum_u Hbar_b,u  dH_b,u / dd_b      (u = unique block elements)
+//         + d phi(|d_b|) / dd_b              (pair repulsion, when present)
 //   F_i += g_b,  F_j -= g_b,  W += g_b (x) d_b.
 // dH/dd is exact: the two-centre block is evaluated in forward-mode dual
 // numbers.
@@ -32,6 +33,12 @@ __global__ void __launch_bounds__(FT) k_forces(int nb, BondModel m, const double
       g1 += hb * u[q].g1;
       g2 += hb * u[q].g2;
     }
+    if (m.rep_A != 0.0) {  // pair repulsion of the bond
+      const D3 ph = pair_repulsion(m, dsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+      g0 += ph.g0;
+      g1 += ph.g1;
+      g2 += ph.g2;
+    }
     int i = bond_atoms[2 * b], j = bond_atoms[2 * b + 1];
     atomicAdd(F + 3 * i, g0);
     atomicAdd(F + 3 * i + 1, g1);
@@ -56,7 +63,29 @@ __global__ void __launch_bounds__(FT) k_forces(int nb, BondModel m, const double
   }
 }
 
+// Per-atom pair repulsion: half of every bond of the atom (its directed
+// edges), in edge order.
+__global__ void __launch_bounds__(FT) k_rep_energy(int n, BondModel m, const long long* __restrict__ row_ptr,
+                                                   const int* __restrict__ bond_of_edge,
+                                                   const double* __restrict__ bond_d, double* __restrict__ erep) {
+  const int i = blockIdx.x * FT + threadIdx.x;
+  if (i >= n) return;
+  double e = 0.0;
+  for (long long q = row_ptr[i]; q < row_ptr[i + 1]; q++) {
+    const double* d = bond_d + 3 * (size_t)bond_of_edge[q];
+    e += 0.5 * pair_repulsion(m, sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+  }
+  erep[i] = e;
+}
+
 }  // namespace
+
+int launch_rep_energy(int n, BondModel m, const long long* row_ptr, const int* bond_of_edge, const double* bond_d,
+                      double* erep, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_rep_energy<<<(n + FT - 1) / FT, FT, 0, s>>>(n, m, row_ptr, bond_of_edge, bond_d, erep);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 int launch_forces(int nb, BondModel m, const double* bond_d, const int* bond_atoms, const double* Hbar, int HSu,
                   double* forces, double* virial, cudaStream_t s) {

@@ -193,9 +193,10 @@ void launch_build_onsite(int n, int norb, int n_spin, double onsite0, double sto
                          const double* m, double* onsite, float* onsite32, cudaStream_t s);
 
 // e_i = s sum U (- I m_i^2 / 4 with m) (+ J q_i^2 / 2, q_i = s sum N - n0, with N)
+//       (+ erep_i with erep)
 int launch_energy(int n, int norb, int n_spin, double spin_factor, double stoner_I, const double* U,
-                  const double* m, double J, const double* N, double n0, double* e_atom, double* red,
-                  unsigned* counter, double* e_total, cudaStream_t s);
+                  const double* m, double J, const double* N, double n0, const double* erep, double* e_atom,
+                  double* red, unsigned* counter, double* e_total, cudaStream_t s);
 
 struct WeightArgs {
   int M, n_mom, n_exp, norb;
@@ -290,5 +291,8 @@ int launch_lincomb(int nu, int nvec, const double* V, const double* coef, const 
 int launch_scale_vec(int nu, const double* x, const double* P, double a, double* out, cudaStream_t st);
 
 // forces.cu
+// Pair repulsion per atom (half of each of its bonds) into erep [n].
+int launch_rep_energy(int n, BondModel m, const long long* row_ptr, const int* bond_of_edge, const double* bond_d,
+                      double* erep, cudaStream_t s);
 int launch_forces(int nb, BondModel m, const double* bond_d, const int* bond_atoms, const double* Hbar, int HSu,
                   double* forces, double* virial, cudaStream_t s);

@@ -353,8 +353,8 @@ __global__ void __launch_bounds__(RT) k_build_onsite(int n, int norb, int n_spin
 __global__ void __launch_bounds__(RT) k_energy(int n, int norb, int n_spin, double sfac, double I,
                                                const double* __restrict__ U, const double* __restrict__ m,
                                                double J, const double* __restrict__ N, double n0,
-                                               double* __restrict__ e_atom, double* red, unsigned* counter,
-                                               double* e_total) {
+                                               const double* __restrict__ erep, double* __restrict__ e_atom,
+                                               double* red, unsigned* counter, double* e_total) {
   __shared__ double sh[RT / 32];
   __shared__ bool last;
   double acc = 0.0;
@@ -371,6 +371,7 @@ __global__ void __launch_bounds__(RT) k_energy(int n, int norb, int n_spin, doub
       q = sfac * q - n0;
       e += 0.5 * J * q * q;
     }
+    if (erep) e += erep[i];
     e_atom[i] = e;
     acc += e;
   }
@@ -444,9 +445,9 @@ void launch_build_onsite(int n, int norb, int n_spin, double onsite0, double sto
 }
 
 int launch_energy(int n, int norb, int n_spin, double spin_factor, double stoner_I, const double* U,
-                  const double* m, double J, const double* N, double n0, double* e_atom, double* red,
-                  unsigned* counter, double* e_total, cudaStream_t s) {
-  k_energy<<<red_grid(n), RT, 0, s>>>(n, norb, n_spin, spin_factor, stoner_I, U, m, J, N, n0, e_atom, red,
+                  const double* m, double J, const double* N, double n0, const double* erep, double* e_atom,
+                  double* red, unsigned* counter, double* e_total, cudaStream_t s) {
+  k_energy<<<red_grid(n), RT, 0, s>>>(n, norb, n_spin, spin_factor, stoner_I, U, m, J, N, n0, erep, e_atom, red,
                                       counter, e_total);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
