@@ -124,6 +124,7 @@ class Settings:
     scf_response: bool = True     # forces include the response of the SCF onsite levels
     bandwidth: object = None      # Bandwidth (None: Gershgorin)
     J_ii: float = 0.0             # variational SCF: onsite charging J_ii of Eq. TB-Uion (eV / e^2)
+    r_path: float = 0.0           # path-radius cut (A), 0 = none ("Performance", item (iii))
 
 
 @dataclass
@@ -131,6 +132,22 @@ class Neighbors:
     row_ptr: np.ndarray  # int64 [n+1]
     col: np.ndarray      # int32 [E]
     img: np.ndarray      # int8  [E, 3]
+    # path-radius cut ("Performance", item (iii)): (pos, cell, r_path) or None
+    path: tuple | None = None
+
+    def with_path_radius(self, pos, cell, r_path: float) -> "Neighbors":
+        """The same list with the path-radius cut r_path (<= 0: none)."""
+        if r_path <= 0:
+            return Neighbors(self.row_ptr, self.col, self.img)
+        return Neighbors(self.row_ptr, self.col, self.img,
+                         (np.ascontiguousarray(pos, dtype=np.float64), np.ascontiguousarray(cell, dtype=np.float64),
+                          float(r_path)))
+
+    def _path_args(self):
+        if self.path is None:
+            return None, None, ctypes.c_double(0.0)
+        pos, cell, r = self.path
+        return _p(pos), _p(cell), ctypes.c_double(r)
 
     @property
     def n_edges(self):
@@ -193,7 +210,7 @@ def cluster(i: int, K: int, nbr: Neighbors, max_sites: int = 200000):
     atom = np.zeros(max_sites, np.int32)
     im = np.zeros((max_sites, 3), np.int8)
     lev = np.zeros(K + 1, np.int32)
-    ns = _lib().orc_cluster(int(i), int(K), _p(nbr.row_ptr), _p(nbr.col), _p(nbr.img),
+    ns = _lib().orc_cluster(int(i), int(K), _p(nbr.row_ptr), _p(nbr.col), _p(nbr.img), *nbr._path_args(),
                             int(max_sites), _p(atom), _p(im), _p(lev))
     if ns < 0:
         raise ValueError("image index overflow in cluster")
@@ -212,7 +229,7 @@ def moments(nbr: Neighbors, H, onsite, n_mom: int, sel=None) -> np.ndarray:
     H = np.ascontiguousarray(H, dtype=np.float64)
     mu = np.zeros((len(sel), norb, n_mom))
     st = _lib().orc_moments(len(sel), _p(sel), n_mom, norb, _p(nbr.row_ptr), _p(nbr.col),
-                            _p(nbr.img), _p(H), _p(onsite), _p(mu))
+                            _p(nbr.img), *nbr._path_args(), _p(H), _p(onsite), _p(mu))
     if st != 0:
         raise ValueError("image index overflow in cluster")
     return mu
@@ -229,7 +246,7 @@ def moments_adjoint(nbr: Neighbors, H, onsite, w, sel=None):
     Hbar = np.zeros((nbr.n_edges, norb, norb))
     Ebar = np.zeros((n, norb))
     st = _lib().orc_moments_adjoint(len(sel), _p(sel), n_mom, norb, _p(nbr.row_ptr),
-                                    _p(nbr.col), _p(nbr.img),
+                                    _p(nbr.col), _p(nbr.img), *nbr._path_args(),
                                     _p(np.ascontiguousarray(H, dtype=np.float64)),
                                     _p(onsite), _p(w), _p(Hbar), _p(Ebar))
     if st != 0:
@@ -678,7 +695,7 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
     norb = model.norb
     S = st.n_spin
     s = 2.0 if S == 1 else 1.0
-    nbr = neighbors(pos, cell, pbc, model.rc)
+    nbr = neighbors(pos, cell, pbc, model.rc).with_path_radius(pos, cell, st.r_path)
     H = blocks(model, pos, cell, nbr)
     delta = np.zeros(n) if delta0 is None else np.array(delta0, np.float64)
     m = None

@@ -289,12 +289,22 @@ static int cmp_u64(const void *a, const void *b) {
   return x < y ? -1 : (x > y);
 }
 
-/* C_0 = {(i,0)}; C_k = C_{k-1} plus every neighbour of a site of C_{k-1}.
- * Only the frontier C_{k-1} \ C_{k-2} can add new sites.  New sites of a
- * level are appended in ascending (atom, sx, sy, sz) order.
+/* Path-radius cut ("Performance", item (iii)): with rpath > 0 only sites
+ * closer than rpath to atom i (distance by the arithmetic of the neighbour
+ * test) join the cluster, so paths that leave that sphere are dropped.
+ * pos, cell may be NULL when rpath <= 0. */
+typedef struct {
+  const double *pos, *cell;
+  double r2; /* rpath^2, or <= 0 for no cut */
+} pathcut;
+
+/* C_0 = {(i,0)}; C_k = C_{k-1} plus every neighbour of a site of C_{k-1}
+ * (inside the path radius when one is set).  Only the frontier
+ * C_{k-1} \ C_{k-2} can add new sites.  New sites of a level are appended
+ * in ascending (atom, sx, sy, sz) order.
  * Returns 0, or -1 if an image index leaves [-127, 127]. */
 static int build_cluster(cluster *c, int i, int K, const long *row_ptr,
-                         const int *col, const signed char *img) {
+                         const int *col, const signed char *img, pathcut pc) {
   long cap = 64, nsite = 1;
   c->K = K;
   c->level_end = (int *)malloc(sizeof(int) * (K + 1));
@@ -323,6 +333,10 @@ static int build_cluster(cluster *c, int i, int K, const long *row_ptr,
         }
         uint64_t key = site_key(col[e], sx, sy, sz);
         if (hm_get(&c->map, key) >= 0 || hm_get(&seen, key) >= 0) continue;
+        if (pc.r2 > 0.0) {
+          double d[3];
+          if (!pair_in_range(pc.pos + 3 * i, pc.pos + 3 * col[e], pc.cell, sx, sy, sz, pc.r2, d)) continue;
+        }
         if (nnew == newcap) {
           newcap *= 2;
           nk = (uint64_t *)realloc(nk, sizeof(uint64_t) * newcap);
@@ -390,10 +404,11 @@ static int neighbour_site(const cluster *c, int t, long e, const int *col,
  * max_sites sites (atom, image) and the K+1 level ends.  Returns the number
  * of sites, or -1 on an image overflow. */
 int orc_cluster(int i, int K, const long *row_ptr, const int *col,
-                const signed char *img, int max_sites, int *site_atom,
-                signed char *site_img, int *level_end) {
+                const signed char *img, const double *pos, const double *cell, double rpath,
+                int max_sites, int *site_atom, signed char *site_img, int *level_end) {
   cluster c;
-  if (build_cluster(&c, i, K, row_ptr, col, img) < 0) {
+  pathcut pc = {pos, cell, rpath > 0.0 ? rpath * rpath : 0.0};
+  if (build_cluster(&c, i, K, row_ptr, col, img, pc) < 0) {
     free_cluster(&c);
     return -1;
   }
@@ -444,13 +459,14 @@ static double dot(const double *x, const double *y, long n) {
  * onsite: [n][norb] for one spin channel.  mu: [nsel][norb][n_mom].
  * Returns 0, or -1 on an image overflow. */
 int orc_moments(int nsel, const int *sel, int n_mom, int norb, const long *row_ptr,
-                const int *col, const signed char *img, const double *H,
-                const double *onsite, double *mu) {
+                const int *col, const signed char *img, const double *pos, const double *cell,
+                double rpath, const double *H, const double *onsite, double *mu) {
   int K = (n_mom - 1) / 2, status = 0;
+  pathcut pc = {pos, cell, rpath > 0.0 ? rpath * rpath : 0.0};
   for (int q = 0; q < nsel; q++) {
     int i = sel[q];
     cluster c;
-    if (build_cluster(&c, i, K, row_ptr, col, img) < 0) status = -1;
+    if (build_cluster(&c, i, K, row_ptr, col, img, pc) < 0) status = -1;
     long len = (long)c.nsite * norb;
     double *prev = (double *)calloc(len, sizeof(double));
     double *cur = (double *)calloc(len, sizeof(double));
@@ -481,13 +497,15 @@ int orc_moments(int nsel, const int *sel, int n_mom, int norb, const long *row_p
  *   Ebar[a][b]    = dU/dE_{a b}    for every onsite level. */
 int orc_moments_adjoint(int nsel, const int *sel, int n_mom, int norb,
                         const long *row_ptr, const int *col, const signed char *img,
+                        const double *pos, const double *cell, double rpath,
                         const double *H, const double *onsite, const double *w,
                         double *Hbar, double *Ebar) {
   int K = (n_mom - 1) / 2, nb = norb * norb, status = 0;
+  pathcut pc = {pos, cell, rpath > 0.0 ? rpath * rpath : 0.0};
   for (int q = 0; q < nsel; q++) {
     int i = sel[q];
     cluster c;
-    if (build_cluster(&c, i, K, row_ptr, col, img) < 0) status = -1;
+    if (build_cluster(&c, i, K, row_ptr, col, img, pc) < 0) status = -1;
     long len = (long)c.nsite * norb;
     double *psi = (double *)calloc(len * (K + 1), sizeof(double)); /* Psi_0..Psi_K */
     double *bar = (double *)calloc(len, sizeof(double));

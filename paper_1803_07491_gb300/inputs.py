@@ -106,6 +106,7 @@ class RunParams:
     bw_a: float = 0.0             # global: A (eV)
     bw_b: float = 1.0             # global: B (eV)
     J_ii: float = 0.0             # variational SCF: onsite charging energy J_ii q_i^2 / 2 (eV / e^2)
+    r_path: float = 0.0           # path-radius cut (A): only sites closer than r_path to the atom; 0 = none
 
 
 @dataclass

@@ -33,4 +33,5 @@ def oracle_settings(r):
                         stoner_I=r.stoner_I, m_mix=r.m_mix, m0=r.m0, dos_floor=r.dos_floor,
                         mixer=r.mixer, mix_history=r.mix_history, scf_response=r.scf_response,
                         bandwidth=None if r.bandwidth == "gershgorin" else
-                        bop.Bandwidth(r.bandwidth, r.bw_beta, r.bw_a, r.bw_b), J_ii=r.J_ii)
+                        bop.Bandwidth(r.bandwidth, r.bw_beta, r.bw_a, r.bw_b), J_ii=r.J_ii,
+                        r_path=r.r_path)
