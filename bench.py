@@ -267,6 +267,7 @@ def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: s
                               else "exact: SCF response included" if stats["forces_scf_response"]
                               else "fixed onsite levels (Hellmann-Feynman form)"),
                    **({"J_ii": w.run.J_ii} if w.run.scf == "variational" else {}),
+                   **({"r_path": w.run.r_path} if w.run.r_path > 0 else {}),
                    "response_iterations": stats["response_iterations"],
                    "precision": precision, "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
@@ -467,7 +468,7 @@ def profile_traffic(family: str):
 def sample_settings(workload: str):
     """Run settings of a 2,000-atom bcc workload (d2000 for the others)."""
     from paper_1803_07491_gb300 import inputs as I
-    return I.workload(workload if workload in ("d2000", "d2000nscf", "d2000var") else "d2000").run
+    return I.workload(workload if workload in ("d2000", "d2000nscf", "d2000var", "d2000cut") else "d2000").run
 
 
 def oracle_sample(n_cells: int, workload: str = "d2000"):
@@ -484,7 +485,8 @@ def oracle_sample(n_cells: int, workload: str = "d2000"):
     t0 = time.perf_counter()
     ob.evaluate(ob.Model(p.norb, tuple(p.b0), p.r0, p.lam, p.rc, p.dc, p.onsite0),
                 ob.Settings(n_e=r.n_e, n_mom=r.n_mom, n_exp=r.n_exp, scf=r.scf, eta=r.eta, scf_tol=r.scf_tol,
-                            scf_max_it=r.scf_max_it, mixer=r.mixer, mix_history=r.mix_history, J_ii=r.J_ii),
+                            scf_max_it=r.scf_max_it, mixer=r.mixer, mix_history=r.mix_history, J_ii=r.J_ii,
+                            r_path=r.r_path),
                 pos, cell, (1, 1, 1))
     return len(pos), time.perf_counter() - t0
 

@@ -121,6 +121,11 @@ enum {
  * which the paper leaves to empirical functions, as the pair form
  * sum over bonds of rep_A exp(-rep_p (r - r0)) fcut(r) (the taper of the
  * bond integrals); each atom's energy holds half of each of its bonds.
+ * r_path > 0: the path-radius cut of "Performance", item (iii): the
+ * cluster of atom i keeps only the sites (atom, image) closer than r_path
+ * to i, so the moments count only the self-returning paths that stay
+ * inside that sphere (an extra approximation; the energy jumps where a site
+ * crosses the sphere, and forces are the derivative between such jumps).
  * bandwidth: one of BOP_BW_*; B is floored at 1e-3 eV in every mode (no
  * derivative flows through a floored B).  bw_beta >= 0 (WEIGHTED), bw_a and
  * bw_b > 0 (GLOBAL, eV); ignored otherwise.  The MLP terminator takes
@@ -148,6 +153,7 @@ typedef struct {
   double bw_a, bw_b;
   double j_ii;  /* VARIATIONAL: onsite charging J_ii >= 0 (eV / e^2) */
   double rep_A, rep_p;  /* pair repulsion (described above): rep_A = 0 for none */
+  double r_path;        /* path-radius cut in A (described above): 0 for none */
 } bop_model;
 
 typedef struct {

@@ -43,7 +43,7 @@ class bop_model(ctypes.Structure):
                 ("mix_history", ctypes.c_int), ("terminator", ctypes.c_int), ("scf_response", ctypes.c_int),
                 ("bandwidth", ctypes.c_int), ("bw_beta", ctypes.c_double), ("bw_a", ctypes.c_double),
                 ("bw_b", ctypes.c_double), ("j_ii", ctypes.c_double), ("rep_A", ctypes.c_double),
-                ("rep_p", ctypes.c_double)]
+                ("rep_p", ctypes.c_double), ("r_path", ctypes.c_double)]
 
 
 class bop_stats(ctypes.Structure):
@@ -155,7 +155,7 @@ def make_model(params, run, precision: str = "fp64") -> bop_model:
                      run.scf_tol, run.scf_max_it, run.stoner_I, run.m_mix, run.m0, run.dos_floor,
                      PREC[precision], MIXER[run.mixer], run.mix_history, TERM[run.terminator],
                      1 if run.scf_response else 0, BANDWIDTH[run.bandwidth], run.bw_beta, run.bw_a, run.bw_b,
-                     run.J_ii, params.rep_A, params.rep_p)
+                     run.J_ii, params.rep_A, params.rep_p, run.r_path)
 
 
 def _check(ctx, st, allow=()):

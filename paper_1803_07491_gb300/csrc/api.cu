@@ -231,6 +231,7 @@ int validate_model(bop_ctx* c, const bop_model* m) {
     return fail(c, BOP_ERR_ARG, "bw_beta must be finite and >= 0");
   if (m->bandwidth == BOP_BW_GLOBAL && !(m->bw_b > 0 && m->bw_b < 1e300 && fabs(m->bw_a) < 1e300))
     return fail(c, BOP_ERR_ARG, "bw_a must be finite and bw_b finite and > 0");
+  if (!(m->r_path >= 0 && m->r_path < 1e300)) return fail(c, BOP_ERR_ARG, "r_path must be finite and >= 0");
   if (!(m->rep_A >= 0 && m->rep_A < 1e300 && m->rep_p >= 0 && m->rep_p < 1e300))
     return fail(c, BOP_ERR_ARG, "rep_A and rep_p must be finite and >= 0");
   if (m->terminator == BOP_TERM_MLP && m->bandwidth != BOP_BW_GERSHGORIN)
@@ -304,6 +305,10 @@ int build_clusters(bop_ctx* c, cudaStream_t s) {
     CK(cudaMemsetAsync(c->max_level.p, 0, sizeof(int) * (K + 2), s));
     ClusterScratch sc{P<unsigned long long>(c->hkeys), P<int>(c->hvals), P<unsigned long long>(c->skeys),
                       P<int>(c->sslot), P<int>(c->scount), hcap, maxs, newcap};
+    PathCut pc;
+    pc.pos = P<double>(c->pos);
+    for (int q = 0; q < 9; q++) pc.cell[q] = c->g.cell[q];
+    pc.r2 = c->m.r_path > 0 ? c->m.r_path * c->m.r_path : 0.0;
     ClusterOut out{};
     out.level_end = P<int>(c->level_end);
     out.atom_nsite = P<int>(c->atom_nsite);
@@ -312,7 +317,7 @@ int build_clusters(bop_ctx* c, cudaStream_t s) {
     {
     Region R0(c, PK_CLUSTER, 1, s);
     if (launch_cluster(0, n, K, P<long long>(c->row_ptr), P<int>(c->col), P<signed char>(c->img),
-                       P<int>(c->bond_of_edge), sc, out, grid, P<unsigned>(c->status), s))
+                       P<int>(c->bond_of_edge), pc, sc, out, grid, P<unsigned>(c->status), s))
       return fail(c, BOP_ERR_CUDA, "cluster pass 0 launch failed");
     }
     unsigned h = 0;
@@ -353,7 +358,7 @@ int build_clusters(bop_ctx* c, cudaStream_t s) {
     {
     Region R1(c, PK_CLUSTER, 1, s);
     if (launch_cluster(1, n, K, P<long long>(c->row_ptr), P<int>(c->col), P<signed char>(c->img),
-                       P<int>(c->bond_of_edge), sc, out, grid, P<unsigned>(c->status), s))
+                       P<int>(c->bond_of_edge), pc, sc, out, grid, P<unsigned>(c->status), s))
       return fail(c, BOP_ERR_CUDA, "cluster pass 1 launch failed");
     }
     CK(cudaMemcpyAsync(P<long long>(c->adj_off) + c->nsite, P<long long>(c->adj_base) + n, sizeof(long long),

@@ -1,7 +1,8 @@
 // Hop levels of (atom, image) sites around every atom: the support of the
 // self-returning paths of Eq. momDOS (C_0 = {i}, C_k = C_{k-1} plus all
-// neighbours of C_{k-1}), with the adjacency between cluster sites that the
-// moments kernels walk.
+// neighbours of C_{k-1}, inside the path radius when one is set:
+// "Performance", item (iii)), with the adjacency between cluster sites that
+// the moments kernels walk.
 //
 // Canonical order (reproducible bit for bit): level, then atom, then image
 // (sx, sy, sz).  Each site's adjacency lists every neighbour inside the
@@ -114,7 +115,7 @@ __device__ int block_exclusive_scan(int* v, int cnt, int* warp_tmp) {
 template <int PASS>
 __global__ void __launch_bounds__(CL_THREADS)
 k_cluster(int n, int K, const long long* __restrict__ row_ptr, const int* __restrict__ col,
-          const signed char* __restrict__ img, const int* __restrict__ bond_of_edge, ClusterScratch sc,
+          const signed char* __restrict__ img, const int* __restrict__ bond_of_edge, PathCut pc, ClusterScratch sc,
           ClusterOut out, unsigned* __restrict__ status) {
   extern __shared__ unsigned long long newkeys[];  // [newcap], a power of two
   __shared__ int s_count, s_fail;
@@ -158,6 +159,11 @@ k_cluster(int n, int K, const long long* __restrict__ row_ptr, const int* __rest
             s_fail = 1;
             raise_error(status, BOP_DEV_ERR_IMAGE);
             continue;
+          }
+          if (pc.r2 > 0.0) {  // path-radius cut: only sites closer than r_path to the atom
+            double d[3];
+            bond_vector(pc.pos + 3 * (size_t)atom, pc.pos + 3 * (size_t)col[e], pc.cell, sx, sy, sz, d);
+            if (!(norm2_rn(d) < pc.r2)) continue;
           }
           unsigned long long key = site_key(col[e], sx, sy, sz);
           int r = h_insert(hk, sc.hcap, key);
@@ -300,17 +306,17 @@ k_cluster(int n, int K, const long long* __restrict__ row_ptr, const int* __rest
 }  // namespace
 
 int launch_cluster(int pass, int n, int K, const long long* row_ptr, const int* col, const signed char* img,
-                   const int* bond_of_edge, ClusterScratch sc, ClusterOut out, int grid, unsigned* status,
-                   cudaStream_t s) {
+                   const int* bond_of_edge, PathCut pc, ClusterScratch sc, ClusterOut out, int grid,
+                   unsigned* status, cudaStream_t s) {
   size_t smem = (size_t)sc.newcap * sizeof(unsigned long long);  // newcap is a power of two
   if (smem > 48 * 1024) {
     auto fn = pass == 0 ? k_cluster<0> : k_cluster<1>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   if (pass == 0)
-    k_cluster<0><<<grid, CL_THREADS, smem, s>>>(n, K, row_ptr, col, img, bond_of_edge, sc, out, status);
+    k_cluster<0><<<grid, CL_THREADS, smem, s>>>(n, K, row_ptr, col, img, bond_of_edge, pc, sc, out, status);
   else
-    k_cluster<1><<<grid, CL_THREADS, smem, s>>>(n, K, row_ptr, col, img, bond_of_edge, sc, out, status);
+    k_cluster<1><<<grid, CL_THREADS, smem, s>>>(n, K, row_ptr, col, img, bond_of_edge, pc, sc, out, status);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -59,9 +59,16 @@ __global__ void k_frac_range(int n, const double* pos, Geometry g, double* out);
 void launch_neighbors(int mode, int n, const double* pos, Geometry g, const int* cell_of, const int* cell_start,
                       const int* cell_atoms, int* deg, const long long* row_ptr, int* col, signed char* img,
                       unsigned* status, cudaStream_t s);
+// Path-radius cut: with r2 > 0 only sites closer than sqrt(r2) to the
+// cluster's atom (bond_vector arithmetic) join its cluster.
+struct PathCut {
+  const double* pos;  // [n][3] device
+  double cell[9];
+  double r2;
+};
 int launch_cluster(int pass, int n, int K, const long long* row_ptr, const int* col, const signed char* img,
-                   const int* bond_of_edge, ClusterScratch sc, ClusterOut out, int grid, unsigned* status,
-                   cudaStream_t s);
+                   const int* bond_of_edge, PathCut pc, ClusterScratch sc, ClusterOut out, int grid,
+                   unsigned* status, cudaStream_t s);
 
 void launch_level_sums(int n, int K, const int* level_end, long long* out, cudaStream_t s);
 

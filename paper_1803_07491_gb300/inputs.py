@@ -187,6 +187,8 @@ def workload(name: str) -> Workload:
               N_d = 6.8; local charge neutrality (Anderson, ANDERSON_STEP);
               9 moments.
     d2000nscf the same cell without SCF (fixed onsite levels).
+    d2000cut  d2000 with the path-radius cut at 5.5 A (five neighbour shells;
+              "Performance", item (iii)).
     d2000var  the same cell with the variational SCF (Eq. BOP_SCF), J_ii =
               20 eV / e^2 (Anderson, ANDERSON_STEP); with J_ii = 2 the minimum
               of this cell sits on a kink of the Gershgorin estimate and the
@@ -211,11 +213,13 @@ def workload(name: str) -> Workload:
     if name == "s128":
         pos, cell = bcc_jittered(4, 4, 4, 0.05, 1)
         return Workload(name, pos, cell, (1, 1, 1), MODEL_S, RunParams(n_e=0.7))
-    if name in ("d2000", "d2000nscf", "d2000var"):
+    if name in ("d2000", "d2000nscf", "d2000var", "d2000cut"):
         pos, cell = bcc_jittered(10, 10, 10, 0.05, 2)
-        scf = {"d2000": "lcn", "d2000nscf": "none", "d2000var": "variational"}[name]
+        scf = {"d2000": "lcn", "d2000nscf": "none", "d2000var": "variational", "d2000cut": "lcn"}[name]
         J = 20.0 if name == "d2000var" else 0.0
-        return Workload(name, pos, cell, (1, 1, 1), MODEL_D, RunParams(n_e=6.8, scf=scf, J_ii=J, **ANDERSON_STEP))
+        r_path = 5.5 if name == "d2000cut" else 0.0
+        return Workload(name, pos, cell, (1, 1, 1), MODEL_D,
+                        RunParams(n_e=6.8, scf=scf, J_ii=J, r_path=r_path, **ANDERSON_STEP))
     if name == "slab16k":
         pos, cell, pbc = slab_with_vacancies(16, 16, 32, 64, 0.08, 3)
         return Workload(name, pos, cell, pbc, MODEL_D, RunParams(n_e=6.8, n_mom=13))
