@@ -78,15 +78,18 @@ def _p(a):
 
 class _CModel(ctypes.Structure):
     _fields_ = [("norb", ctypes.c_int), ("r0", ctypes.c_double), ("lam", ctypes.c_double),
-                ("rc", ctypes.c_double), ("dc", ctypes.c_double), ("b0", ctypes.c_double * 3)]
+                ("rc", ctypes.c_double), ("dc", ctypes.c_double), ("b0", ctypes.c_double * 5)]
 
 
 @dataclass
 class Model:
     """Orthogonal two-centre TB model of one element (Eq. Hij, Eq. cutoff).
 
-    beta_x(r) = b0[x] * exp(-lam (r - r0)) * fcut(r); b0 = (ss sigma,) for s
-    or (dd sigma, dd pi, dd delta) for d, in eV at r0 (Angstrom)."""
+    beta_x(r) = b0[x] * exp(-lam (r - r0)) * fcut(r); b0 = (ss sigma,) for s,
+    (dd sigma, dd pi, dd delta) for d, or (dd sigma, dd pi, dd delta,
+    ss sigma, sd sigma) for sd (norb 6, s first), in eV at r0 (Angstrom).
+    onsite_s: the reference level of the s orbital of an sd model (the d
+    orbitals take onsite0)."""
     norb: int
     b0: tuple
     r0: float
@@ -96,10 +99,11 @@ class Model:
     onsite0: float = 0.0
     rep_A: float = 0.0    # repulsive energy U_rep (Eq. U_B) as a pair form, see pair_repulsion
     rep_p: float = 0.0
+    onsite_s: float = 0.0
 
     def c(self) -> _CModel:
-        b = list(self.b0) + [0.0] * (3 - len(self.b0))
-        return _CModel(self.norb, self.r0, self.lam, self.rc, self.dc, (ctypes.c_double * 3)(*b))
+        b = list(self.b0) + [0.0] * (5 - len(self.b0))
+        return _CModel(self.norb, self.r0, self.lam, self.rc, self.dc, (ctypes.c_double * 5)(*b))
 
 
 @dataclass
@@ -716,6 +720,8 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
         onsite = np.zeros((S, n, norb))
         for v in range(S):
             onsite[v] = model.onsite0 + delta[:, None]
+            if norb == 6:
+                onsite[v][:, 0] = model.onsite_s + delta
             if st.scf == "stoner":
                 sign = -1.0 if v == 0 else 1.0
                 onsite[v] += sign * 0.5 * st.stoner_I * m[:, None]

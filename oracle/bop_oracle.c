@@ -45,13 +45,15 @@ typedef double complex cplx;
 
 static const double PI = 3.14159265358979323846;
 
-/* Model of one element.  norb = 1 (s) or 5 (d).  b0[] holds the bond
- * integrals at r0: s -> {ss sigma}, d -> {dd sigma, dd pi, dd delta}.
- * beta(r) = b0 * exp(-lam (r - r0)) * fcut(r)  (exponential form). */
+/* Model of one element.  norb = 1 (s), 5 (d) or 6 (sd: s first, then the
+ * five d orbitals).  b0[] holds the bond integrals at r0: s -> {ss sigma},
+ * d -> {dd sigma, dd pi, dd delta}, sd -> {dd sigma, dd pi, dd delta,
+ * ss sigma, sd sigma}.  beta(r) = b0 * exp(-lam (r - r0)) * fcut(r)
+ * (exponential form). */
 typedef struct {
   int norb;
   double r0, lam, rc, dc;
-  double b0[3];
+  double b0[5];
 } orc_model;
 
 /* ------------------------------------------------------------------ */
@@ -165,22 +167,53 @@ static cplx bond_integral(const orc_model *m, int x, cplx r) {
   return m->b0[x] * cexp(-m->lam * (r - m->r0)) * fcut(m, r);
 }
 
+static void d_block(const orc_model *m, const cplx *d, cplx r, cplx E[5][5]);
+
 /* Block <i beta|H|j gamma> for the bond vector d = r_j - r_i.
  * d orbitals ordered d_{3z^2-r^2}, d_zx, d_yz, d_{x^2-y^2}, d_xy (the order
- * stated under Eq. Hij).  Output row-major [beta][gamma]. */
+ * stated under Eq. Hij); sd blocks put s first.  Output row-major
+ * [beta][gamma]. */
 void orc_block_c(const orc_model *m, const cplx *d, cplx *B) {
   cplx r = csqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
   if (m->norb == 1) {
     B[0] = bond_integral(m, 0, r);
     return;
   }
+  cplx E[5][5];
+  d_block(m, d, r, E);
+  if (m->norb == 5) {
+    for (int b = 0; b < 5; b++)
+      for (int g = 0; g < 5; g++) B[b * 5 + g] = E[b][g];
+    return;
+  }
+  /* sd: the s-d elements of the Slater-Koster table, each an even function
+   * of the direction cosines, so <s|H|d> = <d|H|s> and the block is
+   * symmetric. */
+  cplx ss = bond_integral(m, 3, r), sd = bond_integral(m, 4, r);
+  cplx l = d[0] / r, mm = d[1] / r, n = d[2] / r;
+  const double r3 = sqrt(3.0);
+  cplx f[5];
+  f[0] = (n * n - 0.5 * (l * l + mm * mm)) * sd; /* 3z^2 - r^2 */
+  f[1] = r3 * n * l * sd;                         /* zx */
+  f[2] = r3 * mm * n * sd;                        /* yz */
+  f[3] = 0.5 * r3 * (l * l - mm * mm) * sd;       /* x^2 - y^2 */
+  f[4] = r3 * l * mm * sd;                        /* xy */
+  B[0] = ss;
+  for (int g = 0; g < 5; g++) {
+    B[1 + g] = f[g];
+    B[(1 + g) * 6] = f[g];
+    for (int b = 0; b < 5; b++) B[(1 + b) * 6 + 1 + g] = E[b][g];
+  }
+}
+
+/* The 5x5 d-d block (dd sigma, pi, delta = b0[0..2]). */
+static void d_block(const orc_model *m, const cplx *d, cplx r, cplx E[5][5]) {
   cplx s = bond_integral(m, 0, r), p = bond_integral(m, 1, r),
        t = bond_integral(m, 2, r); /* sigma, pi, delta */
   cplx l = d[0] / r, mm = d[1] / r, n = d[2] / r;
   cplx L = l * l, M = mm * mm, N = n * n;
   const double r3 = sqrt(3.0);
   enum { Z2 = 0, ZX = 1, YZ = 2, X2Y2 = 3, XY = 4 };
-  cplx E[5][5];
   E[XY][XY] = 3.0 * L * M * s + (L + M - 4.0 * L * M) * p + (N + L * M) * t;
   E[YZ][YZ] = 3.0 * M * N * s + (M + N - 4.0 * M * N) * p + (L + M * N) * t;
   E[ZX][ZX] = 3.0 * N * L * s + (N + L - 4.0 * N * L) * p + (M + N * L) * t;
@@ -209,13 +242,11 @@ void orc_block_c(const orc_model *m, const cplx *d, cplx *B) {
   const int pairs[10][2] = {{XY, YZ}, {YZ, ZX}, {ZX, XY}, {XY, X2Y2}, {YZ, X2Y2},
                             {ZX, X2Y2}, {XY, Z2}, {YZ, Z2}, {ZX, Z2}, {X2Y2, Z2}};
   for (int q = 0; q < 10; q++) E[pairs[q][1]][pairs[q][0]] = E[pairs[q][0]][pairs[q][1]];
-  for (int b = 0; b < 5; b++)
-    for (int g = 0; g < 5; g++) B[b * 5 + g] = E[b][g];
 }
 
 /* Real-valued block for a bond vector d (used by the tests directly). */
 void orc_block(const orc_model *m, const double *d, double *B) {
-  cplx dc[3] = {d[0], d[1], d[2]}, Bc[25];
+  cplx dc[3] = {d[0], d[1], d[2]}, Bc[36];
   orc_block_c(m, dc, Bc);
   for (int q = 0; q < m->norb * m->norb; q++) B[q] = creal(Bc[q]);
 }
@@ -574,7 +605,7 @@ void orc_bond_gradient(int n, const double *pos, const double *cell, const long 
       double d[3];
       edge_vector(pos, cell, i, col[e], img + 3 * e, d);
       for (int c = 0; c < 3; c++) {
-        cplx dc[3] = {d[0], d[1], d[2]}, B[25];
+        cplx dc[3] = {d[0], d[1], d[2]}, B[36];
         dc[c] += h * I;
         orc_block_c(m, dc, B);
         double acc = 0.0;

@@ -60,7 +60,8 @@ def jittered(pos, cell, pbc, sigma: float, rng):
 class ModelParams:
     """Exponential two-centre bond integrals with a cosine taper."""
     norb: int          # 1 = s, 5 = d
-    b0: tuple          # eV at r0: (ss sigma,) or (dd sigma, dd pi, dd delta)
+    b0: tuple          # eV at r0: (ss sigma,), (dd sigma, dd pi, dd delta) or, for sd,
+    #                    (dd sigma, dd pi, dd delta, ss sigma, sd sigma)
     r0: float          # Angstrom
     lam: float         # 1/Angstrom
     rc: float          # cutoff radius, Angstrom
@@ -68,6 +69,7 @@ class ModelParams:
     onsite0: float = 0.0
     rep_A: float = 0.0   # pair repulsion rep_A exp(-rep_p (r - r0)) fcut(r), eV; 0 = none
     rep_p: float = 0.0   # 1/Angstrom
+    onsite_s: float = 0.0  # sd model (norb 6): reference level of the s orbital, eV
 
 
 # s-valent model: ss sigma = -1.0 eV exp(-1.5 (r - 2.48)), taper 3.2-3.6 A
@@ -75,6 +77,11 @@ MODEL_S = ModelParams(norb=1, b0=(-1.0,), r0=2.48, lam=1.5, rc=3.6, dc=0.4)
 # canonical d model: sigma:pi:delta = -6:4:-1 scaled to dd sigma(2.48) = -0.9 eV,
 # exp decay 1.8/A, cutoff 3.6 A with a 0.4 A taper (1st + 2nd bcc shells)
 MODEL_D = ModelParams(norb=5, b0=(-0.9, 0.6, -0.15), r0=2.48, lam=1.8, rc=3.6, dc=0.4)
+# sd-valent model (norb 6, s first): the canonical d block plus ss sigma =
+# -1.4 eV and sd sigma = -0.7 eV at r0 with the same decay, s level 3 eV
+# above the d level
+MODEL_SD = ModelParams(norb=6, b0=(-0.9, 0.6, -0.15, -1.4, -0.7), r0=2.48, lam=1.8, rc=3.6, dc=0.4,
+                       onsite_s=3.0)
 # the same with a pair repulsion decaying twice as fast as the bond integrals,
 # its amplitude chosen so that perfect bcc of the cells below has zero
 # pressure without SCF (a stable lattice for MD; checked by the oracle tests)
@@ -264,7 +271,7 @@ def small_bcc(n1, n2, n3, sigma, seed, model=MODEL_D, run=None, pbc=(1, 1, 1)):
     pos, cell = bcc_cell(n1, n2, n3)
     rng = np.random.default_rng(seed)
     pos = jittered(pos, cell, pbc, sigma, rng)
-    run = run or RunParams(n_e=6.8 if model.norb == 5 else 0.7)
+    run = run or RunParams(n_e={1: 0.7, 5: 6.8, 6: 8.0}[model.norb])
     return Workload(f"bcc{n1}x{n2}x{n3}", pos, cell, tuple(pbc), model, run)
 
 

@@ -23,7 +23,7 @@ def ob():
 
 def oracle_model(p):
     from oracle import bop
-    return bop.Model(p.norb, tuple(p.b0), p.r0, p.lam, p.rc, p.dc, p.onsite0, p.rep_A, p.rep_p)
+    return bop.Model(p.norb, tuple(p.b0), p.r0, p.lam, p.rc, p.dc, p.onsite0, p.rep_A, p.rep_p, p.onsite_s)
 
 
 def oracle_settings(r):
