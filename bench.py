@@ -249,7 +249,8 @@ def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: s
     if flops is not None:
         achieved = flops / (per_region_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": fam, "achieved": round(achieved, 4), "peak": round(peak, 3),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": profile_traffic(fam),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "traffic": profile_traffic(fam, args.workload),
                 "peak_source": "derived: SMs x lanes x 2 x max SM clock (FP64 for the scalar stages)",
                 "region_ms": round(per_region_ms, 4)}
     return {
@@ -452,14 +453,15 @@ def stats_products(ctx, bop) -> int:
     return st.get("moment_products", 0)
 
 
-def profile_traffic(family: str):
-    """DRAM bytes per launch region of the family from the committed ncu
-    summary (profiles/traffic.json), or None."""
+def profile_traffic(family: str, workload: str):
+    """DRAM bytes per launch region of the family on this workload from the
+    committed ncu summary (profiles/traffic.json), or None (not captured for
+    this workload's kernel instantiation)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:
-        return json.load(open(p)).get(family)
+        return json.load(open(p)).get(workload, {}).get(family)
     except (ValueError, OSError):
         return None
 

@@ -83,8 +83,12 @@ enum {
 
 /* Model and run settings.
  * beta_x(r) = b0[x] * exp(-lam (r - r0)) * fcut(r), fcut the cosine taper
- * of Eq. cutoff on [rc - dc, rc]; b0 = {ss sigma} (norb 1) or
- * {dd sigma, dd pi, dd delta} (norb 5) in eV at r0.
+ * of Eq. cutoff on [rc - dc, rc]; b0 = {ss sigma} (norb 1),
+ * {dd sigma, dd pi, dd delta} (norb 5) or {dd sigma, dd pi, dd delta,
+ * ss sigma, sd sigma} (norb 6: sd-valent, the s orbital first, then the d
+ * orbitals in the order 3z^2-r^2, zx, yz, x^2-y^2, xy) in eV at r0; unused
+ * entries are ignored.  Onsite reference levels: onsite0 for every orbital,
+ * except onsite_s for the s orbital of an sd model.
  * n_mom odd in [3, 17]; n_exp in [n_mom - 1, 253].
  * n_e: electrons per atom summed over spin.  n_spin 1 (non-magnetic, spin
  * factor 2) or 2 (collinear, Stoner).
@@ -132,7 +136,7 @@ enum {
  * BOP_BW_GERSHGORIN only. */
 typedef struct {
   int norb;
-  double b0[3];
+  double b0[5];
   double r0, lam, rc, dc;
   double onsite0;
   int n_mom;
@@ -154,6 +158,7 @@ typedef struct {
   double j_ii;  /* VARIATIONAL: onsite charging J_ii >= 0 (eV / e^2) */
   double rep_A, rep_p;  /* pair repulsion (described above): rep_A = 0 for none */
   double r_path;        /* path-radius cut in A (described above): 0 for none */
+  double onsite_s;      /* sd model: reference level of the s orbital (eV) */
 } bop_model;
 
 typedef struct {
@@ -229,11 +234,13 @@ int bop_get_cluster(bop_ctx* ctx, int atom, int* site_atom, signed char* site_im
 
 /* Copies the bonds: atoms [nb][2] (i < j or image-ordered), bond vectors
  * d = r_j + S.cell - r_i [nb][3], unique block elements [nb][15] (d; the
- * upper triangle row by row) or [nb][1] (s). Any pointer may be NULL. */
+ * upper triangle row by row), [nb][21] (sd, likewise, s first) or [nb][1]
+ * (s). Any pointer may be NULL. */
 int bop_get_bonds(bop_ctx* ctx, int* atoms, double* d, double* blocks, bop_stream stream);
 
 /* Moments (Eq. momDOS) of every orbital for the given onsite levels.
- *   onsite  device [n_spin][n][norb] (FP64) or NULL for onsite0 everywhere
+ *   onsite  device [n_spin][n][norb] (FP64) or NULL for the reference
+ *           levels (onsite0, and onsite_s on the s orbital of an sd model)
  *   mu      device [n_spin][n][norb][n_mom] output (FP64 storage; FP32
  *           arithmetic when precision = FP32)
  * Requires a build. */

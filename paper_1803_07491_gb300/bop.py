@@ -33,7 +33,7 @@ class BopError(RuntimeError):
 
 
 class bop_model(ctypes.Structure):
-    _fields_ = [("norb", ctypes.c_int), ("b0", ctypes.c_double * 3), ("r0", ctypes.c_double),
+    _fields_ = [("norb", ctypes.c_int), ("b0", ctypes.c_double * 5), ("r0", ctypes.c_double),
                 ("lam", ctypes.c_double), ("rc", ctypes.c_double), ("dc", ctypes.c_double),
                 ("onsite0", ctypes.c_double), ("n_mom", ctypes.c_int), ("n_exp", ctypes.c_int),
                 ("n_spin", ctypes.c_int), ("n_e", ctypes.c_double), ("scf", ctypes.c_int),
@@ -43,7 +43,7 @@ class bop_model(ctypes.Structure):
                 ("mix_history", ctypes.c_int), ("terminator", ctypes.c_int), ("scf_response", ctypes.c_int),
                 ("bandwidth", ctypes.c_int), ("bw_beta", ctypes.c_double), ("bw_a", ctypes.c_double),
                 ("bw_b", ctypes.c_double), ("j_ii", ctypes.c_double), ("rep_A", ctypes.c_double),
-                ("rep_p", ctypes.c_double), ("r_path", ctypes.c_double)]
+                ("rep_p", ctypes.c_double), ("r_path", ctypes.c_double), ("onsite_s", ctypes.c_double)]
 
 
 class bop_stats(ctypes.Structure):
@@ -149,13 +149,13 @@ def _stream(stream=None):
 
 def make_model(params, run, precision: str = "fp64") -> bop_model:
     """bop_model from inputs.ModelParams + inputs.RunParams."""
-    b0 = list(params.b0) + [0.0] * (3 - len(params.b0))
-    return bop_model(params.norb, (ctypes.c_double * 3)(*b0), params.r0, params.lam, params.rc, params.dc,
+    b0 = list(params.b0) + [0.0] * (5 - len(params.b0))
+    return bop_model(params.norb, (ctypes.c_double * 5)(*b0), params.r0, params.lam, params.rc, params.dc,
                      params.onsite0, run.n_mom, run.n_exp, run.n_spin, run.n_e, SCF[run.scf], run.eta,
                      run.scf_tol, run.scf_max_it, run.stoner_I, run.m_mix, run.m0, run.dos_floor,
                      PREC[precision], MIXER[run.mixer], run.mix_history, TERM[run.terminator],
                      1 if run.scf_response else 0, BANDWIDTH[run.bandwidth], run.bw_beta, run.bw_a, run.bw_b,
-                     run.J_ii, params.rep_A, params.rep_p, run.r_path)
+                     run.J_ii, params.rep_A, params.rep_p, run.r_path, params.onsite_s)
 
 
 def _check(ctx, st, allow=()):
@@ -217,7 +217,7 @@ def bop_get_bonds(ctx, norb: int, stream=None):
     st = bop_get_stats(ctx)
     nb = st["n_bonds"]
     dev = torch.device("cuda")
-    hs = 1 if norb == 1 else 15
+    hs = {1: 1, 5: 15, 6: 21}[norb]
     atoms = torch.empty((max(nb, 1), 2), dtype=torch.int32, device=dev)
     d = torch.empty((max(nb, 1), 3), dtype=torch.float64, device=dev)
     blk = torch.empty((max(nb, 1), hs), dtype=torch.float64, device=dev)

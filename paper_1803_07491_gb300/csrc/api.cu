@@ -198,7 +198,7 @@ int exclusive_scan(bop_ctx* c, const Tin* in, Tout* out, long long n, cudaStream
 
 int validate_model(bop_ctx* c, const bop_model* m) {
   if (!m) return fail(c, BOP_ERR_ARG, "model is NULL");
-  if (m->norb != 1 && m->norb != 5) return fail(c, BOP_ERR_ARG, "norb must be 1 (s) or 5 (d)");
+  if (m->norb != 1 && m->norb != 5 && m->norb != 6) return fail(c, BOP_ERR_ARG, "norb must be 1 (s), 5 (d) or 6 (sd)");
   if (m->n_mom < 3 || m->n_mom > BOP_MAX_NMOM || m->n_mom % 2 == 0)
     return fail(c, BOP_ERR_ARG, "n_mom must be odd in [3, %d]", BOP_MAX_NMOM);
   if (m->n_exp < m->n_mom - 1 || m->n_exp > BOP_MAX_NEXP)
@@ -955,8 +955,8 @@ int bop_create(bop_ctx** out, const bop_model* model) {
   }
   c->m = *model;
   c->norb = model->norb;
-  c->HS = model->norb == 1 ? 1 : BOP_HS_D;
-  c->HSu = model->norb == 1 ? 1 : 15;
+  c->HS = block_store(model->norb);
+  c->HSu = block_unique(model->norb);
   c->n_mom = model->n_mom;
   c->K = (model->n_mom - 1) / 2;
   c->Kp = c->K;
@@ -965,7 +965,7 @@ int bop_create(bop_ctx** out, const bop_model* model) {
   c->fp64 = model->precision == BOP_PREC_FP64;
   c->sfac = model->n_spin == 1 ? 2.0 : 1.0;
   c->bm.norb = model->norb;
-  for (int q = 0; q < 3; q++) c->bm.b0[q] = model->b0[q];
+  for (int q = 0; q < 5; q++) c->bm.b0[q] = model->b0[q];
   c->bm.r0 = model->r0;
   c->bm.lam = model->lam;
   c->bm.rc = model->rc;
@@ -1185,7 +1185,7 @@ int bop_moments(bop_ctx* c, const double* onsite, double* mu, bop_stream stream)
     launch_to_float(P<double>(c->onsite), P<float>(c->onsite32), M, s);
   } else {
     Region R(c, PK_ONSITE, 1, s);
-    launch_build_onsite(c->n, c->norb, c->S, c->m.onsite0, 0.0, nullptr, nullptr, P<double>(c->onsite),
+    launch_build_onsite(c->n, c->norb, c->S, c->m.onsite0, c->m.onsite_s, 0.0, nullptr, nullptr, P<double>(c->onsite),
                         P<float>(c->onsite32), s);
   }
   CKS(run_moments(c, P<double>(c->onsite), mu, s));
@@ -1302,7 +1302,7 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
     a.it = it;
     {
       Region R(c, PK_ONSITE, 1, s);
-      launch_build_onsite(n, c->norb, c->S, c->m.onsite0, c->m.stoner_I, P<double>(c->delta),
+      launch_build_onsite(n, c->norb, c->S, c->m.onsite0, c->m.onsite_s, c->m.stoner_I, P<double>(c->delta),
                           stoner ? P<double>(c->mval) : nullptr, P<double>(c->onsite), P<float>(c->onsite32), s);
     }
     CKS(run_moments(c, P<double>(c->onsite), P<double>(c->mu), s, var_store ? c->psis.p : nullptr));

@@ -9,6 +9,7 @@
 #define BOP_MAX_NEXP 253           // expansion length n_exp
 #define BOP_MAX_DEG 64             // neighbours per atom
 #define BOP_HS_D 16                // stored elements of a d block (15 unique + pad)
+#define BOP_HS_SD 24               // stored elements of an sd block (21 unique + pad)
 
 // Error bits raised by kernels into the context's device status word.
 #define BOP_DEV_ERR_DEGREE 1u      // more than BOP_MAX_DEG neighbours
@@ -19,8 +20,8 @@
 
 // Parameters of the exponential two-centre model (beta = b0 e^{-lam(r-r0)} fcut).
 struct BondModel {
-  int norb;
-  double b0[3];
+  int norb;     // 1 (s), 5 (d) or 6 (sd: s first)
+  double b0[5];  // s: ss sigma; d: dd sigma, pi, delta; sd: dd sigma, pi, delta, ss sigma, sd sigma
   double r0, lam, rc, dc;
   double rep_A, rep_p;  // pair repulsion A e^{-p(r-r0)} fcut(r); A = 0: none
 };
@@ -108,13 +109,40 @@ __device__ __forceinline__ S pair_repulsion(const BondModel& m, S r) {
 // 0 = 3z^2-r^2, 1 = zx, 2 = yz, 3 = x^2-y^2, 4 = xy; u[] holds the upper
 // triangle row by row: (0,0) (0,1) (0,2) (0,3) (0,4) (1,1) (1,2) (1,3)
 // (1,4) (2,2) (2,3) (2,4) (3,3) (3,4) (4,4).
+// sd (norb 6): u[] holds the 21-element upper triangle of the 6x6 block,
+// s first: (s,s) (s,d0..d4), then the d rows as above; the s-d elements are
+// even in the direction cosines, so the block is symmetric.
 template <class S>
-__device__ void sk_unique(const BondModel& m, const S d[3], S u[15]) {
+__device__ void sk_unique_d(const BondModel& m, const S d[3], S r, S u[15]);
+
+template <class S>
+__device__ void sk_unique(const BondModel& m, const S d[3], S u[21]) {
   S r = dsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
   if (m.norb == 1) {
     u[0] = bond_integral(m, 0, r);
     return;
   }
+  if (m.norb == 5) {
+    sk_unique_d(m, d, r, u);
+    return;
+  }
+  S ud[15];
+  sk_unique_d(m, d, r, ud);
+  const S ss = bond_integral(m, 3, r), sd = bond_integral(m, 4, r);
+  const S l = d[0] / r, mm = d[1] / r, n = d[2] / r;
+  const double r3 = 1.7320508075688772;
+  u[0] = ss;
+  u[1] = (n * n - 0.5 * (l * l + mm * mm)) * sd;  // 3z^2 - r^2
+  u[2] = r3 * n * l * sd;                          // zx
+  u[3] = r3 * mm * n * sd;                         // yz
+  u[4] = 0.5 * r3 * (l * l - mm * mm) * sd;        // x^2 - y^2
+  u[5] = r3 * l * mm * sd;                         // xy
+#pragma unroll
+  for (int q = 0; q < 15; q++) u[6 + q] = ud[q];   // the d rows keep their order
+}
+
+template <class S>
+__device__ void sk_unique_d(const BondModel& m, const S d[3], S r, S u[15]) {
   const S vs = bond_integral(m, 0, r), vp = bond_integral(m, 1, r), vd = bond_integral(m, 2, r);
   const S l = d[0] / r, mm = d[1] / r, n = d[2] / r;
   const S L = l * l, M = mm * mm, N = n * n;
@@ -143,10 +171,18 @@ __device__ void sk_unique(const BondModel& m, const S d[3], S u[15]) {
   u[14] = 3.0 * L * M * vs + (LpM - 4.0 * L * M) * vp + (N + L * M) * vd;
 }
 
-// Position of element (b, g) of a 5x5 symmetric block in the unique list.
-__host__ __device__ __forceinline__ int sym_index(int b, int g) {
-  if (b > g) { int t = b; b = g; g = t; }
-  return b * 5 - (b * (b - 1)) / 2 + (g - b);
+// Position of element (b, g) of an NO x NO symmetric block in the unique
+// list (upper triangle, row by row).
+__host__ __device__ __forceinline__ constexpr int sym_index_n(int b, int g, int no) {
+  return b <= g ? b * no - (b * (b - 1)) / 2 + (g - b) : g * no - (g * (g - 1)) / 2 + (b - g);
+}
+__host__ __device__ __forceinline__ int sym_index(int b, int g) { return sym_index_n(b, g, 5); }
+// stored / unique elements of a block
+__host__ __device__ __forceinline__ constexpr int block_store(int norb) {
+  return norb == 1 ? 1 : (norb == 5 ? BOP_HS_D : BOP_HS_SD);
+}
+__host__ __device__ __forceinline__ constexpr int block_unique(int norb) {
+  return norb == 1 ? 1 : (norb == 5 ? 15 : 21);
 }
 
 // The FP64 bond-vector arithmetic of the neighbour test, one rounding per

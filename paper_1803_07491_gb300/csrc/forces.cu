@@ -23,9 +23,9 @@ __global__ void __launch_bounds__(FT) k_forces(int nb, BondModel m, const double
     d[0] = {dv[0], 1.0, 0.0, 0.0};
     d[1] = {dv[1], 0.0, 1.0, 0.0};
     d[2] = {dv[2], 0.0, 0.0, 1.0};
-    D3 u[15];
+    D3 u[21];
     sk_unique<D3>(m, d, u);
-    const int nu = m.norb == 1 ? 1 : 15;
+    const int nu = block_unique(m.norb);
     double g0 = 0.0, g1 = 0.0, g2 = 0.0;
     for (int q = 0; q < nu; q++) {
       double hb = Hbar[(size_t)b * HSu + q];

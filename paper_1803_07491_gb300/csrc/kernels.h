@@ -196,7 +196,8 @@ struct ScfArgs {
 int launch_scf_residual(const ScfArgs& a, cudaStream_t s);
 int launch_scf_apply(const ScfArgs& a, cudaStream_t s);
 void launch_to_float(const double* in, float* out, size_t n, cudaStream_t s);
-void launch_build_onsite(int n, int norb, int n_spin, double onsite0, double stoner_I, const double* delta,
+void launch_build_onsite(int n, int norb, int n_spin, double onsite0, double onsite_s, double stoner_I,
+                         const double* delta,
                          const double* m, double* onsite, float* onsite32, cudaStream_t s);
 
 // e_i = s sum U (- I m_i^2 / 4 with m) (+ J q_i^2 / 2, q_i = s sum N - n0, with N)

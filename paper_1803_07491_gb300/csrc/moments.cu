@@ -10,7 +10,8 @@
 // shared memory (ping-pong); the last level Psi_K is never stored, only its
 // inner products.  Each thread owns one cluster site per pass and gathers
 // the 5x5 blocks of its bonds (15 unique elements, 16-element records) from
-// L2.  Products in T (float or double), moments written as double.
+// L2 (for sd blocks 21 unique elements in 24-element records).  Products in
+// T (float or double), moments written as double.
 //
 // Adjoint: one CTA per work item as well, Psi_0..Psi_K and the cotangents
 // Psi-bar_1..Psi-bar_K kept in the CTA's slot of global scratch; the bond
@@ -22,14 +23,21 @@ namespace {
 
 constexpr int MOM_THREADS = 256;
 
+// stored elements of one bond block (unique upper triangle + pad to 16 bytes)
+template <int NO>
+__host__ __device__ constexpr int hb_count() {
+  return NO == 1 ? 1 : (NO == 5 ? 16 : 24);
+}
+
 template <typename T>
 struct Blk;
 template <>
 struct Blk<float> {
-  __device__ static void load(const float* __restrict__ h, float u[16]) {
+  template <int HB>
+  __device__ static void load(const float* __restrict__ h, float u[HB]) {
     const float4* p = reinterpret_cast<const float4*>(h);
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < HB / 4; q++) {
       float4 v = __ldg(p + q);
       u[4 * q] = v.x; u[4 * q + 1] = v.y; u[4 * q + 2] = v.z; u[4 * q + 3] = v.w;
     }
@@ -37,19 +45,21 @@ struct Blk<float> {
 };
 template <>
 struct Blk<double> {
-  __device__ static void load(const double* __restrict__ h, double u[16]) {
+  template <int HB>
+  __device__ static void load(const double* __restrict__ h, double u[HB]) {
     const double2* p = reinterpret_cast<const double2*>(h);
 #pragma unroll
-    for (int q = 0; q < 8; q++) {
+    for (int q = 0; q < HB / 2; q++) {
       double2 v = __ldg(p + q);
       u[2 * q] = v.x; u[2 * q + 1] = v.y;
     }
   }
 };
 
-// unique element of (row, col) in the 15-element upper triangle
-__device__ __forceinline__ constexpr int U5(int b, int g) {
-  return b <= g ? b * 5 - (b * (b - 1)) / 2 + (g - b) : g * 5 - (g * (g - 1)) / 2 + (b - g);
+// unique element of (row, col) in the upper triangle of an NO x NO block
+template <int NO>
+__device__ __forceinline__ constexpr int UI(int b, int g) {
+  return b <= g ? b * NO - (b * (b - 1)) / 2 + (g - b) : g * NO - (g * (g - 1)) / 2 + (b - g);
 }
 
 // acc[r][c] += B[r][g] * x[g][c] for the symmetric block B given by u[].
@@ -61,8 +71,8 @@ __device__ __forceinline__ void block_apply(const T* __restrict__ hrec, const T*
 #pragma unroll
     for (int c = 0; c < NC; c++) acc[0][c] += h * x[c];
   } else {
-    T u[16];
-    Blk<T>::load(hrec, u);
+    T u[hb_count<NO>()];
+    Blk<T>::template load<hb_count<NO>()>(hrec, u);
     T xs[NO][NC];
 #pragma unroll
     for (int g = 0; g < NO; g++)
@@ -72,7 +82,7 @@ __device__ __forceinline__ void block_apply(const T* __restrict__ hrec, const T*
     for (int r = 0; r < NO; r++)
 #pragma unroll
       for (int g = 0; g < NO; g++) {
-        T h = u[U5(r, g)];
+        T h = u[UI<NO>(r, g)];
 #pragma unroll
         for (int c = 0; c < NC; c++) acc[r][c] += h * xs[g][c];
       }
@@ -192,11 +202,11 @@ __device__ __forceinline__ void store_row(T* __restrict__ p, const T x[N]) {
 }
 
 template <typename T, int NO>
-__device__ __forceinline__ void load_bond(const T* __restrict__ h, T u[NO == 1 ? 1 : 16]) {
+__device__ __forceinline__ void load_bond(const T* __restrict__ h, T u[hb_count<NO>()]) {
   if constexpr (NO == 1) {
     u[0] = __ldg(h);
   } else {
-    Blk<T>::load(h, u);
+    Blk<T>::template load<hb_count<NO>()>(h, u);
   }
 }
 
@@ -211,7 +221,7 @@ __device__ __forceinline__ void block_fma(const T* u, const T* x, T acc[NO][NC])
     for (int r = 0; r < NO; r++)
 #pragma unroll
       for (int g = 0; g < NO; g++) {
-        const T h = u[U5(r, g)];
+        const T h = u[UI<NO>(r, g)];
 #pragma unroll
         for (int c = 0; c < NC; c++) acc[r][c] += h * x[g * NC + c];
       }
@@ -225,7 +235,7 @@ __device__ __forceinline__ void gather_pf(const int2* __restrict__ adj, long lon
                                           const T* __restrict__ H, int HS, const T* __restrict__ x,
                                           T acc[NO][NC]) {
   if (cnt <= 0) return;
-  constexpr int HB = NO == 1 ? 1 : 16;
+  constexpr int HB = hb_count<NO>();
   int2 en = __ldg(adj + q0);
   T hb[HB];
   load_bond<T, NO>(H + (size_t)en.y * HS, hb);
@@ -249,7 +259,7 @@ __device__ __forceinline__ void gather_pf(const int2* __restrict__ adj, long lon
 template <typename T, int NO, int NC, int PS>
 __device__ __forceinline__ void gather_pf2(const int2* __restrict__ ent, int cnt, const T* __restrict__ H, int HS,
                                            const T* __restrict__ x, T acc[NO][NC]) {
-  constexpr int HB = NO == 1 ? 1 : 16;
+  constexpr int HB = hb_count<NO>();
   constexpr int N = NO * NC;
   if (cnt <= 0) return;
   int2 e0 = ent[0];
@@ -298,7 +308,7 @@ k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
           const long long* __restrict__ psi_off, long long psi_tot) {
   constexpr int N = NO * NC;
   constexpr int PS = (N == 1) ? 1 : Row<T, N>::PS;
-  constexpr int HB = NO == 1 ? 1 : 16;
+  constexpr int HB = hb_count<NO>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* buf[2];
   buf[0] = reinterpret_cast<T*>(smem_raw);
@@ -464,7 +474,7 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
           double* __restrict__ Hbar, int HSu, double* __restrict__ Ebar) {
   constexpr int N = NO * NC;
   constexpr int PS = (N == 1) ? 1 : Row<T, N>::PS;
-  constexpr int HB = NO == 1 ? 1 : 16;
+  constexpr int HB = hb_count<NO>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* buf[2];
   buf[0] = reinterpret_cast<T*>(smem_raw);
@@ -659,7 +669,7 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
 #pragma unroll
               for (int g = b; g < NO; g++) {
                 const T v = G[b][g] + (b != g ? G[g][b] : T(0));  // sum in T, one conversion
-                atomicAdd(hbp + U5(b, g), (double)v);
+                atomicAdd(hbp + UI<NO>(b, g), (double)v);
               }
           }
         }
@@ -803,7 +813,7 @@ k_moments_adj(ClusterView cv, const T* __restrict__ H, int HS, const T* __restri
 #pragma unroll
             for (int g = b; g < NO; g++) {
               double v = (double)G[b][g] + (b != g ? (double)G[g][b] : 0.0);
-              atomicAdd(hb + U5(b, g), v);
+              atomicAdd(hb + UI<NO>(b, g), v);
             }
         }
       }
@@ -922,29 +932,38 @@ int run_reverse_mode(const AdjointArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-// Column grouping: all 5 starting orbitals in one CTA when both Psi levels
-// fit in shared memory, one CTA per starting orbital otherwise.
+// Column grouping: all starting orbitals of an atom in one CTA when both Psi
+// levels fit in shared memory, one CTA per starting orbital otherwise.
 int moments_columns(int norb, int cap_sum, int fp64) {
   if (norb == 1) return 1;
-  size_t bytes = (size_t)cap_sum * 25 * (fp64 ? 8 : 4);
-  return bytes <= 100 * 1024 ? 5 : 1;
+  size_t bytes = (size_t)cap_sum * norb * norb * (fp64 ? 8 : 4);
+  return bytes <= 100 * 1024 ? norb : 1;
 }
 
 int launch_moments(const MomentsArgs& a, int fp64, cudaStream_t s) {
   int nc = moments_columns(a.norb, a.cap_even + a.cap_odd, fp64);
   if (a.norb == 1) return fp64 ? run_forward<double, 1, 1>(a, s) : run_forward<float, 1, 1>(a, s);
+  if (a.norb == 6) {
+    if (nc == 6) return fp64 ? run_forward<double, 6, 6>(a, s) : run_forward<float, 6, 6>(a, s);
+    return fp64 ? run_forward<double, 6, 1>(a, s) : run_forward<float, 6, 1>(a, s);
+  }
   if (nc == 5) return fp64 ? run_forward<double, 5, 5>(a, s) : run_forward<float, 5, 5>(a, s);
   return fp64 ? run_forward<double, 5, 1>(a, s) : run_forward<float, 5, 1>(a, s);
 }
 
-int adjoint_columns(int norb) { return norb == 1 ? 1 : 5; }
+int adjoint_columns(int norb) { return norb; }
 
 int launch_moments_adjoint(const AdjointArgs& a, int fp64, cudaStream_t s) {
   if (a.pstore != nullptr) {  // reverse sweep over stored Psi
     if (a.norb == 1) return fp64 ? run_reverse_mode<double, 1, 1>(a, s) : run_reverse_mode<float, 1, 1>(a, s);
+    if (a.norb == 6) {
+      if (a.nc == 6) return fp64 ? run_reverse_mode<double, 6, 6>(a, s) : run_reverse_mode<float, 6, 6>(a, s);
+      return fp64 ? run_reverse_mode<double, 6, 1>(a, s) : run_reverse_mode<float, 6, 1>(a, s);
+    }
     if (a.nc == 5) return fp64 ? run_reverse_mode<double, 5, 5>(a, s) : run_reverse_mode<float, 5, 5>(a, s);
     return fp64 ? run_reverse_mode<double, 5, 1>(a, s) : run_reverse_mode<float, 5, 1>(a, s);
   }
   if (a.norb == 1) return fp64 ? run_adjoint<double, 1, 1>(a, s) : run_adjoint<float, 1, 1>(a, s);
+  if (a.norb == 6) return fp64 ? run_adjoint<double, 6, 6>(a, s) : run_adjoint<float, 6, 6>(a, s);
   return fp64 ? run_adjoint<double, 5, 5>(a, s) : run_adjoint<float, 5, 5>(a, s);
 }

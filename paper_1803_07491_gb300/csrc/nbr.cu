@@ -229,9 +229,9 @@ __global__ void k_bond_blocks(int nb, const double* __restrict__ pos, Geometry g
   bond_d[3 * b] = d[0];
   bond_d[3 * b + 1] = d[1];
   bond_d[3 * b + 2] = d[2];
-  double u[15];
+  double u[21];
   sk_unique<double>(m, d, u);
-  int nu = m.norb == 1 ? 1 : 15;
+  const int nu = block_unique(m.norb);
   for (int q = 0; q < HS; q++) {
     double v = q < nu ? u[q] : 0.0;
     H64[(size_t)b * HS + q] = v;

@@ -335,8 +335,9 @@ __global__ void __launch_bounds__(RT) k_scf_apply(ScfArgs A) {
   }
 }
 
-// E_ialpha,nu = E^0 + delta_i -/+ I m_i / 2 (spin up lower).
-__global__ void __launch_bounds__(RT) k_build_onsite(int n, int norb, int n_spin, double e0, double I,
+// E_ialpha,nu = E^0_alpha + delta_i -/+ I m_i / 2 (spin up lower); E^0 is
+// es for the s orbital of an sd model (orbital 0), e0 otherwise.
+__global__ void __launch_bounds__(RT) k_build_onsite(int n, int norb, int n_spin, double e0, double es, double I,
                                                      const double* __restrict__ delta,
                                                      const double* __restrict__ m, double* __restrict__ on,
                                                      float* __restrict__ on32) {
@@ -344,7 +345,7 @@ __global__ void __launch_bounds__(RT) k_build_onsite(int n, int norb, int n_spin
   int tot = n_spin * n * norb;
   if (q >= tot) return;
   int i = (q / norb) % n, v = q / (n * norb);
-  double e = e0 + (delta ? delta[i] : 0.0);
+  double e = (norb == 6 && q % norb == 0 ? es : e0) + (delta ? delta[i] : 0.0);
   if (m && n_spin == 2) e += (v == 0 ? -0.5 : 0.5) * I * m[i];
   on[q] = e;
   if (on32) on32[q] = (float)e;
@@ -437,10 +438,11 @@ void launch_to_float(const double* in, float* out, size_t n, cudaStream_t s) {
   if (n) k_to_float<<<(unsigned)((n + RT - 1) / RT), RT, 0, s>>>(in, out, n);
 }
 
-void launch_build_onsite(int n, int norb, int n_spin, double onsite0, double stoner_I, const double* delta,
+void launch_build_onsite(int n, int norb, int n_spin, double onsite0, double onsite_s, double stoner_I,
+                         const double* delta,
                          const double* m, double* onsite, float* onsite32, cudaStream_t s) {
   int tot = n_spin * n * norb;
-  k_build_onsite<<<(tot + RT - 1) / RT, RT, 0, s>>>(n, norb, n_spin, onsite0, stoner_I, delta, m, onsite,
+  k_build_onsite<<<(tot + RT - 1) / RT, RT, 0, s>>>(n, norb, n_spin, onsite0, onsite_s, stoner_I, delta, m, onsite,
                                                    onsite32);
 }
 

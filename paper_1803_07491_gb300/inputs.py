@@ -194,6 +194,8 @@ def workload(name: str) -> Workload:
               N_d = 6.8; local charge neutrality (Anderson, ANDERSON_STEP);
               9 moments.
     d2000nscf the same cell without SCF (fixed onsite levels).
+    sd2000    the d2000 cell with the sd-valent model MODEL_SD (6 orbitals,
+              8 electrons per atom), local charge neutrality.
     d2000cut  d2000 with the path-radius cut at 5.5 A (five neighbour shells;
               "Performance", item (iii)).
     d2000var  the same cell with the variational SCF (Eq. BOP_SCF), J_ii =
@@ -227,6 +229,9 @@ def workload(name: str) -> Workload:
         r_path = 5.5 if name == "d2000cut" else 0.0
         return Workload(name, pos, cell, (1, 1, 1), MODEL_D,
                         RunParams(n_e=6.8, scf=scf, J_ii=J, r_path=r_path, **ANDERSON_STEP))
+    if name == "sd2000":
+        pos, cell = bcc_jittered(10, 10, 10, 0.05, 2)
+        return Workload(name, pos, cell, (1, 1, 1), MODEL_SD, RunParams(n_e=8.0, scf="lcn", **ANDERSON_STEP))
     if name == "slab16k":
         pos, cell, pbc = slab_with_vacancies(16, 16, 32, 64, 0.08, 3)
         return Workload(name, pos, cell, pbc, MODEL_D, RunParams(n_e=6.8, n_mom=13))
