@@ -60,23 +60,82 @@ __global__ void __launch_bounds__(CT) k_expand(ScalarArgs A) {
 // Sums over the sine series of one orbital at x = cos(phi) (Clenshaw):
 //   N    = gs_0 (1 - phi/pi) + sum_k (gs_{k-2} - gs_k)/(pi k) sin(k phi)
 //   dNde = (2/pi) sum_m gs_m sin((m+1) phi)            (= dN/d eps)
-// gs_j = 0 outside 0..ne; inv[k] = 1/k.
+// gs_j = 0 outside 0..ne; inv[k] = 1/k.  With sin(k phi) = s U_{k-1}(x),
+// each sum over U_j is split into its even and odd terms, which obey
+// U_{j+2} = y U_j - U_{j-2} with y = 4x^2 - 2: four independent Clenshaw
+// chains of half the length (U_0 = 1, U_2 - y U_0 = 1; U_1 = 2x,
+// U_3 - y U_1 = 0), so that the FP64 pipe is not left waiting on one chain.
 __device__ __forceinline__ void count_and_dos(const double* __restrict__ gsig, const double* __restrict__ inv,
                                               int M, int o, int ne, double x, double* N, double* dNde) {
   auto G = [&](int j) -> double { return (j >= 0 && j <= ne) ? gsig[(size_t)j * M + o] : 0.0; };
   const double phi = acos(x), s = sqrt(fmax(0.0, 1.0 - x * x));
-  const double x2 = 2.0 * x;
+  const double y = 4.0 * x * x - 2.0;
+  // S = sum_j a_{j+1} U_j, a_k = (gs_{k-2} - gs_k)/k;  C = sum_j gs_j U_j
+  double be1 = 0.0, be2 = 0.0, bo1 = 0.0, bo2 = 0.0;
+  double ce1 = 0.0, ce2 = 0.0, co1 = 0.0, co2 = 0.0;
+  const int top = (ne + 2) / 2;
+  double g1 = G(2 * top + 1), g2 = G(2 * top + 2);  // gs_{2i+1}, gs_{2i+2}
+  for (int i = top; i >= 0; i--) {
+    const int j = 2 * i;
+    const double gm1 = G(j - 1), g0 = G(j);
+    const double ae = (gm1 - g1) * inv[j + 1];  // a_{j+1}
+    const double ao = (g0 - g2) * inv[j + 2];   // a_{j+2}
+    const double be0 = ae + y * be1 - be2;
+    const double bo0 = ao + y * bo1 - bo2;
+    const double ce0 = g0 + y * ce1 - ce2;
+    const double co0 = g1 + y * co1 - co2;
+    be2 = be1;
+    be1 = be0;
+    bo2 = bo1;
+    bo1 = bo0;
+    ce2 = ce1;
+    ce1 = ce0;
+    co2 = co1;
+    co1 = co0;
+    g2 = g0;
+    g1 = gm1;
+  }
+  const double S = (be1 + be2) + 2.0 * x * bo1;
+  const double C = (ce1 + ce2) + 2.0 * x * co1;
+  *N = G(0) * (1.0 - phi / PI) + s * S / PI;
+  *dNde = (2.0 / PI) * s * C;
+}
+
+// The same sums by a pair of adjacent lanes (par = lane & 1): the even
+// chains on lane 0, the odd ones on lane 1, exchanged at the end, so that an
+// orbital's FP64 work runs on two lanes (twice the warps for the same
+// orbitals; measured faster than one lane and than four lanes per orbital).
+// pm: the pair's lane mask.  Both lanes return N and dNde.
+__device__ __forceinline__ void count_and_dos2(const double* __restrict__ gsig, const double* __restrict__ inv,
+                                               int M, int o, int ne, double x, int par, unsigned pm, double* N,
+                                               double* dNde) {
+  auto G = [&](int j) -> double { return (j >= 0 && j <= ne) ? gsig[(size_t)j * M + o] : 0.0; };
+  const double y = 4.0 * x * x - 2.0;
+  // lane par sums the terms U_j with j = 2i + par:
+  //   S_par = sum_i a_{j+1} U_j, a_k = (gs_{k-2} - gs_k)/k;  C_par = sum_i gs_j U_j
   double b1 = 0.0, b2 = 0.0, c1 = 0.0, c2 = 0.0;
-  for (int k = ne + 2; k >= 1; k--) {  // coefficient of U_{k-1}
-    const double b0 = (G(k - 2) - G(k)) * inv[k] + x2 * b1 - b2;
+  const int top = (ne + 2) / 2;
+  double gp = G(2 * top + par + 1);  // gs_{j+1}
+  for (int i = top; i >= 0; i--) {
+    const int j = 2 * i + par;
+    const double gm = G(j - 1), g0 = G(j);
+    const double a = (gm - gp) * inv[j + 1];
+    const double b0 = a + y * b1 - b2;
+    const double c0 = g0 + y * c1 - c2;
     b2 = b1;
     b1 = b0;
-    const double c0 = G(k - 1) + x2 * c1 - c2;
     c2 = c1;
     c1 = c0;
+    gp = gm;
   }
-  *N = G(0) * (1.0 - phi / PI) + s * b1 / PI;
-  *dNde = (2.0 / PI) * s * c1;
+  // even: U_0 = 1, U_2 - y U_0 = 1;  odd: U_1 = 2x, U_3 - y U_1 = 0
+  const double Sp = par == 0 ? b1 + b2 : 2.0 * x * b1;
+  const double Cp = par == 0 ? c1 + c2 : 2.0 * x * c1;
+  const double S = Sp + __shfl_xor_sync(pm, Sp, 1);
+  const double C = Cp + __shfl_xor_sync(pm, Cp, 1);
+  const double phi = acos(x), s = sqrt(fmax(0.0, 1.0 - x * x));
+  *N = G(0) * (1.0 - phi / PI) + s * S / PI;
+  *dNde = (2.0 / PI) * s * C;
 }
 
 constexpr int RT2 = 32;  // threads per block of the per-orbital FP64 kernels (see CT)
@@ -350,18 +409,24 @@ __global__ void __launch_bounds__(FC) k_fermi_coop(int M, const double* __restri
   bool done = hi - lo < tol;
   if (done) ef = 0.5 * (lo + hi);
   bool evaluated = false;
+  // two lanes per orbital (count_and_dos2): thread t takes orbital t / 2
+  const int par = threadIdx.x & 1;
+  const unsigned pm = 3u << ((threadIdx.x & 31) & ~1);
   for (int r = 0; !done && r < max_rounds; r++) {
     double aN = 0.0, aD = 0.0;
-    for (int o = b * FC + threadIdx.x; o < M; o += stride) {
+    for (int t = b * FC + threadIdx.x; (t >> 1) < M; t += stride) {
+      const int o = t >> 1;
       const double bi = b_inf[o];
       const double xr = (E - a_inf[o]) / (2.0 * bi);
       double Nv, dN;
-      count_and_dos(gsig, inv, M, o, ne, clamp1(xr), &Nv, &dN);
+      count_and_dos2(gsig, inv, M, o, ne, clamp1(xr), par, pm, &Nv, &dN);
       const double d = (xr > -1.0 && xr < 1.0) ? dN / (2.0 * bi) : 0.0;
-      aN += Nv;
-      aD += d;
-      Nout[o] = Nv;
-      dos[o] = d;
+      if (par == 0) {
+        aN += Nv;
+        aD += d;
+        Nout[o] = Nv;
+        dos[o] = d;
+      }
     }
     evaluated = true;
     aN = coop_block_reduce(aN, sh, false);
@@ -400,13 +465,16 @@ __global__ void __launch_bounds__(FC) k_fermi_coop(int M, const double* __restri
     st->done = done ? 1 : 0;
   }
   if (!evaluated) {  // bracket narrower than tol: N and DOS at its midpoint
-    for (int o = b * FC + threadIdx.x; o < M; o += stride) {
+    for (int t = b * FC + threadIdx.x; (t >> 1) < M; t += stride) {
+      const int o = t >> 1;
       const double bi = b_inf[o];
       const double xr = (ef - a_inf[o]) / (2.0 * bi);
       double Nv, dN;
-      count_and_dos(gsig, inv, M, o, ne, clamp1(xr), &Nv, &dN);
-      Nout[o] = Nv;
-      dos[o] = (xr > -1.0 && xr < 1.0) ? dN / (2.0 * bi) : 0.0;
+      count_and_dos2(gsig, inv, M, o, ne, clamp1(xr), par, pm, &Nv, &dN);
+      if (par == 0) {
+        Nout[o] = Nv;
+        dos[o] = (xr > -1.0 && xr < 1.0) ? dN / (2.0 * bi) : 0.0;
+      }
     }
   }
 }
@@ -604,7 +672,7 @@ int launch_fermi_coop(int M, const double* gsig, const double* inv, const double
                       int max_rounds, double tol, double* N, double* dos, cudaStream_t s) {
   const int gmax = fermi_coop_grid();
   if (gmax <= 0) return -2;
-  int g = (M + FC - 1) / FC;
+  int g = (2 * M + FC - 1) / FC;  // two lanes per orbital
   if (g > gmax) g = gmax;
   if (g < 1) g = 1;
   void* args[] = {&M, &gsig, &inv, &a_inf, &b_inf, &n_exp, &spin_factor, &target, &st, &partials, &warm,
