@@ -763,7 +763,7 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
     CKS(compute_weights(c, c->sfac, nullptr, 0.0, wU, P<double>(c->rdUE), s));
     CKS(compute_weights(c, 0.0, nullptr, 1.0, wN, nullptr, s));
   } else {  // both from one forward pass of the chain
-    CKS(ensure(c, c->zscr, sizeof(double) * (size_t)M * (c->n_exp + 1) * 3));
+    CKS(ensure(c, c->zscr, sizeof(double) * (size_t)M * (c->n_exp + 1) * 4));
     WeightArgs wa;
     wa.M = M;
     wa.n_mom = c->n_mom;

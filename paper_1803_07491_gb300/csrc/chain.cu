@@ -528,50 +528,49 @@ __global__ void __launch_bounds__(CT) k_weights(WeightArgs A) {
   if (bad) raise_error(A.status, BOP_DEV_ERR_NONFINITE);
 }
 
-// Two weight sets at once, w1 for (cU1, cN1) and w2 for (cU2, cN2), both
-// at fixed E_F (no E_F multiplier): the SCF-response solve needs dU/dmu and
-// dN/dmu.  The forward part of the chain runs once.  zscratch holds sigma_m
-// and the two cotangents ([3][n_exp+1][M]).
+// Two weight sets, w1 for (cU1, cN1) and w2 for (cU2, cN2), both at fixed
+// E_F, on two lanes per orbital (t = 2 o + q, q the seed): each lane runs the
+// forward part of the chain and the reverse for its own seed, so that the
+// FP64 work spreads over twice the warps.  zscratch: [4][n_exp+1][M] (sigma
+// and its cotangent per seed).
 template <int KP>
-__global__ void __launch_bounds__(CT) k_weights_pair(WeightArgs A, double cU1, double cN1, double cU2, double cN2,
-                                                     double* __restrict__ w2) {
-  const int o = blockIdx.x * CT + threadIdx.x;
+__global__ void __launch_bounds__(CT) k_weights_split(WeightArgs A, double cU1, double cN1, double cU2, double cN2,
+                                                      double* __restrict__ w2) {
+  const int t = blockIdx.x * CT + threadIdx.x;
+  const int o = t >> 1, q = t & 1;
   if (o >= A.M) return;
   const int M = A.M, nm = 2 * KP + 1;
+  const double cU = q ? cU2 : cU1, cN = q ? cN2 : cN1;
   double mu[BOP_MAX_NMOM];
   for (int n = 0; n < nm; n++) mu[n] = A.mu[(size_t)o * nm + n];
   Rec r;
   RecTape<KP> tp;
   recursion_taped<KP>(mu, r, tp);
-  const Term t = bandwidth(r, A.bw);
+  const Term tm = bandwidth(r, A.bw);
   Chain ch;
-  chain_params(r, t, KP, ch);
-  double abar[2][KPMAX + 1], bbar[2][KPMAX + 2];
-  for (int q = 0; q < 2; q++) {
-    for (int k = 0; k <= KPMAX; k++) abar[q][k] = 0.0;
-    for (int k = 0; k <= KPMAX + 1; k++) bbar[q][k] = 0.0;
-  }
-  double abar_inf[2] = {0.0, 0.0}, bbar_inf[2] = {0.0, 0.0}, dE[2];
-  const double cU[2] = {cU1, cU2}, cN[2] = {cN1, cN2};
+  chain_params(r, tm, KP, ch);
+  double abar[KPMAX + 1], bbar[KPMAX + 2];
+  for (int k = 0; k <= KPMAX; k++) abar[k] = 0.0;
+  for (int k = 0; k <= KPMAX + 1; k++) bbar[k] = 0.0;
+  double abar_inf = 0.0, bbar_inf = 0.0;
   const size_t zl = (size_t)(A.n_exp + 1) * M;
-  double* zb[2] = {A.zscratch + zl, A.zscratch + 2 * zl};
-  chain_reverse_ns<KP, 2>(ch, r.nlev, KP, t.a_inf, t.b_inf, A.onsite[o], A.st->ef, A.g, A.inv, A.n_exp, M, o, cU,
-                          cN, A.zscratch, zb, abar, bbar, abar_inf, bbar_inf, dE);
-  if (A.dU_dE) A.dU_dE[o] = dE[0];
+  double* zs = A.zscratch + (size_t)q * 2 * zl;
+  const double dE = chain_reverse<KP>(ch, r.nlev, KP, tm.a_inf, tm.b_inf, A.onsite[o], A.st->ef, A.g, A.inv,
+                                      A.n_exp, M, o, cU, cN, zs, zs + zl, abar, bbar, abar_inf, bbar_inf);
+  if (q == 0 && A.dU_dE) A.dU_dE[o] = dE;
+  bandwidth_reverse(r, tm, A.bw, abar_inf, bbar_inf, abar, bbar);
+  double mub[BOP_MAX_NMOM];
+  for (int n = 0; n < nm; n++) mub[n] = 0.0;
+  recursion_reverse<KP>(mu, r, tp, abar, bbar, mub);
+  double* w = q ? w2 : A.w;
   bool bad = false;
-  for (int q = 0; q < 2; q++) {
-    bandwidth_reverse(r, t, A.bw, abar_inf[q], bbar_inf[q], abar[q], bbar[q]);
-    double mub[BOP_MAX_NMOM];
-    for (int n = 0; n < nm; n++) mub[n] = 0.0;
-    recursion_reverse<KP>(mu, r, tp, abar[q], bbar[q], mub);
-    double* w = q == 0 ? A.w : w2;
-    for (int n = 0; n < nm; n++) {
-      w[(size_t)o * nm + n] = mub[n];
-      bad |= !isfinite(mub[n]);
-    }
+  for (int n = 0; n < nm; n++) {
+    w[(size_t)o * nm + n] = mub[n];
+    bad |= !isfinite(mub[n]);
   }
   if (bad) raise_error(A.status, BOP_DEV_ERR_NONFINITE);
 }
+
 
 int red_grid2(int M) {
   int g = (M + RT2 - 1) / RT2;
@@ -618,16 +617,16 @@ int launch_weights(const WeightArgs& a, cudaStream_t s) {
 
 int launch_weights_pair(const WeightArgs& a, double cU1, double cN1, double cU2, double cN2, double* w2,
                         cudaStream_t s) {
-  const int g = (a.M + CT - 1) / CT, Kp = (a.n_mom - 1) / 2;
+  const int g = (2 * a.M + CT - 1) / CT, Kp = (a.n_mom - 1) / 2;
   switch (Kp) {
-    case 1: k_weights_pair<1><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
-    case 2: k_weights_pair<2><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
-    case 3: k_weights_pair<3><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
-    case 4: k_weights_pair<4><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
-    case 5: k_weights_pair<5><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
-    case 6: k_weights_pair<6><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
-    case 7: k_weights_pair<7><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
-    case 8: k_weights_pair<8><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 1: k_weights_split<1><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 2: k_weights_split<2><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 3: k_weights_split<3><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 4: k_weights_split<4><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 5: k_weights_split<5><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 6: k_weights_split<6><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 7: k_weights_split<7><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+    case 8: k_weights_split<8><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
     default: return -1;
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -229,7 +229,7 @@ struct WeightArgs {
 };
 int launch_weights(const WeightArgs& a, cudaStream_t s);
 // Weights of L1 = cU1 U + cN1 N into a.w and of L2 = cU2 U + cN2 N into w2 at
-// fixed E_F (a.lam unused), one forward pass; a.zscratch: [3][n_exp+1][M].
+// fixed E_F (a.lam unused), one lane per seed; a.zscratch: [4][n_exp+1][M].
 int launch_weights_pair(const WeightArgs& a, double cU1, double cN1, double cU2, double cN2, double* w2,
                         cudaStream_t s);
 int launch_ef_response(int M, int n_exp, const double* gsig, const double* inv, const double* a_inf,
