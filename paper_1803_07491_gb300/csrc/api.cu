@@ -747,7 +747,9 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
   CKS(ensure(c, c->rwt, sizeof(double) * (size_t)M * nm));
   CKS(ensure(c, c->rdUE, sizeof(double) * (size_t)M));
   CKS(ensure(c, c->rvec, sizeof(double) * (size_t)nu * (GM_KRYLOV + 6)));
-  CKS(ensure(c, c->rcoef, sizeof(double) * (GM_KRYLOV + 2)));
+  // coef: [0, K+2) host-set coefficients; then the Gram-Schmidt passes and
+  // the norm of one Arnoldi step, read back together
+  CKS(ensure(c, c->rcoef, sizeof(double) * (3 * GM_KRYLOV + 8)));
   double* V = P<double>(c->rvec);                 // Krylov basis [GM_KRYLOV + 1][nu]
   double* rhs = V + (size_t)(GM_KRYLOV + 1) * nu;  // dE/du
   double* Pd = rhs + nu;                           // diagonal preconditioner
@@ -842,20 +844,20 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
       double* u = V + (size_t)(j + 1) * nu;
       if (launch_scale_vec(nu, vj, Pd, 1.0, tmp, s)) return fail(c, BOP_ERR_CUDA, "response kernels failed");
       CKS(matvec(tmp, u));
-      // classical Gram-Schmidt, twice
-      double h[GM_KRYLOV + 1], h2[GM_KRYLOV + 1];
-      for (int pass = 0; pass < 2; pass++) {
-        double* hp = pass ? h2 : h;
-        if (launch_dots(nu, j + 1, V, u, coef, s)) return fail(c, BOP_ERR_CUDA, "response kernels failed");
-        CKS(read_back(c, coef, hp, j + 1, s));
-        if (launch_axpy_multi(nu, j + 1, V, coef, u, s)) return fail(c, BOP_ERR_CUDA, "response kernels failed");
-      }
-      for (int q = 0; q <= j; q++) h[q] += h2[q];
-      double hn = 0.0;
-      CKS(dot(u, u, &hn));
-      hn = std::sqrt(hn);
-      if (hn > 0.0 && launch_scale_vec(nu, u, nullptr, 1.0 / hn, u, s))
+      // classical Gram-Schmidt, twice, with the coefficients kept on the
+      // device; then |u|^2 and u / |u| (device norm): one readback per step
+      double* gs1 = coef + GM_KRYLOV + 2;
+      double* gs2 = gs1 + GM_KRYLOV + 1;
+      double* nrm = gs2 + GM_KRYLOV + 1;
+      if (launch_dots(nu, j + 1, V, u, gs1, s) || launch_axpy_multi(nu, j + 1, V, gs1, u, s) ||
+          launch_dots(nu, j + 1, V, u, gs2, s) || launch_axpy_multi(nu, j + 1, V, gs2, u, s) ||
+          launch_dots(nu, 1, u, u, nrm, s) || launch_scale_by_inv_norm(nu, u, nrm, s))
         return fail(c, BOP_ERR_CUDA, "response kernels failed");
+      double hb[3 * GM_KRYLOV + 4];
+      CKS(read_back(c, gs1, hb, 2 * (GM_KRYLOV + 1) + 1, s));
+      double h[GM_KRYLOV + 1];
+      for (int q = 0; q <= j; q++) h[q] = hb[q] + hb[GM_KRYLOV + 1 + q];
+      const double hn = std::sqrt(hb[2 * (GM_KRYLOV + 1)]);
       // Givens rotations on the new Hessenberg column
       for (int q = 0; q < j; q++) {
         const double t0 = cs[q] * h[q] + sn[q] * h[q + 1];
@@ -885,7 +887,6 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
     if (launch_lincomb(nu, k, V, coef, Pd, 1.0, yc, s)) return fail(c, BOP_ERR_CUDA, "response kernels failed");
     CK(cudaMemcpyAsync(coef, &minus_one, sizeof(double), cudaMemcpyHostToDevice, s));
     if (launch_axpy_multi(nu, 1, yc, coef, y, s)) return fail(c, BOP_ERR_CUDA, "response kernels failed");
-    CK(cudaStreamSynchronize(s));
     conv = rel <= rtol;
   }
   c->st.response_iterations = iters;

@@ -279,6 +279,7 @@ const float* mlp_norm_dev(const bop_mlp* net);
 int launch_var_lambda(int n, int norb, double s, double J, double n0, const double* N, const double* dos,
                       const double* onsite, const FermiState* st, double* q, double* lam, double* red,
                       unsigned* counter, cudaStream_t stream);
+int launch_scale_by_inv_norm(int nu, double* u, const double* nsq, cudaStream_t stream);
 int launch_scale_weights(int n, int norb, int S, int n_mom, double s, int stoner, const double* v, double sign,
                          const double* wN, const double* wU, double* w_out, cudaStream_t st);
 // out_u = derivative w.r.t. u of a function whose onsite-level derivative is Eb (+ dUE):

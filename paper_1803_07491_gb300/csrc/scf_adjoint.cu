@@ -161,6 +161,14 @@ __global__ void __launch_bounds__(VT) k_var_lambda(int n, int norb, double s, do
   *counter = 0;
 }
 
+// u /= sqrt(*nsq) when *nsq > 0 (the norm stays on the device)
+__global__ void k_scale_by_inv_norm(int nu, double* __restrict__ u, const double* __restrict__ nsq) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double q = *nsq;
+  if (i >= nu || !(q > 0.0)) return;
+  u[i] = u[i] * (1.0 / sqrt(q));
+}
+
 unsigned grid(long long n) { return (unsigned)((n + VT - 1) / VT); }
 int ok() { return cudaGetLastError() == cudaSuccess ? 0 : -1; }
 
@@ -215,5 +223,10 @@ int launch_var_lambda(int n, int norb, double s, double J, double n0, const doub
   if (g < 1) g = 1;
   if (g > 1024) g = 1024;
   k_var_lambda<<<g, VT, 0, stream>>>(n, norb, s, J, n0, N, dos, onsite, st, q, lam, red, counter);
+  return ok();
+}
+
+int launch_scale_by_inv_norm(int nu, double* u, const double* nsq, cudaStream_t stream) {
+  k_scale_by_inv_norm<<<grid(nu), VT, 0, stream>>>(nu, u, nsq);
   return ok();
 }
