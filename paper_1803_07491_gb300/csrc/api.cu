@@ -1116,7 +1116,9 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
   CK(cudaMemsetAsync(c->lsum.p, 0, sizeof(long long) * (n + 1), s));
   launch_level_sums(n, c->K, P<int>(c->level_end), P<long long>(c->lsum), s);
   CKS(exclusive_scan(c, P<long long>(c->lsum), P<long long>(c->psi_off), n + 1, s));
+  unsigned long long np = 0;
   CK(cudaMemcpyAsync(&c->psi_tot, P<long long>(c->psi_off) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&np, c->nprod.p, sizeof(np), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   c->psi_valid = false;
   c->built = true;
@@ -1128,11 +1130,7 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
   c->st.n_sites = c->nsite;
   c->st.n_adj = c->nadj;
   c->st.max_cluster = c->maxlev[c->K];
-  {
-    unsigned long long np = 0;
-    CK(cudaMemcpy(&np, c->nprod.p, sizeof(np), cudaMemcpyDeviceToHost));
-    c->st.moment_products = (long long)np;
-  }
+  c->st.moment_products = (long long)np;
   return BOP_OK;
 }
 
