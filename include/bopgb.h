@@ -186,8 +186,8 @@ typedef struct {
   int n_unbounded;           /* orbitals (all spins) of the last energy, constant
                                 terminator, whose expansion has some |sigma_m| > m + 1:
                                 the chain has weight outside [A - 2B, A + 2B] and the
-                                Chebyshev series grows with n_exp (0 for the Gershgorin
-                                and min / max estimates in practice) */
+                                Chebyshev series grows with n_exp.  Checked for the
+                                estimates other than BOP_BW_GERSHGORIN (0 there) */
 } bop_stats;
 
 /* Library version (major * 10000 + minor * 100 + patch). */

@@ -515,9 +515,11 @@ int run_scalar(bop_ctx* c, int M, const double* mu, cudaStream_t s) {
   a.status = P<unsigned>(c->status);
   a.bw = band_sel(c->m);
   // lcount: [0] learned orbitals, [1] orbitals outside the estimated band
+  // (checked for the estimates other than Gershgorin, whose band holds every
+  // Gershgorin disc; the check costs FP64 work in every coefficient)
   CKS(ensure(c, c->lcount, 2 * sizeof(unsigned)));
   CK(cudaMemsetAsync(c->lcount.p, 0, 2 * sizeof(unsigned), s));
-  a.n_unbounded = P<unsigned>(c->lcount) + 1;
+  a.n_unbounded = c->m.bandwidth != BOP_BW_GERSHGORIN ? P<unsigned>(c->lcount) + 1 : nullptr;
   Region R(c, PK_EXPAND, 1, s);
   if (launch_expand(a, s)) return fail(c, BOP_ERR_CUDA, "expand launch failed");
   return BOP_OK;

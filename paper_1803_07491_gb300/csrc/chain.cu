@@ -29,6 +29,21 @@ namespace {
 constexpr int CT = 32;  // threads per block: one orbital per thread, small blocks so that
                          // a few thousand orbitals still spread over all SMs (FP64-bound)
 
+// Fewer orbitals than one warp per SM sub-partition: the FP64 kernels then
+// give each orbital two lanes (the Fermi sums, the two seeds of the response
+// weights) so that every sub-partition's FP64 unit has work; with more
+// orbitals one lane per orbital avoids duplicating the per-orbital setup.
+int few_orbitals(int M) {
+  static int cap = 0;
+  if (cap == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cap = (sms > 0 ? sms : 1) * 4 * 32;
+  }
+  return M < cap;
+}
+
 // moments -> (a, b, a_inf, b_inf) -> g_m sigma_m, m = 0..n_exp, stored
 // coefficient-major gsig[m][M].
 template <int KP>
@@ -52,7 +67,8 @@ __global__ void __launch_bounds__(CT) k_expand(ScalarArgs A) {
   double Q[NP], P[NP];
   gen_polys<KP>(ch, r.nlev, Q, P);
   bool outside = false;
-  const double last = sigma_series<KP>(Q, P, ne, A.g, A.gsig, M, o, A.n_unbounded ? &outside : nullptr);
+  const double last = A.n_unbounded ? sigma_series<KP, true>(Q, P, ne, A.g, A.gsig, M, o, &outside)
+                                    : sigma_series<KP, false>(Q, P, ne, A.g, A.gsig, M, o);
   if (outside) atomicAdd(A.n_unbounded, 1u);
   if (!isfinite(t.a_inf) || !isfinite(t.b_inf) || !isfinite(last)) raise_error(A.status, BOP_DEV_ERR_NONFINITE);
 }
@@ -60,51 +76,33 @@ __global__ void __launch_bounds__(CT) k_expand(ScalarArgs A) {
 // Sums over the sine series of one orbital at x = cos(phi) (Clenshaw):
 //   N    = gs_0 (1 - phi/pi) + sum_k (gs_{k-2} - gs_k)/(pi k) sin(k phi)
 //   dNde = (2/pi) sum_m gs_m sin((m+1) phi)            (= dN/d eps)
-// gs_j = 0 outside 0..ne; inv[k] = 1/k.  With sin(k phi) = s U_{k-1}(x),
-// each sum over U_j is split into its even and odd terms, which obey
-// U_{j+2} = y U_j - U_{j-2} with y = 4x^2 - 2: four independent Clenshaw
-// chains of half the length (U_0 = 1, U_2 - y U_0 = 1; U_1 = 2x,
-// U_3 - y U_1 = 0), so that the FP64 pipe is not left waiting on one chain.
+// gs_j = 0 outside 0..ne; inv[k] = 1/k.
 __device__ __forceinline__ void count_and_dos(const double* __restrict__ gsig, const double* __restrict__ inv,
                                               int M, int o, int ne, double x, double* N, double* dNde) {
   auto G = [&](int j) -> double { return (j >= 0 && j <= ne) ? gsig[(size_t)j * M + o] : 0.0; };
   const double phi = acos(x), s = sqrt(fmax(0.0, 1.0 - x * x));
-  const double y = 4.0 * x * x - 2.0;
-  // S = sum_j a_{j+1} U_j, a_k = (gs_{k-2} - gs_k)/k;  C = sum_j gs_j U_j
-  double be1 = 0.0, be2 = 0.0, bo1 = 0.0, bo2 = 0.0;
-  double ce1 = 0.0, ce2 = 0.0, co1 = 0.0, co2 = 0.0;
-  const int top = (ne + 2) / 2;
-  double g1 = G(2 * top + 1), g2 = G(2 * top + 2);  // gs_{2i+1}, gs_{2i+2}
-  for (int i = top; i >= 0; i--) {
-    const int j = 2 * i;
-    const double gm1 = G(j - 1), g0 = G(j);
-    const double ae = (gm1 - g1) * inv[j + 1];  // a_{j+1}
-    const double ao = (g0 - g2) * inv[j + 2];   // a_{j+2}
-    const double be0 = ae + y * be1 - be2;
-    const double bo0 = ao + y * bo1 - bo2;
-    const double ce0 = g0 + y * ce1 - ce2;
-    const double co0 = g1 + y * co1 - co2;
-    be2 = be1;
-    be1 = be0;
-    bo2 = bo1;
-    bo1 = bo0;
-    ce2 = ce1;
-    ce1 = ce0;
-    co2 = co1;
-    co1 = co0;
-    g2 = g0;
-    g1 = gm1;
+  const double x2 = 2.0 * x;
+  double b1 = 0.0, b2 = 0.0, c1 = 0.0, c2 = 0.0;
+  for (int k = ne + 2; k >= 1; k--) {  // coefficient of U_{k-1}
+    const double b0 = (G(k - 2) - G(k)) * inv[k] + x2 * b1 - b2;
+    b2 = b1;
+    b1 = b0;
+    const double c0 = G(k - 1) + x2 * c1 - c2;
+    c2 = c1;
+    c1 = c0;
   }
-  const double S = (be1 + be2) + 2.0 * x * bo1;
-  const double C = (ce1 + ce2) + 2.0 * x * co1;
-  *N = G(0) * (1.0 - phi / PI) + s * S / PI;
-  *dNde = (2.0 / PI) * s * C;
+  *N = G(0) * (1.0 - phi / PI) + s * b1 / PI;
+  *dNde = (2.0 / PI) * s * c1;
 }
 
-// The same sums by a pair of adjacent lanes (par = lane & 1): the even
-// chains on lane 0, the odd ones on lane 1, exchanged at the end, so that an
-// orbital's FP64 work runs on two lanes (twice the warps for the same
-// orbitals; measured faster than one lane and than four lanes per orbital).
+// The same sums by a pair of adjacent lanes (par = lane & 1): with
+// sin(k phi) = s U_{k-1}(x), each sum over U_j splits into its even and odd
+// terms, which obey U_{j+2} = y U_j - U_{j-2} with y = 4x^2 - 2; lane 0 runs
+// the even Clenshaw chains (U_0 = 1, U_2 - y U_0 = 1), lane 1 the odd ones
+// (U_1 = 2x, U_3 - y U_1 = 0), exchanged at the end.  An orbital's FP64
+// work thus runs on two lanes (twice the warps for the same orbitals;
+// measured faster than one lane and than four lanes per orbital when there
+// are fewer orbitals than one warp per SM sub-partition).
 // pm: the pair's lane mask.  Both lanes return N and dNde.
 __device__ __forceinline__ void count_and_dos2(const double* __restrict__ gsig, const double* __restrict__ inv,
                                                int M, int o, int ne, double x, int par, unsigned pm, double* N,
@@ -381,7 +379,7 @@ __global__ void __launch_bounds__(FC) k_fermi_coop(int M, const double* __restri
                                                    const double* __restrict__ b_inf, int ne, double sfac,
                                                    double target, FermiState* st, double* part, int warm,
                                                    int max_rounds, double tol, double* __restrict__ Nout,
-                                                   double* __restrict__ dos) {
+                                                   double* __restrict__ dos, int lanes) {
   cooperative_groups::grid_group grid = cooperative_groups::this_grid();
   __shared__ double sh[FC / 32 + 1];
   __shared__ double fr[FC / 32 + 1];
@@ -409,17 +407,20 @@ __global__ void __launch_bounds__(FC) k_fermi_coop(int M, const double* __restri
   bool done = hi - lo < tol;
   if (done) ef = 0.5 * (lo + hi);
   bool evaluated = false;
-  // two lanes per orbital (count_and_dos2): thread t takes orbital t / 2
-  const int par = threadIdx.x & 1;
+  // lanes (1 or 2) per orbital: thread t takes orbital t / lanes; with two,
+  // the pair shares the sums (count_and_dos2)
+  const int sh_l = lanes == 2 ? 1 : 0;
+  const int par = lanes == 2 ? (threadIdx.x & 1) : 0;
   const unsigned pm = 3u << ((threadIdx.x & 31) & ~1);
   for (int r = 0; !done && r < max_rounds; r++) {
     double aN = 0.0, aD = 0.0;
-    for (int t = b * FC + threadIdx.x; (t >> 1) < M; t += stride) {
-      const int o = t >> 1;
+    for (int t = b * FC + threadIdx.x; (t >> sh_l) < M; t += stride) {
+      const int o = t >> sh_l;
       const double bi = b_inf[o];
       const double xr = (E - a_inf[o]) / (2.0 * bi);
       double Nv, dN;
-      count_and_dos2(gsig, inv, M, o, ne, clamp1(xr), par, pm, &Nv, &dN);
+      if (sh_l) count_and_dos2(gsig, inv, M, o, ne, clamp1(xr), par, pm, &Nv, &dN);
+      else count_and_dos(gsig, inv, M, o, ne, clamp1(xr), &Nv, &dN);
       const double d = (xr > -1.0 && xr < 1.0) ? dN / (2.0 * bi) : 0.0;
       if (par == 0) {
         aN += Nv;
@@ -465,12 +466,13 @@ __global__ void __launch_bounds__(FC) k_fermi_coop(int M, const double* __restri
     st->done = done ? 1 : 0;
   }
   if (!evaluated) {  // bracket narrower than tol: N and DOS at its midpoint
-    for (int t = b * FC + threadIdx.x; (t >> 1) < M; t += stride) {
-      const int o = t >> 1;
+    for (int t = b * FC + threadIdx.x; (t >> sh_l) < M; t += stride) {
+      const int o = t >> sh_l;
       const double bi = b_inf[o];
       const double xr = (ef - a_inf[o]) / (2.0 * bi);
       double Nv, dN;
-      count_and_dos2(gsig, inv, M, o, ne, clamp1(xr), par, pm, &Nv, &dN);
+      if (sh_l) count_and_dos2(gsig, inv, M, o, ne, clamp1(xr), par, pm, &Nv, &dN);
+      else count_and_dos(gsig, inv, M, o, ne, clamp1(xr), &Nv, &dN);
       if (par == 0) {
         Nout[o] = Nv;
         dos[o] = (xr > -1.0 && xr < 1.0) ? dN / (2.0 * bi) : 0.0;
@@ -524,6 +526,51 @@ __global__ void __launch_bounds__(CT) k_weights(WeightArgs A) {
   for (int n = 0; n < nm; n++) {
     A.w[(size_t)o * nm + n] = mub[n];
     bad |= !isfinite(mub[n]);
+  }
+  if (bad) raise_error(A.status, BOP_DEV_ERR_NONFINITE);
+}
+
+// Two weight sets at once, w1 for (cU1, cN1) and w2 for (cU2, cN2), both
+// at fixed E_F (no E_F multiplier): the SCF-response solve needs dU/dmu and
+// dN/dmu.  The forward part of the chain runs once.  zscratch holds sigma_m
+// and the two cotangents ([3][n_exp+1][M]).
+template <int KP>
+__global__ void __launch_bounds__(CT) k_weights_pair(WeightArgs A, double cU1, double cN1, double cU2, double cN2,
+                                                     double* __restrict__ w2) {
+  const int o = blockIdx.x * CT + threadIdx.x;
+  if (o >= A.M) return;
+  const int M = A.M, nm = 2 * KP + 1;
+  double mu[BOP_MAX_NMOM];
+  for (int n = 0; n < nm; n++) mu[n] = A.mu[(size_t)o * nm + n];
+  Rec r;
+  RecTape<KP> tp;
+  recursion_taped<KP>(mu, r, tp);
+  const Term t = bandwidth(r, A.bw);
+  Chain ch;
+  chain_params(r, t, KP, ch);
+  double abar[2][KPMAX + 1], bbar[2][KPMAX + 2];
+  for (int q = 0; q < 2; q++) {
+    for (int k = 0; k <= KPMAX; k++) abar[q][k] = 0.0;
+    for (int k = 0; k <= KPMAX + 1; k++) bbar[q][k] = 0.0;
+  }
+  double abar_inf[2] = {0.0, 0.0}, bbar_inf[2] = {0.0, 0.0}, dE[2];
+  const double cU[2] = {cU1, cU2}, cN[2] = {cN1, cN2};
+  const size_t zl = (size_t)(A.n_exp + 1) * M;
+  double* zb[2] = {A.zscratch + zl, A.zscratch + 2 * zl};
+  chain_reverse_ns<KP, 2>(ch, r.nlev, KP, t.a_inf, t.b_inf, A.onsite[o], A.st->ef, A.g, A.inv, A.n_exp, M, o, cU,
+                          cN, A.zscratch, zb, abar, bbar, abar_inf, bbar_inf, dE);
+  if (A.dU_dE) A.dU_dE[o] = dE[0];
+  bool bad = false;
+  for (int q = 0; q < 2; q++) {
+    bandwidth_reverse(r, t, A.bw, abar_inf[q], bbar_inf[q], abar[q], bbar[q]);
+    double mub[BOP_MAX_NMOM];
+    for (int n = 0; n < nm; n++) mub[n] = 0.0;
+    recursion_reverse<KP>(mu, r, tp, abar[q], bbar[q], mub);
+    double* w = q == 0 ? A.w : w2;
+    for (int n = 0; n < nm; n++) {
+      w[(size_t)o * nm + n] = mub[n];
+      bad |= !isfinite(mub[n]);
+    }
   }
   if (bad) raise_error(A.status, BOP_DEV_ERR_NONFINITE);
 }
@@ -617,7 +664,23 @@ int launch_weights(const WeightArgs& a, cudaStream_t s) {
 
 int launch_weights_pair(const WeightArgs& a, double cU1, double cN1, double cU2, double cN2, double* w2,
                         cudaStream_t s) {
-  const int g = (2 * a.M + CT - 1) / CT, Kp = (a.n_mom - 1) / 2;
+  const int Kp = (a.n_mom - 1) / 2;
+  if (!few_orbitals(a.M)) {  // enough warps already: one lane, one forward pass for both seeds
+    const int g = (a.M + CT - 1) / CT;
+    switch (Kp) {
+      case 1: k_weights_pair<1><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+      case 2: k_weights_pair<2><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+      case 3: k_weights_pair<3><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+      case 4: k_weights_pair<4><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+      case 5: k_weights_pair<5><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+      case 6: k_weights_pair<6><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+      case 7: k_weights_pair<7><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+      case 8: k_weights_pair<8><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
+      default: return -1;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  }
+  const int g = (2 * a.M + CT - 1) / CT;
   switch (Kp) {
     case 1: k_weights_split<1><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
     case 2: k_weights_split<2><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
@@ -671,11 +734,12 @@ int launch_fermi_coop(int M, const double* gsig, const double* inv, const double
                       int max_rounds, double tol, double* N, double* dos, cudaStream_t s) {
   const int gmax = fermi_coop_grid();
   if (gmax <= 0) return -2;
-  int g = (2 * M + FC - 1) / FC;  // two lanes per orbital
+  int lanes = few_orbitals(M) ? 2 : 1;
+  int g = (lanes * M + FC - 1) / FC;
   if (g > gmax) g = gmax;
   if (g < 1) g = 1;
   void* args[] = {&M, &gsig, &inv, &a_inf, &b_inf, &n_exp, &spin_factor, &target, &st, &partials, &warm,
-                  &max_rounds, &tol, &N, &dos};
+                  &max_rounds, &tol, &N, &dos, &lanes};
   if (cudaLaunchCooperativeKernel((const void*)k_fermi_coop, g, FC, args, 0, s) != cudaSuccess) return -1;
   return 0;
 }

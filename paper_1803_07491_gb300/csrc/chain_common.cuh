@@ -43,12 +43,12 @@ __device__ __forceinline__ void gen_polys(const Chain& ch, int L, double Q[2 * K
 
 // g_m sigma_m, m = 0..ne, into gsig[m][M] from the recurrence
 // sigma_m = [D_1]_m - sum_{j>=1} [D_0]_j sigma_{m-j}.  Returns sigma_ne.
-template <int KP>
-// With a non-null `outside`, *outside becomes true if some |sigma_m| > m + 1:
-// sigma_m is the integral of U_m(x) times a density of unit weight, and
-// |U_m| <= m + 1 on [-1, 1], so the density then has weight outside the
-// estimated band (a bound state of the terminated chain) and the series
-// grows with m.
+// With CHECK, *outside becomes true if some |sigma_m| > m + 1: sigma_m is
+// the integral of U_m(x) times a density of unit weight, and |U_m| <= m + 1
+// on [-1, 1], so the density then has weight outside the estimated band (a
+// bound state of the terminated chain) and the series grows with m.  (A
+// separate instantiation: the check is FP64 work in every coefficient.)
+template <int KP, bool CHECK = false>
 __device__ __forceinline__ double sigma_series(double Q[2 * KP + 1], double P[2 * KP + 1], int ne,
                                                const double* __restrict__ g, double* __restrict__ gsig, int M,
                                                int o, bool* outside = nullptr) {
@@ -67,7 +67,7 @@ __device__ __forceinline__ double sigma_series(double Q[2 * KP + 1], double P[2 
     for (int j = NP - 2; j >= 1; j--) h[j] = h[j - 1];
     h[0] = v;
     gsig[(size_t)m * M + o] = g[m] * v;
-    if (outside && fabs(v) > (m + 1) * (1.0 + 1e-9)) *outside = true;
+    if (CHECK && fabs(v) > (m + 1) * (1.0 + 1e-9)) *outside = true;
   }
   return h[0];
 }

@@ -112,7 +112,7 @@ __device__ int block_exclusive_scan(int* v, int cnt, int* warp_tmp) {
   return carry;
 }
 
-template <int PASS>
+template <int PASS, bool CUT>
 __global__ void __launch_bounds__(CL_THREADS)
 k_cluster(int n, int K, const long long* __restrict__ row_ptr, const int* __restrict__ col,
           const signed char* __restrict__ img, const int* __restrict__ bond_of_edge, PathCut pc, ClusterScratch sc,
@@ -160,7 +160,7 @@ k_cluster(int n, int K, const long long* __restrict__ row_ptr, const int* __rest
             raise_error(status, BOP_DEV_ERR_IMAGE);
             continue;
           }
-          if (pc.r2 > 0.0) {  // path-radius cut: only sites closer than r_path to the atom
+          if (CUT) {  // path-radius cut: only sites closer than r_path to the atom
             double d[3];
             bond_vector(pc.pos + 3 * (size_t)atom, pc.pos + 3 * (size_t)col[e], pc.cell, sx, sy, sz, d);
             if (!(norm2_rn(d) < pc.r2)) continue;
@@ -309,14 +309,13 @@ int launch_cluster(int pass, int n, int K, const long long* row_ptr, const int* 
                    const int* bond_of_edge, PathCut pc, ClusterScratch sc, ClusterOut out, int grid,
                    unsigned* status, cudaStream_t s) {
   size_t smem = (size_t)sc.newcap * sizeof(unsigned long long);  // newcap is a power of two
-  if (smem > 48 * 1024) {
-    auto fn = pass == 0 ? k_cluster<0> : k_cluster<1>;
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  }
-  if (pass == 0)
-    k_cluster<0><<<grid, CL_THREADS, smem, s>>>(n, K, row_ptr, col, img, bond_of_edge, pc, sc, out, status);
-  else
-    k_cluster<1><<<grid, CL_THREADS, smem, s>>>(n, K, row_ptr, col, img, bond_of_edge, pc, sc, out, status);
+  // the path cut is a separate instantiation: its distance arithmetic costs
+  // registers that the uncut BFS does not need
+  const bool cut = pc.r2 > 0.0;
+  auto fn = pass == 0 ? (cut ? k_cluster<0, true> : k_cluster<0, false>)
+                      : (cut ? k_cluster<1, true> : k_cluster<1, false>);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  fn<<<grid, CL_THREADS, smem, s>>>(n, K, row_ptr, col, img, bond_of_edge, pc, sc, out, status);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
