@@ -74,8 +74,9 @@ struct bop_ctx {
   // learned terminator
   bop_mlp* net = nullptr;
   DBuf lbase, lnlev, lflag, lxs, lys, lZ1, lH1, lZ2, lH2, lybar, lcot, lxbar, lcount;
-  // SCF response of the forces
-  DBuf rwN, rwt, rdUE, rvec, rcoef;
+  // SCF response of the forces (rjv: per-site values of one dN/dmu sweep, the
+  // rows of the Jacobian)
+  DBuf rwN, rwt, rdUE, rvec, rcoef, rjv, rjcnt, rjptr, rjidx, rjrow;
   // variational SCF: dU_B/d delta, q; weights in w valid for the final state
   DBuf vgrad, vq;
   bool var_w_valid = false;
@@ -673,7 +674,8 @@ int prepare_psi_store(bop_ctx* c, cudaStream_t s) {
 
 // One reverse sweep of the moments with weights w: Hbar += dL/dH (if not
 // NULL), Ebar += dL/dE (if not NULL).  Over the stored Psi when present.
-int adjoint_pass(bop_ctx* c, const double* w, double* Hbar, double* Ebar, cudaStream_t s) {
+int adjoint_pass(bop_ctx* c, const double* w, double* Hbar, double* Ebar, cudaStream_t s,
+                 double* siteval = nullptr) {
   const int n = c->n;
   AdjointArgs aa;
   memset(&aa, 0, sizeof(aa));
@@ -705,7 +707,10 @@ int adjoint_pass(bop_ctx* c, const double* w, double* Hbar, double* Ebar, cudaSt
     aa.max_sites = c->maxlev[c->K] > 0 ? c->maxlev[c->K] : 1;
     aa.max_adj = c->maxlev[c->K + 1] > 0 ? c->maxlev[c->K + 1] : 1;
     aa.cap_eb = c->maxlev[c->K - 1] > 0 ? c->maxlev[c->K - 1] : 1;
+    aa.siteval = siteval;
+    aa.sv_stride = c->nsite;
   } else {
+    if (siteval) return fail(c, BOP_ERR_STATE, "per-site cotangents need the stored Psi");
     int nc = adjoint_columns(c->norb);
     size_t per_site = (size_t)c->norb * nc;
     long long levsum = 0;
@@ -798,8 +803,39 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
                      nullptr, rhs, s) ||
       launch_precond_diag(n, norb, S, c->sfac, c->m.dos_floor, P<double>(c->dos), Pd, s))
     return fail(c, BOP_ERR_CUDA, "response kernels failed");
-  // J^T v -> out
+  // J^T v -> out.  With the stored Psi, one sweep with the dN/dmu weights
+  // gives every row of J as per-site values (the weights of a product only
+  // scale each work item's), and each product is then a sparse pass over
+  // them instead of a reverse sweep.
+  const bool use_rows = c->psi_valid;
+  if (use_rows) {
+    const size_t ns = (size_t)(c->nsite > 0 ? c->nsite : 1);
+    CKS(ensure(c, c->rjv, sizeof(double) * (size_t)S * ns));
+    CKS(ensure(c, c->rjcnt, sizeof(int) * (size_t)(n + 1)));
+    CKS(ensure(c, c->rjptr, sizeof(long long) * (size_t)(n + 1)));
+    CKS(ensure(c, c->rjidx, sizeof(long long) * ns));
+    CKS(ensure(c, c->rjrow, sizeof(int) * ns));
+    CK(cudaMemsetAsync(c->rjv.p, 0, sizeof(double) * (size_t)S * c->nsite, s));
+    CKS(adjoint_pass(c, wN, nullptr, nullptr, s, P<double>(c->rjv)));
+    // transpose of the rows (structure only)
+    CK(cudaMemsetAsync(c->rjcnt.p, 0, sizeof(int) * (size_t)(n + 1), s));
+    if (launch_jt_build(n, c->K, P<long long>(c->site_off), P<int>(c->level_end), P<int>(c->site_atom),
+                        P<int>(c->rjcnt), 0, nullptr, nullptr, nullptr, s))
+      return fail(c, BOP_ERR_CUDA, "response kernels failed");
+    CKS(exclusive_scan(c, P<int>(c->rjcnt), P<long long>(c->rjptr), n + 1, s));
+    CK(cudaMemsetAsync(c->rjcnt.p, 0, sizeof(int) * (size_t)(n + 1), s));
+    if (launch_jt_build(n, c->K, P<long long>(c->site_off), P<int>(c->level_end), P<int>(c->site_atom),
+                        P<int>(c->rjcnt), 1, P<long long>(c->rjptr), P<long long>(c->rjidx), P<int>(c->rjrow), s))
+      return fail(c, BOP_ERR_CUDA, "response kernels failed");
+  }
   auto matvec = [&](const double* v, double* out) -> int {
+    if (use_rows) {
+      if (launch_jt_gather(n, S, P<long long>(c->rjptr), P<long long>(c->rjidx), P<int>(c->rjrow),
+                           P<double>(c->rjv), c->nsite, v, c->sfac, stoner ? 1 : 0, Eb, s) ||
+          launch_project(n, 1, S, I, Eb, nullptr, nullptr, 0.0, stoner ? v + n : nullptr, out, s))
+        return fail(c, BOP_ERR_CUDA, "response kernels failed");
+      return BOP_OK;
+    }
     if (launch_scale_weights(n, norb, S, nm, c->sfac, stoner ? 1 : 0, v, 1.0, wN, nullptr, P<double>(c->rwt), s))
       return fail(c, BOP_ERR_CUDA, "response kernels failed");
     CK(cudaMemsetAsync(Eb, 0, sizeof(double) * M, s));
@@ -1010,7 +1046,7 @@ int bop_destroy(bop_ctx* c) {
                   &c->adjscr, &c->Hbar, &c->Ebar, &c->status, &c->cub_tmp, &c->nprod,
                   &c->ginv, &c->hx, &c->hf, &c->gamma, &c->scfred, &c->lbase, &c->lnlev, &c->lflag, &c->lxs,
                   &c->lys, &c->lZ1, &c->lH1, &c->lZ2, &c->lH2, &c->lybar, &c->lcot, &c->lxbar, &c->lcount,
-                  &c->rwN, &c->rwt, &c->rdUE, &c->rvec, &c->rcoef, &c->vgrad, &c->vq, &c->erep,
+                  &c->rwN, &c->rwt, &c->rdUE, &c->rvec, &c->rcoef, &c->rjv, &c->rjcnt, &c->rjptr, &c->rjidx, &c->rjrow, &c->vgrad, &c->vq, &c->erep,
                   &c->psi_off, &c->psis, &c->psib, &c->lsum};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);

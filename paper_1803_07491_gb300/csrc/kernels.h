@@ -113,6 +113,11 @@ struct AdjointArgs {
   int nc;              // columns per work item used by the forward pass that stored Psi
   int cap_even, cap_odd;  // largest even / odd level |C_k|, k = 1..K
   int max_sites, max_adj, cap_eb;  // cap_eb: largest |C_K-1|
+  // stored-Psi sweep only: per cluster site t of work item (spin, atom i),
+  // sum over the orbitals of dL/dE_t (+=), at siteval[spin * sv_stride +
+  // site_off[i] + t] (t < |C_K-1|); may be null
+  double* siteval;
+  long long sv_stride;
 };
 int launch_moments_adjoint(const AdjointArgs& a, int fp64, cudaStream_t s);
 
@@ -280,6 +285,17 @@ int launch_var_lambda(int n, int norb, double s, double J, double n0, const doub
                       const double* onsite, const FermiState* st, double* q, double* lam, double* red,
                       unsigned* counter, cudaStream_t stream);
 int launch_scale_by_inv_norm(int nu, double* u, const double* nsq, cudaStream_t stream);
+// J^T v of the SCF response from the per-site values of one sweep with the
+// dN/dmu weights (AdjointArgs.siteval).  The transpose of the rows: for
+// every atom j the global sites of other atoms' clusters (first |C_K-1|
+// sites) whose atom is j, with the owning atom (stage 0: counts into cnt;
+// stage 1 after the scan of cnt into ptr: fill, cnt zeroed first).  Then
+// Eb[spin][j] = sum over the entries of c_{i,spin} val[spin][site], c =
+// s v[i] (+ sigma_spin v[n + i] for Stoner).  Eb: [S][n].
+int launch_jt_build(int n, int K, const long long* site_off, const int* level_end, const int* site_atom,
+                    int* cnt, int stage, const long long* ptr, long long* idx, int* row, cudaStream_t stream);
+int launch_jt_gather(int n, int S, const long long* ptr, const long long* idx, const int* row, const double* val,
+                     long long stride, const double* v, double s, int stoner, double* Eb, cudaStream_t stream);
 int launch_scale_weights(int n, int norb, int S, int n_mom, double s, int stoner, const double* v, double sign,
                          const double* wN, const double* wU, double* w_out, cudaStream_t st);
 // out_u = derivative w.r.t. u of a function whose onsite-level derivative is Eb (+ dUE):

@@ -471,7 +471,8 @@ __global__ void __launch_bounds__(FWD_THREADS, sizeof(T) == 4 ? 2 : 1)
 k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_mom,
           RevSmem L, int n_items, int chunk, const T* __restrict__ pstore, T* __restrict__ pbstore,
           const long long* __restrict__ psi_off, long long psi_tot, const double* __restrict__ wts,
-          double* __restrict__ Hbar, int HSu, double* __restrict__ Ebar) {
+          double* __restrict__ Hbar, int HSu, double* __restrict__ Ebar, double* __restrict__ siteval,
+          long long sv_stride) {
   constexpr int N = NO * NC;
   constexpr int PS = (N == 1) ? 1 : Row<T, N>::PS;
   constexpr int HB = hb_count<NO>();
@@ -625,6 +626,14 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
       for (int q = tid; q < neb * NO; q += FWD_THREADS) {
         const int t = q / NO, r = q % NO;
         atomicAdd(Ebar + ((size_t)spin * n + (L.stage ? s_atom[t] : satom[t])) * NO + r, (double)eb[q]);
+      }
+    }
+    if (siteval != nullptr) {  // per-site sums over the orbitals (one row of the SCF Jacobian)
+      for (int t = tid; t < neb; t += FWD_THREADS) {
+        double a = 0.0;
+#pragma unroll
+        for (int r = 0; r < NO; r++) a += (double)eb[t * NO + r];
+        atomicAdd(siteval + (size_t)spin * sv_stride + s0 + t, a);
       }
     }
     if (HBAR) {
@@ -921,7 +930,7 @@ int run_reverse(const AdjointArgs& a, cudaStream_t s) {
   const int grid = (n_items + chunk - 1) / chunk;
   fn<<<grid, FWD_THREADS, smem, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n, a.n_mom, L, n_items, chunk,
                                       (const T*)a.pstore, (T*)a.pbstore, a.psi_off, a.psi_tot, a.w, a.Hbar, a.HSu,
-                                      a.Ebar);
+                                      a.Ebar, a.siteval, a.sv_stride);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

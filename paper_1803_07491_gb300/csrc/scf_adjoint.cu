@@ -169,6 +169,57 @@ __global__ void k_scale_by_inv_norm(int nu, double* __restrict__ u, const double
   u[i] = u[i] * (1.0 / sqrt(q));
 }
 
+// Transpose of the Jacobian rows: for every atom j the entries (i, site)
+// with site_atom[site] = j among the first |C_K-1| sites of i's cluster.
+// Count, then fill (rows in arbitrary order within an atom).
+__global__ void k_jt_count(int n, int K, const long long* __restrict__ site_off, const int* __restrict__ level_end,
+                           const int* __restrict__ site_atom, int* __restrict__ cnt) {
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const long long s0 = site_off[i];
+  const int neb = level_end[(size_t)i * (K + 1) + K - 1];
+  for (int t = lane; t < neb; t += 32) atomicAdd(cnt + site_atom[s0 + t], 1);
+}
+
+__global__ void k_jt_fill(int n, int K, const long long* __restrict__ site_off, const int* __restrict__ level_end,
+                          const int* __restrict__ site_atom, const long long* __restrict__ ptr,
+                          int* __restrict__ fill, long long* __restrict__ idx, int* __restrict__ row) {
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const long long s0 = site_off[i];
+  const int neb = level_end[(size_t)i * (K + 1) + K - 1];
+  for (int t = lane; t < neb; t += 32) {
+    const int j = site_atom[s0 + t];
+    const long long q = ptr[j] + atomicAdd(fill + j, 1);
+    idx[q] = s0 + t;
+    row[q] = i;
+  }
+}
+
+// One warp per (spin, atom j): Eb[spin][j] = sum over j's entries of
+// c_{i,spin} val[spin][site], c = s v[i] (+ sigma_spin v[n + i] for Stoner).
+__global__ void k_jt_gather(int n, int S, const long long* __restrict__ ptr, const long long* __restrict__ idx,
+                            const int* __restrict__ row, const double* __restrict__ val, long long stride,
+                            const double* __restrict__ v, double s, int stoner, double* __restrict__ Eb) {
+  const int wg = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (wg >= S * n) return;
+  const int spin = wg / n, j = wg % n;
+  const double sg = spin == 0 ? 1.0 : -1.0;
+  const double* vs = val + (size_t)spin * stride;
+  double a = 0.0;
+  for (long long q = ptr[j] + lane; q < ptr[j + 1]; q += 32) {
+    const int i = row[q];
+    double c = s * v[i];
+    if (stoner) c += sg * v[n + i];
+    a += c * vs[idx[q]];
+  }
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (lane == 0) Eb[(size_t)spin * n + j] = a;
+}
+
 unsigned grid(long long n) { return (unsigned)((n + VT - 1) / VT); }
 int ok() { return cudaGetLastError() == cudaSuccess ? 0 : -1; }
 
@@ -228,5 +279,20 @@ int launch_var_lambda(int n, int norb, double s, double J, double n0, const doub
 
 int launch_scale_by_inv_norm(int nu, double* u, const double* nsq, cudaStream_t stream) {
   k_scale_by_inv_norm<<<grid(nu), VT, 0, stream>>>(nu, u, nsq);
+  return ok();
+}
+
+int launch_jt_build(int n, int K, const long long* site_off, const int* level_end, const int* site_atom,
+                    int* cnt, int stage, const long long* ptr, long long* idx, int* row, cudaStream_t stream) {
+  const long long threads = (long long)n * 32;
+  if (stage == 0) k_jt_count<<<grid(threads), VT, 0, stream>>>(n, K, site_off, level_end, site_atom, cnt);
+  else k_jt_fill<<<grid(threads), VT, 0, stream>>>(n, K, site_off, level_end, site_atom, ptr, cnt, idx, row);
+  return ok();
+}
+
+int launch_jt_gather(int n, int S, const long long* ptr, const long long* idx, const int* row, const double* val,
+                     long long stride, const double* v, double s, int stoner, double* Eb, cudaStream_t stream) {
+  const long long threads = (long long)S * n * 32;
+  k_jt_gather<<<grid(threads), VT, 0, stream>>>(n, S, ptr, idx, row, val, stride, v, s, stoner, Eb);
   return ok();
 }
