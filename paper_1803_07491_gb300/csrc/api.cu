@@ -80,6 +80,9 @@ struct bop_ctx {
   // variational SCF: dU_B/d delta, q; weights in w valid for the final state
   DBuf vgrad, vq;
   bool var_w_valid = false;
+  // the last bop_energy was followed by bop_forces: the next one stores Psi
+  // in its SCF passes for the reverse sweeps (no extra forward pass)
+  bool forces_follow = false;
   DBuf erep;  // pair repulsion per atom
   // stored Psi of every work item for the reverse sweeps (when it fits)
   DBuf psi_off, psis, psib, lsum;
@@ -659,10 +662,10 @@ int psi_store_alloc(bop_ctx* c, bool* fits) {
 }
 
 int prepare_psi_store(bop_ctx* c, cudaStream_t s) {
-  // the variational SCF loop stores Psi in its forward passes; the last one
-  // is at the final onsite levels
-  if (c->m.scf == BOP_SCF_VARIATIONAL) return BOP_OK;
-  c->psi_valid = false;
+  // the SCF loop may have stored Psi in its forward passes; the last one is
+  // at the final onsite levels
+  c->forces_follow = true;
+  if (c->m.scf == BOP_SCF_VARIATIONAL || c->psi_valid) return BOP_OK;
   const bool several = (c->m.scf == BOP_SCF_LCN || c->m.scf == BOP_SCF_STONER) && c->m.scf_response;
   bool fits = false;
   if (several) CKS(psi_store_alloc(c, &fits));
@@ -1322,10 +1325,15 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   a.grad = nullptr;
   a.J = c->m.j_ii;
   // SCF residual of this iteration (for VARIATIONAL after the gradient sweep)
-  // the variational SCF sweeps back once per iteration: store Psi in each
-  // forward pass when it fits
+  // the variational SCF sweeps back once per iteration, and the response
+  // solve of forces that are expected to follow sweeps back several times:
+  // store Psi in each forward pass when it fits (the last pass is at the
+  // final onsite levels)
   bool var_store = false;
-  if (variational) CKS(psi_store_alloc(c, &var_store));
+  const bool resp_store = (c->m.scf == BOP_SCF_LCN || c->m.scf == BOP_SCF_STONER) && c->m.scf_response &&
+                          c->forces_follow;
+  if (variational || resp_store) CKS(psi_store_alloc(c, &var_store));
+  c->forces_follow = false;
   auto residual = [&]() -> int {
     if (variational) {
       CKS(var_gradient(c, s));
