@@ -274,7 +274,8 @@ def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: s
                    "terminator": w.run.terminator,
                    "scf_iterations": stats["scf_iterations"], "scf_tol": w.run.scf_tol,
                    "bisection_rounds": stats["bisection_rounds"],
-                   "forces": ("exact: U_B stationary in the shifts" if w.run.scf == "variational"
+                   "forces": ("exact (no SCF)" if w.run.scf == "none"
+                              else "exact: U_B stationary in the shifts" if w.run.scf == "variational"
                               else "exact: SCF response included" if stats["forces_scf_response"]
                               else "fixed onsite levels (Hellmann-Feynman form)"),
                    **({"J_ii": w.run.J_ii} if w.run.scf == "variational" else {}),
