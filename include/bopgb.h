@@ -258,7 +258,9 @@ int bop_recursion(bop_ctx* ctx, int M, const double* mu, double* a, double* b, i
  *   e_atom    device [n] bond (+ exchange) energy per atom, or NULL
  *   delta_io  device [n] LCN onsite shifts: read as the starting guess
  *             (warm start) and overwritten with the result; NULL = start
- *             from 0 and keep internally
+ *             from 0 and keep internally.  With delta_io the first Fermi
+ *             solve also starts from the previous call's Fermi level (when
+ *             it lies in the new bracket)
  *   m_io      device [n] Stoner moments, same convention (NULL = m0)
  *   stats_host optional host struct
  * Synchronises stream once per SCF iteration (convergence flag) and at

@@ -83,6 +83,7 @@ struct bop_ctx {
   // the last bop_energy was followed by bop_forces: the next one stores Psi
   // in its SCF passes for the reverse sweeps (no extra forward pass)
   bool forces_follow = false;
+  bool ef_solved = false;  // fstate holds a Fermi level of an earlier solve
   DBuf erep;  // pair repulsion per atom
   // stored Psi of every work item for the reverse sweeps (when it fits)
   DBuf psi_off, psis, psib, lsum;
@@ -867,9 +868,11 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
       CK(cudaMemcpyAsync(coef, &one, sizeof(double), cudaMemcpyHostToDevice, s));
       if (launch_axpy_multi(nu, 1, tmp, coef, V, s)) return fail(c, BOP_ERR_CUDA, "response kernels failed");
     }
-    double beta = 0.0;
-    CKS(dot(V, V, &beta));
-    beta = std::sqrt(beta);
+    double beta = bnorm;  // y = 0 in the first cycle: the residual is g
+    if (cyc > 0) {
+      CKS(dot(V, V, &beta));
+      beta = std::sqrt(beta);
+    }
     if (beta <= rtol * bnorm) {
       conv = true;
       rel = beta / bnorm;
@@ -1353,7 +1356,9 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
     CKS(run_moments(c, P<double>(c->onsite), P<double>(c->mu), s, var_store ? c->psis.p : nullptr));
     c->psi_valid = var_store;
     CKS(run_scalar(c, M, P<double>(c->mu), s));
-    CKS(fermi_and_N(c, it > 0, s));
+    // warm Fermi start: later SCF iterations, and the first one of a
+    // warm-started call after a previous solve
+    CKS(fermi_and_N(c, it > 0 || (delta_io != nullptr && c->ef_solved), s));
     const bool last_it = c->m.scf == BOP_SCF_NONE || it >= c->m.scf_max_it;
     if (!last_it) CKS(residual());
     // one synchronisation per iteration: Fermi solve converged?  SCF converged?
@@ -1409,6 +1414,7 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   CK(cudaMemcpyAsync(&et, c->e_total.p, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(nl, c->lcount.p, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CKS(check_status(c, s));
+  c->ef_solved = true;
   c->st.n_learned = (int)nl[0];
   c->st.n_unbounded = (int)nl[1];
   c->st.scf_iterations = it;
