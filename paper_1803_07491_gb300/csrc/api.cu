@@ -1333,8 +1333,11 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   // store Psi in each forward pass when it fits (the last pass is at the
   // final onsite levels)
   bool var_store = false;
-  const bool resp_store = (c->m.scf == BOP_SCF_LCN || c->m.scf == BOP_SCF_STONER) && c->m.scf_response &&
-                          c->forces_follow;
+  // (without an SCF the one forward pass stores Psi for the single reverse
+  // sweep of the forces, which then needs no recomputation)
+  const bool resp_store = c->forces_follow && (c->m.scf == BOP_SCF_NONE || ((c->m.scf == BOP_SCF_LCN ||
+                                                                            c->m.scf == BOP_SCF_STONER) &&
+                                                                           c->m.scf_response));
   if (variational || resp_store) CKS(psi_store_alloc(c, &var_store));
   c->forces_follow = false;
   auto residual = [&]() -> int {
