@@ -69,6 +69,8 @@ def _lib():
         L.orc_cluster.restype = ctypes.c_int
         L.orc_moments.restype = ctypes.c_int
         L.orc_moments_adjoint.restype = ctypes.c_int
+        L.orc_moments_nc.restype = ctypes.c_int
+        L.orc_moments_nc_adjoint.restype = ctypes.c_int
     return _LIB
 
 
@@ -129,6 +131,7 @@ class Settings:
     bandwidth: object = None      # Bandwidth (None: Gershgorin)
     J_ii: float = 0.0             # variational SCF: onsite charging J_ii of Eq. TB-Uion (eV / e^2)
     r_path: float = 0.0           # path-radius cut (A), 0 = none ("Performance", item (iii))
+    noncollinear: bool = False    # one moment direction per atom (section "Magnetism"), n_spin = 2
 
 
 @dataclass
@@ -256,6 +259,80 @@ def moments_adjoint(nbr: Neighbors, H, onsite, w, sel=None):
     if st != 0:
         raise ValueError("image index overflow in cluster")
     return Hbar, Ebar
+
+
+def moments_nc(nbr: Neighbors, H, onsite2, sdir, n_mom: int, sel=None) -> np.ndarray:
+    """Global 2x2 spin moments M_n[a][b] = <i alpha, a|H^n|i alpha, b> of
+    non-collinear magnetism (section "Magnetism", Eq. onsite_CM): hopping
+    H_e x 1, onsite matrix (E_up + E_dn)/2 + (E_dn - E_up)/2 s_i . sigma,
+    spin basis along z.  onsite2: [2, n, norb] (E_up, E_dn), sdir: [n, 3]
+    unit moment directions.  Returns [nsel, norb, n_mom, 2, 2] complex."""
+    assert n_mom % 2 == 1 and n_mom >= 3
+    onsite2 = np.ascontiguousarray(onsite2, dtype=np.float64)
+    _, n, norb = onsite2.shape
+    sdir = np.ascontiguousarray(sdir, dtype=np.float64)
+    sel = np.arange(n, dtype=np.int32) if sel is None else np.ascontiguousarray(sel, np.int32)
+    M = np.zeros((len(sel), norb, n_mom, 2, 2), np.complex128)
+    st = _lib().orc_moments_nc(len(sel), _p(sel), n, n_mom, norb, _p(nbr.row_ptr), _p(nbr.col), _p(nbr.img),
+                               *nbr._path_args(), _p(np.ascontiguousarray(H, dtype=np.float64)), _p(onsite2),
+                               _p(sdir), _p(M))
+    if st != 0:
+        raise ValueError("image index overflow in cluster")
+    return M
+
+
+def moments_nc_adjoint(nbr: Neighbors, H, onsite2, sdir, W, sel=None):
+    """Reverse sweep of ``moments_nc`` for L = sum_n Re Tr(W_n M_n), W
+    [nsel, norb, n_mom, 2, 2] Hermitian: returns (Hbar [E, norb, norb] =
+    dL/dH_e, Obar [n, norb, 4] = dL/d(Ebar, h_x, h_y, h_z) of every onsite
+    matrix Ebar + h . sigma)."""
+    onsite2 = np.ascontiguousarray(onsite2, dtype=np.float64)
+    _, n, norb = onsite2.shape
+    sel = np.arange(n, dtype=np.int32) if sel is None else np.ascontiguousarray(sel, np.int32)
+    W = np.ascontiguousarray(W, dtype=np.complex128)
+    n_mom = W.shape[2]
+    Hbar = np.zeros((nbr.n_edges, norb, norb))
+    Obar = np.zeros((n, norb, 4))
+    st = _lib().orc_moments_nc_adjoint(len(sel), _p(sel), n, n_mom, norb, _p(nbr.row_ptr), _p(nbr.col),
+                                       _p(nbr.img), *nbr._path_args(),
+                                       _p(np.ascontiguousarray(H, dtype=np.float64)), _p(onsite2),
+                                       _p(np.ascontiguousarray(sdir, dtype=np.float64)), _p(W), _p(Hbar), _p(Obar))
+    if st != 0:
+        raise ValueError("image index overflow in cluster")
+    return Hbar, Obar
+
+
+def pauli_vector(M) -> np.ndarray:
+    """Tr(sigma M) of 2x2 matrices [..., 2, 2] -> [..., 3] (real part)."""
+    vx = M[..., 0, 1] + M[..., 1, 0]
+    vy = 1j * (M[..., 0, 1] - M[..., 1, 0])
+    vz = M[..., 0, 0] - M[..., 1, 1]
+    return np.real(np.stack([vx, vy, vz], axis=-1))
+
+
+def local_moments(M, sdir) -> np.ndarray:
+    """Moments of the local up / down channels (Eq. onsite-noncollinear),
+    mu_nu = Tr(P_nu M) with the projectors P_up = (1 - s.sigma)/2 (spin
+    antiparallel to the moment direction s, the lower level) and
+    P_dn = (1 + s.sigma)/2.  M [n, norb, n_mom, 2, 2] -> [2, n, norb, n_mom]."""
+    tr = np.real(M[..., 0, 0] + M[..., 1, 1])
+    sv = np.einsum("iamx,ix->iam", pauli_vector(M), sdir)
+    return np.stack([0.5 * (tr - sv), 0.5 * (tr + sv)])
+
+
+def global_weights(w, sdir) -> np.ndarray:
+    """Weights in the global spin frame from the local ones (section
+    "Torques"): W = (w_up + w_dn)/2 1 + (w_dn - w_up)/2 s.sigma.
+    w [2, n, norb, n_mom] -> [n, norb, n_mom, 2, 2] complex."""
+    a = 0.5 * (w[0] + w[1])
+    c = 0.5 * (w[1] - w[0])
+    sx, sy, sz = (sdir[:, x][:, None, None] for x in range(3))
+    W = np.zeros(a.shape + (2, 2), np.complex128)
+    W[..., 0, 0] = a + c * sz
+    W[..., 1, 1] = a - c * sz
+    W[..., 0, 1] = c * (sx - 1j * sy)
+    W[..., 1, 0] = c * (sx + 1j * sy)
+    return W
 
 
 def bond_gradient(model: Model, pos, cell, nbr: Neighbors, Hbar) -> np.ndarray:
@@ -684,7 +761,7 @@ def variational_gradient(st: Settings, nbr: Neighbors, H, onsite, mu_f, E_F, sta
 # ---------------------------------------------------------------- driver
 
 def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = True,
-             delta0=None, m_init=None):
+             delta0=None, m_init=None, spin_dir=None):
     """Energy (and forces, virial) of the analytic BOP for one structure.
 
     Flow of Fig. BOP-calculation: neighbours -> H -> [moments -> recursion ->
@@ -693,7 +770,15 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
     with E_F following the electron count.  With an SCF the forces are the
     total derivative of the self-consistent energy (``scf_response``, the
     default; see ``scf_response_weights``), otherwise the derivative at fixed
-    onsite levels (the Hellmann-Feynman form of Eq. F_k)."""
+    onsite levels (the Hellmann-Feynman form of Eq. F_k).
+
+    Non-collinear magnetism (``st.noncollinear``, section "Magnetism"):
+    spin_dir [n, 3] fixes the direction of every atom's moment; the
+    moments are the 2x2 spin moments of ``moments_nc`` projected on the
+    local up / down channels, which then take the place of the two
+    collinear spin channels (Stoner SCF of the magnitudes m_i, or fixed
+    magnitudes m_init without an SCF).  The torques of Eq. torque,
+    t_i = dU/ds_i x s_i, are returned with the forces."""
     pos = np.asarray(pos, np.float64)
     n = len(pos)
     norb = model.norb
@@ -703,7 +788,14 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
     H = blocks(model, pos, cell, nbr)
     delta = np.zeros(n) if delta0 is None else np.array(delta0, np.float64)
     m = None
-    if st.scf == "stoner":
+    nc = st.noncollinear
+    if nc:
+        assert S == 2 and st.scf in ("none", "stoner") and not (st.scf == "stoner" and st.scf_response)
+        assert st.terminator == "constant"
+        sdir = np.array(spin_dir, np.float64)
+        sdir = sdir / np.linalg.norm(sdir, axis=1)[:, None]
+    magnetic = st.scf == "stoner" or nc
+    if magnetic:
         m = np.full(n, st.m0) if m_init is None else np.array(m_init, np.float64)
     N0 = st.n_e
     target = st.n_e * n
@@ -722,10 +814,14 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
             onsite[v] = model.onsite0 + delta[:, None]
             if norb == 6:
                 onsite[v][:, 0] = model.onsite_s + delta
-            if st.scf == "stoner":
+            if magnetic:
                 sign = -1.0 if v == 0 else 1.0
                 onsite[v] += sign * 0.5 * st.stoner_I * m[:, None]
-        mu = np.stack([moments(nbr, H, onsite[v], st.n_mom) for v in range(S)])
+        if nc:
+            Mnc = moments_nc(nbr, H, onsite, sdir, st.n_mom)
+            mu = local_moments(Mnc, sdir)
+        else:
+            mu = np.stack([moments(nbr, H, onsite[v], st.n_mom) for v in range(S)])
         mu_f = mu.reshape(-1, st.n_mom)
         ex = stage(mu_f)
         E_F, n_bis = fermi_bisect(ex, s, target)
@@ -777,7 +873,7 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
             m = x_new[n:]
         it += 1
     e_atom = s * U.reshape(S, n, norb).sum(axis=(0, 2))
-    if st.scf == "stoner":
+    if magnetic:
         e_atom = e_atom - 0.25 * st.stoner_I * m ** 2
     if st.scf == "variational":
         q = s * Nsv.sum(axis=(0, 2)) - N0
@@ -792,7 +888,7 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
                a=ex.a, b=ex.b, a_inf=ex.a_inf, b_inf=ex.b_inf, N=Nsv, delta=delta, m=m,
                scf_iterations=it, scf_converged=converged, bisection_steps=n_bis,
                neighbors=nbr, H=H, onsite=onsite, forces_include_scf_response=st.scf == "none",
-               learned=getattr(ex, "learned", None),
+               learned=getattr(ex, "learned", None), M_nc=Mnc if nc else None,
                unbounded=outside_band(ex.sigma))
     if want_forces:
         w, dU_dE, dN, _, _, dU = weights(mu_f, onsite.reshape(-1), E_F, st.n_exp, s, stage)
@@ -807,9 +903,19 @@ def evaluate(model: Model, st: Settings, pos, cell, pbc, want_forces: bool = Tru
             out.update(scf_multipliers=lam_scf)
         out["forces_include_scf_response"] = st.scf in ("none", "variational") or resp
         Hbar = np.zeros((nbr.n_edges, norb, norb))
-        for v in range(S):
-            hb, _ = moments_adjoint(nbr, H, onsite[v], w[v])
-            Hbar += hb
+        if nc:
+            # weights in the global frame; torques (section "Torques"):
+            # dU/ds = 1/2 Tr(Theta~ sigma) Delta + 1/2 sum_n (w_dn - w_up) Tr(sigma M_n)
+            # per orbital, Delta = E_dn - E_up; the term -I m m_i of the same
+            # equation is parallel to s_i and drops out of t = dU/ds x s
+            Hbar, Obar = moments_nc_adjoint(nbr, H, onsite, sdir, global_weights(w, sdir))
+            dUds = 0.5 * np.einsum("ia,iax->ix", onsite[1] - onsite[0], Obar[:, :, 1:])
+            dUds += 0.5 * np.einsum("iam,iamx->ix", w[1] - w[0], pauli_vector(Mnc))
+            out.update(torques=np.cross(dUds, sdir), dU_ds=dUds, Obar=Obar)
+        else:
+            for v in range(S):
+                hb, _ = moments_adjoint(nbr, H, onsite[v], w[v])
+                Hbar += hb
         g = bond_gradient(model, pos, cell, nbr, Hbar)
         if model.rep_A != 0.0:
             dvec = edge_vectors(pos, cell, nbr)

@@ -622,3 +622,207 @@ void orc_edge_vectors(int n, const double *pos, const double *cell, const long *
     for (long e = row_ptr[i]; e < row_ptr[i + 1]; e++)
       edge_vector(pos, cell, i, col[e], img + 3 * e, dvec + 3 * e);
 }
+
+/* ------------------------------------------------------------------ */
+/* Non-collinear magnetism: spinor moments and their reverse sweep      */
+/* ------------------------------------------------------------------ */
+
+/* Section "Magnetism", Eq. onsite_CM and Eq. onsite-noncollinear: the
+ * hopping is spin independent (H_e x 1), the onsite matrix of orbital b of
+ * atom a is
+ *     O_ab = Ebar 1 + h . sigma,   Ebar = (E_up + E_dn)/2,
+ *                                  h = (E_dn - E_up)/2 s_a,
+ * s_a the unit direction of the atom's moment; in the frame along s_a it is
+ * diag(E_up, E_dn), the lower level E_up belonging to the spin antiparallel
+ * to s_a.  onsite2: [2][n][norb] (E_up, E_dn), sdir: [n][3].  Amplitudes
+ * are [site][orbital][spin] complex, spin the basis along z. */
+static void onsite_field(const double *onsite2, const double *sdir, int n, int norb, int a, int b,
+                         double *eb, double h[3]) {
+  double eu = onsite2[(long)a * norb + b], ed = onsite2[((long)n + a) * norb + b];
+  *eb = 0.5 * (eu + ed);
+  for (int x = 0; x < 3; x++) h[x] = 0.5 * (ed - eu) * sdir[3 * a + x];
+}
+
+/* out += H in for one starting column, rows t < rows, columns s < cols */
+static void apply_H_nc(const cluster *c, int rows, int cols, int norb, int n, const long *row_ptr,
+                       const int *col, const signed char *img, const double *H,
+                       const double *onsite2, const double *sdir, const cplx *in, cplx *out) {
+  int nb = norb * norb;
+  for (int t = 0; t < rows; t++) {
+    int a = c->atom[t];
+    if (t < cols)
+      for (int b = 0; b < norb; b++) {
+        double eb, h[3];
+        onsite_field(onsite2, sdir, n, norb, a, b, &eb, h);
+        cplx u = in[(t * norb + b) * 2], d = in[(t * norb + b) * 2 + 1];
+        /* (Ebar + h.sigma)(u, d), sigma_x = [[0,1],[1,0]],
+         * sigma_y = [[0,-i],[i,0]], sigma_z = diag(1,-1) */
+        out[(t * norb + b) * 2] += (eb + h[2]) * u + (h[0] - I * h[1]) * d;
+        out[(t * norb + b) * 2 + 1] += (h[0] + I * h[1]) * u + (eb - h[2]) * d;
+      }
+    for (long e = row_ptr[a]; e < row_ptr[a + 1]; e++) {
+      int s = neighbour_site(c, t, e, col, img);
+      if (s < 0 || s >= cols) continue;
+      const double *B = H + e * nb;
+      for (int b = 0; b < norb; b++)
+        for (int g = 0; g < norb; g++)
+          for (int sp = 0; sp < 2; sp++)
+            out[(t * norb + b) * 2 + sp] += B[b * norb + g] * in[(s * norb + g) * 2 + sp];
+    }
+  }
+}
+
+/* <x|y> = sum conj(x) y */
+static cplx cdot(const cplx *x, const cplx *y, long len) {
+  cplx acc = 0.0;
+  for (long q = 0; q < len; q++) acc += conj(x[q]) * y[q];
+  return acc;
+}
+
+/* Psi_0..Psi_K of both starting columns |i alpha, z-up>, |i alpha, z-down>
+ * into psi[col][k][len] (len = nsite * norb * 2). */
+static void spinor_levels(const cluster *c, int K, int al, int norb, int n, const long *row_ptr,
+                          const int *col, const signed char *img, const double *H,
+                          const double *onsite2, const double *sdir, cplx *psi, long len) {
+  memset(psi, 0, sizeof(cplx) * 2 * (K + 1) * len);
+  for (int a = 0; a < 2; a++) {
+    cplx *p = psi + (long)a * (K + 1) * len;
+    p[al * 2 + a] = 1.0;
+    for (int k = 1; k <= K; k++)
+      apply_H_nc(c, c->level_end[k], c->level_end[k - 1], norb, n, row_ptr, col, img, H, onsite2, sdir,
+                 p + (k - 1) * len, p + k * len);
+  }
+}
+
+/* Global 2x2 moments M_n[a][b] = <i alpha, a|H^n|i alpha, b>, n < n_mom,
+ * by the merge property (Eq. xi_merge) for both starting spin states:
+ * M_2k = <Psi_k^a|Psi_k^b>, M_2k-1 = <Psi_k-1^a|Psi_k^b>.
+ * M: [nsel][norb][n_mom][2][2] complex.  Returns 0, or -1 on an image
+ * overflow. */
+int orc_moments_nc(int nsel, const int *sel, int n, int n_mom, int norb, const long *row_ptr,
+                   const int *col, const signed char *img, const double *pos, const double *cell,
+                   double rpath, const double *H, const double *onsite2, const double *sdir, cplx *M) {
+  int K = (n_mom - 1) / 2, status = 0;
+  pathcut pc = {pos, cell, rpath > 0.0 ? rpath * rpath : 0.0};
+  for (int q = 0; q < nsel; q++) {
+    cluster c;
+    if (build_cluster(&c, sel[q], K, row_ptr, col, img, pc) < 0) status = -1;
+    long len = (long)c.nsite * norb * 2;
+    cplx *psi = (cplx *)calloc(2 * (K + 1) * len, sizeof(cplx));
+    for (int al = 0; al < norb; al++) {
+      spinor_levels(&c, K, al, norb, n, row_ptr, col, img, H, onsite2, sdir, psi, len);
+      cplx *m = M + ((long)q * norb + al) * n_mom * 4;
+      for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++) {
+          const cplx *pa = psi + (long)a * (K + 1) * len, *pb = psi + (long)b * (K + 1) * len;
+          m[a * 2 + b] = a == b ? 1.0 : 0.0;
+          for (int k = 1; k <= K; k++) {
+            m[(2 * k - 1) * 4 + a * 2 + b] =
+                cdot(pa + (k - 1) * len, pb + k * len, (long)c.level_end[k - 1] * norb * 2);
+            m[(2 * k) * 4 + a * 2 + b] = cdot(pa + k * len, pb + k * len, (long)c.level_end[k] * norb * 2);
+          }
+        }
+    }
+    free(psi);
+    free_cluster(&c);
+  }
+  return status;
+}
+
+/* Reverse sweep of orc_moments_nc for L = sum_n Re Tr(W_n M_n) with
+ * Hermitian 2x2 weights W: [nsel][norb][n_mom][2][2] complex (Eq.
+ * dUdLambda-noncollinear).  A term Re sum_ab W_ba <p^a|q^b> gives the
+ * cotangents (d/dRe + i d/dIm) p-bar^c += sum_b W_bc q^b and
+ * q-bar^c += sum_a W_ac p^a.  Accumulates (+=)
+ *   Hbar[e][b][g] = dL/dH_e[b][g] for every directed edge,
+ *   Obar[a][b][0..3] = dL/d(Ebar, h_x, h_y, h_z) of orbital b of atom a. */
+int orc_moments_nc_adjoint(int nsel, const int *sel, int n, int n_mom, int norb, const long *row_ptr,
+                           const int *col, const signed char *img, const double *pos,
+                           const double *cell, double rpath, const double *H, const double *onsite2,
+                           const double *sdir, const cplx *W, double *Hbar, double *Obar) {
+  int K = (n_mom - 1) / 2, nb = norb * norb, status = 0;
+  pathcut pc = {pos, cell, rpath > 0.0 ? rpath * rpath : 0.0};
+  for (int q = 0; q < nsel; q++) {
+    cluster c;
+    if (build_cluster(&c, sel[q], K, row_ptr, col, img, pc) < 0) status = -1;
+    long len = (long)c.nsite * norb * 2;
+    cplx *psi = (cplx *)calloc(2 * (K + 1) * len, sizeof(cplx));
+    cplx *bar = (cplx *)calloc(2 * len, sizeof(cplx));
+    cplx *nbar = (cplx *)calloc(2 * len, sizeof(cplx));
+    for (int al = 0; al < norb; al++) {
+      const cplx *w = W + ((long)q * norb + al) * n_mom * 4; /* w[m*4 + a*2 + b] */
+      spinor_levels(&c, K, al, norb, n, row_ptr, col, img, H, onsite2, sdir, psi, len);
+#define PSI(a, k) (psi + ((long)(a) * (K + 1) + (k)) * len)
+      /* Psi-bar_K: 2 W_2K (self product) and W_2K-1 (q = Psi_K) */
+      for (int cc = 0; cc < 2; cc++)
+        for (long x = 0; x < len; x++) {
+          cplx v = 0.0;
+          for (int b = 0; b < 2; b++) {
+            v += 2.0 * w[(2 * K) * 4 + b * 2 + cc] * PSI(b, K)[x];
+            v += w[(2 * K - 1) * 4 + b * 2 + cc] * PSI(b, K - 1)[x];
+          }
+          bar[cc * len + x] = v;
+        }
+      for (int k = K; k >= 1; k--) {
+        int rows = c.level_end[k], cols = c.level_end[k - 1];
+        memset(nbar, 0, sizeof(cplx) * 2 * len);
+        for (int cc = 0; cc < 2; cc++) {
+          const cplx *pin = PSI(cc, k - 1), *bk = bar + cc * len;
+          cplx *nb_ = nbar + cc * len;
+          for (int t = 0; t < rows; t++) {
+            int a = c.atom[t];
+            if (t < cols)
+              for (int b = 0; b < norb; b++) {
+                double eb, h[3];
+                onsite_field(onsite2, sdir, n, norb, a, b, &eb, h);
+                cplx bu = bk[(t * norb + b) * 2], bd = bk[(t * norb + b) * 2 + 1];
+                cplx pu = pin[(t * norb + b) * 2], pd = pin[(t * norb + b) * 2 + 1];
+                double *ob = Obar + ((long)a * norb + b) * 4;
+                ob[0] += creal(conj(bu) * pu + conj(bd) * pd);
+                ob[1] += creal(conj(bu) * pd + conj(bd) * pu);
+                ob[2] += creal(conj(bu) * (-I * pd) + conj(bd) * (I * pu));
+                ob[3] += creal(conj(bu) * pu - conj(bd) * pd);
+                /* O is Hermitian: the cotangent goes back through O itself */
+                nb_[(t * norb + b) * 2] += (eb + h[2]) * bu + (h[0] - I * h[1]) * bd;
+                nb_[(t * norb + b) * 2 + 1] += (h[0] + I * h[1]) * bu + (eb - h[2]) * bd;
+              }
+            for (long e = row_ptr[a]; e < row_ptr[a + 1]; e++) {
+              int s = neighbour_site(&c, t, e, col, img);
+              if (s < 0 || s >= cols) continue;
+              const double *B = H + e * nb;
+              double *Bb = Hbar + e * nb;
+              for (int b = 0; b < norb; b++)
+                for (int g = 0; g < norb; g++)
+                  for (int sp = 0; sp < 2; sp++) {
+                    Bb[b * norb + g] += creal(conj(bk[(t * norb + b) * 2 + sp]) * pin[(s * norb + g) * 2 + sp]);
+                    nb_[(s * norb + g) * 2 + sp] += B[b * norb + g] * bk[(t * norb + b) * 2 + sp];
+                  }
+            }
+          }
+        }
+        if (k == 1) break;
+        /* dot-product cotangents of Psi_k-1: M_2(k-1) (self), M_2k-1 (as
+         * p, partner Psi_k), M_2k-3 (as q, partner Psi_k-2) */
+        for (int cc = 0; cc < 2; cc++)
+          for (long x = 0; x < len; x++) {
+            cplx v = 0.0;
+            if (x < (long)cols * norb * 2) {
+              v = nbar[cc * len + x];
+              for (int b = 0; b < 2; b++) {
+                v += 2.0 * w[(2 * k - 2) * 4 + b * 2 + cc] * PSI(b, k - 1)[x];
+                v += w[(2 * k - 1) * 4 + b * 2 + cc] * PSI(b, k)[x];
+                v += w[(2 * k - 3) * 4 + b * 2 + cc] * PSI(b, k - 2)[x];
+              }
+            }
+            bar[cc * len + x] = v;
+          }
+#undef PSI
+      }
+    }
+    free(psi);
+    free(bar);
+    free(nbar);
+    free_cluster(&c);
+  }
+  return status;
+}

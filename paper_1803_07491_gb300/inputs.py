@@ -114,6 +114,7 @@ class RunParams:
     bw_b: float = 1.0             # global: B (eV)
     J_ii: float = 0.0             # variational SCF: onsite charging energy J_ii q_i^2 / 2 (eV / e^2)
     r_path: float = 0.0           # path-radius cut (A): only sites closer than r_path to the atom; 0 = none
+    noncollinear: bool = False    # one moment direction per atom (n_spin = 2, scf none | stoner)
 
 
 @dataclass
@@ -185,6 +186,20 @@ def maxwell_velocities(n: int, T: float, mass: float, seed: int) -> np.ndarray:
     return v - v.mean(axis=0)
 
 
+def random_directions(n: int, seed: int) -> np.ndarray:
+    """n unit vectors uniform on the sphere: default_rng(seed).normal
+    (n, 3), each row divided by its norm."""
+    v = np.random.default_rng(seed).normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1)[:, None]
+
+
+def spiral_directions(pos: np.ndarray, period: float, cone: float) -> np.ndarray:
+    """A conical spin spiral along x: s_i = (sin c cos q x_i, sin c sin q x_i,
+    cos c), q = 2 pi / period (A), c = cone (radians)."""
+    ph = 2.0 * np.pi * pos[:, 0] / period
+    return np.stack([np.sin(cone) * np.cos(ph), np.sin(cone) * np.sin(ph), np.full(len(pos), np.cos(cone))], axis=1)
+
+
 def workload(name: str) -> Workload:
     """Named workloads.
 
@@ -215,6 +230,11 @@ def workload(name: str) -> Workload:
               MODEL_D_REP, as the start of an NVE run: Maxwell-Boltzmann
               velocities at 300 K (seed 7, no net momentum), iron's mass,
               time step 1 fs (meta: vel, mass, dt).
+    nc2000    the mag2000 cell with non-collinear moments: a conical spin
+              spiral along x (one period over the cell, cone angle 60
+              degrees; meta: spin_dir), Stoner SCF of the magnitudes at fixed
+              directions (forces and torques at the self-consistent onsite
+              levels).
     learned131k 131,072-atom bcc (32x32x64x2), jitter 0.05 A, seed 5;
               canonical d; 9 moments; no SCF (evaluation cell of the
               learned terminator).
@@ -240,6 +260,11 @@ def workload(name: str) -> Workload:
         pos, cell = bcc_jittered(n, n, n, 0.05, 4)
         return Workload(name, pos, cell, (1, 1, 1), MODEL_D,
                         RunParams(n_e=6.8, n_spin=2, scf="stoner", stoner_I=0.8, m_mix=1.0, **ANDERSON_STEP))
+    if name == "nc2000":
+        w = workload("mag2000")
+        run = replace(w.run, noncollinear=True, scf_response=False)
+        sd = spiral_directions(w.pos, w.cell[0, 0], np.pi / 3)
+        return Workload(name, w.pos, w.cell, w.pbc, w.model, run, dict(spin_dir=sd))
     if name == "fcc2048":
         pos, cell = fcc_jittered(8, 8, 8, 0.05, 6)
         return Workload(name, pos, cell, (1, 1, 1), MODEL_D, RunParams(n_e=6.8, scf="lcn", **ANDERSON_STEP))

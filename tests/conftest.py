@@ -34,4 +34,4 @@ def oracle_settings(r):
                         mixer=r.mixer, mix_history=r.mix_history, scf_response=r.scf_response,
                         bandwidth=None if r.bandwidth == "gershgorin" else
                         bop.Bandwidth(r.bandwidth, r.bw_beta, r.bw_a, r.bw_b), J_ii=r.J_ii,
-                        r_path=r.r_path)
+                        r_path=r.r_path, noncollinear=r.noncollinear)
