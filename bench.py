@@ -100,10 +100,14 @@ def algorithmic_flops(family: str, w, stats: dict, prof: dict, n_spin: int, step
     """FLOPs one launch region of a family must do (per region)."""
     norb, n_mom, n_exp = w.model.norb, w.run.n_mom, w.run.n_exp
     M = n_spin * w.n_atoms * norb
+    # columns per atom and cluster pair: every starting orbital of each spin
+    # channel, or for non-collinear moments the four reals of both starting
+    # spinors of every starting orbital
+    cols = 8 * norb if w.run.noncollinear else n_spin * norb
     if family == "moments":
         # block products Psi_k(t) += B_ts Psi_k-1(s) over the cluster pairs,
-        # norb x norb x norb multiply-adds each (all starting orbitals)
-        return 2.0 * stats["moment_products"] * n_spin * norb ** 3
+        # norb x norb multiply-adds per column
+        return 2.0 * stats["moment_products"] * norb ** 2 * cols
     if family == "adjoint":
         # a reverse sweep runs H^T over Psi-bar (one moments pass) and, when
         # bond cotangents are wanted, forms sum_k Psi-bar_k(t) Psi_k-1(s)^T
@@ -111,7 +115,7 @@ def algorithmic_flops(family: str, w, stats: dict, prof: dict, n_spin: int, step
         # pass (recomputing it, where it does not fit, is not counted).  One
         # sweep per step forms bond cotangents, the others (SCF-response
         # products, variational residuals) only onsite ones
-        one = 2.0 * stats["moment_products"] * n_spin * norb ** 3
+        one = 2.0 * stats["moment_products"] * norb ** 2 * cols
         regions = max(1, prof["adjoint"]["regions"])
         with_h = min(steps, regions)
         return one * (2.0 * with_h + 1.0 * (regions - with_h)) / regions
@@ -280,6 +284,8 @@ def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: s
                               else "fixed onsite levels (Hellmann-Feynman form)"),
                    **({"J_ii": w.run.J_ii} if w.run.scf == "variational" else {}),
                    **({"r_path": w.run.r_path} if w.run.r_path > 0 else {}),
+                   **({"noncollinear": "conical spin spiral, torques with the forces"}
+                      if w.run.noncollinear else {}),
                    "response_iterations": stats["response_iterations"],
                    "precision": precision, "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}"},
@@ -312,6 +318,9 @@ def run_ours(args):
             # FP32 moments put a floor of a few 1e-6 electrons under N_i
             w = I.with_run(w, scf_tol=FP32_VAR_TOL if w.run.scf == "variational" else FP32_SCF_TOL)
         ctx = bop.Context(w.model, w.run, args.precision)
+        if "spin_dir" in w.meta:  # non-collinear: directions kept across builds of the same cell
+            ctx.build(w.pos, w.cell, w.pbc)
+            ctx.set_spin_directions(w.meta["spin_dir"])
         line = measure(bop, ctx, w, args, world, args.steps, args.warmup, args.precision)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)

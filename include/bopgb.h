@@ -133,7 +133,23 @@ enum {
  * bandwidth: one of BOP_BW_*; B is floored at 1e-3 eV in every mode (no
  * derivative flows through a floored B).  bw_beta >= 0 (WEIGHTED), bw_a and
  * bw_b > 0 (GLOBAL, eV); ignored otherwise.  The MLP terminator takes
- * BOP_BW_GERSHGORIN only. */
+ * BOP_BW_GERSHGORIN only.
+ * noncollinear = 1: non-collinear magnetism (section "Magnetism", Eqs.
+ * onsite_CM and onsite-noncollinear) with one fixed moment direction s_i
+ * per atom (bop_set_spin_directions).  The onsite matrix of orbital alpha
+ * of atom i in the spin basis along z is
+ *   (E_up + E_dn)/2 1 + (E_dn - E_up)/2 s_i . sigma,
+ *   E_up/dn = E0 + delta_i -/+ stoner_I m_i / 2,
+ * so that in the frame of s_i it is diag(E_up, E_dn), the lower level E_up
+ * belonging to the spin antiparallel to s_i; the hopping is spin
+ * independent.  The moments of the two local channels (starting states the
+ * local spin states of the orbital) take the place of the collinear spin
+ * channels; with every s_i equal the results are the collinear ones.
+ * Needs n_spin = 2, scf STONER (magnitudes m_i self-consistent at fixed
+ * directions, scf_response = 0: forces and torques at the self-consistent
+ * onsite levels) or NONE (magnitudes fixed by m_io of bop_energy, m0 when
+ * NULL), the constant terminator.  The energy per atom includes
+ * -stoner_I m_i^2 / 4 in both cases. */
 typedef struct {
   int norb;
   double b0[5];
@@ -159,6 +175,7 @@ typedef struct {
   double rep_A, rep_p;  /* pair repulsion (described above): rep_A = 0 for none */
   double r_path;        /* path-radius cut in A (described above): 0 for none */
   double onsite_s;      /* sd model: reference level of the s orbital (eV) */
+  int noncollinear;     /* 1: non-collinear magnetism (described above), 0: collinear */
 } bop_model;
 
 typedef struct {
@@ -283,6 +300,31 @@ int bop_energy(bop_ctx* ctx, double* e_atom, double* delta_io, double* m_io, bop
  *   forces device [n][3], virial device [3][3] (row-major), either may be NULL.
  * Errors: BOP_ERR_STATE without a preceding bop_energy. */
 int bop_forces(bop_ctx* ctx, double* forces, double* virial, bop_stats* stats_host, bop_stream stream);
+
+/* Moment directions of a noncollinear model (section "Magnetism"):
+ * s device [n][3], one direction per atom of the structure built last,
+ * normalised by the library (copied through the host once).  Needed before
+ * bop_energy; kept until the next call or the next structure of another
+ * size.  Errors: BOP_ERR_ARG for a collinear model or a vector of norm
+ * below 1e-12 or not finite, BOP_ERR_STATE without a built structure. */
+int bop_set_spin_directions(bop_ctx* ctx, const double* s, bop_stream stream);
+
+/* Magnetic torques of Eq. torque after bop_forces of a noncollinear model:
+ * t_i = dU/ds_i x s_i, dU/ds_i the derivative of the energy of the last
+ * bop_energy call with respect to the direction s_i at fixed magnitudes
+ * m_i and shifts delta_i (E_F following the electron count):
+ *   dU/ds_i = sum_alpha [ (E_dn - E_up)/2 Tr(Theta~_ii sigma)
+ *                         + sum_n (w_dn,n - w_up,n)/2 Tr(sigma M_n) ],
+ * Theta~_ii the 2x2 derivative of the energy with respect to the onsite
+ * matrix (reverse sweep of the spin moments), w the weights of the local
+ * channels and M_n the 2x2 spin moments of the orbital; the term of the
+ * paper's expression along m_i is parallel to s_i and drops out of the
+ * cross product.  Rotating s_i by a small angle e about a unit axis a
+ * changes the energy by -e t_i . a.
+ *   t device [n][3].
+ * Errors: BOP_ERR_ARG for a collinear model, BOP_ERR_STATE without a
+ * preceding bop_forces. */
+int bop_torques(bop_ctx* ctx, double* t, bop_stream stream);
 
 /* Memory for the reverse sweeps of bop_forces.  When several reverse sweeps
  * follow (an SCF with scf_response = 1) and all starting orbitals of an atom

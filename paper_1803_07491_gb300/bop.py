@@ -43,7 +43,8 @@ class bop_model(ctypes.Structure):
                 ("mix_history", ctypes.c_int), ("terminator", ctypes.c_int), ("scf_response", ctypes.c_int),
                 ("bandwidth", ctypes.c_int), ("bw_beta", ctypes.c_double), ("bw_a", ctypes.c_double),
                 ("bw_b", ctypes.c_double), ("j_ii", ctypes.c_double), ("rep_A", ctypes.c_double),
-                ("rep_p", ctypes.c_double), ("r_path", ctypes.c_double), ("onsite_s", ctypes.c_double)]
+                ("rep_p", ctypes.c_double), ("r_path", ctypes.c_double), ("onsite_s", ctypes.c_double),
+                ("noncollinear", ctypes.c_int)]
 
 
 class bop_stats(ctypes.Structure):
@@ -116,6 +117,8 @@ def lib(path: str | None = None):
         "bop_mlp_predict": ([_VP, ctypes.c_longlong, _VP, _VP, _VP], ctypes.c_int),
         "bop_set_mlp": ([_VP, _VP], ctypes.c_int),
         "bop_set_store_budget": ([_VP, ctypes.c_longlong], ctypes.c_int),
+        "bop_set_spin_directions": ([_VP, _VP, _VP], ctypes.c_int),
+        "bop_torques": ([_VP, _VP, _VP], ctypes.c_int),
         "bop_md_verlet": ([ctypes.c_int, _VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                            _VP], ctypes.c_int),
         "bop_reset_profile": ([_VP], ctypes.c_int),
@@ -155,7 +158,8 @@ def make_model(params, run, precision: str = "fp64") -> bop_model:
                      run.scf_tol, run.scf_max_it, run.stoner_I, run.m_mix, run.m0, run.dos_floor,
                      PREC[precision], MIXER[run.mixer], run.mix_history, TERM[run.terminator],
                      1 if run.scf_response else 0, BANDWIDTH[run.bandwidth], run.bw_beta, run.bw_a, run.bw_b,
-                     run.J_ii, params.rep_A, params.rep_p, run.r_path, params.onsite_s)
+                     run.J_ii, params.rep_A, params.rep_p, run.r_path, params.onsite_s,
+                     1 if run.noncollinear else 0)
 
 
 def _check(ctx, st, allow=()):
@@ -261,6 +265,18 @@ def bop_forces(ctx, n: int, stream=None):
     s = bop_stats()
     _check(ctx, lib().bop_forces(ctx, _ptr(F), _ptr(W), ctypes.byref(s), _stream(stream)))
     return F, W
+
+
+def bop_set_spin_directions(ctx, sdir, stream=None):
+    """Moment directions [n][3] of a non-collinear model (device float64)."""
+    sdir = torch.as_tensor(sdir, dtype=torch.float64, device="cuda").contiguous()
+    _check(ctx, lib().bop_set_spin_directions(ctx, _ptr(sdir), _stream(stream)))
+
+
+def bop_torques(ctx, n: int, stream=None):
+    t = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    _check(ctx, lib().bop_torques(ctx, _ptr(t), _stream(stream)))
+    return t
 
 
 def bop_forces_stats(ctx, n: int, stream=None):
@@ -478,6 +494,7 @@ class Result:
     forces: torch.Tensor | None
     virial: torch.Tensor | None
     stats: dict
+    torques: torch.Tensor | None = None
 
 
 class Context:
@@ -529,13 +546,29 @@ class Context:
         bop_md_verlet(None, vel, forces, dt, mass, 1, stream=stream)
         return e, st
 
-    def evaluate(self, pos, cell, pbc, forces=True) -> Result:
+    def set_spin_directions(self, sdir, stream=None):
+        bop_set_spin_directions(self.h, sdir, stream)
+
+    def torques(self, stream=None):
+        return bop_torques(self.h, self.n, stream)
+
+    def evaluate(self, pos, cell, pbc, forces=True, spin_dir=None, m=None) -> Result:
+        """Energy (and forces, virial; torques of a non-collinear model,
+        whose moment directions spin_dir [n][3] are set after the build;
+        m: moment magnitudes, the start of a Stoner SCF or fixed without
+        one)."""
         self.build(pos, cell, pbc)
-        e, st = self.energy()
-        F = W = None
+        if spin_dir is not None:
+            self.set_spin_directions(spin_dir)
+        if m is not None:
+            m = torch.as_tensor(m, dtype=torch.float64, device="cuda").clone()
+        e, st = self.energy(m=m)
+        F = W = T = None
         if forces:
             F, W = self.forces()
-        return Result(e, st["e_total"], st["e_fermi"], F, W, st)
+            if self.run.noncollinear:
+                T = self.torques()
+        return Result(e, st["e_total"], st["e_fermi"], F, W, st, T)
 
 
 class BopEnergy(torch.autograd.Function):

@@ -85,6 +85,11 @@ struct bop_ctx {
   bool forces_follow = false;
   bool ef_solved = false;  // fstate holds a Fermi level of an earlier solve
   DBuf erep;  // pair repulsion per atom
+  // non-collinear magnetism: unit moment directions [n][3] (sdir_n atoms),
+  // Tr(sigma M_n) [n][norb][n_mom][3], onsite cotangents [n][norb][4],
+  // torques [n][3], per-CTA spinor scratch
+  DBuf sdir, vmom, obar, torque, ncscr;
+  int sdir_n = -1;
   // stored Psi of every work item for the reverse sweeps (when it fits)
   DBuf psi_off, psis, psib, lsum;
   long long psi_tot = 0;
@@ -241,6 +246,15 @@ int validate_model(bop_ctx* c, const bop_model* m) {
     return fail(c, BOP_ERR_ARG, "rep_A and rep_p must be finite and >= 0");
   if (m->terminator == BOP_TERM_MLP && m->bandwidth != BOP_BW_GERSHGORIN)
     return fail(c, BOP_ERR_ARG, "the MLP terminator takes the Gershgorin band width only");
+  if (m->noncollinear != 0 && m->noncollinear != 1) return fail(c, BOP_ERR_ARG, "noncollinear must be 0 or 1");
+  if (m->noncollinear) {
+    if (m->n_spin != 2) return fail(c, BOP_ERR_ARG, "noncollinear needs n_spin = 2");
+    if (m->scf != BOP_SCF_NONE && m->scf != BOP_SCF_STONER)
+      return fail(c, BOP_ERR_ARG, "noncollinear needs scf STONER or NONE");
+    if (m->scf == BOP_SCF_STONER && m->scf_response)
+      return fail(c, BOP_ERR_ARG, "noncollinear STONER needs scf_response = 0");
+    if (m->terminator != BOP_TERM_CONSTANT) return fail(c, BOP_ERR_ARG, "noncollinear needs the constant terminator");
+  }
   return BOP_OK;
 }
 
@@ -418,7 +432,41 @@ int forward_nc(bop_ctx* c) {
   return moments_columns(c->norb, ce + co, c->fp64);
 }
 
+// Arguments of the spinor kernel (non-collinear magnetism): per-CTA scratch
+// for Psi and Psi-bar of all levels of one work item.
+int nc_args(bop_ctx* c, NcArgs* a) {
+  if (c->sdir_n != c->n) return fail(c, BOP_ERR_STATE, "noncollinear model: bop_set_spin_directions first");
+  memset(a, 0, sizeof(*a));
+  a->cv = cview(c);
+  a->H = c->fp64 ? c->H64.p : c->H32.p;
+  a->HS = c->HS;
+  a->onsite = c->fp64 ? c->onsite.p : c->onsite32.p;
+  a->sdir = P<double>(c->sdir);
+  a->n = c->n;
+  a->norb = c->norb;
+  a->n_mom = c->n_mom;
+  long long levsum = 0;
+  for (int k = 0; k <= c->K; k++) levsum += c->maxlev[k];
+  a->slot_elems = 2 * (size_t)levsum * c->norb * 8 + 64;
+  const int nwork = c->n * c->norb;
+  a->slots = nwork < 1216 ? nwork : 1216;
+  const size_t esz = c->fp64 ? sizeof(double) : sizeof(float);
+  CKS(ensure(c, c->ncscr, esz * a->slot_elems * (a->slots > 0 ? a->slots : 1)));
+  a->scratch = c->ncscr.p;
+  return BOP_OK;
+}
+
 int run_moments(bop_ctx* c, const double* onsite_dev, double* mu, cudaStream_t s, void* pstore = nullptr) {
+  if (c->m.noncollinear) {  // the onsite levels are in c->onsite / c->onsite32
+    NcArgs a;
+    CKS(nc_args(c, &a));
+    CKS(ensure(c, c->vmom, sizeof(double) * (size_t)c->n * c->norb * c->n_mom * 3));
+    a.mu = mu;
+    a.vmom = P<double>(c->vmom);
+    Region R(c, PK_MOMENTS, 1, s);
+    if (launch_nc(a, c->fp64, s)) return fail(c, BOP_ERR_CUDA, "spinor moments launch failed");
+    return BOP_OK;
+  }
   MomentsArgs a;
   a.cv = cview(c);
   a.H = c->fp64 ? c->H64.p : c->H32.p;
@@ -665,8 +713,8 @@ int psi_store_alloc(bop_ctx* c, bool* fits) {
 int prepare_psi_store(bop_ctx* c, cudaStream_t s) {
   // the SCF loop may have stored Psi in its forward passes; the last one is
   // at the final onsite levels
-  c->forces_follow = true;
-  if (c->m.scf == BOP_SCF_VARIATIONAL || c->psi_valid) return BOP_OK;
+  c->forces_follow = !c->m.noncollinear;
+  if (c->m.scf == BOP_SCF_VARIATIONAL || c->psi_valid || c->m.noncollinear) return BOP_OK;
   const bool several = (c->m.scf == BOP_SCF_LCN || c->m.scf == BOP_SCF_STONER) && c->m.scf_response;
   bool fits = false;
   if (several) CKS(psi_store_alloc(c, &fits));
@@ -1053,7 +1101,8 @@ int bop_destroy(bop_ctx* c) {
                   &c->ginv, &c->hx, &c->hf, &c->gamma, &c->scfred, &c->lbase, &c->lnlev, &c->lflag, &c->lxs,
                   &c->lys, &c->lZ1, &c->lH1, &c->lZ2, &c->lH2, &c->lybar, &c->lcot, &c->lxbar, &c->lcount,
                   &c->rwN, &c->rwt, &c->rdUE, &c->rvec, &c->rcoef, &c->rjv, &c->rjcnt, &c->rjptr, &c->rjidx, &c->rjrow, &c->vgrad, &c->vq, &c->erep,
-                  &c->psi_off, &c->psis, &c->psib, &c->lsum};
+                  &c->psi_off, &c->psis, &c->psib, &c->lsum, &c->sdir, &c->vmom, &c->obar, &c->torque,
+                  &c->ncscr};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -1285,7 +1334,12 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   if (delta_io) CK(cudaMemcpyAsync(c->delta.p, delta_io, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   else CK(cudaMemsetAsync(c->delta.p, 0, sizeof(double) * n, s));
   const bool stoner = c->m.scf == BOP_SCF_STONER;
-  if (stoner) {
+  // moment magnitudes: Stoner SCF, or fixed for a non-collinear model without SCF
+  const bool magnetic = stoner || c->m.noncollinear;
+  if (c->m.noncollinear && c->sdir_n != n)
+    return fail(c, BOP_ERR_STATE, "noncollinear model: bop_set_spin_directions first");
+  if (magnetic) {
+    CKS(ensure(c, c->mval, sizeof(double) * n));
     if (m_io) CK(cudaMemcpyAsync(c->mval.p, m_io, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     else {
       std::vector<double> h(n, c->m.m0);
@@ -1354,7 +1408,7 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
     {
       Region R(c, PK_ONSITE, 1, s);
       launch_build_onsite(n, c->norb, c->S, c->m.onsite0, c->m.onsite_s, c->m.stoner_I, P<double>(c->delta),
-                          stoner ? P<double>(c->mval) : nullptr, P<double>(c->onsite), P<float>(c->onsite32), s);
+                          magnetic ? P<double>(c->mval) : nullptr, P<double>(c->onsite), P<float>(c->onsite32), s);
     }
     CKS(run_moments(c, P<double>(c->onsite), P<double>(c->mu), s, var_store ? c->psis.p : nullptr));
     c->psi_valid = var_store;
@@ -1404,14 +1458,14 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   }
   {
   Region Re(c, PK_ENERGY, 1, s);
-  if (launch_energy(n, c->norb, c->S, c->sfac, c->m.stoner_I, P<double>(c->U), stoner ? P<double>(c->mval) : nullptr,
+  if (launch_energy(n, c->norb, c->S, c->sfac, c->m.stoner_I, P<double>(c->U), magnetic ? P<double>(c->mval) : nullptr,
                     c->m.j_ii, variational ? P<double>(c->N) : nullptr, c->m.n_e, rep ? P<double>(c->erep) : nullptr,
                     e_atom ? e_atom : P<double>(c->e_atom), P<double>(c->partials), P<unsigned>(c->counter),
                     P<double>(c->e_total), s))
     return fail(c, BOP_ERR_CUDA, "energy launch failed");
   }
   if (delta_io) CK(cudaMemcpyAsync(delta_io, c->delta.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  if (m_io && stoner) CK(cudaMemcpyAsync(m_io, c->mval.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  if (m_io && magnetic) CK(cudaMemcpyAsync(m_io, c->mval.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   double et = 0.0;
   unsigned nl[2] = {0, 0};
   CK(cudaMemcpyAsync(&et, c->e_total.p, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1467,8 +1521,30 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
         return fail(c, BOP_ERR_CUDA, "E_F response launch failed");
     }
     CKS(compute_weights(c, c->sfac, P<double>(c->lam), 0.0, P<double>(c->w), nullptr, s));
-    CK(cudaMemsetAsync(c->Ebar.p, 0, sizeof(double) * (size_t)M, s));
-    CKS(adjoint_pass(c, P<double>(c->w), P<double>(c->Hbar), P<double>(c->Ebar), s));
+    if (c->m.noncollinear) {
+      // reverse sweep of the spinor moments: bond and onsite-matrix
+      // cotangents, then the torques of Eq. torque
+      NcArgs a;
+      CKS(nc_args(c, &a));
+      CKS(ensure(c, c->obar, sizeof(double) * (size_t)n * c->norb * 4));
+      CKS(ensure(c, c->torque, sizeof(double) * 3 * (size_t)n));
+      CK(cudaMemsetAsync(c->obar.p, 0, sizeof(double) * (size_t)n * c->norb * 4, s));
+      a.w = P<double>(c->w);
+      a.Hbar = P<double>(c->Hbar);
+      a.HSu = c->HSu;
+      a.obar = P<double>(c->obar);
+      {
+        Region R(c, PK_ADJOINT, 1, s);
+        if (launch_nc(a, c->fp64, s)) return fail(c, BOP_ERR_CUDA, "spinor reverse sweep launch failed");
+      }
+      Region R(c, PK_FORCES, 1, s);
+      if (launch_torques(n, c->norb, c->n_mom, P<double>(c->onsite), P<double>(c->sdir), P<double>(c->w),
+                         P<double>(c->vmom), P<double>(c->obar), P<double>(c->torque), s))
+        return fail(c, BOP_ERR_CUDA, "torques launch failed");
+    } else {
+      CK(cudaMemsetAsync(c->Ebar.p, 0, sizeof(double) * (size_t)M, s));
+      CKS(adjoint_pass(c, P<double>(c->w), P<double>(c->Hbar), P<double>(c->Ebar), s));
+    }
   }
   DBuf* fb = nullptr;
   DBuf tf, tv;
@@ -1502,6 +1578,39 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   if (solve_status != BOP_OK)
     return fail(c, solve_status, "SCF-response solve stopped at relative residual %g after %d iterations",
                 c->st.response_residual, c->st.response_iterations);
+  return BOP_OK;
+}
+
+int bop_set_spin_directions(bop_ctx* c, const double* sd, bop_stream stream) {
+  if (!c) return BOP_ERR_ARG;
+  if (!c->m.noncollinear) return fail(c, BOP_ERR_ARG, "spin directions need a noncollinear model");
+  if (!c->built) return fail(c, BOP_ERR_STATE, "no structure built");
+  if (!sd) return fail(c, BOP_ERR_ARG, "directions are NULL");
+  cudaStream_t s = S_(stream);
+  const int n = c->n;
+  std::vector<double> h(3 * (size_t)n);
+  CK(cudaMemcpyAsync(h.data(), sd, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int i = 0; i < n; i++) {
+    double* v = h.data() + 3 * (size_t)i;
+    const double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (!(r >= 1e-12 && r < 1e300)) return fail(c, BOP_ERR_ARG, "direction of atom %d has norm %g", i, r);
+    for (int x = 0; x < 3; x++) v[x] /= r;
+  }
+  CKS(ensure(c, c->sdir, sizeof(double) * 3 * (size_t)n));
+  CK(cudaMemcpyAsync(c->sdir.p, h.data(), sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  c->sdir_n = n;
+  c->energized = c->weighted = false;
+  return BOP_OK;
+}
+
+int bop_torques(bop_ctx* c, double* t, bop_stream stream) {
+  if (!c) return BOP_ERR_ARG;
+  if (!c->m.noncollinear) return fail(c, BOP_ERR_ARG, "torques need a noncollinear model");
+  if (!c->weighted) return fail(c, BOP_ERR_STATE, "bop_torques needs a preceding bop_forces");
+  if (!t) return fail(c, BOP_ERR_ARG, "t is NULL");
+  CK(cudaMemcpyAsync(t, c->torque.p, sizeof(double) * 3 * (size_t)c->n, cudaMemcpyDeviceToDevice, S_(stream)));
   return BOP_OK;
 }
 

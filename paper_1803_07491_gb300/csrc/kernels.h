@@ -121,6 +121,31 @@ struct AdjointArgs {
 };
 int launch_moments_adjoint(const AdjointArgs& a, int fp64, cudaStream_t s);
 
+// Non-collinear spin moments (moments.cu): work item (atom, orbital), the
+// two local spin states of the atom as starting spinors.
+struct NcArgs {
+  ClusterView cv;
+  const void* H;       // float or double [nb][HS]
+  int HS;
+  const void* onsite;  // float or double [2][n][norb]: E_up, E_dn
+  const double* sdir;  // [n][3] unit moment directions
+  int n, norb, n_mom;
+  void* scratch;       // per-CTA Psi / Psi-bar storage
+  size_t slot_elems;   // elements of T per CTA: 2 sum_k max |C_k| norb 8
+  int slots;
+  // forward (w == NULL): local channel moments and Tr(sigma M_n)
+  double* mu;          // [2][n][norb][n_mom]
+  double* vmom;        // [n][norb][n_mom][3]
+  // reverse (w != NULL): cotangents of sum w mu
+  const double* w;     // [2][n][norb][n_mom]
+  double* Hbar;        // [nb][HSu] (+=)
+  int HSu;
+  double* obar;        // [n][norb][4] (+=): d/d(Ebar, h_x, h_y, h_z)
+};
+int launch_nc(const NcArgs& a, int fp64, cudaStream_t s);
+int launch_torques(int n, int norb, int n_mom, const double* onsite, const double* sdir, const double* w,
+                   const double* vmom, const double* obar, double* t, cudaStream_t s);
+
 // Band centre / width estimate of the constant terminator (BOP_BW_* of
 // bopgb.h): mode, beta of the weighted average, (A, B) of the global mode.
 struct BandSel {

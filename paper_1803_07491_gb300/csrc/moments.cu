@@ -852,6 +852,354 @@ k_moments_adj(ClusterView cv, const T* __restrict__ H, int HS, const T* __restri
   }
 }
 
+// ------------------------------------------------------------------ non-collinear spin moments
+// Non-collinear magnetism (section "Magnetism", Eqs. onsite_CM and
+// onsite-noncollinear).  Work item (atom i, orbital alpha); its two
+// starting states are the local spin states of atom i, chi_up antiparallel
+// to the moment direction s_i (eigenvalue -1 of s_i.sigma, the lower level)
+// and chi_dn parallel, complex 2-spinors in the spin basis along z.  A site
+// row holds NO x 8 reals, column c = nu * 4 + sp * 2 + ri (starting spinor
+// nu, spin component sp, real / imaginary part).  The hopping H_e x 1 acts
+// on the orbital index (block_apply with 8 columns); the onsite matrix
+// Ebar + h.sigma, Ebar = (E_up + E_dn)/2, h = (E_dn - E_up)/2 s_j, mixes
+// the four reals of each spinor.  In this real form every operator is
+// symmetric, so the reverse sweep gathers with the same rows.
+//   forward (wts == NULL): local channel moments mu_nu,n = <chi_nu|H^n|chi_nu>
+//   into mu[nu] and Tr(sigma M_n) of the global 2x2 moments M_n into vmom;
+//   reverse (wts != NULL): cotangents of L = sum w_nu,n mu_nu,n for every
+//   bond block (Hbar, FP64 atomics) and every onsite matrix
+//   (obar = dL/d(Ebar, h_x, h_y, h_z)).
+// Psi_0..Psi_K (and Psi-bar_1..Psi-bar_K) of the item live in the CTA's
+// slot of global scratch, as in k_moments_adj.
+constexpr int NCS = 8;
+
+// chi_up = (-(x - i y), 1 + z) r, chi_dn = (1 + z, x + i y) r for z >= 0,
+// chi_up = (1 - z, -(x + i y)) r, chi_dn = (x - i y, 1 - z) r otherwise
+// (r normalises; the second form avoids the zero of 1 + z at s = -z).
+__device__ __forceinline__ void start_spinors(const double* s, double* out) {
+  const double x = s[0], y = s[1], z = s[2];
+  if (z >= 0.0) {
+    const double r = 1.0 / sqrt(2.0 * (1.0 + z));
+    out[0] = -x * r; out[1] = y * r; out[2] = (1.0 + z) * r; out[3] = 0.0;
+    out[4] = (1.0 + z) * r; out[5] = 0.0; out[6] = x * r; out[7] = y * r;
+  } else {
+    const double r = 1.0 / sqrt(2.0 * (1.0 - z));
+    out[0] = (1.0 - z) * r; out[1] = 0.0; out[2] = -x * r; out[3] = -y * r;
+    out[4] = x * r; out[5] = -y * r; out[6] = (1.0 - z) * r; out[7] = 0.0;
+  }
+}
+
+// y = (Ebar + h.sigma) x for both spinors of one orbital row
+template <typename T>
+__device__ __forceinline__ void spin_onsite(T eb, T hx, T hy, T hz, const T* __restrict__ x, T* y) {
+#pragma unroll
+  for (int nu = 0; nu < 2; nu++) {
+    const T ur = x[4 * nu], ui = x[4 * nu + 1], dr = x[4 * nu + 2], di = x[4 * nu + 3];
+    y[4 * nu] = (eb + hz) * ur + hx * dr + hy * di;
+    y[4 * nu + 1] = (eb + hz) * ui + hx * di - hy * dr;
+    y[4 * nu + 2] = (eb - hz) * dr + hx * ur - hy * ui;
+    y[4 * nu + 3] = (eb - hz) * di + hx * ui + hy * ur;
+  }
+}
+
+// acc = (H x)[t] over columns s < ncol (onsite term when t < ncol)
+template <typename T, int NO>
+__device__ __forceinline__ void gather_row_nc(const ClusterView& cv, const T* __restrict__ H, int HS,
+                                              const T* __restrict__ E, const double* __restrict__ sdir, int n,
+                                              const int* __restrict__ satom, const long long* __restrict__ aoff,
+                                              int t, int ncol, const T* __restrict__ x, T acc[NO][NCS]) {
+#pragma unroll
+  for (int r = 0; r < NO; r++)
+#pragma unroll
+    for (int c = 0; c < NCS; c++) acc[r][c] = T(0);
+  if (t < ncol) {
+    const int j = satom[t];
+    const T sx = (T)sdir[3 * (size_t)j], sy = (T)sdir[3 * (size_t)j + 1], sz = (T)sdir[3 * (size_t)j + 2];
+#pragma unroll
+    for (int r = 0; r < NO; r++) {
+      const T eu = E[(size_t)j * NO + r], ed = E[((size_t)n + j) * NO + r];
+      const T f = T(0.5) * (ed - eu);
+      spin_onsite<T>(T(0.5) * (eu + ed), f * sx, f * sy, f * sz, x + ((size_t)t * NO + r) * NCS, acc[r]);
+    }
+  }
+  const long long q1 = aoff[t + 1];
+  for (long long q = aoff[t]; q < q1; q++) {
+    const int2 en = cv.adj[q];
+    if (en.x >= ncol) break;
+    block_apply<T, NO, NCS>(H + (size_t)en.y * HS, x + (size_t)en.x * NO * NCS, acc);
+  }
+}
+
+// Tr(sigma M) of M = C L C^dagger, C = (chi_up chi_dn), L = [[Luu, Lud],
+// [conj(Lud), Ldd]] the moments between the local states.
+__device__ __forceinline__ void pauli_from_local(const double* chi, double Luu, double Ldd, double Lr, double Li,
+                                                 double v[3]) {
+  // C_a,nu = chi[nu * 4 + a * 2] + i chi[nu * 4 + a * 2 + 1]
+  double M00 = 0.0, M11 = 0.0, M01r = 0.0, M01i = 0.0;
+  const double L[2][2][2] = {{{Luu, 0.0}, {Lr, Li}}, {{Lr, -Li}, {Ldd, 0.0}}};  // [nu][nu'][re/im]
+#pragma unroll
+  for (int nu = 0; nu < 2; nu++)
+#pragma unroll
+    for (int mu_ = 0; mu_ < 2; mu_++) {
+      const double lr = L[nu][mu_][0], li = L[nu][mu_][1];
+      // M_ab += C_a,nu L_nu,mu conj(C_b,mu)
+      const double c0r = chi[nu * 4], c0i = chi[nu * 4 + 1], c1r = chi[nu * 4 + 2], c1i = chi[nu * 4 + 3];
+      const double d0r = chi[mu_ * 4], d0i = chi[mu_ * 4 + 1], d1r = chi[mu_ * 4 + 2], d1i = chi[mu_ * 4 + 3];
+      // x = C_a,nu L
+      const double x0r = c0r * lr - c0i * li, x0i = c0r * li + c0i * lr;
+      const double x1r = c1r * lr - c1i * li, x1i = c1r * li + c1i * lr;
+      M00 += x0r * d0r + x0i * d0i;
+      M11 += x1r * d1r + x1i * d1i;
+      M01r += x0r * d1r + x0i * d1i;
+      M01i += x0i * d1r - x0r * d1i;
+    }
+  v[0] = 2.0 * M01r;
+  v[1] = -2.0 * M01i;
+  v[2] = M00 - M11;
+}
+
+template <typename T, int NO>
+__global__ void __launch_bounds__(MOM_THREADS)
+k_nc(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, const double* __restrict__ sdir,
+     int n, int n_mom, int nwork, T* __restrict__ scratch, size_t slot_elems, double* __restrict__ mu,
+     double* __restrict__ vmom, const double* __restrict__ wts, double* __restrict__ Hbar, int HSu,
+     double* __restrict__ obar) {
+  constexpr int RW = NO * NCS;
+  __shared__ T ws[2][BOP_MAX_NMOM];
+  __shared__ int s_lev[BOP_MAX_K + 1];
+  __shared__ long long s_off[BOP_MAX_K + 2];
+  __shared__ T red[8][MOM_THREADS / 32];
+  __shared__ double chi[NCS];
+  const bool rev = wts != nullptr;
+  const int K = cv.K;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  T* psi = scratch + (size_t)blockIdx.x * slot_elems;
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int atom = w / NO, al = w % NO;
+    const long long s0 = cv.site_off[atom];
+    const int* lev = cv.level_end + (size_t)atom * (K + 1);
+    const int* satom = cv.site_atom + s0;
+    const long long* aoff = cv.adj_off + s0;
+    if (tid <= K) s_lev[tid] = lev[tid];
+    if (tid == 0) {  // Psi_k at s_off[k], Psi-bar_k at s_off[K+1] + (s_off[k] - s_off[1])
+      long long o = 0;
+      for (int k = 0; k <= K; k++) {
+        s_off[k] = o;
+        o += (long long)lev[k] * RW;
+      }
+      s_off[K + 1] = o;
+      start_spinors(sdir + 3 * (size_t)atom, chi);
+    }
+    if (rev)
+      for (int q = tid; q < 2 * n_mom; q += blockDim.x) {
+        const int nu = q / n_mom, m = q % n_mom;
+        ws[nu][m] = (T)wts[(((size_t)nu * n + atom) * NO + al) * n_mom + m];
+      }
+    __syncthreads();
+    T* P = psi;
+    T* Pb = psi + s_off[K + 1] - s_off[1];
+    for (int q = tid; q < RW; q += blockDim.x) P[q] = (q / NCS == al) ? (T)chi[q % NCS] : T(0);
+    if (!rev && tid < 2) {
+      mu[(((size_t)tid * n + atom) * NO + al) * n_mom] = 1.0;
+      vmom[(((size_t)atom * NO + al) * n_mom) * 3 + tid] = 0.0;
+      if (tid == 0) vmom[(((size_t)atom * NO + al) * n_mom) * 3 + 2] = 0.0;
+    }
+    __syncthreads();
+    for (int k = 1; k <= K; k++) {
+      const T* x = P + s_off[k - 1];
+      T* y = P + s_off[k];
+      T d[8];
+#pragma unroll
+      for (int v = 0; v < 8; v++) d[v] = T(0);
+      for (int t = tid; t < s_lev[k]; t += blockDim.x) {
+        T acc[NO][NCS];
+        gather_row_nc<T, NO>(cv, H, HS, onsite, sdir, n, satom, aoff, t, s_lev[k - 1], x, acc);
+#pragma unroll
+        for (int r = 0; r < NO; r++)
+#pragma unroll
+          for (int c = 0; c < NCS; c++) y[((size_t)t * NO + r) * NCS + c] = acc[r][c];
+        if (!rev) {
+          // <Psi^nu|Psi^nu'>: up-up, dn-dn, and Re / Im of up-dn
+#pragma unroll
+          for (int r = 0; r < NO; r++) {
+            const T* a = acc[r];
+            d[4] += a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3];
+            d[5] += a[4] * a[4] + a[5] * a[5] + a[6] * a[6] + a[7] * a[7];
+            d[6] += a[0] * a[4] + a[1] * a[5] + a[2] * a[6] + a[3] * a[7];
+            d[7] += a[0] * a[5] - a[1] * a[4] + a[2] * a[7] - a[3] * a[6];
+            if (t < s_lev[k - 1]) {
+              const T* p = x + ((size_t)t * NO + r) * NCS;
+              d[0] += p[0] * a[0] + p[1] * a[1] + p[2] * a[2] + p[3] * a[3];
+              d[1] += p[4] * a[4] + p[5] * a[5] + p[6] * a[6] + p[7] * a[7];
+              d[2] += p[0] * a[4] + p[1] * a[5] + p[2] * a[6] + p[3] * a[7];
+              d[3] += p[0] * a[5] - p[1] * a[4] + p[2] * a[7] - p[3] * a[6];
+            }
+          }
+        }
+      }
+      if (!rev) {
+#pragma unroll
+        for (int v = 0; v < 8; v++) {
+          const T r_ = warp_sum(d[v]);
+          if (lane == 0) red[v][wid] = r_;
+        }
+        __syncthreads();
+        if (tid < 2) {  // moment 2k-1 (tid 0) and 2k (tid 1)
+          double L[4];
+          for (int v = 0; v < 4; v++) {
+            T a = T(0);
+            for (int q = 0; q < MOM_THREADS / 32; q++) a += red[4 * tid + v][q];
+            L[v] = (double)a;
+          }
+          const int m = 2 * k - 1 + tid;
+          mu[((size_t)atom * NO + al) * n_mom + m] = L[0];
+          mu[(((size_t)n + atom) * NO + al) * n_mom + m] = L[1];
+          double v3[3];
+          pauli_from_local(chi, L[0], L[1], L[2], L[3], v3);
+          for (int xx = 0; xx < 3; xx++) vmom[(((size_t)atom * NO + al) * n_mom + m) * 3 + xx] = v3[xx];
+        }
+      }
+      __syncthreads();
+    }
+    if (rev) {
+      // Psi-bar_K = 2 w_2K Psi_K + w_2K-1 Psi_K-1 (weights of each spinor's columns)
+      {
+        const T* PK = P + s_off[K];
+        const T* PK1 = P + s_off[K - 1];
+        T* B = Pb + s_off[K];
+        for (int q = tid; q < s_lev[K] * RW; q += blockDim.x) {
+          const int t = q / RW, nu = (q % NCS) >> 2;
+          T v = T(2) * ws[nu][2 * K] * PK[q];
+          if (t < s_lev[K - 1]) v += ws[nu][2 * K - 1] * PK1[q];
+          B[q] = v;
+        }
+      }
+      __syncthreads();
+      for (int k = K; k >= 2; k--) {
+        const T* xb = Pb + s_off[k];
+        T* yb = Pb + s_off[k - 1];
+        const T* Pk = P + s_off[k];
+        const T* Pk1 = P + s_off[k - 1];
+        const T* Pk2 = P + s_off[k - 2];
+        for (int t = tid; t < s_lev[k - 1]; t += blockDim.x) {
+          T acc[NO][NCS];
+          gather_row_nc<T, NO>(cv, H, HS, onsite, sdir, n, satom, aoff, t, s_lev[k], xb, acc);
+#pragma unroll
+          for (int r = 0; r < NO; r++)
+#pragma unroll
+            for (int c = 0; c < NCS; c++) {
+              const size_t q = ((size_t)t * NO + r) * NCS + c;
+              const int nu = c >> 2;
+              T v = acc[r][c] + T(2) * ws[nu][2 * k - 2] * Pk1[q] + ws[nu][2 * k - 1] * Pk[q];
+              if (t < s_lev[k - 2]) v += ws[nu][2 * k - 3] * Pk2[q];
+              yb[q] = v;
+            }
+        }
+        __syncthreads();
+      }
+      for (int t = tid; t < s_lev[K]; t += blockDim.x) {
+        const int lt = site_level(s_lev, K, t);
+        for (long long q = aoff[t]; q < aoff[t + 1]; q++) {
+          const int2 en = cv.adj[q];
+          const int sidx = en.x;
+          if (sidx >= s_lev[K - 1]) break;
+          const int ls = site_level(s_lev, K, sidx);
+          const int kmin = lt > ls + 1 ? lt : ls + 1;
+          T G[NO][NO];
+#pragma unroll
+          for (int b = 0; b < NO; b++)
+#pragma unroll
+            for (int g = 0; g < NO; g++) G[b][g] = T(0);
+          for (int k = kmin; k <= K; k++) {
+            const T* pb = Pb + s_off[k] + (size_t)t * RW;
+            const T* ps = P + s_off[k - 1] + (size_t)sidx * RW;
+#pragma unroll
+            for (int b = 0; b < NO; b++)
+#pragma unroll
+              for (int g = 0; g < NO; g++) {
+                T a = T(0);
+#pragma unroll
+                for (int c = 0; c < NCS; c++) a += pb[b * NCS + c] * ps[g * NCS + c];
+                G[b][g] += a;
+              }
+          }
+          double* hb = Hbar + (size_t)en.y * HSu;
+          if constexpr (NO == 1) {
+            atomicAdd(hb, (double)G[0][0]);
+          } else {
+#pragma unroll
+            for (int b = 0; b < NO; b++)
+#pragma unroll
+              for (int g = b; g < NO; g++) atomicAdd(hb + UI<NO>(b, g), (double)G[b][g] + (b != g ? (double)G[g][b] : 0.0));
+          }
+        }
+        if (lt + 1 <= K) {
+          // dL/d(Ebar, h) of the onsite matrix of (atom of t, b): the
+          // derivatives of Ebar + h.sigma in the real form
+          double* op = obar + (size_t)satom[t] * NO * 4;
+#pragma unroll
+          for (int b = 0; b < NO; b++) {
+            T o0 = T(0), ox = T(0), oy = T(0), oz = T(0);
+            for (int k = lt + 1; k <= K; k++) {
+              const T* pb = Pb + s_off[k] + (size_t)t * RW + b * NCS;
+              const T* pt = P + s_off[k - 1] + (size_t)t * RW + b * NCS;
+#pragma unroll
+              for (int nu = 0; nu < 2; nu++) {
+                const T bur = pb[4 * nu], bui = pb[4 * nu + 1], bdr = pb[4 * nu + 2], bdi = pb[4 * nu + 3];
+                const T pur = pt[4 * nu], pui = pt[4 * nu + 1], pdr = pt[4 * nu + 2], pdi = pt[4 * nu + 3];
+                o0 += bur * pur + bui * pui + bdr * pdr + bdi * pdi;
+                ox += bur * pdr + bui * pdi + bdr * pur + bdi * pui;
+                oy += bur * pdi - bui * pdr - bdr * pui + bdi * pur;
+                oz += bur * pur + bui * pui - bdr * pdr - bdi * pdi;
+              }
+            }
+            atomicAdd(op + 4 * b, (double)o0);
+            atomicAdd(op + 4 * b + 1, (double)ox);
+            atomicAdd(op + 4 * b + 2, (double)oy);
+            atomicAdd(op + 4 * b + 3, (double)oz);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Torques of Eq. torque, one thread per atom: dU/ds_i = sum_alpha
+// [ (E_dn - E_up)/2 dU/dh_i alpha + sum_n (w_dn - w_up)/2 Tr(sigma M_n) ],
+// t_i = dU/ds_i x s_i.
+__global__ void k_torques(int n, int norb, int n_mom, const double* __restrict__ onsite,
+                          const double* __restrict__ sdir, const double* __restrict__ w,
+                          const double* __restrict__ vmom, const double* __restrict__ obar, double* __restrict__ t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double g[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < norb; a++) {
+    const size_t o = (size_t)i * norb + a;
+    const double half_delta = 0.5 * (onsite[(size_t)n * norb + o] - onsite[o]);
+    for (int x = 0; x < 3; x++) g[x] += half_delta * obar[o * 4 + 1 + x];
+    for (int m = 0; m < n_mom; m++) {
+      const double c = 0.5 * (w[((size_t)n * norb + o) * n_mom + m] - w[o * n_mom + m]);
+      for (int x = 0; x < 3; x++) g[x] += c * vmom[(o * n_mom + m) * 3 + x];
+    }
+  }
+  const double sx = sdir[3 * (size_t)i], sy = sdir[3 * (size_t)i + 1], sz = sdir[3 * (size_t)i + 2];
+  t[3 * (size_t)i] = g[1] * sz - g[2] * sy;
+  t[3 * (size_t)i + 1] = g[2] * sx - g[0] * sz;
+  t[3 * (size_t)i + 2] = g[0] * sy - g[1] * sx;
+}
+
+template <typename T, int NO>
+int run_nc(const NcArgs& a, cudaStream_t s) {
+  const int nwork = a.n * NO;
+  if (nwork == 0) return 0;
+  const int grid = nwork < a.slots ? nwork : a.slots;
+  k_nc<T, NO><<<grid, MOM_THREADS, 0, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.sdir, a.n, a.n_mom,
+                                           nwork, (T*)a.scratch, a.slot_elems, a.mu, a.vmom, a.w, a.Hbar, a.HSu,
+                                           a.obar);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 template <typename T, int NO, int NC>
 int run_forward(const MomentsArgs& a, cudaStream_t s) {
   constexpr int N = NO * NC;
@@ -975,4 +1323,17 @@ int launch_moments_adjoint(const AdjointArgs& a, int fp64, cudaStream_t s) {
   if (a.norb == 1) return fp64 ? run_adjoint<double, 1, 1>(a, s) : run_adjoint<float, 1, 1>(a, s);
   if (a.norb == 6) return fp64 ? run_adjoint<double, 6, 6>(a, s) : run_adjoint<float, 6, 6>(a, s);
   return fp64 ? run_adjoint<double, 5, 5>(a, s) : run_adjoint<float, 5, 5>(a, s);
+}
+
+int launch_nc(const NcArgs& a, int fp64, cudaStream_t s) {
+  if (a.norb == 1) return fp64 ? run_nc<double, 1>(a, s) : run_nc<float, 1>(a, s);
+  if (a.norb == 6) return fp64 ? run_nc<double, 6>(a, s) : run_nc<float, 6>(a, s);
+  return fp64 ? run_nc<double, 5>(a, s) : run_nc<float, 5>(a, s);
+}
+
+int launch_torques(int n, int norb, int n_mom, const double* onsite, const double* sdir, const double* w,
+                   const double* vmom, const double* obar, double* t, cudaStream_t s) {
+  if (n == 0) return 0;
+  k_torques<<<(n + 127) / 128, 128, 0, s>>>(n, norb, n_mom, onsite, sdir, w, vmom, obar, t);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
