@@ -113,7 +113,9 @@ def test_spiral_workload_properties(bop):
     """The 2,000-atom spin-spiral workload as benched (FP32 products):
     converged SCF, torques normal to the moments and summing to zero (no
     spin-orbit coupling), forces summing to zero."""
-    w = I.workload("nc2000")
+    # FP32 moments put a floor of a few 1e-6 electrons under the SCF
+    # residual: the tolerance the benchmark takes with FP32 products
+    w = I.with_run(I.workload("nc2000"), scf_tol=3e-5)
     ctx = bop.Context(w.model, w.run, "fp32")
     res = ctx.evaluate(w.pos, w.cell, w.pbc, spin_dir=w.meta["spin_dir"])
     ctx.close()
