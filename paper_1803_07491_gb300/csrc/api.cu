@@ -445,6 +445,11 @@ int nc_args(bop_ctx* c, NcArgs* a) {
   a->n = c->n;
   a->norb = c->norb;
   a->n_mom = c->n_mom;
+  a->cap_even = a->cap_odd = 1;
+  for (int k = 0; k < c->K; k++) {  // level K is never stored by the forward pass
+    int& cap = (k & 1) ? a->cap_odd : a->cap_even;
+    if (c->maxlev[k] > cap) cap = c->maxlev[k];
+  }
   long long levsum = 0;
   for (int k = 0; k <= c->K; k++) levsum += c->maxlev[k];
   a->slot_elems = 2 * (size_t)levsum * c->norb * 8 + 64;

@@ -130,6 +130,7 @@ struct NcArgs {
   const void* onsite;  // float or double [2][n][norb]: E_up, E_dn
   const double* sdir;  // [n][3] unit moment directions
   int n, norb, n_mom;
+  int cap_even, cap_odd;  // largest even / odd level |C_k| (k < K) over atoms (forward in shared memory)
   void* scratch;       // per-CTA Psi / Psi-bar storage
   size_t slot_elems;   // elements of T per CTA: 2 sum_k max |C_k| norb 8
   int slots;

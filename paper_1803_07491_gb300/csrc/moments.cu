@@ -1165,6 +1165,95 @@ k_nc(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsi
   }
 }
 
+// Forward-only form of k_nc: Psi_k-1 and Psi_k in two shared-memory
+// buffers (even and odd levels, each sized for the largest such level
+// below K over all atoms; Psi_K is never stored, only its inner products).
+template <typename T, int NO>
+__global__ void __launch_bounds__(MOM_THREADS)
+k_nc_fwd(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite,
+         const double* __restrict__ sdir, int n, int n_mom, int nwork, int cap_even, double* __restrict__ mu,
+         double* __restrict__ vmom) {
+  constexpr int RW = NO * NCS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* const buf0 = reinterpret_cast<T*>(smem_raw);
+  T* const buf1 = buf0 + (size_t)cap_even * RW;
+  __shared__ int s_lev[BOP_MAX_K + 1];
+  __shared__ T red[8][MOM_THREADS / 32];
+  __shared__ double chi[NCS];
+  const int K = cv.K;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const int atom = w / NO, al = w % NO;
+    const long long s0 = cv.site_off[atom];
+    const int* lev = cv.level_end + (size_t)atom * (K + 1);
+    const int* satom = cv.site_atom + s0;
+    const long long* aoff = cv.adj_off + s0;
+    if (tid <= K) s_lev[tid] = lev[tid];
+    if (tid == 0) start_spinors(sdir + 3 * (size_t)atom, chi);
+    __syncthreads();
+    for (int q = tid; q < RW; q += blockDim.x) buf0[q] = (q / NCS == al) ? (T)chi[q % NCS] : T(0);
+    if (tid < 2) {
+      mu[(((size_t)tid * n + atom) * NO + al) * n_mom] = 1.0;
+      vmom[(((size_t)atom * NO + al) * n_mom) * 3 + tid] = 0.0;
+      if (tid == 0) vmom[(((size_t)atom * NO + al) * n_mom) * 3 + 2] = 0.0;
+    }
+    __syncthreads();
+    for (int k = 1; k <= K; k++) {
+      const T* x = (k & 1) ? buf0 : buf1;  // level k-1
+      T* y = (k & 1) ? buf1 : buf0;        // level k
+      T d[8];
+#pragma unroll
+      for (int v = 0; v < 8; v++) d[v] = T(0);
+      for (int t = tid; t < s_lev[k]; t += blockDim.x) {
+        T acc[NO][NCS];
+        gather_row_nc<T, NO>(cv, H, HS, onsite, sdir, n, satom, aoff, t, s_lev[k - 1], x, acc);
+#pragma unroll
+        for (int r = 0; r < NO; r++) {
+          const T* a = acc[r];
+          d[4] += a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3];
+          d[5] += a[4] * a[4] + a[5] * a[5] + a[6] * a[6] + a[7] * a[7];
+          d[6] += a[0] * a[4] + a[1] * a[5] + a[2] * a[6] + a[3] * a[7];
+          d[7] += a[0] * a[5] - a[1] * a[4] + a[2] * a[7] - a[3] * a[6];
+          if (t < s_lev[k - 1]) {
+            const T* p = x + ((size_t)t * NO + r) * NCS;
+            d[0] += p[0] * a[0] + p[1] * a[1] + p[2] * a[2] + p[3] * a[3];
+            d[1] += p[4] * a[4] + p[5] * a[5] + p[6] * a[6] + p[7] * a[7];
+            d[2] += p[0] * a[4] + p[1] * a[5] + p[2] * a[6] + p[3] * a[7];
+            d[3] += p[0] * a[5] - p[1] * a[4] + p[2] * a[7] - p[3] * a[6];
+          }
+        }
+        if (k < K) {
+#pragma unroll
+          for (int r = 0; r < NO; r++)
+#pragma unroll
+            for (int c = 0; c < NCS; c++) y[((size_t)t * NO + r) * NCS + c] = acc[r][c];
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 8; v++) {
+        const T r_ = warp_sum(d[v]);
+        if (lane == 0) red[v][wid] = r_;
+      }
+      __syncthreads();
+      if (tid < 2) {  // moment 2k-1 (tid 0) and 2k (tid 1)
+        double L[4];
+        for (int v = 0; v < 4; v++) {
+          T a = T(0);
+          for (int q = 0; q < MOM_THREADS / 32; q++) a += red[4 * tid + v][q];
+          L[v] = (double)a;
+        }
+        const int m = 2 * k - 1 + tid;
+        mu[((size_t)atom * NO + al) * n_mom + m] = L[0];
+        mu[(((size_t)n + atom) * NO + al) * n_mom + m] = L[1];
+        double v3[3];
+        pauli_from_local(chi, L[0], L[1], L[2], L[3], v3);
+        for (int xx = 0; xx < 3; xx++) vmom[(((size_t)atom * NO + al) * n_mom + m) * 3 + xx] = v3[xx];
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Torques of Eq. torque, one thread per atom: dU/ds_i = sum_alpha
 // [ (E_dn - E_up)/2 dU/dh_i alpha + sum_n (w_dn - w_up)/2 Tr(sigma M_n) ],
 // t_i = dU/ds_i x s_i.
@@ -1194,6 +1283,17 @@ int run_nc(const NcArgs& a, cudaStream_t s) {
   const int nwork = a.n * NO;
   if (nwork == 0) return 0;
   const int grid = nwork < a.slots ? nwork : a.slots;
+  // forward only: both stored levels in shared memory when they fit
+  const size_t smem = (size_t)(a.cap_even + a.cap_odd) * NO * NCS * sizeof(T);
+  if (a.w == nullptr && a.cap_even >= 1 && a.cap_odd >= 1 && smem <= 200 * 1024) {
+    auto fn = k_nc_fwd<T, NO>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return -1;
+    fn<<<grid, MOM_THREADS, smem, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.sdir, a.n, a.n_mom, nwork,
+                                       a.cap_even, a.mu, a.vmom);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  }
   k_nc<T, NO><<<grid, MOM_THREADS, 0, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.sdir, a.n, a.n_mom,
                                            nwork, (T*)a.scratch, a.slot_elems, a.mu, a.vmom, a.w, a.Hbar, a.HSu,
                                            a.obar);
