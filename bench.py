@@ -487,10 +487,14 @@ def profile_traffic(family: str, workload: str):
 
 
 # ------------------------------------------------------------ CPU oracle
+SAMPLED_AS_SUCH = ("d2000", "d2000nscf", "d2000var", "d2000cut", "mag2000", "mag65k", "nc2000")
+
+
 def sample_settings(workload: str):
-    """Run settings of a 2,000-atom bcc workload (d2000 for the others)."""
+    """Run settings of a bcc workload of the canonical d model (d2000 for
+    the others)."""
     from paper_1803_07491_gb300 import inputs as I
-    return I.workload(workload if workload in ("d2000", "d2000nscf", "d2000var", "d2000cut") else "d2000").run
+    return I.workload(workload if workload in SAMPLED_AS_SUCH else "d2000").run
 
 
 def oracle_sample(n_cells: int, workload: str = "d2000"):
@@ -498,28 +502,37 @@ def oracle_sample(n_cells: int, workload: str = "d2000"):
     model and settings (jitter 0.05 A, seed 2): a bounded sample of the
     workload; the per-atom work of the method does not depend on the cell
     size (clusters are built with periodic images)."""
+    import numpy as np
+
     from oracle import bop as ob
     from paper_1803_07491_gb300 import inputs as I
     ob.build()
     pos, cell = I.bcc_jittered(n_cells, n_cells, n_cells, 0.05, 2)
     r = sample_settings(workload)
     p = I.MODEL_D
+    # the spin spiral of the sample cell: one period over it, as the workload's
+    sdir = I.spiral_directions(pos, cell[0, 0], np.pi / 3) if r.noncollinear else None
     t0 = time.perf_counter()
     ob.evaluate(ob.Model(p.norb, tuple(p.b0), p.r0, p.lam, p.rc, p.dc, p.onsite0),
-                ob.Settings(n_e=r.n_e, n_mom=r.n_mom, n_exp=r.n_exp, scf=r.scf, eta=r.eta, scf_tol=r.scf_tol,
-                            scf_max_it=r.scf_max_it, mixer=r.mixer, mix_history=r.mix_history, J_ii=r.J_ii,
-                            r_path=r.r_path),
-                pos, cell, (1, 1, 1))
+                ob.Settings(n_e=r.n_e, n_mom=r.n_mom, n_exp=r.n_exp, n_spin=r.n_spin, scf=r.scf, eta=r.eta,
+                            scf_tol=r.scf_tol, scf_max_it=r.scf_max_it, stoner_I=r.stoner_I, m_mix=r.m_mix,
+                            m0=r.m0, mixer=r.mixer, mix_history=r.mix_history, scf_response=r.scf_response,
+                            J_ii=r.J_ii, r_path=r.r_path, noncollinear=r.noncollinear),
+                pos, cell, (1, 1, 1), spin_dir=sdir)
     return len(pos), time.perf_counter() - t0
 
 
 def sample_label(workload: str) -> str:
-    scf = sample_settings(workload).scf
-    return {"lcn": "LCN SCF", "none": "no SCF", "variational": "variational SCF"}[scf]
+    r = sample_settings(workload)
+    label = {"lcn": "LCN SCF", "none": "no SCF", "variational": "variational SCF", "stoner": "Stoner SCF"}[r.scf]
+    return ("non-collinear spin spiral, " + label) if r.noncollinear else label
 
 
 def cpu_baseline(workload: str):
-    k = 2 if sample_settings(workload).scf == "variational" else 3
+    r = sample_settings(workload)
+    # about 10-30 s on one core: the variational SCF and the collinear Stoner
+    # SCF with its dense response solve take the 16-atom cell
+    k = 2 if r.scf == "variational" or (r.scf == "stoner" and not r.noncollinear) else 3
     n, t = oracle_sample(k, workload)
     return {"value": round(n / t, 3), "unit": "atoms/s", "cores": 1, "kind": "oracle",
             "sample": f"oracle E+F ({sample_label(workload)}, 9 moments, canonical d) of a {n}-atom "
