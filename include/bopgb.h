@@ -425,7 +425,7 @@ int bop_fermi_level_noalloc(int M, int n_exp, const double* gsig, const double* 
  * (a*_inf, b*_inf) that a 17-moment run of the same orbital would give, and
  * the constant terminator then starts after level 8.  The paper has no such
  * network; its constant terminator is the fallback and the reference the
- * network is judged against.
+ * network is compared with.
  *   inputs x (BOP_MLP_NIN = 18): (a_k - a_inf)/b_inf, k = 0..3; b_k/b_inf,
  *     k = 1..4; a_inf; b_inf; mu-hat_1 .. mu-hat_8 (Eq. sigma_i normalisation);
  *     a_inf, b_inf from the 9-moment Gershgorin bounds;
