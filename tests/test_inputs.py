@@ -27,3 +27,20 @@ def test_md_workload():
     assert w.n_atoms == 2000 and w.meta["dt"] == 1.0 and w.meta["mass"] == I.MASS_FE
     assert w.meta["vel"].shape == (2000, 3)
     assert np.array_equal(w.pos, I.workload("d2000").pos)
+
+
+def test_spin_directions():
+    """Unit vectors; the spiral keeps its cone angle and turns once over one
+    period along x; the spin-spiral workload lays it over the mag2000 cell."""
+    d = I.random_directions(5000, 4)
+    assert np.allclose(np.linalg.norm(d, axis=1), 1.0)
+    assert np.all(np.abs(d.mean(axis=0)) < 0.05)
+    assert np.array_equal(d, I.random_directions(5000, 4))
+    pos = np.array([[0.0, 0, 0], [2.5, 1, 1], [5.0, 2, 0], [10.0, 0, 3]])
+    s = I.spiral_directions(pos, 10.0, np.pi / 3)
+    assert np.allclose(np.linalg.norm(s, axis=1), 1.0)
+    assert np.allclose(s[:, 2], 0.5)
+    assert np.allclose(s[0], s[3]) and np.allclose(s[2, :2], -s[0, :2]) and np.allclose(s[1, 0], 0.0)
+    w = I.workload("nc2000")
+    assert w.run.noncollinear and w.run.scf == "stoner" and not w.run.scf_response
+    assert np.array_equal(w.pos, I.workload("mag2000").pos) and w.meta["spin_dir"].shape == (2000, 3)
