@@ -14,5 +14,6 @@ from .bop import (  # noqa: F401
     bond_gradient, edge_vectors, sk_block, recursion_coefficients, gershgorin,
     normalised_moments, cheb_p, sigma_from_moments, zeta_sigma, jackson,
     chi_hat, orbital_N_U, dos_at, fermi_bisect, scalar_stage, weights,
-    evaluate,
+    evaluate, moments_nc, moments_nc_adjoint, local_moments, global_weights,
+    pauli_vector,
 )

@@ -27,6 +27,13 @@ Readings of the paper taken here (each listed in the design doc):
     drives sum_alpha (Theta~_ii - N_i) = dU_B/d delta_i to zero, with
     U_B = U_bond + sum_i J_ii q_i^2 / 2 (one species: U_prom and the
     electronegativity term sum to E^0 sum_i q_i = 0 at fixed electron count).
+  * non-collinear magnetism fixes one moment direction s_i per atom; the
+    onsite matrix is (E_up + E_dn)/2 + (E_dn - E_up)/2 s_i.sigma, the lower
+    level E_up belonging to the spin antiparallel to s_i (the convention
+    under which the paper's torque expression and its global weights hold
+    with their printed signs); the local channel moments Tr(P_nu M_n) take
+    the place of the collinear spin channels; torques t_i = dU/ds_i x s_i
+    at fixed magnitudes.
 """
 from __future__ import annotations
 

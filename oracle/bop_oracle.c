@@ -34,6 +34,13 @@
  *   orc_bond_gradient
  *                   g_e = sum_{beta gamma} Hbar_e dH_e/dd_e by complex-step
  *                   differentiation of orc_block (exact to rounding).
+ *   orc_moments_nc  non-collinear magnetism (section "Magnetism"): the 2x2
+ *                   spin moments <i alpha, a|H^n|i alpha, b> of the spinor
+ *                   Hamiltonian H_e x 1 + onsite Ebar + h.sigma, by the same
+ *                   recursion with complex 2-spinor amplitudes.
+ *   orc_moments_nc_adjoint
+ *                   its reverse sweep for sum_n Re Tr(W_n M_n): bond
+ *                   cotangents and those of every onsite matrix.
  */
 #include <complex.h>
 #include <math.h>
