@@ -260,6 +260,9 @@ int bop_get_bonds(bop_ctx* ctx, int* atoms, double* d, double* blocks, bop_strea
  *           levels (onsite0, and onsite_s on the s orbital of an sd model)
  *   mu      device [n_spin][n][norb][n_mom] output (FP64 storage; FP32
  *           arithmetic when precision = FP32)
+ * For a noncollinear model onsite holds (E_up, E_dn) of every orbital and
+ * mu the moments of the local up / down channels of the directions set by
+ * bop_set_spin_directions (BOP_ERR_STATE without them).
  * Requires a build. */
 int bop_moments(bop_ctx* ctx, const double* onsite, double* mu, bop_stream stream);
 
