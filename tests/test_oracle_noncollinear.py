@@ -171,3 +171,28 @@ def test_stoner_scf_at_fixed_directions(ob):
     assert np.max(np.abs((N[0] - N[1]).sum(axis=1) - out["m"])) < 1e-9
     assert np.max(np.abs(N.sum(axis=(0, 2)) - w.run.n_e)) < 1e-10
     assert np.min(out["m"]) > 0.5
+
+
+def test_local_channels_and_global_weights(ob):
+    """The projections and the global weights of section "Torques": for a
+    moment along +z the up channel (lower level, spin antiparallel to s) is
+    the z-down spin, and W = (w_up + w_dn)/2 + (w_dn - w_up)/2 s.sigma gives
+    Re Tr(W M) = sum_nu w_nu Tr(P_nu M) for any Hermitian M."""
+    rng = np.random.default_rng(106)
+    n, norb, nm = 7, 5, 9
+    A = rng.normal(size=(n, norb, nm, 2, 2)) + 1j * rng.normal(size=(n, norb, nm, 2, 2))
+    M = A + np.conj(np.swapaxes(A, -1, -2))
+    z = np.tile([0.0, 0.0, 1.0], (n, 1))
+    mu = ob.local_moments(M, z)
+    assert np.allclose(mu[0], M[..., 1, 1].real) and np.allclose(mu[1], M[..., 0, 0].real)
+    s = I.random_directions(n, 107)
+    w = rng.normal(size=(2, n, norb, nm))
+    W = ob.global_weights(w, s)
+    assert np.allclose(W, np.conj(np.swapaxes(W, -1, -2)))
+    lhs = np.real(np.einsum("iamab,iamba->", W, M))
+    assert np.isclose(lhs, np.sum(w * ob.local_moments(M, s)), rtol=1e-13)
+    # Tr(sigma M) against the Pauli matrices written out
+    P = [np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.diag([1.0, -1.0])]
+    v = ob.pauli_vector(M)
+    for x in range(3):
+        assert np.allclose(v[..., x], np.real(np.einsum("ab,iamba->iam", P[x], M)))
