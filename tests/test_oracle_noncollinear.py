@@ -189,10 +189,10 @@ def test_local_channels_and_global_weights(ob):
     w = rng.normal(size=(2, n, norb, nm))
     W = ob.global_weights(w, s)
     assert np.allclose(W, np.conj(np.swapaxes(W, -1, -2)))
-    lhs = np.real(np.einsum("iamab,iamba->", W, M))
+    lhs = np.real(np.einsum("iompq,iomqp->", W, M))
     assert np.isclose(lhs, np.sum(w * ob.local_moments(M, s)), rtol=1e-13)
     # Tr(sigma M) against the Pauli matrices written out
     P = [np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.diag([1.0, -1.0])]
     v = ob.pauli_vector(M)
     for x in range(3):
-        assert np.allclose(v[..., x], np.real(np.einsum("ab,iamba->iam", P[x], M)))
+        assert np.allclose(v[..., x], np.real(np.einsum("pq,iomqp->iom", P[x], M)))
