@@ -8,7 +8,8 @@ weights w_n = dU/dmu_n are taken by complex-step differentiation of the
 scalar stage, which is exact to rounding and independent of any hand-written
 chain rule.
 
-Readings of the paper taken here (each listed in the design doc):
+Readings of the paper taken here (where the text is silent, garbled or
+inconsistent):
   * n moments means mu_0 .. mu_{n-1}; n is odd, K = (n-1)/2 hops.
   * the phase is eps = +cos(phi) (band bottom at phi = pi); Eq. chi and
     Eq. Fermi-phase are only consistent with that sign.
@@ -965,9 +966,14 @@ def scf_response_weights(st: Settings, nbr: Neighbors, H, onsite, m, wU, dUE, wN
     sig = np.array([1.0, -1.0]) if S == 2 else np.array([1.0])
     nu = 2 * n if stoner else n
 
-    def ebar_of(wts):
-        """d(sum wts . mu)/dE for every orbital: [S, n, norb]."""
-        return np.stack([moments_adjoint(nbr, H, onsite[v], wts[v])[1] for v in range(S)])
+    def ebar_of(wts, atom=None):
+        """d(sum wts . mu)/dE for every orbital: [S, n, norb].  With ``atom``
+        the weights vanish outside that atom, so only its cluster is swept
+        (the other clusters would add exact zeros)."""
+        if atom is None:
+            return np.stack([moments_adjoint(nbr, H, onsite[v], wts[v])[1] for v in range(S)])
+        sel = np.array([atom], np.int32)
+        return np.stack([moments_adjoint(nbr, H, onsite[v], wts[v][atom:atom + 1], sel)[1] for v in range(S)])
 
     def project(eb):
         """Derivative with respect to u of a function whose derivative with
@@ -988,7 +994,7 @@ def scf_response_weights(st: Settings, nbr: Neighbors, H, onsite, m, wU, dUE, wN
             c[:, i] = s
         else:
             c[:, i - n] = sig
-        row = project(ebar_of(c[:, :, None, None] * wN))
+        row = project(ebar_of(c[:, :, None, None] * wN, i % n))
         if i >= n:
             row[i] -= 1.0
         J[i] = row

@@ -10,7 +10,7 @@ form but predicts, from the first 9 moments of an orbital, the next four
 levels of its chain and the band centre / width that a 17-moment run would
 give; the constant terminator then starts after level 8.
 
-Readings taken here (each listed in the design doc):
+Readings taken here (the paper describes no such network):
   * inputs x (18): (a_k - a_inf)/b_inf for k = 0..3, b_k/b_inf for k = 1..4,
     a_inf, b_inf (eV), mu-hat_1 .. mu-hat_8 (Eq. sigma_i normalisation), all
     with the 9-moment Gershgorin a_inf, b_inf;

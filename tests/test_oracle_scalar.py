@@ -125,6 +125,30 @@ def test_jackson_factors(ob):
     assert np.all(np.diff(g) < 0) and np.all(g[:-1] > 0)
 
 
+def test_jackson_factors_worked_by_hand(ob):
+    """Eq. Jackson evaluated by hand at small N = n_exp, then g_m =
+    g^J_{m+1} / g^J_1 (m = 0..N).
+    N = 2: pi/(N+1) = pi/3; g^J_1 = (2 cos(pi/3) + sin(pi/3) cot(pi/3))/3
+      = (1 + 1/2)/3 = 1/2, g^J_2 = (cos(2pi/3) + sin(2pi/3) cot(pi/3))/3
+      = (-1/2 + 1/2)/3 = 0, g^J_3 = 0 (sin(pi) = 0, N - 3 + 1 = 0):
+      g = [1, 0, 0].
+    N = 3: pi/4; g^J_1 = (3/sqrt2 + 1/sqrt2)/4 = 1/sqrt2,
+      g^J_2 = (2 cos(pi/2) + 1)/4 = 1/4, g^J_3 = (-1/sqrt2 + 1/sqrt2)/4 = 0:
+      g = [1, sqrt2/4, 0, 0].
+    N = 5: pi/6, cot(pi/6) = sqrt3; g^J_1 = (5 sqrt3/2 + sqrt3/2)/6 =
+      sqrt3/2, g^J_2 = (4/2 + 3/2)/6 = 7/12, g^J_3 = (0 + sqrt3)/6,
+      g^J_4 = (2 (-1/2) + 3/2)/6 = 1/12, g^J_5 = (-sqrt3/2 + sqrt3/2)/6 = 0:
+      g = [1, 7/(6 sqrt3), 1/3, 1/(6 sqrt3), 0, 0]."""
+    r3 = np.sqrt(3.0)
+    cases = {2: [1.0, 0.0, 0.0],
+             3: [1.0, np.sqrt(2.0) / 4.0, 0.0, 0.0],
+             5: [1.0, 7.0 / (6.0 * r3), 1.0 / 3.0, 1.0 / (6.0 * r3), 0.0, 0.0]}
+    for N, ref in cases.items():
+        g = ob.jackson(N)
+        assert g.shape == (N + 1,)
+        assert np.allclose(g, ref, atol=1e-15, rtol=1e-14), (N, g)
+
+
 @pytest.mark.parametrize("m", [0, 1, 2, 5, 12])
 def test_chi_hat_is_integral_of_dos_basis(ob, m):
     """chi_{m+1}(phi_F) = int_{-1}^{eps_F} (2/pi) sqrt(1-eps^2) U_m(eps) d eps
