@@ -229,7 +229,8 @@ const char* bop_last_error(const bop_ctx* ctx);
  *   cell_host host [3][3], rows = lattice vectors (right-handed or not)
  *   pbc_host  host [3], 1 = periodic along that lattice vector
  * Copies pos into the context.  Synchronises stream (reads back sizes).
- * Errors: BOP_ERR_ARG (atom outside the cell, singular cell),
+ * Errors: BOP_ERR_ARG (atom outside the cell, a NaN or Inf coordinate,
+ * singular cell),
  * BOP_ERR_OVERFLOW (> 64 neighbours of an atom, image index beyond
  * +-127, cluster scratch exhausted after retries). */
 int bop_build_hamiltonian(bop_ctx* ctx, int n, const double* pos, const double* cell_host,
@@ -329,6 +330,17 @@ int bop_set_spin_directions(bop_ctx* ctx, const double* s, bop_stream stream);
  * preceding bop_forces. */
 int bop_torques(bop_ctx* ctx, double* t, bop_stream stream);
 
+/* Limits of the SCF-response solve of bop_forces (GMRES, described there):
+ * max_iterations caps its Arnoldi iterations (0 = the default, 3 cycles of
+ * 40), rtol its relative residual (0 = the default of the precision).  A
+ * solve that stops at the cap above rtol makes bop_forces return
+ * BOP_ERR_NO_CONVERGENCE with forces and virial from the last iterate and
+ * the residual in bop_stats.response_residual.  The paper's SCF loop has a
+ * "maximum number of steps" too ("Program flow", self-consistency); this is
+ * the same guard for the linear solve of the exact forces.
+ * Errors: BOP_ERR_ARG for max_iterations < 0 or rtol < 0 or not finite. */
+int bop_set_response_limits(bop_ctx* ctx, int max_iterations, double rtol);
+
 /* Memory for the reverse sweeps of bop_forces.  When several reverse sweeps
  * follow (an SCF with scf_response = 1) and all starting orbitals of an atom
  * share one work item of the moments kernel, bop_forces runs one extra
@@ -398,23 +410,27 @@ int bop_get_profile(bop_ctx* ctx, bop_kernel_time* out_host, int max, int* n_out
  * advance, because their host framework pre-reserves all GPU memory at
  * start-up (a new allocation would fail or bypass its accounting), or
  * because an allocation would synchronise the device at a point they do not
- * control.  It runs the library's bisection kernels (the same root as the
- * Newton-accelerated search of bop_energy, within 1e-13 eV) with their
- * scratch in a 16 MiB file-scope __device__ array that every GPU loading the
- * library keeps until the process exits.
+ * control.  It runs the library's bisection kernels (100 halvings or a
+ * bracket narrower than 1e-13 eV; the root of the Newton-accelerated search
+ * of bop_energy, which stops on its own rule: the two agree to 1e-9 eV in
+ * the tests) with their scratch in a 16 MiB file-scope __device__ array
+ * that every GPU loading the library keeps until the process exits.
  *   M            orbitals (all spins)
  *   n_exp        expansion length of gsig (2 .. 253)
  *   gsig         device [n_exp+1][M]: g_m sigma_m, as written by bop_recursion
  *   a_inf, b_inf device [M]: terminator of every orbital (bop_recursion)
  *   spin_factor  2 for non-magnetic orbitals, 1 per collinear spin channel
- *   n_electrons  total electron count the Fermi level must hold
+ *   n_electrons  total electron count the Fermi level must hold, in
+ *                (0, spin_factor M); outside it BOP_ERR_BRACKET (no launch)
  *   e_fermi      device [1] output
  * Caller-owned inputs and output; nothing is allocated.  The scratch needs
  * 16896 + 8 (n_exp + 3) M bytes: larger problems (more than 10,300 orbitals
  * at n_exp = 200) are rejected with BOP_ERR_OVERFLOW and a message on
  * stderr, before anything is launched.  The first call on a device looks up
  * the array's device address (once per device), so make that first call
- * before any stream capture.  All calls share the one array, which keeps
+ * before any stream capture; the address is kept for the life of the
+ * process and does not survive a cudaDeviceReset, after which this entry
+ * point is not supported.  All calls share the one array, which keeps
  * the last call's contents: calls that overlap on the GPU (other streams,
  * other host threads) race and must be serialised by the caller. */
 int bop_fermi_level_noalloc(int M, int n_exp, const double* gsig, const double* a_inf, const double* b_inf,

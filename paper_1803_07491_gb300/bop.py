@@ -117,6 +117,7 @@ def lib(path: str | None = None):
         "bop_mlp_predict": ([_VP, ctypes.c_longlong, _VP, _VP, _VP], ctypes.c_int),
         "bop_set_mlp": ([_VP, _VP], ctypes.c_int),
         "bop_set_store_budget": ([_VP, ctypes.c_longlong], ctypes.c_int),
+        "bop_set_response_limits": ([_VP, ctypes.c_int, ctypes.c_double], ctypes.c_int),
         "bop_set_spin_directions": ([_VP, _VP, _VP], ctypes.c_int),
         "bop_torques": ([_VP, _VP, _VP], ctypes.c_int),
         "bop_md_verlet": ([ctypes.c_int, _VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -279,12 +280,15 @@ def bop_torques(ctx, n: int, stream=None):
     return t
 
 
-def bop_forces_stats(ctx, n: int, stream=None):
-    """bop_forces plus its statistics (SCF-response solve)."""
+def bop_forces_stats(ctx, n: int, stream=None, allow_noconv=False):
+    """bop_forces plus its statistics (SCF-response solve).  allow_noconv:
+    a response solve stopped at its limit returns the forces of its last
+    iterate instead of raising."""
     F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     W = torch.empty((3, 3), dtype=torch.float64, device="cuda")
     s = bop_stats()
-    _check(ctx, lib().bop_forces(ctx, _ptr(F), _ptr(W), ctypes.byref(s), _stream(stream)))
+    _check(ctx, lib().bop_forces(ctx, _ptr(F), _ptr(W), ctypes.byref(s), _stream(stream)),
+           allow=(BOP_ERR_NO_CONVERGENCE,) if allow_noconv else ())
     return F, W, s.as_dict()
 
 
@@ -422,6 +426,10 @@ def bop_mlp_predict(net, x: torch.Tensor, stream=None) -> torch.Tensor:
     y = torch.empty((x.shape[0], MLP_NOUT), dtype=torch.float32, device=x.device)
     _mcheck(net, lib().bop_mlp_predict(net, x.shape[0], _ptr(x), _ptr(y), _stream(stream)))
     return y
+
+
+def bop_set_response_limits(ctx, max_iterations: int = 0, rtol: float = 0.0):
+    _check(ctx, lib().bop_set_response_limits(ctx, int(max_iterations), float(rtol)))
 
 
 def bop_set_store_budget(ctx, nbytes: int):

@@ -95,6 +95,8 @@ struct bop_ctx {
   long long psi_tot = 0;
   bool psi_valid = false;
   size_t store_budget = (size_t)-1;
+  int resp_max_it = 0;     // cap of the SCF-response solve's iterations (0: GM_KRYLOV x GM_CYCLES)
+  double resp_rtol = 0.0;  // its relative tolerance (0: the precision's default)
   DBuf status;
   DBuf cub_tmp;
   DBuf nprod;
@@ -222,7 +224,7 @@ int validate_model(bop_ctx* c, const bop_model* m) {
   if (m->scf == BOP_SCF_STONER && m->n_spin != 2) return fail(c, BOP_ERR_ARG, "STONER needs n_spin = 2");
   if (m->n_spin == 2 && m->scf != BOP_SCF_STONER && m->scf != BOP_SCF_NONE)
     return fail(c, BOP_ERR_ARG, "n_spin = 2 needs scf STONER or NONE");
-  if (m->n_e < 0 || m->n_e > 2.0 * m->norb) return fail(c, BOP_ERR_ARG, "n_e must be in [0, 2 norb]");
+  if (!(m->n_e >= 0 && m->n_e <= 2.0 * m->norb)) return fail(c, BOP_ERR_ARG, "n_e must be in [0, 2 norb]");
   if (m->precision != BOP_PREC_FP64 && m->precision != BOP_PREC_FP32)
     return fail(c, BOP_ERR_ARG, "precision must be FP64 or FP32");
   if (m->scf != BOP_SCF_NONE && (m->scf_max_it < 0 || !(m->scf_tol > 0)))
@@ -806,7 +808,9 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
   const bool stoner = c->m.scf == BOP_SCF_STONER;
   const int nu = stoner ? 2 * n : n;
   const double I = c->m.stoner_I;
-  const double rtol = c->fp64 ? 1e-10 : 1e-4;  // FP32 products: at the SCF tolerance's level
+  // FP32 products: at the SCF tolerance's level
+  const double rtol = c->resp_rtol > 0.0 ? c->resp_rtol : (c->fp64 ? 1e-10 : 1e-4);
+  const int max_it = c->resp_max_it > 0 ? c->resp_max_it : GM_KRYLOV * GM_CYCLES;
   CKS(ensure(c, c->rwN, sizeof(double) * (size_t)M * nm));
   CKS(ensure(c, c->rwt, sizeof(double) * (size_t)M * nm));
   CKS(ensure(c, c->rdUE, sizeof(double) * (size_t)M));
@@ -913,7 +917,7 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
   double rel = 0.0;
   bool conv = bnorm == 0.0;
   const double one = 1.0, minus_one = -1.0;
-  for (int cyc = 0; cyc < GM_CYCLES && !conv; cyc++) {
+  for (int cyc = 0; cyc < GM_CYCLES && !conv && iters < max_it; cyc++) {
     // residual r = g - J^T y into V_0
     CK(cudaMemcpyAsync(V, rhs, sizeof(double) * nu, cudaMemcpyDeviceToDevice, s));
     if (cyc > 0) {
@@ -971,7 +975,7 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
       k = j + 1;
       iters++;
       rel = std::fabs(gv[j + 1]) / bnorm;
-      if (rel <= rtol || hn == 0.0) break;
+      if (rel <= rtol || hn == 0.0 || iters >= max_it) break;
     }
     // z = H^-1 g (upper triangular), y += P sum z_q V_q
     double z[GM_KRYLOV];
@@ -1170,6 +1174,8 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
       mn = fmin(mn, fr[6 * q + a]);
       mx = fmax(mx, fr[6 * q + 3 + a]);
     }
+    if (std::isinf(mn) || std::isinf(mx))
+      return fail(c, BOP_ERR_ARG, "non-finite atom positions (NaN or Inf)");
     if (mn < -1e-9 || mx >= 1.0 + 1e-9)
       return fail(c, BOP_ERR_ARG, "atoms outside the cell along axis %d (fractional range [%g, %g])", a, mn, mx);
   }
@@ -1667,6 +1673,15 @@ int bop_evaluate_host(bop_ctx* c, int n, const double* pos_host, const double* c
   for (DBuf* q : {&dpos, &dF, &dW})
     if (q->p) cudaFree(q->p);
   return r;
+}
+
+int bop_set_response_limits(bop_ctx* c, int max_iterations, double rtol) {
+  if (!c) return BOP_ERR_ARG;
+  if (max_iterations < 0 || !(rtol >= 0.0) || !std::isfinite(rtol))
+    return fail(c, BOP_ERR_ARG, "response limits: max_iterations >= 0 and a finite rtol >= 0");
+  c->resp_max_it = max_iterations;
+  c->resp_rtol = rtol;
+  return BOP_OK;
 }
 
 int bop_set_store_budget(bop_ctx* c, long long bytes) {

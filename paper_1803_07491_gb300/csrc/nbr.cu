@@ -240,13 +240,18 @@ __global__ void k_bond_blocks(int nb, const double* __restrict__ pos, Geometry g
 }
 
 // Largest / smallest fractional coordinate along each axis (validation that
-// all atoms lie inside the cell).
+// all atoms lie inside the cell; a non-finite coordinate makes the range
+// infinite, which fmin / fmax alone would skip).
 __global__ void k_frac_range(int n, const double* __restrict__ pos, Geometry g, double* __restrict__ out) {
   __shared__ double smin[3][256], smax[3][256];
   double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     for (int a = 0; a < 3; a++) {
       double f = pos[3 * i] * g.inv[a] + pos[3 * i + 1] * g.inv[3 + a] + pos[3 * i + 2] * g.inv[6 + a];
+      if (!isfinite(f)) {  // a NaN / Inf position: both ends of the range become infinite
+        mn[a] = -INFINITY;
+        mx[a] = INFINITY;
+      }
       mn[a] = fmin(mn[a], f);
       mx[a] = fmax(mx[a], f);
     }

@@ -40,7 +40,9 @@ std::mutex g_mutex;
 unsigned char* g_addr[MAX_DEVICES] = {nullptr};
 
 // Device address of the scratch on the current device, looked up once per
-// device (with that device current).
+// device (with that device current) and kept for the life of the process:
+// it does not survive a cudaDeviceReset (or any other reset of the primary
+// context), after which calls of this entry point are not supported.
 int scratch_address(unsigned char** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return BOP_ERR_CUDA;
@@ -86,6 +88,13 @@ extern "C" int bop_fermi_level_noalloc(int M, int n_exp, const double* gsig, con
     fprintf(stderr, "bop_fermi_level_noalloc: invalid argument (need M >= 1, 2 <= n_exp <= %d, pointers)\n",
             BOP_MAX_NEXP);
     return BOP_ERR_ARG;
+  }
+  // a count outside (0, s M) has no Fermi level inside the band: the search
+  // would end at a bracket edge with a meaningless E_F
+  if (!(n_electrons > 0.0 && n_electrons < spin_factor * (double)M)) {
+    fprintf(stderr, "bop_fermi_level_noalloc: n_electrons = %g outside (0, %g) (spin_factor x M)\n", n_electrons,
+            spin_factor * (double)M);
+    return BOP_ERR_BRACKET;
   }
   const size_t need = OFF_D + (size_t)(n_exp + 3) * (size_t)M * sizeof(double);
   if (need > NOALLOC_BYTES) {

@@ -7,7 +7,8 @@ bop_fermi_level_noalloc runs the library's Fermi-level search with its
 scratch in a static device array.  This test checks, through the C ABI, that
 two calls in a row give the Fermi level that bop_energy found for the same
 orbitals, within the 1e-9 eV used by the other Fermi-level tests, and that a
-problem too large for the static array is refused.
+problem too large for the static array, or an electron count no Fermi level
+inside the band can hold, is refused.
 """
 import numpy as np
 import pytest
@@ -42,4 +43,14 @@ def test_fermi_level_noalloc_matches_bop_energy():
     zeros = torch.zeros(20000, dtype=torch.float64, device="cuda")
     status = bop.bop_fermi_level_noalloc(big, zeros, zeros + 1.0, 2.0, 1.0, out)
     assert status == bop.BOP_ERR_OVERFLOW
+    # an electron count that no Fermi level inside the band holds: refused
+    # before any launch instead of ending at a bracket edge
+    for n_el in (0.0, -1.0, 2.0 * M, 2.0 * M + 5.0, float("nan")):
+        status = bop.bop_fermi_level_noalloc(gsig_cm, a_inf, b_inf, 2.0, n_el, out)
+        assert status == bop.BOP_ERR_BRACKET
+    # the entry point still works after the refusals
+    out.fill_(np.nan)
+    status = bop.bop_fermi_level_noalloc(gsig_cm, a_inf, b_inf, 2.0, w.run.n_e * w.n_atoms, out)
+    torch.cuda.synchronize()
+    assert status == bop.BOP_OK and abs(float(out.item()) - res.e_fermi) < 1e-9
     ctx.close()
