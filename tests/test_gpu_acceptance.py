@@ -1,0 +1,107 @@
+"""Element-by-element checks of the self-consistent 2,000-atom workloads
+against the FP64 oracle's stored run of the same cells
+(tests/golden/make_golden_2000.py, which calls only the oracle):
+
+  d2000    canonical d, local charge neutrality (Eq. BOP_LCN), the
+           2,000-atom cell of the bench;
+  mag2000  canonical d, collinear Stoner magnetism (section "Magnetism",
+           Eqs. onsite_NCM and TB-UX) from a ferromagnetic start.
+
+Both precisions of the library run with the SCF tolerance the bench uses
+for them (FP64: 1e-9 electrons, FP32 products: 3e-5).  Every atom's energy,
+every force component (with the response of the self-consistent onsite
+levels, the exact gradient, and without it, the Hellmann-Feynman form of
+Eq. F_k), every magnetic moment and onsite shift, the Fermi level and the
+virial are compared with the oracle's.  Tolerances (FP64 / FP32 products):
+energies 1e-6 / 1e-3 eV per atom (the bounds of the FP64 and FP32 modes),
+forces 1e-6 / 2e-3 eV/A, moments 1e-7 / 1e-3 mu_B, shifts 1e-7 / 1e-3 eV,
+E_F 1e-8 / 1e-4 eV.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1803_07491_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+FP32_SCF_TOL = 3e-5
+
+TOL = {  # (energy eV/atom, force eV/A, moment mu_B, shift eV, E_F eV)
+    "fp64": dict(e=1e-6, f=1e-6, m=1e-7, d=1e-7, ef=1e-8),
+    "fp32": dict(e=1e-3, f=2e-3, m=1e-3, d=1e-3, ef=1e-4),
+}
+
+
+@pytest.fixture(scope="module")
+def bop():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_07491_gb300 import build, bop as b
+    build.build()
+    return b
+
+
+def _golden(name):
+    path = os.path.join(HERE, "golden", f"{name}_oracle.npz")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not written (tests/golden/make_golden_2000.py)")
+    return dict(np.load(path))
+
+
+def _run(bop, w, prec, response):
+    w = I.with_run(w, scf_response=response)
+    ctx = bop.Context(w.model, w.run, prec)
+    ctx.build(w.pos, w.cell, w.pbc)
+    n = w.n_atoms
+    delta = torch.zeros(n, dtype=torch.float64, device="cuda")
+    m = torch.full((n,), w.run.m0, dtype=torch.float64, device="cuda") if w.run.n_spin == 2 else None
+    e, st = ctx.energy(delta=delta, m=m)
+    F, W, fs = bop.bop_forces_stats(ctx.h, n)
+    ctx.close()
+    assert st["scf_converged"] == 1
+    if response:
+        assert fs["response_converged"] == 1 and fs["forces_scf_response"] == 1
+    out = dict(e_atom=e.cpu().numpy(), delta=delta.cpu().numpy(), forces=F.cpu().numpy(),
+               virial=W.cpu().numpy(), e_fermi=st["e_fermi"])
+    if m is not None:
+        out["m"] = m.cpu().numpy()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["d2000", "mag2000"])
+def test_scf_workload_against_oracle(bop, name, prec):
+    ref = _golden(name)
+    w = I.workload(name)
+    if prec == "fp32":
+        w = I.with_run(w, scf_tol=FP32_SCF_TOL)
+    tol = TOL[prec]
+    got = _run(bop, w, prec, True)
+    err = {
+        "energy": np.max(np.abs(got["e_atom"] - ref["e_atom"])),
+        "forces": np.max(np.abs(got["forces"] - ref["forces"])),
+        "shift": np.max(np.abs(got["delta"] - ref["delta"])),
+        "e_fermi": abs(got["e_fermi"] - float(ref["e_fermi"])),
+        "virial": np.max(np.abs(got["virial"] - ref["virial"])),
+    }
+    if "m" in ref:
+        err["moment"] = np.max(np.abs(got["m"] - ref["m"]))
+    hf = _run(bop, w, prec, False)
+    err["forces_hf"] = np.max(np.abs(hf["forces"] - ref["forces_hf"]))
+    err["energy_hf_run"] = np.max(np.abs(hf["e_atom"] - ref["e_atom"]))
+    print(f"\n{name} {prec}: " + ", ".join(f"{k} {v:.3e}" for k, v in err.items()))
+    assert err["energy"] < tol["e"] and err["energy_hf_run"] < tol["e"]
+    assert err["forces"] < tol["f"] and err["forces_hf"] < tol["f"]
+    assert err["shift"] < tol["d"]
+    assert err["e_fermi"] < tol["ef"]
+    # the virial is extensive (a sum over 14,000 bonds)
+    assert err["virial"] < tol["f"] * w.n_atoms ** 0.5 * 3.0
+    if "moment" in err:
+        assert err["moment"] < tol["m"]
+    # the response changes the forces by more than the tolerance: the check
+    # tells the two forms apart
+    assert np.max(np.abs(ref["forces"] - ref["forces_hf"])) > 10 * TOL["fp64"]["f"]
