@@ -298,8 +298,8 @@ int bop_energy(bop_ctx* ctx, double* e_atom, double* delta_io, double* m_io, bop
  * J = dR/du, the multipliers y of J^T y = dE/du (GMRES, right-preconditioned
  * by the inverse local DOS, each product J^T v one reverse sweep of the
  * moments) give dE/dx = dE/dx|_u - y . dR/dx|_u; stats report its
- * iterations and residual (relative tolerance 1e-10 in FP64 mode, 1e-4
- * with FP32 products).  BOP_ERR_NO_CONVERGENCE if it stops at 120
+ * iterations and residual (relative tolerance 1e-10 in FP64 mode, 1e-6
+ * with FP32 products, where the forces reach the FP32 noise floor).  BOP_ERR_NO_CONVERGENCE if it stops at 120
  * iterations above tolerance (outputs then use the last iterate).
  *   forces device [n][3], virial device [3][3] (row-major), either may be NULL.
  * Errors: BOP_ERR_STATE without a preceding bop_energy. */

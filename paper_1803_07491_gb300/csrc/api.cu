@@ -92,6 +92,8 @@ struct bop_ctx {
   int sdir_n = -1;
   // stored Psi of every work item for the reverse sweeps (when it fits)
   DBuf psi_off, psis, psib, lsum;
+  DBuf cw_misc, cw_keys, cw_epack;  // warp cluster builder: max degree / failure flags, site keys per
+                                    // atom, packed neighbour edges
   long long psi_tot = 0;
   bool psi_valid = false;
   size_t store_budget = (size_t)-1;
@@ -300,8 +302,99 @@ int geometry(bop_ctx* c, const double* cell, const int* pbc, Geometry* g) {
   return BOP_OK;
 }
 
+// Warp-per-atom builder (clusters of at most cluster_warp_max_sites()
+// sites, atoms of at most 32 neighbours); *done = false when it does not
+// apply, and the block builder below runs instead.
+int build_clusters_warp(bop_ctx* c, cudaStream_t s, bool* done) {
+  *done = false;
+  const int n = c->n, K = c->K;
+  if (n == 0 || (c->cl_maxs && c->cl_maxs > cluster_warp_max_sites())) return BOP_OK;
+  if (K > 5 && !(c->m.r_path > 0)) return BOP_OK;  // bcc has 1,105 sites within 6 hops
+  CKS(ensure(c, c->cw_misc, 4 * sizeof(int)));
+  CK(cudaMemsetAsync(c->cw_misc.p, 0, 4 * sizeof(int), s));
+  launch_max_degree(n, P<long long>(c->row_ptr), P<int>(c->cw_misc), s);
+  int misc[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(misc, c->cw_misc.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int max_deg = misc[0];
+  if (max_deg > 32) return BOP_OK;
+  int* wfail = P<int>(c->cw_misc) + 1;
+  CKS(ensure(c, c->level_end, sizeof(int) * (size_t)n * (K + 1)));
+  CKS(ensure(c, c->atom_nsite, sizeof(int) * (n + 1)));
+  CKS(ensure(c, c->atom_nadj, sizeof(int) * (n + 1)));
+  CK(cudaMemsetAsync(c->atom_nsite.p, 0, sizeof(int) * (n + 1), s));
+  CK(cudaMemsetAsync(c->atom_nadj.p, 0, sizeof(int) * (n + 1), s));
+  CKS(ensure(c, c->max_level, sizeof(int) * (K + 2)));
+  CKS(ensure(c, c->site_off, sizeof(long long) * (n + 1)));
+  CKS(ensure(c, c->adj_base, sizeof(long long) * (n + 1)));
+  CKS(ensure(c, c->cw_keys, sizeof(unsigned long long) * (size_t)n * cluster_warp_max_sites()));
+  CKS(ensure(c, c->cw_epack, sizeof(int2) * (size_t)(c->E > 0 ? c->E : 1)));
+  launch_pack_edges(c->E, P<int>(c->col), P<signed char>(c->img), P<int2>(c->cw_epack), s);
+  CK(cudaMemsetAsync(c->max_level.p, 0, sizeof(int) * (K + 2), s));
+  PathCut pc;
+  pc.pos = P<double>(c->pos);
+  for (int q = 0; q < 9; q++) pc.cell[q] = c->g.cell[q];
+  pc.r2 = c->m.r_path > 0 ? c->m.r_path * c->m.r_path : 0.0;
+  ClusterOut out{};
+  out.level_end = P<int>(c->level_end);
+  out.atom_nsite = P<int>(c->atom_nsite);
+  out.atom_nadj = P<int>(c->atom_nadj);
+  out.max_level = P<int>(c->max_level);
+  {
+    Region R0(c, PK_CLUSTER, 1, s);
+    if (launch_cluster_warp(0, n, K, max_deg, P<long long>(c->row_ptr), P<int2>(c->cw_epack),
+                            P<int>(c->bond_of_edge), pc, P<unsigned long long>(c->cw_keys), out, wfail,
+                            P<unsigned>(c->status), s))
+      return fail(c, BOP_ERR_CUDA, "cluster pass 0 launch failed");
+  }
+  CK(cudaMemcpyAsync(misc, c->cw_misc.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKS(check_status(c, s));  // synchronises
+  if (misc[1] != 0) return BOP_OK;  // too large for the warp builder
+  CKS(exclusive_scan(c, P<int>(c->atom_nsite), P<long long>(c->site_off), n + 1, s));
+  CKS(exclusive_scan(c, P<int>(c->atom_nadj), P<long long>(c->adj_base), n + 1, s));
+  long long tot[2];
+  CK(cudaMemcpyAsync(&tot[0], P<long long>(c->site_off) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&tot[1], P<long long>(c->adj_base) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->maxlev, c->max_level.p, sizeof(int) * (K + 2), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  c->nsite = tot[0];
+  c->nadj = tot[1];
+  CKS(ensure(c, c->site_atom, sizeof(int) * c->nsite));
+  CKS(ensure(c, c->site_img, 3 * c->nsite));
+  CKS(ensure(c, c->adj_off, sizeof(long long) * (c->nsite + 1)));
+  CKS(ensure(c, c->adj, sizeof(int2) * c->nadj));
+  CKS(ensure(c, c->lvcnt, sizeof(unsigned long long) * c->nsite));
+  out.site_off = P<long long>(c->site_off);
+  out.adj_base = P<long long>(c->adj_base);
+  out.site_atom = P<int>(c->site_atom);
+  out.site_img = P<signed char>(c->site_img);
+  out.adj_off = P<long long>(c->adj_off);
+  out.adj = P<int2>(c->adj);
+  out.lvcnt = P<unsigned long long>(c->lvcnt);
+  CKS(ensure(c, c->nprod, sizeof(unsigned long long)));
+  CK(cudaMemsetAsync(c->nprod.p, 0, sizeof(unsigned long long), s));
+  out.n_products = P<unsigned long long>(c->nprod);
+  {
+    Region R1(c, PK_CLUSTER, 1, s);
+    if (launch_cluster_warp(1, n, K, max_deg, P<long long>(c->row_ptr), P<int2>(c->cw_epack),
+                            P<int>(c->bond_of_edge), pc, P<unsigned long long>(c->cw_keys), out, wfail,
+                            P<unsigned>(c->status), s))
+      return fail(c, BOP_ERR_CUDA, "cluster pass 1 launch failed");
+  }
+  CK(cudaMemcpyAsync(P<long long>(c->adj_off) + c->nsite, P<long long>(c->adj_base) + n, sizeof(long long),
+                     cudaMemcpyDeviceToDevice, s));
+  CKS(check_status(c, s));
+  *done = true;
+  return BOP_OK;
+}
+
 int build_clusters(bop_ctx* c, cudaStream_t s) {
   const int n = c->n, K = c->K;
+  {
+    bool done = false;
+    CKS(build_clusters_warp(c, s, &done));
+    if (done) return BOP_OK;
+  }
   int grid = n < 1216 ? n : 1216;
   int maxs = c->cl_maxs ? c->cl_maxs : (K <= 4 ? 1024 : (K <= 6 ? 2048 : 4096));
   CKS(ensure(c, c->level_end, sizeof(int) * (size_t)n * (K + 1)));
@@ -733,7 +826,7 @@ int prepare_psi_store(bop_ctx* c, cudaStream_t s) {
 
 // One reverse sweep of the moments with weights w: Hbar += dL/dH (if not
 // NULL), Ebar += dL/dE (if not NULL).  Over the stored Psi when present.
-int adjoint_pass(bop_ctx* c, const double* w, double* Hbar, double* Ebar, cudaStream_t s,
+int adjoint_pass(bop_ctx* c, const double* w, void* Hbar, double* Ebar, cudaStream_t s,
                  double* siteval = nullptr) {
   const int n = c->n;
   AdjointArgs aa;
@@ -748,7 +841,7 @@ int adjoint_pass(bop_ctx* c, const double* w, double* Hbar, double* Ebar, cudaSt
   aa.n_mom = c->n_mom;
   aa.w = w;
   aa.Hbar = Hbar;
-  aa.HSu = c->HSu;
+  aa.HSh = bond_cotangent_stride(c->norb, c->fp64);
   aa.Ebar = Ebar;
   if (c->psi_valid) {
     aa.pstore = c->psis.p;
@@ -808,8 +901,10 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
   const bool stoner = c->m.scf == BOP_SCF_STONER;
   const int nu = stoner ? 2 * n : n;
   const double I = c->m.stoner_I;
-  // FP32 products: at the SCF tolerance's level
-  const double rtol = c->resp_rtol > 0.0 ? c->resp_rtol : (c->fp64 ? 1e-10 : 1e-4);
+  // FP32 products: 1e-6 reaches the FP32 noise floor of the forces (measured
+  // on the 2,000-atom LCN / Stoner cells against the FP64 oracle: 1e-5 /
+  // 9e-5 eV/A, against 1e-3 / 6e-3 at 1e-4) for a few more iterations
+  const double rtol = c->resp_rtol > 0.0 ? c->resp_rtol : (c->fp64 ? 1e-10 : 1e-6);
   const int max_it = c->resp_max_it > 0 ? c->resp_max_it : GM_KRYLOV * GM_CYCLES;
   CKS(ensure(c, c->rwN, sizeof(double) * (size_t)M * nm));
   CKS(ensure(c, c->rwt, sizeof(double) * (size_t)M * nm));
@@ -996,7 +1091,7 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
   // final weights w = wU - c wN, then Hbar
   if (launch_scale_weights(n, norb, S, nm, c->sfac, stoner ? 1 : 0, y, -1.0, wN, wU, wU, s))
     return fail(c, BOP_ERR_CUDA, "response kernels failed");
-  CKS(adjoint_pass(c, wU, P<double>(c->Hbar), nullptr, s));
+  CKS(adjoint_pass(c, wU, c->Hbar.p, nullptr, s));
   return conv ? BOP_OK : BOP_ERR_NO_CONVERGENCE;
 }
 
@@ -1111,7 +1206,7 @@ int bop_destroy(bop_ctx* c) {
                   &c->lys, &c->lZ1, &c->lH1, &c->lZ2, &c->lH2, &c->lybar, &c->lcot, &c->lxbar, &c->lcount,
                   &c->rwN, &c->rwt, &c->rdUE, &c->rvec, &c->rcoef, &c->rjv, &c->rjcnt, &c->rjptr, &c->rjidx, &c->rjrow, &c->vgrad, &c->vq, &c->erep,
                   &c->psi_off, &c->psis, &c->psib, &c->lsum, &c->sdir, &c->vmom, &c->obar, &c->torque,
-                  &c->ncscr};
+                  &c->ncscr, &c->cw_misc, &c->cw_keys, &c->cw_epack};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -1506,9 +1601,12 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   const int n = c->n, M = c->S * n * c->norb;
   CKS(ensure(c, c->w, sizeof(double) * (size_t)M * c->n_mom));
   CKS(ensure(c, c->zscr, sizeof(double) * (size_t)M * (c->n_exp + 1) * 2));
-  CKS(ensure(c, c->Hbar, sizeof(double) * (size_t)(c->nb > 0 ? c->nb : 1) * c->HSu));
+  // bond cotangents in the product type (FP32: float4 reductions)
+  const size_t hbar_bytes = (c->fp64 ? sizeof(double) : sizeof(float)) * (size_t)(c->nb > 0 ? c->nb : 1) *
+                            bond_cotangent_stride(c->norb, c->fp64);
+  CKS(ensure(c, c->Hbar, hbar_bytes));
   CKS(ensure(c, c->Ebar, sizeof(double) * (size_t)M));
-  CK(cudaMemsetAsync(c->Hbar.p, 0, sizeof(double) * (size_t)(c->nb > 0 ? c->nb : 1) * c->HSu, s));
+  CK(cudaMemsetAsync(c->Hbar.p, 0, hbar_bytes, s));
   CKS(prepare_psi_store(c, s));
   int solve_status = BOP_OK;
   c->st.response_iterations = 0;
@@ -1518,7 +1616,7 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
     // U_B is stationary in the shifts: its weights at fixed shifts give the
     // exact derivative (no response solve)
     if (!c->var_w_valid) CKS(var_weights(c, s));
-    CKS(adjoint_pass(c, P<double>(c->w), P<double>(c->Hbar), nullptr, s));
+    CKS(adjoint_pass(c, P<double>(c->w), c->Hbar.p, nullptr, s));
   } else if (c->m.scf != BOP_SCF_NONE && c->m.scf_response) {
     solve_status = scf_response(c, s);
     if (solve_status != BOP_OK && solve_status != BOP_ERR_NO_CONVERGENCE) return solve_status;
@@ -1541,8 +1639,8 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
       CKS(ensure(c, c->torque, sizeof(double) * 3 * (size_t)n));
       CK(cudaMemsetAsync(c->obar.p, 0, sizeof(double) * (size_t)n * c->norb * 4, s));
       a.w = P<double>(c->w);
-      a.Hbar = P<double>(c->Hbar);
-      a.HSu = c->HSu;
+      a.Hbar = c->Hbar.p;
+      a.HSh = bond_cotangent_stride(c->norb, c->fp64);
       a.obar = P<double>(c->obar);
       {
         Region R(c, PK_ADJOINT, 1, s);
@@ -1554,7 +1652,7 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
         return fail(c, BOP_ERR_CUDA, "torques launch failed");
     } else {
       CK(cudaMemsetAsync(c->Ebar.p, 0, sizeof(double) * (size_t)M, s));
-      CKS(adjoint_pass(c, P<double>(c->w), P<double>(c->Hbar), P<double>(c->Ebar), s));
+      CKS(adjoint_pass(c, P<double>(c->w), c->Hbar.p, P<double>(c->Ebar), s));
     }
   }
   DBuf* fb = nullptr;
@@ -1575,7 +1673,7 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
   {
     Region Rf(c, PK_FORCES, c->nb > 0 ? 1 : 0, s);
     if (c->nb > 0 && launch_forces((int)c->nb, c->bm, P<double>(c->bond_d), P<int>(c->bond_atoms),
-                                   P<double>(c->Hbar), c->HSu, F, W, s))
+                                   c->Hbar.p, bond_cotangent_stride(c->norb, c->fp64), c->fp64, F, W, s))
       return fail(c, BOP_ERR_CUDA, "forces launch failed");
   }
   int r = check_status(c, s);

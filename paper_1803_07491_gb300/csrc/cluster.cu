@@ -303,6 +303,292 @@ k_cluster(int n, int K, const long long* __restrict__ row_ptr, const int* __rest
   }
 }
 
+// ---------------------------------------------------------------- warp builder
+// The same clusters (same canonical order, same adjacency and level counts)
+// with one warp per atom: a cluster of a few hundred sites has levels of
+// 1, 14, 50, 110, ... new sites, which a warp covers without block-wide
+// barriers, and every hash probe stays in shared memory.  Pass 0 runs the
+// breadth-first search, counts the adjacency and keeps each atom's site
+// keys in global scratch; pass 1 reloads them, fills the hash table and
+// writes the sites, the sorted adjacency and the level counts.  Clusters of
+// more than CW_MAXS sites, or atoms with more than MAXD neighbours, raise
+// *wfail and the caller falls back to the block builder above.
+constexpr int CW_WARPS = 4;   // warps per CTA
+constexpr int CW_MAXS = 512;  // sites of one cluster
+constexpr int CW_HC = 1024;   // hash slots per warp (a power of two, 2 CW_MAXS)
+
+struct CwSmem {
+  unsigned long long hk[CW_HC];
+  unsigned long long sk[CW_MAXS];  // site keys in canonical order
+  unsigned long long nb[CW_MAXS];  // new keys of one level
+  unsigned short hv[CW_HC];        // local index of every stored key
+  int lev[BOP_MAX_K + 1];
+  int cnt, fail;
+};
+
+__device__ __forceinline__ int cw_find(const unsigned long long* hk, unsigned long long key) {
+  unsigned s = hash_slot(key, CW_HC - 1);
+  for (int probe = 0; probe < CW_HC; probe++) {
+    const unsigned long long c = hk[s];
+    if (c == key) return (int)s;
+    if (c == EMPTY) return -1;
+    s = (s + 1) & (CW_HC - 1);
+  }
+  return -1;
+}
+
+// 1: inserted, 0: present, -1: full.  slot receives the key's slot.
+__device__ __forceinline__ int cw_insert(unsigned long long* hk, unsigned long long key, int* slot) {
+  unsigned s = hash_slot(key, CW_HC - 1);
+  for (int probe = 0; probe < CW_HC; probe++) {
+    const unsigned long long c = hk[s];
+    if (c == key) {
+      *slot = (int)s;
+      return 0;
+    }
+    if (c == EMPTY) {
+      const unsigned long long prev = atomicCAS(&hk[s], EMPTY, key);
+      if (prev == EMPTY) {
+        *slot = (int)s;
+        return 1;
+      }
+      if (prev == key) {
+        *slot = (int)s;
+        return 0;
+      }
+    }
+    s = (s + 1) & (CW_HC - 1);
+  }
+  return -1;
+}
+
+// Image of a packed edge record: byte c of y holds image component c + 128.
+__device__ __forceinline__ int epk_img(int y, int c) { return (int)(((unsigned)y >> (8 * c)) & 0xffu) - 128; }
+
+template <int PASS, bool CUT, int MAXD>
+__global__ void __launch_bounds__(32 * CW_WARPS)
+k_cluster_warp(int n, int K, const long long* __restrict__ row_ptr, const int2* __restrict__ epack,
+               const int* __restrict__ bond_of_edge, PathCut pc,
+               unsigned long long* __restrict__ gkeys, ClusterOut out, int* __restrict__ wfail,
+               unsigned* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char cw_raw[];
+  CwSmem& sm = reinterpret_cast<CwSmem*>(cw_raw)[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * CW_WARPS;
+  for (int atom = blockIdx.x * CW_WARPS + (threadIdx.x >> 5); atom < n; atom += nwarps) {
+    for (int q = lane; q < CW_HC; q += 32) sm.hk[q] = EMPTY;
+    if (lane == 0) {
+      sm.fail = 0;
+      sm.cnt = 0;
+    }
+    __syncwarp();
+    unsigned long long* gk = gkeys + (size_t)atom * CW_MAXS;
+    int nsite;
+    if (PASS == 0) {
+      // breadth-first search over hop levels
+      if (lane == 0) {
+        const unsigned long long k0 = site_key(atom, 0, 0, 0);
+        int sl = 0;
+        cw_insert(sm.hk, k0, &sl);
+        sm.hv[sl] = 0;
+        sm.sk[0] = k0;
+        sm.lev[0] = 1;
+      }
+      __syncwarp();
+      nsite = 1;
+      for (int k = 1; k <= K; k++) {
+        const int f0 = k >= 2 ? sm.lev[k - 2] : 0, f1 = sm.lev[k - 1];
+        for (int t = f0 + lane; t < f1; t += 32) {
+          const unsigned long long kt = sm.sk[t];
+          const int a = key_atom(kt);
+          const int ix = key_img(kt, 0), iy = key_img(kt, 1), iz = key_img(kt, 2);
+          const long long e0 = row_ptr[a];
+          int deg = (int)(row_ptr[a + 1] - e0);
+          if (deg > MAXD) {
+            atomicOr(wfail, 2);
+            deg = MAXD;
+          }
+          int2 pe[MAXD];  // the atom's edges, all loads in flight together
+#pragma unroll
+          for (int j = 0; j < MAXD; j++)
+            if (j < deg) pe[j] = __ldg(epack + e0 + j);
+#pragma unroll
+          for (int j = 0; j < MAXD; j++) {
+            if (j >= deg) continue;
+            const int sx = ix + epk_img(pe[j].y, 0), sy = iy + epk_img(pe[j].y, 1), sz = iz + epk_img(pe[j].y, 2);
+            if (sx < -127 || sx > 127 || sy < -127 || sy > 127 || sz < -127 || sz > 127) {
+              sm.fail = 1;
+              raise_error(status, BOP_DEV_ERR_IMAGE);
+              continue;
+            }
+            if (CUT) {
+              double d[3];
+              bond_vector(pc.pos + 3 * (size_t)atom, pc.pos + 3 * (size_t)pe[j].x, pc.cell, sx, sy, sz, d);
+              if (!(norm2_rn(d) < pc.r2)) continue;
+            }
+            const unsigned long long key = site_key(pe[j].x, sx, sy, sz);
+            int sl = 0;
+            const int r = cw_insert(sm.hk, key, &sl);
+            if (r == 1) {
+              const int q = atomicAdd(&sm.cnt, 1);
+              if (q < CW_MAXS) sm.nb[q] = key;
+            } else if (r < 0) {
+              sm.fail = 1;
+            }
+          }
+        }
+        __syncwarp();
+        const int cnt = sm.cnt;
+        if (cnt > CW_MAXS - nsite) sm.fail = 1;
+        __syncwarp();
+        if (sm.fail) break;
+        // canonical order inside the level: rank of every new key among them
+        for (int q = lane; q < cnt; q += 32) {
+          const unsigned long long key = sm.nb[q];
+          int r = 0;
+          for (int p = 0; p < cnt; p++) r += sm.nb[p] < key ? 1 : 0;
+          sm.sk[nsite + r] = key;
+          const int sl = cw_find(sm.hk, key);
+          sm.hv[sl >= 0 ? sl : 0] = (unsigned short)(nsite + r);
+        }
+        __syncwarp();
+        nsite += cnt;
+        if (lane == 0) {
+          sm.lev[k] = nsite;
+          sm.cnt = 0;
+        }
+        __syncwarp();
+      }
+      if (sm.fail) {
+        if (lane == 0) {
+          atomicOr(wfail, 1);
+          out.atom_nsite[atom] = 0;
+          out.atom_nadj[atom] = 0;
+        }
+        __syncwarp();
+        continue;
+      }
+      for (int t = lane; t < nsite; t += 32) gk[t] = sm.sk[t];
+    } else {
+      // pass 1: the keys of pass 0 (canonical order) and the level ends
+      for (int k = lane; k <= K; k += 32) sm.lev[k] = out.level_end[(size_t)atom * (K + 1) + k];
+      __syncwarp();
+      nsite = sm.lev[K];
+      for (int t = lane; t < nsite; t += 32) {
+        const unsigned long long key = gk[t];
+        sm.sk[t] = key;
+        int sl = 0;
+        cw_insert(sm.hk, key, &sl);
+        sm.hv[sl] = (unsigned short)t;
+      }
+      __syncwarp();
+    }
+    // adjacency of every site: the neighbours inside the cluster, by local index
+    const long long s0 = PASS == 1 ? out.site_off[atom] : 0;
+    const long long a0 = PASS == 1 ? out.adj_base[atom] : 0;
+    int run = 0;
+    unsigned long long prod = 0;
+    for (int tb = 0; tb < nsite; tb += 32) {
+      const int t = tb + lane;
+      unsigned long long ent[MAXD];
+      int deg = 0, c = 0;
+      int lt = 0;
+      if (t < nsite) {
+        const unsigned long long kt = sm.sk[t];
+        const int a = key_atom(kt);
+        const int ix = key_img(kt, 0), iy = key_img(kt, 1), iz = key_img(kt, 2);
+        const long long e0 = row_ptr[a];
+        deg = (int)(row_ptr[a + 1] - e0);
+        if (deg > MAXD) {
+          atomicOr(wfail, 2);
+          deg = MAXD;
+        }
+        int2 pe[MAXD];
+        int bnd[MAXD];
+#pragma unroll
+        for (int j = 0; j < MAXD; j++) {
+          if (j < deg) {
+            pe[j] = __ldg(epack + e0 + j);
+            bnd[j] = PASS == 1 ? __ldg(bond_of_edge + e0 + j) : 0;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < MAXD; j++) {
+          ent[j] = ~0ull;
+          if (j < deg) {
+            const int sx = ix + epk_img(pe[j].y, 0), sy = iy + epk_img(pe[j].y, 1), sz = iz + epk_img(pe[j].y, 2);
+            if (sx >= -127 && sx <= 127 && sy >= -127 && sy <= 127 && sz >= -127 && sz <= 127) {
+              const int sl = cw_find(sm.hk, site_key(pe[j].x, sx, sy, sz));
+              if (sl >= 0) {
+                ent[j] = ((unsigned long long)sm.hv[sl] << 32) | (unsigned)bnd[j];
+                c++;
+              }
+            }
+          }
+        }
+        while (lt < K && t >= sm.lev[lt]) lt++;
+      }
+      // offsets of this chunk's rows
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int off = run + incl - c;
+      run += __shfl_sync(0xffffffffu, incl, 31);
+      if (PASS == 1 && t < nsite) {
+        const unsigned long long kt = sm.sk[t];
+        out.site_atom[s0 + t] = key_atom(kt);
+        out.site_img[3 * (s0 + t)] = (signed char)key_img(kt, 0);
+        out.site_img[3 * (s0 + t) + 1] = (signed char)key_img(kt, 1);
+        out.site_img[3 * (s0 + t) + 2] = (signed char)key_img(kt, 2);
+        out.adj_off[s0 + t] = a0 + off;
+        unsigned long long lc = 0;
+        int cntk[BOP_MAX_K];
+#pragma unroll
+        for (int k = 0; k < BOP_MAX_K; k++) cntk[k] = 0;
+#pragma unroll
+        for (int j = 0; j < MAXD; j++) {
+          if (ent[j] == ~0ull) continue;
+          int rank = 0;
+#pragma unroll
+          for (int i = 0; i < MAXD; i++) rank += ent[i] < ent[j] ? 1 : 0;
+          const int sidx = (int)(ent[j] >> 32);
+          out.adj[a0 + off + rank] = make_int2(sidx, (int)(unsigned)(ent[j] & 0xffffffffu));
+#pragma unroll
+          for (int k = 0; k < BOP_MAX_K; k++)
+            if (k < K && sidx < sm.lev[k]) cntk[k]++;
+          int ls = 0;
+          while (ls < K && sidx >= sm.lev[ls]) ls++;
+          const int k0 = lt > ls + 1 ? lt : ls + 1;
+          if (k0 <= K) prod += (unsigned long long)(K - k0 + 1);
+        }
+#pragma unroll
+        for (int k = 0; k < BOP_MAX_K; k++)
+          if (k < K) lc |= (unsigned long long)cntk[k] << (8 * k);
+        out.lvcnt[s0 + t] = lc;
+      }
+    }
+    if (PASS == 0) {
+      if (lane == 0) {
+        out.atom_nsite[atom] = nsite;
+        out.atom_nadj[atom] = run;
+        atomicMax(&out.max_level[K + 1], run);
+      }
+      for (int k = lane; k <= K; k += 32) {
+        out.level_end[(size_t)atom * (K + 1) + k] = sm.lev[k];
+        atomicMax(&out.max_level[k], sm.lev[k]);
+      }
+    } else {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) prod += __shfl_xor_sync(0xffffffffu, prod, o);
+      if (lane == 0 && prod) atomicAdd(out.n_products, prod);
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace
 
 int launch_cluster(int pass, int n, int K, const long long* row_ptr, const int* col, const signed char* img,
@@ -317,6 +603,70 @@ int launch_cluster(int pass, int n, int K, const long long* row_ptr, const int* 
   if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   fn<<<grid, CL_THREADS, smem, s>>>(n, K, row_ptr, col, img, bond_of_edge, pc, sc, out, status);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Neighbour edges packed as {col, image bytes + 128} for the warp builder.
+__global__ void k_pack_edges(long long E, const int* __restrict__ col, const signed char* __restrict__ img,
+                             int2* __restrict__ out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (long long)gridDim.x * blockDim.x) {
+    const unsigned b = (unsigned)(img[3 * e] + 128) | ((unsigned)(img[3 * e + 1] + 128) << 8) |
+                       ((unsigned)(img[3 * e + 2] + 128) << 16);
+    out[e] = make_int2(col[e], (int)b);
+  }
+}
+
+void launch_pack_edges(long long E, const int* col, const signed char* img, int2* out, cudaStream_t s) {
+  if (E > 0) k_pack_edges<<<(int)((E + 255) / 256 < 8192 ? (E + 255) / 256 : 8192), 256, 0, s>>>(E, col, img, out);
+}
+
+int launch_cluster_warp(int pass, int n, int K, int max_deg, const long long* row_ptr, const int2* epack,
+                        const int* bond_of_edge, PathCut pc, unsigned long long* gkeys,
+                        ClusterOut out, int* wfail, unsigned* status, cudaStream_t s) {
+  if (n == 0) return 0;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int need = (n + CW_WARPS - 1) / CW_WARPS;
+  const int grid = need < sms * 4 ? need : sms * 4;
+  const bool cut = pc.r2 > 0.0;
+  const size_t smem = sizeof(CwSmem) * CW_WARPS;
+#define CW_LAUNCH(P, C, D)                                                                                       \
+  do {                                                                                                           \
+    cudaFuncSetAttribute(k_cluster_warp<P, C, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
+    k_cluster_warp<P, C, D><<<grid, 32 * CW_WARPS, smem, s>>>(n, K, row_ptr, epack, bond_of_edge, pc, gkeys, out,  \
+                                                              wfail, status);                                    \
+  } while (0)
+  if (max_deg <= 16) {
+    if (pass == 0) {
+      if (cut) CW_LAUNCH(0, true, 16); else CW_LAUNCH(0, false, 16);
+    } else {
+      if (cut) CW_LAUNCH(1, true, 16); else CW_LAUNCH(1, false, 16);
+    }
+  } else {
+    if (pass == 0) {
+      if (cut) CW_LAUNCH(0, true, 32); else CW_LAUNCH(0, false, 32);
+    } else {
+      if (cut) CW_LAUNCH(1, true, 32); else CW_LAUNCH(1, false, 32);
+    }
+  }
+#undef CW_LAUNCH
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int cluster_warp_max_sites() { return CW_MAXS; }
+
+// Largest row_ptr[i+1] - row_ptr[i] into *out (atomic max; *out starts at 0).
+__global__ void k_max_degree(int n, const long long* __restrict__ row_ptr, int* __restrict__ out) {
+  int m = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    m = max(m, (int)(row_ptr[i + 1] - row_ptr[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+void launch_max_degree(int n, const long long* row_ptr, int* out, cudaStream_t s) {
+  if (n > 0) k_max_degree<<<64, 256, 0, s>>>(n, row_ptr, out);
 }
 
 // Rows of one stored Psi sweep per atom: sum_{k=0..K} |C_k|.

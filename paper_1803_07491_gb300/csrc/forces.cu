@@ -1,6 +1,7 @@
 // Forces and virial from the bond cotangents (Eq. F_k, Eq. sigma_k): for
 // every bond b with vector d_b = r_j + S.cell - r_i,
-//   g_b = sum_u Hbar_b,u  dH_b,u / dd_b      (u = unique block elements)
+//   g_b = sum_u Hbar_b,u  dH_b,u / dd_b      (u = unique block elements;
+//                                             Hbar in the product type)
 //         + d phi(|d_b|) / dd_b              (pair repulsion, when present)
 //   F_i += g_b,  F_j -= g_b,  W += g_b (x) d_b.
 // dH/dd is exact: the two-centre block is evaluated in forward-mode dual
@@ -11,9 +12,10 @@ namespace {
 
 constexpr int FT = 256;
 
+template <typename HT>
 __global__ void __launch_bounds__(FT) k_forces(int nb, BondModel m, const double* __restrict__ bond_d,
-                                               const int* __restrict__ bond_atoms, const double* __restrict__ Hbar,
-                                               int HSu, double* __restrict__ F, double* __restrict__ W) {
+                                               const int* __restrict__ bond_atoms, const HT* __restrict__ Hbar,
+                                               int HSh, double* __restrict__ F, double* __restrict__ W) {
   __shared__ double sw[9][FT / 32];
   double w9[9];
   for (int q = 0; q < 9; q++) w9[q] = 0.0;
@@ -28,7 +30,7 @@ __global__ void __launch_bounds__(FT) k_forces(int nb, BondModel m, const double
     const int nu = block_unique(m.norb);
     double g0 = 0.0, g1 = 0.0, g2 = 0.0;
     for (int q = 0; q < nu; q++) {
-      double hb = Hbar[(size_t)b * HSu + q];
+      double hb = (double)Hbar[(size_t)b * HSh + q];
       g0 += hb * u[q].g0;
       g1 += hb * u[q].g1;
       g2 += hb * u[q].g2;
@@ -87,11 +89,14 @@ int launch_rep_energy(int n, BondModel m, const long long* row_ptr, const int* b
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_forces(int nb, BondModel m, const double* bond_d, const int* bond_atoms, const double* Hbar, int HSu,
-                  double* forces, double* virial, cudaStream_t s) {
+int launch_forces(int nb, BondModel m, const double* bond_d, const int* bond_atoms, const void* Hbar, int HSh,
+                  int fp64, double* forces, double* virial, cudaStream_t s) {
   int g = (nb + FT - 1) / FT;
   if (g > 4096) g = 4096;
   if (g < 1) g = 1;
-  k_forces<<<g, FT, 0, s>>>(nb, m, bond_d, bond_atoms, Hbar, HSu, forces, virial);
+  if (fp64)
+    k_forces<double><<<g, FT, 0, s>>>(nb, m, bond_d, bond_atoms, (const double*)Hbar, HSh, forces, virial);
+  else
+    k_forces<float><<<g, FT, 0, s>>>(nb, m, bond_d, bond_atoms, (const float*)Hbar, HSh, forces, virial);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -71,6 +71,18 @@ int launch_cluster(int pass, int n, int K, const long long* row_ptr, const int* 
                    unsigned* status, cudaStream_t s);
 
 void launch_level_sums(int n, int K, const int* level_end, long long* out, cudaStream_t s);
+// Warp-per-atom cluster builder (cluster.cu): the same outputs as
+// launch_cluster for clusters of at most cluster_warp_max_sites() sites and
+// atoms of at most 32 neighbours; pass 0 keeps every atom's site keys in
+// gkeys [n][cluster_warp_max_sites()].  *wfail != 0 after a pass: fall back
+// to launch_cluster.
+int launch_cluster_warp(int pass, int n, int K, int max_deg, const long long* row_ptr, const int2* epack,
+                        const int* bond_of_edge, PathCut pc, unsigned long long* gkeys,
+                        ClusterOut out, int* wfail, unsigned* status, cudaStream_t s);
+// epack[e] = {col[e], image bytes + 128} of every directed neighbour edge.
+void launch_pack_edges(long long E, const int* col, const signed char* img, int2* epack, cudaStream_t s);
+int cluster_warp_max_sites();
+void launch_max_degree(int n, const long long* row_ptr, int* out, cudaStream_t s);
 
 struct MomentsArgs {
   ClusterView cv;
@@ -102,8 +114,8 @@ struct AdjointArgs {
   void* scratch;       // per-CTA Psi / Psi-bar storage
   size_t slot_elems;   // elements of T per CTA
   int slots;
-  double* Hbar;        // [nb][HSu]   (+=)
-  int HSu;
+  void* Hbar;          // [nb][HSh] (+=), the product type T (bond_cotangent_stride)
+  int HSh;
   double* Ebar;        // [S][n][norb] (+=), may be null
   // reverse sweep over stored Psi (pstore != NULL; layout of MomentsArgs.pstore)
   const void* pstore;
@@ -120,6 +132,9 @@ struct AdjointArgs {
   long long sv_stride;
 };
 int launch_moments_adjoint(const AdjointArgs& a, int fp64, cudaStream_t s);
+// Elements per bond of the cotangent array Hbar: the unique block elements
+// (1, 15, 21), padded to a multiple of four in FP32 (float4 reductions).
+int bond_cotangent_stride(int norb, int fp64);
 
 // Non-collinear spin moments (moments.cu): work item (atom, orbital), the
 // two local spin states of the atom as starting spinors.
@@ -139,8 +154,8 @@ struct NcArgs {
   double* vmom;        // [n][norb][n_mom][3]
   // reverse (w != NULL): cotangents of sum w mu
   const double* w;     // [2][n][norb][n_mom]
-  double* Hbar;        // [nb][HSu] (+=)
-  int HSu;
+  void* Hbar;          // [nb][HSh] (+=), the product type T (bond_cotangent_stride)
+  int HSh;
   double* obar;        // [n][norb][4] (+=): d/d(Ebar, h_x, h_y, h_z)
 };
 int launch_nc(const NcArgs& a, int fp64, cudaStream_t s);
@@ -345,5 +360,5 @@ int launch_scale_vec(int nu, const double* x, const double* P, double a, double*
 // Pair repulsion per atom (half of each of its bonds) into erep [n].
 int launch_rep_energy(int n, BondModel m, const long long* row_ptr, const int* bond_of_edge, const double* bond_d,
                       double* erep, cudaStream_t s);
-int launch_forces(int nb, BondModel m, const double* bond_d, const int* bond_atoms, const double* Hbar, int HSu,
+int launch_forces(int nb, BondModel m, const double* bond_d, const int* bond_atoms, const void* Hbar, int HSh, int fp64,
                   double* forces, double* virial, cudaStream_t s);

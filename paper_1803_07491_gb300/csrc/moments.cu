@@ -62,6 +62,41 @@ __device__ __forceinline__ constexpr int UI(int b, int g) {
   return b <= g ? b * NO - (b * (b - 1)) / 2 + (g - b) : g * NO - (g * (g - 1)) / 2 + (b - g);
 }
 
+// Stride of one bond's cotangents: the unique block elements, padded to a
+// multiple of four for FP32 (vector atomics), unpadded for FP64.
+template <typename T, int NO>
+__host__ __device__ constexpr int hbar_stride() {
+  return (NO == 1 || sizeof(T) == 8) ? NO * (NO + 1) / 2 : (NO * (NO + 1) / 2 + 3) / 4 * 4;
+}
+
+// Adds dL/dB (G[b][g] = dL/dB_bg of one orientation of a symmetric block)
+// to the bond's unique elements: u(b, g) collects G[b][g] + G[g][b].  FP32
+// cotangents go out as float4 reductions (four per d block instead of 15
+// scalar ones), FP64 as scalar FP64 atomics.
+template <typename T, int NO>
+__device__ __forceinline__ void add_bond_cotangent(T* __restrict__ hbp, const T G[NO][NO]) {
+  if constexpr (NO == 1) {
+    atomicAdd(hbp, G[0][0]);
+  } else if constexpr (sizeof(T) == 4) {
+    constexpr int HV = hbar_stride<T, NO>();
+    float v[HV];
+#pragma unroll
+    for (int q = 0; q < HV; q++) v[q] = 0.f;
+#pragma unroll
+    for (int b = 0; b < NO; b++)
+#pragma unroll
+      for (int g = b; g < NO; g++) v[UI<NO>(b, g)] = G[b][g] + (b != g ? G[g][b] : 0.f);
+    float4* dst = reinterpret_cast<float4*>(hbp);
+#pragma unroll
+    for (int q = 0; q < HV / 4; q++) atomicAdd(dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+  } else {
+#pragma unroll
+    for (int b = 0; b < NO; b++)
+#pragma unroll
+      for (int g = b; g < NO; g++) atomicAdd(hbp + UI<NO>(b, g), G[b][g] + (b != g ? G[g][b] : T(0)));
+  }
+}
+
 // acc[r][c] += B[r][g] * x[g][c] for the symmetric block B given by u[].
 template <typename T, int NO, int NC>
 __device__ __forceinline__ void block_apply(const T* __restrict__ hrec, const T* __restrict__ x,
@@ -471,7 +506,7 @@ __global__ void __launch_bounds__(FWD_THREADS, sizeof(T) == 4 ? 2 : 1)
 k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_mom,
           RevSmem L, int n_items, int chunk, const T* __restrict__ pstore, T* __restrict__ pbstore,
           const long long* __restrict__ psi_off, long long psi_tot, const double* __restrict__ wts,
-          double* __restrict__ Hbar, int HSu, double* __restrict__ Ebar, double* __restrict__ siteval,
+          T* __restrict__ Hbar, int HSh, double* __restrict__ Ebar, double* __restrict__ siteval,
           long long sv_stride) {
   constexpr int N = NO * NC;
   constexpr int PS = (N == 1) ? 1 : Row<T, N>::PS;
@@ -669,18 +704,7 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
                 G[b][g] += a;
               }
           }
-          double* hbp = Hbar + (size_t)en.y * HSu;
-          if constexpr (NO == 1) {
-            atomicAdd(hbp, (double)G[0][0]);
-          } else {
-#pragma unroll
-            for (int b = 0; b < NO; b++)
-#pragma unroll
-              for (int g = b; g < NO; g++) {
-                const T v = G[b][g] + (b != g ? G[g][b] : T(0));  // sum in T, one conversion
-                atomicAdd(hbp + UI<NO>(b, g), (double)v);
-              }
-          }
+          add_bond_cotangent<T, NO>(Hbar + (size_t)en.y * HSh, G);
         }
       }
     }
@@ -699,7 +723,7 @@ template <typename T, int NO, int NC>
 __global__ void __launch_bounds__(MOM_THREADS)
 k_moments_adj(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_mom,
               int nwork, const double* __restrict__ wts, T* __restrict__ scratch, size_t slot_elems,
-              double* __restrict__ Hbar, int HSu, double* __restrict__ Ebar) {
+              T* __restrict__ Hbar, int HSh, double* __restrict__ Ebar) {
   __shared__ T ws[NC][BOP_MAX_NMOM];
   __shared__ int s_lev[BOP_MAX_K + 1];
   __shared__ long long s_off[BOP_MAX_K + 2];
@@ -813,18 +837,7 @@ k_moments_adj(ClusterView cv, const T* __restrict__ H, int HS, const T* __restri
               G[b][g] += a;
             }
         }
-        double* hb = Hbar + (size_t)en.y * HSu;
-        if constexpr (NO == 1) {
-          atomicAdd(hb, (double)G[0][0]);
-        } else {
-#pragma unroll
-          for (int b = 0; b < NO; b++)
-#pragma unroll
-            for (int g = b; g < NO; g++) {
-              double v = (double)G[b][g] + (b != g ? (double)G[g][b] : 0.0);
-              atomicAdd(hb + UI<NO>(b, g), v);
-            }
-        }
+        add_bond_cotangent<T, NO>(Hbar + (size_t)en.y * HSh, G);
       }
       if (Ebar != nullptr) {
         double eb[NO];
@@ -867,7 +880,8 @@ k_moments_adj(ClusterView cv, const T* __restrict__ H, int HS, const T* __restri
 //   forward (wts == NULL): local channel moments mu_nu,n = <chi_nu|H^n|chi_nu>
 //   into mu[nu] and Tr(sigma M_n) of the global 2x2 moments M_n into vmom;
 //   reverse (wts != NULL): cotangents of L = sum w_nu,n mu_nu,n for every
-//   bond block (Hbar, FP64 atomics) and every onsite matrix
+//   bond block (Hbar, in the product type: float4 reductions in FP32) and
+//   every onsite matrix
 //   (obar = dL/d(Ebar, h_x, h_y, h_z)).
 // Psi_0..Psi_K (and Psi-bar_1..Psi-bar_K) of the item live in the CTA's
 // slot of global scratch, as in k_moments_adj.
@@ -962,7 +976,7 @@ template <typename T, int NO>
 __global__ void __launch_bounds__(MOM_THREADS)
 k_nc(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, const double* __restrict__ sdir,
      int n, int n_mom, int nwork, T* __restrict__ scratch, size_t slot_elems, double* __restrict__ mu,
-     double* __restrict__ vmom, const double* __restrict__ wts, double* __restrict__ Hbar, int HSu,
+     double* __restrict__ vmom, const double* __restrict__ wts, T* __restrict__ Hbar, int HSh,
      double* __restrict__ obar) {
   constexpr int RW = NO * NCS;
   __shared__ T ws[2][BOP_MAX_NMOM];
@@ -1123,15 +1137,7 @@ k_nc(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsi
                 G[b][g] += a;
               }
           }
-          double* hb = Hbar + (size_t)en.y * HSu;
-          if constexpr (NO == 1) {
-            atomicAdd(hb, (double)G[0][0]);
-          } else {
-#pragma unroll
-            for (int b = 0; b < NO; b++)
-#pragma unroll
-              for (int g = b; g < NO; g++) atomicAdd(hb + UI<NO>(b, g), (double)G[b][g] + (b != g ? (double)G[g][b] : 0.0));
-          }
+          add_bond_cotangent<T, NO>(Hbar + (size_t)en.y * HSh, G);
         }
         if (lt + 1 <= K) {
           // dL/d(Ebar, h) of the onsite matrix of (atom of t, b): the
@@ -1295,7 +1301,7 @@ int run_nc(const NcArgs& a, cudaStream_t s) {
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
   }
   k_nc<T, NO><<<grid, MOM_THREADS, 0, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.sdir, a.n, a.n_mom,
-                                           nwork, (T*)a.scratch, a.slot_elems, a.mu, a.vmom, a.w, a.Hbar, a.HSu,
+                                           nwork, (T*)a.scratch, a.slot_elems, a.mu, a.vmom, a.w, (T*)a.Hbar, a.HSh,
                                            a.obar);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -1339,7 +1345,7 @@ int run_adjoint(const AdjointArgs& a, cudaStream_t s) {
   int grid = nwork < a.slots ? nwork : a.slots;
   k_moments_adj<T, NO, NC><<<grid, MOM_THREADS, 0, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n,
                                                        a.n_mom, nwork, a.w, (T*)a.scratch, a.slot_elems,
-                                                       a.Hbar, a.HSu, a.Ebar);
+                                                       (T*)a.Hbar, a.HSh, a.Ebar);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -1377,7 +1383,7 @@ int run_reverse(const AdjointArgs& a, cudaStream_t s) {
   const int chunk = (n_items + slots - 1) / slots;
   const int grid = (n_items + chunk - 1) / chunk;
   fn<<<grid, FWD_THREADS, smem, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n, a.n_mom, L, n_items, chunk,
-                                      (const T*)a.pstore, (T*)a.pbstore, a.psi_off, a.psi_tot, a.w, a.Hbar, a.HSu,
+                                      (const T*)a.pstore, (T*)a.pbstore, a.psi_off, a.psi_tot, a.w, (T*)a.Hbar, a.HSh,
                                       a.Ebar, a.siteval, a.sv_stride);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -1409,6 +1415,12 @@ int launch_moments(const MomentsArgs& a, int fp64, cudaStream_t s) {
 }
 
 int adjoint_columns(int norb) { return norb; }
+
+int bond_cotangent_stride(int norb, int fp64) {
+  if (norb == 1) return 1;
+  if (norb == 5) return fp64 ? hbar_stride<double, 5>() : hbar_stride<float, 5>();
+  return fp64 ? hbar_stride<double, 6>() : hbar_stride<float, 6>();
+}
 
 int launch_moments_adjoint(const AdjointArgs& a, int fp64, cudaStream_t s) {
   if (a.pstore != nullptr) {  // reverse sweep over stored Psi

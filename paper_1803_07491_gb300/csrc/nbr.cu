@@ -77,10 +77,14 @@ __device__ __forceinline__ uint64_t nbr_key(int j, int sx, int sy, int sz) {
          (uint64_t)(sz + 128);
 }
 
-// One warp per atom.  The lanes test the atoms of each candidate cell
-// (32 at a time); hits go to a per-warp list in shared memory in ballot
-// order.  mode 0: count neighbours; mode 1: every entry's rank among the
-// keys (j, sx, sy, sz) gives its slot in the sorted row.
+// One warp per atom.  The candidate cells (27, or more along axes with
+// fewer than three cells) are enumerated 32 at a time, one per lane, with
+// their atom ranges; a warp scan of the range lengths flattens their atoms
+// into one candidate list that the lanes test 32 at a time, so a warp waits
+// on a few rounds of loads instead of one round per cell.  Hits go to a
+// per-warp list in shared memory in ballot order.  mode 0: count
+// neighbours; mode 1: every entry's rank among the keys (j, sx, sy, sz)
+// gives its slot in the sorted row.
 constexpr int NBR_WARPS = 4;
 
 template <int MODE>
@@ -90,6 +94,7 @@ k_neighbors(int n, const double* __restrict__ pos, Geometry g, const int* __rest
             const long long* __restrict__ row_ptr, int* __restrict__ col, signed char* __restrict__ img,
             unsigned* __restrict__ status) {
   __shared__ uint64_t skeys[NBR_WARPS][BOP_MAX_DEG];
+  __shared__ int s_start[NBR_WARPS][32], s_pre[NBR_WARPS][33], s_img[NBR_WARPS][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int i = blockIdx.x * NBR_WARPS + wib;
   if (i >= n) return;  // whole warp
@@ -100,41 +105,65 @@ k_neighbors(int n, const double* __restrict__ pos, Geometry g, const int* __rest
   const unsigned lt_mask = (1u << lane) - 1u;
   int cnt = 0;
   const int n0 = axis_count(g, 0), n1 = axis_count(g, 1), n2 = axis_count(g, 2);
-  for (int q0 = 0; q0 < n0; q0++) {
-    if (!axis_valid(g, 0, c3[0], q0)) continue;
-    for (int q1 = 0; q1 < n1; q1++) {
-      if (!axis_valid(g, 1, c3[1], q1)) continue;
-      for (int q2 = 0; q2 < n2; q2++) {
-        if (!axis_valid(g, 2, c3[2], q2)) continue;
+  const int ncand = n0 * n1 * n2;
+  if (lane == 0) s_pre[wib][0] = 0;
+  for (int cb = 0; cb < ncand; cb += 32) {
+    const int q = cb + lane;
+    int len = 0, start = 0, im = 0;
+    if (q < ncand) {
+      const int q0 = q / (n1 * n2), q1 = (q / n2) % n1, q2 = q % n2;
+      if (axis_valid(g, 0, c3[0], q0) && axis_valid(g, 1, c3[1], q1) && axis_valid(g, 2, c3[2], q2)) {
         int cx, cy, cz, sx, sy, sz;
         AxisIter it;
         it.get(g, 0, c3[0], q0, &cx, &sx);
         it.get(g, 1, c3[1], q1, &cy, &sy);
         it.get(g, 2, c3[2], q2, &cz, &sz);
         const int cc = (cx * g.nc[1] + cy) * g.nc[2] + cz;
-        const int p0 = cell_start[cc], p1 = cell_start[cc + 1];
-        for (int base = p0; base < p1; base += 32) {
-          const int p = base + lane;
-          bool hit = false;
-          uint64_t key = 0;
-          if (p < p1) {
-            const int j = cell_atoms[p];
-            if (!(j == i && sx == 0 && sy == 0 && sz == 0)) {
-              double d[3];
-              bond_vector(pi, pos + 3 * j, g.cell, sx, sy, sz, d);
-              hit = norm2_rn(d) < rc2;
-              key = nbr_key(j, sx, sy, sz);
-            }
-          }
-          const unsigned bal = __ballot_sync(0xffffffffu, hit);
-          if (hit) {
-            const int slot = cnt + __popc(bal & lt_mask);
-            if (slot < BOP_MAX_DEG) skeys[wib][slot] = key;
-          }
-          cnt += __popc(bal);
-        }
+        start = cell_start[cc];
+        len = cell_start[cc + 1] - start;
+        im = ((sx + 128) << 16) | ((sy + 128) << 8) | (sz + 128);
       }
     }
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    s_start[wib][lane] = start;
+    s_pre[wib][lane + 1] = incl;
+    s_img[wib][lane] = im;
+    __syncwarp();
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    for (int base = 0; base < tot; base += 32) {
+      const int p = base + lane;
+      bool hit = false;
+      uint64_t key = 0;
+      if (p < tot) {
+        int lo = 0, hi = 31;  // the candidate cell c with s_pre[c] <= p < s_pre[c + 1]
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_pre[wib][mid] <= p) lo = mid;
+          else hi = mid - 1;
+        }
+        const int j = cell_atoms[s_start[wib][lo] + (p - s_pre[wib][lo])];
+        const int code = s_img[wib][lo];
+        const int sx = ((code >> 16) & 0xff) - 128, sy = ((code >> 8) & 0xff) - 128, sz = (code & 0xff) - 128;
+        if (!(j == i && sx == 0 && sy == 0 && sz == 0)) {
+          double d[3];
+          bond_vector(pi, pos + 3 * j, g.cell, sx, sy, sz, d);
+          hit = norm2_rn(d) < rc2;
+          key = nbr_key(j, sx, sy, sz);
+        }
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const int slot = cnt + __popc(bal & lt_mask);
+        if (slot < BOP_MAX_DEG) skeys[wib][slot] = key;
+      }
+      cnt += __popc(bal);
+    }
+    __syncwarp();
   }
   if (MODE == 0) {
     if (lane == 0) {
