@@ -60,8 +60,17 @@ enum bop_status {
   BOP_ERR_BRACKET = 5,        /* Fermi level could not be bracketed */
   BOP_ERR_NUMERIC = 6,        /* NaN/Inf in the scalar stages */
   BOP_ERR_STATE = 7,          /* call order violated (e.g. forces before energy) */
-  BOP_ERR_OVERFLOW = 8        /* neighbour degree / cluster / image index limit exceeded */
+  BOP_ERR_OVERFLOW = 8,       /* neighbour degree / cluster / image index limit exceeded */
+  BOP_ERR_COLLECTIVE = 9      /* the reduce function of bop_set_reduce reported a failure */
 };
+
+/* Reductions over the processes of a spatial decomposition (bop_set_reduce). */
+enum { BOP_REDUCE_SUM = 0, BOP_REDUCE_MAX = 1 };
+/* Replaces values[0..count) on every process by their sum (op
+ * BOP_REDUCE_SUM) or maximum (BOP_REDUCE_MAX) over all processes, in place;
+ * host memory; returns 0 on success.  Every process calls it the same number
+ * of times in the same order. */
+typedef int (*bop_reduce_fn)(double* values, int count, int op, void* user);
 
 enum { BOP_SCF_NONE = 0, BOP_SCF_LCN = 1, BOP_SCF_STONER = 2, BOP_SCF_VARIATIONAL = 3 };
 enum { BOP_PREC_FP64 = 0, BOP_PREC_FP32 = 1 };
@@ -330,6 +339,36 @@ int bop_set_spin_directions(bop_ctx* ctx, const double* s, bop_stream stream);
  * preceding bop_forces. */
 int bop_torques(bop_ctx* ctx, double* t, bop_stream stream);
 
+/* Spatial decomposition (section "Performance", parallelisation: the paper
+ * decomposes the structure into spatial domains, one per process).  Each
+ * process builds its domain as one structure: its own atoms first, then the
+ * halo, every atom (with the periodic image it needs) within K r_cut of an
+ * own atom along the decomposed directions, K = (n_mom - 1)/2, so that the
+ * cluster of every own atom lies inside the domain.
+ *
+ * bop_set_centers(ctx, n_centers): from the next bop_build_hamiltonian on,
+ * only atoms [0, n_centers) of a structure are centres: they get clusters,
+ * moments, electrons and energies; atoms [n_centers, n) are environment
+ * atoms, which take part in the neighbour list, the bond blocks and the
+ * clusters of the centres as sites, receive the forces of the bonds they
+ * take part in, and have energy 0 in e_atom.  0 (the default) makes every
+ * atom a centre.  Errors: BOP_ERR_ARG for n_centers < 0; the build returns
+ * BOP_ERR_ARG when n_centers exceeds the atoms of the structure.
+ *
+ * bop_set_reduce(ctx, fn, user): the context combines its global sums over
+ * all processes with fn (NULL: one process): the band edges and the sums of
+ * every Newton round of the Fermi-level search (one E_F for the whole
+ * structure), the total energy in bop_stats, and the two sums of the E_F
+ * multiplier of the forces.  The forces a process returns are its centres'
+ * contributions to the forces on every atom of its domain (own and halo):
+ * summed over the processes by global atom they give the forces of the
+ * whole structure; the virial likewise.
+ *
+ * With centres or a reduce function the model must have scf NONE and be
+ * collinear (bop_energy returns BOP_ERR_ARG otherwise). */
+int bop_set_centers(bop_ctx* ctx, int n_centers);
+int bop_set_reduce(bop_ctx* ctx, bop_reduce_fn fn, void* user);
+
 /* Limits of the SCF-response solve of bop_forces (GMRES, described there):
  * max_iterations caps its Arnoldi iterations (0 = the default, 3 cycles of
  * 40), rtol its relative residual (0 = the default of the precision).  A
@@ -345,9 +384,10 @@ int bop_set_response_limits(bop_ctx* ctx, int max_iterations, double rtol);
  * follow (an SCF with scf_response = 1) and all starting orbitals of an atom
  * share one work item of the moments kernel, bop_forces runs one extra
  * forward pass that stores Psi_k of every atom's cluster (rows of norb x
- * norb values per site and level, FP32 or FP64 as the precision) together
- * with a cotangent copy, when both fit in a third of the free device
- * memory, and every reverse sweep then reads Psi instead of recomputing it.
+ * norb values per site and level, FP32 or FP64 as the precision) when it
+ * fits in a third of the free device memory, and every reverse sweep then
+ * reads Psi instead of recomputing it (the sweep that forms the bond
+ * cotangents forms them level by level from the same store).
  * bytes >= 0 caps that store (0 = always recompute, which also frees it);
  * bytes < 0 restores the default. */
 int bop_set_store_budget(bop_ctx* ctx, long long bytes);

@@ -17,6 +17,11 @@ from . import build as _build
 
 BOP_OK, BOP_ERR_ARG, BOP_ERR_CUDA, BOP_ERR_OOM, BOP_ERR_NO_CONVERGENCE = 0, 1, 2, 3, 4
 BOP_ERR_BRACKET, BOP_ERR_NUMERIC, BOP_ERR_STATE, BOP_ERR_OVERFLOW = 5, 6, 7, 8
+BOP_ERR_COLLECTIVE = 9
+BOP_REDUCE_SUM, BOP_REDUCE_MAX = 0, 1
+# bop_reduce_fn: int (*)(double* values, int count, int op, void* user)
+REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                             ctypes.c_void_p)
 SCF = {"none": 0, "lcn": 1, "stoner": 2, "variational": 3}
 PREC = {"fp64": 0, "fp32": 1}
 MIXER = {"linear": 0, "anderson": 1}
@@ -118,6 +123,8 @@ def lib(path: str | None = None):
         "bop_set_mlp": ([_VP, _VP], ctypes.c_int),
         "bop_set_store_budget": ([_VP, ctypes.c_longlong], ctypes.c_int),
         "bop_set_response_limits": ([_VP, ctypes.c_int, ctypes.c_double], ctypes.c_int),
+        "bop_set_centers": ([_VP, ctypes.c_int], ctypes.c_int),
+        "bop_set_reduce": ([_VP, REDUCE_FN, _VP], ctypes.c_int),
         "bop_set_spin_directions": ([_VP, _VP, _VP], ctypes.c_int),
         "bop_torques": ([_VP, _VP, _VP], ctypes.c_int),
         "bop_md_verlet": ([ctypes.c_int, _VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -430,6 +437,15 @@ def bop_mlp_predict(net, x: torch.Tensor, stream=None) -> torch.Tensor:
 
 def bop_set_response_limits(ctx, max_iterations: int = 0, rtol: float = 0.0):
     _check(ctx, lib().bop_set_response_limits(ctx, int(max_iterations), float(rtol)))
+
+
+def bop_set_centers(ctx, n_centers: int):
+    _check(ctx, lib().bop_set_centers(ctx, int(n_centers)))
+
+
+def bop_set_reduce(ctx, fn):
+    """fn: a REDUCE_FN (kept alive by the caller), or None for one process."""
+    _check(ctx, lib().bop_set_reduce(ctx, fn if fn is not None else REDUCE_FN(), None))
 
 
 def bop_set_store_budget(ctx, nbytes: int):

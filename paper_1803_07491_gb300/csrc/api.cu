@@ -56,8 +56,13 @@ struct bop_ctx {
   int norb, HS, HSu, K, Kp, n_mom, n_exp, S, fp64;
   double sfac;
   int device;
-  // structure
-  int n = 0;
+  // structure: n atoms, of which the first nc have clusters (centres); the
+  // others are environment (halo) atoms of a spatial domain
+  int n = 0, nc = 0, nc_req = 0;
+  // reductions over the processes of a spatial decomposition (NULL: one process)
+  bop_reduce_fn reduce_fn = nullptr;
+  void* reduce_user = nullptr;
+  double ef_host = 0.0;  // E_F of the last distributed solve (its warm start)
   long long E = 0, nb = 0, nsite = 0, nadj = 0;
   Geometry g;
   int maxlev[BOP_MAX_K + 2];  // largest |C_k| per level, then the largest adjacency
@@ -91,7 +96,8 @@ struct bop_ctx {
   DBuf sdir, vmom, obar, torque, ncscr;
   int sdir_n = -1;
   // stored Psi of every work item for the reverse sweeps (when it fits)
-  DBuf psi_off, psis, psib, lsum;
+  DBuf psi_off, psis, lsum;
+  DBuf fev;  // two device doubles of the distributed Fermi solve
   DBuf cw_misc, cw_keys, cw_epack;  // warp cluster builder: max degree / failure flags, site keys per
                                     // atom, packed neighbour edges
   long long psi_tot = 0;
@@ -307,7 +313,7 @@ int geometry(bop_ctx* c, const double* cell, const int* pbc, Geometry* g) {
 // apply, and the block builder below runs instead.
 int build_clusters_warp(bop_ctx* c, cudaStream_t s, bool* done) {
   *done = false;
-  const int n = c->n, K = c->K;
+  const int n = c->nc, K = c->K;  // clusters of the centres
   if (n == 0 || (c->cl_maxs && c->cl_maxs > cluster_warp_max_sites())) return BOP_OK;
   if (K > 5 && !(c->m.r_path > 0)) return BOP_OK;  // bcc has 1,105 sites within 6 hops
   CKS(ensure(c, c->cw_misc, 4 * sizeof(int)));
@@ -389,7 +395,7 @@ int build_clusters_warp(bop_ctx* c, cudaStream_t s, bool* done) {
 }
 
 int build_clusters(bop_ctx* c, cudaStream_t s) {
-  const int n = c->n, K = c->K;
+  const int n = c->nc, K = c->K;  // clusters of the centres
   {
     bool done = false;
     CKS(build_clusters_warp(c, s, &done));
@@ -488,9 +494,10 @@ ClusterView cview(bop_ctx* c) {
 }
 
 int size_state(bop_ctx* c) {
-  const size_t M = (size_t)c->S * c->n * c->norb;
-  CKS(ensure(c, c->onsite, sizeof(double) * M));
-  CKS(ensure(c, c->onsite32, sizeof(float) * M));
+  const size_t M = (size_t)c->S * c->nc * c->norb;      // orbitals of the centres
+  const size_t Mon = (size_t)c->S * c->n * c->norb;     // onsite levels of every atom
+  CKS(ensure(c, c->onsite, sizeof(double) * Mon));
+  CKS(ensure(c, c->onsite32, sizeof(float) * Mon));
   CKS(ensure(c, c->delta, sizeof(double) * c->n));
   CKS(ensure(c, c->mval, sizeof(double) * c->n));
   CKS(ensure(c, c->delta_new, sizeof(double) * c->n));
@@ -572,7 +579,8 @@ int run_moments(bop_ctx* c, const double* onsite_dev, double* mu, cudaStream_t s
   a.H = c->fp64 ? c->H64.p : c->H32.p;
   a.HS = c->HS;
   a.onsite = c->fp64 ? (const void*)onsite_dev : (const void*)c->onsite32.p;
-  a.n = c->n;
+  a.n = c->nc;
+  a.n_on = c->n;
   a.n_spin = c->S;
   a.norb = c->norb;
   a.n_mom = c->n_mom;
@@ -678,11 +686,86 @@ int run_scalar(bop_ctx* c, int M, const double* mu, cudaStream_t s) {
   return BOP_OK;
 }
 
+// Sum (or max) of v[0..n) over the processes of a spatial decomposition;
+// nothing with one process.
+int reduce_over_ranks(bop_ctx* c, double* v, int n, int op) {
+  if (!c->reduce_fn) return BOP_OK;
+  if (c->reduce_fn(v, n, op, c->reduce_user) != 0) return fail(c, BOP_ERR_COLLECTIVE, "reduce callback failed");
+  return BOP_OK;
+}
+
+// Fermi level over several processes ("DOS and Fermi energy": one E_F for
+// the whole structure): the bracket and the sums of every Newton round are
+// this process's, reduced over the processes, and the update rules are those
+// of k_fermi_newton; then N and DOS of this process's orbitals at E_F.
+int fermi_distributed(bop_ctx* c, int warm, cudaStream_t s) {
+  const int M = c->S * c->nc * c->norb;
+  CKS(ensure(c, c->fev, 2 * sizeof(double)));
+  double ncg = (double)c->nc;
+  CKS(reduce_over_ranks(c, &ncg, 1, BOP_REDUCE_SUM));
+  const double target = c->m.n_e * ncg;
+  double v[2];
+  auto eval = [&](int mode, double E) -> int {
+    {
+      Region R(c, PK_FERMI, 1, s);
+      if (launch_fermi_eval(mode, M, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf),
+                            P<double>(c->b_inf), c->n_exp, E, P<double>(c->partials), P<unsigned>(c->counter),
+                            P<double>(c->fev), s))
+        return fail(c, BOP_ERR_CUDA, "fermi launch failed");
+    }
+    CK(cudaMemcpyAsync(v, c->fev.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return reduce_over_ranks(c, v, 2, mode == 0 ? BOP_REDUCE_MAX : BOP_REDUCE_SUM);
+  };
+  CKS(eval(0, 0.0));
+  double lo = -v[0] - 1e-3, hi = v[1] + 1e-3;
+  double E = (warm && c->ef_solved && c->ef_host > lo && c->ef_host < hi) ? c->ef_host : 0.5 * (lo + hi);
+  FermiState fs;
+  memset(&fs, 0, sizeof(fs));
+  double ef = 0.5 * (lo + hi);
+  bool done = hi - lo < FERMI_TOL;
+  while (!done) {
+    CKS(eval(1, E));
+    const double f = c->sfac * v[0] - target, fp = c->sfac * v[1];
+    fs.iters++;
+    if (f == 0.0) {
+      ef = E;
+      break;
+    }
+    if (f < 0.0) lo = E;
+    else hi = E;
+    double xn = fp > 0.0 ? E - f / fp : lo - 1.0;
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+    if (std::fabs(xn - E) < FERMI_TOL || hi - lo < FERMI_TOL || fs.iters >= FERMI_MAX_ROUNDS) {
+      ef = xn;
+      done = true;
+    } else {
+      E = xn;
+    }
+  }
+  if (fs.iters >= FERMI_MAX_ROUNDS)
+    return fail(c, BOP_ERR_BRACKET, "Fermi level not converged after %d rounds", fs.iters);
+  fs.lo = lo;
+  fs.hi = hi;
+  fs.mid = E;
+  fs.ef = ef;
+  fs.done = 1;
+  c->ef_host = ef;
+  CK(cudaMemcpyAsync(c->fstate.p, &fs, sizeof(fs), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  Region R(c, PK_NU, 1, s);
+  if (launch_orbital_N(M, c->n_exp, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf),
+                       P<double>(c->b_inf), P<FermiState>(c->fstate), P<double>(c->N), P<double>(c->dos), s))
+    return fail(c, BOP_ERR_CUDA, "orbital N launch failed");
+  return BOP_OK;
+}
+
 // Fermi level (Newton steps inside the bisection bracket) and N, DOS of every
 // orbital at E_F.  warm: start from the previous solve's E_F.
 int fermi_and_N(bop_ctx* c, int warm, cudaStream_t s) {
-  const int M = c->S * c->n * c->norb;
-  const double target = c->m.n_e * c->n;
+  if (c->reduce_fn) return fermi_distributed(c, warm, s);
+  const int M = c->S * c->nc * c->norb;
+  const double target = c->m.n_e * c->nc;
   {
     // one cooperative launch: bracket, Newton rounds to convergence, N and DOS
     Region R(c, PK_FERMI, 1, s);
@@ -710,11 +793,11 @@ int fermi_and_N(bop_ctx* c, int warm, cudaStream_t s) {
 
 // More Newton rounds for a solve that has not converged, then N and DOS again.
 int fermi_more(bop_ctx* c, cudaStream_t s) {
-  const int M = c->S * c->n * c->norb;
+  const int M = c->S * c->nc * c->norb;
   {
     Region R(c, PK_FERMI, FERMI_ROUNDS_MORE, s);
     if (launch_fermi_more(M, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf), P<double>(c->b_inf),
-                          c->n_exp, c->sfac, c->m.n_e * c->n, P<FermiState>(c->fstate), P<double>(c->partials),
+                          c->n_exp, c->sfac, c->m.n_e * c->nc, P<FermiState>(c->fstate), P<double>(c->partials),
                           P<unsigned>(c->counter), FERMI_ROUNDS_MORE, FERMI_MAX_ROUNDS, FERMI_TOL, s))
       return fail(c, BOP_ERR_CUDA, "fermi launch failed");
   }
@@ -731,7 +814,7 @@ int fermi_more(bop_ctx* c, cudaStream_t s) {
 // into w [M][n_mom]; dUE [M] = direct dL/dE (may be NULL).
 int compute_weights(bop_ctx* c, double cU, const double* lam, double cN0, double* w, double* dUE, cudaStream_t s,
                     const double* var_q = nullptr, const double* var_lam = nullptr, double var_J = 0.0) {
-  const int M = c->S * c->n * c->norb;
+  const int M = c->S * c->nc * c->norb;
   WeightArgs wa;
   wa.M = M;
   wa.n_mom = c->n_mom;
@@ -802,10 +885,9 @@ int psi_store_alloc(bop_ctx* c, bool* fits) {
   const size_t bytes = (size_t)c->S * (c->norb / nc) * (size_t)c->psi_tot * psi_row(c->norb * nc, c->fp64) * esz;
   size_t freeb = 0, totalb = 0;
   CK(cudaMemGetInfo(&freeb, &totalb));
-  const size_t held = c->psis.bytes + c->psib.bytes;
-  if (2 * bytes > (freeb + held) / 3 || 2 * bytes > c->store_budget) return BOP_OK;
+  const size_t held = c->psis.bytes;
+  if (bytes > (freeb + held) / 3 || bytes > c->store_budget) return BOP_OK;
   CKS(ensure(c, c->psis, bytes));
-  CKS(ensure(c, c->psib, bytes));
   *fits = true;
   return BOP_OK;
 }
@@ -828,9 +910,10 @@ int prepare_psi_store(bop_ctx* c, cudaStream_t s) {
 // NULL), Ebar += dL/dE (if not NULL).  Over the stored Psi when present.
 int adjoint_pass(bop_ctx* c, const double* w, void* Hbar, double* Ebar, cudaStream_t s,
                  double* siteval = nullptr) {
-  const int n = c->n;
+  const int n = c->nc;
   AdjointArgs aa;
   memset(&aa, 0, sizeof(aa));
+  aa.n_on = c->n;
   aa.cv = cview(c);
   aa.H = c->fp64 ? c->H64.p : c->H32.p;
   aa.HS = c->HS;
@@ -845,7 +928,6 @@ int adjoint_pass(bop_ctx* c, const double* w, void* Hbar, double* Ebar, cudaStre
   aa.Ebar = Ebar;
   if (c->psi_valid) {
     aa.pstore = c->psis.p;
-    aa.pbstore = c->psib.p;
     aa.psi_off = P<long long>(c->psi_off);
     aa.psi_tot = c->psi_tot;
     aa.nc = forward_nc(c);
@@ -1205,8 +1287,8 @@ int bop_destroy(bop_ctx* c) {
                   &c->ginv, &c->hx, &c->hf, &c->gamma, &c->scfred, &c->lbase, &c->lnlev, &c->lflag, &c->lxs,
                   &c->lys, &c->lZ1, &c->lH1, &c->lZ2, &c->lH2, &c->lybar, &c->lcot, &c->lxbar, &c->lcount,
                   &c->rwN, &c->rwt, &c->rdUE, &c->rvec, &c->rcoef, &c->rjv, &c->rjcnt, &c->rjptr, &c->rjidx, &c->rjrow, &c->vgrad, &c->vq, &c->erep,
-                  &c->psi_off, &c->psis, &c->psib, &c->lsum, &c->sdir, &c->vmom, &c->obar, &c->torque,
-                  &c->ncscr, &c->cw_misc, &c->cw_keys, &c->cw_epack};
+                  &c->psi_off, &c->psis, &c->lsum, &c->sdir, &c->vmom, &c->obar, &c->torque,
+                  &c->ncscr, &c->cw_misc, &c->cw_keys, &c->cw_epack, &c->fev};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
@@ -1228,7 +1310,9 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
   if (n < 1 || !pos || !cell || !pbc) return fail(c, BOP_ERR_ARG, "need n >= 1, pos, cell and pbc");
   cudaStream_t s = S_(stream);
   c->built = c->energized = c->weighted = false;
+  if (c->nc_req > n) return fail(c, BOP_ERR_ARG, "%d centres requested for %d atoms", c->nc_req, n);
   c->n = n;
+  c->nc = c->nc_req > 0 ? c->nc_req : n;
   CKS(geometry(c, cell, pbc, &c->g));
   const Geometry& g = c->g;
   CKS(ensure(c, c->pos, sizeof(double) * 3 * n));
@@ -1310,13 +1394,14 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
   CKS(build_clusters(c, s));
   CKS(size_state(c));
   // per-atom row offsets of a stored Psi sweep
-  CKS(ensure(c, c->lsum, sizeof(long long) * (n + 1)));
-  CKS(ensure(c, c->psi_off, sizeof(long long) * (n + 1)));
-  CK(cudaMemsetAsync(c->lsum.p, 0, sizeof(long long) * (n + 1), s));
-  launch_level_sums(n, c->K, P<int>(c->level_end), P<long long>(c->lsum), s);
-  CKS(exclusive_scan(c, P<long long>(c->lsum), P<long long>(c->psi_off), n + 1, s));
+  const int nc = c->nc;
+  CKS(ensure(c, c->lsum, sizeof(long long) * (nc + 1)));
+  CKS(ensure(c, c->psi_off, sizeof(long long) * (nc + 1)));
+  CK(cudaMemsetAsync(c->lsum.p, 0, sizeof(long long) * (nc + 1), s));
+  launch_level_sums(nc, c->K, P<int>(c->level_end), P<long long>(c->lsum), s);
+  CKS(exclusive_scan(c, P<long long>(c->lsum), P<long long>(c->psi_off), nc + 1, s));
   unsigned long long np = 0;
-  CK(cudaMemcpyAsync(&c->psi_tot, P<long long>(c->psi_off) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&c->psi_tot, P<long long>(c->psi_off) + nc, sizeof(long long), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&np, c->nprod.p, sizeof(np), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   c->psi_valid = false;
@@ -1344,7 +1429,7 @@ int bop_get_neighbors(bop_ctx* c, long long* row_ptr, int* col, signed char* img
 
 int bop_get_cluster(bop_ctx* c, int atom, int* site_atom, signed char* site_img, int* level_end, bop_stream stream) {
   if (!c || !c->built) return fail(c, BOP_ERR_STATE, "no structure built");
-  if (atom < 0 || atom >= c->n) return fail(c, BOP_ERR_ARG, "atom index out of range");
+  if (atom < 0 || atom >= c->nc) return fail(c, BOP_ERR_ARG, "atom index out of range (clusters of the centres)");
   cudaStream_t s = S_(stream);
   long long s0 = 0;
   int lev[BOP_MAX_K + 1];
@@ -1376,7 +1461,7 @@ int bop_moments(bop_ctx* c, const double* onsite, double* mu, bop_stream stream)
   if (!c || !c->built) return fail(c, BOP_ERR_STATE, "no structure built");
   if (!mu) return fail(c, BOP_ERR_ARG, "mu is NULL");
   cudaStream_t s = S_(stream);
-  const size_t M = (size_t)c->S * c->n * c->norb;
+  const size_t M = (size_t)c->S * c->n * c->norb;  // onsite levels of every atom
   if (onsite) {
     CK(cudaMemcpyAsync(c->onsite.p, onsite, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
     Region R(c, PK_ONSITE, 1, s);
@@ -1431,8 +1516,10 @@ int bop_recursion(bop_ctx* c, int M, const double* mu, double* a, double* b, int
 
 int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_stats* st, bop_stream stream) {
   if (!c || !c->built) return fail(c, BOP_ERR_STATE, "no structure built");
+  if ((c->reduce_fn || c->nc < c->n) && (c->m.scf != BOP_SCF_NONE || c->m.noncollinear))
+    return fail(c, BOP_ERR_ARG, "a spatial domain (centres or a reduce function) needs scf NONE, collinear");
   cudaStream_t s = S_(stream);
-  const int n = c->n, M = c->S * n * c->norb;
+  const int n = c->n, nc = c->nc, M = c->S * nc * c->norb;
   c->energized = c->weighted = false;
   c->psi_valid = false;
   c->var_w_valid = false;
@@ -1564,11 +1651,13 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   }
   {
   Region Re(c, PK_ENERGY, 1, s);
-  if (launch_energy(n, c->norb, c->S, c->sfac, c->m.stoner_I, P<double>(c->U), magnetic ? P<double>(c->mval) : nullptr,
+  double* ea = e_atom ? e_atom : P<double>(c->e_atom);
+  if (launch_energy(nc, c->norb, c->S, c->sfac, c->m.stoner_I, P<double>(c->U), magnetic ? P<double>(c->mval) : nullptr,
                     c->m.j_ii, variational ? P<double>(c->N) : nullptr, c->m.n_e, rep ? P<double>(c->erep) : nullptr,
-                    e_atom ? e_atom : P<double>(c->e_atom), P<double>(c->partials), P<unsigned>(c->counter),
-                    P<double>(c->e_total), s))
+                    ea, P<double>(c->partials), P<unsigned>(c->counter), P<double>(c->e_total), s))
     return fail(c, BOP_ERR_CUDA, "energy launch failed");
+  // environment atoms of a spatial domain carry no energy of their own
+  if (nc < n) CK(cudaMemsetAsync(ea + nc, 0, sizeof(double) * (size_t)(n - nc), s));
   }
   if (delta_io) CK(cudaMemcpyAsync(delta_io, c->delta.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   if (m_io && magnetic) CK(cudaMemcpyAsync(m_io, c->mval.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -1577,6 +1666,7 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   CK(cudaMemcpyAsync(&et, c->e_total.p, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(nl, c->lcount.p, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CKS(check_status(c, s));
+  CKS(reduce_over_ranks(c, &et, 1, BOP_REDUCE_SUM));  // the whole structure's energy
   c->ef_solved = true;
   c->st.n_learned = (int)nl[0];
   c->st.n_unbounded = (int)nl[1];
@@ -1598,14 +1688,14 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
 int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_stream stream) {
   if (!c || !c->built || !c->energized) return fail(c, BOP_ERR_STATE, "bop_forces needs a preceding bop_energy");
   cudaStream_t s = S_(stream);
-  const int n = c->n, M = c->S * n * c->norb;
+  const int n = c->n, M = c->S * c->nc * c->norb;
   CKS(ensure(c, c->w, sizeof(double) * (size_t)M * c->n_mom));
   CKS(ensure(c, c->zscr, sizeof(double) * (size_t)M * (c->n_exp + 1) * 2));
   // bond cotangents in the product type (FP32: float4 reductions)
   const size_t hbar_bytes = (c->fp64 ? sizeof(double) : sizeof(float)) * (size_t)(c->nb > 0 ? c->nb : 1) *
                             bond_cotangent_stride(c->norb, c->fp64);
   CKS(ensure(c, c->Hbar, hbar_bytes));
-  CKS(ensure(c, c->Ebar, sizeof(double) * (size_t)M));
+  CKS(ensure(c, c->Ebar, sizeof(double) * (size_t)c->S * n * c->norb));  // onsite cotangents of every atom
   CK(cudaMemsetAsync(c->Hbar.p, 0, hbar_bytes, s));
   CKS(prepare_psi_store(c, s));
   int solve_status = BOP_OK;
@@ -1629,6 +1719,16 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
                              P<double>(c->partials), P<unsigned>(c->counter), P<double>(c->lam), s))
         return fail(c, BOP_ERR_CUDA, "E_F response launch failed");
     }
+    if (c->reduce_fn) {
+      // one E_F for all processes: its multiplier from the sums of all of them
+      double l[3];
+      CK(cudaMemcpyAsync(l, c->lam.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      CKS(reduce_over_ranks(c, l + 1, 2, BOP_REDUCE_SUM));
+      l[0] = l[2] > 0.0 ? l[1] / l[2] : 0.0;
+      CK(cudaMemcpyAsync(c->lam.p, l, 3 * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cudaStreamSynchronize(s));
+    }
     CKS(compute_weights(c, c->sfac, P<double>(c->lam), 0.0, P<double>(c->w), nullptr, s));
     if (c->m.noncollinear) {
       // reverse sweep of the spinor moments: bond and onsite-matrix
@@ -1651,7 +1751,7 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
                          P<double>(c->vmom), P<double>(c->obar), P<double>(c->torque), s))
         return fail(c, BOP_ERR_CUDA, "torques launch failed");
     } else {
-      CK(cudaMemsetAsync(c->Ebar.p, 0, sizeof(double) * (size_t)M, s));
+      CK(cudaMemsetAsync(c->Ebar.p, 0, sizeof(double) * (size_t)c->S * n * c->norb, s));
       CKS(adjoint_pass(c, P<double>(c->w), c->Hbar.p, P<double>(c->Ebar), s));
     }
   }
@@ -1727,7 +1827,7 @@ int bop_get_orbital_state(bop_ctx* c, double* mu, double* N, double* U, double* 
                           double* weights, double* onsite, bop_stream stream) {
   if (!c || !c->energized) return fail(c, BOP_ERR_STATE, "no energy computed");
   cudaStream_t s = S_(stream);
-  const size_t M = (size_t)c->S * c->n * c->norb;
+  const size_t M = (size_t)c->S * c->nc * c->norb;
   if (mu) CK(cudaMemcpyAsync(mu, c->mu.p, sizeof(double) * M * c->n_mom, cudaMemcpyDeviceToDevice, s));
   if (N) CK(cudaMemcpyAsync(N, c->N.p, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
   if (U) CK(cudaMemcpyAsync(U, c->U.p, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
@@ -1773,6 +1873,20 @@ int bop_evaluate_host(bop_ctx* c, int n, const double* pos_host, const double* c
   return r;
 }
 
+int bop_set_centers(bop_ctx* c, int n_centers) {
+  if (!c) return BOP_ERR_ARG;
+  if (n_centers < 0) return fail(c, BOP_ERR_ARG, "n_centers must be >= 0");
+  c->nc_req = n_centers;
+  return BOP_OK;
+}
+
+int bop_set_reduce(bop_ctx* c, bop_reduce_fn fn, void* user) {
+  if (!c) return BOP_ERR_ARG;
+  c->reduce_fn = fn;
+  c->reduce_user = user;
+  return BOP_OK;
+}
+
 int bop_set_response_limits(bop_ctx* c, int max_iterations, double rtol) {
   if (!c) return BOP_ERR_ARG;
   if (max_iterations < 0 || !(rtol >= 0.0) || !std::isfinite(rtol))
@@ -1786,7 +1900,7 @@ int bop_set_store_budget(bop_ctx* c, long long bytes) {
   if (!c) return BOP_ERR_ARG;
   c->store_budget = bytes < 0 ? (size_t)-1 : (size_t)bytes;
   if (c->store_budget == 0) {
-    for (DBuf* b : {&c->psis, &c->psib})
+    for (DBuf* b : {&c->psis})
       if (b->p) {
         cudaFree(b->p);
         b->p = nullptr;

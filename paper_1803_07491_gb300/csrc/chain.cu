@@ -242,6 +242,68 @@ __global__ void __launch_bounds__(RT2) k_fermi_newton(int M, const double* __res
   }
 }
 
+// Pieces of a Fermi-level solve whose sums span several processes (a
+// spatial domain per rank): mode 0 writes out = {-min(a_inf - 2 b_inf),
+// max(a_inf + 2 b_inf)} over the orbitals, mode 1 writes out = {sum_o N_o(E),
+// sum_o n_o(E)} (the DOS per energy, as k_fermi_newton), both for this
+// process's orbitals; the caller reduces them over the processes.
+__global__ void __launch_bounds__(RT2) k_fermi_eval(int mode, int M, int ne, const double* __restrict__ gsig,
+                                                    const double* __restrict__ inv, const double* __restrict__ a_inf,
+                                                    const double* __restrict__ b_inf, double E, double* partials,
+                                                    unsigned* counter, double* out) {
+  __shared__ double sh[RT2 / 32];
+  __shared__ bool last;
+  double v0 = mode == 0 ? -1e300 : 0.0, v1 = mode == 0 ? -1e300 : 0.0;
+  for (int o = blockIdx.x * RT2 + threadIdx.x; o < M; o += gridDim.x * RT2) {
+    const double ai = a_inf[o], bi = b_inf[o];
+    if (mode == 0) {
+      v0 = fmax(v0, -(ai - 2.0 * bi));
+      v1 = fmax(v1, ai + 2.0 * bi);
+    } else {
+      const double xr = (E - ai) / (2.0 * bi);
+      double N, dN;
+      count_and_dos(gsig, inv, M, o, ne, clamp1(xr), &N, &dN);
+      v0 += N;
+      if (xr > -1.0 && xr < 1.0) v1 += dN / (2.0 * bi);
+    }
+  }
+  double b0, b1;
+  if (mode == 0) {
+    __shared__ double smx[2][RT2];
+    smx[0][threadIdx.x] = v0;
+    smx[1][threadIdx.x] = v1;
+    __syncthreads();
+    for (int w = RT2 / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) {
+        smx[0][threadIdx.x] = fmax(smx[0][threadIdx.x], smx[0][threadIdx.x + w]);
+        smx[1][threadIdx.x] = fmax(smx[1][threadIdx.x], smx[1][threadIdx.x + w]);
+      }
+      __syncthreads();
+    }
+    b0 = smx[0][0];
+    b1 = smx[1][0];
+  } else {
+    b0 = block_sum<RT2>(v0, sh);
+    b1 = block_sum<RT2>(v1, sh);
+  }
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = b0;
+    partials[2 * blockIdx.x + 1] = b1;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __shared__ double fr[RT2 / 32 + 1];
+  const double t0 = final_reduce<RT2>(partials, 2, 0, gridDim.x, mode == 0, fr);
+  const double t1 = final_reduce<RT2>(partials, 2, 1, gridDim.x, mode == 0, fr);
+  if (threadIdx.x == 0) {
+    out[0] = t0;
+    out[1] = t1;
+    *counter = 0;
+  }
+}
+
 // N and DOS (per energy) of every orbital at E_F.
 __global__ void __launch_bounds__(RT2) k_orbital_N(int M, int ne, const double* __restrict__ gsig,
                                                    const double* __restrict__ inv, const double* __restrict__ a_inf,
@@ -692,6 +754,13 @@ int launch_weights_pair(const WeightArgs& a, double cU1, double cN1, double cU2,
     case 8: k_weights_split<8><<<g, CT, 0, s>>>(a, cU1, cN1, cU2, cN2, w2); break;
     default: return -1;
   }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_fermi_eval(int mode, int M, const double* gsig, const double* inv, const double* a_inf,
+                      const double* b_inf, int n_exp, double E, double* partials, unsigned* counter, double* out,
+                      cudaStream_t s) {
+  k_fermi_eval<<<red_grid2(M), RT2, 0, s>>>(mode, M, n_exp, gsig, inv, a_inf, b_inf, E, partials, counter, out);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

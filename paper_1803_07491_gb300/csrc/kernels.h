@@ -88,8 +88,9 @@ struct MomentsArgs {
   ClusterView cv;
   const void* H;       // float or double [nb][HS]
   int HS;
-  const void* onsite;  // float or double [S][n][norb]
-  int n, n_spin, norb, n_mom;
+  const void* onsite;  // float or double [S][n_on][norb]
+  int n, n_spin, norb, n_mom;  // n: atoms with clusters (centers), the first n of the structure
+  int n_on;            // atoms of the structure (stride of the onsite levels)
   int cap_even;        // largest stored even level |C_k| (k < K) over atoms
   int cap_odd;         // largest stored odd level |C_k| (k < K) over atoms
   int max_sites;       // largest cluster |C_K|
@@ -108,18 +109,18 @@ struct AdjointArgs {
   ClusterView cv;
   const void* H;
   int HS;
-  const void* onsite;
-  int n, n_spin, norb, n_mom;
+  const void* onsite;  // [S][n_on][norb]
+  int n, n_spin, norb, n_mom;  // n: centers, as MomentsArgs
+  int n_on;            // atoms of the structure (stride of onsite and Ebar)
   const double* w;     // [S][n][norb][n_mom]
   void* scratch;       // per-CTA Psi / Psi-bar storage
   size_t slot_elems;   // elements of T per CTA
   int slots;
   void* Hbar;          // [nb][HSh] (+=), the product type T (bond_cotangent_stride)
   int HSh;
-  double* Ebar;        // [S][n][norb] (+=), may be null
+  double* Ebar;        // [S][n_on][norb] (+=), may be null
   // reverse sweep over stored Psi (pstore != NULL; layout of MomentsArgs.pstore)
   const void* pstore;
-  void* pbstore;       // Psi-bar store, same layout (needed when Hbar != NULL)
   const long long* psi_off;
   long long psi_tot;
   int nc;              // columns per work item used by the forward pass that stored Psi
@@ -196,6 +197,12 @@ int launch_fermi(int M, const double* D, const double* gsig, const double* a_inf
                  double spin_factor, double target, FermiState* st, double* partials, unsigned* counter,
                  int max_rounds, double tol, cudaStream_t s);
 
+// One piece of a Fermi-level solve spread over several processes (chain.cu):
+// mode 0: out = {-min(a_inf - 2 b_inf), max(a_inf + 2 b_inf)}; mode 1: out =
+// {sum N_o(E), sum n_o(E)} over this process's M orbitals (out device [2]).
+int launch_fermi_eval(int mode, int M, const double* gsig, const double* inv, const double* a_inf,
+                      const double* b_inf, int n_exp, double E, double* partials, unsigned* counter, double* out,
+                      cudaStream_t s);
 int launch_orbital_NU(int M, int n_exp, const double* gsig, const double* inv, const double* a_inf,
                       const double* b_inf, const double* onsite, const FermiState* st, double* N, double* U,
                       double* dos, cudaStream_t s);

@@ -320,6 +320,54 @@ __device__ __forceinline__ void gather_pf2(const int2* __restrict__ ent, int cnt
   }
 }
 
+// The reverse sweep's gather with the bond cotangents of the same pairs:
+// for each entry s of row t (t in C_{k-1}, s in C_k), acc += B_ts x[s]
+// (when gather is set) and dL/dB of the forward pair (s, t), x[s] pt^T
+// summed over the columns (x = Psi-bar_k, pt = Psi_k-1(t)), goes to the
+// bond's unique elements; the blocks of the next two entries are in flight.
+template <typename T, int NO, int NC, int PS>
+__device__ __forceinline__ void gather_cot(const int2* __restrict__ ent, int cnt, const T* __restrict__ H, int HS,
+                                           const T* __restrict__ x, T acc[NO][NC], bool gather, const T pt[NO * NC],
+                                           T* __restrict__ Hbar, int HSh) {
+  constexpr int HB = hb_count<NO>();
+  constexpr int N = NO * NC;
+  if (cnt <= 0) return;
+  int2 e0 = ent[0];
+  int2 e1 = cnt > 1 ? ent[1] : e0;
+  T h0[HB], h1[HB];
+  if (gather) {
+    load_bond<T, NO>(H + (size_t)e0.y * HS, h0);
+    if (cnt > 1) load_bond<T, NO>(H + (size_t)e1.y * HS, h1);
+  }
+  for (int e = 0; e < cnt; e++) {
+    const int sidx = e0.x, bond = e0.y;
+    T hc[HB];
+#pragma unroll
+    for (int q = 0; q < HB; q++) hc[q] = h0[q];
+    e0 = e1;
+#pragma unroll
+    for (int q = 0; q < HB; q++) h0[q] = h1[q];
+    if (e + 2 < cnt) {
+      e1 = ent[e + 2];
+      if (gather) load_bond<T, NO>(H + (size_t)e1.y * HS, h1);
+    }
+    T xs[N];
+    load_row<T, N, PS>(x + (size_t)sidx * PS, xs);
+    if (gather) block_fma<T, NO, NC>(hc, xs, acc);
+    T G[NO][NO];
+#pragma unroll
+    for (int b = 0; b < NO; b++)
+#pragma unroll
+      for (int g = 0; g < NO; g++) {
+        T a = T(0);
+#pragma unroll
+        for (int c = 0; c < NC; c++) a += xs[b * NC + c] * pt[g * NC + c];
+        G[b][g] = a;
+      }
+    add_bond_cotangent<T, NO>(Hbar + (size_t)bond * HSh, G);
+  }
+}
+
 // Forward kernel.  A persistent CTA takes a run of consecutive work items
 // (spin, atom[, alpha]); neighbouring atoms share most of their clusters'
 // blocks, which then come from L1.  For each item the atom's adjacency,
@@ -338,8 +386,8 @@ struct FwdSmem {
 
 template <typename T, int NO, int NC>
 __global__ void __launch_bounds__(FWD_THREADS, sizeof(T) == 4 ? 2 : 1)
-k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_mom,
-          FwdSmem L, int n_items, int chunk, double* __restrict__ mu, T* __restrict__ pstore,
+k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_on,
+          int n_mom, FwdSmem L, int n_items, int chunk, double* __restrict__ mu, T* __restrict__ pstore,
           const long long* __restrict__ psi_off, long long psi_tot) {
   constexpr int N = NO * NC;
   constexpr int PS = (N == 1) ? 1 : Row<T, N>::PS;
@@ -368,7 +416,7 @@ k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
     const int2* adj = cv.adj + abase;
     const unsigned long long* lvc = cv.lvcnt + s0;
     const int* satom = cv.site_atom + s0;
-    const T* E = onsite + (size_t)spin * n * NO;
+    const T* E = onsite + (size_t)spin * n_on * NO;
     if (L.stage) {
       const int nadj = (int)(cv.adj_off[s0 + nsite] - abase);
       for (int q = tid; q < nadj; q += FWD_THREADS) s_adj[q] = __ldg(adj + q);
@@ -488,9 +536,11 @@ k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
 // buffers (even / odd levels), the adjacency staged, one site row per
 // thread.  The onsite cotangents dL/dE_t = sum_k Psi-bar_k[t] . Psi_k-1[t]
 // are accumulated per site in shared memory and added once per item.
-// With HBAR the Psi-bar levels are also stored, and the bond cotangents
-// sum_k Psi-bar_k(t) Psi_k-1(s)^T are formed per cluster edge from the two
-// stores and added to the bond's unique elements with FP64 atomics.
+// With HBAR the gather of level k also forms the bond cotangents of its
+// pairs, Psi-bar_k(s) Psi_k-1(t)^T for the forward pair (s in C_k, t in
+// C_{k-1}) (Psi-bar_k(s) is the gather's operand, Psi_k-1(t) one stored row
+// per site), and adds them to the bond's unique elements (gather_cot); at
+// k = 1 only these products run.
 struct RevSmem {
   int cap_even, cap_odd, max_sites, max_adj, cap_eb;
   bool stage;
@@ -503,8 +553,9 @@ __host__ __device__ constexpr size_t eb_elems(int cap_eb) {
 
 template <typename T, int NO, int NC, bool HBAR>
 __global__ void __launch_bounds__(FWD_THREADS, sizeof(T) == 4 ? 2 : 1)
-k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_mom,
-          RevSmem L, int n_items, int chunk, const T* __restrict__ pstore, T* __restrict__ pbstore,
+k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_on,
+          int n_mom,
+          RevSmem L, int n_items, int chunk, const T* __restrict__ pstore,
           const long long* __restrict__ psi_off, long long psi_tot, const double* __restrict__ wts,
           T* __restrict__ Hbar, int HSh, double* __restrict__ Ebar, double* __restrict__ siteval,
           long long sv_stride) {
@@ -538,10 +589,9 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
     const int2* adj = cv.adj + abase;
     const unsigned long long* lvc = cv.lvcnt + s0;
     const int* satom = cv.site_atom + s0;
-    const T* E = onsite + (size_t)spin * n * NO;
+    const T* E = onsite + (size_t)spin * n_on * NO;
     const size_t ib = ((size_t)(spin * (NO / NC) + grp) * psi_tot + psi_off[atom]) * PS;
     const T* P = pstore + ib;
-    T* PB = HBAR ? pbstore + ib : nullptr;
     if (L.stage) {
       const int nadj = (int)(cv.adj_off[s0 + nsite] - abase);
       for (int q = tid; q < nadj; q += FWD_THREADS) s_adj[q] = __ldg(adj + q);
@@ -581,7 +631,6 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
           for (int q = 0; q < N; q++) row[q] += ws[q % NC][2 * K - 1] * pk1[q];
         }
         store_row<T, N, PS>(xb + (size_t)t * PS, row);
-        if (HBAR) store_row<T, N, PS>(PB + (size_t)(s_lo[K] + t) * PS, row);
       }
     }
     __syncthreads();
@@ -608,6 +657,8 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
 #pragma unroll
             for (int c = 0; c < NC; c++) acc[r][c] = er * xt[r * NC + c];
           }
+        }
+        if (k >= 2 || HBAR) {
           int cnt;
           if (k < K) {
             const unsigned long long lc = L.stage ? s_lvc[t] : lvc[t];
@@ -617,7 +668,15 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
           }
           if (cnt > 0) {
             const int q0 = L.stage ? s_aoff[t] : (int)(cv.adj_off[s0 + t] - abase);
-            gather_pf2<T, NO, NC, PS>(L.stage ? s_adj + q0 : adj + q0, cnt, H, HS, xb, acc);
+            const int2* ents = L.stage ? s_adj + q0 : adj + q0;
+            if constexpr (HBAR) {
+              // with the bond cotangents of the forward pairs (s, t) of level k
+              T pt[N];
+              load_row<T, N, PS>(r1, pt);
+              gather_cot<T, NO, NC, PS>(ents, cnt, H, HS, xb, acc, k >= 2, pt, Hbar, HSh);
+            } else {
+              gather_pf2<T, NO, NC, PS>(ents, cnt, H, HS, xb, acc);
+            }
           }
         }
         // onsite cotangent of level k: Psi-bar_k[t] . Psi_k-1[t] (rows read after the gather)
@@ -652,7 +711,6 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
             for (int q = 0; q < N; q++) row[q] += ws[q % NC][2 * k - 3] * p2[q];
           }
           store_row<T, N, PS>(yb + (size_t)t * PS, row);
-          if (HBAR) store_row<T, N, PS>(PB + (size_t)(s_lo[k - 1] + t) * PS, row);
         }
       }
       __syncthreads();
@@ -660,7 +718,7 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
     if (Ebar != nullptr) {
       for (int q = tid; q < neb * NO; q += FWD_THREADS) {
         const int t = q / NO, r = q % NO;
-        atomicAdd(Ebar + ((size_t)spin * n + (L.stage ? s_atom[t] : satom[t])) * NO + r, (double)eb[q]);
+        atomicAdd(Ebar + ((size_t)spin * n_on + (L.stage ? s_atom[t] : satom[t])) * NO + r, (double)eb[q]);
       }
     }
     if (siteval != nullptr) {  // per-site sums over the orbitals (one row of the SCF Jacobian)
@@ -669,43 +727,6 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
 #pragma unroll
         for (int r = 0; r < NO; r++) a += (double)eb[t * NO + r];
         atomicAdd(siteval + (size_t)spin * sv_stride + s0 + t, a);
-      }
-    }
-    if (HBAR) {
-      // bond cotangents from the two stores (the item's rows were written by this CTA)
-      for (int t = tid; t < s_lev[K]; t += FWD_THREADS) {
-        int lt = 0;
-        while (lt < K && t >= s_lev[lt]) lt++;
-        const int q0 = L.stage ? s_aoff[t] : (int)(cv.adj_off[s0 + t] - abase);
-        const int q1 = L.stage ? s_aoff[t + 1] : (int)(cv.adj_off[s0 + t + 1] - abase);
-        for (int q = q0; q < q1; q++) {
-          const int2 en = L.stage ? s_adj[q] : adj[q];
-          const int sidx = en.x;
-          if (sidx >= s_lev[K - 1]) break;
-          int ls = 0;
-          while (ls < K && sidx >= s_lev[ls]) ls++;
-          const int kmin = lt > ls + 1 ? lt : ls + 1;
-          T G[NO][NO];
-#pragma unroll
-          for (int b = 0; b < NO; b++)
-#pragma unroll
-            for (int g = 0; g < NO; g++) G[b][g] = T(0);
-          for (int k = kmin; k <= K; k++) {
-            T pb[N], ps[N];
-            load_row<T, N, PS>(PB + (size_t)(s_lo[k] + t) * PS, pb);
-            load_row<T, N, PS>(P + (size_t)(s_lo[k - 1] + sidx) * PS, ps);
-#pragma unroll
-            for (int b = 0; b < NO; b++)
-#pragma unroll
-              for (int g = 0; g < NO; g++) {
-                T a = T(0);
-#pragma unroll
-                for (int c = 0; c < NC; c++) a += pb[b * NC + c] * ps[g * NC + c];
-                G[b][g] += a;
-              }
-          }
-          add_bond_cotangent<T, NO>(Hbar + (size_t)en.y * HSh, G);
-        }
       }
     }
     __syncthreads();
@@ -721,7 +742,7 @@ __device__ __forceinline__ int site_level(const int* lev, int K, int t) {
 
 template <typename T, int NO, int NC>
 __global__ void __launch_bounds__(MOM_THREADS)
-k_moments_adj(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_mom,
+k_moments_adj(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__ onsite, int n, int n_on, int n_mom,
               int nwork, const double* __restrict__ wts, T* __restrict__ scratch, size_t slot_elems,
               T* __restrict__ Hbar, int HSh, double* __restrict__ Ebar) {
   __shared__ T ws[NC][BOP_MAX_NMOM];
@@ -738,7 +759,7 @@ k_moments_adj(ClusterView cv, const T* __restrict__ H, int HS, const T* __restri
     const int* lev = cv.level_end + (size_t)atom * (K + 1);
     const int* satom = cv.site_atom + s0;
     const long long* aoff = cv.adj_off + s0;
-    const T* E = onsite + (size_t)spin * n * NO;
+    const T* E = onsite + (size_t)spin * n_on * NO;
     if (tid <= K) s_lev[tid] = lev[tid];
     if (tid == 0) {  // Psi_k at s_off[k], Psi-bar_k at s_off[K+1] + (s_off[k] - s_off[1])
       long long o = 0;
@@ -855,7 +876,7 @@ k_moments_adj(ClusterView cv, const T* __restrict__ H, int HS, const T* __restri
           }
         }
         if (lt + 1 <= K) {
-          double* ep = Ebar + ((size_t)spin * n + satom[t]) * NO;
+          double* ep = Ebar + ((size_t)spin * n_on + satom[t]) * NO;
 #pragma unroll
           for (int b = 0; b < NO; b++) atomicAdd(ep + b, eb[b]);
         }
@@ -1334,8 +1355,8 @@ int run_forward(const MomentsArgs& a, cudaStream_t s) {
   const int slots = sms * per_sm;
   const int chunk = (n_items + slots - 1) / slots;
   const int grid = (n_items + chunk - 1) / chunk;
-  fn<<<grid, FWD_THREADS, smem, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n, a.n_mom, L, n_items,
-                                      chunk, a.mu, (T*)a.pstore, a.psi_off, a.psi_tot);
+  fn<<<grid, FWD_THREADS, smem, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n, a.n_on, a.n_mom, L,
+                                      n_items, chunk, a.mu, (T*)a.pstore, a.psi_off, a.psi_tot);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -1343,7 +1364,7 @@ template <typename T, int NO, int NC>
 int run_adjoint(const AdjointArgs& a, cudaStream_t s) {
   int nwork = a.n * a.n_spin * (NO / NC);
   int grid = nwork < a.slots ? nwork : a.slots;
-  k_moments_adj<T, NO, NC><<<grid, MOM_THREADS, 0, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n,
+  k_moments_adj<T, NO, NC><<<grid, MOM_THREADS, 0, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n, a.n_on,
                                                        a.n_mom, nwork, a.w, (T*)a.scratch, a.slot_elems,
                                                        (T*)a.Hbar, a.HSh, a.Ebar);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -1382,8 +1403,9 @@ int run_reverse(const AdjointArgs& a, cudaStream_t s) {
   const int slots = sms * per_sm;
   const int chunk = (n_items + slots - 1) / slots;
   const int grid = (n_items + chunk - 1) / chunk;
-  fn<<<grid, FWD_THREADS, smem, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n, a.n_mom, L, n_items, chunk,
-                                      (const T*)a.pstore, (T*)a.pbstore, a.psi_off, a.psi_tot, a.w, (T*)a.Hbar, a.HSh,
+  fn<<<grid, FWD_THREADS, smem, s>>>(a.cv, (const T*)a.H, a.HS, (const T*)a.onsite, a.n, a.n_on, a.n_mom, L, n_items,
+                                      chunk,
+                                      (const T*)a.pstore, a.psi_off, a.psi_tot, a.w, (T*)a.Hbar, a.HSh,
                                       a.Ebar, a.siteval, a.sv_stride);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
