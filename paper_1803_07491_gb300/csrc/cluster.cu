@@ -313,15 +313,18 @@ k_cluster(int n, int K, const long long* __restrict__ row_ptr, const int* __rest
 // writes the sites, the sorted adjacency and the level counts.  Clusters of
 // more than CW_MAXS sites, or atoms with more than MAXD neighbours, raise
 // *wfail and the caller falls back to the block builder above.
-constexpr int CW_WARPS = 4;   // warps per CTA
+constexpr int CW_WARPS = 3;   // warps per CTA (five CTAs of 14 KB per warp fit an SM)
 constexpr int CW_MAXS = 512;  // sites of one cluster
+constexpr int CW_NB = 256;    // new sites of one level
 constexpr int CW_HC = 1024;   // hash slots per warp (a power of two, 2 CW_MAXS)
+// A hash entry is the 48-bit site key with the site's local index + 1 in
+// the top 16 bits (0 while the index is not yet assigned).
+constexpr unsigned long long CW_KEY = (1ull << 48) - 1;
 
 struct CwSmem {
   unsigned long long hk[CW_HC];
   unsigned long long sk[CW_MAXS];  // site keys in canonical order
-  unsigned long long nb[CW_MAXS];  // new keys of one level
-  unsigned short hv[CW_HC];        // local index of every stored key
+  unsigned long long nb[CW_NB];    // new keys of one level
   int lev[BOP_MAX_K + 1];
   int cnt, fail;
 };
@@ -330,19 +333,24 @@ __device__ __forceinline__ int cw_find(const unsigned long long* hk, unsigned lo
   unsigned s = hash_slot(key, CW_HC - 1);
   for (int probe = 0; probe < CW_HC; probe++) {
     const unsigned long long c = hk[s];
-    if (c == key) return (int)s;
     if (c == EMPTY) return -1;
+    if ((c & CW_KEY) == key) return (int)s;
     s = (s + 1) & (CW_HC - 1);
   }
   return -1;
 }
 
-// 1: inserted, 0: present, -1: full.  slot receives the key's slot.
+__device__ __forceinline__ int cw_index(const unsigned long long* hk, int slot) {
+  return (int)(hk[slot] >> 48) - 1;
+}
+
+// 1: inserted (index unassigned), 0: present, -1: full.  slot receives the
+// key's slot.
 __device__ __forceinline__ int cw_insert(unsigned long long* hk, unsigned long long key, int* slot) {
   unsigned s = hash_slot(key, CW_HC - 1);
   for (int probe = 0; probe < CW_HC; probe++) {
     const unsigned long long c = hk[s];
-    if (c == key) {
+    if (c != EMPTY && (c & CW_KEY) == key) {
       *slot = (int)s;
       return 0;
     }
@@ -352,7 +360,7 @@ __device__ __forceinline__ int cw_insert(unsigned long long* hk, unsigned long l
         *slot = (int)s;
         return 1;
       }
-      if (prev == key) {
+      if ((prev & CW_KEY) == key) {
         *slot = (int)s;
         return 0;
       }
@@ -360,6 +368,30 @@ __device__ __forceinline__ int cw_insert(unsigned long long* hk, unsigned long l
     s = (s + 1) & (CW_HC - 1);
   }
   return -1;
+}
+
+// Ascending bitonic sort of a[0..cnt) by one warp, padded with EMPTY to the
+// next power of two (at most CW_NB).
+__device__ __forceinline__ void cw_sort(unsigned long long* a, int cnt, int lane) {
+  int P = 1;
+  while (P < cnt) P <<= 1;
+  for (int i = cnt + lane; i < P; i += 32) a[i] = EMPTY;
+  __syncwarp();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < P; i += 32) {
+        const int l = i ^ j;
+        if (l > i) {
+          const unsigned long long x = a[i], y = a[l];
+          const bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
 }
 
 // Image of a packed edge record: byte c of y holds image component c + 128.
@@ -390,7 +422,7 @@ k_cluster_warp(int n, int K, const long long* __restrict__ row_ptr, const int2* 
         const unsigned long long k0 = site_key(atom, 0, 0, 0);
         int sl = 0;
         cw_insert(sm.hk, k0, &sl);
-        sm.hv[sl] = 0;
+        sm.hk[sl] = k0 | (1ull << 48);
         sm.sk[0] = k0;
         sm.lev[0] = 1;
       }
@@ -431,7 +463,7 @@ k_cluster_warp(int n, int K, const long long* __restrict__ row_ptr, const int2* 
             const int r = cw_insert(sm.hk, key, &sl);
             if (r == 1) {
               const int q = atomicAdd(&sm.cnt, 1);
-              if (q < CW_MAXS) sm.nb[q] = key;
+              if (q < CW_NB) sm.nb[q] = key;
             } else if (r < 0) {
               sm.fail = 1;
             }
@@ -439,17 +471,16 @@ k_cluster_warp(int n, int K, const long long* __restrict__ row_ptr, const int2* 
         }
         __syncwarp();
         const int cnt = sm.cnt;
-        if (cnt > CW_MAXS - nsite) sm.fail = 1;
+        if (cnt > CW_NB || cnt > CW_MAXS - nsite) sm.fail = 1;
         __syncwarp();
         if (sm.fail) break;
-        // canonical order inside the level: rank of every new key among them
+        // canonical order inside the level: the new keys sorted
+        cw_sort(sm.nb, cnt, lane);
         for (int q = lane; q < cnt; q += 32) {
           const unsigned long long key = sm.nb[q];
-          int r = 0;
-          for (int p = 0; p < cnt; p++) r += sm.nb[p] < key ? 1 : 0;
-          sm.sk[nsite + r] = key;
+          sm.sk[nsite + q] = key;
           const int sl = cw_find(sm.hk, key);
-          sm.hv[sl >= 0 ? sl : 0] = (unsigned short)(nsite + r);
+          if (sl >= 0) sm.hk[sl] = key | ((unsigned long long)(nsite + q + 1) << 48);
         }
         __syncwarp();
         nsite += cnt;
@@ -479,7 +510,7 @@ k_cluster_warp(int n, int K, const long long* __restrict__ row_ptr, const int2* 
         sm.sk[t] = key;
         int sl = 0;
         cw_insert(sm.hk, key, &sl);
-        sm.hv[sl] = (unsigned short)t;
+        sm.hk[sl] = key | ((unsigned long long)(t + 1) << 48);
       }
       __syncwarp();
     }
@@ -503,25 +534,34 @@ k_cluster_warp(int n, int K, const long long* __restrict__ row_ptr, const int2* 
           atomicOr(wfail, 2);
           deg = MAXD;
         }
-        int2 pe[MAXD];
-        int bnd[MAXD];
+        // without a path cut every neighbour of a site within K-1 hops is in
+        // the cluster: pass 0 counts those without looking them up
+        const bool inner = !CUT && PASS == 0 && t < sm.lev[K > 0 ? K - 1 : 0] && K > 0;
+        if (inner) {
+          c = deg;
 #pragma unroll
-        for (int j = 0; j < MAXD; j++) {
-          if (j < deg) {
-            pe[j] = __ldg(epack + e0 + j);
-            bnd[j] = PASS == 1 ? __ldg(bond_of_edge + e0 + j) : 0;
+          for (int j = 0; j < MAXD; j++) ent[j] = ~0ull;
+        } else {
+          int2 pe[MAXD];
+          int bnd[MAXD];
+#pragma unroll
+          for (int j = 0; j < MAXD; j++) {
+            if (j < deg) {
+              pe[j] = __ldg(epack + e0 + j);
+              bnd[j] = PASS == 1 ? __ldg(bond_of_edge + e0 + j) : 0;
+            }
           }
-        }
 #pragma unroll
-        for (int j = 0; j < MAXD; j++) {
-          ent[j] = ~0ull;
-          if (j < deg) {
-            const int sx = ix + epk_img(pe[j].y, 0), sy = iy + epk_img(pe[j].y, 1), sz = iz + epk_img(pe[j].y, 2);
-            if (sx >= -127 && sx <= 127 && sy >= -127 && sy <= 127 && sz >= -127 && sz <= 127) {
-              const int sl = cw_find(sm.hk, site_key(pe[j].x, sx, sy, sz));
-              if (sl >= 0) {
-                ent[j] = ((unsigned long long)sm.hv[sl] << 32) | (unsigned)bnd[j];
-                c++;
+          for (int j = 0; j < MAXD; j++) {
+            ent[j] = ~0ull;
+            if (j < deg) {
+              const int sx = ix + epk_img(pe[j].y, 0), sy = iy + epk_img(pe[j].y, 1), sz = iz + epk_img(pe[j].y, 2);
+              if (sx >= -127 && sx <= 127 && sy >= -127 && sy <= 127 && sz >= -127 && sz <= 127) {
+                const int sl = cw_find(sm.hk, site_key(pe[j].x, sx, sy, sz));
+                if (sl >= 0) {
+                  ent[j] = ((unsigned long long)cw_index(sm.hk, sl) << 32) | (unsigned)bnd[j];
+                  c++;
+                }
               }
             }
           }
@@ -627,7 +667,7 @@ int launch_cluster_warp(int pass, int n, int K, int max_deg, const long long* ro
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int need = (n + CW_WARPS - 1) / CW_WARPS;
-  const int grid = need < sms * 4 ? need : sms * 4;
+  const int grid = need < sms * 5 ? need : sms * 5;
   const bool cut = pc.r2 > 0.0;
   const size_t smem = sizeof(CwSmem) * CW_WARPS;
 #define CW_LAUNCH(P, C, D)                                                                                       \
