@@ -24,6 +24,7 @@ constexpr int FERMI_ROUNDS_WARM = 5;  // ... and from the previous SCF iteration
 constexpr int FERMI_ROUNDS_MORE = 64;  // extra rounds if a solve has not converged
 constexpr int FERMI_MAX_ROUNDS = 256;  // hard cap per solve
 constexpr double FERMI_TOL = 1e-13;    // eV
+constexpr int FERMI_F32_START = 65536; // orbitals from which a cold solve starts with FP32 rounds
 
 namespace {
 
@@ -98,6 +99,7 @@ struct bop_ctx {
   // stored Psi of every work item for the reverse sweeps (when it fits)
   DBuf psi_off, psis, lsum;
   DBuf fev;  // two device doubles of the distributed Fermi solve
+  DBuf gs32;  // FP32 copy of gsig for the starting point of a cold Fermi solve
   DBuf cw_misc, cw_keys, cw_epack;  // warp cluster builder: max degree / failure flags, site keys per
                                     // atom, packed neighbour edges
   long long psi_tot = 0;
@@ -767,12 +769,23 @@ int fermi_and_N(bop_ctx* c, int warm, cudaStream_t s) {
   const int M = c->S * c->nc * c->norb;
   const double target = c->m.n_e * c->nc;
   {
-    // one cooperative launch: bracket, Newton rounds to convergence, N and DOS
+    // one cooperative launch: bracket, Newton rounds to convergence, N and DOS;
+    // a cold start of many orbitals takes its starting point from Newton
+    // rounds on an FP32 copy of the coefficients (the FP64 rounds that follow
+    // decide the root, inside the full bracket)
+    const float* gs32 = nullptr;
+    if (!warm && M >= FERMI_F32_START) {
+      CKS(ensure(c, c->gs32, sizeof(float) * (size_t)M * (c->n_exp + 1)));
+      Region R(c, PK_FERMI, 1, s);
+      if (launch_gsig_f32(M, c->n_exp, P<double>(c->gsig), P<float>(c->gs32), s))
+        return fail(c, BOP_ERR_CUDA, "fermi launch failed");
+      gs32 = P<float>(c->gs32);
+    }
     Region R(c, PK_FERMI, 1, s);
     const int r = launch_fermi_coop(M, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf),
                                     P<double>(c->b_inf), c->n_exp, c->sfac, target, P<FermiState>(c->fstate),
                                     P<double>(c->partials), warm, FERMI_MAX_ROUNDS, FERMI_TOL, P<double>(c->N),
-                                    P<double>(c->dos), s);
+                                    P<double>(c->dos), s, gs32);
     if (r == 0) return BOP_OK;
     if (r != -2) return fail(c, BOP_ERR_CUDA, "fermi launch failed");
   }
@@ -1288,7 +1301,7 @@ int bop_destroy(bop_ctx* c) {
                   &c->lys, &c->lZ1, &c->lH1, &c->lZ2, &c->lH2, &c->lybar, &c->lcot, &c->lxbar, &c->lcount,
                   &c->rwN, &c->rwt, &c->rdUE, &c->rvec, &c->rcoef, &c->rjv, &c->rjcnt, &c->rjptr, &c->rjidx, &c->rjrow, &c->vgrad, &c->vq, &c->erep,
                   &c->psi_off, &c->psis, &c->lsum, &c->sdir, &c->vmom, &c->obar, &c->torque,
-                  &c->ncscr, &c->cw_misc, &c->cw_keys, &c->cw_epack, &c->fev};
+                  &c->ncscr, &c->cw_misc, &c->cw_keys, &c->cw_epack, &c->fev, &c->gs32};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);

@@ -95,6 +95,28 @@ __device__ __forceinline__ void count_and_dos(const double* __restrict__ gsig, c
   *dNde = (2.0 / PI) * s * c1;
 }
 
+// count_and_dos in FP32 on an FP32 copy of the coefficients: only for the
+// starting point of the FP64 Newton search (its sums carry errors of ~1e-6
+// of the electron count, far above the FP64 tolerance).
+__device__ __forceinline__ void count_and_dos_f32(const float* __restrict__ gs32, int M, int o, int ne, float x,
+                                                  float* N, float* dNde) {
+  auto G = [&](int j) -> float { return (j >= 0 && j <= ne) ? gs32[(size_t)j * M + o] : 0.f; };
+  const float phi = acosf(x), s = sqrtf(fmaxf(0.f, 1.f - x * x));
+  const float x2 = 2.f * x;
+  float b1 = 0.f, b2 = 0.f, c1 = 0.f, c2 = 0.f;
+  for (int k = ne + 2; k >= 1; k--) {
+    const float b0 = (G(k - 2) - G(k)) / (float)k + x2 * b1 - b2;
+    b2 = b1;
+    b1 = b0;
+    const float c0 = G(k - 1) + x2 * c1 - c2;
+    c2 = c1;
+    c1 = c0;
+  }
+  const float pi = 3.14159265358979f;
+  *N = G(0) * (1.f - phi / pi) + s * b1 / pi;
+  *dNde = (2.f / pi) * s * c1;
+}
+
 // The same sums by a pair of adjacent lanes (par = lane & 1): with
 // sin(k phi) = s U_{k-1}(x), each sum over U_j splits into its even and odd
 // terms, which obey U_{j+2} = y U_j - U_{j-2} with y = 4x^2 - 2; lane 0 runs
@@ -441,7 +463,8 @@ __global__ void __launch_bounds__(FC) k_fermi_coop(int M, const double* __restri
                                                    const double* __restrict__ b_inf, int ne, double sfac,
                                                    double target, FermiState* st, double* part, int warm,
                                                    int max_rounds, double tol, double* __restrict__ Nout,
-                                                   double* __restrict__ dos, int lanes) {
+                                                   double* __restrict__ dos, int lanes,
+                                                   const float* __restrict__ gs32) {
   cooperative_groups::grid_group grid = cooperative_groups::this_grid();
   __shared__ double sh[FC / 32 + 1];
   __shared__ double fr[FC / 32 + 1];
@@ -464,6 +487,40 @@ __global__ void __launch_bounds__(FC) k_fermi_coop(int M, const double* __restri
   double hi = final_reduce<FC>(part, 2, 1, nb, true, fr) + 1e-3;
   const double prev = st->ef;
   double E = (warm && prev > lo && prev < hi) ? prev : 0.5 * (lo + hi);
+  if (gs32 != nullptr && !(warm && prev > lo && prev < hi)) {
+    // cold start: safeguarded Newton rounds on FP32 sums (their own bracket,
+    // which the FP64 rounds below do not inherit) give the starting point
+    double l32 = lo, h32 = hi;
+    for (int r = 0; r < 16; r++) {
+      double aN = 0.0, aD = 0.0;
+      for (int o = b * FC + threadIdx.x; o < M; o += stride) {
+        const float bi = (float)b_inf[o];
+        const float xr = (float)((E - a_inf[o]) / (2.0 * b_inf[o]));
+        float Nv, dN;
+        count_and_dos_f32(gs32, M, o, ne, fminf(1.f, fmaxf(-1.f, xr)), &Nv, &dN);
+        aN += Nv;
+        if (xr > -1.f && xr < 1.f) aD += dN / (2.f * bi);
+      }
+      aN = coop_block_reduce(aN, sh, false);
+      aD = coop_block_reduce(aD, sh, false);
+      double* pr = part + (size_t)((r + 1) & 1) * 2 * nb;
+      if (threadIdx.x == 0) {
+        pr[2 * b] = aN;
+        pr[2 * b + 1] = aD;
+      }
+      grid.sync();
+      const double f = sfac * final_reduce<FC>(pr, 2, 0, nb, false, fr) - target;
+      const double fp = sfac * final_reduce<FC>(pr, 2, 1, nb, false, fr);
+      if (f < 0.0) l32 = E; else h32 = E;
+      double xn = fp > 0.0 ? E - f / fp : l32 - 1.0;
+      if (!(xn > l32 && xn < h32)) xn = 0.5 * (l32 + h32);
+      const double step = fabs(xn - E);
+      E = xn;
+      if (step < 1e-5 || h32 - l32 < 1e-5) break;
+    }
+    if (!(E > lo && E < hi)) E = 0.5 * (lo + hi);
+    grid.sync();  // every block has read the last FP32 partials before they are reused
+  }
   double ef = E;
   int iters = 0;
   bool done = hi - lo < tol;
@@ -800,7 +857,7 @@ int fermi_coop_grid() {
 
 int launch_fermi_coop(int M, const double* gsig, const double* inv, const double* a_inf, const double* b_inf,
                       int n_exp, double spin_factor, double target, FermiState* st, double* partials, int warm,
-                      int max_rounds, double tol, double* N, double* dos, cudaStream_t s) {
+                      int max_rounds, double tol, double* N, double* dos, cudaStream_t s, const float* gs32) {
   const int gmax = fermi_coop_grid();
   if (gmax <= 0) return -2;
   int lanes = few_orbitals(M) ? 2 : 1;
@@ -808,9 +865,21 @@ int launch_fermi_coop(int M, const double* gsig, const double* inv, const double
   if (g > gmax) g = gmax;
   if (g < 1) g = 1;
   void* args[] = {&M, &gsig, &inv, &a_inf, &b_inf, &n_exp, &spin_factor, &target, &st, &partials, &warm,
-                  &max_rounds, &tol, &N, &dos, &lanes};
+                  &max_rounds, &tol, &N, &dos, &lanes, &gs32};
   if (cudaLaunchCooperativeKernel((const void*)k_fermi_coop, g, FC, args, 0, s) != cudaSuccess) return -1;
   return 0;
+}
+
+__global__ void k_to_f32(long long n, const double* __restrict__ in, float* __restrict__ out) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    out[q] = (float)in[q];
+}
+
+int launch_gsig_f32(int M, int n_exp, const double* gsig, float* gs32, cudaStream_t s) {
+  const long long n = (long long)M * (n_exp + 1);
+  const long long g = (n + 255) / 256;
+  k_to_f32<<<(int)(g < 65536 ? g : 65536), 256, 0, s>>>(n, gsig, gs32);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int launch_orbital_N(int M, int n_exp, const double* gsig, const double* inv, const double* a_inf,

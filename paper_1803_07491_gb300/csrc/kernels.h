@@ -221,7 +221,10 @@ void launch_inverse_table(double* inv, int n, cudaStream_t s);
 // launch unavailable.
 int launch_fermi_coop(int M, const double* gsig, const double* inv, const double* a_inf, const double* b_inf,
                       int n_exp, double spin_factor, double target, FermiState* st, double* partials, int warm,
-                      int max_rounds, double tol, double* N, double* dos, cudaStream_t s);
+                      int max_rounds, double tol, double* N, double* dos, cudaStream_t s,
+                      const float* gs32 = nullptr);
+// FP32 copy of gsig [n_exp+1][M] (the starting point of a cold Fermi search).
+int launch_gsig_f32(int M, int n_exp, const double* gsig, float* gs32, cudaStream_t s);
 
 struct ScfArgs {
   int n, norb, n_spin, mode;  // mode 1 = LCN, 2 = Stoner
