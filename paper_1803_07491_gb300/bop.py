@@ -596,20 +596,34 @@ class Context:
 
 
 class BopEnergy(torch.autograd.Function):
-    """E_total(pos) with the exact gradient from the adjoint kernels.
+    """E_total(pos, cell) with the exact gradient from the adjoint kernels.
 
-    forward: bop_build_hamiltonian + bop_energy; backward: bop_forces
-    (dE/dpos = -F) scaled by the incoming gradient."""
+    forward: bop_build_hamiltonian + bop_energy + bop_forces; backward:
+    dE/dpos = -F, and when the cell is a tensor dE/dcell at fixed Cartesian
+    positions from the virial (Eq. sigma_k): with bond vectors
+    d = r_j - r_i + sum_c S_c cell[c], W_ab = sum_bonds g_a d_b =
+    sum_i (dE/dr_i)_a r_ib + sum_c (dE/dcell[c])_a cell[c]_b, so
+    dE/dcell = (cell^-1)^T (W + F^T pos)^T.  Both scaled by the incoming
+    gradient.  cell: [3][3] rows (numpy, a list or a tensor)."""
 
     @staticmethod
     def forward(actx, pos, ctx: Context, cell, pbc):
-        ctx.build(pos.detach(), cell, pbc)
+        cell_is_tensor = torch.is_tensor(cell)
+        cell_np = cell.detach().cpu().numpy() if cell_is_tensor else np.asarray(cell, np.float64)
+        ctx.build(pos.detach(), cell_np, pbc)
         e, st = ctx.energy()
-        F, _ = ctx.forces()
-        actx.save_for_backward(F)
+        F, W = ctx.forces()
+        actx.cell_is_tensor = cell_is_tensor
+        actx.cell_meta = (cell.device, cell.dtype) if cell_is_tensor else None
+        actx.save_for_backward(F, W, pos.detach(), torch.as_tensor(cell_np, dtype=torch.float64, device=pos.device))
         return torch.as_tensor(st["e_total"], dtype=torch.float64, device=pos.device)
 
     @staticmethod
     def backward(actx, g):
-        (F,) = actx.saved_tensors
-        return -F * g, None, None, None
+        F, W, pos, cell = actx.saved_tensors
+        g_cell = None
+        if actx.cell_is_tensor:
+            dE_dcell_T = (W + F.T @ pos) @ torch.linalg.inv(cell)
+            dev, dt = actx.cell_meta
+            g_cell = (dE_dcell_T.T * g).to(device=dev, dtype=dt)
+        return -F * g, None, g_cell, None

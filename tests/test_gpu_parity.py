@@ -205,3 +205,41 @@ def test_autograd_function(bop):
     E.backward()
     F, _ = ctx.forces()
     assert torch.allclose(pos.grad, -F)
+
+
+def test_autograd_cell_gradient_by_finite_differences(bop):
+    """The cell as a differentiable input (Eq. sigma_k): dE/dcell at fixed
+    Cartesian positions against central differences of the energy (FP64,
+    d-valent, 16 atoms moved away from the cell faces), and the symmetric
+    strain derivative that follows from it equals the symmetric virial."""
+    w = I.small_bcc(2, 2, 2, 0.05, 31)
+    pos_np = I.wrap(w.pos + 0.37, w.cell, w.pbc)
+    frac = np.linalg.solve(w.cell.T, pos_np.T).T
+    assert frac.min() > 1e-3 and frac.max() < 1.0 - 1e-3
+    ctx = bop.Context(w.model, w.run, "fp64")
+    pos = torch.tensor(pos_np, dtype=torch.float64, device="cuda", requires_grad=True)
+    cell = torch.tensor(w.cell, dtype=torch.float64, requires_grad=True)
+    E = bop.BopEnergy.apply(pos, ctx, cell, w.pbc)
+    E.backward()
+    g = cell.grad.numpy()
+
+    def energy(c):
+        ctx.build(pos_np, c, w.pbc)
+        _, st = ctx.energy()
+        return st["e_total"]
+
+    h = 1e-5
+    for (c, a) in [(0, 0), (1, 2), (2, 1), (2, 2), (0, 1)]:
+        cp, cm = w.cell.copy(), w.cell.copy()
+        cp[c, a] += h
+        cm[c, a] -= h
+        fd = (energy(cp) - energy(cm)) / (2 * h)
+        assert abs(g[c, a] - fd) < 1e-6 + 1e-6 * abs(fd), (c, a, g[c, a], fd)
+    # homogeneous deformation r -> (1 + e) r of positions and cell: dE/de =
+    # F^T... = (dE/dpos)^T pos + (dE/dcell)^T cell = W
+    ctx.build(pos_np, w.cell, w.pbc)
+    ctx.energy()
+    _, W = ctx.forces()
+    dEde = (-ctx.forces()[0]).cpu().numpy().T @ pos_np + g.T @ w.cell
+    assert np.allclose(dEde, W.cpu().numpy(), atol=1e-9)
+    ctx.close()
