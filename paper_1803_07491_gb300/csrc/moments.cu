@@ -142,6 +142,55 @@ __device__ __forceinline__ void prefetch_row_l2(const T* p) {
       reinterpret_cast<const char*>(p) + BYTES - 1));
 }
 
+// Asynchronous copies global -> shared (cp.async, no register round trip),
+// so that all of a thread's staging copies of a work item are in flight at
+// once; cp_async_wait_all() waits for the thread's own copies, a barrier
+// then publishes them to the CTA.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Extent of one atom's cluster in the cluster arrays: first site, number of
+// sites, adjacency range.  Read in two steps (sites, then adjacency) one work
+// item ahead, so that the next item's staging starts without waiting on
+// dependent loads.
+struct ItemExt {
+  long long s0, abase, aend;
+  int nsite;
+};
+__device__ __forceinline__ void ext_sites(const ClusterView& cv, int atom, ItemExt& x) {
+  x.s0 = cv.site_off[atom];
+  x.nsite = cv.level_end[(size_t)atom * (cv.K + 1) + cv.K];
+}
+__device__ __forceinline__ void ext_adj(const ClusterView& cv, ItemExt& x) {
+  x.abase = cv.adj_off[x.s0];
+  x.aend = cv.adj_off[x.s0 + x.nsite];
+}
+
+// One work item's cluster data in shared memory: the adjacency entries of its
+// sites, their adjacency offsets (absolute, as in the cluster arrays), level
+// counts and atoms.
+__device__ __forceinline__ void stage_item(const ClusterView& cv, const ItemExt& x, int2* s_adj, long long* s_aoff,
+                                           unsigned long long* s_lvc, int* s_atom, int tid, int nthr) {
+  const long long s0 = x.s0, abase = x.abase;
+  const int nsite = x.nsite, nadj = (int)(x.aend - x.abase);
+  for (int q = tid; q < nadj; q += nthr) cp_async8(s_adj + q, cv.adj + abase + q);
+  for (int q = tid; q <= nsite; q += nthr) cp_async8(s_aoff + q, cv.adj_off + s0 + q);
+  for (int q = tid; q < nsite; q += nthr) {
+    cp_async8(s_lvc + q, cv.lvcnt + s0 + q);
+    cp_async4(s_atom + q, cv.site_atom + s0 + q);
+  }
+  cp_async_wait_all();
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -399,33 +448,31 @@ k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
   unsigned char* tail = align16(reinterpret_cast<unsigned char*>(buf[1] + (size_t)L.cap_odd * PS));
   int2* s_adj = reinterpret_cast<int2*>(tail);
   unsigned long long* s_lvc = reinterpret_cast<unsigned long long*>(s_adj + (L.stage ? L.max_adj : 0));
-  int* s_aoff = reinterpret_cast<int*>(s_lvc + (L.stage ? L.max_sites : 0));
-  int* s_atom = s_aoff + (L.stage ? L.max_sites + 1 : 0);
+  long long* s_aoff = reinterpret_cast<long long*>(s_lvc + (L.stage ? L.max_sites : 0));
+  int* s_atom = reinterpret_cast<int*>(s_aoff + (L.stage ? L.max_sites + 1 : 0));
   __shared__ T red[2 * NC][FWD_THREADS / 32];
   const int K = cv.K;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int w0 = blockIdx.x * chunk, w1 = min(n_items, w0 + chunk);
+  ItemExt nx{};
+  if (w0 < w1) {
+    ext_sites(cv, ((NC == NO) ? w0 : (w0 / NO)) % n, nx);
+    ext_adj(cv, nx);
+  }
   for (int w = w0; w < w1; w++) {
     const int grp = (NC == NO) ? 0 : (w % NO);
     const int sa = (NC == NO) ? w : (w / NO);
     const int spin = sa / n, atom = sa % n;
-    const long long s0 = cv.site_off[atom];
+    const ItemExt cur = nx;
+    const long long s0 = cur.s0, abase = cur.abase;
     const int* lev = cv.level_end + (size_t)atom * (K + 1);
-    const int nsite = lev[K];
-    const long long abase = cv.adj_off[s0];
     const int2* adj = cv.adj + abase;
     const unsigned long long* lvc = cv.lvcnt + s0;
     const int* satom = cv.site_atom + s0;
     const T* E = onsite + (size_t)spin * n_on * NO;
-    if (L.stage) {
-      const int nadj = (int)(cv.adj_off[s0 + nsite] - abase);
-      for (int q = tid; q < nadj; q += FWD_THREADS) s_adj[q] = __ldg(adj + q);
-      for (int q = tid; q <= nsite; q += FWD_THREADS) s_aoff[q] = (int)(cv.adj_off[s0 + q] - abase);
-      for (int q = tid; q < nsite; q += FWD_THREADS) {
-        s_lvc[q] = lvc[q];
-        s_atom[q] = satom[q];
-      }
-    }
+    if (L.stage) stage_item(cv, cur, s_adj, s_aoff, s_lvc, s_atom, tid, FWD_THREADS);
+    const bool more = w + 1 < w1;
+    if (more) ext_sites(cv, ((NC == NO) ? w + 1 : ((w + 1) / NO)) % n, nx);
     for (int q = tid; q < N; q += FWD_THREADS) {
       const int r = q / NC, c = q % NC;
       buf[0][q] = (NC == NO) ? T(r == c ? 1 : 0) : T(r == grp ? 1 : 0);
@@ -473,7 +520,7 @@ k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
         const unsigned long long lc = L.stage ? s_lvc[t] : lvc[t];
         const int cnt = (int)((lc >> (8 * (k - 1))) & 0xff);
         if (cnt > 0) {
-          const int q0 = L.stage ? s_aoff[t] : (int)(cv.adj_off[s0 + t] - abase);
+          const int q0 = (int)((L.stage ? s_aoff[t] : cv.adj_off[s0 + t]) - abase);
           gather_pf2<T, NO, NC, PS>(L.stage ? s_adj + q0 : adj + q0, cnt, H, HS, prev, acc);
         }
         if (in_prev) {  // row t of Psi_k-1 again (shared memory), rather than kept live over the gather
@@ -522,6 +569,7 @@ k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
       }
       __syncthreads();
     }
+    if (more) ext_adj(cv, nx);
   }
 }
 
@@ -570,37 +618,35 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
   unsigned char* tail = align16(reinterpret_cast<unsigned char*>(eb + eb_elems<T, NO>(L.cap_eb)));
   int2* s_adj = reinterpret_cast<int2*>(tail);
   unsigned long long* s_lvc = reinterpret_cast<unsigned long long*>(s_adj + (L.stage ? L.max_adj : 0));
-  int* s_aoff = reinterpret_cast<int*>(s_lvc + (L.stage ? L.max_sites : 0));
-  int* s_atom = s_aoff + (L.stage ? L.max_sites + 1 : 0);
+  long long* s_aoff = reinterpret_cast<long long*>(s_lvc + (L.stage ? L.max_sites : 0));
+  int* s_atom = reinterpret_cast<int*>(s_aoff + (L.stage ? L.max_sites + 1 : 0));
   __shared__ T ws[NC][BOP_MAX_NMOM];
   __shared__ int s_lev[BOP_MAX_K + 1];
   __shared__ long long s_lo[BOP_MAX_K + 1];
   const int K = cv.K;
   const int tid = threadIdx.x;
   const int w0 = blockIdx.x * chunk, w1 = min(n_items, w0 + chunk);
+  ItemExt nx{};
+  if (w0 < w1) {
+    ext_sites(cv, ((NC == NO) ? w0 : (w0 / NO)) % n, nx);
+    ext_adj(cv, nx);
+  }
   for (int w = w0; w < w1; w++) {
     const int grp = (NC == NO) ? 0 : (w % NO);
     const int sa = (NC == NO) ? w : (w / NO);
     const int spin = sa / n, atom = sa % n;
-    const long long s0 = cv.site_off[atom];
+    const ItemExt cur = nx;
+    const long long s0 = cur.s0, abase = cur.abase;
     const int* lev = cv.level_end + (size_t)atom * (K + 1);
-    const int nsite = lev[K];
-    const long long abase = cv.adj_off[s0];
     const int2* adj = cv.adj + abase;
     const unsigned long long* lvc = cv.lvcnt + s0;
     const int* satom = cv.site_atom + s0;
     const T* E = onsite + (size_t)spin * n_on * NO;
     const size_t ib = ((size_t)(spin * (NO / NC) + grp) * psi_tot + psi_off[atom]) * PS;
     const T* P = pstore + ib;
-    if (L.stage) {
-      const int nadj = (int)(cv.adj_off[s0 + nsite] - abase);
-      for (int q = tid; q < nadj; q += FWD_THREADS) s_adj[q] = __ldg(adj + q);
-      for (int q = tid; q <= nsite; q += FWD_THREADS) s_aoff[q] = (int)(cv.adj_off[s0 + q] - abase);
-      for (int q = tid; q < nsite; q += FWD_THREADS) {
-        s_lvc[q] = lvc[q];
-        s_atom[q] = satom[q];
-      }
-    }
+    if (L.stage) stage_item(cv, cur, s_adj, s_aoff, s_lvc, s_atom, tid, FWD_THREADS);
+    const bool more = w + 1 < w1;
+    if (more) ext_sites(cv, ((NC == NO) ? w + 1 : ((w + 1) / NO)) % n, nx);
     if (tid <= K) s_lev[tid] = lev[tid];
     if (tid == 0) {
       long long o = 0;
@@ -664,10 +710,10 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
             const unsigned long long lc = L.stage ? s_lvc[t] : lvc[t];
             cnt = (int)((lc >> (8 * k)) & 0xff);
           } else {
-            cnt = L.stage ? s_aoff[t + 1] - s_aoff[t] : (int)(cv.adj_off[s0 + t + 1] - cv.adj_off[s0 + t]);
+            cnt = L.stage ? (int)(s_aoff[t + 1] - s_aoff[t]) : (int)(cv.adj_off[s0 + t + 1] - cv.adj_off[s0 + t]);
           }
           if (cnt > 0) {
-            const int q0 = L.stage ? s_aoff[t] : (int)(cv.adj_off[s0 + t] - abase);
+            const int q0 = (int)((L.stage ? s_aoff[t] : cv.adj_off[s0 + t]) - abase);
             const int2* ents = L.stage ? s_adj + q0 : adj + q0;
             if constexpr (HBAR) {
               // with the bond cotangents of the forward pairs (s, t) of level k
@@ -729,6 +775,7 @@ k_adj_rev(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
         atomicAdd(siteval + (size_t)spin * sv_stride + s0 + t, a);
       }
     }
+    if (more) ext_adj(cv, nx);
     __syncthreads();
   }
 }
@@ -1333,7 +1380,7 @@ int run_forward(const MomentsArgs& a, cudaStream_t s) {
   constexpr int PS = (N == 1) ? 1 : Row<T, N>::PS;
   FwdSmem L{a.cap_even, a.cap_odd, a.max_sites, a.max_adj, true};
   size_t psi = (size_t)(a.cap_even + a.cap_odd) * PS * sizeof(T);
-  size_t stage = (size_t)a.max_adj * 8 + (size_t)a.max_sites * 8 + (size_t)(a.max_sites + 1) * 4 +
+  size_t stage = (size_t)a.max_adj * 8 + (size_t)a.max_sites * 8 + (size_t)(a.max_sites + 1) * 8 +
                  (size_t)a.max_sites * 4 + 16;
   size_t smem = psi + stage;
   // stage the adjacency only while two CTAs (FP32) still fit on an SM
@@ -1376,7 +1423,7 @@ int run_reverse(const AdjointArgs& a, cudaStream_t s) {
   constexpr int PS = (N == 1) ? 1 : Row<T, N>::PS;
   RevSmem L{a.cap_even, a.cap_odd, a.max_sites, a.max_adj, a.cap_eb, true};
   const size_t psi = (size_t)(a.cap_even + a.cap_odd) * PS * sizeof(T) + eb_elems<T, NO>(a.cap_eb) * sizeof(T);
-  const size_t stage = (size_t)a.max_adj * 8 + (size_t)a.max_sites * 8 + (size_t)(a.max_sites + 1) * 4 +
+  const size_t stage = (size_t)a.max_adj * 8 + (size_t)a.max_sites * 8 + (size_t)(a.max_sites + 1) * 8 +
                        (size_t)a.max_sites * 4 + 16;
   auto fn = k_adj_rev<T, NO, NC, HBAR>;
   size_t smem = psi + stage;
