@@ -442,6 +442,7 @@ def run_learned(args, bop, I, world: int, rank: int):
     constant-terminator energy of every atom (FP64), then E+F throughput of
     the learned 9-moment form (the line) and of the cheapest
     constant-terminator form whose mean per-atom error is within 1 meV."""
+    import torch
     net, info = train_learned(bop, I, LEARNED_CELLS, LEARNED_EPOCHS, LEARNED_BATCH)
     w = I.workload("learned131k")
 
@@ -464,7 +465,11 @@ def run_learned(args, bop, I, world: int, rank: int):
         err[f"constant_{n_star}_fp32"] = atom_errors(energy(I.with_run(w, n_mom=n_star).run, "fp32")[0], e_ref)
     wl = I.with_run(w, terminator="mlp")
     ctx = bop.Context(wl.model, wl.run, args.precision, net=net)
+    # an NVTX range around the learned form's measurement, so that a profiler
+    # can take the launches of these steps alone (--nvtx-include learned_step/)
+    torch.cuda.nvtx.range_push("learned_step")
     line = measure(bop, ctx, wl, args, world, args.steps, args.warmup, args.precision)
+    torch.cuda.nvtx.range_pop()
     ctx.close()
     wp = I.with_run(w, n_mom=n_star)
     ctx = bop.Context(wp.model, wp.run, args.precision)
