@@ -125,16 +125,27 @@ def algorithmic_flops(family: str, w, stats: dict, prof: dict, n_spin: int, step
         regions = max(1, prof["adjoint"]["regions"])
         with_h = min(steps, regions)
         return one * (2.0 * with_h + 1.0 * (regions - with_h)) / regions
-    K = (n_mom - 1) // 2
+    # levels of the chain the expansion runs on (the learned terminator
+    # continues the 9-moment chain to 8 levels)
+    K = 8 if w.run.terminator == "mlp" else (n_mom - 1) // 2
+    # the FP32-products mode runs the sigma_m recurrences in FP32 with one
+    # spin channel; only the FP64 work is counted against the FP64 peak then
+    sig32 = stats.get("precision") == "fp32" and n_spin == 1 and not w.run.noncollinear
     if family == "expand":
         # sigma_m from the 2K-term recurrence of the generating function,
-        # times g_m: (4K + 1) flops per coefficient
-        return M * (n_exp + 1) * (4.0 * K + 1.0)
+        # times g_m: (4K + 1) flops per coefficient (1 in FP64 with FP32 recurrences)
+        return M * (n_exp + 1) * (1.0 if sig32 else 4.0 * K + 1.0)
     if family == "weights":
-        # the forward recurrence and, per seed (two for the SCF-response
-        # pair dU/dmu, dN/dmu, else one), its adjoint with the N / U sums
+        # per coefficient in FP64: chi_{m+2} and the sine recurrence (6), the
+        # N, P and DOS sums (9) and per seed the sigma cotangent (5); with
+        # FP64 recurrences also the forward recurrence (4K + 1) and per seed
+        # its adjoint (4K + 2).  Two seeds for the SCF-response pair
+        # dU/dmu, dN/dmu, else one
         seeds = 2 if (w.run.scf in ("lcn", "stoner") and w.run.scf_response) else 1
-        return M * (n_exp + 1) * (4.0 * K + 1.0 + seeds * (4.0 * K + 2.0))
+        fp64_sums = 15.0 + 5.0 * seeds
+        if sig32:
+            return M * (n_exp + 1) * fp64_sums
+        return M * (n_exp + 1) * (fp64_sums + 4.0 * K + 1.0 + seeds * (4.0 * K + 2.0))
     if family == "fermi":
         rounds = max(1, stats["bisection_rounds"])
         return rounds * M * (n_exp + 2) * 4.0
@@ -260,8 +271,8 @@ def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: s
 
     # roofline of the dominant kernel family (live CUDA-event times)
     fam = max(prof, key=lambda k: prof[k]["ms"])
-    flops = algorithmic_flops(fam, w, {**stats, "moment_products": stats_products(ctx, bop)}, prof, w.run.n_spin,
-                              prof_steps)
+    flops = algorithmic_flops(fam, w, {**stats, "moment_products": stats_products(ctx, bop), "precision": precision},
+                              prof, w.run.n_spin, prof_steps)
     per_region_ms = prof[fam]["ms"] / max(1, prof[fam]["regions"])
     fp64_family = fam in ("expand", "fermi", "weights", "orbital_NU", "ef_response") or precision == "fp64"
     peak = PEAK_FP64_TFLOPS if fp64_family else PEAK_FP32_TFLOPS
@@ -277,7 +288,9 @@ def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: s
         "metric": METRIC, "value": round(value, 2), "unit": "atoms/s", "n_gpus": world, "steps": steps,
         "warmup": warmup, "ms_per_step": round(t_ms / steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "fp32 products + fp64 scalar stages" if precision == "fp32" else "f64",
+        "dtype": ("f64" if precision == "fp64" else
+                  "fp32 products and sigma recurrences + fp64 recursion, band width, Fermi level, sums"
+                  if w.run.n_spin == 1 and not w.run.noncollinear else "fp32 products + fp64 scalar stages"),
         "data": "synthetic (seeded jittered bcc, random-free model parameters)",
         "config": {"workload": args.workload, "atoms": w.n_atoms, "orbitals": w.model.norb,
                    "n_mom": w.run.n_mom, "n_exp": w.run.n_exp, "scf": w.run.scf,
@@ -460,6 +473,8 @@ def run_learned(args, bop, I, world: int, rank: int):
     err["learned_9"] = atom_errors(el, e_ref)
     el32, _ = energy(I.with_run(w, terminator="mlp").run, "fp32", True)
     err["learned_9_fp32"] = atom_errors(el32, e_ref)
+    # the FP32-products error of the learned form itself (FP32 against FP64, per atom)
+    err["learned_9_fp32_vs_fp64"] = atom_errors(el32, el)
     n_star = next((nm for nm in (9, 11, 13, 15) if err[f"constant_{nm}"]["mean_abs"] <= 1.0), 17)
     if n_star != 17:
         err[f"constant_{n_star}_fp32"] = atom_errors(energy(I.with_run(w, n_mom=n_star).run, "fp32")[0], e_ref)

@@ -604,11 +604,19 @@ int run_moments(bop_ctx* c, const double* onsite_dev, double* mu, cudaStream_t s
   return BOP_OK;
 }
 
+// The sigma_m recurrences run in FP32 in the FP32-products mode of a single
+// spin channel.  With two spin channels the Stoner moments amplify the
+// error of N(E) by the exchange enhancement 1/(1 - I n(E_F)) (measured on
+// the 2,000-atom Stoner cell: Hellmann-Feynman forces 9e-3 eV/A off the FP64
+// oracle against < 5e-4 with FP64 recurrences), so they stay FP64 there.
+bool sig32_mode(const bop_ctx* c) { return !c->fp64 && c->S == 1; }
+
 LearnedArgs learned_args(bop_ctx* c, int M, const double* mu) {
   LearnedArgs L;
   L.M = M;
   L.n_exp = c->n_exp;
   L.fp64 = c->fp64;
+  L.sig32 = sig32_mode(c);
   L.mu = mu;
   L.base = P<double>(c->lbase);
   L.nlev = P<int>(c->lnlev);
@@ -683,6 +691,7 @@ int run_scalar(bop_ctx* c, int M, const double* mu, cudaStream_t s) {
   CKS(ensure(c, c->lcount, 2 * sizeof(unsigned)));
   CK(cudaMemsetAsync(c->lcount.p, 0, 2 * sizeof(unsigned), s));
   a.n_unbounded = c->m.bandwidth != BOP_BW_GERSHGORIN ? P<unsigned>(c->lcount) + 1 : nullptr;
+  a.sig32 = sig32_mode(c);
   Region R(c, PK_EXPAND, 1, s);
   if (launch_expand(a, s)) return fail(c, BOP_ERR_CUDA, "expand launch failed");
   return BOP_OK;
@@ -846,6 +855,7 @@ int compute_weights(bop_ctx* c, double cU, const double* lam, double cN0, double
   wa.zscratch = P<double>(c->zscr);
   wa.status = P<unsigned>(c->status);
   wa.bw = band_sel(c->m);
+  wa.sig32 = sig32_mode(c);
   wa.var_q = var_q;
   wa.var_lam = var_lam;
   wa.var_J = var_J;
@@ -1044,6 +1054,7 @@ int scf_response(bop_ctx* c, cudaStream_t s) {
     wa.bw = band_sel(c->m);
     wa.var_q = wa.var_lam = nullptr;
     wa.var_J = 0.0;
+    wa.sig32 = sig32_mode(c);
     Region R(c, PK_WEIGHTS, 1, s);
     if (launch_weights_pair(wa, c->sfac, 0.0, 0.0, 1.0, wN, s)) return fail(c, BOP_ERR_CUDA, "weights launch failed");
   }

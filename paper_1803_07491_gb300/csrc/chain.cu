@@ -67,8 +67,13 @@ __global__ void __launch_bounds__(CT) k_expand(ScalarArgs A) {
   double Q[NP], P[NP];
   gen_polys<KP>(ch, r.nlev, Q, P);
   bool outside = false;
-  const double last = A.n_unbounded ? sigma_series<KP, true>(Q, P, ne, A.g, A.gsig, M, o, &outside)
-                                    : sigma_series<KP, false>(Q, P, ne, A.g, A.gsig, M, o);
+  double last;
+  if (A.sig32)
+    last = A.n_unbounded ? sigma_series<KP, true, true>(Q, P, ne, A.g, A.gsig, M, o, &outside)
+                         : sigma_series<KP, false, true>(Q, P, ne, A.g, A.gsig, M, o);
+  else
+    last = A.n_unbounded ? sigma_series<KP, true>(Q, P, ne, A.g, A.gsig, M, o, &outside)
+                         : sigma_series<KP, false>(Q, P, ne, A.g, A.gsig, M, o);
   if (outside) atomicAdd(A.n_unbounded, 1u);
   if (!isfinite(t.a_inf) || !isfinite(t.b_inf) || !isfinite(last)) raise_error(A.status, BOP_DEV_ERR_NONFINITE);
 }
@@ -440,8 +445,12 @@ __global__ void __launch_bounds__(RT2) k_ef_response2(int M, int ne, const doubl
 // blocks take the same decision without a second synchronisation.  The
 // partial buffers alternate between rounds (a block can only overwrite a
 // buffer after every block has passed the next grid barrier).
-constexpr int FC = 64;  // threads per block of the cooperative solve
+// Threads per block of the cooperative solve: 64 for few orbitals (more
+// blocks), 256 for many (the sums walk each orbital's coefficients one cache
+// line per term, so the rounds wait on memory unless many warps are resident).
+constexpr int FC_SMALL = 64, FC_LARGE = 256;
 
+template <int FC>
 __device__ __forceinline__ double coop_block_reduce(double v, double* sh, bool take_max) {
   for (int o = 16; o > 0; o >>= 1) {
     const double w = __shfl_xor_sync(0xffffffffu, v, o);
@@ -458,6 +467,7 @@ __device__ __forceinline__ double coop_block_reduce(double v, double* sh, bool t
 // Rounds evaluate N and the DOS of every orbital at the current iterate and
 // store them; the stored values are those of the last iterate E, within
 // tol of E_F (the SCF residual uses them; the energy is evaluated at E_F).
+template <int FC>
 __global__ void __launch_bounds__(FC) k_fermi_coop(int M, const double* __restrict__ gsig,
                                                    const double* __restrict__ inv, const double* __restrict__ a_inf,
                                                    const double* __restrict__ b_inf, int ne, double sfac,
@@ -476,8 +486,8 @@ __global__ void __launch_bounds__(FC) k_fermi_coop(int M, const double* __restri
     mn = fmin(mn, a_inf[o] - 2.0 * b_inf[o]);
     mx = fmax(mx, a_inf[o] + 2.0 * b_inf[o]);
   }
-  mn = coop_block_reduce(-mn, sh, true);
-  mx = coop_block_reduce(mx, sh, true);
+  mn = coop_block_reduce<FC>(-mn, sh, true);
+  mx = coop_block_reduce<FC>(mx, sh, true);
   if (threadIdx.x == 0) {
     part[2 * b] = mn;
     part[2 * b + 1] = mx;
@@ -501,8 +511,8 @@ __global__ void __launch_bounds__(FC) k_fermi_coop(int M, const double* __restri
         aN += Nv;
         if (xr > -1.f && xr < 1.f) aD += dN / (2.f * bi);
       }
-      aN = coop_block_reduce(aN, sh, false);
-      aD = coop_block_reduce(aD, sh, false);
+      aN = coop_block_reduce<FC>(aN, sh, false);
+      aD = coop_block_reduce<FC>(aD, sh, false);
       double* pr = part + (size_t)((r + 1) & 1) * 2 * nb;
       if (threadIdx.x == 0) {
         pr[2 * b] = aN;
@@ -549,8 +559,8 @@ __global__ void __launch_bounds__(FC) k_fermi_coop(int M, const double* __restri
       }
     }
     evaluated = true;
-    aN = coop_block_reduce(aN, sh, false);
-    aD = coop_block_reduce(aD, sh, false);
+    aN = coop_block_reduce<FC>(aN, sh, false);
+    aD = coop_block_reduce<FC>(aD, sh, false);
     double* pr = part + (size_t)((r + 1) & 1) * 2 * nb;
     if (threadIdx.x == 0) {
       pr[2 * b] = aN;
@@ -635,7 +645,7 @@ __global__ void __launch_bounds__(CT) k_weights(WeightArgs A) {
   double abar_inf = 0.0, bbar_inf = 0.0;
   const double dE = chain_reverse<KP>(ch, r.nlev, KP, t.a_inf, t.b_inf, A.onsite[o], A.st->ef, A.g, A.inv, A.n_exp,
                                       M, o, cU, cN, A.zscratch, A.zscratch + (size_t)(A.n_exp + 1) * M, abar, bbar,
-                                      abar_inf, bbar_inf);
+                                      abar_inf, bbar_inf, A.sig32 != 0);
   if (A.dU_dE) A.dU_dE[o] = dE;
   bandwidth_reverse(r, t, A.bw, abar_inf, bbar_inf, abar, bbar);
   double mub[BOP_MAX_NMOM];
@@ -677,7 +687,7 @@ __global__ void __launch_bounds__(CT) k_weights_pair(WeightArgs A, double cU1, d
   const size_t zl = (size_t)(A.n_exp + 1) * M;
   double* zb[2] = {A.zscratch + zl, A.zscratch + 2 * zl};
   chain_reverse_ns<KP, 2>(ch, r.nlev, KP, t.a_inf, t.b_inf, A.onsite[o], A.st->ef, A.g, A.inv, A.n_exp, M, o, cU,
-                          cN, A.zscratch, zb, abar, bbar, abar_inf, bbar_inf, dE);
+                          cN, A.zscratch, zb, abar, bbar, abar_inf, bbar_inf, dE, A.sig32 != 0);
   if (A.dU_dE) A.dU_dE[o] = dE[0];
   bool bad = false;
   for (int q = 0; q < 2; q++) {
@@ -722,7 +732,8 @@ __global__ void __launch_bounds__(CT) k_weights_split(WeightArgs A, double cU1, 
   const size_t zl = (size_t)(A.n_exp + 1) * M;
   double* zs = A.zscratch + (size_t)q * 2 * zl;
   const double dE = chain_reverse<KP>(ch, r.nlev, KP, tm.a_inf, tm.b_inf, A.onsite[o], A.st->ef, A.g, A.inv,
-                                      A.n_exp, M, o, cU, cN, zs, zs + zl, abar, bbar, abar_inf, bbar_inf);
+                                      A.n_exp, M, o, cU, cN, zs, zs + zl, abar, bbar, abar_inf, bbar_inf,
+                                      A.sig32 != 0);
   if (q == 0 && A.dU_dE) A.dU_dE[o] = dE;
   bandwidth_reverse(r, tm, A.bw, abar_inf, bbar_inf, abar, bbar);
   double mub[BOP_MAX_NMOM];
@@ -842,6 +853,7 @@ int launch_fermi_more(int M, const double* gsig, const double* inv, const double
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+template <int FC>
 int fermi_coop_grid() {
   static int g = 0;
   if (g == 0) {
@@ -849,7 +861,7 @@ int fermi_coop_grid() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fermi_coop, FC, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fermi_coop<FC>, FC, 0);
     g = coop && per > 0 ? sms * (per < 4 ? per : 4) : -1;
   }
   return g;
@@ -858,15 +870,18 @@ int fermi_coop_grid() {
 int launch_fermi_coop(int M, const double* gsig, const double* inv, const double* a_inf, const double* b_inf,
                       int n_exp, double spin_factor, double target, FermiState* st, double* partials, int warm,
                       int max_rounds, double tol, double* N, double* dos, cudaStream_t s, const float* gs32) {
-  const int gmax = fermi_coop_grid();
+  const bool few = few_orbitals(M);
+  const int fc = few ? FC_SMALL : FC_LARGE;
+  const int gmax = few ? fermi_coop_grid<FC_SMALL>() : fermi_coop_grid<FC_LARGE>();
   if (gmax <= 0) return -2;
-  int lanes = few_orbitals(M) ? 2 : 1;
-  int g = (lanes * M + FC - 1) / FC;
+  int lanes = few ? 2 : 1;
+  int g = (lanes * M + fc - 1) / fc;
   if (g > gmax) g = gmax;
   if (g < 1) g = 1;
   void* args[] = {&M, &gsig, &inv, &a_inf, &b_inf, &n_exp, &spin_factor, &target, &st, &partials, &warm,
                   &max_rounds, &tol, &N, &dos, &lanes, &gs32};
-  if (cudaLaunchCooperativeKernel((const void*)k_fermi_coop, g, FC, args, 0, s) != cudaSuccess) return -1;
+  const void* fn = few ? (const void*)k_fermi_coop<FC_SMALL> : (const void*)k_fermi_coop<FC_LARGE>;
+  if (cudaLaunchCooperativeKernel(fn, g, fc, args, 0, s) != cudaSuccess) return -1;
   return 0;
 }
 

@@ -185,6 +185,7 @@ struct ScalarArgs {
   unsigned* status;
   BandSel bw;
   unsigned* n_unbounded;  // may be null: orbitals with some |sigma_m| > m + 1
+  int sig32 = 0;          // 1: the sigma_m recurrence in FP32 (FP32-products mode)
 };
 int launch_expand(const ScalarArgs& a, cudaStream_t s);
 void launch_jackson(double* g, int n_exp, cudaStream_t s);
@@ -282,6 +283,7 @@ struct WeightArgs {
   const double* var_q;
   const double* var_lam;
   double var_J;
+  int sig32 = 0;  // 1: the sigma_m recurrences (forward and reverse) in FP32 (FP32-products mode)
 };
 int launch_weights(const WeightArgs& a, cudaStream_t s);
 // Weights of L1 = cU1 U + cN1 N into a.w and of L2 = cU2 U + cN2 N into w2 at
@@ -295,6 +297,7 @@ int launch_ef_response(int M, int n_exp, const double* gsig, const double* inv, 
 // learned.cu: the learned terminator (n_mom = 9, continued to 8 levels)
 struct LearnedArgs {
   int M, n_exp, fp64;
+  int sig32;             // 1: the sigma_m recurrences in FP32
   const double* mu;      // [M][9]
   double* base;          // [M][10]: a_0..a_3, b_1..b_4, a_inf, b_inf of the 9-moment chain
   int* nlev;             // [M] levels of the 9-moment chain

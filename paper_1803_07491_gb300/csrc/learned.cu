@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(CT) k_expand_learned(LearnedArgs A) {
     chain_params(r, t, ok ? KX : KB, ch);
     double Q[2 * KX + 1], P[2 * KX + 1];
     gen_polys<KX>(ch, r.nlev, Q, P);
-    const double last = sigma_series<KX>(Q, P, A.n_exp, A.g, A.gsig, A.M, o);
+    const double last = A.sig32 ? sigma_series<KX, false, true>(Q, P, A.n_exp, A.g, A.gsig, A.M, o)
+                                : sigma_series<KX>(Q, P, A.n_exp, A.g, A.gsig, A.M, o);
     A.a_inf[o] = t.a_inf;
     A.b_inf[o] = t.b_inf;
     A.flag[o] = (A.flag[o] & 1) | (ok ? 2 : 0);
@@ -182,7 +183,8 @@ __global__ void __launch_bounds__(CT) k_weights_learned_a(LearnedArgs A) {
   double abar_inf = 0.0, bbar_inf = 0.0;
   const double dE = chain_reverse<KX>(ch, r.nlev, learned ? KX : KB, t.a_inf, t.b_inf, W.onsite[o], W.st->ef, W.g,
                                       W.inv, W.n_exp, M, o, cU, cN, W.zscratch,
-                                      W.zscratch + (size_t)(W.n_exp + 1) * M, abar, bbar, abar_inf, bbar_inf);
+                                      W.zscratch + (size_t)(W.n_exp + 1) * M, abar, bbar, abar_inf, bbar_inf,
+                                      A.sig32 != 0);
   if (W.dU_dE) W.dU_dE[o] = dE;
   double yb[NO];
   for (int j = 0; j < NO; j++) yb[j] = 0.0;
