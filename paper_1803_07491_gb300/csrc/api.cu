@@ -193,6 +193,13 @@ T* P(DBuf& b) {
 
 cudaStream_t S_(bop_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// The sigma_m recurrences run in FP32 in the FP32-products mode of a single
+// spin channel.  With two spin channels the Stoner moments amplify the
+// error of N(E) by the exchange enhancement 1/(1 - I n(E_F)) (measured on
+// the 2,000-atom Stoner cell: Hellmann-Feynman forces 9e-3 eV/A off the FP64
+// oracle against < 5e-4 with FP64 recurrences), so they stay FP64 there.
+bool sig32_mode(const bop_ctx* c) { return !c->fp64 && c->S == 1; }
+
 int check_status(bop_ctx* c, cudaStream_t s) {
   unsigned h = 0;
   CK(cudaMemcpyAsync(&h, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -604,13 +611,6 @@ int run_moments(bop_ctx* c, const double* onsite_dev, double* mu, cudaStream_t s
   return BOP_OK;
 }
 
-// The sigma_m recurrences run in FP32 in the FP32-products mode of a single
-// spin channel.  With two spin channels the Stoner moments amplify the
-// error of N(E) by the exchange enhancement 1/(1 - I n(E_F)) (measured on
-// the 2,000-atom Stoner cell: Hellmann-Feynman forces 9e-3 eV/A off the FP64
-// oracle against < 5e-4 with FP64 recurrences), so they stay FP64 there.
-bool sig32_mode(const bop_ctx* c) { return !c->fp64 && c->S == 1; }
-
 LearnedArgs learned_args(bop_ctx* c, int M, const double* mu) {
   LearnedArgs L;
   L.M = M;
@@ -893,13 +893,12 @@ int psi_row(int N, int fp64) {
 }
 
 // Stores Psi of every work item (one more forward pass at the current
-// onsite levels) when it pays and fits: several reverse sweeps follow (the
-// SCF-response solve), all starting orbitals share one work item (the
-// stored-Psi sweep keeps two Psi-bar levels of all five columns in shared
-// memory; with one column per item it gathers every block five times and is
-// slower than recomputing), and the store and its cotangent copy fit in a
-// third of the free device memory (psi_store_alloc).  Otherwise the reverse
-// sweeps recompute Psi.
+// onsite levels) when it fits: all starting orbitals share one work item
+// (the stored-Psi sweep keeps two Psi-bar levels of all five columns in
+// shared memory; with one column per item it gathers every block five times
+// and is slower than recomputing), and the store fits in a third of the free
+// device memory and the store budget (psi_store_alloc).  Otherwise the
+// reverse sweeps recompute Psi.
 int psi_store_alloc(bop_ctx* c, bool* fits) {
   *fits = false;
   const int nc = forward_nc(c);
@@ -920,9 +919,11 @@ int prepare_psi_store(bop_ctx* c, cudaStream_t s) {
   // at the final onsite levels
   c->forces_follow = !c->m.noncollinear;
   if (c->m.scf == BOP_SCF_VARIATIONAL || c->psi_valid || c->m.noncollinear) return BOP_OK;
-  const bool several = (c->m.scf == BOP_SCF_LCN || c->m.scf == BOP_SCF_STONER) && c->m.scf_response;
+  // a forward pass that stores Psi and the stored-Psi sweeps cost less than
+  // the recomputing sweep even for one sweep (131,072 atoms: 12 + 21 ms
+  // against 71 ms), so store whenever it fits
   bool fits = false;
-  if (several) CKS(psi_store_alloc(c, &fits));
+  CKS(psi_store_alloc(c, &fits));
   if (!fits) return BOP_OK;
   CKS(run_moments(c, P<double>(c->onsite), P<double>(c->mu), s, c->psis.p));
   c->psi_valid = true;
