@@ -398,7 +398,7 @@ __device__ __forceinline__ void cw_sort(unsigned long long* a, int cnt, int lane
 __device__ __forceinline__ int epk_img(int y, int c) { return (int)(((unsigned)y >> (8 * c)) & 0xffu) - 128; }
 
 template <int PASS, bool CUT, int MAXD>
-__global__ void __launch_bounds__(32 * CW_WARPS)
+__global__ void __launch_bounds__(32 * CW_WARPS, 5)
 k_cluster_warp(int n, int K, const long long* __restrict__ row_ptr, const int2* __restrict__ epack,
                const int* __restrict__ bond_of_edge, PathCut pc,
                unsigned long long* __restrict__ gkeys, ClusterOut out, int* __restrict__ wfail,
@@ -588,13 +588,18 @@ k_cluster_warp(int n, int K, const long long* __restrict__ row_ptr, const int2* 
         int cntk[BOP_MAX_K];
 #pragma unroll
         for (int k = 0; k < BOP_MAX_K; k++) cntk[k] = 0;
+        // the entries' local indices (distinct within a site; unused entries
+        // 0xffffffff): the rank of an entry by its local index is its rank
+        unsigned hi[MAXD];
+#pragma unroll
+        for (int j = 0; j < MAXD; j++) hi[j] = (unsigned)(ent[j] >> 32);
 #pragma unroll
         for (int j = 0; j < MAXD; j++) {
           if (ent[j] == ~0ull) continue;
           int rank = 0;
 #pragma unroll
-          for (int i = 0; i < MAXD; i++) rank += ent[i] < ent[j] ? 1 : 0;
-          const int sidx = (int)(ent[j] >> 32);
+          for (int i = 0; i < MAXD; i++) rank += hi[i] < hi[j] ? 1 : 0;
+          const int sidx = (int)hi[j];
           out.adj[a0 + off + rank] = make_int2(sidx, (int)(unsigned)(ent[j] & 0xffffffffu));
 #pragma unroll
           for (int k = 0; k < BOP_MAX_K; k++)
