@@ -1,7 +1,8 @@
 // The learned-terminator network 18 -> 128 -> 128 -> 10 (GELU): training
 // (FP32 forward, reverse mode, Adam) and inference (bfloat16 weights,
-// FP32 or FP64 activations) as tiled SIMT GEMMs with fused bias / GELU /
-// GELU-derivative epilogues, plus the bop_mlp object of the C ABI.
+// FP32 or FP64 activations) as tiled GEMMs with fused bias / GELU /
+// GELU-derivative epilogues (the FP32 inference on the tensor pipe, the rest
+// as SIMT tiles), plus the bop_mlp object of the C ABI.
 //
 // The layers are small dense contractions (K = 18, 128, 10) applied to
 // every orbital of a structure (hundreds of thousands of rows); the MLP is
@@ -151,6 +152,154 @@ int gemm(int M, int N, int K, const void* A, int lda, const void* B, int ldb, vo
   const int splits = kchunk > 0 ? (K + kchunk - 1) / kchunk : 1;
   dim3 grid((M + GBM - 1) / GBM, (N + GBN - 1) / GBN, splits < 1 ? 1 : splits);
   k_gemm<T, TAe, TBe, TA, TB, EPI><<<grid, GT, 0, s>>>(g);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------- inference on the tensor pipe
+// The FP32-activation inference GEMMs with bfloat16 weights on the tensor
+// cores (mma.sync m16n8k16, bfloat16 operands, FP32 accumulation).  Every
+// activation is split into three bfloat16 parts, a = a1 + a2 + a3 (a1 the
+// rounding of a, a2 of the remainder, a3 of what is left: 24 significant
+// bits, the FP32 value to within its last bits); the weights are exactly
+// bfloat16, every product of parts is exact in FP32, and the three products
+// accumulate in FP32, so that the result is the FP32 product of the FP32
+// activations with the bfloat16 weights up to the order of the sums.
+//
+// C[m][n] = sum_k A[m][k] W(k, n) (+ epilogue), A float [M][lda] (k < K),
+// W(k, n) = TB ? B[n ldb + k] : B[k ldb + n] (bfloat16), n < N.  KP, NP: K
+// and N padded to the MMA tile (16, 8).  Persistent blocks of four warps,
+// each warp 16 rows of a 64-row tile; the weights are staged once per block
+// as Ws[n][k] (k contiguous: the B fragment's pairs are one 32-bit load).
+constexpr int TC_WARPS = 4, TC_ROWS = 16 * TC_WARPS;
+
+__device__ __forceinline__ unsigned pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+
+// a = p[0] + p[1] + p[2] in bfloat16 parts
+__device__ __forceinline__ void split3(float a, __nv_bfloat16 p[3]) {
+  p[0] = __float2bfloat16_rn(a);
+  float r = a - __bfloat162float(p[0]);
+  p[1] = __float2bfloat16_rn(r);
+  r = r - __bfloat162float(p[1]);
+  p[2] = __float2bfloat16_rn(r);
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int KP, int NP, bool TB, int EPI>
+__global__ void __launch_bounds__(32 * TC_WARPS) k_gemm_tc(GemmArgs g) {
+  static_assert(KP % 16 == 0 && NP % 8 == 0, "tile padding");
+  constexpr int WS = KP + 8;  // bfloat16 per weight row (conflict-free fragment loads)
+  constexpr int AS = KP + 8;  // floats per staged activation row
+  extern __shared__ __align__(16) unsigned char tc_raw[];
+  __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(tc_raw);
+  float* As = reinterpret_cast<float*>(tc_raw + (size_t)NP * WS * sizeof(__nv_bfloat16));
+  const float* A = static_cast<const float*>(g.A);
+  const __nv_bfloat16* B = static_cast<const __nv_bfloat16*>(g.B);
+  float* C = static_cast<float*>(g.C);
+  float* Z = static_cast<float*>(g.Z);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gq = lane >> 2, tq = lane & 3;
+  for (int q = tid; q < NP * KP; q += 32 * TC_WARPS) {
+    const int n = q / KP, k = q % KP;
+    __nv_bfloat16 w = __float2bfloat16_rn(0.f);
+    if (n < g.N && k < g.K) w = TB ? B[(size_t)n * g.ldb + k] : B[(size_t)k * g.ldb + n];
+    Ws[n * WS + k] = w;
+  }
+  float* Aw = As + (size_t)warp * 16 * AS;
+  for (int m0 = blockIdx.x * TC_ROWS; m0 < g.M; m0 += gridDim.x * TC_ROWS) {
+    __syncthreads();  // the weights (first tile) and the previous tile's reads are done
+    const int r0 = m0 + warp * 16;
+    for (int q = lane; q < 16 * KP; q += 32) {
+      const int r = q / KP, k = q % KP;
+      const int m = r0 + r;
+      Aw[r * AS + k] = (m < g.M && k < g.K) ? A[(size_t)m * g.lda + k] : 0.f;
+    }
+    __syncwarp();
+    float acc[NP / 8][4];
+#pragma unroll
+    for (int t = 0; t < NP / 8; t++)
+#pragma unroll
+      for (int j = 0; j < 4; j++) acc[t][j] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < KP; kk += 16) {
+      // A fragments of the three parts: rows gq, gq + 8; columns 2tq, 2tq + 1 (+8)
+      unsigned af[3][4];
+      const int rr[4] = {gq, gq + 8, gq, gq + 8};
+      const int cc[4] = {kk + 2 * tq, kk + 2 * tq, kk + 2 * tq + 8, kk + 2 * tq + 8};
+#pragma unroll
+      for (int f = 0; f < 4; f++) {
+        const float2 v = *reinterpret_cast<const float2*>(Aw + rr[f] * AS + cc[f]);
+        __nv_bfloat16 p0[3], p1[3];
+        split3(v.x, p0);
+        split3(v.y, p1);
+#pragma unroll
+        for (int sp = 0; sp < 3; sp++) af[sp][f] = pack_bf16x2(p0[sp], p1[sp]);
+      }
+#pragma unroll
+      for (int t = 0; t < NP / 8; t++) {
+        const __nv_bfloat16* wr = Ws + (t * 8 + gq) * WS + kk + 2 * tq;
+        const unsigned b0 = *reinterpret_cast<const unsigned*>(wr);
+        const unsigned b1 = *reinterpret_cast<const unsigned*>(wr + 8);
+#pragma unroll
+        for (int sp = 2; sp >= 0; sp--) mma_bf16(acc[t], af[sp], b0, b1);
+      }
+    }
+    // epilogue: acc[t] = rows gq, gq + 8; columns t*8 + 2tq, + 1
+#pragma unroll
+    for (int t = 0; t < NP / 8; t++)
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int m = r0 + gq + 8 * h;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+          const int n = t * 8 + 2 * tq + j;
+          if (n >= g.N) continue;
+          const size_t o = (size_t)m * g.ldc + n;
+          float v = acc[t][2 * h + j];
+          if (EPI == EPI_BIAS) {
+            v += g.bias[n];
+          } else if (EPI == EPI_BIAS_GELU) {
+            v += g.bias[n];
+            Z[o] = v;
+            v = gelu(v);
+          } else if (EPI == EPI_DGELU) {
+            v *= gelu_d(Z[o]);
+          }
+          C[o] = v;
+        }
+      }
+  }
+}
+
+template <int KP, int NP, bool TB, int EPI>
+int gemm_tc(int M, int N, int K, const float* A, int lda, const __nv_bfloat16* B, int ldb, float* C, int ldc,
+            const float* bias, float* Z, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return 0;
+  if (K > KP || N > NP) return -1;
+  GemmArgs g{M, N, K, lda, ldb, ldc, K, A, B, C, bias, Z};
+  constexpr size_t smem = (size_t)NP * (KP + 8) * sizeof(__nv_bfloat16) + (size_t)TC_ROWS * (KP + 8) * sizeof(float);
+  auto fn = k_gemm_tc<KP, NP, TB, EPI>;
+  static int per_sm = 0, sms = 0;
+  if (per_sm == 0) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * TC_WARPS, smem);
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int tiles = (M + TC_ROWS - 1) / TC_ROWS;
+  const int grid = tiles < sms * per_sm ? tiles : sms * per_sm;
+  fn<<<grid, 32 * TC_WARPS, smem, s>>>(g);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -393,13 +542,13 @@ int mlp_infer_forward(int fp64, int M, const void* xs, const float* params, cons
                                                                          params + OFF_B2, Z2, 0, s);
     r |= gemm<double, double, __nv_bfloat16, false, true, EPI_BIAS>(M, NO, NH, H2, NH, w + OFF_W3, NH, ys, NO,
                                                                     params + OFF_B3, nullptr, 0, s);
-  } else {
-    r |= gemm<float, float, __nv_bfloat16, false, true, EPI_BIAS_GELU>(M, NH, NI, xs, NI, w + OFF_W1, NI, H1, NH,
-                                                                       params + OFF_B1, Z1, 0, s);
-    r |= gemm<float, float, __nv_bfloat16, false, true, EPI_BIAS_GELU>(M, NH, NH, H1, NH, w + OFF_W2, NH, H2, NH,
-                                                                       params + OFF_B2, Z2, 0, s);
-    r |= gemm<float, float, __nv_bfloat16, false, true, EPI_BIAS>(M, NO, NH, H2, NH, w + OFF_W3, NH, ys, NO,
-                                                                  params + OFF_B3, nullptr, 0, s);
+  } else {  // tensor pipe (three bfloat16 parts per FP32 activation)
+    r |= gemm_tc<32, 128, true, EPI_BIAS_GELU>(M, NH, NI, (const float*)xs, NI, w + OFF_W1, NI, (float*)H1, NH,
+                                               params + OFF_B1, (float*)Z1, s);
+    r |= gemm_tc<128, 128, true, EPI_BIAS_GELU>(M, NH, NH, (const float*)H1, NH, w + OFF_W2, NH, (float*)H2, NH,
+                                                params + OFF_B2, (float*)Z2, s);
+    r |= gemm_tc<128, 16, true, EPI_BIAS>(M, NO, NH, (const float*)H2, NH, w + OFF_W3, NH, (float*)ys, NO,
+                                          params + OFF_B3, nullptr, s);
   }
   return r;
 }
@@ -416,13 +565,13 @@ int mlp_infer_backward(int fp64, int M, const void* ybar, const void* wbf, void*
                                                                       nullptr, Z1, 0, s);
     r |= gemm<double, double, __nv_bfloat16, false, false, EPI_NONE>(M, NI, NH, dZ1, NH, w + OFF_W1, NI, xbar, NI,
                                                                      nullptr, nullptr, 0, s);
-  } else {
-    r |= gemm<float, float, __nv_bfloat16, false, false, EPI_DGELU>(M, NH, NO, ybar, NO, w + OFF_W3, NH, dZ2, NH,
-                                                                    nullptr, Z2, 0, s);
-    r |= gemm<float, float, __nv_bfloat16, false, false, EPI_DGELU>(M, NH, NH, dZ2, NH, w + OFF_W2, NH, dZ1, NH,
-                                                                    nullptr, Z1, 0, s);
-    r |= gemm<float, float, __nv_bfloat16, false, false, EPI_NONE>(M, NI, NH, dZ1, NH, w + OFF_W1, NI, xbar, NI,
-                                                                   nullptr, nullptr, 0, s);
+  } else {  // tensor pipe (three bfloat16 parts per FP32 cotangent)
+    r |= gemm_tc<16, 128, false, EPI_DGELU>(M, NH, NO, (const float*)ybar, NO, w + OFF_W3, NH, (float*)dZ2, NH,
+                                            nullptr, (float*)Z2, s);
+    r |= gemm_tc<128, 128, false, EPI_DGELU>(M, NH, NH, (const float*)dZ2, NH, w + OFF_W2, NH, (float*)dZ1, NH,
+                                             nullptr, (float*)Z1, s);
+    r |= gemm_tc<128, 24, false, EPI_NONE>(M, NI, NH, (const float*)dZ1, NH, w + OFF_W1, NI, (float*)xbar, NI,
+                                           nullptr, nullptr, s);
   }
   return r;
 }
