@@ -584,15 +584,17 @@ k_cluster_warp(int n, int K, const long long* __restrict__ row_ptr, const int2* 
         out.site_img[3 * (s0 + t) + 1] = (signed char)key_img(kt, 1);
         out.site_img[3 * (s0 + t) + 2] = (signed char)key_img(kt, 2);
         out.adj_off[s0 + t] = a0 + off;
-        unsigned long long lc = 0;
-        int cntk[BOP_MAX_K];
+        // level ends in registers (levels above K never match)
+        int lv[BOP_MAX_K];
 #pragma unroll
-        for (int k = 0; k < BOP_MAX_K; k++) cntk[k] = 0;
+        for (int k = 0; k < BOP_MAX_K; k++) lv[k] = k < K ? sm.lev[k] : 0x7fffffff;
         // the entries' local indices (distinct within a site; unused entries
         // 0xffffffff): the rank of an entry by its local index is its rank
         unsigned hi[MAXD];
 #pragma unroll
         for (int j = 0; j < MAXD; j++) hi[j] = (unsigned)(ent[j] >> 32);
+        // per-level entry counts, one byte per level (at most MAXD each)
+        unsigned long long per_level = 0;
 #pragma unroll
         for (int j = 0; j < MAXD; j++) {
           if (ent[j] == ~0ull) continue;
@@ -601,17 +603,17 @@ k_cluster_warp(int n, int K, const long long* __restrict__ row_ptr, const int2* 
           for (int i = 0; i < MAXD; i++) rank += hi[i] < hi[j] ? 1 : 0;
           const int sidx = (int)hi[j];
           out.adj[a0 + off + rank] = make_int2(sidx, (int)(unsigned)(ent[j] & 0xffffffffu));
+          int ls = 0;  // level of the entry's site
 #pragma unroll
-          for (int k = 0; k < BOP_MAX_K; k++)
-            if (k < K && sidx < sm.lev[k]) cntk[k]++;
-          int ls = 0;
-          while (ls < K && sidx >= sm.lev[ls]) ls++;
+          for (int k = 0; k < BOP_MAX_K; k++) ls += sidx >= lv[k] ? 1 : 0;
+          if (ls < K) per_level += 1ull << (8 * ls);
           const int k0 = lt > ls + 1 ? lt : ls + 1;
           if (k0 <= K) prod += (unsigned long long)(K - k0 + 1);
         }
-#pragma unroll
-        for (int k = 0; k < BOP_MAX_K; k++)
-          if (k < K) lc |= (unsigned long long)cntk[k] << (8 * k);
+        // byte k of lvcnt: entries of level <= k, k < K (the byte-wise prefix
+        // sum of per_level: every partial sum is at most MAXD <= 32 < 256)
+        unsigned long long lc = per_level * 0x0101010101010101ull;
+        if (K < 8) lc &= (1ull << (8 * K)) - 1ull;
         out.lvcnt[s0 + t] = lc;
       }
     }
