@@ -117,3 +117,40 @@ def test_impossible_electron_count_is_refused(bop, n_e):
     with pytest.raises(bop.BopError) as e:
         bop.bop_create(bop.make_model(I.MODEL_D, run))
     assert e.value.status == bop.BOP_ERR_ARG
+
+
+def test_collective_failure_and_single_process_reduce(bop):
+    """The reduce callback of a spatial decomposition: one that fails makes
+    bop_energy return BOP_ERR_COLLECTIVE (the failure of a collective, made
+    on the host), and the context evaluates again afterwards; one that
+    leaves the sums as they are (one process) gives the run without a
+    callback (the distributed Fermi search follows the same rules)."""
+    w = I.small_bcc(2, 2, 2, 0.05, 48)
+    ref = bop.Context(w.model, w.run, "fp64").evaluate(w.pos, w.cell, w.pbc)
+    ctx = bop.Context(w.model, w.run, "fp64")
+    calls = []
+
+    def fail(values, count, op, user):
+        calls.append(op)
+        return 1
+
+    def identity(values, count, op, user):
+        calls.append(op)
+        return 0
+
+    bad = bop.REDUCE_FN(fail)
+    bop.bop_set_reduce(ctx.h, bad)
+    ctx.build(w.pos, w.cell, w.pbc)
+    with pytest.raises(bop.BopError) as e:
+        ctx.energy()
+    assert e.value.status == bop.BOP_ERR_COLLECTIVE and calls
+    calls.clear()
+    good = bop.REDUCE_FN(identity)
+    bop.bop_set_reduce(ctx.h, good)
+    res = ctx.evaluate(w.pos, w.cell, w.pbc)
+    assert calls
+    assert abs(res.e_fermi - ref.e_fermi) < 1e-9
+    assert abs(res.e_total - ref.e_total) < 1e-9 * w.n_atoms
+    assert np.max(np.abs(res.forces.cpu().numpy() - ref.forces.cpu().numpy())) < 1e-9
+    bop.bop_set_reduce(ctx.h, None)
+    ctx.close()
