@@ -398,7 +398,7 @@ __device__ __forceinline__ void cw_sort(unsigned long long* a, int cnt, int lane
 __device__ __forceinline__ int epk_img(int y, int c) { return (int)(((unsigned)y >> (8 * c)) & 0xffu) - 128; }
 
 template <int PASS, bool CUT, int MAXD>
-__global__ void __launch_bounds__(32 * CW_WARPS, 5)
+__global__ void __launch_bounds__(32 * CW_WARPS, MAXD <= 16 ? 5 : 2)
 k_cluster_warp(int n, int K, const long long* __restrict__ row_ptr, const int2* __restrict__ epack,
                const int* __restrict__ bond_of_edge, PathCut pc,
                unsigned long long* __restrict__ gkeys, ClusterOut out, int* __restrict__ wfail,

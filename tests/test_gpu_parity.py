@@ -243,3 +243,33 @@ def test_autograd_cell_gradient_by_finite_differences(bop):
     dEde = (-ctx.forces()[0]).cpu().numpy().T @ pos_np + g.T @ w.cell
     assert np.allclose(dEde, W.cpu().numpy(), atol=1e-9)
     ctx.close()
+
+
+def test_repeated_builds_of_one_context(bop, ob):
+    """One context evaluates structures of the same atom count in turn:
+    small displacements (the clusters keep their sizes), large ones
+    (neighbours cross r_cut, the clusters change) and the first structure
+    again.  Every evaluation equals the oracle's: clusters bit-exact,
+    energies and forces (no state of one build leaks into the next)."""
+    base = I.small_bcc(3, 3, 3, 0.03, 61)  # 54 atoms, d orbitals, no SCF
+    rng = np.random.default_rng(62)
+    A = base.pos
+    A2 = I.wrap(A + rng.normal(scale=0.005, size=A.shape), base.cell, base.pbc)
+    B = I.wrap(A + rng.normal(scale=0.4, size=A.shape), base.cell, base.pbc)
+    K = (base.run.n_mom - 1) // 2
+    m = oracle_model(base.model)
+    ctx = bop.Context(base.model, base.run, "fp64")
+    for pos in (A, A2, B, A):
+        res = ctx.evaluate(pos, base.cell, base.pbc)
+        nbr = ob.neighbors(pos, base.cell, base.pbc, m.rc)
+        ref = ob.evaluate(m, oracle_settings(base.run), pos, base.cell, base.pbc)
+        assert abs(res.e_total - ref["e_total"]) < 1e-9 * base.n_atoms
+        assert np.max(np.abs(res.forces.cpu().numpy() - ref["forces"])) < 1e-8
+        st = ctx.build(pos, base.cell, base.pbc)
+        for atom in (0, 27, 53):
+            sa, si, lev = bop.bop_get_cluster(ctx.h, atom, K, st["max_cluster"])
+            ra, ri, rl = ob.cluster(atom, K, nbr)
+            assert np.array_equal(lev.cpu().numpy(), rl)
+            assert np.array_equal(sa.cpu().numpy(), ra)
+            assert np.array_equal(si.cpu().numpy(), ri)
+    ctx.close()
