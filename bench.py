@@ -128,24 +128,19 @@ def algorithmic_flops(family: str, w, stats: dict, prof: dict, n_spin: int, step
     # levels of the chain the expansion runs on (the learned terminator
     # continues the 9-moment chain to 8 levels)
     K = 8 if w.run.terminator == "mlp" else (n_mom - 1) // 2
-    # the FP32-products mode runs the sigma_m recurrences in FP32 with one
-    # spin channel; only the FP64 work is counted against the FP64 peak then
-    sig32 = stats.get("precision") == "fp32" and n_spin == 1 and not w.run.noncollinear
     if family == "expand":
         # sigma_m from the 2K-term recurrence of the generating function,
-        # times g_m: (4K + 1) flops per coefficient (1 in FP64 with FP32 recurrences)
-        return M * (n_exp + 1) * (1.0 if sig32 else 4.0 * K + 1.0)
+        # times g_m: (4K + 1) flops per coefficient (FP32 with one spin
+        # channel in the FP32-products mode, else FP64)
+        return M * (n_exp + 1) * (4.0 * K + 1.0)
     if family == "weights":
-        # per coefficient in FP64: chi_{m+2} and the sine recurrence (6), the
-        # N, P and DOS sums (9) and per seed the sigma cotangent (5); with
-        # FP64 recurrences also the forward recurrence (4K + 1) and per seed
-        # its adjoint (4K + 2).  Two seeds for the SCF-response pair
-        # dU/dmu, dN/dmu, else one
+        # per coefficient: chi_{m+2} and the sine (6), the N, P and DOS sums
+        # (9) and per seed the sigma cotangent (5), the forward recurrence
+        # (4K + 1) and per seed its adjoint (4K + 2).  Two seeds for the
+        # SCF-response pair dU/dmu, dN/dmu, else one.  All of it in FP32 with
+        # one spin channel in the FP32-products mode, else in FP64
         seeds = 2 if (w.run.scf in ("lcn", "stoner") and w.run.scf_response) else 1
-        fp64_sums = 15.0 + 5.0 * seeds
-        if sig32:
-            return M * (n_exp + 1) * fp64_sums
-        return M * (n_exp + 1) * (fp64_sums + 4.0 * K + 1.0 + seeds * (4.0 * K + 2.0))
+        return M * (n_exp + 1) * (15.0 + 5.0 * seeds + 4.0 * K + 1.0 + seeds * (4.0 * K + 2.0))
     if family == "fermi":
         rounds = max(1, stats["bisection_rounds"])
         return rounds * M * (n_exp + 2) * 4.0
@@ -274,7 +269,9 @@ def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: s
     flops = algorithmic_flops(fam, w, {**stats, "moment_products": stats_products(ctx, bop), "precision": precision},
                               prof, w.run.n_spin, prof_steps)
     per_region_ms = prof[fam]["ms"] / max(1, prof[fam]["regions"])
-    fp64_family = fam in ("expand", "fermi", "weights", "orbital_NU", "ef_response") or precision == "fp64"
+    sig32 = precision == "fp32" and w.run.n_spin == 1 and not w.run.noncollinear
+    fp64_family = (fam in ("fermi", "orbital_NU", "ef_response") or precision == "fp64"
+                   or (fam in ("expand", "weights") and not sig32))
     peak = PEAK_FP64_TFLOPS if fp64_family else PEAK_FP32_TFLOPS
     roof = None
     if flops is not None:
@@ -289,7 +286,7 @@ def measure(bop, ctx, w, args, world: int, steps: int, warmup: int, precision: s
         "warmup": warmup, "ms_per_step": round(t_ms / steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": ("f64" if precision == "fp64" else
-                  "fp32 products and sigma recurrences + fp64 recursion, band width, Fermi level, sums"
+                  "fp32 products, sigma recurrences and weight sums + fp64 recursion, band width, Fermi level, energy"
                   if w.run.n_spin == 1 and not w.run.noncollinear else "fp32 products + fp64 scalar stages"),
         "data": "synthetic (seeded jittered bcc, random-free model parameters)",
         "config": {"workload": args.workload, "atoms": w.n_atoms, "orbitals": w.model.norb,

@@ -117,10 +117,11 @@ enum {
  * jumps across zero; the loop then stops at scf_max_it.
  * precision: FP64 everywhere, or FP32 products and accumulation in the
  * moments and their reverse sweep; with one spin channel the sigma_m
- * recurrences of the expansion and of the weights run in FP32 as well (two
- * spin channels keep them in FP64: the exchange enhancement of the Stoner
- * moments amplifies their rounding).  The moments -> recursion coefficients,
- * the band width, the Fermi level and the N, U and DOS sums stay FP64.
+ * recurrences of the expansion and of the weights, and the weights' sums
+ * over the coefficients, run in FP32 as well (two spin channels keep them in
+ * FP64: the exchange enhancement of the Stoner moments amplifies their
+ * rounding).  The moments -> recursion coefficients, the band width, the
+ * Fermi level and the energy's N and U sums stay FP64.
  * mixer: BOP_MIX_LINEAR (x += F, F the preconditioned residual above) or
  * BOP_MIX_ANDERSON (type-II Broyden over the last mix_history <= 8
  * iterations, one of the paper's mixers); both converge to the same

@@ -203,7 +203,7 @@ __device__ inline void chain_reverse_ns(const Chain& ch, int L, int Kb, double a
 #pragma unroll
       for (int j = NP - 2; j >= 1; j--) hf[j] = hf[j - 1];
       hf[0] = v;
-      zs[(size_t)m * M + o] = (double)v;
+      reinterpret_cast<float*>(zs)[(size_t)m * M + o] = v;  // FP32 scratch with f32
     }
   } else {
     double h[NP - 1];
@@ -229,7 +229,51 @@ __device__ inline void chain_reverse_ns(const Chain& ch, int L, int Kb, double a
     Pbar[q] = cU[q] * bi;
   }
   double Nv = 0.0, Pv = 0.0, dN = 0.0, dP = 0.0;
-  {
+  if (f32) {
+    // the same sums in FP32 (sigma_m and its cotangent in FP32 scratch): the
+    // sines s_j = sin(j phi) = sinpi(j phi/pi) directly (no recurrence, so no
+    // growth near the band edges), chi_j carried from step to step
+    const float* zsf = reinterpret_cast<const float*>(zs);
+    float* zbf[NS];
+    float Nbf[NS], Pbf[NS];
+#pragma unroll
+    for (int q = 0; q < NS; q++) {
+      zbf[q] = reinterpret_cast<float*>(zb[q]);
+      Nbf[q] = (float)Nbar[q];
+      Pbf[q] = (float)Pbar[q];
+    }
+    const float theta = (float)(phi / PI), phim = (float)(phi - PI);
+    constexpr float INV_PI_F = 0.318309886183790672f;
+    auto chi = [&](int j, float sjm1, float sjp1) -> float {
+      if (j == 0) return 0.f;
+      const float lo = (j == 1) ? phim : __fdividef(sjm1, (float)(j - 1));  // s~_{j-1}
+      return (__fdividef(sjp1, (float)(j + 1)) - lo) * INV_PI_F;
+    };
+    float s0 = 0.f, sp1 = sinpif(theta), sp2 = sinpif(2.f * theta), sp3 = sinpif(3.f * theta);
+    float c_m = 0.f, c_m1 = chi(1, s0, sp2);
+    float Nf = 0.f, Pf = 0.f, dNf = 0.f, dPf = 0.f;
+    for (int m = 0; m <= ne; m++) {
+      const float c_m2 = chi(m + 2, sp1, sp3);
+      const float gm = (float)g[m];
+      const float gsm = gm * zsf[(size_t)m * M + o];
+      Nf += gsm * c_m1;
+      Pf += gsm * (c_m2 + c_m);
+      dNf += gsm * sp1;
+      dPf += gsm * (sp2 + s0);
+#pragma unroll
+      for (int q = 0; q < NS; q++) zbf[q][(size_t)m * M + o] = gm * (Nbf[q] * c_m1 + Pbf[q] * (c_m2 + c_m));
+      c_m = c_m1;
+      c_m1 = c_m2;
+      s0 = sp1;
+      sp1 = sp2;
+      sp2 = sp3;
+      sp3 = sinpif((float)(m + 4) * theta);
+    }
+    Nv = Nf;
+    Pv = Pf;
+    dN = dNf * (2.0 / PI);
+    dP = dPf * (2.0 / PI);
+  } else {
     // sines s_j = sin(j phi) by the recurrence; chi_j = (s~_{j+1} - s~_{j-1})/pi,
     // s~_k = sin(k phi)/k, s~_0 = phi - pi
     double s0 = 0.0, sp1 = s1, sp2 = 2.0 * x * s1, sp3 = 2.0 * x * sp2 - s1;  // s_m..s_{m+3}
@@ -281,12 +325,13 @@ __device__ inline void chain_reverse_ns(const Chain& ch, int L, int Kb, double a
 #pragma unroll
     for (int j = 0; j < NP; j++) qf[j] = (float)Dk[0][j];
     float lf[NS][NP - 1], qb[NS][NP], sw[NP - 1];
+    const float* zsf = reinterpret_cast<const float*>(zs);
 #pragma unroll
     for (int j = 0; j < NP - 1; j++) {
 #pragma unroll
       for (int q = 0; q < NS; q++) lf[q][j] = 0.f;
       const int mm = ne - 1 - j;
-      sw[j] = mm >= 0 ? (float)zs[(size_t)mm * M + o] : 0.f;
+      sw[j] = mm >= 0 ? zsf[(size_t)mm * M + o] : 0.f;
     }
 #pragma unroll
     for (int q = 0; q < NS; q++)
@@ -295,7 +340,7 @@ __device__ inline void chain_reverse_ns(const Chain& ch, int L, int Kb, double a
     for (int m = ne; m >= 0; m--) {
 #pragma unroll
       for (int q = 0; q < NS; q++) {
-        float lam = (float)zb[q][(size_t)m * M + o];
+        float lam = reinterpret_cast<const float*>(zb[q])[(size_t)m * M + o];
 #pragma unroll
         for (int j = 1; j < NP; j++) lam -= qf[j] * lf[q][j - 1];
         if (m < NP) Pb[q][m] += (double)lam;
@@ -308,7 +353,7 @@ __device__ inline void chain_reverse_ns(const Chain& ch, int L, int Kb, double a
 #pragma unroll
       for (int j = 0; j < NP - 2; j++) sw[j] = sw[j + 1];
       const int mm = m - NP;
-      sw[NP - 2] = mm >= 0 ? (float)zs[(size_t)mm * M + o] : 0.f;
+      sw[NP - 2] = mm >= 0 ? zsf[(size_t)mm * M + o] : 0.f;
     }
 #pragma unroll
     for (int q = 0; q < NS; q++)
