@@ -102,6 +102,7 @@ struct bop_ctx {
   DBuf gs32;  // FP32 copy of gsig for the starting point of a cold Fermi solve
   DBuf cw_misc, cw_keys, cw_epack;  // warp cluster builder: max degree / failure flags, site keys per
                                     // atom, packed neighbour edges
+  int cw_maxdeg = -1;  // largest degree of the centres, read back with the neighbour list's status
   long long psi_tot = 0;
   bool psi_valid = false;
   size_t store_budget = (size_t)-1;
@@ -325,13 +326,18 @@ int build_clusters_warp(bop_ctx* c, cudaStream_t s, bool* done) {
   const int n = c->nc, K = c->K;  // clusters of the centres
   if (n == 0 || (c->cl_maxs && c->cl_maxs > cluster_warp_max_sites())) return BOP_OK;
   if (K > 5 && !(c->m.r_path > 0)) return BOP_OK;  // bcc has 1,105 sites within 6 hops
-  CKS(ensure(c, c->cw_misc, 4 * sizeof(int)));
-  CK(cudaMemsetAsync(c->cw_misc.p, 0, 4 * sizeof(int), s));
-  launch_max_degree(n, P<long long>(c->row_ptr), P<int>(c->cw_misc), s);
   int misc[4] = {0, 0, 0, 0};
-  CK(cudaMemcpyAsync(misc, c->cw_misc.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  const int max_deg = misc[0];
+  CKS(ensure(c, c->cw_misc, 4 * sizeof(int)));
+  if (c->cw_maxdeg < 0) {  // not read with the neighbour list
+    CK(cudaMemsetAsync(c->cw_misc.p, 0, 4 * sizeof(int), s));
+    launch_max_degree(n, P<long long>(c->row_ptr), P<int>(c->cw_misc), s);
+    CK(cudaMemcpyAsync(misc, c->cw_misc.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    c->cw_maxdeg = misc[0];
+  }
+  const int max_deg = c->cw_maxdeg;
+  c->cw_maxdeg = -1;
+  CK(cudaMemsetAsync(P<int>(c->cw_misc) + 1, 0, 3 * sizeof(int), s));
   if (max_deg > 32) return BOP_OK;
   int* wfail = P<int>(c->cw_misc) + 1;
   CKS(ensure(c, c->level_end, sizeof(int) * (size_t)n * (K + 1)));
@@ -362,16 +368,17 @@ int build_clusters_warp(bop_ctx* c, cudaStream_t s, bool* done) {
                             P<unsigned>(c->status), s))
       return fail(c, BOP_ERR_CUDA, "cluster pass 0 launch failed");
   }
-  CK(cudaMemcpyAsync(misc, c->cw_misc.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  CKS(check_status(c, s));  // synchronises
-  if (misc[1] != 0) return BOP_OK;  // too large for the warp builder
+  // the sizes and the flags of pass 0 in one synchronisation (the scans run
+  // before it is known whether pass 0 succeeded; they are discarded if not)
   CKS(exclusive_scan(c, P<int>(c->atom_nsite), P<long long>(c->site_off), n + 1, s));
   CKS(exclusive_scan(c, P<int>(c->atom_nadj), P<long long>(c->adj_base), n + 1, s));
   long long tot[2];
   CK(cudaMemcpyAsync(&tot[0], P<long long>(c->site_off) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&tot[1], P<long long>(c->adj_base) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(c->maxlev, c->max_level.p, sizeof(int) * (K + 2), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  CK(cudaMemcpyAsync(misc, c->cw_misc.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CKS(check_status(c, s));  // synchronises
+  if (misc[1] != 0) return BOP_OK;  // too large for the warp builder
   c->nsite = tot[0];
   c->nadj = tot[1];
   CKS(ensure(c, c->site_atom, sizeof(int) * c->nsite));
@@ -398,8 +405,7 @@ int build_clusters_warp(bop_ctx* c, cudaStream_t s, bool* done) {
   }
   CK(cudaMemcpyAsync(P<long long>(c->adj_off) + c->nsite, P<long long>(c->adj_base) + n, sizeof(long long),
                      cudaMemcpyDeviceToDevice, s));
-  CKS(check_status(c, s));
-  *done = true;
+  *done = true;  // the status of pass 1 is read with the structure's last readback
   return BOP_OK;
 }
 
@@ -1415,7 +1421,15 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
   }
   }
   CK(cudaGetLastError());
+  // the centres' largest degree (the cluster builder's variant) read back
+  // with the neighbour list's status
+  int md[4] = {0, 0, 0, 0};
+  CKS(ensure(c, c->cw_misc, 4 * sizeof(int)));
+  CK(cudaMemsetAsync(c->cw_misc.p, 0, 4 * sizeof(int), s));
+  launch_max_degree(c->nc, P<long long>(c->row_ptr), P<int>(c->cw_misc), s);
+  CK(cudaMemcpyAsync(md, c->cw_misc.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   CKS(check_status(c, s));
+  c->cw_maxdeg = md[0];
   CKS(build_clusters(c, s));
   CKS(size_state(c));
   // per-atom row offsets of a stored Psi sweep
@@ -1428,7 +1442,7 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
   unsigned long long np = 0;
   CK(cudaMemcpyAsync(&c->psi_tot, P<long long>(c->psi_off) + nc, sizeof(long long), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&np, c->nprod.p, sizeof(np), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  CKS(check_status(c, s));  // synchronises; also the status of the cluster writes
   c->psi_valid = false;
   c->built = true;
   memset(&c->st, 0, sizeof(c->st));
