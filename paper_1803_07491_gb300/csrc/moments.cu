@@ -455,7 +455,10 @@ k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
   unsigned long long* s_lvc = reinterpret_cast<unsigned long long*>(s_adj + (L.stage ? L.max_adj : 0));
   long long* s_aoff = reinterpret_cast<long long*>(s_lvc + (L.stage ? L.max_sites : 0));
   int* s_atom = reinterpret_cast<int*>(s_aoff + (L.stage ? L.max_sites + 1 : 0));
-  __shared__ T red[2 * NC][FWD_THREADS / 32];
+  // per-warp partial sums of the two moments of a level, in two buffers
+  // (level parity): the reads of level k's partials need no barrier before
+  // level k + 1 starts writing its own
+  __shared__ T red[2][2 * NC][FWD_THREADS / 32];
   const int K = cv.K;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int w0 = blockIdx.x * chunk, w1 = min(n_items, w0 + chunk);
@@ -560,19 +563,20 @@ k_moments(ClusterView cv, const T* __restrict__ H, int HS, const T* __restrict__
       for (int c = 0; c < NC; c++) {
         T a = warp_sum(d1[c]), b = warp_sum(d2[c]);
         if (lane == 0) {
-          red[c][wid] = a;
-          red[NC + c][wid] = b;
+          red[k & 1][c][wid] = a;
+          red[k & 1][NC + c][wid] = b;
         }
       }
+      // level k's rows and partials are complete; level k + 1 writes the
+      // other Psi buffer (read last at level k - 1) and the other partials
       __syncthreads();
       if (tid < 2 * NC) {
         T acc = T(0);
-        for (int q = 0; q < FWD_THREADS / 32; q++) acc += red[tid][q];
+        for (int q = 0; q < FWD_THREADS / 32; q++) acc += red[k & 1][tid][q];
         const int c = tid % NC;
         const int m = tid < NC ? 2 * k - 1 : 2 * k;
         out[(size_t)c * n_mom + m] = (double)acc;
       }
-      __syncthreads();
     }
     if (more) ext_adj(cv, nx);
   }
