@@ -38,41 +38,67 @@ struct ClusterView {
 };
 
 // ---------------------------------------------------------------- duals
-// Value plus its gradient with respect to the three bond-vector components.
-struct D3 {
-  double v, g0, g1, g2;
+// Value plus its gradient with respect to the three bond-vector components,
+// in FP64 (D3) or FP32 (D3f, the forces of the FP32-products mode).
+template <class T>
+struct D3T {
+  T v, g0, g1, g2;
 };
+using D3 = D3T<double>;
+using D3f = D3T<float>;
 __device__ __forceinline__ D3 dmk(double v) { return {v, 0.0, 0.0, 0.0}; }
-__device__ __forceinline__ D3 operator+(D3 a, D3 b) { return {a.v + b.v, a.g0 + b.g0, a.g1 + b.g1, a.g2 + b.g2}; }
-__device__ __forceinline__ D3 operator-(D3 a, D3 b) { return {a.v - b.v, a.g0 - b.g0, a.g1 - b.g1, a.g2 - b.g2}; }
-__device__ __forceinline__ D3 operator*(D3 a, D3 b) {
+template <class T>
+__device__ __forceinline__ D3T<T> operator+(D3T<T> a, D3T<T> b) {
+  return {a.v + b.v, a.g0 + b.g0, a.g1 + b.g1, a.g2 + b.g2};
+}
+template <class T>
+__device__ __forceinline__ D3T<T> operator-(D3T<T> a, D3T<T> b) {
+  return {a.v - b.v, a.g0 - b.g0, a.g1 - b.g1, a.g2 - b.g2};
+}
+template <class T>
+__device__ __forceinline__ D3T<T> operator*(D3T<T> a, D3T<T> b) {
   return {a.v * b.v, a.g0 * b.v + a.v * b.g0, a.g1 * b.v + a.v * b.g1, a.g2 * b.v + a.v * b.g2};
 }
-__device__ __forceinline__ D3 operator*(double s, D3 a) { return {s * a.v, s * a.g0, s * a.g1, s * a.g2}; }
-__device__ __forceinline__ D3 operator*(D3 a, double s) { return s * a; }
-__device__ __forceinline__ D3 operator+(D3 a, double s) { return {a.v + s, a.g0, a.g1, a.g2}; }
-__device__ __forceinline__ D3 operator+(double s, D3 a) { return a + s; }
-__device__ __forceinline__ D3 operator-(D3 a, double s) { return {a.v - s, a.g0, a.g1, a.g2}; }
-__device__ __forceinline__ D3 operator-(double s, D3 a) { return {s - a.v, -a.g0, -a.g1, -a.g2}; }
-__device__ __forceinline__ D3 operator/(D3 a, D3 b) {
-  double q = a.v / b.v, ib = 1.0 / b.v;
+// a constant of the model (FP64) taken in the dual's type
+template <class T>
+__device__ __forceinline__ D3T<T> operator*(double s, D3T<T> a) {
+  const T t = (T)s;
+  return {t * a.v, t * a.g0, t * a.g1, t * a.g2};
+}
+template <class T>
+__device__ __forceinline__ D3T<T> operator*(D3T<T> a, double s) { return s * a; }
+template <class T>
+__device__ __forceinline__ D3T<T> operator+(D3T<T> a, double s) { return {a.v + (T)s, a.g0, a.g1, a.g2}; }
+template <class T>
+__device__ __forceinline__ D3T<T> operator+(double s, D3T<T> a) { return a + s; }
+template <class T>
+__device__ __forceinline__ D3T<T> operator-(D3T<T> a, double s) { return {a.v - (T)s, a.g0, a.g1, a.g2}; }
+template <class T>
+__device__ __forceinline__ D3T<T> operator-(double s, D3T<T> a) { return {(T)s - a.v, -a.g0, -a.g1, -a.g2}; }
+template <class T>
+__device__ __forceinline__ D3T<T> operator/(D3T<T> a, D3T<T> b) {
+  const T q = a.v / b.v, ib = T(1) / b.v;
   return {q, (a.g0 - q * b.g0) * ib, (a.g1 - q * b.g1) * ib, (a.g2 - q * b.g2) * ib};
 }
-__device__ __forceinline__ D3 dsqrt(D3 a) {
-  double r = sqrt(a.v), h = 0.5 / r;
+template <class T>
+__device__ __forceinline__ D3T<T> dsqrt(D3T<T> a) {
+  const T r = sqrt(a.v), h = T(0.5) / r;
   return {r, a.g0 * h, a.g1 * h, a.g2 * h};
 }
-__device__ __forceinline__ D3 dexp(D3 a) {
-  double e = exp(a.v);
+template <class T>
+__device__ __forceinline__ D3T<T> dexp(D3T<T> a) {
+  const T e = exp(a.v);
   return {e, a.g0 * e, a.g1 * e, a.g2 * e};
 }
-__device__ __forceinline__ D3 dcos(D3 a) {
-  double s, c;
+template <class T>
+__device__ __forceinline__ D3T<T> dcos(D3T<T> a) {
+  T s, c;
   sincos(a.v, &s, &c);
   return {c, -s * a.g0, -s * a.g1, -s * a.g2};
 }
+template <class T>
+__device__ __forceinline__ double dval(D3T<T> x) { return (double)x.v; }
 __device__ __forceinline__ double dval(double x) { return x; }
-__device__ __forceinline__ double dval(D3 x) { return x.v; }
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ double dexp(double x) { return exp(x); }
 __device__ __forceinline__ double dcos(double x) { return cos(x); }

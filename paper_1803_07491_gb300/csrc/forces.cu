@@ -19,24 +19,29 @@ __global__ void __launch_bounds__(FT) k_forces(int nb, BondModel m, const double
   __shared__ double sw[9][FT / 32];
   double w9[9];
   for (int q = 0; q < 9; q++) w9[q] = 0.0;
+  // block derivatives in the cotangents' type: FP32 duals in the
+  // FP32-products mode (relative error ~1e-6 of dH/dd), FP64 otherwise
+  using DT = typename std::conditional<sizeof(HT) == 4, D3f, D3>::type;
+  using ST = decltype(DT{}.v);
   for (int b = blockIdx.x * FT + threadIdx.x; b < nb; b += gridDim.x * FT) {
-    D3 d[3];
+    DT d[3];
     double dv[3] = {bond_d[3 * b], bond_d[3 * b + 1], bond_d[3 * b + 2]};
-    d[0] = {dv[0], 1.0, 0.0, 0.0};
-    d[1] = {dv[1], 0.0, 1.0, 0.0};
-    d[2] = {dv[2], 0.0, 0.0, 1.0};
-    D3 u[21];
-    sk_unique<D3>(m, d, u);
+    d[0] = {(ST)dv[0], ST(1), ST(0), ST(0)};
+    d[1] = {(ST)dv[1], ST(0), ST(1), ST(0)};
+    d[2] = {(ST)dv[2], ST(0), ST(0), ST(1)};
+    DT u[21];
+    sk_unique<DT>(m, d, u);
     const int nu = block_unique(m.norb);
-    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    ST a0 = ST(0), a1 = ST(0), a2 = ST(0);
     for (int q = 0; q < nu; q++) {
-      double hb = (double)Hbar[(size_t)b * HSh + q];
-      g0 += hb * u[q].g0;
-      g1 += hb * u[q].g1;
-      g2 += hb * u[q].g2;
+      const ST hb = (ST)Hbar[(size_t)b * HSh + q];
+      a0 += hb * u[q].g0;
+      a1 += hb * u[q].g1;
+      a2 += hb * u[q].g2;
     }
+    double g0 = a0, g1 = a1, g2 = a2;
     if (m.rep_A != 0.0) {  // pair repulsion of the bond
-      const D3 ph = pair_repulsion(m, dsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+      const DT ph = pair_repulsion(m, dsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
       g0 += ph.g0;
       g1 += ph.g1;
       g2 += ph.g2;
