@@ -120,8 +120,9 @@ enum {
  * recurrences of the expansion and of the weights, and the weights' sums
  * over the coefficients, run in FP32 as well (two spin channels keep them in
  * FP64: the exchange enhancement of the Stoner moments amplifies their
- * rounding).  The moments -> recursion coefficients, the band width, the
- * Fermi level and the energy's N and U sums stay FP64.
+ * rounding).  In FP32 mode the forces take the bond blocks' position
+ * derivatives in FP32 too.  The moments -> recursion coefficients, the band
+ * width, the Fermi level and the energy's N and U sums stay FP64.
  * mixer: BOP_MIX_LINEAR (x += F, F the preconditioned residual above) or
  * BOP_MIX_ANDERSON (type-II Broyden over the last mix_history <= 8
  * iterations, one of the paper's mixers); both converge to the same
