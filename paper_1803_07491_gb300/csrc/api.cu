@@ -109,6 +109,8 @@ struct bop_ctx {
   int resp_max_it = 0;     // cap of the SCF-response solve's iterations (0: GM_KRYLOV x GM_CYCLES)
   double resp_rtol = 0.0;  // its relative tolerance (0: the precision's default)
   DBuf status;
+  // pinned host staging of the small reads taken at a synchronisation
+  void* pin = nullptr;
   DBuf cub_tmp;
   DBuf nprod;
   int cl_hcap = 0, cl_maxs = 0, cl_slots = 0;
@@ -201,10 +203,52 @@ cudaStream_t S_(bop_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 // oracle against < 5e-4 with FP64 recurrences), so they stay FP64 there.
 bool sig32_mode(const bop_ctx* c) { return !c->fp64 && c->S == 1; }
 
-int check_status(bop_ctx* c, cudaStream_t s) {
-  unsigned h = 0;
-  CK(cudaMemcpyAsync(&h, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+constexpr size_t PIN_BYTES = 16384;
+
+// The small device-to-host reads of one synchronisation point: each lands in
+// the context's pinned staging area (an asynchronous copy, where a copy into
+// pageable memory synchronises the stream by itself), and all of them are
+// copied to their destinations once the stream has synchronised.  A read
+// that does not fit goes straight to its destination.
+struct Readback {
+  bop_ctx* c;
+  cudaStream_t s;
+  int n = 0;
+  size_t used = 0;
+  void* dst[16];
+  size_t off[16], len[16];
+  Readback(bop_ctx* c_, cudaStream_t s_) : c(c_), s(s_) {}
+  // an error return between add and sync: the staged copies land before the
+  // staging area is used again
+  ~Readback() {
+    if (n > 0) cudaStreamSynchronize(s);
+  }
+  int add(void* h, const void* d, size_t bytes) {
+    const size_t at = (used + 15) & ~(size_t)15;
+    if (c->pin == nullptr || n == 16 || at + bytes > PIN_BYTES) {
+      CK(cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, s));
+      return BOP_OK;
+    }
+    CK(cudaMemcpyAsync(static_cast<char*>(c->pin) + at, d, bytes, cudaMemcpyDeviceToHost, s));
+    dst[n] = h;
+    off[n] = at;
+    len[n++] = bytes;
+    used = at + bytes;
+    return BOP_OK;
+  }
+  // synchronises s and copies the staged reads out
+  int sync() {
+    CK(cudaStreamSynchronize(s));
+    for (int q = 0; q < n; q++) memcpy(dst[q], static_cast<char*>(c->pin) + off[q], len[q]);
+    n = 0;
+    used = 0;
+    return BOP_OK;
+  }
+  // the same, with the device status word read and decoded (check_status)
+  int finish();
+};
+
+int decode_status(bop_ctx* c, unsigned h, cudaStream_t s) {
   if (h == 0) return BOP_OK;
   CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), s));
   if (h & BOP_DEV_ERR_DEGREE) return fail(c, BOP_ERR_OVERFLOW, "an atom has more than %d neighbours", BOP_MAX_DEG);
@@ -213,6 +257,18 @@ int check_status(bop_ctx* c, cudaStream_t s) {
   if (h & BOP_DEV_ERR_REVERSE) return fail(c, BOP_ERR_ARG, "neighbour list not symmetric");
   if (h & BOP_DEV_ERR_NONFINITE) return fail(c, BOP_ERR_NUMERIC, "non-finite value in the scalar stages");
   return fail(c, BOP_ERR_CUDA, "device status 0x%x", h);
+}
+
+int Readback::finish() {
+  unsigned h = 0;
+  CKS(add(&h, c->status.p, sizeof(unsigned)));
+  CKS(sync());
+  return decode_status(c, h, s);
+}
+
+int check_status(bop_ctx* c, cudaStream_t s) {
+  Readback rb(c, s);
+  return rb.finish();
 }
 
 // Exclusive prefix sum accumulated in the output type (an int count
@@ -331,8 +387,9 @@ int build_clusters_warp(bop_ctx* c, cudaStream_t s, bool* done) {
   if (c->cw_maxdeg < 0) {  // not read with the neighbour list
     CK(cudaMemsetAsync(c->cw_misc.p, 0, 4 * sizeof(int), s));
     launch_max_degree(n, P<long long>(c->row_ptr), P<int>(c->cw_misc), s);
-    CK(cudaMemcpyAsync(misc, c->cw_misc.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    Readback rb(c, s);
+    CKS(rb.add(misc, c->cw_misc.p, 4 * sizeof(int)));
+    CKS(rb.sync());
     c->cw_maxdeg = misc[0];
   }
   const int max_deg = c->cw_maxdeg;
@@ -373,11 +430,14 @@ int build_clusters_warp(bop_ctx* c, cudaStream_t s, bool* done) {
   CKS(exclusive_scan(c, P<int>(c->atom_nsite), P<long long>(c->site_off), n + 1, s));
   CKS(exclusive_scan(c, P<int>(c->atom_nadj), P<long long>(c->adj_base), n + 1, s));
   long long tot[2];
-  CK(cudaMemcpyAsync(&tot[0], P<long long>(c->site_off) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&tot[1], P<long long>(c->adj_base) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(c->maxlev, c->max_level.p, sizeof(int) * (K + 2), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(misc, c->cw_misc.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  CKS(check_status(c, s));  // synchronises
+  {
+    Readback rb(c, s);
+    CKS(rb.add(&tot[0], P<long long>(c->site_off) + n, sizeof(long long)));
+    CKS(rb.add(&tot[1], P<long long>(c->adj_base) + n, sizeof(long long)));
+    CKS(rb.add(c->maxlev, c->max_level.p, sizeof(int) * (K + 2)));
+    CKS(rb.add(misc, c->cw_misc.p, 4 * sizeof(int)));
+    CKS(rb.finish());  // synchronises
+  }
   if (misc[1] != 0) return BOP_OK;  // too large for the warp builder
   c->nsite = tot[0];
   c->nadj = tot[1];
@@ -456,8 +516,11 @@ int build_clusters(bop_ctx* c, cudaStream_t s) {
       return fail(c, BOP_ERR_CUDA, "cluster pass 0 launch failed");
     }
     unsigned h = 0;
-    CK(cudaMemcpyAsync(&h, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    {
+      Readback rb(c, s);
+      CKS(rb.add(&h, c->status.p, sizeof(unsigned)));
+      CKS(rb.sync());
+    }
     if (h & BOP_DEV_ERR_CLUSTER) {
       CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), s));
       maxs *= 2;
@@ -469,10 +532,13 @@ int build_clusters(bop_ctx* c, cudaStream_t s) {
     CKS(exclusive_scan(c, P<int>(c->atom_nsite), P<long long>(c->site_off), n + 1, s));
     CKS(exclusive_scan(c, P<int>(c->atom_nadj), P<long long>(c->adj_base), n + 1, s));
     long long tot[2];
-    CK(cudaMemcpyAsync(&tot[0], P<long long>(c->site_off) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&tot[1], P<long long>(c->adj_base) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(c->maxlev, c->max_level.p, sizeof(int) * (K + 2), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    {
+      Readback rb(c, s);
+      CKS(rb.add(&tot[0], P<long long>(c->site_off) + n, sizeof(long long)));
+      CKS(rb.add(&tot[1], P<long long>(c->adj_base) + n, sizeof(long long)));
+      CKS(rb.add(c->maxlev, c->max_level.p, sizeof(int) * (K + 2)));
+      CKS(rb.sync());
+    }
     c->nsite = tot[0];
     c->nadj = tot[1];
     CKS(ensure(c, c->site_atom, sizeof(int) * c->nsite));
@@ -730,8 +796,11 @@ int fermi_distributed(bop_ctx* c, int warm, cudaStream_t s) {
                             P<double>(c->fev), s))
         return fail(c, BOP_ERR_CUDA, "fermi launch failed");
     }
-    CK(cudaMemcpyAsync(v, c->fev.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    {
+      Readback rb(c, s);
+      CKS(rb.add(v, c->fev.p, 2 * sizeof(double)));
+      CKS(rb.sync());
+    }
     return reduce_over_ranks(c, v, 2, mode == 0 ? BOP_REDUCE_MAX : BOP_REDUCE_SUM);
   };
   CKS(eval(0, 0.0));
@@ -1000,9 +1069,9 @@ constexpr int GM_CYCLES = 3;    // cycles (restarts + 1)
 
 // Reads nv doubles from the device (synchronises s).
 int read_back(bop_ctx* c, const double* d, double* h, int nv, cudaStream_t s) {
-  CK(cudaMemcpyAsync(h, d, sizeof(double) * nv, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  return BOP_OK;
+  Readback rb(c, s);
+  CKS(rb.add(h, d, sizeof(double) * nv));
+  return rb.sync();
 }
 
 // SCF response of the forces: weights w = wU - c wN with the multipliers y
@@ -1294,6 +1363,10 @@ int bop_create(bop_ctx** out, const bop_model* model) {
   }
   cudaMemset(c->status.p, 0, sizeof(unsigned));
   cudaMemset(c->counter.p, 0, sizeof(unsigned));
+  if (cudaHostAlloc(&c->pin, PIN_BYTES, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    c->pin = nullptr;  // reads go straight to their destinations
+  }
   launch_jackson(P<double>(c->gjack), c->n_exp, 0);
   launch_inverse_table(P<double>(c->ginv), c->n_exp + 8, 0);
   if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -1322,6 +1395,7 @@ int bop_destroy(bop_ctx* c) {
                   &c->ncscr, &c->cw_misc, &c->cw_keys, &c->cw_epack, &c->fev, &c->gs32};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
+  if (c->pin) cudaFreeHost(c->pin);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   delete c;
   return BOP_OK;
@@ -1375,9 +1449,12 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
   }
   double fr[6 * 64];
   long long E = 0;
-  CK(cudaMemcpyAsync(fr, c->frac.p, sizeof(double) * 6 * 64, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&E, P<long long>(c->row_ptr) + n, sizeof(long long), cudaMemcpyDeviceToHost, s));
-  CKS(check_status(c, s));
+  {
+    Readback rb(c, s);
+    CKS(rb.add(fr, c->frac.p, sizeof(double) * 6 * 64));
+    CKS(rb.add(&E, P<long long>(c->row_ptr) + n, sizeof(long long)));
+    CKS(rb.finish());
+  }
   for (int a = 0; a < 3; a++) {
     double mn = 1e300, mx = -1e300;
     for (int q = 0; q < 64; q++) {
@@ -1427,8 +1504,11 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
   CKS(ensure(c, c->cw_misc, 4 * sizeof(int)));
   CK(cudaMemsetAsync(c->cw_misc.p, 0, 4 * sizeof(int), s));
   launch_max_degree(c->nc, P<long long>(c->row_ptr), P<int>(c->cw_misc), s);
-  CK(cudaMemcpyAsync(md, c->cw_misc.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  CKS(check_status(c, s));
+  {
+    Readback rb(c, s);
+    CKS(rb.add(md, c->cw_misc.p, 4 * sizeof(int)));
+    CKS(rb.finish());
+  }
   c->cw_maxdeg = md[0];
   CKS(build_clusters(c, s));
   CKS(size_state(c));
@@ -1440,9 +1520,12 @@ int bop_build_hamiltonian(bop_ctx* c, int n, const double* pos, const double* ce
   launch_level_sums(nc, c->K, P<int>(c->level_end), P<long long>(c->lsum), s);
   CKS(exclusive_scan(c, P<long long>(c->lsum), P<long long>(c->psi_off), nc + 1, s));
   unsigned long long np = 0;
-  CK(cudaMemcpyAsync(&c->psi_tot, P<long long>(c->psi_off) + nc, sizeof(long long), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&np, c->nprod.p, sizeof(np), cudaMemcpyDeviceToHost, s));
-  CKS(check_status(c, s));  // synchronises; also the status of the cluster writes
+  {
+    Readback rb(c, s);
+    CKS(rb.add(&c->psi_tot, P<long long>(c->psi_off) + nc, sizeof(long long)));
+    CKS(rb.add(&np, c->nprod.p, sizeof(np)));
+    CKS(rb.finish());  // synchronises; also the status of the cluster writes
+  }
   c->psi_valid = false;
   c->built = true;
   memset(&c->st, 0, sizeof(c->st));
@@ -1652,9 +1735,10 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
     if (!last_it) CKS(residual());
     // one synchronisation per iteration: Fermi solve converged?  SCF converged?
     for (int extra = 0;; extra++) {
-      CK(cudaMemcpyAsync(&fs, c->fstate.p, sizeof(FermiState), cudaMemcpyDeviceToHost, s));
-      if (!last_it) CK(cudaMemcpyAsync(res, c->result.p, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
-      CKS(check_status(c, s));
+      Readback rb(c, s);
+      CKS(rb.add(&fs, c->fstate.p, sizeof(FermiState)));
+      if (!last_it) CKS(rb.add(res, c->result.p, sizeof(double) * 4));
+      CKS(rb.finish());
       if (fs.done) break;
       if (fs.iters >= FERMI_MAX_ROUNDS || extra >= 4)
         return fail(c, BOP_ERR_BRACKET, "Fermi level not converged after %d rounds", fs.iters);
@@ -1702,9 +1786,12 @@ int bop_energy(bop_ctx* c, double* e_atom, double* delta_io, double* m_io, bop_s
   if (m_io && magnetic) CK(cudaMemcpyAsync(m_io, c->mval.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   double et = 0.0;
   unsigned nl[2] = {0, 0};
-  CK(cudaMemcpyAsync(&et, c->e_total.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(nl, c->lcount.p, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-  CKS(check_status(c, s));
+  {
+    Readback rb(c, s);
+    CKS(rb.add(&et, c->e_total.p, sizeof(double)));
+    CKS(rb.add(nl, c->lcount.p, 2 * sizeof(unsigned)));
+    CKS(rb.finish());
+  }
   CKS(reduce_over_ranks(c, &et, 1, BOP_REDUCE_SUM));  // the whole structure's energy
   c->ef_solved = true;
   c->st.n_learned = (int)nl[0];
@@ -1761,8 +1848,11 @@ int bop_forces(bop_ctx* c, double* forces, double* virial, bop_stats* st, bop_st
     if (c->reduce_fn) {
       // one E_F for all processes: its multiplier from the sums of all of them
       double l[3];
-      CK(cudaMemcpyAsync(l, c->lam.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+      {
+        Readback rb(c, s);
+        CKS(rb.add(l, c->lam.p, 3 * sizeof(double)));
+        CKS(rb.sync());
+      }
       CKS(reduce_over_ranks(c, l + 1, 2, BOP_REDUCE_SUM));
       l[0] = l[2] > 0.0 ? l[1] / l[2] : 0.0;
       CK(cudaMemcpyAsync(c->lam.p, l, 3 * sizeof(double), cudaMemcpyHostToDevice, s));
