@@ -2,7 +2,8 @@
 self-consistent energy): parity with the oracle's dense implicit-function
 solve on small cells (LCN and Stoner, FP64 and FP32 products), the
 Hellmann-Feynman form when the response is switched off, and central
-differences of the GPU's own energy on the 2,000-atom LCN workload."""
+differences of the GPU's own energy on the 2,000-atom LCN workload and a
+2,662-atom Stoner cell."""
 import numpy as np
 import pytest
 
@@ -86,6 +87,41 @@ def test_d2000_lcn_forces_by_finite_differences(bop):
 
     h = 1e-4
     for (i, c) in [(0, 0), (1234, 2)]:
+        p, q = w.pos.copy(), w.pos.copy()
+        p[i, c] += h
+        q[i, c] -= h
+        fd = -(energy(p) - energy(q)) / (2 * h)
+        assert abs(F[i, c] - fd) < 2e-5 + 1e-4 * abs(fd), (i, c, F[i, c], fd)
+    ctx.close()
+
+
+def test_stoner_forces_by_finite_differences(bop):
+    """A 2,662-atom Stoner cell in FP64 (5,324 unknowns of the response
+    solve: shifts and moments): forces with the SCF response against
+    central differences of the GPU energy, h = 1e-4 A (SCF to 1e-11,
+    warm-started from the converged shifts and moments)."""
+    base = I.workload("mag2000")
+    pos, cell = I.bcc_jittered(11, 11, 11, 0.05, 9)
+    w = I.with_run(I.Workload("mag2662", pos, cell, (1, 1, 1), base.model, base.run), scf_tol=1e-11)
+    ctx = bop.Context(w.model, w.run, "fp64")
+    ctx.build(w.pos, w.cell, w.pbc)
+    delta = torch.zeros(w.n_atoms, dtype=torch.float64, device="cuda")
+    m = torch.full((w.n_atoms,), w.run.m0, dtype=torch.float64, device="cuda")
+    _, st = ctx.energy(delta=delta, m=m)
+    assert st["scf_converged"] == 1
+    F, W, fs = bop.bop_forces_stats(ctx.h, w.n_atoms)
+    assert fs["response_converged"] == 1 and fs["forces_scf_response"] == 1
+    F = F.cpu().numpy()
+    d0, m0 = delta.clone(), m.clone()
+
+    def energy(p):
+        ctx.build(p, w.cell, w.pbc)
+        _, s = ctx.energy(delta=d0.clone(), m=m0.clone())
+        assert s["scf_converged"] == 1
+        return s["e_total"]
+
+    h = 1e-4
+    for (i, c) in [(0, 1), (2000, 0)]:
         p, q = w.pos.copy(), w.pos.copy()
         p[i, c] += h
         q[i, c] -= h
