@@ -141,18 +141,25 @@ constexpr int NPAR = 64;  // partial sums per block: 3 + h(h+1)/2 + 2h + 1 <= 64
 
 __device__ __forceinline__ int hslot(int it, int S1) { return ((it % S1) + S1) % S1; }
 
+// HH: the history depth of this update (min(it, hist) for Anderson, 0 for
+// linear mixing), a template argument so that the per-thread sums, the
+// history differences and the normal equations stay in registers.
+template <int HH>
 __global__ void __launch_bounds__(RT) k_scf_residual(ScfArgs A) {
-  __shared__ double sh[NPAR][RT / 32];
-  __shared__ bool last;
-  const int H = A.hist, S1 = H + 1;
-  const int h = A.mixer == 1 ? (A.it < H ? A.it : H) : 0;
-  const int slot = hslot(A.it, S1);
-  const int nA = h * (h + 1) / 2;  // A_jl, j <= l
+  constexpr int h = HH;
+  constexpr int nA = h * (h + 1) / 2;  // A_jl, j <= l
   // acc: [0] max|res| [1] max|dm| [2] sum F_delta (or sum delta_new) [3..3+nA) A
   //      [3+nA .. 3+nA+h) b_j   [3+nA+h .. 3+nA+2h) sum dF_j (delta part)
-  const int nv = 3 + nA + 2 * h;
-  double acc[NPAR];
-  for (int q = 0; q < NPAR; q++) acc[q] = 0.0;
+  constexpr int nv = 3 + nA + 2 * h;
+  static_assert(nv <= NPAR, "partials per block");
+  __shared__ double sh[nv][RT / 32];
+  __shared__ double tot_s[nv];
+  __shared__ bool last;
+  const int S1 = A.hist + 1;
+  const int slot = hslot(A.it, S1);
+  double acc[nv];
+#pragma unroll
+  for (int q = 0; q < nv; q++) acc[q] = 0.0;
   const int ncomp = A.mode == 2 ? 2 : 1;
   for (int i = blockIdx.x * RT + threadIdx.x; i < A.n; i += gridDim.x * RT) {
     double Ni = 0.0, di = 0.0;
@@ -194,24 +201,30 @@ __global__ void __launch_bounds__(RT) k_scf_residual(ScfArgs A) {
       const double fk = c == 0 ? Fd : Fm;
       A.hx[(size_t)slot * n2 + idx] = c == 0 ? A.delta[i] : A.m[i];
       A.hf[(size_t)slot * n2 + idx] = fk;
-      double df[8];
+      double df[h > 0 ? h : 1];
+#pragma unroll
       for (int j = 0; j < h; j++) {
         const int s0 = hslot(A.it - h + j, S1), s1 = hslot(A.it - h + j + 1, S1);
         const double f1 = (j == h - 1) ? fk : A.hf[(size_t)s1 * n2 + idx];
         df[j] = f1 - A.hf[(size_t)s0 * n2 + idx];
       }
-      int q = 3;
+#pragma unroll
       for (int j = 0; j < h; j++)
-        for (int l = j; l < h; l++) acc[q++] += df[j] * df[l];
+#pragma unroll
+        for (int l = j; l < h; l++) acc[3 + j * h - j * (j - 1) / 2 + (l - j)] += df[j] * df[l];
+#pragma unroll
       for (int j = 0; j < h; j++) acc[3 + nA + j] += df[j] * fk;
       if (c == 0) {
         acc[2] += fk;
+#pragma unroll
         for (int j = 0; j < h; j++) acc[3 + nA + h + j] += df[j];
       }
     }
   }
-  // block reduction: max for [0], [1], sums for the rest
+  // block reduction: max for [0], [1], sums for the rest (a fixed shuffle
+  // tree per quantity, then one thread per quantity over the warps in order)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
   for (int q = 0; q < nv; q++) {
     double v = acc[q];
     for (int o = 16; o > 0; o >>= 1) {
@@ -221,19 +234,18 @@ __global__ void __launch_bounds__(RT) k_scf_residual(ScfArgs A) {
     if (lane == 0) sh[q][wid] = v;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < nv; q++) {
-      double v = q < 2 ? 0.0 : 0.0;
-      for (int w = 0; w < RT / 32; w++) v = q < 2 ? fmax(v, sh[q][w]) : v + sh[q][w];
-      A.red[(size_t)NPAR * blockIdx.x + q] = v;
-    }
+  if (threadIdx.x < nv) {
+    const int q = threadIdx.x;
+    double v = 0.0;
+    for (int w = 0; w < RT / 32; w++) v = q < 2 ? fmax(v, sh[q][w]) : v + sh[q][w];
+    A.red[(size_t)NPAR * blockIdx.x + q] = v;
     __threadfence();
-    last = atomicAdd(A.counter, 1u) == gridDim.x - 1;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(A.counter, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!last) return;
   // one thread per reduced quantity, blocks in ascending order (fixed order)
-  __shared__ double tot_s[NPAR];
   if (threadIdx.x < nv) {
     const int q = threadIdx.x;
     double v = 0.0;
@@ -245,61 +257,77 @@ __global__ void __launch_bounds__(RT) k_scf_residual(ScfArgs A) {
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  double tot[NPAR];
-  for (int q = 0; q < nv; q++) tot[q] = tot_s[q];
-  const bool conv = tot[0] < A.tol && (A.mode != 2 || tot[1] < 10.0 * A.tol);
-  A.result[0] = tot[0];
-  A.result[1] = tot[1];
+  const bool conv = tot_s[0] < A.tol && (A.mode != 2 || tot_s[1] < 10.0 * A.tol);
+  A.result[0] = tot_s[0];
+  A.result[1] = tot_s[1];
   A.result[2] = conv ? 1.0 : 0.0;
-  if (A.mixer == 0) {
-    A.result[3] = tot[2] / A.n;  // mean of delta_new
+  if (A.mixer == 0 || h == 0) {
+    A.result[3] = tot_s[2] / A.n;  // mean of delta_new (linear) or of x + F (no history yet)
   } else {
     // normal equations of the least-squares problem, Gaussian elimination
-    double G[8][9];
+    // with partial pivoting (row exchanges as predicated swaps of fixed rows)
+    double G[h > 0 ? h : 1][h + 1];
     double dmax = 0.0;
-    int q = 3;
+#pragma unroll
     for (int j = 0; j < h; j++)
+#pragma unroll
       for (int l = j; l < h; l++) {
-        G[j][l] = G[l][j] = tot[q++];
-        if (j == l) dmax = fmax(dmax, tot[q - 1]);
+        const double g = tot_s[3 + j * h - j * (j - 1) / 2 + (l - j)];
+        G[j][l] = g;
+        G[l][j] = g;
+        if (j == l) dmax = fmax(dmax, g);
       }
+#pragma unroll
     for (int j = 0; j < h; j++) {
-      G[j][h] = tot[3 + nA + j];
+      G[j][h] = tot_s[3 + nA + j];
       G[j][j] += 1e-12 * dmax + 1e-300;
     }
     bool ok = true;
-    for (int c = 0; c < h && ok; c++) {
+#pragma unroll
+    for (int c = 0; c < h; c++) {
       int pr = c;
+      double best = fabs(G[c][c]);
+#pragma unroll
       for (int r = c + 1; r < h; r++)
-        if (fabs(G[r][c]) > fabs(G[pr][c])) pr = r;
-      if (!(fabs(G[pr][c]) > 0.0)) {
-        ok = false;
-        break;
-      }
-      if (pr != c)
-        for (int k = 0; k <= h; k++) {
-          double t = G[c][k];
-          G[c][k] = G[pr][k];
-          G[pr][k] = t;
+        if (fabs(G[r][c]) > best) {
+          best = fabs(G[r][c]);
+          pr = r;
         }
-      for (int r = c + 1; r < h; r++) {
-        const double f = G[r][c] / G[c][c];
-        for (int k = c; k <= h; k++) G[r][k] -= f * G[c][k];
+      if (!(best > 0.0)) ok = false;
+#pragma unroll
+      for (int r = c + 1; r < h; r++)
+        if (r == pr)
+#pragma unroll
+          for (int k = 0; k <= h; k++) {
+            const double t = G[c][k];
+            G[c][k] = G[r][k];
+            G[r][k] = t;
+          }
+      if (ok) {
+#pragma unroll
+        for (int r = c + 1; r < h; r++) {
+          const double f = G[r][c] / G[c][c];
+#pragma unroll
+          for (int k = c; k <= h; k++) G[r][k] -= f * G[c][k];
+        }
       }
     }
-    double gam[8];
+    double gam[h > 0 ? h : 1];
+#pragma unroll
     for (int j = h - 1; j >= 0; j--) {
       double v = ok ? G[j][h] : 0.0;
       if (ok) {
+#pragma unroll
         for (int k = j + 1; k < h; k++) v -= G[j][k] * gam[k];
         v /= G[j][j];
       }
       gam[j] = isfinite(v) ? v : 0.0;
     }
-    double mean = tot[2];
+    double mean = tot_s[2];
+#pragma unroll
     for (int j = 0; j < h; j++) {
       A.gamma[j] = gam[j];
-      mean -= gam[j] * tot[3 + nA + h + j];
+      mean -= gam[j] * tot_s[3 + nA + h + j];
     }
     A.result[3] = mean / A.n;  // mean of the updated delta before the gauge shift
   }
@@ -425,7 +453,20 @@ int launch_fermi(int M, const double* D, const double* gsig, const double* a_inf
 
 
 int launch_scf_residual(const ScfArgs& a, cudaStream_t s) {
-  k_scf_residual<<<red_grid(a.n), RT, 0, s>>>(a);
+  const int h = a.mixer == 1 ? (a.it < a.hist ? a.it : a.hist) : 0;
+  const int g = red_grid(a.n);
+  switch (h) {
+    case 0: k_scf_residual<0><<<g, RT, 0, s>>>(a); break;
+    case 1: k_scf_residual<1><<<g, RT, 0, s>>>(a); break;
+    case 2: k_scf_residual<2><<<g, RT, 0, s>>>(a); break;
+    case 3: k_scf_residual<3><<<g, RT, 0, s>>>(a); break;
+    case 4: k_scf_residual<4><<<g, RT, 0, s>>>(a); break;
+    case 5: k_scf_residual<5><<<g, RT, 0, s>>>(a); break;
+    case 6: k_scf_residual<6><<<g, RT, 0, s>>>(a); break;
+    case 7: k_scf_residual<7><<<g, RT, 0, s>>>(a); break;
+    case 8: k_scf_residual<8><<<g, RT, 0, s>>>(a); break;
+    default: return -1;
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
