@@ -203,6 +203,20 @@ cudaStream_t S_(bop_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 // oracle against < 5e-4 with FP64 recurrences), so they stay FP64 there.
 bool sig32_mode(const bop_ctx* c) { return !c->fp64 && c->S == 1; }
 
+// Stopping rule of the Fermi search: a Newton step shorter than this.  The
+// root is then known to about C tol^2 (C = |N''| / 2N', of order 10 per eV
+// for the Jackson-damped DOS), far inside tol, while the N and DOS stored
+// per orbital are those of the last evaluation, within tol of E_F: that
+// bounds the SCF residual they feed (the energy, the weights and the E_F
+// response are evaluated at E_F itself).  FP64 mode: 1e-13 eV.  FP32
+// products: 1e-6 eV, or 1e-2 of the SCF tolerance when that is smaller.
+double fermi_tol(const bop_ctx* c) {
+  if (c->fp64) return FERMI_TOL;
+  double t = 1e-6;
+  if (c->m.scf != BOP_SCF_NONE) t = std::fmin(t, 1e-2 * c->m.scf_tol);
+  return std::fmax(t, FERMI_TOL);
+}
+
 constexpr size_t PIN_BYTES = 16384;
 
 // The small device-to-host reads of one synchronisation point: each lands in
@@ -809,7 +823,8 @@ int fermi_distributed(bop_ctx* c, int warm, cudaStream_t s) {
   FermiState fs;
   memset(&fs, 0, sizeof(fs));
   double ef = 0.5 * (lo + hi);
-  bool done = hi - lo < FERMI_TOL;
+  const double ftol = fermi_tol(c);
+  bool done = hi - lo < ftol;
   while (!done) {
     CKS(eval(1, E));
     const double f = c->sfac * v[0] - target, fp = c->sfac * v[1];
@@ -822,7 +837,7 @@ int fermi_distributed(bop_ctx* c, int warm, cudaStream_t s) {
     else hi = E;
     double xn = fp > 0.0 ? E - f / fp : lo - 1.0;
     if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-    if (std::fabs(xn - E) < FERMI_TOL || hi - lo < FERMI_TOL || fs.iters >= FERMI_MAX_ROUNDS) {
+    if (std::fabs(xn - E) < ftol || hi - lo < ftol || fs.iters >= FERMI_MAX_ROUNDS) {
       ef = xn;
       done = true;
     } else {
@@ -868,7 +883,7 @@ int fermi_and_N(bop_ctx* c, int warm, cudaStream_t s) {
     Region R(c, PK_FERMI, 1, s);
     const int r = launch_fermi_coop(M, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf),
                                     P<double>(c->b_inf), c->n_exp, c->sfac, target, P<FermiState>(c->fstate),
-                                    P<double>(c->partials), warm, FERMI_MAX_ROUNDS, FERMI_TOL, P<double>(c->N),
+                                    P<double>(c->partials), warm, FERMI_MAX_ROUNDS, fermi_tol(c), P<double>(c->N),
                                     P<double>(c->dos), s, gs32);
     if (r == 0) return BOP_OK;
     if (r != -2) return fail(c, BOP_ERR_CUDA, "fermi launch failed");
@@ -878,7 +893,7 @@ int fermi_and_N(bop_ctx* c, int warm, cudaStream_t s) {
     Region R(c, PK_FERMI, 1 + rounds, s);
     if (launch_fermi_newton(M, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf), P<double>(c->b_inf),
                             c->n_exp, c->sfac, target, P<FermiState>(c->fstate), P<double>(c->partials),
-                            P<unsigned>(c->counter), warm, rounds, FERMI_MAX_ROUNDS, FERMI_TOL, s))
+                            P<unsigned>(c->counter), warm, rounds, FERMI_MAX_ROUNDS, fermi_tol(c), s))
       return fail(c, BOP_ERR_CUDA, "fermi launch failed");
   }
   Region R(c, PK_NU, 1, s);
@@ -895,7 +910,7 @@ int fermi_more(bop_ctx* c, cudaStream_t s) {
     Region R(c, PK_FERMI, FERMI_ROUNDS_MORE, s);
     if (launch_fermi_more(M, P<double>(c->gsig), P<double>(c->ginv), P<double>(c->a_inf), P<double>(c->b_inf),
                           c->n_exp, c->sfac, c->m.n_e * c->nc, P<FermiState>(c->fstate), P<double>(c->partials),
-                          P<unsigned>(c->counter), FERMI_ROUNDS_MORE, FERMI_MAX_ROUNDS, FERMI_TOL, s))
+                          P<unsigned>(c->counter), FERMI_ROUNDS_MORE, FERMI_MAX_ROUNDS, fermi_tol(c), s))
       return fail(c, BOP_ERR_CUDA, "fermi launch failed");
   }
   Region R(c, PK_NU, 1, s);
